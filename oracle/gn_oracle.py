@@ -1,0 +1,363 @@
+"""Plain FP64 CPU oracle for generalized Nystrom (GN), its stabilised form (SGN)
+and the HMT range finder.  TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this module.  The library's CUDA path never calls it and shares no code with
+it; the two meet only at the seeded inputs drawn by ``gn_synth``.
+
+Everything here is numpy in FP64, written to be read against the paper
+(Nakatsukasa, "Fast and stable randomized low-rank matrix approximation",
+arXiv:2009.11392).  Citations name the paper's sections, equations and
+algorithms.  Library primitives used as single steps: matrix products (``@``)
+and, for cross-checks only, LAPACK's SVD / pseudoinverse.  The Householder QR,
+the epsilon-truncation, the second QR, the triangular solves, the norm
+estimator and the adjoint are written out step by step here.
+
+Every function is pinned by a CPU test (tests/test_oracle_pins.py) against a
+fact the paper or the mathematics fixes (exact recovery, Eckart-Young,
+interpolation, invariance, SVD-based epsilon-pinv, hand-derived worked
+examples, finite differences).  No function is "parity unpinned".
+"""
+from __future__ import annotations
+
+import numpy as np
+
+U64 = 2.0 ** -53          # unit roundoff of IEEE double
+U32 = 2.0 ** -24          # unit roundoff of IEEE single (FP32 accumulation)
+
+PLAIN, SGN, AUTO = 0, 1, 2
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2, step 2: the two sketches
+# ---------------------------------------------------------------------------
+def sketch(A, X, Y):
+    """AX (m x r) and Y^T A ((r+l) x n): Algorithm 2, step 2 (Section 2)."""
+    A = np.asarray(A, dtype=np.float64)
+    return A @ np.asarray(X, np.float64), np.asarray(Y, np.float64).T @ A
+
+
+def core_matrix(YtA, X):
+    """C = (Y^T A) X, the (r+l) x r core (Algorithm 2 step 2; Section 2.3)."""
+    return np.asarray(YtA, np.float64) @ np.asarray(X, np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Householder QR (Algorithm 2 step 2, "QR factorization Y^T A X = QR")
+# ---------------------------------------------------------------------------
+def householder_qr(C):
+    """Thin Householder QR, C = Q R, Q (M x N) orthonormal columns, R (N x N).
+
+    Column j is reflected by H_j = I - tau_j v_j v_j^T with v_j[0] = 1, the
+    reflector that maps x = C[j:, j] to beta e_1 with beta = -sign(x_0)||x||
+    (sign(0) = +1).  When x[1:] is already zero no reflection is applied
+    (tau = 0).  Q is accumulated backwards from [I; 0].  Finally diag(R) is
+    made non-negative by flipping rows of R and the matching columns of Q, so
+    that Q and R are unique for a full-rank C.
+    """
+    W = np.array(C, dtype=np.float64, copy=True)
+    M, N = W.shape
+    if M < N:
+        raise ValueError("householder_qr needs a tall or square matrix")
+    V = np.zeros((M, N))
+    tau = np.zeros(N)
+    for j in range(N):
+        x = W[j:, j].copy()
+        alpha = x[0]
+        tail = float(np.dot(x[1:], x[1:]))
+        v = np.zeros(M - j)
+        v[0] = 1.0
+        if tail == 0.0:
+            t = 0.0
+            beta = alpha
+        else:
+            normx = np.sqrt(alpha * alpha + tail)
+            beta = -normx if alpha >= 0.0 else normx
+            v[1:] = x[1:] / (alpha - beta)
+            t = (beta - alpha) / beta
+        if t != 0.0:
+            w = v @ W[j:, j:]
+            W[j:, j:] -= t * np.outer(v, w)
+        W[j, j] = beta
+        W[j + 1:, j] = 0.0
+        V[j:, j] = v
+        tau[j] = t
+    R = np.triu(W[:N, :])
+    Q = np.zeros((M, N))
+    Q[:N, :N] = np.eye(N)
+    for j in range(N - 1, -1, -1):
+        if tau[j] == 0.0:
+            continue
+        v = V[j:, j]
+        w = v @ Q[j:, :]
+        Q[j:, :] -= tau[j] * np.outer(v, w)
+    s = np.where(np.diag(R) < 0.0, -1.0, 1.0)
+    return Q * s[None, :], s[:, None] * R
+
+
+# ---------------------------------------------------------------------------
+# Section 5.1.1: epsilon-truncation of R and the second QR
+# ---------------------------------------------------------------------------
+def truncation_rank(R, eps):
+    """k = index of the first diagonal entry of R with |R_ii| <= eps (k = N if none).
+
+    Section 5.1.1 truncates the bottom-right corner of R where its diagonal
+    falls below eps; an entry equal to eps counts as dropped."""
+    d = np.abs(np.diag(R))
+    small = np.nonzero(d <= eps)[0]
+    return int(small[0]) if small.size else R.shape[0]
+
+
+def rinv_norm_estimate(R, iters=20):
+    """Power-method estimate of ||R^{-1}||_2 (Section 5.1.2).
+
+    Iterates z <- R^{-1} R^{-T} z from the all-ones start, each step two
+    triangular solves (O(r^2)); returns sqrt(||z_{k+1}|| / ||z_k||) with z_k of
+    unit norm.  A zero on the diagonal of R gives +inf."""
+    R = np.asarray(R, np.float64)
+    if np.any(np.diag(R) == 0.0):
+        return np.inf
+    z = np.ones(R.shape[0]) / np.sqrt(R.shape[0])
+    est = 0.0
+    with np.errstate(over="ignore", invalid="ignore"):
+        for _ in range(iters):
+            y = forward_subst_lower(R.T, z)          # R^T y = z
+            w = back_subst_upper(R, y)               # R w = y
+            nw = np.linalg.norm(w)
+            if not np.isfinite(nw):
+                return np.inf
+            est = np.sqrt(nw)
+            if nw == 0.0:
+                break
+            z = w / nw
+    return float(est)
+
+
+def forward_subst_lower(L, b):
+    """Solve L x = b for lower-triangular L (vector b), row by row."""
+    n = L.shape[0]
+    x = np.zeros(n)
+    for i in range(n):
+        x[i] = (b[i] - L[i, :i] @ x[:i]) / L[i, i]
+    return x
+
+
+def back_subst_upper(U, b):
+    """Solve U x = b for upper-triangular U (vector b), bottom row first."""
+    n = U.shape[0]
+    x = np.zeros(n)
+    for i in range(n - 1, -1, -1):
+        x[i] = (b[i] - U[i, i + 1:] @ x[i + 1:]) / U[i, i]
+    return x
+
+
+def right_solve_upper(B, R):
+    """F with F R = B, R upper triangular (k x k): F = B R^{-1}, column by column.
+
+    Column j of F R is sum_{i<=j} F[:, i] R[i, j], so F[:, j] follows from the
+    earlier columns (eq. 5.1's AX/R).  Each row of F is an independent
+    triangular solve, the row-wise structure Theorem 4.1 relies on."""
+    B = np.asarray(B, np.float64)
+    k = R.shape[0]
+    F = np.zeros((B.shape[0], k))
+    for j in range(k):
+        F[:, j] = (B[:, j] - F[:, :j] @ R[:j, j]) / R[j, j]
+    return F
+
+
+def right_solve_upper_transpose(B, R2):
+    """F with F R2^T = B, R2 upper triangular (k x k): F = B R2^{-T}.
+
+    (F R2^T)[:, j] = sum_{i>=j} F[:, i] R2[j, i], so columns are found from the
+    last one backwards."""
+    B = np.asarray(B, np.float64)
+    k = R2.shape[0]
+    F = np.zeros((B.shape[0], k))
+    for j in range(k - 1, -1, -1):
+        F[:, j] = (B[:, j] - F[:, j + 1:] @ R2[j, j + 1:]) / R2[j, j]
+    return F
+
+
+def core(YtA, X, eps, mode=AUTO, C=None):
+    """Core of (S)GN: C = (Y^T A)X, C = QR, truncation, second QR.
+
+    mode PLAIN: k = r, the pseudoinverse is R^{-1} Q^T (eq. 5.1).
+    mode SGN:   k = truncation_rank(R, eps); if k < r, R_1 = R[:k, :] and the
+                QR R_1^T = Q_2 R_2 gives (Y^T A X)_eps^+ = Q_2 R_2^{-T} Q_1^T
+                (Section 5.1.1; the transpose on R_2 follows from
+                Q_1 R_1 = Q_1 R_2^T Q_2^T).
+    mode AUTO:  the detector of Section 5.1.2: SGN when the power-method
+                estimate of ||R^{-1}||_2 is at least 1/eps, else PLAIN.
+    Returns a dict with C, Q, R, k, Q2, R2 (None when k = r), rinv_est, sgn.
+    """
+    if C is None:
+        C = core_matrix(YtA, X)
+    Q, R = householder_qr(C)
+    r = R.shape[0]
+    est = rinv_norm_estimate(R)
+    if mode == PLAIN:
+        use_sgn = False
+    elif mode == SGN:
+        use_sgn = True
+    else:
+        use_sgn = bool(eps > 0.0 and est * eps >= 1.0)
+    k = truncation_rank(R, eps) if use_sgn else r
+    Q2 = R2 = None
+    if k < r:
+        Q2, R2 = householder_qr(R[:k, :].T)
+    return dict(C=C, Q=Q, R=R, k=k, Q2=Q2, R2=R2, rinv_est=est, sgn=use_sgn)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2, step 3 and eq. 5.1: the factors, multiplied in the stable order
+# ---------------------------------------------------------------------------
+def factors(AX, YtA, c):
+    """F = (AX) R^{-1} (or (AX) Q_2 R_2^{-T} after truncation), G = Q_1^T (Y^T A).
+
+    Never forms the core pseudoinverse (Section 5.1, the order rule)."""
+    k = c["k"]
+    if c["Q2"] is None:
+        F = right_solve_upper(AX, c["R"])
+    else:
+        F = right_solve_upper_transpose(np.asarray(AX, np.float64) @ c["Q2"], c["R2"])
+    G = c["Q"][:, :k].T @ np.asarray(YtA, np.float64)
+    return F, G
+
+
+def gn(A, X, Y, eps=0.0, mode=AUTO):
+    """Full (S)GN: returns (Ahat, parts) with Ahat = F G, F and G as above."""
+    AX, YtA = sketch(A, X, Y)
+    c = core(YtA, X, eps, mode)
+    F, G = factors(AX, YtA, c)
+    return F @ G, dict(AX=AX, YtA=YtA, F=F, G=G, **c)
+
+
+def error_fro(A, F, G):
+    """||A - F G||_F (the accuracy measure of Section 7.1)."""
+    return float(np.linalg.norm(np.asarray(A, np.float64) - F @ G))
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 (HMT) and the comparison forms used only as cross-checks
+# ---------------------------------------------------------------------------
+def hmt(A, X):
+    """HMT range finder (Algorithm 1): Q = orth(AX) by Householder QR, B = Q^T A.
+
+    Returns (Q, B); the approximant is Q B.  The optional small SVD of B in
+    step 4 does not change Q B and is omitted."""
+    A = np.asarray(A, np.float64)
+    Q, _ = householder_qr(A @ np.asarray(X, np.float64))
+    return Q, Q.T @ A
+
+
+def gn_definition(A, X, Y):
+    """The plain definition AX (Y^T A X)^+ Y^T A of eq. 2.1, via LAPACK pinv.
+
+    Numerically unsafe in general (Section 5.1's footnote); cross-check only on
+    well-conditioned inputs."""
+    A = np.asarray(A, np.float64)
+    AX = A @ X
+    return AX @ np.linalg.pinv(Y.T @ AX) @ (Y.T @ A)
+
+
+def sgn_svd(A, X, Y, eps):
+    """SGN with the SVD-based epsilon-pseudoinverse (Section 2, eq. 2.2 and
+    Section 5.1.1): drop singular values of Y^T A X that are <= eps."""
+    A = np.asarray(A, np.float64)
+    AX = A @ X
+    YtA = Y.T @ A
+    U, s, Vt = np.linalg.svd(YtA @ X, full_matrices=False)
+    keep = s > eps
+    core_pinv = (Vt[keep].T / s[keep]) @ U[:, keep].T
+    return (AX @ core_pinv) @ YtA
+
+
+def tropp17(A, X, Y):
+    """Q (Y^T Q)^+ Y^T A with Q = orth(AX): mathematically equal to GN
+    (Section 2.4.1 and Section 7.1)."""
+    A = np.asarray(A, np.float64)
+    Q, _ = householder_qr(A @ X)
+    return Q @ (np.linalg.pinv(Y.T @ Q) @ (Y.T @ A))
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of A -> Ahat (plain GN, full-rank core); derivation in the docstring
+# ---------------------------------------------------------------------------
+def gn_backward(A, X, Y, Gup):
+    """Gradient of L(A) = <Gup, Ahat(A)> for plain GN with X, Y fixed.
+
+    With C = Y^T A X = QR of full column rank, C^+ = R^{-1} Q^T and
+    d(C^+) = -C^+ dC C^+ + (C^T C)^{-1} dC^T (I - C C^+).  Collecting the three
+    places A enters Ahat = AX C^+ Y^T A gives
+
+        grad = (S1 Q R^{-T} + Y K) X^T + Y (Q S2),
+        S1 = Gup (Y^T A)^T,  F = AX R^{-1},  S2 = F^T Gup,  W = F^T S1,
+        K  = (I - Q Q^T) W^T R^{-T} - Q W Q R^{-T}.
+
+    Every C^+ appears through Q and triangular solves with R, never an explicit
+    inverse (the paper's Section 5.1 rule)."""
+    A = np.asarray(A, np.float64)
+    AX, YtA = sketch(A, X, Y)
+    Q, R = householder_qr(YtA @ X)
+    F = right_solve_upper(AX, R)                  # AX R^{-1}
+    S1 = Gup @ YtA.T                              # m x (r+l)
+    S2 = F.T @ Gup                                # r x n
+    W = F.T @ S1                                  # r x (r+l)
+    # M R^{-T} for a matrix M is the transpose of the solve R^{-1} M^T ... written
+    # as a right solve with R^T:  Z R^T = M  <=>  Z = M R^{-T}.
+    S1Q_RinvT = right_solve_upper_transpose(S1 @ Q, R)
+    Wt_RinvT = right_solve_upper_transpose(W.T, R)          # W^T R^{-T}
+    WQ_RinvT = right_solve_upper_transpose(W @ Q, R)        # W Q R^{-T}
+    K = Wt_RinvT - Q @ (Q.T @ Wt_RinvT) - Q @ WQ_RinvT
+    return (S1Q_RinvT + Y @ K) @ X.T + Y @ (Q @ S2)
+
+
+def gn_loss(A, X, Y, Gup):
+    """<Gup, Ahat> for plain GN; used by the finite-difference pin."""
+    Ahat, _ = gn(A, X, Y, 0.0, PLAIN)
+    return float(np.sum(Gup * Ahat))
+
+
+# ---------------------------------------------------------------------------
+# Operand quantisation of the mixed-precision path (matched inputs)
+# ---------------------------------------------------------------------------
+def quantize_bf16(x):
+    """Round to bfloat16 and return the exact FP64 value of the result.
+
+    FP64 -> FP32 (round to nearest even) -> BF16 (round to nearest even on the
+    upper 16 bits of the FP32 pattern).  Values stay finite in this code's
+    range; NaN handling is not needed for the synthetic inputs."""
+    f = np.asarray(x, np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def split_bf16(x):
+    """hi + lo split of the FP32-rounded value: hi = bf16(x), lo = bf16(x - hi)."""
+    f = np.asarray(x, np.float64).astype(np.float32).astype(np.float64)
+    hi = quantize_bf16(f)
+    lo = quantize_bf16(f - hi)
+    return hi, lo
+
+
+def scale_eps(A_norm2, X_norm2, Y_norm2, u):
+    """eps = 10 u ||A|| ||X|| ||Y||, the scale-consistent threshold (Section 4.1's
+    'eps = 10u' for ||A|| = 1 and O(1) sketches, rescaled to the actual norms)."""
+    return 10.0 * u * A_norm2 * X_norm2 * Y_norm2
+
+
+def norm2_estimate(M, iters=30):
+    """Power-iteration estimate of ||M||_2 from the all-ones start."""
+    M = np.asarray(M, np.float64)
+    v = np.ones(M.shape[1]) / np.sqrt(M.shape[1])
+    s = 0.0
+    for _ in range(iters):
+        w = M.T @ (M @ v)
+        nw = np.linalg.norm(w)
+        if nw == 0.0:
+            return 0.0
+        s = np.sqrt(nw)
+        v = w / nw
+    return float(s)

@@ -1,0 +1,374 @@
+"""Pins of the FP64 CPU oracle against facts the paper and the mathematics fix.
+
+Each test names the passage it follows.  None of them re-types an oracle
+formula: they check closed forms, invariants, library routines (LAPACK QR /
+SVD), hand-derived worked examples and finite differences, chosen so that a
+dropped term, a wrong sign, a wrong index or a transposed operand in the oracle
+fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gn_oracle as O
+import gn_synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RNG = np.random.default_rng(12345)
+
+
+def _np(t):
+    return t.numpy() if hasattr(t, "numpy") else np.asarray(t)
+
+
+def _lowrank(m, n, k, seed, decay=None):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, k)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    s = np.ones(k) if decay is None else decay
+    return (U * s) @ V.T, s
+
+
+def _sk(m, n, r, l, seed):
+    rng = np.random.default_rng(seed + 1)
+    return rng.standard_normal((n, r)), rng.standard_normal((m, r + l))
+
+
+# --------------------------------------------------------------------------- QR
+@pytest.mark.parametrize("shape", [(7, 5), (30, 20), (120, 80), (64, 64)])
+def test_householder_qr_backward_stable_and_orthonormal(shape):
+    """Textbook Householder: ||C - QR|| <= c u ||C||, ||Q^T Q - I|| <= c u."""
+    C = RNG.standard_normal(shape)
+    Q, R = O.householder_qr(C)
+    u = O.U64
+    assert np.allclose(R, np.triu(R))
+    assert np.all(np.diag(R) >= 0)
+    assert np.linalg.norm(C - Q @ R) <= 50 * u * np.linalg.norm(C) * shape[1]
+    assert np.linalg.norm(Q.T @ Q - np.eye(shape[1])) <= 50 * u * shape[1]
+
+
+def test_householder_qr_matches_lapack_up_to_signs():
+    """LAPACK's R equals ours after making its diagonal non-negative."""
+    C = RNG.standard_normal((50, 30))
+    Ql, Rl = np.linalg.qr(C)
+    s = np.sign(np.diag(Rl))
+    Q, R = O.householder_qr(C)
+    assert np.allclose(R, s[:, None] * Rl, atol=1e-12)
+    assert np.allclose(Q, Ql * s[None, :], atol=1e-12)
+
+
+def test_householder_qr_zero_and_dependent_columns():
+    """A zero column gives R_jj = 0 with no reflection; Q stays orthonormal."""
+    C = RNG.standard_normal((10, 4))
+    C[:, 2] = 0.0
+    Q, R = O.householder_qr(C)
+    assert abs(R[2, 2]) < 1e-15
+    assert np.linalg.norm(C - Q @ R) < 1e-13
+    assert np.linalg.norm(Q.T @ Q - np.eye(4)) < 1e-13
+
+
+def test_householder_reflector_sign_avoids_cancellation():
+    """beta = -sign(alpha)||x|| keeps alpha - beta free of cancellation: on
+    columns that are already almost e_j the computed Q stays orthonormal to
+    roundoff (the other sign choice loses orthogonality here)."""
+    C = np.eye(12, 8) + 1e-9 * RNG.standard_normal((12, 8))
+    Q, R = O.householder_qr(C)
+    assert np.linalg.norm(Q.T @ Q - np.eye(8)) <= 100 * O.U64
+    assert np.linalg.norm(C - Q @ R) <= 100 * O.U64
+
+
+def test_truncation_rank_rule():
+    """Section 5.1.1: k is the first index whose |R_ii| <= eps (ties dropped)."""
+    R = np.diag([3.0, 2.0, 1e-9, 5e-10]) + np.triu(np.ones((4, 4)), 1)
+    assert O.truncation_rank(R, 1e-9) == 2
+    assert O.truncation_rank(R, 0.9e-9) == 3
+    assert O.truncation_rank(R, 1e-12) == 4
+    R2 = np.diag([3.0, -1e-12, 2.0])
+    assert O.truncation_rank(R2, 1e-10) == 1
+
+
+# ----------------------------------------------------- hand-derived worked examples
+@pytest.mark.parametrize("name", ["worked_rank1_r1.json", "worked_rank1_r2_sgn.json"])
+def test_golden_worked_examples(name):
+    g = json.load(open(os.path.join(GOLDEN, name)))
+    A, X, Y = (np.array(g[k], float) for k in ("A", "X", "Y"))
+    mode = {"plain": O.PLAIN, "sgn": O.SGN}[g["mode"]]
+    Ahat, p = O.gn(A, X, Y, g["eps"], mode)
+    e = g["expect"]
+    assert p["k"] == e["k"]
+    for key in ("AX", "YtA", "C", "R", "Q", "F", "G"):
+        if key in e:
+            assert np.allclose(p[key], np.array(e[key]), atol=1e-14), key
+    if "R_row0" in e:
+        assert np.allclose(p["R"][0], e["R_row0"], atol=1e-14)
+        assert np.allclose(p["Q"][:, 0], e["Q_col0"], atol=1e-14)
+        assert np.allclose(p["R2"], e["R2"], atol=1e-14)
+        assert np.allclose(p["Q2"], e["Q2"], atol=1e-14)
+    assert np.allclose(Ahat, np.array(e["Ahat"]), atol=1e-13)
+
+
+# ------------------------------------------------------------ GN: what it must do
+@pytest.mark.parametrize("k0,r,l", [(5, 5, 3), (8, 12, 6), (20, 20, 10)])
+def test_exact_recovery_of_low_rank_inputs(k0, r, l):
+    """rank(A) <= r => range(AX) = range(A) and GN returns A (Section 3.1).
+
+    For k0 < r the core is rank deficient, so SGN (eq. 2.2) is used."""
+    m, n = 80, 60
+    A, _ = _lowrank(m, n, k0, 7)
+    X, Y = _sk(m, n, r, l, 7)
+    mode = O.PLAIN if k0 == r else O.SGN
+    eps = O.scale_eps(1.0, np.linalg.norm(X, 2), np.linalg.norm(Y, 2), O.U64)
+    Ahat, p = O.gn(A, X, Y, eps, mode)
+    assert np.linalg.norm(A - Ahat) / np.linalg.norm(A) < 1e-12
+    if k0 < r:
+        assert p["k"] == k0
+
+
+def test_eckart_young_lower_bound_and_rank():
+    """||A - Ahat||_F >= (sum_{i>r} sigma_i^2)^(1/2) and rank(Ahat) <= r."""
+    m, n, r, l = 60, 40, 8, 4
+    A = RNG.standard_normal((m, n)) * (0.7 ** np.arange(n))[None, :]
+    X, Y = _sk(m, n, r, l, 3)
+    Ahat, _ = O.gn(A, X, Y, 0.0, O.PLAIN)
+    s = np.linalg.svd(A, compute_uv=False)
+    assert np.linalg.norm(A - Ahat) >= np.sqrt(np.sum(s[r:] ** 2)) * (1 - 1e-12)
+    assert np.linalg.norm(A - Ahat, 2) >= s[r] * (1 - 1e-12)
+    sh = np.linalg.svd(Ahat, compute_uv=False)
+    assert sh[r] <= 1e-12 * sh[0]
+
+
+def test_interpolation_AhatX_equals_AX():
+    """eq. (anni): (I - P_{AX,Y}) AX = 0, so Ahat X = AX (Section 3.1)."""
+    m, n, r, l = 50, 40, 6, 3
+    A = RNG.standard_normal((m, n))
+    X, Y = _sk(m, n, r, l, 4)
+    Ahat, _ = O.gn(A, X, Y, 0.0, O.PLAIN)
+    assert np.linalg.norm(Ahat @ X - A @ X) <= 1e-11 * np.linalg.norm(A @ X)
+
+
+def test_invariance_under_sketch_mixing():
+    """P_{XM,YN} = P_{X,Y} (Notation, Section 1).  With a tall core (l > 0) the
+    identity holds for X -> XM; the Y -> YN part needs Y^T A X square (l = 0),
+    because (N^T C)^+ N^T differs from C^+ for a tall C."""
+    m, n, r, l = 45, 35, 5, 3
+    A = RNG.standard_normal((m, n))
+    X, Y = _sk(m, n, r, l, 5)
+    M = np.eye(r) + 0.3 * RNG.standard_normal((r, r))
+    A1, _ = O.gn(A, X, Y, 0.0, O.PLAIN)
+    A2, _ = O.gn(A, X @ M, Y, 0.0, O.PLAIN)
+    assert np.linalg.norm(A1 - A2) <= 1e-10 * np.linalg.norm(A1)
+    Ys = Y[:, :r]
+    N = np.eye(r) + 0.3 * RNG.standard_normal((r, r))
+    B1, _ = O.gn(A, X, Ys, 0.0, O.PLAIN)
+    B2, _ = O.gn(A, X @ M, Ys @ N, 0.0, O.PLAIN)
+    assert np.linalg.norm(B1 - B2) <= 1e-9 * np.linalg.norm(B1)
+
+
+def test_matches_pinv_definition_when_well_conditioned():
+    """The QR route of eq. 5.1 equals the definition of eq. 2.1 (LAPACK pinv)."""
+    m, n, r, l = 40, 30, 6, 3
+    A = RNG.standard_normal((m, n))
+    X, Y = _sk(m, n, r, l, 6)
+    Ahat, _ = O.gn(A, X, Y, 0.0, O.PLAIN)
+    assert np.linalg.norm(Ahat - O.gn_definition(A, X, Y)) <= 1e-11 * np.linalg.norm(Ahat)
+
+
+def test_equals_tropp17():
+    """GN and Q(Y^T Q)^+ Y^T A with Q = orth(AX) agree (Section 7.1)."""
+    m, n, r, l = 70, 50, 10, 5
+    A = RNG.standard_normal((m, n)) * (0.8 ** np.arange(n))[None, :]
+    X, Y = _sk(m, n, r, l, 8)
+    Ahat, _ = O.gn(A, X, Y, 0.0, O.PLAIN)
+    assert np.linalg.norm(Ahat - O.tropp17(A, X, Y)) <= 1e-9 * np.linalg.norm(Ahat)
+
+
+def test_gn_with_Y_equal_AX_is_hmt():
+    """With Y = AX (l = 0), GN = Q Q^T A = HMT (Section 2.4.1)."""
+    m, n, r = 60, 45, 7
+    A = RNG.standard_normal((m, n))
+    X = RNG.standard_normal((n, r))
+    Ahat, _ = O.gn(A, X, A @ X, 0.0, O.PLAIN)
+    Q, B = O.hmt(A, X)
+    assert np.linalg.norm(Ahat - Q @ B) <= 1e-10 * np.linalg.norm(A)
+
+
+def test_sgn_qr_truncation_equals_svd_eps_pinv():
+    """Section 5.1.1: the QR truncation + second QR gives the SVD eps-pinv when
+    there is a gap around eps.  Also fixes the transpose on R_2: the printed
+    R_2^{-1} form disagrees with the SVD by O(1)."""
+    m, n, k0, r, l = 60, 50, 6, 10, 5
+    A, _ = _lowrank(m, n, k0, 9, decay=np.linspace(1.0, 0.1, k0))
+    X, Y = _sk(m, n, r, l, 9)
+    eps = 1e-8 * np.linalg.norm(Y.T @ A @ X, 2)
+    Ahat, p = O.gn(A, X, Y, eps, O.SGN)
+    assert p["k"] == k0
+    ref = O.sgn_svd(A, X, Y, eps)
+    assert np.linalg.norm(Ahat - ref) <= 1e-10 * np.linalg.norm(ref)
+    # the untransposed reading
+    bad = (A @ X) @ (p["Q2"] @ np.linalg.inv(p["R2"]) @ p["Q"][:, :p["k"]].T) @ (Y.T @ A)
+    assert np.linalg.norm(bad - ref) > 1e-3 * np.linalg.norm(ref)
+
+
+def test_sgn_without_truncation_equals_plain():
+    m, n, r, l = 40, 30, 6, 3
+    A = RNG.standard_normal((m, n))
+    X, Y = _sk(m, n, r, l, 10)
+    A1, p1 = O.gn(A, X, Y, 1e-14, O.SGN)
+    A2, _ = O.gn(A, X, Y, 0.0, O.PLAIN)
+    assert p1["k"] == r
+    assert np.linalg.norm(A1 - A2) <= 1e-12 * np.linalg.norm(A1)
+
+
+def test_detector_and_stress_input():
+    """Section 4.2 / 5.1.2: exactly low-rank A makes R's trailing diagonal tiny;
+    the ||R^{-1}|| estimate flags it and AUTO switches to SGN, whose error is
+    at roundoff level."""
+    m, n, k0, r, l = 100, 80, 7, 12, 6
+    A, _ = _lowrank(m, n, k0, 11)
+    X, Y = _sk(m, n, r, l, 11)
+    eps = O.scale_eps(1.0, np.linalg.norm(X, 2), np.linalg.norm(Y, 2), O.U64)
+    Ahat, p = O.gn(A, X, Y, eps, O.AUTO)
+    assert p["sgn"] and p["k"] == k0
+    assert np.linalg.norm(A - Ahat) / np.linalg.norm(A) < 1e-12
+    # on a well-conditioned problem AUTO stays plain
+    B = RNG.standard_normal((m, n))
+    _, q = O.gn(B, X, Y, eps, O.AUTO)
+    assert not q["sgn"] and q["k"] == r
+
+
+def test_rinv_norm_estimate_matches_svd():
+    """Power method on R^{-1} R^{-T} converges to 1/sigma_min(R)."""
+    C = RNG.standard_normal((40, 25)) @ np.diag(np.logspace(0, -6, 25))
+    _, R = O.householder_qr(C)
+    est = O.rinv_norm_estimate(R, iters=200)
+    true = 1.0 / np.linalg.svd(R, compute_uv=False)[-1]
+    assert abs(est - true) <= 1e-6 * true
+    Z = R.copy()
+    Z[3, 3] = 0.0
+    assert O.rinv_norm_estimate(Z) == np.inf
+
+
+def test_triangular_solves_against_library():
+    """F R = B and F R^T = B, checked against LAPACK's triangular solver via
+    numpy.linalg.solve on the dense triangle."""
+    R = np.triu(RNG.standard_normal((9, 9))) + 4 * np.eye(9)
+    B = RNG.standard_normal((13, 9))
+    F1 = O.right_solve_upper(B, R)
+    F2 = O.right_solve_upper_transpose(B, R)
+    assert np.allclose(F1, np.linalg.solve(R.T, B.T).T, atol=1e-12)
+    assert np.allclose(F2, np.linalg.solve(R, B.T).T, atol=1e-12)
+
+
+def test_hmt_orthonormal_and_projection():
+    """Algorithm 1: Q^T Q = I, Q B = Q Q^T A, and ||A - QB|| >= sigma_{r+1}."""
+    m, n, r = 70, 40, 9
+    A = RNG.standard_normal((m, n)) * (0.75 ** np.arange(n))[None, :]
+    X = RNG.standard_normal((n, r))
+    Q, B = O.hmt(A, X)
+    assert np.linalg.norm(Q.T @ Q - np.eye(r)) < 1e-13
+    Qa, _ = np.linalg.qr(A @ X)
+    assert np.linalg.norm(Q @ B - Qa @ (Qa.T @ A)) < 1e-12 * np.linalg.norm(A)
+    s = np.linalg.svd(A, compute_uv=False)
+    assert np.linalg.norm(A - Q @ B, 2) >= s[r] * (1 - 1e-12)
+
+
+def test_expected_error_bounds_over_seeds():
+    """Theorems 3.1 and 3.2 in expectation (20 seeds): the HMT error is within
+    sqrt(1 + r/(r - rhat - 1)) of the best rank-rhat error, and GN's is within
+    sqrt(1 + (r+l)/(l-1)) of HMT's root-mean-square error."""
+    m, n, r, l, rhat = 120, 90, 16, 8, 8
+    rng = np.random.default_rng(21)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = 0.8 ** np.arange(n)
+    A = (U * s) @ V.T
+    e_gn, e_hmt2 = [], []
+    for t in range(20):
+        X, Y = _sk(m, n, r, l, 100 + t)
+        Ahat, _ = O.gn(A, X, Y, 0.0, O.PLAIN)
+        Q, B = O.hmt(A, X)
+        e_gn.append(np.linalg.norm(A - Ahat))
+        e_hmt2.append(np.linalg.norm(A - Q @ B) ** 2)
+    tail = np.sqrt(np.sum(s[rhat:] ** 2))
+    hmt_rms = np.sqrt(np.mean(e_hmt2))
+    assert hmt_rms <= np.sqrt(1 + r / (r - rhat - 1)) * tail * 1.05
+    assert np.mean(e_gn) <= np.sqrt(1 + (r + l) / (l - 1)) * hmt_rms * 1.05
+
+
+def test_config1_error_above_truncated_svd_tail():
+    """The 1000 x 500 geometric case: sigma is known by construction, so the
+    GN error is at least the tail (sum_{i>20} sigma_i^2)^(1/2) and, by
+    Theorem 3.2, not far above it."""
+    p = gn_synth.config1()
+    A, X, Y = _np(p.a), _np(p.x), _np(p.y)
+    Ahat, q = O.gn(A, X, Y, p.eps, O.AUTO)
+    s = 2.0 ** (-np.arange(1, 501) / 10.0)
+    tail = np.sqrt(np.sum(s[p.r:] ** 2))
+    err = np.linalg.norm(A - Ahat)
+    assert tail * (1 - 1e-9) <= err <= 6 * tail
+    assert q["k"] == p.r and not q["sgn"]
+
+
+def test_adjoint_matches_central_differences():
+    """Gradient of <G, Ahat> (plain GN, X and Y fixed) against central
+    differences in FP64 on 64 x 48, r = 8, l = 4: 16 random directions and 200
+    single entries."""
+    m, n, r, l = 64, 48, 8, 4
+    rng = np.random.default_rng(31)
+    A = rng.standard_normal((m, n)) * (0.9 ** np.arange(n))[None, :]
+    X, Y = rng.standard_normal((n, r)), rng.standard_normal((m, r + l))
+    G = rng.standard_normal((m, n))
+    grad = O.gn_backward(A, X, Y, G)
+    h = 1e-6 * np.linalg.norm(A)
+    for _ in range(16):
+        D = rng.standard_normal((m, n))
+        D /= np.linalg.norm(D)
+        fd = (O.gn_loss(A + h * D, X, Y, G) - O.gn_loss(A - h * D, X, Y, G)) / (2 * h)
+        an = np.sum(grad * D)
+        assert abs(fd - an) <= 1e-6 * max(1.0, np.linalg.norm(grad))
+    idx = rng.choice(m * n, size=200, replace=False)
+    for f in idx:
+        i, j = divmod(int(f), n)
+        E = np.zeros((m, n))
+        E[i, j] = 1.0
+        fd = (O.gn_loss(A + h * E, X, Y, G) - O.gn_loss(A - h * E, X, Y, G)) / (2 * h)
+        assert abs(fd - grad[i, j]) <= 1e-6 * max(1.0, np.linalg.norm(grad))
+
+
+def test_adjoint_linear_in_G_and_zero_for_zero_G():
+    m, n, r, l = 20, 15, 4, 2
+    rng = np.random.default_rng(32)
+    A = rng.standard_normal((m, n))
+    X, Y = rng.standard_normal((n, r)), rng.standard_normal((m, r + l))
+    G1, G2 = rng.standard_normal((m, n)), rng.standard_normal((m, n))
+    g1, g2 = O.gn_backward(A, X, Y, G1), O.gn_backward(A, X, Y, G2)
+    g12 = O.gn_backward(A, X, Y, 2 * G1 - G2)
+    assert np.allclose(g12, 2 * g1 - g2, atol=1e-9)
+    assert np.allclose(O.gn_backward(A, X, Y, 0 * G1), 0.0)
+
+
+# -------------------------------------------------------------- quantisation
+def test_quantize_bf16_against_torch():
+    """Round to nearest even on the FP32 pattern equals torch's bfloat16 cast
+    of the FP32 value, and integers below 256 are exact."""
+    import torch
+    x = RNG.standard_normal(10000) * 10.0 ** RNG.integers(-6, 6, 10000)
+    f32 = torch.tensor(x).to(torch.float32)
+    ref = f32.to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(O.quantize_bf16(x), ref)
+    ints = np.arange(-255, 256, dtype=float)
+    assert np.array_equal(O.quantize_bf16(ints), ints)
+    # exact halfway cases round to the even neighbour (7 fraction bits)
+    ties = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 2 + 2.0 ** -7])
+    assert np.array_equal(O.quantize_bf16(ties), [1.0, 1 + 2.0 ** -6, -1.0, 2.0])
+
+
+def test_split_bf16_is_accurate_to_16_bits():
+    x = RNG.standard_normal(5000)
+    hi, lo = O.split_bf16(x)
+    f = x.astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(hi + lo - f) <= 2.0 ** -16 * np.abs(f) + 1e-300)
+    assert np.array_equal(O.quantize_bf16(hi), hi)
+    assert np.array_equal(O.quantize_bf16(lo), lo)
