@@ -1,0 +1,467 @@
+#!/usr/bin/env python
+"""Throughput of generalized Nystrom (GN) on one GB300 per rank.
+
+Workload: A = W1 diag(i^-2) W2^T + 1e-8 N (2000 modes), 32768 x 16384, sketch
+sizes r = 1000, l = 500 (Gaussian X, Y), the mixed-precision path: A, X, Y in
+BF16 (tensor-core sketch, FP32 accumulation), FP64 core.  One step = one
+approximation in the paper's output form (Algorithm 2 and the text after it:
+AX, Y^T A, Q, R): the fused sketch launch, the core product C = (Y^T A) X on
+the tensor cores (three bf16 slices of Y^T A), Householder QR of C in FP64 and
+the Section 5.1.2 detector / Section 5.1.1 truncation (mode AUTO).
+
+Prints ONE JSON line (rank 0).  Also reported, outside the timed region:
+the split-BF16 path, the plain FP64 GPU path on the same matrix, the factor
+formation F, G, the error ||A - F G||_F of each path, and the FP64 CPU oracle
+timed on a row sample of the same workload (cpu_baseline).
+
+--impl reference times the FP64 CPU oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import gn_synth  # noqa: E402
+
+METRIC = "GN approximations/s (32768x16384, r=1000, l=500, BF16 tensor-core sketch + FP64 core)"
+UNIT = "approximations/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gn", choices=["gn", "reference"])
+    ap.add_argument("--m", type=int, default=32768)
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--r", type=int, default=1000)
+    ap.add_argument("--no-extras", action="store_true", help="skip split/FP64/error/CPU side measurements")
+    ap.add_argument("--cpu-rows", type=int, default=512, help="row sample of the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def config_dict(a, precision="bf16"):
+    return {
+        "workload": f"GN dense {a.m}x{a.n} low-rank+noise (i^-2, 2000 modes, 1e-8 noise), r={a.r}, "
+                    f"l={a.r // 2}, Gaussian sketches, {precision} operands, FP64 core, mode AUTO",
+        "m": a.m, "n": a.n, "r": a.r, "l": a.r // 2,
+        "l2": "inputs larger than L2 (A alone is %.2f GB in BF16)" % (2.0 * a.m * a.n / 1e9),
+        "parallelism": "replicas" if a.gpus > 1 else "single GPU",
+    }
+
+
+# --------------------------------------------------------------------------- peaks
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if "Active" in v and "Not" not in v:
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id_for_smi(local_rank):
+    try:
+        u = torch.cuda.get_device_properties(local_rank).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            return vis.split(",")[local_rank]
+        return local_rank
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(a, rows, seed=gn_synth.DEFAULT_SEED):
+    """FP64 CPU oracle on a row sample of the workload: the sketches of `rows`
+    rows (scaled by m/rows to the full matrix) and the full core (C, QR,
+    detector, truncation) on a core of the full shape.  Returns seconds per
+    approximation and a description."""
+    from oracle import gn_oracle as O
+    l = a.r // 2
+    A_s = gn_synth.lowrank_plus_noise(rows, a.n, 2000, gn_synth.power_decay(2000, 2.0), 1e-8, seed + 7).numpy()
+    X, Y_s = gn_synth.sketches(rows, a.n, a.r, l, seed + 7)
+    X, Y_s = X.numpy(), Y_s.numpy()
+    t0 = time.perf_counter()
+    AX_s, YtA_s = O.sketch(A_s, X, Y_s)
+    t1 = time.perf_counter()
+    O.core(YtA_s, X, 1e-300, O.AUTO)
+    t2 = time.perf_counter()
+    per = (t1 - t0) * (a.m / rows) + (t2 - t1)
+    desc = (f"FP64 numpy oracle: sketch of {rows} of {a.m} rows (x{a.m // rows} to the full matrix) "
+            f"+ full {a.r + l}x{a.r} core (QR, detector); sketch {t1 - t0:.2f}s, core {t2 - t1:.2f}s")
+    return per, desc
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    rows = 256
+    times = []
+    for i in range(a.warmup + a.steps):
+        per, desc = cpu_oracle_sample(a, rows, gn_synth.DEFAULT_SEED + i)
+        if i >= a.warmup:
+            times.append(per)
+    per = statistics.mean(times)
+    v = 1.0 / per
+    line = {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference", "config": config_dict(a, "FP64 (oracle)"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        backend = "nccl" if (a.impl == "gn" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import paper_2009_11392_gb300 as gn
+    from paper_2009_11392_gb300 import build as _b  # noqa: F401
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m, n, r = a.m, a.n, a.r
+    l = r // 2
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    H = gn.Handle(stream)
+
+    # ---- inputs (seeded, drawn on the device; FP64)
+    p = gn_synth.config3(r=r, device=dev, m=m, n=n)
+    A64, X64, Y64 = p.a, p.x, p.y
+    # eps of Section 4.1 rescaled to the operands: 10 u32 ||A|| ||X|| ||Y||
+    def norm2(M, it=20):
+        v = torch.ones(M.shape[1], dtype=torch.float32, device=dev)
+        M32 = M.float()
+        s = 0.0
+        for _ in range(it):
+            w = M32.T @ (M32 @ v)
+            s = math.sqrt(w.norm().item())
+            v = w / w.norm()
+        return s
+    eps = 10 * 2.0 ** -24 * norm2(A64) * norm2(X64) * norm2(Y64)
+
+    # ---- a1: operand quantisation (reported separately)
+    q0 = torch.cuda.Event(enable_timing=True)
+    q1 = torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    Ab = H.quantize(A64)
+    q1.record(stream)
+    Xb, Yb = H.quantize(X64), H.quantize(Y64)
+    torch.cuda.synchronize()
+    quantize_ms = q0.elapsed_time(q1)
+
+    ws = H.workspace(m, n, r, l, gn.BF16X2)
+    AX = torch.empty(m, r, dtype=torch.float32, device=dev)
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device=dev)
+    core = gn.Core.empty(r, l, dev)
+
+    def step(A_op, A_lo=None, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        H.sketch(A_op, Xb, Yb, AX, YtA, ws, A_lo=A_lo)
+        if ev is not None:
+            ev[1].record(stream)
+        H.core(YtA, Xb, eps, gn.AUTO, core, ws)
+
+    for _ in range(a.warmup):
+        step(Ab)
+    torch.cuda.synchronize()
+    if H.sync_status() != 0:
+        raise RuntimeError("device status after warm-up")
+
+    sampler = ClockSampler(gpu_id_for_smi(local))
+    sampler.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = gn.kernel_launches()
+    t0.record(stream)
+    for i in range(a.steps):
+        step(Ab, ev=evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = gn.kernel_launches() - launches0
+    clocks = sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    sketch_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+    if H.sync_status() != 0:
+        raise RuntimeError("device status after timed steps")
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    per_step_ms = elapsed_ms / a.steps
+    value = world * a.steps / (elapsed_ms / 1e3)
+
+    # ---- end to end through the API with host buffers (H2D inputs, D2H outputs)
+    Ah = torch.empty(m, n, dtype=torch.bfloat16, pin_memory=True)
+    Ah.copy_(Ab)
+    Xh = torch.empty(Xb.shape, dtype=torch.bfloat16, pin_memory=True)
+    Xh.copy_(Xb)
+    Yh = torch.empty(Yb.shape, dtype=torch.bfloat16, pin_memory=True)
+    Yh.copy_(Yb)
+    outs = [torch.empty(AX.shape, dtype=torch.float32, pin_memory=True),
+            torch.empty(YtA.shape, dtype=torch.float32, pin_memory=True),
+            torch.empty(core.Q.shape, dtype=torch.float64, pin_memory=True),
+            torch.empty(core.R.shape, dtype=torch.float64, pin_memory=True)]
+    h2d = Ah.numel() * 2 + Xh.numel() * 2 + Yh.numel() * 2
+    d2h = sum(o.numel() * o.element_size() for o in outs)
+    Ad = gn.padded(m, n, torch.bfloat16, dev)
+    Xd = gn.padded(n, r, torch.bfloat16, dev)
+    Yd = gn.padded(m, r + l, torch.bfloat16, dev)
+
+    def e2e_step():
+        Ad.copy_(Ah, non_blocking=True)
+        Xd.copy_(Xh, non_blocking=True)
+        Yd.copy_(Yh, non_blocking=True)
+        H.sketch(Ad, Xd, Yd, AX, YtA, ws)
+        H.core(YtA, Xd, eps, gn.AUTO, core, ws)
+        for o, s in zip(outs, (AX, YtA, core.Q, core.R)):
+            o.copy_(s, non_blocking=True)
+
+    for _ in range(max(1, a.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / a.steps
+    del Ad, Xd, Yd
+
+    peaks, peak_kind = measured_peaks()
+    flops = 2.0 * m * n * (2 * r + l)
+    achieved = flops / (sketch_ms / 1e3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    roof_ms = max(2.0 * m * n / (peaks["hbm_gbs"] * 1e9), flops / (peak * 1e12)) * 1e3
+
+    extras = {}
+    if not a.no_extras and rank == 0:
+        extras = side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, ws, AX, YtA, core, peaks)
+
+    cpu = None
+    if rank == 0 and world >= 1 and not a.no_extras:
+        try:
+            per, desc = cpu_oracle_sample(a, a.cpu_rows)
+            cpu = {"value": 1.0 / per, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
+        except Exception as ex:  # pragma: no cover
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
+
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            t = json.load(open(tp)).get(f"sketch_bf16_{m}x{n}_r{r}")
+            traffic = t
+        except Exception:
+            traffic = None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded low-rank + noise, Gaussian sketches)",
+            "config": config_dict(a),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "tc_multigemm_kernel (fused AX + Y^T A sketch launch)",
+                         "kernel_ms": sketch_ms, "algorithmic_flops": flops,
+                         "peak_kind": f"bf16 sustained, {peak_kind}",
+                         "step_roofline_ms": roof_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "quantize_ms": quantize_ms,
+            "eps": eps,
+            "k": core.k, "sgn": core.sgn, "rinv_est": core.rinv_est,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, ws, AX, YtA, core, peaks):
+    """Outside the timed region: split-BF16 throughput, factors, errors of each
+    path against the FP64 A, and the plain FP64 GPU path on the same matrix."""
+    m, n, r = a.m, a.n, a.r
+    l = r // 2
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    F = torch.empty(m, r, dtype=torch.float64, device=dev)
+    G = torch.empty(r, n, dtype=torch.float64, device=dev)
+    e2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    normA = A64.norm().item()
+
+    def err_of(AXt, YtAt, c):
+        H.factors(AXt, YtAt, c, F, G, ws)
+        H.error_fro2(A64, F[:, :c.k], G[:c.k], e2, ws)
+        torch.cuda.synchronize()
+        return math.sqrt(e2.item())
+
+    # factors time (FP64 trsm + G) for the bf16 path
+    f0, f1 = ev(), ev()
+    f0.record(stream)
+    H.factors(AX, YtA, core, F, G, ws)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    out["factors_ms"] = f0.elapsed_time(f1)
+    out["err_bf16"] = err_of(AX, YtA, core)
+
+    # split bf16 (hi + lo) path
+    Ahi, Alo = H.quantize(A64, split=True)
+    s0, s1 = ev(), ev()
+    H.sketch(Ahi, Xb, Yb, AX, YtA, ws, A_lo=Alo)
+    H.core(YtA, Xb, eps, gn.AUTO, core, ws)
+    torch.cuda.synchronize()
+    reps = max(3, a.steps // 2)
+    k0, k1 = ev(), ev()
+    s0.record(stream)
+    for _ in range(reps):
+        k0.record(stream)
+        H.sketch(Ahi, Xb, Yb, AX, YtA, ws, A_lo=Alo)
+        k1.record(stream)
+        H.core(YtA, Xb, eps, gn.AUTO, core, ws)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    split_ms = s0.elapsed_time(s1) / reps
+    split_sketch_ms = k0.elapsed_time(k1)
+    fl2 = 2 * 2.0 * m * n * (2 * r + l)
+    out["split_bf16"] = {"approx_per_s": 1e3 / split_ms, "ms_per_step": split_ms, "sketch_ms": split_sketch_ms,
+                         "sketch_tflops": fl2 / (split_sketch_ms / 1e3) / 1e12,
+                         "err": err_of(AX, YtA, core)}
+    del Ahi, Alo
+
+    # plain FP64 GPU path on the same matrix (one step)
+    AX64 = torch.empty(m, r, dtype=torch.float64, device=dev)
+    YtA64 = torch.empty(r + l, n, dtype=torch.float64, device=dev)
+    c64 = gn.Core.empty(r, l, dev)
+    ws64 = H.workspace(m, n, r, l, gn.F64)
+    eps64 = eps * 2.0 ** -29
+    p0, p1, p2 = ev(), ev(), ev()
+    p0.record(stream)
+    H.sketch(A64, X64, Y64, AX64, YtA64, ws64)
+    p1.record(stream)
+    H.core(YtA64, X64, eps64, gn.AUTO, c64, ws64)
+    p2.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = p0.elapsed_time(p2)
+    out["fp64_path"] = {"approx_per_s": 1e3 / fp64_ms, "ms_per_step": fp64_ms, "sketch_ms": p0.elapsed_time(p1),
+                        "sketch_tflops": 2.0 * m * n * (2 * r + l) / (p0.elapsed_time(p1) / 1e3) / 1e12,
+                        "err": None}
+    out["fp64_path"]["err"] = err_of(AX64, YtA64, c64)
+    out["norm_A_fro"] = normA
+    out["err_floor_note"] = ("errors are ||A - F G||_F against the FP64 A; the bf16 path's floor is the "
+                             "bf16 storage of A, split bf16 and FP64 reach the sketch error itself")
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * gn.h -- C ABI of the GB300 generalized Nystrom (GN) library.
+ *
+ * Generalized Nystrom (Nakatsukasa, arXiv:2009.11392, eq. 2.1 and Algorithm 2)
+ * approximates a dense m x n matrix A by
+ *
+ *     A_hat = (AX) (Y^T A X)^+_eps (Y^T A),   X: n x r,  Y: m x (r+l),
+ *
+ * evaluated in the stable order of eq. 5.1: C = Y^T A X = QR (Householder),
+ * F = (AX) R^{-1} by triangular solve, G = Q^T (Y^T A), A_hat = F G.  The
+ * stabilised form (SGN, eq. 2.2, Section 5.1.1) truncates R where its diagonal
+ * falls to eps and re-factors R_1^T = Q_2 R_2, giving F = (AX) Q_2 R_2^{-T}.
+ *
+ * Conventions shared by every call
+ *   - Matrices are row-major device arrays described by gn_mat: element (i, j)
+ *     is at data + i*ld + j.  All pointers in a gn_mat are DEVICE pointers
+ *     unless a call says otherwise.  The caller allocates and owns every
+ *     buffer; the library never frees caller memory.
+ *   - Calls are asynchronous on the handle's CUDA stream.  Argument, shape and
+ *     dtype errors are detected on the host and returned before anything is
+ *     enqueued.  Device-side failures (a bounded wait that expired, a
+ *     non-finite core) are latched in a device status word that
+ *     gn_sync_status() returns.
+ *   - Scratch memory is a caller-provided device buffer (ws, ws_bytes) sized by
+ *     gn_workspace_size(); a call given too small a buffer returns
+ *     GN_ERR_WORKSPACE.  Calls that share one workspace must be ordered on one
+ *     stream.
+ *   - There is no CPU fallback: every step runs in this library's CUDA kernels
+ *     (sm_103a).  A missing device or a CUDA error gives GN_ERR_CUDA.
+ */
+#ifndef GN_H
+#define GN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GN_OK = 0,
+    GN_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, bad leading dimension */
+    GN_ERR_SHAPE = 2,         /* inconsistent sizes, or r, l outside 1 <= r <= min(m,n), l >= 1 */
+    GN_ERR_DTYPE = 3,         /* dtype combination not supported by the call */
+    GN_ERR_WORKSPACE = 4,     /* ws_bytes below gn_workspace_size() */
+    GN_ERR_CUDA = 5,          /* a CUDA runtime / driver call failed */
+    GN_ERR_NONFINITE = 6,     /* a non-finite value reached the core */
+    GN_ERR_TIMEOUT = 7,       /* a bounded device-side wait expired */
+    GN_ERR_UNSUPPORTED = 8,   /* valid request this build does not implement */
+    GN_ERR_ALIGNMENT = 9      /* operand address / leading dimension breaks a TMA rule */
+} gn_status;
+
+typedef enum {
+    GN_F64 = 0,     /* double */
+    GN_F32 = 1,     /* float */
+    GN_BF16 = 2,    /* bfloat16 (2 bytes) */
+    GN_BF16X2 = 3   /* split bfloat16: value = data + lo, both bf16, same layout */
+} gn_dtype;
+
+typedef enum {
+    GN_MODE_PLAIN = 0,   /* plain GN (eq. 2.1 via eq. 5.1): k = r, F = (AX) R^{-1} */
+    GN_MODE_SGN = 1,     /* stabilised GN (eq. 2.2, Section 5.1.1): truncate at eps */
+    GN_MODE_AUTO = 2     /* Section 5.1.2: plain unless est||R^{-1}||_2 >= 1/eps */
+} gn_mode;
+
+typedef struct {
+    void* data;      /* device pointer, row-major */
+    void* lo;        /* GN_BF16X2 only: low-order bf16 part (same rows, cols, ld) */
+    int64_t rows;
+    int64_t cols;
+    int64_t ld;      /* leading dimension in elements, >= cols */
+    int32_t dtype;   /* gn_dtype */
+} gn_mat;
+
+/* The small core produced by gn_core().  Q, R, Q2, R2, C are caller-allocated
+ * DEVICE arrays in FP64; r, l, k, sgn and rinv_est are host fields.
+ *   Q   : (r+l) x r, ld = r.  Thin Q of C = Y^T A X; its first k columns are Q_1.
+ *   R   : r x r, ld = r.  Upper triangular, diag(R) >= 0.
+ *   Q2  : r x r, ld = r.  Q of R_1^T (only the first k columns used; SGN, k < r).
+ *   R2  : r x r, ld = r.  R of R_1^T (leading k x k block used; SGN, k < r).
+ *   C   : (r+l) x r, ld = r.  The core matrix itself (kept for diagnostics).
+ * After gn_core() returns, the host fields hold: k (truncation rank, = r for
+ * plain GN), sgn (1 when the truncated branch was taken), rinv_est (the
+ * power-method estimate of ||R^{-1}||_2; computed in SGN and AUTO modes,
+ * 0 in PLAIN mode). */
+typedef struct {
+    double* Q;
+    double* R;
+    double* Q2;
+    double* R2;
+    double* C;
+    int64_t r;
+    int64_t l;
+    int64_t k;
+    int32_t sgn;
+    double rinv_est;
+} gn_core_t;
+
+typedef struct gn_handle_s* gn_handle;
+
+/* ------------------------------------------------------------------ handle */
+
+/* Create a handle bound to the current CUDA device and to `stream` (a
+ * cudaStream_t; NULL = legacy default stream).  Allocates one 64-byte device
+ * status word.  Returns GN_ERR_CUDA when no device is usable. */
+gn_status gn_create(gn_handle* out, void* stream);
+gn_status gn_destroy(gn_handle h);
+gn_status gn_set_stream(gn_handle h, void* stream);
+
+/* Synchronise the handle's stream, then return (and clear) the latched device
+ * status: GN_OK, GN_ERR_TIMEOUT or GN_ERR_NONFINITE, or GN_ERR_CUDA if the
+ * stream reported an error. */
+gn_status gn_sync_status(gn_handle h);
+
+/* Device-side wait limit in nanoseconds for the pipelined kernels' mbarrier
+ * waits (default 2e9).  A wait that exceeds it latches GN_ERR_TIMEOUT, the
+ * kernel drains its in-flight copies, frees its tensor memory and returns. */
+gn_status gn_set_wait_limit(gn_handle h, uint64_t ns);
+
+const char* gn_status_string(gn_status s);
+
+/* Number of SMs of the handle's device (the persistent grids use it). */
+int gn_device_sm_count(gn_handle h);
+
+/* Total number of CUDA kernels this library has launched in the process
+ * (all handles).  A diagnostic counter: differences around a region count the
+ * library's launches inside it. */
+uint64_t gn_kernel_launches(void);
+
+/* ----------------------------------------------------------------- sizing */
+
+/* Scratch bytes needed by gn_sketch/gn_core/gn_factors/gn_approx/gn_hmt for
+ * an m x n problem with sketch sizes r, l whose sketch operands have dtype
+ * `op_dtype` (GN_F64 for the plain FP64 path; GN_BF16 / GN_BF16X2 for the
+ * tensor-core path).  One buffer of this size serves every call on the shape. */
+gn_status gn_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l,
+                            int32_t op_dtype, size_t* bytes);
+
+/* ------------------------------------------------------ Algorithm 2, step 1-2 */
+
+/* Operand preparation for the tensor-core path (mixed precision).
+ * src: GN_F64 or GN_F32 matrix; dst: same rows/cols, dtype GN_BF16 (round to
+ * nearest even via FP32) or GN_BF16X2 (dst.data = bf16(x32), dst.lo =
+ * bf16(x32 - hi), x32 = fp32(x)).  dst.ld must be a multiple of 8 and the
+ * data (and lo) pointers 16-byte aligned, the layout TMA needs. */
+gn_status gn_quantize(gn_handle h, const gn_mat* src, gn_mat* dst);
+
+/* The two sketches of Algorithm 2, step 2: AX (m x r) and Y^T A ((r+l) x n).
+ *   A: m x n; X: n x r; Y: m x (r+l) (Y is passed untransposed).
+ *   GN_F64 operands: AX, YtA are GN_F64; computed with FP64 FMA.
+ *   GN_BF16 / GN_BF16X2 A with GN_BF16 X, Y: one launch of the tcgen05
+ *     tensor-core kernel, FP32 accumulation; AX, YtA are GN_F32.  Operand
+ *     ld must be a multiple of 8, bases 16-byte aligned (GN_ERR_ALIGNMENT).
+ * Outputs are overwritten (no accumulation into them). */
+gn_status gn_sketch(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,
+                    gn_mat* AX, gn_mat* YtA, void* ws, size_t ws_bytes);
+
+/* The core of Algorithm 2 step 2 and Section 5.1: C = (Y^T A) X, Householder
+ * C = QR with diag(R) >= 0, then per `mode` the eps-truncation and the
+ * second QR of Section 5.1.1, and (SGN/AUTO) the Section 5.1.2 estimate of
+ * ||R^{-1}||_2 by 6 power iterations from the all-ones vector.
+ *   YtA: (r+l) x n, GN_F64 or GN_F32; X: n x r, GN_F64 or GN_BF16.
+ *   GN_F64 x GN_F64: C in FP64.  GN_F32 x GN_BF16: C from three bf16 slices
+ *   of Y^T A on the tensor cores (FP32 accumulate per slice, slices summed in
+ *   FP64).
+ *   eps >= 0 is an absolute threshold on |R_ii| (the caller scales it).
+ * Blocks the host once in SGN / AUTO mode to read k (the later shapes depend
+ * on it); PLAIN mode does not block. */
+gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, int32_t mode,
+                  gn_core_t* core, void* ws, size_t ws_bytes);
+
+/* ------------------------------------------------------------- Algorithm 2, step 3 */
+
+/* F = (AX) R^{-1} (k = r) or (AX) Q_2 R_2^{-T} (k < r), by blocked triangular
+ * solve in FP64, and G = Q_1^T (Y^T A) in FP64 (eq. 5.1; never forms the core
+ * pseudoinverse).  AX: m x r and YtA: (r+l) x n in GN_F64 or GN_F32.
+ * F: m x k, G: k x n, both GN_F64 (only the first core->k columns / rows are
+ * written; F and G may be allocated r wide / r tall). */
+gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_core_t* core,
+                     gn_mat* F, gn_mat* G, void* ws, size_t ws_bytes);
+
+/* Sketch + core + factors in one call (Algorithm 2).  AX, YtA are outputs
+ * (GN_F64 for FP64 operands, GN_F32 for the tensor-core path). */
+gn_status gn_approx(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,
+                    double eps, int32_t mode, gn_mat* AX, gn_mat* YtA, gn_core_t* core,
+                    gn_mat* F, gn_mat* G, void* ws, size_t ws_bytes);
+
+/* ||A - F G||_F^2 accumulated in FP64 without storing F G (the accuracy measure
+ * of Section 7.1).  A: m x n GN_F64, GN_F32, GN_BF16 or GN_BF16X2 (data+lo);
+ * F: m x k GN_F64; G: k x n GN_F64.  The result is written to the DEVICE
+ * double *out (overwritten). */
+gn_status gn_error_fro2(gn_handle h, const gn_mat* A, const gn_mat* F, const gn_mat* G,
+                        double* out, void* ws, size_t ws_bytes);
+
+/* ---------------------------------------------------------------- Algorithm 1 */
+
+/* HMT range finder (Algorithm 1): AX, Householder QR AX = Q R_x, B = Q^T A.
+ * All GN_F64: A m x n, X n x r, Q m x r (output), B r x n (output). */
+gn_status gn_hmt(gn_handle h, const gn_mat* A, const gn_mat* X, gn_mat* Q, gn_mat* B,
+                 void* ws, size_t ws_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GN_H */

@@ -1,0 +1,262 @@
+"""GB300 generalized Nystrom (GN) low-rank approximation -- Python binding.
+
+A thin ctypes layer over the C ABI declared in ``include/gn.h`` (library
+``_build/libgn.so``).  It only marshals torch tensors into ``gn_mat`` /
+``gn_core_t`` descriptors and checks return codes; every step of the method
+runs in the library's CUDA kernels.  PyTorch supplies device memory and the
+stream.  There is no CPU fallback: importing the package fails when the
+shared library is missing, and every call raises on a non-OK status.
+
+Entry points (same names as the C ABI):
+    quantize, sketch, core, factors, approx, error_fro2, hmt
+plus ``workspace`` (sized by gn_workspace_size) and ``Core`` (the small
+factors of Section 5.1 held in caller-owned tensors).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "GNError", "Handle", "Core", "lib_path", "lib", "F64", "F32", "BF16", "BF16X2",
+    "PLAIN", "SGN", "AUTO", "ABI_SYMBOLS", "mat", "round8", "padded",
+]
+
+F64, F32, BF16, BF16X2 = 0, 1, 2, 3
+PLAIN, SGN, AUTO = 0, 1, 2
+
+# Every symbol declared in include/gn.h.
+ABI_SYMBOLS = (
+    "gn_create", "gn_destroy", "gn_set_stream", "gn_sync_status", "gn_set_wait_limit",
+    "gn_status_string", "gn_device_sm_count", "gn_workspace_size", "gn_quantize",
+    "gn_sketch", "gn_core", "gn_factors", "gn_approx", "gn_error_fro2", "gn_hmt",
+    "gn_kernel_launches",
+)
+
+
+class GnMat(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("rows", ctypes.c_int64),
+                ("cols", ctypes.c_int64), ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32)]
+
+
+class GnCoreT(ctypes.Structure):
+    _fields_ = [("Q", ctypes.c_void_p), ("R", ctypes.c_void_p), ("Q2", ctypes.c_void_p),
+                ("R2", ctypes.c_void_p), ("C", ctypes.c_void_p), ("r", ctypes.c_int64),
+                ("l", ctypes.c_int64), ("k", ctypes.c_int64), ("sgn", ctypes.c_int32),
+                ("rinv_est", ctypes.c_double)]
+
+
+def kernel_launches() -> int:
+    """Kernels launched so far by the library in this process."""
+    return int(lib.gn_kernel_launches())
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        if os.environ.get("GN_AUTOBUILD", "1") == "1":
+            _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"GN CUDA library not built: {path} is missing (run the package's build.py)")
+    L = ctypes.CDLL(path)
+    P, I32, I64, D, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    M = ctypes.POINTER(GnMat)
+    C = ctypes.POINTER(GnCoreT)
+    sig = {
+        "gn_create": ([ctypes.POINTER(P), P], I32),
+        "gn_destroy": ([P], I32),
+        "gn_set_stream": ([P, P], I32),
+        "gn_sync_status": ([P], I32),
+        "gn_set_wait_limit": ([P, ctypes.c_uint64], I32),
+        "gn_status_string": ([I32], ctypes.c_char_p),
+        "gn_device_sm_count": ([P], ctypes.c_int),
+        "gn_workspace_size": ([I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
+        "gn_quantize": ([P, M, M], I32),
+        "gn_sketch": ([P, M, M, M, M, M, P, SZ], I32),
+        "gn_core": ([P, M, M, D, I32, C, P, SZ], I32),
+        "gn_factors": ([P, M, M, C, M, M, P, SZ], I32),
+        "gn_approx": ([P, M, M, M, D, I32, M, M, C, M, M, P, SZ], I32),
+        "gn_error_fro2": ([P, M, M, M, P, P, SZ], I32),
+        "gn_hmt": ([P, M, M, M, M, P, SZ], I32),
+        "gn_kernel_launches": ([], ctypes.c_uint64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+class GNError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.gn_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise GNError(status, where)
+
+
+_TORCH_DT = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
+
+
+def round8(x: int) -> int:
+    return (x + 7) // 8 * 8
+
+
+def mat(t: torch.Tensor, lo: torch.Tensor | None = None) -> GnMat:
+    """gn_mat for a row-major 2-D CUDA tensor (stride (ld, 1)); ``lo`` makes it split bf16."""
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("operands must be 2-D row-major (stride(1) == 1)")
+    if not t.is_cuda:
+        raise ValueError("operands must be CUDA tensors")
+    dt = _TORCH_DT.get(t.dtype)
+    if dt is None:
+        raise ValueError(f"unsupported dtype {t.dtype}")
+    ld = t.stride(0) if t.shape[0] > 1 else max(t.shape[1], t.stride(0))
+    m = GnMat(t.data_ptr(), 0, t.shape[0], t.shape[1], ld, dt)
+    if lo is not None:
+        if lo.shape != t.shape or lo.stride() != t.stride() or lo.dtype != torch.bfloat16:
+            raise ValueError("lo must match data in shape, stride and bf16 dtype")
+        m.lo = lo.data_ptr()
+        m.dtype = BF16X2
+    return m
+
+
+def padded(rows: int, cols: int, dtype, device) -> torch.Tensor:
+    """An uninitialised rows x cols tensor whose leading dimension is a multiple
+    of 8 elements (the TMA rule for bf16 operands)."""
+    return torch.empty(rows, round8(cols), dtype=dtype, device=device)[:, :cols]
+
+
+@dataclass
+class Core:
+    C: torch.Tensor
+    Q: torch.Tensor
+    R: torch.Tensor
+    Q2: torch.Tensor
+    R2: torch.Tensor
+    r: int
+    l: int
+    k: int = 0
+    sgn: int = 0
+    rinv_est: float = 0.0
+
+    @staticmethod
+    def empty(r: int, l: int, device) -> "Core":
+        z = lambda a, b: torch.empty(a, b, dtype=torch.float64, device=device)
+        return Core(z(r + l, r), z(r + l, r), z(r, r), z(r, r), z(r, r), r, l)
+
+    def cstruct(self) -> GnCoreT:
+        return GnCoreT(self.Q.data_ptr(), self.R.data_ptr(), self.Q2.data_ptr(), self.R2.data_ptr(),
+                       self.C.data_ptr(), self.r, self.l, self.k, self.sgn, self.rinv_est)
+
+    def update(self, c: GnCoreT):
+        self.k, self.sgn, self.rinv_est = int(c.k), int(c.sgn), float(c.rinv_est)
+
+
+class Handle:
+    """Owns a gn_handle bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("GN needs a CUDA device; there is no CPU path")
+        self.stream = stream or torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.gn_create(ctypes.byref(h), ctypes.c_void_p(self.stream.cuda_stream)), "gn_create")
+        self._h = h
+
+    @property
+    def h(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib.gn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sm_count(self) -> int:
+        return lib.gn_device_sm_count(self._h)
+
+    def sync_status(self) -> int:
+        return lib.gn_sync_status(self._h)
+
+    def set_wait_limit(self, ns: int):
+        _check(lib.gn_set_wait_limit(self._h, int(ns)), "gn_set_wait_limit")
+
+    # ---------------------------------------------------------------- sizing
+    @staticmethod
+    def workspace_bytes(m, n, r, l, op_dtype) -> int:
+        b = ctypes.c_size_t()
+        _check(lib.gn_workspace_size(m, n, r, l, op_dtype, ctypes.byref(b)), "gn_workspace_size")
+        return int(b.value)
+
+    def workspace(self, m, n, r, l, op_dtype, device=None) -> torch.Tensor:
+        nb = self.workspace_bytes(m, n, r, l, op_dtype)
+        return torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+
+    # ---------------------------------------------------------------- calls
+    def quantize(self, src: torch.Tensor, split: bool = False):
+        """FP64/FP32 -> bf16 (or split bf16 hi, lo) with an 8-aligned leading dimension."""
+        hi = padded(src.shape[0], src.shape[1], torch.bfloat16, src.device)
+        lo = padded(src.shape[0], src.shape[1], torch.bfloat16, src.device) if split else None
+        d = mat(hi, lo)
+        _check(lib.gn_quantize(self._h, ctypes.byref(mat(src)), ctypes.byref(d)), "gn_quantize")
+        return (hi, lo) if split else hi
+
+    def sketch(self, A, X, Y, AX, YtA, ws, A_lo=None):
+        _check(lib.gn_sketch(self._h, ctypes.byref(mat(A, A_lo)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
+                             ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.c_void_p(ws.data_ptr()),
+                             ws.numel()), "gn_sketch")
+
+    def core(self, YtA, X, eps: float, mode: int, core: Core, ws) -> Core:
+        c = core.cstruct()
+        _check(lib.gn_core(self._h, ctypes.byref(mat(YtA)), ctypes.byref(mat(X)), float(eps), int(mode),
+                           ctypes.byref(c), ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_core")
+        core.update(c)
+        return core
+
+    def factors(self, AX, YtA, core: Core, F, G, ws):
+        c = core.cstruct()
+        _check(lib.gn_factors(self._h, ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.byref(c),
+                              ctypes.byref(mat(F)), ctypes.byref(mat(G)), ctypes.c_void_p(ws.data_ptr()),
+                              ws.numel()), "gn_factors")
+
+    def approx(self, A, X, Y, eps, mode, AX, YtA, core: Core, F, G, ws, A_lo=None) -> Core:
+        c = core.cstruct()
+        _check(lib.gn_approx(self._h, ctypes.byref(mat(A, A_lo)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
+                             float(eps), int(mode), ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)),
+                             ctypes.byref(c), ctypes.byref(mat(F)), ctypes.byref(mat(G)),
+                             ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_approx")
+        core.update(c)
+        return core
+
+    def error_fro2(self, A, F, G, out, ws, A_lo=None):
+        """Writes ||A - F G||_F^2 into the 1-element float64 CUDA tensor ``out``."""
+        _check(lib.gn_error_fro2(self._h, ctypes.byref(mat(A, A_lo)), ctypes.byref(mat(F)), ctypes.byref(mat(G)),
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel()),
+               "gn_error_fro2")
+
+    def hmt(self, A, X, Q, B, ws):
+        _check(lib.gn_hmt(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Q)),
+                          ctypes.byref(mat(B)), ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_hmt")

@@ -1,0 +1,504 @@
+// The C ABI of the library (include/gn.h): argument checks on the host, then
+// the stream-ordered launch sequence of each call.  Nothing here computes: every
+// step runs in the kernels of gn_tc.cu (tensor cores) and gn_f64.cu (FP64).
+#include "gn_internal.cuh"
+
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include <atomic>
+
+using namespace gn;
+
+namespace gn {
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace gn
+
+namespace {
+
+constexpr int DIAG_ITERS = 6;
+
+bool valid_dtype(int32_t d) { return d >= GN_F64 && d <= GN_BF16X2; }
+
+size_t elem_size(int32_t d) {
+    switch (d) {
+        case GN_F64: return 8;
+        case GN_F32: return 4;
+        default: return 2;
+    }
+}
+
+gn_status check_mat(const gn_mat* a, long long rows, long long cols) {
+    if (!a || !a->data) return GN_ERR_INVALID_ARG;
+    if (!valid_dtype(a->dtype)) return GN_ERR_DTYPE;
+    if (a->rows != rows || a->cols != cols) return GN_ERR_SHAPE;
+    if (a->ld < a->cols || a->ld <= 0) return GN_ERR_INVALID_ARG;
+    if (a->dtype == GN_BF16X2 && !a->lo) return GN_ERR_INVALID_ARG;
+    return GN_OK;
+}
+
+gn_status check_tma_operand(const gn_mat* a) {
+    if ((reinterpret_cast<uintptr_t>(a->data) & 15) || (a->ld % 8)) return GN_ERR_ALIGNMENT;
+    if (a->dtype == GN_BF16X2 && (reinterpret_cast<uintptr_t>(a->lo) & 15)) return GN_ERR_ALIGNMENT;
+    return GN_OK;
+}
+
+gn_status check_sizes(long long m, long long n, long long r, long long l) {
+    if (m <= 0 || n <= 0) return GN_ERR_SHAPE;
+    if (r < 1 || r > std::min(m, n) || l < 1 || r + l > m) return GN_ERR_SHAPE;
+    if (m > (1LL << 31) - 1 || n > (1LL << 31) - 1) return GN_ERR_SHAPE;
+    return GN_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+
+// Bump allocator over the caller's workspace.
+struct Carve {
+    char* base;
+    size_t cap;
+    size_t off;
+    bool ok;
+    template <typename T>
+    T* take(size_t count) {
+        const size_t bytes = align256(count * sizeof(T));
+        if (off + bytes > cap) {
+            ok = false;
+            return nullptr;
+        }
+        T* p = reinterpret_cast<T*>(base + off);
+        off += bytes;
+        return p;
+    }
+    double* rest(size_t* bytes) {
+        const size_t o = align256(off);
+        *bytes = o < cap ? cap - o : 0;
+        return reinterpret_cast<double*>(base + o);
+    }
+};
+
+long long round8(long long x) { return (x + 7) / 8 * 8; }
+
+// ---------------------------------------------------------------- sizing helpers
+size_t core_ws(long long n, long long r, long long l, int mixed, int sms) {
+    const long long rl = r + l;
+    size_t b = 0;
+    b += align256(sizeof(double) * rl * r);            // W for the QR of C
+    b += align256(sizeof(double) * r * r);             // W2 for the QR of R_1^T
+    b += align256(sizeof(double) * std::max<long long>(r, 64));   // diag scratch
+    b += 256;                                          // k, est
+    if (mixed) {
+        b += 3 * align256(sizeof(__nv_bfloat16) * rl * round8(n));
+        b += 3 * align256(sizeof(float) * rl * r);
+    }
+    size_t inner = std::max(qr_ws_bytes(rl, r, sms), dgemm_ws_bytes(rl, r, n, sms));
+    return b + inner + 1024;
+}
+
+size_t factors_ws(long long m, long long r, int sms) { return trsm_ws_bytes(m, r, sms) + dgemm_ws_bytes(m, r, r, sms) + 1024; }
+
+size_t hmt_ws(long long m, long long n, long long r, int sms) {
+    return align256(sizeof(double) * m * r) + align256(sizeof(double) * r * r) + qr_ws_bytes(m, r, sms) +
+           dgemm_ws_bytes(r, n, m, sms) + 1024;
+}
+
+gn_status launch_sketch_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* AX,
+                           gn_mat* YtA) {
+    const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols;
+    TcParams p;
+    memset(&p, 0, sizeof(p));
+    int nm = 0;
+    const int mAk = nm++, mAmn = nm++;
+    GN_TRY(tc_make_map_bf16(&p.maps[mAk], A->data, m, n, A->ld, 64, 128));
+    GN_TRY(tc_make_map_bf16(&p.maps[mAmn], A->data, m, n, A->ld, 64, 64));
+    int mLk = -1, mLmn = -1;
+    const int nsrc = A->dtype == GN_BF16X2 ? 2 : 1;
+    if (nsrc == 2) {
+        mLk = nm++;
+        mLmn = nm++;
+        GN_TRY(tc_make_map_bf16(&p.maps[mLk], A->lo, m, n, A->ld, 64, 128));
+        GN_TRY(tc_make_map_bf16(&p.maps[mLmn], A->lo, m, n, A->ld, 64, 64));
+    }
+    const int mX = nm++, mY = nm++;
+    GN_TRY(tc_make_map_bf16(&p.maps[mX], X->data, n, r, X->ld, 64, 64));
+    GN_TRY(tc_make_map_bf16(&p.maps[mY], Y->data, m, rl, Y->ld, 64, 64));
+
+    // GEMM 0: AX (m x r) = A (K-major) . X (MN-major), K = n
+    TcGemm& g0 = p.g[0];
+    g0.M = static_cast<int>(m);
+    g0.N = static_cast<int>(r);
+    g0.K = static_cast<int>(n);
+    g0.bn = static_cast<int>(std::min<long long>(256, (r + 63) / 64 * 64));
+    g0.a_mn = 0;
+    g0.b_mn = 1;
+    g0.nsrc = nsrc;
+    g0.a_map[0] = mAk;
+    g0.b_map[0] = mX;
+    if (nsrc == 2) {
+        g0.a_map[1] = mLk;
+        g0.b_map[1] = mX;
+    }
+    g0.D = static_cast<float*>(AX->data);
+    g0.ldd = AX->ld;
+    // GEMM 1: Y^T A ((r+l) x n) = Y^T (MN-major A operand) . A (MN-major B), K = m
+    TcGemm& g1 = p.g[1];
+    g1.M = static_cast<int>(rl);
+    g1.N = static_cast<int>(n);
+    g1.K = static_cast<int>(m);
+    // Per-tile cost ~ bn * K: halve the N tile when K is twice the other GEMM's.
+    g1.bn = (m >= 2 * n) ? 128 : 256;
+    g1.a_mn = 1;
+    g1.b_mn = 1;
+    g1.nsrc = nsrc;
+    g1.a_map[0] = mY;
+    g1.b_map[0] = mAmn;
+    if (nsrc == 2) {
+        g1.a_map[1] = mY;
+        g1.b_map[1] = mLmn;
+    }
+    g1.D = static_cast<float*>(YtA->data);
+    g1.ldd = YtA->ld;
+    // Order: the longer-K GEMM first (its tiles are the expensive ones).
+    if (m >= n) {
+        TcGemm t = p.g[0];
+        p.g[0] = p.g[1];
+        p.g[1] = t;
+    }
+    p.ngemm = 2;
+    return tc_launch(h, &p);
+}
+
+}  // namespace
+
+// ============================================================================ API
+extern "C" {
+
+const char* gn_status_string(gn_status s) {
+    switch (s) {
+        case GN_OK: return "ok";
+        case GN_ERR_INVALID_ARG: return "invalid argument";
+        case GN_ERR_SHAPE: return "invalid shape";
+        case GN_ERR_DTYPE: return "unsupported dtype combination";
+        case GN_ERR_WORKSPACE: return "workspace too small";
+        case GN_ERR_CUDA: return "CUDA error";
+        case GN_ERR_NONFINITE: return "non-finite value in the core";
+        case GN_ERR_TIMEOUT: return "device-side wait timed out";
+        case GN_ERR_UNSUPPORTED: return "unsupported request";
+        case GN_ERR_ALIGNMENT: return "operand breaks a TMA alignment rule";
+    }
+    return "unknown status";
+}
+
+gn_status gn_create(gn_handle* out, void* stream) {
+    if (!out) return GN_ERR_INVALID_ARG;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GN_ERR_CUDA;
+    int sms = 0;
+    GN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    gn_handle h = new (std::nothrow) gn_handle_s;
+    if (!h) return GN_ERR_INVALID_ARG;
+    h->device = dev;
+    h->sm_count = sms;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->wait_limit_ns = 2000000000ULL;
+    if (cudaMalloc(&h->dstatus, 64) != cudaSuccess) {
+        delete h;
+        return GN_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(h->dstatus, 0, 64, h->stream) != cudaSuccess) {
+        cudaFree(h->dstatus);
+        delete h;
+        return GN_ERR_CUDA;
+    }
+    *out = h;
+    return GN_OK;
+}
+
+gn_status gn_destroy(gn_handle h) {
+    if (!h) return GN_ERR_INVALID_ARG;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->dstatus);
+    delete h;
+    return GN_OK;
+}
+
+gn_status gn_set_stream(gn_handle h, void* stream) {
+    if (!h) return GN_ERR_INVALID_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return GN_OK;
+}
+
+gn_status gn_set_wait_limit(gn_handle h, uint64_t ns) {
+    if (!h || ns == 0) return GN_ERR_INVALID_ARG;
+    h->wait_limit_ns = ns;
+    return GN_OK;
+}
+
+int gn_device_sm_count(gn_handle h) { return h ? h->sm_count : 0; }
+
+uint64_t gn_kernel_launches(void) { return launch_count(); }
+
+gn_status gn_sync_status(gn_handle h) {
+    if (!h) return GN_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return GN_ERR_CUDA;
+    int32_t st[2] = {0, 0};
+    GN_CUDA_TRY(cudaMemcpy(st, h->dstatus, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st[0] != 0) GN_CUDA_TRY(cudaMemset(h->dstatus, 0, 64));
+    return static_cast<gn_status>(st[0]);
+}
+
+gn_status gn_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t op_dtype, size_t* bytes) {
+    if (!bytes) return GN_ERR_INVALID_ARG;
+    GN_TRY(check_sizes(m, n, r, l));
+    if (op_dtype != GN_F64 && op_dtype != GN_BF16 && op_dtype != GN_BF16X2) return GN_ERR_DTYPE;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int mixed = op_dtype != GN_F64;
+    size_t b = core_ws(n, r, l, mixed, sms);
+    b = std::max(b, factors_ws(m, r, sms));
+    b = std::max(b, hmt_ws(m, n, r, sms));
+    b = std::max(b, error_ws_bytes(m, n, sms));
+    *bytes = b;
+    return GN_OK;
+}
+
+gn_status gn_quantize(gn_handle h, const gn_mat* src, gn_mat* dst) {
+    if (!h || !src || !dst) return GN_ERR_INVALID_ARG;
+    GN_TRY(check_mat(src, src->rows, src->cols));
+    GN_TRY(check_mat(dst, src->rows, src->cols));
+    if (src->dtype != GN_F64 && src->dtype != GN_F32) return GN_ERR_DTYPE;
+    if (dst->dtype != GN_BF16 && dst->dtype != GN_BF16X2) return GN_ERR_DTYPE;
+    GN_TRY(check_tma_operand(dst));
+    return quantize_bf16(h, src->data, src->dtype == GN_F64, src->rows, src->cols, src->ld,
+                         static_cast<__nv_bfloat16*>(dst->data),
+                         dst->dtype == GN_BF16X2 ? static_cast<__nv_bfloat16*>(dst->lo) : nullptr, dst->ld);
+}
+
+gn_status gn_sketch(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* AX,
+                    gn_mat* YtA, void* ws, size_t ws_bytes) {
+    if (!h || !A || !X || !Y || !AX || !YtA) return GN_ERR_INVALID_ARG;
+    const long long m = A->rows, n = A->cols, r = X->cols;
+    if (!Y) return GN_ERR_INVALID_ARG;
+    const long long l = Y->cols - r;
+    GN_TRY(check_sizes(m, n, r, l));
+    GN_TRY(check_mat(A, m, n));
+    GN_TRY(check_mat(X, n, r));
+    GN_TRY(check_mat(Y, m, r + l));
+    GN_TRY(check_mat(AX, m, r));
+    GN_TRY(check_mat(YtA, r + l, n));
+    if (A->dtype == GN_F64) {
+        if (X->dtype != GN_F64 || Y->dtype != GN_F64 || AX->dtype != GN_F64 || YtA->dtype != GN_F64)
+            return GN_ERR_DTYPE;
+        double* gws = static_cast<double*>(ws);
+        GN_TRY(dgemm(h, m, r, n, 1.0, static_cast<const double*>(A->data), A->ld, 0,
+                     static_cast<const double*>(X->data), X->ld, 0, 0.0, static_cast<double*>(AX->data),
+                     AX->ld, gws, ws_bytes));
+        GN_TRY(dgemm(h, r + l, n, m, 1.0, static_cast<const double*>(Y->data), Y->ld, 1,
+                     static_cast<const double*>(A->data), A->ld, 0, 0.0, static_cast<double*>(YtA->data),
+                     YtA->ld, gws, ws_bytes));
+        return GN_OK;
+    }
+    if (A->dtype == GN_BF16 || A->dtype == GN_BF16X2) {
+        if (X->dtype != GN_BF16 || Y->dtype != GN_BF16 || AX->dtype != GN_F32 || YtA->dtype != GN_F32)
+            return GN_ERR_DTYPE;
+        GN_TRY(check_tma_operand(A));
+        GN_TRY(check_tma_operand(X));
+        GN_TRY(check_tma_operand(Y));
+        return launch_sketch_tc(h, A, X, Y, AX, YtA);
+    }
+    return GN_ERR_DTYPE;
+}
+
+gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, int32_t mode,
+                  gn_core_t* core, void* ws, size_t ws_bytes) {
+    if (!h || !YtA || !X || !core || !ws) return GN_ERR_INVALID_ARG;
+    if (mode < GN_MODE_PLAIN || mode > GN_MODE_AUTO || !(eps >= 0.0)) return GN_ERR_INVALID_ARG;
+    const long long n = X->rows, r = X->cols, rl = YtA->rows, l = rl - r;
+    if (r < 1 || l < 1 || n < r) return GN_ERR_SHAPE;
+    GN_TRY(check_mat(YtA, rl, n));
+    GN_TRY(check_mat(X, n, r));
+    if (!core->Q || !core->R || !core->C || ((mode != GN_MODE_PLAIN) && (!core->Q2 || !core->R2)))
+        return GN_ERR_INVALID_ARG;
+    const int mixed = (YtA->dtype == GN_F32 && X->dtype == GN_BF16);
+    const int fp64 = (YtA->dtype == GN_F64 && X->dtype == GN_F64);
+    if (!mixed && !fp64) return GN_ERR_DTYPE;
+    if (ws_bytes < core_ws(n, r, l, mixed, h->sm_count)) return GN_ERR_WORKSPACE;
+    core->r = r;
+    core->l = l;
+
+    Carve cv{static_cast<char*>(ws), ws_bytes, 0, true};
+    double* W = cv.take<double>(rl * r);
+    double* W2 = cv.take<double>(r * r);
+    double* zscr = cv.take<double>(std::max<long long>(r, 64));
+    double* est_d = cv.take<double>(1);
+    int* k_d = cv.take<int>(1);
+    __nv_bfloat16 *s_hi = nullptr, *s_mid = nullptr, *s_lo = nullptr;
+    float *c_hi = nullptr, *c_mid = nullptr, *c_lo = nullptr;
+    const long long lds = round8(n);
+    if (mixed) {
+        s_hi = cv.take<__nv_bfloat16>(rl * lds);
+        s_mid = cv.take<__nv_bfloat16>(rl * lds);
+        s_lo = cv.take<__nv_bfloat16>(rl * lds);
+        c_hi = cv.take<float>(rl * r);
+        c_mid = cv.take<float>(rl * r);
+        c_lo = cv.take<float>(rl * r);
+    }
+    size_t inner_bytes = 0;
+    double* inner = cv.rest(&inner_bytes);
+    if (!cv.ok) return GN_ERR_WORKSPACE;
+
+    // C = (Y^T A) X  ((r+l) x r, FP64, ld = r)
+    if (fp64) {
+        GN_TRY(dgemm(h, rl, r, n, 1.0, static_cast<const double*>(YtA->data), YtA->ld, 0,
+                     static_cast<const double*>(X->data), X->ld, 0, 0.0, core->C, r, inner, inner_bytes));
+    } else {
+        GN_TRY(check_tma_operand(X));
+        GN_TRY(split3_bf16(h, static_cast<const float*>(YtA->data), rl, n, YtA->ld, s_hi, s_mid, s_lo, lds));
+        TcParams p;
+        memset(&p, 0, sizeof(p));
+        __nv_bfloat16* sl[3] = {s_hi, s_mid, s_lo};
+        float* cl[3] = {c_hi, c_mid, c_lo};
+        for (int s = 0; s < 3; ++s) GN_TRY(tc_make_map_bf16(&p.maps[s], sl[s], rl, n, lds, 64, 128));
+        GN_TRY(tc_make_map_bf16(&p.maps[3], X->data, n, r, X->ld, 64, 64));
+        for (int s = 0; s < 3; ++s) {
+            TcGemm& g = p.g[s];
+            g.M = static_cast<int>(rl);
+            g.N = static_cast<int>(r);
+            g.K = static_cast<int>(n);
+            g.bn = static_cast<int>(std::min<long long>(256, (r + 63) / 64 * 64));
+            g.a_mn = 0;
+            g.b_mn = 1;
+            g.nsrc = 1;
+            g.a_map[0] = s;
+            g.b_map[0] = 3;
+            g.D = cl[s];
+            g.ldd = r;
+        }
+        p.ngemm = 3;
+        GN_TRY(tc_launch(h, &p));
+        GN_TRY(sum3_f32_to_f64(h, c_hi, c_mid, c_lo, rl, r, r, core->C, r));
+    }
+    // Householder QR of a copy of C.
+    GN_CUDA_TRY(cudaMemcpy2DAsync(W, r * sizeof(double), core->C, r * sizeof(double), r * sizeof(double), rl,
+                                  cudaMemcpyDeviceToDevice, h->stream));
+    GN_TRY(householder_qr(h, W, rl, r, r, core->Q, r, core->R, r, inner, inner_bytes));
+    core->k = r;
+    core->sgn = 0;
+    core->rinv_est = 0.0;
+    if (mode == GN_MODE_PLAIN) return GN_OK;
+
+    GN_TRY(core_diagnostics(h, core->R, r, r, eps, 1, DIAG_ITERS, est_d, k_d, zscr, sizeof(double) * std::max<long long>(r, 64)));
+    int k_h = 0;
+    double est_h = 0.0;
+    GN_CUDA_TRY(cudaMemcpyAsync(&k_h, k_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    GN_CUDA_TRY(cudaMemcpyAsync(&est_h, est_d, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    GN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    core->rinv_est = est_h;
+    const int use_sgn = (mode == GN_MODE_SGN) || (eps > 0.0 && est_h * eps >= 1.0);
+    core->sgn = use_sgn;
+    if (!use_sgn) return GN_OK;
+    core->k = k_h;
+    if (k_h >= r) return GN_OK;
+    if (k_h == 0) return GN_ERR_NONFINITE;   // every |R_ii| <= eps: nothing left of the core
+    // Section 5.1.1: QR of R_1^T (r x k), R_1 = R[0:k, :].
+    GN_TRY(transpose_rows_f64(h, core->R, k_h, r, r, k_h, W2, k_h));
+    GN_TRY(householder_qr(h, W2, r, k_h, k_h, core->Q2, r, core->R2, r, inner, inner_bytes));
+    return GN_OK;
+}
+
+gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_core_t* core, gn_mat* F,
+                     gn_mat* G, void* ws, size_t ws_bytes) {
+    if (!h || !AX || !YtA || !core || !F || !G || !ws) return GN_ERR_INVALID_ARG;
+    const long long m = AX->rows, r = core->r, l = core->l, k = core->k, n = YtA->cols;
+    if (k < 1 || k > r) return GN_ERR_INVALID_ARG;
+    GN_TRY(check_mat(AX, m, r));
+    GN_TRY(check_mat(YtA, r + l, n));
+    if (!F->data || !G->data || F->dtype != GN_F64 || G->dtype != GN_F64) return GN_ERR_DTYPE;
+    if (F->rows != m || F->cols < k || G->rows < k || G->cols != n || F->ld < F->cols || G->ld < n)
+        return GN_ERR_SHAPE;
+    if (AX->dtype != GN_F64 && AX->dtype != GN_F32) return GN_ERR_DTYPE;
+    if (YtA->dtype != GN_F64 && YtA->dtype != GN_F32) return GN_ERR_DTYPE;
+    if (ws_bytes < factors_ws(m, r, h->sm_count)) return GN_ERR_WORKSPACE;
+    double* Fd = static_cast<double*>(F->data);
+    double* Gd = static_cast<double*>(G->data);
+    double* gws = static_cast<double*>(ws);
+    const bool truncated = core->sgn && k < r;
+    if (!truncated) {
+        // F = AX R^{-1}
+        if (AX->dtype == GN_F32) {
+            GN_TRY(copy_f32_to_f64(h, static_cast<const float*>(AX->data), m, r, AX->ld, Fd, F->ld));
+        } else {
+            GN_CUDA_TRY(cudaMemcpy2DAsync(Fd, F->ld * 8, AX->data, AX->ld * 8, r * 8, m, cudaMemcpyDeviceToDevice,
+                                          h->stream));
+        }
+        GN_TRY(trsm_right_upper(h, Fd, m, r, F->ld, core->R, r, 0, gws, ws_bytes));
+    } else {
+        // F = (AX Q_2) R_2^{-T}
+        if (AX->dtype == GN_F32)
+            GN_TRY(dgemm_a32(h, m, k, r, 1.0, static_cast<const float*>(AX->data), AX->ld, 0, core->Q2, r, 0,
+                             0.0, Fd, F->ld, gws, ws_bytes));
+        else
+            GN_TRY(dgemm(h, m, k, r, 1.0, static_cast<const double*>(AX->data), AX->ld, 0, core->Q2, r, 0, 0.0,
+                         Fd, F->ld, gws, ws_bytes));
+        GN_TRY(trsm_right_upper(h, Fd, m, k, F->ld, core->R2, r, 1, gws, ws_bytes));
+    }
+    // G = Q_1^T (Y^T A)
+    if (YtA->dtype == GN_F32)
+        GN_TRY(dgemm_b32(h, k, n, r + l, 1.0, core->Q, r, 1, static_cast<const float*>(YtA->data), YtA->ld, 0,
+                         0.0, Gd, G->ld, gws, ws_bytes));
+    else
+        GN_TRY(dgemm(h, k, n, r + l, 1.0, core->Q, r, 1, static_cast<const double*>(YtA->data), YtA->ld, 0, 0.0,
+                     Gd, G->ld, gws, ws_bytes));
+    return GN_OK;
+}
+
+gn_status gn_approx(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, double eps, int32_t mode,
+                    gn_mat* AX, gn_mat* YtA, gn_core_t* core, gn_mat* F, gn_mat* G, void* ws, size_t ws_bytes) {
+    GN_TRY(gn_sketch(h, A, X, Y, AX, YtA, ws, ws_bytes));
+    GN_TRY(gn_core(h, YtA, X, eps, mode, core, ws, ws_bytes));
+    return gn_factors(h, AX, YtA, core, F, G, ws, ws_bytes);
+}
+
+gn_status gn_error_fro2(gn_handle h, const gn_mat* A, const gn_mat* F, const gn_mat* G, double* out, void* ws,
+                        size_t ws_bytes) {
+    if (!h || !A || !F || !G || !out || !ws) return GN_ERR_INVALID_ARG;
+    const long long m = A->rows, n = A->cols, k = F->cols;
+    GN_TRY(check_mat(A, m, n));
+    GN_TRY(check_mat(F, m, k));
+    GN_TRY(check_mat(G, k, n));
+    if (F->dtype != GN_F64 || G->dtype != GN_F64) return GN_ERR_DTYPE;
+    return error_fro2(h, A->data, A->dtype, A->lo, m, n, A->ld, static_cast<const double*>(F->data), F->ld,
+                      static_cast<const double*>(G->data), G->ld, k, out, static_cast<double*>(ws), ws_bytes);
+}
+
+gn_status gn_hmt(gn_handle h, const gn_mat* A, const gn_mat* X, gn_mat* Q, gn_mat* B, void* ws, size_t ws_bytes) {
+    if (!h || !A || !X || !Q || !B || !ws) return GN_ERR_INVALID_ARG;
+    const long long m = A->rows, n = A->cols, r = X->cols;
+    if (r < 1 || r > std::min(m, n)) return GN_ERR_SHAPE;
+    GN_TRY(check_mat(A, m, n));
+    GN_TRY(check_mat(X, n, r));
+    GN_TRY(check_mat(Q, m, r));
+    GN_TRY(check_mat(B, r, n));
+    if (A->dtype != GN_F64 || X->dtype != GN_F64 || Q->dtype != GN_F64 || B->dtype != GN_F64) return GN_ERR_DTYPE;
+    if (ws_bytes < hmt_ws(m, n, r, h->sm_count)) return GN_ERR_WORKSPACE;
+    Carve cv{static_cast<char*>(ws), ws_bytes, 0, true};
+    double* W = cv.take<double>(m * r);
+    double* Rx = cv.take<double>(r * r);
+    size_t inner_bytes = 0;
+    double* inner = cv.rest(&inner_bytes);
+    if (!cv.ok) return GN_ERR_WORKSPACE;
+    // AX (Algorithm 1, step 2), then its Householder QR (step 3)
+    GN_TRY(dgemm(h, m, r, n, 1.0, static_cast<const double*>(A->data), A->ld, 0,
+                 static_cast<const double*>(X->data), X->ld, 0, 0.0, W, r, inner, inner_bytes));
+    GN_TRY(householder_qr(h, W, m, r, r, static_cast<double*>(Q->data), Q->ld, Rx, r, inner, inner_bytes));
+    // B = Q^T A (step 4; a second pass over A)
+    return dgemm(h, r, n, m, 1.0, static_cast<const double*>(Q->data), Q->ld, 1,
+                 static_cast<const double*>(A->data), A->ld, 0, 0.0, static_cast<double*>(B->data), B->ld, inner,
+                 inner_bytes);
+}
+
+}  // extern "C"

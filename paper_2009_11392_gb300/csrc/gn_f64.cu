@@ -1,0 +1,869 @@
+// FP64 kernels of the stable core of generalized Nystrom (Section 5.1) and of
+// the plain FP64 GN path:
+//   * a tiled FP64 GEMM (DFMA) with optional split-K, used for the FP64
+//     sketches, the core product C = (Y^T A) X, the WY updates of the QR and
+//     the factor products;
+//   * blocked Householder QR with compact-WY trailing updates (Algorithm 2
+//     step 2, "Y^T A X = QR"), diag(R) made non-negative;
+//   * blocked right triangular solves F R = B and F R^T = B (eq. 5.1's AX/R
+//     and Section 5.1.1's Q_2 R_2^{-T});
+//   * the truncation rank and the power-method estimate of ||R^{-1}||_2
+//     (Sections 5.1.1 and 5.1.2);
+//   * operand quantisation (FP64/FP32 -> BF16, split BF16) and the fused
+//     ||A - F G||_F^2 accumulation.
+// On GB300 FP64 runs on the CUDA cores at a small fraction of the FP32 rate,
+// so these kernels aim at keeping the DFMA pipes busy (enough CTAs, split-K for
+// skinny products) rather than at data movement.
+#include "gn_internal.cuh"
+
+#include <algorithm>
+
+namespace gn {
+namespace {
+
+constexpr int GT = 64;    // GEMM tile (M and N)
+constexpr int GK = 16;    // GEMM K step
+constexpr int GTHREADS = 256;
+
+template <typename TA>
+__device__ __forceinline__ double ld_a(const TA* p) { return static_cast<double>(*p); }
+template <>
+__device__ __forceinline__ double ld_a<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return static_cast<double>(__bfloat162float(*p));
+}
+
+// Epilogue modes of the tiled FP64 product.
+enum { EPI_STORE = 0, EPI_PARTIAL = 1, EPI_ERR = 2 };
+
+struct ErrArgs {
+    const void* A;     // reference matrix of ||A - F G||
+    const void* A_lo;  // low part for split bf16
+    int a_dtype;
+    long long lda;
+    double* partial;   // one double per CTA
+};
+
+__device__ __forceinline__ double load_ref(const ErrArgs& e, long long i, long long j) {
+    const long long off = i * e.lda + j;
+    switch (e.a_dtype) {
+        case GN_F64: return static_cast<const double*>(e.A)[off];
+        case GN_F32: return static_cast<double>(static_cast<const float*>(e.A)[off]);
+        case GN_BF16:
+            return static_cast<double>(__bfloat162float(static_cast<const __nv_bfloat16*>(e.A)[off]));
+        default:
+            return static_cast<double>(__bfloat162float(static_cast<const __nv_bfloat16*>(e.A)[off])) +
+                   static_cast<double>(__bfloat162float(static_cast<const __nv_bfloat16*>(e.A_lo)[off]));
+    }
+}
+
+// C tile = alpha * op(A) op(B) (+ beta C); 64 x 64 tile, 256 threads, each a
+// 4 x 4 block of outputs at rows ty + 16 i and columns tx + 16 j.
+template <typename TA, typename TB_, int EPI>
+__global__ void __launch_bounds__(GTHREADS) dgemm_kernel(
+    int M, int N, int K, double alpha, const TA* __restrict__ A, long long lda, int ta,
+    const TB_* __restrict__ B, long long ldb, int tb, double beta, double* C, long long ldc,
+    double* part, int kchunk, ErrArgs err) {
+    __shared__ double As[GK][GT + 1];
+    __shared__ double Bs[GK][GT + 1];
+    __shared__ double red[GTHREADS / 32];
+    const int m0 = blockIdx.y * GT;
+    const int n0 = blockIdx.x * GT;
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    const int tx = threadIdx.x & 15;
+    const int ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    for (int k0 = kbeg; k0 < kend; k0 += GK) {
+#pragma unroll
+        for (int e = threadIdx.x; e < GT * GK; e += GTHREADS) {
+            int mm, kk;
+            if (ta) { mm = e & 63; kk = e >> 6; } else { kk = e & 15; mm = e >> 4; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            double v = 0.0;
+            if (gm < M && gk < kend)
+                v = ta ? ld_a(A + static_cast<long long>(gk) * lda + gm)
+                       : ld_a(A + static_cast<long long>(gm) * lda + gk);
+            As[kk][mm] = v;
+        }
+#pragma unroll
+        for (int e = threadIdx.x; e < GT * GK; e += GTHREADS) {
+            int nn, kk;
+            if (tb) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
+            const int gn_ = n0 + nn, gk = k0 + kk;
+            double v = 0.0;
+            if (gn_ < N && gk < kend)
+                v = tb ? ld_a(B + static_cast<long long>(gn_) * ldb + gk)
+                       : ld_a(B + static_cast<long long>(gk) * ldb + gn_);
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+
+    if (EPI == EPI_ERR) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int gm = m0 + ty + 16 * i, gn_ = n0 + tx + 16 * j;
+                if (gm < M && gn_ < N) {
+                    const double d = load_ref(err, gm, gn_) - acc[i][j];
+                    s = fma(d, d, s);
+                }
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < GTHREADS / 32; ++w) t += red[w];
+            err.partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gm = m0 + ty + 16 * i, gn_ = n0 + tx + 16 * j;
+            if (gm < M && gn_ < N) {
+                if (EPI == EPI_PARTIAL) {
+                    part[(static_cast<long long>(blockIdx.z) * M + gm) * N + gn_] = alpha * acc[i][j];
+                } else {
+                    double* c = C + static_cast<long long>(gm) * ldc + gn_;
+                    *c = beta == 0.0 ? alpha * acc[i][j] : fma(beta, *c, alpha * acc[i][j]);
+                }
+            }
+        }
+}
+
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const double* __restrict__ part,
+                                     double beta, double* C, long long ldc) {
+    const long long total = static_cast<long long>(M) * N;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < splits; ++z) s += part[z * total + e];
+        const long long i = e / N, j = e % N;
+        double* c = C + i * ldc + j;
+        *c = beta == 0.0 ? s : fma(beta, *c, s);
+    }
+}
+
+__global__ void reduce_sum_kernel(const double* __restrict__ part, long long n, double* out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) t += red[w];
+        *out = t;
+    }
+}
+
+int choose_splits(long long M, long long N, long long K, int sm_count) {
+    const long long tiles = ((M + GT - 1) / GT) * ((N + GT - 1) / GT);
+    if (tiles >= sm_count || K < 512) return 1;
+    long long s = (2LL * sm_count + tiles - 1) / tiles;
+    s = std::min(s, K / 256);
+    s = std::min<long long>(s, 64);
+    return static_cast<int>(std::max<long long>(s, 1));
+}
+
+template <typename TA, typename TB_>
+gn_status dgemm_impl(gn_handle h, long long M, long long N, long long K, double alpha, const TA* A,
+                     long long lda, int ta, const TB_* B, long long ldb, int tb, double beta,
+                     double* C, long long ldc, double* ws, size_t ws_bytes) {
+    if (M <= 0 || N <= 0) return GN_OK;
+    if (K <= 0) {   // C = beta C
+        if (beta == 0.0) return set_zero_f64(h, C, M, N, ldc);
+        dim3 grid(static_cast<unsigned>((N + GT - 1) / GT), static_cast<unsigned>((M + GT - 1) / GT), 1);
+        ErrArgs e{};
+        dgemm_kernel<TA, TB_, EPI_STORE><<<grid, GTHREADS, 0, h->stream>>>(
+            (int)M, (int)N, 0, 0.0, A, lda, ta, B, ldb, tb, beta, C, ldc, nullptr, 1, e); count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        return GN_OK;
+    }
+    int splits = choose_splits(M, N, K, h->sm_count);
+    while (splits > 1 && static_cast<size_t>(splits) * M * N * sizeof(double) > ws_bytes) --splits;
+    if (ws == nullptr) splits = 1;
+    int kchunk = static_cast<int>(((K + splits - 1) / splits + GK - 1) / GK * GK);
+    splits = static_cast<int>((K + kchunk - 1) / kchunk);
+    dim3 grid(static_cast<unsigned>((N + GT - 1) / GT), static_cast<unsigned>((M + GT - 1) / GT),
+              static_cast<unsigned>(splits));
+    ErrArgs e{};
+    if (splits == 1) {
+        dgemm_kernel<TA, TB_, EPI_STORE><<<grid, GTHREADS, 0, h->stream>>>(
+            (int)M, (int)N, (int)K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, nullptr, kchunk, e); count_launch();
+    } else {
+        dgemm_kernel<TA, TB_, EPI_PARTIAL><<<grid, GTHREADS, 0, h->stream>>>(
+            (int)M, (int)N, (int)K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, ws, kchunk, e); count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        const long long total = M * N;
+        const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 4LL * h->sm_count));
+        splitk_reduce_kernel<<<blocks, 256, 0, h->stream>>>((int)M, (int)N, splits, ws, beta, C, ldc); count_launch();
+    }
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+// --------------------------------------------------------------------------
+// Householder QR
+// --------------------------------------------------------------------------
+constexpr int QR_THREADS = 512;
+constexpr int QR_WARPS = QR_THREADS / 32;
+constexpr int QR_JB = 16;                 // panel width
+constexpr size_t QR_SMEM_PANEL_MAX = 196 * 1024;
+
+// Sum of `n` per-thread values across the CTA; results in out[0..n).
+template <int NV>
+__device__ void block_sum_vec(double (&v)[NV], int n, double* red /* [QR_WARPS][NV] */, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        if (c >= n) break;
+        double s = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp * NV + c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < n) {
+        double s = 0.0;
+        for (int w = 0; w < QR_WARPS; ++w) s += red[w * NV + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Factor the panel W[j0:M, j0:j0+jb] in place: R above the diagonal, the
+// Householder vectors (unit leading entry) below it.  Writes the explicit
+// vectors into V (column j0+c holds v in rows j0+c..M-1, zeros above), tau,
+// and the upper-triangular T of the compact WY form H_0...H_{jb-1} = I - V T V^T.
+__global__ void __launch_bounds__(QR_THREADS) qr_panel_kernel(double* W, long long ld, int M, int j0,
+                                                              int jb, double* V, long long ldv,
+                                                              double* tau, double* T, int use_smem) {
+    extern __shared__ double sh[];
+    __shared__ double red[QR_WARPS * QR_JB];
+    __shared__ double wsum[QR_JB];
+    __shared__ double s_tau, s_beta, s_scale;
+    __shared__ double tloc[QR_JB * QR_JB];
+    __shared__ double tauloc[QR_JB];
+    const int Mp = M - j0;
+    const int tid = threadIdx.x;
+    double* P;
+    long long ldp;
+    if (use_smem) {
+        P = sh;
+        ldp = jb;
+        for (long long e = tid; e < static_cast<long long>(Mp) * jb; e += QR_THREADS) {
+            const long long i = e / jb;
+            const int c = static_cast<int>(e % jb);
+            P[e] = W[(j0 + i) * ld + j0 + c];
+        }
+        __syncthreads();
+    } else {
+        P = W + static_cast<long long>(j0) * ld + j0;
+        ldp = ld;
+    }
+
+    for (int c = 0; c < jb; ++c) {
+        double acc1[1] = {0.0};
+        for (int i = c + 1 + tid; i < Mp; i += QR_THREADS) {
+            const double x = P[i * ldp + c];
+            acc1[0] = fma(x, x, acc1[0]);
+        }
+        block_sum_vec<1>(acc1, 1, red, wsum);
+        if (tid == 0) {
+            const double alpha = P[static_cast<long long>(c) * ldp + c];
+            const double tail = wsum[0];
+            if (tail == 0.0) {
+                s_tau = 0.0;
+                s_beta = alpha;
+                s_scale = 0.0;
+            } else {
+                const double nx = sqrt(fma(alpha, alpha, tail));
+                const double beta = alpha >= 0.0 ? -nx : nx;
+                s_tau = (beta - alpha) / beta;
+                s_beta = beta;
+                s_scale = 1.0 / (alpha - beta);
+            }
+        }
+        __syncthreads();
+        const double t = s_tau;
+        if (t != 0.0) {
+            const double sc = s_scale;
+            for (int i = c + 1 + tid; i < Mp; i += QR_THREADS) P[i * ldp + c] *= sc;
+            __syncthreads();
+            const int nrem = jb - c - 1;
+            if (nrem > 0) {
+                double w[QR_JB];
+#pragma unroll
+                for (int q = 0; q < QR_JB; ++q) w[q] = 0.0;
+                for (int i = c + tid; i < Mp; i += QR_THREADS) {
+                    const double vi = (i == c) ? 1.0 : P[i * ldp + c];
+                    const double* row = P + i * ldp + c + 1;
+#pragma unroll
+                    for (int q = 0; q < QR_JB; ++q)
+                        if (q < nrem) w[q] = fma(vi, row[q], w[q]);
+                }
+                block_sum_vec<QR_JB>(w, nrem, red, wsum);
+                for (int i = c + tid; i < Mp; i += QR_THREADS) {
+                    const double vi = (i == c) ? 1.0 : P[i * ldp + c];
+                    double* row = P + i * ldp + c + 1;
+#pragma unroll
+                    for (int q = 0; q < QR_JB; ++q)
+                        if (q < nrem) row[q] = fma(-t * vi, wsum[q], row[q]);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            P[static_cast<long long>(c) * ldp + c] = s_beta;
+            tauloc[c] = t;
+            tau[j0 + c] = t;
+        }
+        __syncthreads();
+    }
+
+    // Explicit V and the write-back of the panel.
+    for (long long e = tid; e < static_cast<long long>(Mp) * jb; e += QR_THREADS) {
+        const long long i = e / jb;
+        const int c = static_cast<int>(e % jb);
+        const double pv = P[i * ldp + c];
+        double v;
+        if (i < c) v = 0.0;
+        else if (i == c) v = 1.0;
+        else v = tauloc[c] == 0.0 ? 0.0 : pv;
+        V[(j0 + i) * ldv + j0 + c] = v;
+        if (use_smem) W[(j0 + i) * ld + j0 + c] = pv;
+    }
+    __syncthreads();
+
+    // Gram products g_c[q] = v_q^T v_c (q < c) and T (forward, columnwise).
+    for (int c = 1; c < jb; ++c) {
+        double g[QR_JB];
+#pragma unroll
+        for (int q = 0; q < QR_JB; ++q) g[q] = 0.0;
+        for (int i = c + tid; i < Mp; i += QR_THREADS) {   // v_c is zero above row c
+            const double vc = (i == c) ? 1.0 : (tauloc[c] == 0.0 ? 0.0 : P[i * ldp + c]);
+#pragma unroll
+            for (int q = 0; q < QR_JB; ++q) {
+                if (q < c) {
+                    const double vq = (i == q) ? 1.0 : (tauloc[q] == 0.0 ? 0.0 : P[i * ldp + q]);
+                    g[q] = fma(vq, vc, g[q]);
+                }
+            }
+        }
+        block_sum_vec<QR_JB>(g, c, red, tloc + c * QR_JB);   // row c of tloc holds g for column c
+    }
+    if (tid == 0) {
+        double Tm[QR_JB][QR_JB];
+        for (int a = 0; a < QR_JB; ++a)
+            for (int b = 0; b < QR_JB; ++b) Tm[a][b] = 0.0;
+        for (int c = 0; c < jb; ++c) {
+            const double tc = tauloc[c];
+            Tm[c][c] = tc;
+            for (int a = 0; a < c; ++a) {
+                double s = 0.0;
+                for (int b = a; b < c; ++b) s = fma(Tm[a][b], tloc[c * QR_JB + b], s);
+                Tm[a][c] = -tc * s;
+            }
+        }
+        for (int a = 0; a < jb; ++a)
+            for (int b = 0; b < jb; ++b) T[a * jb + b] = Tm[a][b];
+    }
+}
+
+__global__ void qr_init_q_kernel(double* Q, long long ldq, int M, int N) {
+    const long long total = static_cast<long long>(M) * N;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / N, j = e % N;
+        Q[i * ldq + j] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+// R = sign-normalised upper triangle of W[0:N, 0:N]; flips the matching Q columns.
+__global__ void qr_finish_kernel(const double* W, long long ld, int M, int N, double* Q, long long ldq,
+                                 double* R, long long ldr) {
+    const long long totalR = static_cast<long long>(N) * N;
+    const long long totalQ = static_cast<long long>(M) * N;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+         e < totalR + totalQ; e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (e < totalR) {
+            const long long i = e / N, j = e % N;
+            const double s = W[i * ld + i] < 0.0 ? -1.0 : 1.0;
+            R[i * ldr + j] = (j >= i) ? s * W[i * ld + j] : 0.0;
+        } else {
+            const long long f = e - totalR;
+            const long long i = f / N, j = f % N;
+            if (W[j * ld + j] < 0.0) Q[i * ldq + j] = -Q[i * ldq + j];
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Triangular solves on 32-column diagonal blocks, one thread per row of F.
+// --------------------------------------------------------------------------
+constexpr int TB = 32;
+
+// trans == 0: F[:, J] <- F[:, J] R_JJ^{-1}   (forward over columns)
+// trans == 1: F[:, J] <- F[:, J] R_JJ^{-T}   (backward over columns)
+__global__ void trsm_diag_kernel(double* F, long long m, long long ldf, int j0, int jb,
+                                 const double* R, long long ldr, int trans) {
+    __shared__ double Rs[TB][TB + 1];
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+        const int a = e / TB, b = e % TB;
+        Rs[a][b] = (a < jb && b < jb) ? R[static_cast<long long>(j0 + a) * ldr + j0 + b] : 0.0;
+    }
+    __syncthreads();
+    const long long row = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (row >= m) return;
+    double* f = F + row * ldf + j0;
+    double x[TB];
+#pragma unroll
+    for (int j = 0; j < TB; ++j) x[j] = (j < jb) ? f[j] : 0.0;
+    if (!trans) {
+#pragma unroll
+        for (int j = 0; j < TB; ++j) {
+            if (j < jb) {
+                double s = x[j];
+#pragma unroll
+                for (int i = 0; i < TB; ++i)
+                    if (i < j) s = fma(-x[i], Rs[i][j], s);
+                x[j] = s / Rs[j][j];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = TB - 1; j >= 0; --j) {
+            if (j < jb) {
+                double s = x[j];
+#pragma unroll
+                for (int i = 0; i < TB; ++i)
+                    if (i > j && i < jb) s = fma(-x[i], Rs[j][i], s);
+                x[j] = s / Rs[j][j];
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < TB; ++j)
+        if (j < jb) f[j] = x[j];
+}
+
+// --------------------------------------------------------------------------
+// Core diagnostics: truncation rank and est ||R^{-1}||_2 (one CTA).
+// --------------------------------------------------------------------------
+constexpr int DG_THREADS = 1024;
+
+__device__ double dg_block_sum(double s, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < DG_THREADS / 32; ++w) t += red[w];
+    return t;
+}
+
+// Solves in place on vector z (length r, in global scratch):
+//   lower == 1: R^T y = z (forward);  lower == 0: R w = z (backward).
+__device__ void dg_tri_solve(const double* R, long long ldr, int r, double* z, int lower) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nb = (r + 31) / 32;
+    for (int bi = 0; bi < nb; ++bi) {
+        const int b = lower ? bi : nb - 1 - bi;
+        const int j0 = b * 32;
+        const int jb = min(32, r - j0);
+        if (warp == 0) {
+            double zl = lane < jb ? z[j0 + lane] : 0.0;
+            if (lower) {
+                for (int i = 0; i < jb; ++i) {
+                    double yi = __shfl_sync(0xffffffffu, zl, i);
+                    yi = yi / R[(j0 + i) * ldr + j0 + i];
+                    if (lane == i) zl = yi;
+                    if (lane > i && lane < jb) zl = fma(-R[(j0 + i) * ldr + j0 + lane], yi, zl);
+                }
+            } else {
+                for (int i = jb - 1; i >= 0; --i) {
+                    double wi = __shfl_sync(0xffffffffu, zl, i);
+                    wi = wi / R[(j0 + i) * ldr + j0 + i];
+                    if (lane == i) zl = wi;
+                    if (lane < i) zl = fma(-R[(j0 + lane) * ldr + j0 + i], wi, zl);
+                }
+            }
+            if (lane < jb) z[j0 + lane] = zl;
+        }
+        __syncthreads();
+        if (lower) {   // z_j -= sum_{i in block} R[i][j] y_i for j after the block
+            for (int j = j0 + jb + threadIdx.x; j < r; j += DG_THREADS) {
+                double s = z[j];
+                for (int i = 0; i < jb; ++i) s = fma(-R[(j0 + i) * ldr + j], z[j0 + i], s);
+                z[j] = s;
+            }
+        } else {       // z_j -= sum_{i in block} R[j][i] w_i for j before the block
+            for (int j = threadIdx.x; j < j0; j += DG_THREADS) {
+                double s = z[j];
+                const double* rr = R + j * ldr + j0;
+                for (int i = 0; i < jb; ++i) s = fma(-rr[i], z[j0 + i], s);
+                z[j] = s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(DG_THREADS) core_diag_kernel(const double* R, long long ldr, int r,
+                                                               double eps, int want_est, int iters,
+                                                               double* z, double* est_out, int* k_out) {
+    __shared__ double red[32];
+    __shared__ int kmin;
+    if (threadIdx.x == 0) kmin = r;
+    __syncthreads();
+    for (int i = threadIdx.x; i < r; i += DG_THREADS)
+        if (fabs(R[static_cast<long long>(i) * ldr + i]) <= eps) atomicMin(&kmin, i);
+    __syncthreads();
+    if (threadIdx.x == 0) *k_out = kmin;
+    if (!want_est) {
+        if (threadIdx.x == 0) *est_out = 0.0;
+        return;
+    }
+    // zero diagonal -> +inf
+    int has_zero = 0;
+    for (int i = threadIdx.x; i < r; i += DG_THREADS)
+        if (R[static_cast<long long>(i) * ldr + i] == 0.0) has_zero = 1;
+    has_zero = __syncthreads_or(has_zero);
+    if (has_zero) {
+        if (threadIdx.x == 0) *est_out = __longlong_as_double(0x7ff0000000000000LL);
+        return;
+    }
+    const double inv = 1.0 / sqrt(static_cast<double>(r));
+    for (int i = threadIdx.x; i < r; i += DG_THREADS) z[i] = inv;
+    __syncthreads();
+    double est = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        dg_tri_solve(R, ldr, r, z, 1);
+        dg_tri_solve(R, ldr, r, z, 0);
+        double s = 0.0;
+        for (int i = threadIdx.x; i < r; i += DG_THREADS) s = fma(z[i], z[i], s);
+        const double nw = sqrt(dg_block_sum(s, red));
+        if (!isfinite(nw)) {
+            est = __longlong_as_double(0x7ff0000000000000LL);
+            break;
+        }
+        est = sqrt(nw);
+        if (nw == 0.0) break;
+        const double sc = 1.0 / nw;
+        __syncthreads();
+        for (int i = threadIdx.x; i < r; i += DG_THREADS) z[i] *= sc;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *est_out = est;
+}
+
+// --------------------------------------------------------------------------
+// Elementwise helpers
+// --------------------------------------------------------------------------
+__global__ void copy_f32_f64_kernel(const float* __restrict__ s, long long rows, long long cols,
+                                    long long lds, double* d, long long ldd) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e % cols;
+        d[i * ldd + j] = static_cast<double>(s[i * lds + j]);
+    }
+}
+
+__global__ void split3_kernel(const float* __restrict__ s, long long rows, long long cols, long long lds,
+                              __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* lo, long long ldd) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e % cols;
+        const float x = s[i * lds + j];
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(m);
+        hi[i * ldd + j] = h;
+        mid[i * ldd + j] = m;
+        lo[i * ldd + j] = __float2bfloat16_rn(r2);
+    }
+}
+
+__global__ void sum3_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                            const float* __restrict__ c, long long rows, long long cols, long long lds,
+                            double* d, long long ldd) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e % cols;
+        const long long o = i * lds + j;
+        d[i * ldd + j] = static_cast<double>(a[o]) + static_cast<double>(b[o]) + static_cast<double>(c[o]);
+    }
+}
+
+// FP64 / FP32 -> BF16 (round to nearest even through FP32); optional low part.
+__global__ void quantize_kernel(const void* __restrict__ src, int src_f64, long long rows, long long cols,
+                                long long lds, __nv_bfloat16* hi, __nv_bfloat16* lo, long long ldd) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e % cols;
+        const float x = src_f64 ? static_cast<float>(static_cast<const double*>(src)[i * lds + j])
+                                : static_cast<const float*>(src)[i * lds + j];
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi[i * ldd + j] = h;
+        if (lo) lo[i * ldd + j] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+}
+
+__global__ void transpose_rows_kernel(const double* __restrict__ s, long long rows, long long cols,
+                                      long long lds, long long keep, double* d, long long ldd) {
+    // d (cols x rows) = [s[0:keep, :]^T | 0]
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long j = e / rows, i = e % rows;   // d[j][i]
+        d[j * ldd + i] = (i < keep) ? s[i * lds + j] : 0.0;
+    }
+}
+
+__global__ void zero_kernel(double* p, long long rows, long long cols, long long ld) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        p[(e / cols) * ld + e % cols] = 0.0;
+}
+
+int ew_blocks(gn_handle h, long long total) {
+    return static_cast<int>(std::max<long long>(1, std::min<long long>((total + 255) / 256, 8LL * h->sm_count)));
+}
+
+}  // namespace
+
+// ============================================================================ host
+size_t dgemm_ws_bytes(long long M, long long N, long long K, int sm_count) {
+    return static_cast<size_t>(choose_splits(M, N, K, sm_count)) * M * N * sizeof(double);
+}
+
+gn_status dgemm(gn_handle h, long long M, long long N, long long K, double alpha, const double* A,
+                long long lda, int ta, const double* B, long long ldb, int tb, double beta, double* C,
+                long long ldc, double* ws, size_t ws_bytes) {
+    return dgemm_impl<double, double>(h, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, ws, ws_bytes);
+}
+
+gn_status dgemm_a32(gn_handle h, long long M, long long N, long long K, double alpha, const float* A,
+                    long long lda, int ta, const double* B, long long ldb, int tb, double beta, double* C,
+                    long long ldc, double* ws, size_t ws_bytes) {
+    return dgemm_impl<float, double>(h, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, ws, ws_bytes);
+}
+
+gn_status dgemm_b32(gn_handle h, long long M, long long N, long long K, double alpha, const double* A,
+                    long long lda, int ta, const float* B, long long ldb, int tb, double beta, double* C,
+                    long long ldc, double* ws, size_t ws_bytes) {
+    return dgemm_impl<double, float>(h, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, ws, ws_bytes);
+}
+
+gn_status set_zero_f64(gn_handle h, double* p, long long rows, long long cols, long long ld) {
+    if (rows <= 0 || cols <= 0) return GN_OK;
+    zero_kernel<<<ew_blocks(h, rows * cols), 256, 0, h->stream>>>(p, rows, cols, ld); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+// QR workspace: V (M x N), tau (N), T per panel (jb x jb), Z1, Z2 (jb x N), GEMM split-K.
+size_t qr_ws_bytes(long long M, long long N, int sm_count) {
+    const long long panels = (N + QR_JB - 1) / QR_JB;
+    size_t b = sizeof(double) * (M * N + N + panels * QR_JB * QR_JB + 2 * QR_JB * N);
+    b += dgemm_ws_bytes(QR_JB, N, M, sm_count);
+    return b + 256;
+}
+
+gn_status householder_qr(gn_handle h, double* W, long long M, long long N, long long ld, double* Q,
+                         long long ldq, double* R, long long ldr, double* ws, size_t ws_bytes) {
+    if (M < N || N <= 0) return GN_ERR_SHAPE;
+    if (ws_bytes < qr_ws_bytes(M, N, h->sm_count)) return GN_ERR_WORKSPACE;
+    const long long panels = (N + QR_JB - 1) / QR_JB;
+    double* V = ws;
+    double* tau = V + M * N;
+    double* Tall = tau + N;
+    double* Z1 = Tall + panels * QR_JB * QR_JB;
+    double* Z2 = Z1 + QR_JB * N;
+    double* gws = Z2 + QR_JB * N;
+    const size_t gws_bytes = ws_bytes - sizeof(double) * (gws - ws);
+
+    static bool attr = false;
+    if (!attr) {
+        GN_CUDA_TRY(cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(QR_SMEM_PANEL_MAX)));
+        attr = true;
+    }
+    for (long long j0 = 0; j0 < N; j0 += QR_JB) {
+        const int jb = static_cast<int>(std::min<long long>(QR_JB, N - j0));
+        const long long Mp = M - j0;
+        const size_t panel_bytes = static_cast<size_t>(Mp) * jb * sizeof(double);
+        const int use_smem = panel_bytes <= QR_SMEM_PANEL_MAX ? 1 : 0;
+        double* T = Tall + (j0 / QR_JB) * QR_JB * QR_JB;
+        qr_panel_kernel<<<1, QR_THREADS, use_smem ? panel_bytes : 0, h->stream>>>(
+            W, ld, static_cast<int>(M), static_cast<int>(j0), jb, V, N, tau, T, use_smem); count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        const long long N2 = N - j0 - jb;
+        if (N2 > 0) {
+            double* W2 = W + j0 * ld + j0 + jb;
+            const double* Vb = V + j0 * N + j0;
+            // Z1 = V^T W2 ; Z2 = T^T Z1 ; W2 -= V Z2
+            GN_TRY(dgemm(h, jb, N2, Mp, 1.0, Vb, N, 1, W2, ld, 0, 0.0, Z1, N2, gws, gws_bytes));
+            GN_TRY(dgemm(h, jb, N2, jb, 1.0, T, jb, 1, Z1, N2, 0, 0.0, Z2, N2, gws, gws_bytes));
+            GN_TRY(dgemm(h, Mp, N2, jb, -1.0, Vb, N, 0, Z2, N2, 0, 1.0, W2, ld, gws, gws_bytes));
+        }
+    }
+    // Q = H_0 ... H_{N-1} [I; 0], applied block by block from the last panel.
+    qr_init_q_kernel<<<ew_blocks(h, M * N), 256, 0, h->stream>>>(Q, ldq, static_cast<int>(M),
+                                                                  static_cast<int>(N)); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    for (long long j0 = ((N - 1) / QR_JB) * QR_JB; j0 >= 0; j0 -= QR_JB) {
+        const int jb = static_cast<int>(std::min<long long>(QR_JB, N - j0));
+        const long long Mp = M - j0;
+        const long long Nq = N - j0;
+        double* Qs = Q + j0 * ldq + j0;
+        const double* Vb = V + j0 * N + j0;
+        const double* T = Tall + (j0 / QR_JB) * QR_JB * QR_JB;
+        GN_TRY(dgemm(h, jb, Nq, Mp, 1.0, Vb, N, 1, Qs, ldq, 0, 0.0, Z1, Nq, gws, gws_bytes));
+        GN_TRY(dgemm(h, jb, Nq, jb, 1.0, T, jb, 0, Z1, Nq, 0, 0.0, Z2, Nq, gws, gws_bytes));
+        GN_TRY(dgemm(h, Mp, Nq, jb, -1.0, Vb, N, 0, Z2, Nq, 0, 1.0, Qs, ldq, gws, gws_bytes));
+    }
+    qr_finish_kernel<<<ew_blocks(h, N * N + M * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(M),
+                                                                          static_cast<int>(N), Q, ldq,
+                                                                          R, ldr); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+size_t trsm_ws_bytes(long long m, long long k, int sm_count) {
+    return dgemm_ws_bytes(m, TB, k, sm_count) + 256;
+}
+
+gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, long long ldf,
+                           const double* R, long long ldr, int trans, double* ws, size_t ws_bytes) {
+    if (m <= 0 || k <= 0) return GN_OK;
+    const long long nb = (k + TB - 1) / TB;
+    const int blocks = static_cast<int>((m + 127) / 128);
+    for (long long bi = 0; bi < nb; ++bi) {
+        const long long b = trans ? nb - 1 - bi : bi;
+        const long long j0 = b * TB;
+        const int jb = static_cast<int>(std::min<long long>(TB, k - j0));
+        if (!trans && j0 > 0) {
+            // F[:, J] -= F[:, 0:j0] R[0:j0, J]
+            GN_TRY(dgemm(h, m, jb, j0, -1.0, F, ldf, 0, R + j0, ldr, 0, 1.0, F + j0, ldf, ws, ws_bytes));
+        }
+        if (trans && j0 + jb < k) {
+            // F[:, J] -= F[:, J+] R[J, J+]^T
+            const long long kk = k - j0 - jb;
+            GN_TRY(dgemm(h, m, jb, kk, -1.0, F + j0 + jb, ldf, 0, R + j0 * ldr + j0 + jb, ldr, 1, 1.0,
+                         F + j0, ldf, ws, ws_bytes));
+        }
+        trsm_diag_kernel<<<blocks, 128, 0, h->stream>>>(F, m, ldf, static_cast<int>(j0), jb, R, ldr, trans); count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+    }
+    return GN_OK;
+}
+
+gn_status core_diagnostics(gn_handle h, const double* R, long long r, long long ldr, double eps,
+                           int want_estimate, int iters, double* est_out, int* k_out, double* ws,
+                           size_t ws_bytes) {
+    if (ws_bytes < static_cast<size_t>(r) * sizeof(double)) return GN_ERR_WORKSPACE;
+    core_diag_kernel<<<1, DG_THREADS, 0, h->stream>>>(R, ldr, static_cast<int>(r), eps, want_estimate,
+                                                      iters, ws, est_out, k_out); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+gn_status copy_f32_to_f64(gn_handle h, const float* src, long long rows, long long cols, long long lds,
+                          double* dst, long long ldd) {
+    if (rows * cols == 0) return GN_OK;
+    copy_f32_f64_kernel<<<ew_blocks(h, rows * cols), 256, 0, h->stream>>>(src, rows, cols, lds, dst, ldd); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+gn_status split3_bf16(gn_handle h, const float* src, long long rows, long long cols, long long lds,
+                      __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* lo, long long ldd) {
+    if (rows * cols == 0) return GN_OK;
+    split3_kernel<<<ew_blocks(h, rows * cols), 256, 0, h->stream>>>(src, rows, cols, lds, hi, mid, lo, ldd); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+gn_status sum3_f32_to_f64(gn_handle h, const float* a, const float* b, const float* c, long long rows,
+                          long long cols, long long lds, double* dst, long long ldd) {
+    if (rows * cols == 0) return GN_OK;
+    sum3_kernel<<<ew_blocks(h, rows * cols), 256, 0, h->stream>>>(a, b, c, rows, cols, lds, dst, ldd); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+gn_status quantize_bf16(gn_handle h, const void* src, int src_f64, long long rows, long long cols,
+                        long long lds, __nv_bfloat16* hi, __nv_bfloat16* lo, long long ldd) {
+    if (rows * cols == 0) return GN_OK;
+    quantize_kernel<<<ew_blocks(h, rows * cols), 256, 0, h->stream>>>(src, src_f64, rows, cols, lds, hi, lo,
+                                                                      ldd); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+gn_status transpose_rows_f64(gn_handle h, const double* src, long long rows, long long cols,
+                             long long lds, long long keep_rows, double* dst, long long ldd) {
+    if (rows * cols == 0) return GN_OK;
+    transpose_rows_kernel<<<ew_blocks(h, rows * cols), 256, 0, h->stream>>>(src, rows, cols, lds, keep_rows,
+                                                                            dst, ldd); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+size_t error_ws_bytes(long long m, long long n, int) {
+    return static_cast<size_t>(((m + GT - 1) / GT) * ((n + GT - 1) / GT)) * sizeof(double) + 256;
+}
+
+gn_status error_fro2(gn_handle h, const void* A, int a_dtype, const void* A_lo, long long m, long long n,
+                     long long lda, const double* F, long long ldf, const double* G, long long ldg,
+                     long long k, double* out, double* ws, size_t ws_bytes) {
+    if (ws_bytes < error_ws_bytes(m, n, h->sm_count)) return GN_ERR_WORKSPACE;
+    dim3 grid(static_cast<unsigned>((n + GT - 1) / GT), static_cast<unsigned>((m + GT - 1) / GT), 1);
+    ErrArgs e{A, A_lo, a_dtype, lda, ws};
+    const int kk = static_cast<int>(k);
+    dgemm_kernel<double, double, EPI_ERR><<<grid, GTHREADS, 0, h->stream>>>(
+        (int)m, (int)n, kk, 1.0, F, ldf, 0, G, ldg, 0, 0.0, nullptr, 0, nullptr, kk > 0 ? kk : 1, e); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    reduce_sum_kernel<<<1, 1024, 0, h->stream>>>(ws, static_cast<long long>(grid.x) * grid.y, out); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+}  // namespace gn

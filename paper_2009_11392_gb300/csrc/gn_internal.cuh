@@ -1,0 +1,132 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/gn.h"
+
+// Device status word layout (int32 slots of the handle's 64-byte status block).
+enum { GN_DEV_STATUS = 0, GN_DEV_WHERE = 1 };
+
+struct gn_handle_s {
+    int device;
+    int sm_count;
+    cudaStream_t stream;
+    int32_t* dstatus;          // device: [0] latched gn_status, [1] where
+    uint64_t wait_limit_ns;
+};
+
+#define GN_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return GN_ERR_CUDA;          \
+    } while (0)
+
+#define GN_TRY(expr)                                        \
+    do {                                                    \
+        gn_status _s = (expr);                              \
+        if (_s != GN_OK) return _s;                         \
+    } while (0)
+
+// --------------------------------------------------------------------------
+// Tensor-core (tcgen05) multi-GEMM engine: D_g = sum_s A_{g,s} B_{g,s}
+// --------------------------------------------------------------------------
+namespace gn {
+
+// Number of kernels this library has launched (all threads, all handles).
+unsigned long long launch_count();
+void count_launch();
+
+constexpr int TC_MAX_MAPS = 12;
+constexpr int TC_MAX_GEMMS = 4;
+constexpr int TC_MAX_SRC = 3;
+
+struct TcGemm {
+    int M, N, K;             // D is M x N, contraction length K
+    int bn;                  // N tile: multiple of 64 (MN-major B) or 16 (K-major B), <= 256
+    int a_mn, b_mn;          // 0: K-major operand, 1: MN-major operand
+    int nsrc;                // number of (A, B) pairs summed into D
+    int a_map[TC_MAX_SRC];   // tensor-map indices
+    int b_map[TC_MAX_SRC];
+    int tiles_m, tiles_n, kblocks;
+    int tile_base;           // first global tile index of this GEMM
+    float* D;
+    long long ldd;
+    int vec4;                // D rows 16-byte aligned -> float4 stores
+};
+
+struct TcParams {
+    CUtensorMap maps[TC_MAX_MAPS];
+    TcGemm g[TC_MAX_GEMMS];
+    int ngemm;
+    int total_tiles;
+    int32_t* status;
+    unsigned long long wait_limit_ns;
+};
+
+// Host helpers (gn_tc.cu).
+gn_status tc_make_map_bf16(CUtensorMap* map, const void* base, long long rows, long long cols,
+                           long long ld, int box_cols, int box_rows);
+gn_status tc_launch(gn_handle h, TcParams* p);
+
+// --------------------------------------------------------------------------
+// FP64 / FP32 helper kernels (gn_f64.cu)
+// --------------------------------------------------------------------------
+// C = alpha * op(A) op(B) + beta * C  (row-major, FP64).  ta / tb: operand is
+// stored transposed (op(A)[i][k] = A[k*lda + i]).  ws (may be null) enables
+// split-K for skinny outputs: bytes needed = dgemm_ws_bytes(M, N, K).
+size_t dgemm_ws_bytes(long long M, long long N, long long K, int sm_count);
+gn_status dgemm(gn_handle h, long long M, long long N, long long K, double alpha,
+                const double* A, long long lda, int ta, const double* B, long long ldb, int tb,
+                double beta, double* C, long long ldc, double* ws, size_t ws_bytes);
+
+// Same product with an FP32 A operand (promoted to FP64 on load).
+gn_status dgemm_a32(gn_handle h, long long M, long long N, long long K, double alpha,
+                    const float* A, long long lda, int ta, const double* B, long long ldb, int tb,
+                    double beta, double* C, long long ldc, double* ws, size_t ws_bytes);
+
+// Same product with an FP32 B operand.
+gn_status dgemm_b32(gn_handle h, long long M, long long N, long long K, double alpha,
+                    const double* A, long long lda, int ta, const float* B, long long ldb, int tb,
+                    double beta, double* C, long long ldc, double* ws, size_t ws_bytes);
+
+// Householder QR (blocked, compact WY).  W (M x N, ld) is overwritten; Q (M x N,
+// ldq) and R (N x N, ldr) receive the thin factors with diag(R) >= 0.
+size_t qr_ws_bytes(long long M, long long N, int sm_count);
+gn_status householder_qr(gn_handle h, double* W, long long M, long long N, long long ld,
+                         double* Q, long long ldq, double* R, long long ldr,
+                         double* ws, size_t ws_bytes);
+
+// Right triangular solves, FP64, in place on F (m x k):
+//   upper == 1, trans == 0: F <- F R^{-1}   (R upper, k x k)
+//   upper == 1, trans == 1: F <- F R^{-T}
+size_t trsm_ws_bytes(long long m, long long k, int sm_count);
+gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, long long ldf,
+                           const double* R, long long ldr, int trans, double* ws, size_t ws_bytes);
+
+// est ||R^{-1}||_2 by `iters` power iterations (device result in *out);
+// also the truncation rank k (first |R_ii| <= eps) in *k_out.
+gn_status core_diagnostics(gn_handle h, const double* R, long long r, long long ldr, double eps,
+                           int want_estimate, int iters, double* est_out, int* k_out,
+                           double* ws, size_t ws_bytes);
+
+gn_status copy_f32_to_f64(gn_handle h, const float* src, long long rows, long long cols,
+                          long long lds, double* dst, long long ldd);
+gn_status split3_bf16(gn_handle h, const float* src, long long rows, long long cols, long long lds,
+                      __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* lo, long long ldd);
+gn_status sum3_f32_to_f64(gn_handle h, const float* a, const float* b, const float* c,
+                          long long rows, long long cols, long long lds, double* dst, long long ldd);
+gn_status quantize_bf16(gn_handle h, const void* src, int src_f64, long long rows, long long cols,
+                        long long lds, __nv_bfloat16* hi, __nv_bfloat16* lo, long long ldd);
+gn_status transpose_rows_f64(gn_handle h, const double* src, long long rows, long long cols,
+                             long long lds, long long keep_rows, double* dst, long long ldd);
+gn_status error_fro2(gn_handle h, const void* A, int a_dtype, const void* A_lo, long long m,
+                     long long n, long long lda, const double* F, long long ldf, const double* G,
+                     long long ldg, long long k, double* out, double* ws, size_t ws_bytes);
+size_t error_ws_bytes(long long m, long long n, int sm_count);
+gn_status set_zero_f64(gn_handle h, double* p, long long rows, long long cols, long long ld);
+
+}  // namespace gn

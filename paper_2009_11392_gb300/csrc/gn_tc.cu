@@ -1,0 +1,463 @@
+// Tensor-core engine for the sketch products of generalized Nystrom
+// (Algorithm 2, step 2: AX and Y^T A) and for the split-precision core product
+// C = (Y^T A) X.  One persistent, warp-specialised sm_103a kernel computes up
+// to four independent GEMMs D_g = sum_s A_{g,s} B_{g,s} in a single launch:
+//
+//   warp 0      : TMA producer -- cp.async.bulk.tensor tiles of both operands
+//                 into a 4-stage shared-memory ring (128B swizzle), one
+//                 mbarrier with a transaction count per stage;
+//   warp 1      : tcgen05.mma issuer (one thread) -- 128 x bn x 16 BF16 MMAs
+//                 with FP32 accumulators in tensor memory, two accumulator
+//                 buffers of 256 columns so the epilogue of one tile overlaps
+//                 the main loop of the next; also owns the TMEM allocation;
+//   warps 2..5  : epilogue -- tcgen05.ld 32 lanes x 32 columns per warp,
+//                 FP32 stores to global memory.
+//
+// Operands are used in their natural row-major layout: the A operand of a
+// GEMM may be K-major (rows of A contiguous along K) or MN-major, likewise B.
+// For AX, A is K-major and X (n x r, r contiguous) is an MN-major B; for
+// Y^T A, Y (m x (r+l)) is an MN-major A and the data matrix A an MN-major B.
+// Every wait on an mbarrier is bounded by a time limit; on expiry the kernel
+// latches GN_ERR_TIMEOUT in the status word, drains its copies and MMAs,
+// frees its tensor memory and returns.
+#include "gn_internal.cuh"
+
+#include <string.h>
+
+namespace gn {
+namespace {
+
+constexpr int BM = 128;                          // M tile (tcgen05 M)
+constexpr int BK = 64;                           // K per stage: 64 bf16 = one 128B swizzle row
+constexpr int STAGES = 4;
+constexpr int A_STAGE_BYTES = BM * BK * 2;       // 16 KB
+constexpr int B_STAGE_BYTES = 256 * BK * 2;      // 32 KB (bn <= 256)
+constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
+constexpr int ACC_COLS = 256;
+constexpr int TMEM_COLS = 512;
+constexpr int NUM_THREADS = 192;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait.  Returns false when the limit expired or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit,
+                                          volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for tcgen05 (128B swizzle, version 1).
+//   start: shared address; lbo / sbo: leading / stride byte offsets.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t start, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((start & 0x3FFFF) >> 4);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32;
+    d |= static_cast<uint64_t>(1) << 46;   // descriptor version for tcgen05
+    d |= static_cast<uint64_t>(2) << 61;   // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16 with BF16 inputs and an FP32 accumulator.
+__device__ __forceinline__ uint32_t instr_desc_bf16(int m, int n, int a_mn, int b_mn) {
+    return (1u << 4)                                   // D format: F32
+           | (1u << 7)                                 // A format: BF16
+           | (1u << 10)                                // B format: BF16
+           | (static_cast<uint32_t>(a_mn) << 15)       // A major-ness
+           | (static_cast<uint32_t>(b_mn) << 16)       // B major-ness
+           | (static_cast<uint32_t>(n >> 3) << 17)     // N / 8
+           | (static_cast<uint32_t>(m >> 4) << 24);    // M / 16
+}
+
+struct TileCoord {
+    int g, tm, tn;
+};
+
+__device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t) {
+    TileCoord c;
+    c.g = 0;
+#pragma unroll 1
+    for (int i = 1; i < p.ngemm; ++i)
+        if (t >= p.g[i].tile_base) c.g = i;
+    const TcGemm& G = p.g[c.g];
+    const int local = t - G.tile_base;
+    if (G.a_mn) {   // A operand is the small sketch (Y^T): walk M fastest so the big B is shared
+        c.tm = local % G.tiles_m;
+        c.tn = local / G.tiles_m;
+    } else {        // walk N fastest so the big A row panel is shared
+        c.tm = local / G.tiles_n;
+        c.tn = local % G.tiles_n;
+    }
+    return c;
+}
+
+__device__ void latch(int32_t* status, int code, int where, volatile int* abort_flag) {
+    *abort_flag = 1;
+    if (atomicCAS(&status[GN_DEV_STATUS], 0, code) == 0) status[GN_DEV_WHERE] = where;
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __grid_constant__ TcParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;            // 1024-aligned stage ring
+    uint8_t* base_ptr = smem_raw + (base - raw);
+    const uint32_t bars = base + STAGES * STAGE_BYTES;        // barrier block
+    auto full_bar = [&](int s) { return bars + 8u * s; };
+    auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
+    auto tfull_bar = [&](int a) { return bars + 8u * (2 * STAGES + a); };
+    auto tempty_bar = [&](int a) { return bars + 8u * (2 * STAGES + 2 + a); };
+    const uint32_t final_bar = bars + 8u * (2 * STAGES + 4);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 5));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long limit = p.wait_limit_ns;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), 128);
+        }
+        mbar_init(final_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t ephase = 0;
+            uint32_t issued_mask = 0;            // stages that ever received a load
+            uint32_t last_parity = 0;            // parity of the last armed phase per stage
+            bool ok = true;
+            for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
+                const TileCoord c = decode_tile(p, t);
+                const TcGemm& G = p.g[c.g];
+                const int nkb = G.nsrc * G.kblocks;
+                const uint32_t bytes = A_STAGE_BYTES + G.bn * BK * 2;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(empty_bar(stage), ephase ^ 1u, limit, abort_flag)) {
+                        latch(p.status, GN_ERR_TIMEOUT, 1, abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    const int src = kb / G.kblocks;
+                    const int kk = kb - src * G.kblocks;
+                    const CUtensorMap* ma = &p.maps[G.a_map[src]];
+                    const CUtensorMap* mb = &p.maps[G.b_map[src]];
+                    const uint32_t sa = base + stage * STAGE_BYTES;
+                    const uint32_t sb = sa + A_STAGE_BYTES;
+                    const uint32_t fb = full_bar(stage);
+                    mbar_arrive_expect_tx(fb, bytes);
+                    issued_mask |= 1u << stage;
+                    last_parity = (last_parity & ~(1u << stage)) | (ephase << stage);
+                    if (G.a_mn) {
+                        tma_load_2d(sa, ma, fb, c.tm * BM, kk * BK);
+                        tma_load_2d(sa + 8192, ma, fb, c.tm * BM + 64, kk * BK);
+                    } else {
+                        tma_load_2d(sa, ma, fb, kk * BK, c.tm * BM);
+                    }
+                    if (G.b_mn) {
+                        for (int j = 0; j < G.bn / 64; ++j)
+                            tma_load_2d(sb + 8192 * j, mb, fb, c.tn * G.bn + 64 * j, kk * BK);
+                    } else {
+                        tma_load_2d(sb, mb, fb, kk * BK, c.tn * G.bn);
+                    }
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        ephase ^= 1u;
+                    }
+                }
+            }
+            // Drain: every armed stage must have landed before shared memory is released.
+            for (int s = 0; s < STAGES; ++s)
+                if (issued_mask & (1u << s)) {
+                    volatile int no_abort = 0;
+                    if (!mbar_wait(full_bar(s), (last_parity >> s) & 1u, limit, &no_abort))
+                        latch(p.status, GN_ERR_TIMEOUT, 2, abort_flag);
+                }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t fphase = 0;
+            int acc = 0;
+            uint32_t aphase = 0;
+            bool ok = true;
+            bool issued_any = false;
+            for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
+                const TileCoord c = decode_tile(p, t);
+                const TcGemm& G = p.g[c.g];
+                const int nkb = G.nsrc * G.kblocks;
+                const uint32_t idesc = instr_desc_bf16(BM, G.bn, G.a_mn, G.b_mn);
+                if (!mbar_wait(tempty_bar(acc), aphase ^ 1u, limit, abort_flag)) {
+                    latch(p.status, GN_ERR_TIMEOUT, 3, abort_flag);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(full_bar(stage), fphase, limit, abort_flag)) {
+                        latch(p.status, GN_ERR_TIMEOUT, 4, abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = base + stage * STAGE_BYTES;
+                    const uint32_t sb = sa + A_STAGE_BYTES;
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k) {
+                        const uint64_t ad = G.a_mn ? smem_desc(sa + 2048u * k, 8192u, 1024u)
+                                                   : smem_desc(sa + 32u * k, 16u, 1024u);
+                        const uint64_t bd = G.b_mn ? smem_desc(sb + 2048u * k, 8192u, 1024u)
+                                                   : smem_desc(sb + 32u * k, 16u, 1024u);
+                        tc_mma_bf16(d_tmem, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                    }
+                    issued_any = true;
+                    tc_commit(empty_bar(stage));
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        fphase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                tc_commit(tfull_bar(acc));
+                if (++acc == 2) {
+                    acc = 0;
+                    aphase ^= 1u;
+                }
+            }
+            if (issued_any) {   // all MMAs complete before tensor memory is released
+                tc_commit(final_bar);
+                volatile int no_abort = 0;
+                if (!mbar_wait(final_bar, 0, limit, &no_abort))
+                    latch(p.status, GN_ERR_TIMEOUT, 5, abort_flag);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3;   // TMEM lane quarter this warp may access
+        int acc = 0;
+        uint32_t aphase = 0;
+        for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
+            const TileCoord c = decode_tile(p, t);
+            const TcGemm& G = p.g[c.g];
+            const bool got = mbar_wait(tfull_bar(acc), aphase, limit, abort_flag);
+            if (!__all_sync(0xffffffffu, got)) {   // warp-uniform exit: tcgen05.ld is .sync.aligned
+                if (lane == 0) latch(p.status, GN_ERR_TIMEOUT, 6, abort_flag);
+                break;
+            }
+            tc_fence_after();
+            const int row = c.tm * BM + q * 32 + lane;
+            const bool row_ok = row < G.M;
+            float* drow = G.D + static_cast<long long>(row_ok ? row : 0) * G.ldd;
+            for (int c0 = 0; c0 < G.bn; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * ACC_COLS + c0, v);
+                const int col0 = c.tn * G.bn + c0;
+                if (!row_ok || col0 >= G.N) continue;
+                if (G.vec4 && col0 + 32 <= G.N) {
+                    float4* dst = reinterpret_cast<float4*>(drow + col0);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                             __uint_as_float(v[4 * j + 2]),
+                                             __uint_as_float(v[4 * j + 3]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < G.N) drow[col0 + j] = __uint_as_float(v[j]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tempty_bar(acc));
+            if (++acc == 2) {
+                acc = 0;
+                aphase ^= 1u;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+}  // namespace
+
+gn_status tc_make_map_bf16(CUtensorMap* map, const void* base, long long rows, long long cols,
+                           long long ld, int box_cols, int box_rows) {
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * 2) % 16 != 0) return GN_ERR_ALIGNMENT;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return GN_ERR_CUDA;
+    memset(map, 0, sizeof(*map));
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * 2)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GN_OK : GN_ERR_CUDA;
+}
+
+gn_status tc_launch(gn_handle h, TcParams* p) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        attr_set = true;
+    }
+    int total = 0;
+    for (int i = 0; i < p->ngemm; ++i) {
+        TcGemm& G = p->g[i];
+        if (G.bn < 16 || G.bn > 256 || (G.b_mn && G.bn % 64) || G.bn % 16) return GN_ERR_INVALID_ARG;
+        G.tiles_m = static_cast<int>((G.M + BM - 1) / BM);
+        G.tiles_n = static_cast<int>((G.N + G.bn - 1) / G.bn);
+        G.kblocks = static_cast<int>((G.K + BK - 1) / BK);
+        G.tile_base = total;
+        G.vec4 = ((reinterpret_cast<uintptr_t>(G.D) & 15) == 0 && G.ldd % 4 == 0) ? 1 : 0;
+        total += G.tiles_m * G.tiles_n;
+    }
+    p->total_tiles = total;
+    p->status = h->dstatus;
+    p->wait_limit_ns = h->wait_limit_ns;
+    if (total == 0) return GN_OK;
+    const int grid = total < h->sm_count ? total : h->sm_count;
+    tc_multigemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, h->stream>>>(*p); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+}  // namespace gn

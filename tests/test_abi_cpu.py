@@ -1,0 +1,58 @@
+"""Host-side checks of the C ABI that need no GPU: the shared library loads,
+exports every entry point declared in include/gn.h, and the host-only sizing
+and validation logic behaves."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "gn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gn_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2009_11392_gb300 as gn
+    declared = _declared_symbols()
+    assert len(declared) >= 15
+    assert sorted(gn.ABI_SYMBOLS) == declared
+    L = ctypes.CDLL(gn.lib_path())
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_status_strings():
+    import paper_2009_11392_gb300 as gn
+    assert gn.lib.gn_status_string(0) == b"ok"
+    assert gn.lib.gn_status_string(7) == b"device-side wait timed out"
+    assert gn.lib.gn_status_string(99) == b"unknown status"
+
+
+def test_workspace_size_validates_shapes():
+    import paper_2009_11392_gb300 as gn
+    b = ctypes.c_size_t()
+    ws = gn.lib.gn_workspace_size
+    assert ws(1000, 500, 20, 10, gn.F64, ctypes.byref(b)) == 0 and b.value > 0
+    small = b.value
+    assert ws(32768, 16384, 1000, 500, gn.BF16, ctypes.byref(b)) == 0 and b.value > small
+    assert ws(1000, 500, 0, 10, gn.F64, ctypes.byref(b)) == 2          # r < 1
+    assert ws(1000, 500, 501, 10, gn.F64, ctypes.byref(b)) == 2        # r > min(m, n)
+    assert ws(1000, 500, 20, 0, gn.F64, ctypes.byref(b)) == 2          # l < 1
+    assert ws(1000, 500, 20, 10, gn.F32, ctypes.byref(b)) == 3         # no F32 operand path
+    assert ws(1000, 500, 20, 10, gn.F64, None) == 1
+
+
+def test_null_arguments_rejected_on_host():
+    import paper_2009_11392_gb300 as gn
+    assert gn.lib.gn_create(None, None) == 1
+    assert gn.lib.gn_destroy(None) == 1
+    assert gn.lib.gn_sketch(None, None, None, None, None, None, None, 0) == 1
+    assert gn.lib.gn_core(None, None, None, 0.0, 0, None, None, 0) == 1
+    assert gn.lib.gn_factors(None, None, None, None, None, None, None, 0) == 1
+    assert gn.lib.gn_hmt(None, None, None, None, None, None, 0) == 1
+    assert gn.lib.gn_sync_status(None) == 1

@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Inputs come from gn_synth (seeded); the same arrays go to both sides.  Sizes
+span several tiles of every kernel and end in ragged tails.  Tolerances:
+  * FP64 path: <= 1e-10 relative Frobenius for sketches, factors and A_hat;
+  * tensor-core sketches on bf16 operands: exact when every product and
+    partial sum is an integer below 2^24, otherwise within the FP32
+    accumulation bound |err_ij| <= 2 K u32 (|A||X|)_ij;
+  * quantisation: bit-exact against the oracle's rounding.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import gn_synth
+from oracle import gn_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def gn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2009_11392_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def H(gn):
+    return gn.Handle()
+
+
+def cu(t):
+    return torch.as_tensor(t).cuda()
+
+
+def npy(t):
+    return t.detach().double().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def bf16_operand(gn, t):
+    """bf16 copy with an 8-aligned leading dimension (exact when t is bf16-representable)."""
+    p = gn.padded(t.shape[0], t.shape[1], torch.bfloat16, "cuda")
+    p.copy_(t.to(torch.bfloat16))
+    return p
+
+
+# ------------------------------------------------------------------ quantisation
+@pytest.mark.parametrize("shape", [(257, 131), (64, 8)])
+def test_quantize_matches_oracle_bitwise(gn, H, shape):
+    x = gn_synth.gaussian(shape, 5, 0) * 3.0
+    hi = H.quantize(cu(x))
+    hi2, lo2 = H.quantize(cu(x), split=True)
+    torch.cuda.synchronize()
+    q = O.quantize_bf16(x.numpy())
+    oh, ol = O.split_bf16(x.numpy())
+    assert np.array_equal(npy(hi), q)
+    assert np.array_equal(npy(hi2), oh)
+    assert np.array_equal(npy(lo2), ol)
+
+
+# ---------------------------------------------------------------- FP64 sketches
+@pytest.mark.parametrize("m,n,r,l", [(1000, 500, 20, 10), (333, 200, 37, 19)])
+def test_fp64_sketch_parity(gn, H, m, n, r, l):
+    A = gn_synth.gaussian((m, n), 1, 0)
+    X, Y = gn_synth.sketches(m, n, r, l, 2)
+    AX = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float64, device="cuda")
+    ws = H.workspace(m, n, r, l, gn.F64)
+    H.sketch(cu(A), cu(X), cu(Y), AX, YtA, ws)
+    oAX, oYtA = O.sketch(A.numpy(), X.numpy(), Y.numpy())
+    assert rel(npy(AX), oAX) <= 1e-13
+    assert rel(npy(YtA), oYtA) <= 1e-13
+    assert H.sync_status() == 0
+
+
+# --------------------------------------------------------- tensor-core sketches
+@pytest.mark.parametrize("m,n,r,l", [(300, 200, 70, 35), (128, 64, 16, 8), (520, 390, 130, 65)])
+def test_tc_sketch_exact_on_integer_inputs(gn, H, m, n, r, l):
+    """Small integers are exact in bf16, and every partial sum stays an
+    integer below 2^24, so FP32 accumulation is exact: bitwise parity."""
+    g = torch.Generator().manual_seed(m * 7 + n)
+    A = torch.randint(-3, 4, (m, n), generator=g).double()
+    X = torch.randint(-3, 4, (n, r), generator=g).double()
+    Y = torch.randint(-3, 4, (m, r + l), generator=g).double()
+    AX = torch.full((m, r), float("nan"), dtype=torch.float32, device="cuda")
+    YtA = torch.full((r + l, n), float("nan"), dtype=torch.float32, device="cuda")
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    H.sketch(bf16_operand(gn, A), bf16_operand(gn, X), bf16_operand(gn, Y), AX, YtA, ws)
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch(A.numpy(), X.numpy(), Y.numpy())
+    assert np.array_equal(npy(AX), oAX)
+    assert np.array_equal(npy(YtA), oYtA)
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_tc_sketch_fp32_accumulation_bound(gn, H, split):
+    m, n, r, l = 700, 450, 100, 50
+    A = gn_synth.gaussian((m, n), 11, 0)
+    X, Y = gn_synth.sketches(m, n, r, l, 12)
+    Aq, Xq, Yq = (torch.from_numpy(O.quantize_bf16(t.numpy())) for t in (A, X, Y))
+    AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+    ws = H.workspace(m, n, r, l, gn.BF16X2 if split else gn.BF16)
+    if split:
+        hi, lo = O.split_bf16(A.numpy())
+        Ah, Al = bf16_operand(gn, torch.from_numpy(hi)), bf16_operand(gn, torch.from_numpy(lo))
+        H.sketch(Ah, bf16_operand(gn, Xq), bf16_operand(gn, Yq), AX, YtA, ws, A_lo=Al)
+        Aref = hi + lo
+    else:
+        H.sketch(bf16_operand(gn, Aq), bf16_operand(gn, Xq), bf16_operand(gn, Yq), AX, YtA, ws)
+        Aref = Aq.numpy()
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch(Aref, Xq.numpy(), Yq.numpy())
+    bAX = 2 * n * U32 * (np.abs(Aref) @ np.abs(Xq.numpy())) * (2 if split else 1)
+    bYA = 2 * m * U32 * (np.abs(Yq.numpy()).T @ np.abs(Aref)) * (2 if split else 1)
+    assert np.all(np.abs(npy(AX) - oAX) <= bAX)
+    assert np.all(np.abs(npy(YtA) - oYtA) <= bYA)
+
+
+# ------------------------------------------------------------------- core + factors
+def _core_tensors(gn, r, l):
+    return gn.Core.empty(r, l, "cuda")
+
+
+def test_fp64_core_qr_parity(gn, H):
+    m, n, r, l = 400, 300, 48, 24
+    A = gn_synth.gaussian((m, n), 21, 0) * torch.pow(0.9, torch.arange(n, dtype=torch.float64))
+    X, Y = gn_synth.sketches(m, n, r, l, 22)
+    oAX, oYtA = O.sketch(A.numpy(), X.numpy(), Y.numpy())
+    c = O.core(oYtA, X.numpy(), 0.0, O.PLAIN)
+    ws = H.workspace(m, n, r, l, gn.F64)
+    core = _core_tensors(gn, r, l)
+    H.core(cu(oYtA), cu(X), 0.0, gn.PLAIN, core, ws)
+    assert H.sync_status() == 0
+    assert rel(npy(core.C), c["C"]) <= 1e-13
+    kappa = np.linalg.cond(c["R"])
+    tol = max(1e-11, 50 * kappa * 1.1e-16)
+    assert rel(npy(core.R), c["R"]) <= tol
+    assert rel(npy(core.Q), c["Q"]) <= tol
+    assert core.k == r and core.sgn == 0
+
+
+@pytest.mark.parametrize("mode", ["plain", "auto"])
+def test_fp64_gn_config1(gn, H, mode):
+    """The 1000 x 500 geometric case: factors and A_hat at 1e-10."""
+    p = gn_synth.config1()
+    A, X, Y = p.a.numpy(), p.x.numpy(), p.y.numpy()
+    md = O.PLAIN if mode == "plain" else O.AUTO
+    Ahat, o = O.gn(A, X, Y, p.eps, md)
+    m, n = A.shape
+    r, l = p.r, p.l
+    ws = H.workspace(m, n, r, l, gn.F64)
+    AX = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float64, device="cuda")
+    F = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    G = torch.empty(r, n, dtype=torch.float64, device="cuda")
+    core = _core_tensors(gn, r, l)
+    H.approx(cu(A), cu(X), cu(Y), p.eps, gn.PLAIN if mode == "plain" else gn.AUTO, AX, YtA, core, F, G, ws)
+    assert H.sync_status() == 0
+    assert core.k == o["k"] == r
+    assert rel(npy(F), o["F"]) <= 1e-10
+    assert rel(npy(G), o["G"]) <= 1e-10
+    Ah = npy(F) @ npy(G)
+    assert rel(Ah, Ahat) <= 1e-10
+    # fused error kernel
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    H.error_fro2(cu(A), F, G, out, ws)
+    torch.cuda.synchronize()
+    assert abs(math.sqrt(out.item()) - np.linalg.norm(A - Ahat)) <= 1e-9 * np.linalg.norm(A)
+    if mode == "auto":
+        est = O.rinv_norm_estimate(o["R"], iters=6)
+        assert abs(core.rinv_est - est) <= 1e-8 * est
+
+
+def test_fp64_sgn_truncation_parity(gn, H):
+    """Exactly rank-k0 input with k0 < r: the truncated branch (Section 5.1.1)."""
+    m, n, k0, r, l = 300, 220, 9, 24, 12
+    rng = np.random.default_rng(5)
+    U, _ = np.linalg.qr(rng.standard_normal((m, k0)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, k0)))
+    A = (U * np.linspace(2.0, 1.0, k0)) @ V.T
+    X, Y = gn_synth.sketches(m, n, r, l, 6)
+    X, Y = X.numpy(), Y.numpy()
+    eps = O.scale_eps(2.0, np.linalg.norm(X, 2), np.linalg.norm(Y, 2), O.U64)
+    Ahat, o = O.gn(A, X, Y, eps, O.SGN)
+    assert o["k"] == k0
+    ws = H.workspace(m, n, r, l, gn.F64)
+    AX = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float64, device="cuda")
+    F = torch.zeros(m, r, dtype=torch.float64, device="cuda")
+    G = torch.zeros(r, n, dtype=torch.float64, device="cuda")
+    core = _core_tensors(gn, r, l)
+    H.approx(cu(A), cu(X), cu(Y), eps, gn.SGN, AX, YtA, core, F, G, ws)
+    assert H.sync_status() == 0
+    assert core.k == k0 and core.sgn == 1
+    Fk, Gk = npy(F)[:, :k0], npy(G)[:k0]
+    assert rel(Fk @ Gk, Ahat) <= 1e-10
+    assert rel(Fk @ Gk, A) <= 1e-11
+    assert rel(Fk, o["F"]) <= 1e-9 and rel(Gk, o["G"]) <= 1e-9
+
+
+def test_hmt_parity(gn, H):
+    m, n, r = 900, 400, 40
+    A = (gn_synth.gaussian((m, n), 31, 0) * torch.pow(0.95, torch.arange(n, dtype=torch.float64))).numpy()
+    X = gn_synth.gaussian((n, r), 32, 0).numpy()
+    Qo, Bo = O.hmt(A, X)
+    ws = H.workspace(m, n, r, 1, gn.F64)
+    Q = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    B = torch.empty(r, n, dtype=torch.float64, device="cuda")
+    H.hmt(cu(A), cu(X), Q, B, ws)
+    assert H.sync_status() == 0
+    assert rel(npy(Q), Qo) <= 1e-10
+    assert rel(npy(B), Bo) <= 1e-10
+
+
+# -------------------------------------------------------------- mixed-precision path
+def test_mixed_path_matches_oracle_on_quantized_inputs(gn, H):
+    """bf16 sketches + split-bf16 core product: C within FP32 accuracy, and the
+    approximation error within 1.05x of the oracle's on the same quantised A."""
+    m, n, r, l = 1200, 640, 64, 32
+    p = gn_synth.config2(m=m, n=n, r=r, l=l)
+    A = p.a.numpy()
+    Aq = O.quantize_bf16(A)
+    Xq, Yq = O.quantize_bf16(p.x.numpy()), O.quantize_bf16(p.y.numpy())
+    Ahat, o = O.gn(Aq, Xq, Yq, 0.0, O.PLAIN)
+    err_o = np.linalg.norm(Aq - Ahat)
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    Ab = bf16_operand(gn, torch.from_numpy(Aq))
+    Xb = bf16_operand(gn, torch.from_numpy(Xq))
+    Yb = bf16_operand(gn, torch.from_numpy(Yq))
+    AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+    F = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    G = torch.empty(r, n, dtype=torch.float64, device="cuda")
+    core = _core_tensors(gn, r, l)
+    H.approx(Ab, Xb, Yb, 0.0, gn.PLAIN, AX, YtA, core, F, G, ws)
+    assert H.sync_status() == 0
+    # C from the FP32 sketch, exact bf16 X: compare with the oracle's C of the GPU's Y^T A
+    Cref = O.core_matrix(npy(YtA), Xq)
+    bound = 4 * n * U32 * (np.abs(npy(YtA)) @ np.abs(Xq))
+    assert np.all(np.abs(npy(core.C) - Cref) <= bound)
+    Ah = npy(F) @ npy(G)
+    err_g = np.linalg.norm(Aq - Ah)
+    assert err_g <= 1.05 * err_o
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    H.error_fro2(Ab, F, G, out, ws)
+    torch.cuda.synchronize()
+    assert abs(math.sqrt(out.item()) - err_g) <= 1e-6 * err_g
