@@ -150,7 +150,7 @@ def cpu_oracle_sample(a, rows, seed=gn_synth.DEFAULT_SEED):
     t0 = time.perf_counter()
     AX_s, YtA_s = O.sketch(A_s, X, Y_s)
     t1 = time.perf_counter()
-    O.core(YtA_s, X, 1e-300, O.AUTO)
+    O.core(YtA_s, X, 10 * 2.0 ** -53, O.AUTO, eps_relative=True, diag_iters=6)
     t2 = time.perf_counter()
     per = (t1 - t0) * (a.m / rows) + (t2 - t1)
     desc = (f"FP64 numpy oracle: sketch of {rows} of {a.m} rows (x{a.m // rows} to the full matrix) "
@@ -225,17 +225,10 @@ def main():
     # ---- inputs (seeded, drawn on the device; FP64)
     p = gn_synth.config3(r=r, device=dev, m=m, n=n)
     A64, X64, Y64 = p.a, p.x, p.y
-    # eps of Section 4.1 rescaled to the operands: 10 u32 ||A|| ||X|| ||Y||
-    def norm2(M, it=20):
-        v = torch.ones(M.shape[1], dtype=torch.float32, device=dev)
-        M32 = M.float()
-        s = 0.0
-        for _ in range(it):
-            w = M32.T @ (M32 @ v)
-            s = math.sqrt(w.norm().item())
-            v = w / w.norm()
-        return s
-    eps = 10 * 2.0 ** -24 * norm2(A64) * norm2(X64) * norm2(Y64)
+    # Section 4.1's eps = 10u, with u the unit roundoff of the arithmetic that
+    # forms the core (FP32 accumulation here), relative to ||C||_2.
+    eps = 10 * 2.0 ** -24
+    mode = gn.AUTO | gn.EPS_RELATIVE
 
     # ---- a1: operand quantisation (reported separately)
     q0 = torch.cuda.Event(enable_timing=True)
@@ -258,7 +251,7 @@ def main():
         H.sketch(A_op, Xb, Yb, AX, YtA, ws, A_lo=A_lo)
         if ev is not None:
             ev[1].record(stream)
-        H.core(YtA, Xb, eps, gn.AUTO, core, ws)
+        H.core(YtA, Xb, eps, mode, core, ws)
 
     for _ in range(a.warmup):
         step(Ab)
@@ -316,7 +309,7 @@ def main():
         Xd.copy_(Xh, non_blocking=True)
         Yd.copy_(Yh, non_blocking=True)
         H.sketch(Ad, Xd, Yd, AX, YtA, ws)
-        H.core(YtA, Xd, eps, gn.AUTO, core, ws)
+        H.core(YtA, Xd, eps, mode, core, ws)
         for o, s in zip(outs, (AX, YtA, core.Q, core.R)):
             o.copy_(s, non_blocking=True)
 
@@ -341,7 +334,7 @@ def main():
 
     extras = {}
     if not a.no_extras and rank == 0:
-        extras = side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, ws, AX, YtA, core, peaks)
+        extras = side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mode, ws, AX, YtA, core, peaks)
 
     cpu = None
     if rank == 0 and world >= 1 and not a.no_extras:
@@ -378,7 +371,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks,
             "quantize_ms": quantize_ms,
-            "eps": eps,
+            "eps_rel": eps, "eps_abs": core.eps_abs, "c_norm_est": core.c_norm_est,
             "k": core.k, "sgn": core.sgn, "rinv_est": core.rinv_est,
         }
         line.update(extras)
@@ -388,7 +381,7 @@ def main():
         dist.destroy_process_group()
 
 
-def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, ws, AX, YtA, core, peaks):
+def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mode, ws, AX, YtA, core, peaks):
     """Outside the timed region: split-BF16 throughput, factors, errors of each
     path against the FP64 A, and the plain FP64 GPU path on the same matrix."""
     m, n, r = a.m, a.n, a.r
@@ -419,7 +412,7 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, ws,
     Ahi, Alo = H.quantize(A64, split=True)
     s0, s1 = ev(), ev()
     H.sketch(Ahi, Xb, Yb, AX, YtA, ws, A_lo=Alo)
-    H.core(YtA, Xb, eps, gn.AUTO, core, ws)
+    H.core(YtA, Xb, eps, mode, core, ws)
     torch.cuda.synchronize()
     reps = max(3, a.steps // 2)
     k0, k1 = ev(), ev()
@@ -428,7 +421,7 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, ws,
         k0.record(stream)
         H.sketch(Ahi, Xb, Yb, AX, YtA, ws, A_lo=Alo)
         k1.record(stream)
-        H.core(YtA, Xb, eps, gn.AUTO, core, ws)
+        H.core(YtA, Xb, eps, mode, core, ws)
     s1.record(stream)
     torch.cuda.synchronize()
     split_ms = s0.elapsed_time(s1) / reps
@@ -444,12 +437,12 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, ws,
     YtA64 = torch.empty(r + l, n, dtype=torch.float64, device=dev)
     c64 = gn.Core.empty(r, l, dev)
     ws64 = H.workspace(m, n, r, l, gn.F64)
-    eps64 = eps * 2.0 ** -29
+    eps64 = 10 * 2.0 ** -53
     p0, p1, p2 = ev(), ev(), ev()
     p0.record(stream)
     H.sketch(A64, X64, Y64, AX64, YtA64, ws64)
     p1.record(stream)
-    H.core(YtA64, X64, eps64, gn.AUTO, c64, ws64)
+    H.core(YtA64, X64, eps64, mode, c64, ws64)
     p2.record(stream)
     torch.cuda.synchronize()
     fp64_ms = p0.elapsed_time(p2)

@@ -61,7 +61,11 @@ typedef enum {
 typedef enum {
     GN_MODE_PLAIN = 0,   /* plain GN (eq. 2.1 via eq. 5.1): k = r, F = (AX) R^{-1} */
     GN_MODE_SGN = 1,     /* stabilised GN (eq. 2.2, Section 5.1.1): truncate at eps */
-    GN_MODE_AUTO = 2     /* Section 5.1.2: plain unless est||R^{-1}||_2 >= 1/eps */
+    GN_MODE_AUTO = 2,    /* Section 5.1.2: plain unless est||R^{-1}||_2 * eps >= 100 */
+    /* Flag OR'd into the mode: eps is relative to ||C||_2 (estimated by 6 power
+     * iterations on R from the all-ones vector), so eps = 10u reproduces the
+     * paper's eps = 10u for ||A|| = 1 and O(1) sketches (Section 4.1). */
+    GN_EPS_RELATIVE = 0x100
 } gn_mode;
 
 typedef struct {
@@ -83,7 +87,7 @@ typedef struct {
  * After gn_core() returns, the host fields hold: k (truncation rank, = r for
  * plain GN), sgn (1 when the truncated branch was taken), rinv_est (the
  * power-method estimate of ||R^{-1}||_2; computed in SGN and AUTO modes,
- * 0 in PLAIN mode). */
+ * 0 in PLAIN mode), c_norm_est and eps_abs. */
 typedef struct {
     double* Q;
     double* R;
@@ -95,6 +99,8 @@ typedef struct {
     int64_t k;
     int32_t sgn;
     double rinv_est;
+    double c_norm_est;   /* est ||C||_2 (GN_EPS_RELATIVE only, else 0) */
+    double eps_abs;      /* absolute truncation threshold that was used */
 } gn_core_t;
 
 typedef struct gn_handle_s* gn_handle;

@@ -26,6 +26,7 @@ U64 = 2.0 ** -53          # unit roundoff of IEEE double
 U32 = 2.0 ** -24          # unit roundoff of IEEE single (FP32 accumulation)
 
 PLAIN, SGN, AUTO = 0, 1, 2
+AUTO_SWITCH = 100.0     # est||R^{-1}|| * eps at which AUTO takes the SGN branch
 
 
 # ---------------------------------------------------------------------------
@@ -178,7 +179,7 @@ def right_solve_upper_transpose(B, R2):
     return F
 
 
-def core(YtA, X, eps, mode=AUTO, C=None):
+def core(YtA, X, eps, mode=AUTO, C=None, eps_relative=False, diag_iters=20):
     """Core of (S)GN: C = (Y^T A)X, C = QR, truncation, second QR.
 
     mode PLAIN: k = r, the pseudoinverse is R^{-1} Q^T (eq. 5.1).
@@ -186,26 +187,36 @@ def core(YtA, X, eps, mode=AUTO, C=None):
                 QR R_1^T = Q_2 R_2 gives (Y^T A X)_eps^+ = Q_2 R_2^{-T} Q_1^T
                 (Section 5.1.1; the transpose on R_2 follows from
                 Q_1 R_1 = Q_1 R_2^T Q_2^T).
-    mode AUTO:  the detector of Section 5.1.2: SGN when the power-method
-                estimate of ||R^{-1}||_2 is at least 1/eps, else PLAIN.
-    Returns a dict with C, Q, R, k, Q2, R2 (None when k = r), rinv_est, sgn.
+    mode AUTO:  the detector of Section 5.1.2: switch to SGN only when
+                ||R^{-1}|| >> 1/u in the paper's normalisation (||A|| = 1,
+                O(1) sketches), where eps = 10u.  Read with ">>" as a factor
+                10: SGN when est||R^{-1}||_2 * eps >= 100, else PLAIN.
+    eps_relative: eps is relative to ||C||_2 (= ||R||_2), estimated by
+                `diag_iters` power iterations on R from the all-ones vector.
+                In the paper's normalisation (||A|| = 1, O(1) sketches, so
+                ||C|| = O(1)) the rule eps = 10u of Section 4.1 is this with
+                eps = 10u.
+    Returns a dict with C, Q, R, k, Q2, R2 (None when k = r), rinv_est, sgn,
+    eps_abs (the absolute threshold used).
     """
     if C is None:
         C = core_matrix(YtA, X)
     Q, R = householder_qr(C)
     r = R.shape[0]
-    est = rinv_norm_estimate(R)
+    est = rinv_norm_estimate(R, iters=diag_iters)
+    if eps_relative:
+        eps = eps * norm2_estimate(R, iters=diag_iters)
     if mode == PLAIN:
         use_sgn = False
     elif mode == SGN:
         use_sgn = True
     else:
-        use_sgn = bool(eps > 0.0 and est * eps >= 1.0)
+        use_sgn = bool(eps > 0.0 and est * eps >= AUTO_SWITCH)
     k = truncation_rank(R, eps) if use_sgn else r
     Q2 = R2 = None
     if k < r:
         Q2, R2 = householder_qr(R[:k, :].T)
-    return dict(C=C, Q=Q, R=R, k=k, Q2=Q2, R2=R2, rinv_est=est, sgn=use_sgn)
+    return dict(C=C, Q=Q, R=R, k=k, Q2=Q2, R2=R2, rinv_est=est, sgn=use_sgn, eps_abs=eps)
 
 
 # ---------------------------------------------------------------------------
@@ -224,10 +235,10 @@ def factors(AX, YtA, c):
     return F, G
 
 
-def gn(A, X, Y, eps=0.0, mode=AUTO):
+def gn(A, X, Y, eps=0.0, mode=AUTO, eps_relative=False, diag_iters=20):
     """Full (S)GN: returns (Ahat, parts) with Ahat = F G, F and G as above."""
     AX, YtA = sketch(A, X, Y)
-    c = core(YtA, X, eps, mode)
+    c = core(YtA, X, eps, mode, eps_relative=eps_relative, diag_iters=diag_iters)
     F, G = factors(AX, YtA, c)
     return F @ G, dict(AX=AX, YtA=YtA, F=F, G=G, **c)
 

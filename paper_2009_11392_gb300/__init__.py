@@ -24,11 +24,12 @@ from . import build as _build
 
 __all__ = [
     "GNError", "Handle", "Core", "lib_path", "lib", "F64", "F32", "BF16", "BF16X2",
-    "PLAIN", "SGN", "AUTO", "ABI_SYMBOLS", "mat", "round8", "padded",
+    "PLAIN", "SGN", "AUTO", "EPS_RELATIVE", "ABI_SYMBOLS", "mat", "round8", "padded",
 ]
 
 F64, F32, BF16, BF16X2 = 0, 1, 2, 3
 PLAIN, SGN, AUTO = 0, 1, 2
+EPS_RELATIVE = 0x100
 
 # Every symbol declared in include/gn.h.
 ABI_SYMBOLS = (
@@ -48,7 +49,8 @@ class GnCoreT(ctypes.Structure):
     _fields_ = [("Q", ctypes.c_void_p), ("R", ctypes.c_void_p), ("Q2", ctypes.c_void_p),
                 ("R2", ctypes.c_void_p), ("C", ctypes.c_void_p), ("r", ctypes.c_int64),
                 ("l", ctypes.c_int64), ("k", ctypes.c_int64), ("sgn", ctypes.c_int32),
-                ("rinv_est", ctypes.c_double)]
+                ("rinv_est", ctypes.c_double), ("c_norm_est", ctypes.c_double),
+                ("eps_abs", ctypes.c_double)]
 
 
 def kernel_launches() -> int:
@@ -155,6 +157,8 @@ class Core:
     k: int = 0
     sgn: int = 0
     rinv_est: float = 0.0
+    c_norm_est: float = 0.0
+    eps_abs: float = 0.0
 
     @staticmethod
     def empty(r: int, l: int, device) -> "Core":
@@ -163,10 +167,12 @@ class Core:
 
     def cstruct(self) -> GnCoreT:
         return GnCoreT(self.Q.data_ptr(), self.R.data_ptr(), self.Q2.data_ptr(), self.R2.data_ptr(),
-                       self.C.data_ptr(), self.r, self.l, self.k, self.sgn, self.rinv_est)
+                       self.C.data_ptr(), self.r, self.l, self.k, self.sgn, self.rinv_est,
+                       self.c_norm_est, self.eps_abs)
 
     def update(self, c: GnCoreT):
         self.k, self.sgn, self.rinv_est = int(c.k), int(c.sgn), float(c.rinv_est)
+        self.c_norm_est, self.eps_abs = float(c.c_norm_est), float(c.eps_abs)
 
 
 class Handle:

@@ -88,7 +88,7 @@ size_t core_ws(long long n, long long r, long long l, int mixed, int sms) {
     size_t b = 0;
     b += align256(sizeof(double) * rl * r);            // W for the QR of C
     b += align256(sizeof(double) * r * r);             // W2 for the QR of R_1^T
-    b += align256(sizeof(double) * std::max<long long>(r, 64));   // diag scratch
+    b += align256(sizeof(double) * 2 * std::max<long long>(r, 64));   // diag scratch
     b += 256;                                          // k, est
     if (mixed) {
         b += 3 * align256(sizeof(__nv_bfloat16) * rl * round8(n));
@@ -316,6 +316,8 @@ gn_status gn_sketch(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat*
 gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, int32_t mode,
                   gn_core_t* core, void* ws, size_t ws_bytes) {
     if (!h || !YtA || !X || !core || !ws) return GN_ERR_INVALID_ARG;
+    const int eps_rel = (mode & GN_EPS_RELATIVE) ? 1 : 0;
+    mode &= ~GN_EPS_RELATIVE;
     if (mode < GN_MODE_PLAIN || mode > GN_MODE_AUTO || !(eps >= 0.0)) return GN_ERR_INVALID_ARG;
     const long long n = X->rows, r = X->cols, rl = YtA->rows, l = rl - r;
     if (r < 1 || l < 1 || n < r) return GN_ERR_SHAPE;
@@ -333,8 +335,8 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     Carve cv{static_cast<char*>(ws), ws_bytes, 0, true};
     double* W = cv.take<double>(rl * r);
     double* W2 = cv.take<double>(r * r);
-    double* zscr = cv.take<double>(std::max<long long>(r, 64));
-    double* est_d = cv.take<double>(1);
+    double* zscr = cv.take<double>(2 * std::max<long long>(r, 64));
+    double* diag_d = cv.take<double>(3);
     int* k_d = cv.take<int>(1);
     __nv_bfloat16 *s_hi = nullptr, *s_mid = nullptr, *s_lo = nullptr;
     float *c_hi = nullptr, *c_mid = nullptr, *c_lo = nullptr;
@@ -389,16 +391,23 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     core->k = r;
     core->sgn = 0;
     core->rinv_est = 0.0;
+    core->c_norm_est = 0.0;
+    core->eps_abs = eps;
     if (mode == GN_MODE_PLAIN) return GN_OK;
 
-    GN_TRY(core_diagnostics(h, core->R, r, r, eps, 1, DIAG_ITERS, est_d, k_d, zscr, sizeof(double) * std::max<long long>(r, 64)));
+    GN_TRY(core_diagnostics(h, core->R, r, r, eps, eps_rel, 1, DIAG_ITERS, diag_d, k_d, zscr,
+                            sizeof(double) * 2 * std::max<long long>(r, 64)));
     int k_h = 0;
-    double est_h = 0.0;
+    double diag_h[3] = {0.0, 0.0, 0.0};
     GN_CUDA_TRY(cudaMemcpyAsync(&k_h, k_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    GN_CUDA_TRY(cudaMemcpyAsync(&est_h, est_d, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    GN_CUDA_TRY(cudaMemcpyAsync(diag_h, diag_d, sizeof(diag_h), cudaMemcpyDeviceToHost, h->stream));
     GN_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    core->rinv_est = est_h;
-    const int use_sgn = (mode == GN_MODE_SGN) || (eps > 0.0 && est_h * eps >= 1.0);
+    core->rinv_est = diag_h[0];
+    core->c_norm_est = diag_h[1];
+    core->eps_abs = diag_h[2];
+    // Section 5.1.2: switch when ||R^{-1}|| >> 1/u in the paper's normalisation,
+    // where eps = 10u; ">>" read as a factor 10, i.e. est * eps >= 100.
+    const int use_sgn = (mode == GN_MODE_SGN) || (diag_h[2] > 0.0 && diag_h[0] * diag_h[2] >= 100.0);
     core->sgn = use_sgn;
     if (!use_sgn) return GN_OK;
     core->k = k_h;

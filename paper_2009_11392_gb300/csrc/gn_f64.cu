@@ -494,28 +494,36 @@ __device__ double dg_block_sum(double s, double* red) {
 
 // Solves in place on vector z (length r, in global scratch):
 //   lower == 1: R^T y = z (forward);  lower == 0: R w = z (backward).
-__device__ void dg_tri_solve(const double* R, long long ldr, int r, double* z, int lower) {
+// Each 32 x 32 diagonal block is staged in shared memory and solved by warp 0;
+// the rest of the CTA applies the block's contribution to the remaining entries.
+__device__ void dg_tri_solve(const double* R, long long ldr, int r, double* z, int lower,
+                             double (*Rb)[33]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nb = (r + 31) / 32;
     for (int bi = 0; bi < nb; ++bi) {
         const int b = lower ? bi : nb - 1 - bi;
         const int j0 = b * 32;
         const int jb = min(32, r - j0);
+        {
+            const int a = threadIdx.x >> 5, c = threadIdx.x & 31;   // 1024 threads = 32 x 32
+            Rb[a][c] = (a < jb && c < jb) ? R[(j0 + a) * ldr + j0 + c] : 0.0;
+        }
+        __syncthreads();
         if (warp == 0) {
             double zl = lane < jb ? z[j0 + lane] : 0.0;
             if (lower) {
                 for (int i = 0; i < jb; ++i) {
                     double yi = __shfl_sync(0xffffffffu, zl, i);
-                    yi = yi / R[(j0 + i) * ldr + j0 + i];
+                    yi = yi / Rb[i][i];
                     if (lane == i) zl = yi;
-                    if (lane > i && lane < jb) zl = fma(-R[(j0 + i) * ldr + j0 + lane], yi, zl);
+                    if (lane > i && lane < jb) zl = fma(-Rb[i][lane], yi, zl);
                 }
             } else {
                 for (int i = jb - 1; i >= 0; --i) {
                     double wi = __shfl_sync(0xffffffffu, zl, i);
-                    wi = wi / R[(j0 + i) * ldr + j0 + i];
+                    wi = wi / Rb[i][i];
                     if (lane == i) zl = wi;
-                    if (lane < i) zl = fma(-R[(j0 + lane) * ldr + j0 + i], wi, zl);
+                    if (lane < i) zl = fma(-Rb[lane][i], wi, zl);
                 }
             }
             if (lane < jb) z[j0 + lane] = zl;
@@ -539,42 +547,82 @@ __device__ void dg_tri_solve(const double* R, long long ldr, int r, double* z, i
     }
 }
 
+// out[0] = est ||R^{-1}||_2, out[1] = est ||R||_2, out[2] = eps used; *k_out = truncation rank.
 __global__ void __launch_bounds__(DG_THREADS) core_diag_kernel(const double* R, long long ldr, int r,
-                                                               double eps, int want_est, int iters,
-                                                               double* z, double* est_out, int* k_out) {
+                                                               double eps, int eps_relative, int want_est,
+                                                               int iters, double* z, double* out,
+                                                               int* k_out) {
     __shared__ double red[32];
+    __shared__ double Rb[32][33];
     __shared__ int kmin;
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    const double inv = 1.0 / sqrt(static_cast<double>(r));
+    double* y = z + r;
+    // ||R||_2 by power iteration on R^T R from the all-ones vector
+    double rn = 0.0;
+    if (eps_relative) {
+        for (int i = threadIdx.x; i < r; i += DG_THREADS) z[i] = inv;
+        __syncthreads();
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int it = 0; it < iters; ++it) {
+            for (int i = warp; i < r; i += DG_THREADS / 32) {   // y = R z, one warp per row
+                double s = 0.0;
+                for (int j = i + lane; j < r; j += 32) s = fma(R[static_cast<long long>(i) * ldr + j], z[j], s);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) y[i] = s;
+            }
+            __syncthreads();
+            double ss = 0.0;
+            for (int j = threadIdx.x; j < r; j += DG_THREADS) {   // w = R^T y
+                double s = 0.0;
+                for (int i = 0; i <= j; ++i) s = fma(R[static_cast<long long>(i) * ldr + j], y[i], s);
+                z[j] = s;   // each thread owns its j
+                ss = fma(s, s, ss);
+            }
+            const double nw = sqrt(dg_block_sum(ss, red));
+            if (nw == 0.0 || !isfinite(nw)) {
+                rn = nw;
+                break;
+            }
+            rn = sqrt(nw);
+            const double sc = 1.0 / nw;
+            for (int j = threadIdx.x; j < r; j += DG_THREADS) z[j] *= sc;
+            __syncthreads();
+        }
+        eps = eps * rn;
+    }
     if (threadIdx.x == 0) kmin = r;
     __syncthreads();
     for (int i = threadIdx.x; i < r; i += DG_THREADS)
         if (fabs(R[static_cast<long long>(i) * ldr + i]) <= eps) atomicMin(&kmin, i);
     __syncthreads();
-    if (threadIdx.x == 0) *k_out = kmin;
-    if (!want_est) {
-        if (threadIdx.x == 0) *est_out = 0.0;
-        return;
+    if (threadIdx.x == 0) {
+        *k_out = kmin;
+        out[1] = rn;
+        out[2] = eps;
+        out[0] = 0.0;
     }
-    // zero diagonal -> +inf
+    if (!want_est) return;
     int has_zero = 0;
     for (int i = threadIdx.x; i < r; i += DG_THREADS)
         if (R[static_cast<long long>(i) * ldr + i] == 0.0) has_zero = 1;
     has_zero = __syncthreads_or(has_zero);
     if (has_zero) {
-        if (threadIdx.x == 0) *est_out = __longlong_as_double(0x7ff0000000000000LL);
+        if (threadIdx.x == 0) out[0] = inf;
         return;
     }
-    const double inv = 1.0 / sqrt(static_cast<double>(r));
     for (int i = threadIdx.x; i < r; i += DG_THREADS) z[i] = inv;
     __syncthreads();
     double est = 0.0;
     for (int it = 0; it < iters; ++it) {
-        dg_tri_solve(R, ldr, r, z, 1);
-        dg_tri_solve(R, ldr, r, z, 0);
+        dg_tri_solve(R, ldr, r, z, 1, Rb);
+        dg_tri_solve(R, ldr, r, z, 0, Rb);
         double s = 0.0;
         for (int i = threadIdx.x; i < r; i += DG_THREADS) s = fma(z[i], z[i], s);
         const double nw = sqrt(dg_block_sum(s, red));
         if (!isfinite(nw)) {
-            est = __longlong_as_double(0x7ff0000000000000LL);
+            est = inf;
             break;
         }
         est = sqrt(nw);
@@ -584,7 +632,7 @@ __global__ void __launch_bounds__(DG_THREADS) core_diag_kernel(const double* R, 
         for (int i = threadIdx.x; i < r; i += DG_THREADS) z[i] *= sc;
         __syncthreads();
     }
-    if (threadIdx.x == 0) *est_out = est;
+    if (threadIdx.x == 0) out[0] = est;
 }
 
 // --------------------------------------------------------------------------
@@ -796,11 +844,11 @@ gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, lon
 }
 
 gn_status core_diagnostics(gn_handle h, const double* R, long long r, long long ldr, double eps,
-                           int want_estimate, int iters, double* est_out, int* k_out, double* ws,
-                           size_t ws_bytes) {
-    if (ws_bytes < static_cast<size_t>(r) * sizeof(double)) return GN_ERR_WORKSPACE;
-    core_diag_kernel<<<1, DG_THREADS, 0, h->stream>>>(R, ldr, static_cast<int>(r), eps, want_estimate,
-                                                      iters, ws, est_out, k_out); count_launch();
+                           int eps_relative, int want_estimate, int iters, double* out3, int* k_out,
+                           double* ws, size_t ws_bytes) {
+    if (ws_bytes < 2 * static_cast<size_t>(r) * sizeof(double)) return GN_ERR_WORKSPACE;
+    core_diag_kernel<<<1, DG_THREADS, 0, h->stream>>>(R, ldr, static_cast<int>(r), eps, eps_relative,
+                                                      want_estimate, iters, ws, out3, k_out); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     return GN_OK;
 }

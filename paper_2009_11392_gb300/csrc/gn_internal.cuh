@@ -107,10 +107,12 @@ size_t trsm_ws_bytes(long long m, long long k, int sm_count);
 gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, long long ldf,
                            const double* R, long long ldr, int trans, double* ws, size_t ws_bytes);
 
-// est ||R^{-1}||_2 by `iters` power iterations (device result in *out);
-// also the truncation rank k (first |R_ii| <= eps) in *k_out.
+// Core diagnostics (one CTA): out3[0] = est ||R^{-1}||_2 (if want_estimate),
+// out3[1] = est ||R||_2 (if eps_relative), out3[2] = the absolute threshold
+// used (eps, or eps * est ||R||_2); *k_out = first i with |R_ii| <= threshold.
+// ws: 2 r doubles.
 gn_status core_diagnostics(gn_handle h, const double* R, long long r, long long ldr, double eps,
-                           int want_estimate, int iters, double* est_out, int* k_out,
+                           int eps_relative, int want_estimate, int iters, double* out3, int* k_out,
                            double* ws, size_t ws_bytes);
 
 gn_status copy_f32_to_f64(gn_handle h, const float* src, long long rows, long long cols,

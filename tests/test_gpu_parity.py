@@ -256,3 +256,36 @@ def test_mixed_path_matches_oracle_on_quantized_inputs(gn, H):
     H.error_fro2(Ab, F, G, out, ws)
     torch.cuda.synchronize()
     assert abs(math.sqrt(out.item()) - err_g) <= 1e-6 * err_g
+
+
+def test_relative_eps_and_auto_switch(gn, H):
+    """GN_EPS_RELATIVE: eps scales with the 6-iteration power estimate of
+    ||C||_2, as in the oracle.  An exactly zero column of C (zero column of X)
+    gives R_jj = 0, est = inf, and AUTO takes the truncated branch at k = j."""
+    m, n, r, l = 260, 180, 20, 10
+    A = gn_synth.gaussian((m, n), 41, 0).numpy()
+    X, Y = gn_synth.sketches(m, n, r, l, 42)
+    X, Y = X.numpy().copy(), Y.numpy()
+    eps = 10 * O.U64
+    mode = gn.AUTO | gn.EPS_RELATIVE
+    ws = H.workspace(m, n, r, l, gn.F64)
+    AX = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float64, device="cuda")
+    F = torch.zeros(m, r, dtype=torch.float64, device="cuda")
+    G = torch.zeros(r, n, dtype=torch.float64, device="cuda")
+    core = _core_tensors(gn, r, l)
+    H.approx(cu(A), cu(X), cu(Y), eps, mode, AX, YtA, core, F, G, ws)
+    assert H.sync_status() == 0
+    _, o = O.gn(A, X, Y, eps, O.AUTO, eps_relative=True, diag_iters=6)
+    assert core.sgn == 0 and core.k == r and not o["sgn"]
+    assert abs(core.eps_abs - o["eps_abs"]) <= 1e-10 * o["eps_abs"]
+    assert abs(core.rinv_est - o["rinv_est"]) <= 1e-8 * o["rinv_est"]
+    X[:, 7] = 0.0
+    Ahat, o = O.gn(A, X, Y, eps, O.AUTO, eps_relative=True, diag_iters=6)
+    assert o["sgn"] and o["k"] == 7
+    core = _core_tensors(gn, r, l)
+    H.approx(cu(A), cu(X), cu(Y), eps, mode, AX, YtA, core, F, G, ws)
+    assert H.sync_status() == 0
+    assert core.sgn == 1 and core.k == 7 and math.isinf(core.rinv_est)
+    Ah = npy(F)[:, :7] @ npy(G)[:7]
+    assert rel(Ah, Ahat) <= 1e-10

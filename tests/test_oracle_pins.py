@@ -222,20 +222,35 @@ def test_sgn_without_truncation_equals_plain():
 
 
 def test_detector_and_stress_input():
-    """Section 4.2 / 5.1.2: exactly low-rank A makes R's trailing diagonal tiny;
-    the ||R^{-1}|| estimate flags it and AUTO switches to SGN, whose error is
-    at roundoff level."""
+    """Section 4.2 / 5.1.1 / 5.1.2.  An exactly low-rank A makes R's trailing
+    diagonal fall to roundoff: SGN then truncates to the true rank and the error
+    stays at roundoff level, and plain GN is also accurate there (its
+    instability needs ||R^{-1}|| >> 1/u).  An exactly zero column of C (a zero
+    column of X) gives R_jj = 0, an infinite estimate, and AUTO switches."""
     m, n, k0, r, l = 100, 80, 7, 12, 6
     A, _ = _lowrank(m, n, k0, 11)
     X, Y = _sk(m, n, r, l, 11)
     eps = O.scale_eps(1.0, np.linalg.norm(X, 2), np.linalg.norm(Y, 2), O.U64)
-    Ahat, p = O.gn(A, X, Y, eps, O.AUTO)
+    Ahat, p = O.gn(A, X, Y, eps, O.SGN)
     assert p["sgn"] and p["k"] == k0
     assert np.linalg.norm(A - Ahat) / np.linalg.norm(A) < 1e-12
-    # on a well-conditioned problem AUTO stays plain
+    Arel, p2 = O.gn(A, X, Y, 10 * O.U64, O.SGN, eps_relative=True)
+    assert k0 <= p2["k"] <= r and np.linalg.norm(A - Arel) / np.linalg.norm(A) < 1e-12
+    Aplain, q = O.gn(A, X, Y, 10 * O.U64, O.AUTO, eps_relative=True)
+    assert np.linalg.norm(A - Aplain) / np.linalg.norm(A) < 1e-12
+    est = q["rinv_est"]
+    assert est * np.linalg.norm(q["C"], 2) * O.U64 > 0.5     # kappa(R) ~ 1/u, not >> 1/u
+    # exactly singular core: AUTO takes the SGN branch
     B = RNG.standard_normal((m, n))
-    _, q = O.gn(B, X, Y, eps, O.AUTO)
-    assert not q["sgn"] and q["k"] == r
+    Xz = X.copy()
+    Xz[:, 5] = 0.0
+    Bhat, z = O.gn(B, Xz, Y, 10 * O.U64, O.AUTO, eps_relative=True)
+    assert z["rinv_est"] == np.inf and z["sgn"] and z["k"] == 5
+    # well-conditioned: AUTO stays plain
+    _, w = O.gn(B, X, Y, 10 * O.U64, O.AUTO, eps_relative=True)
+    assert not w["sgn"] and w["k"] == r
+    # the relative threshold is eps * ||C||_2
+    assert abs(w["eps_abs"] - 10 * O.U64 * np.linalg.norm(w["C"], 2)) <= 1e-3 * w["eps_abs"]
 
 
 def test_rinv_norm_estimate_matches_svd():
