@@ -209,7 +209,15 @@ gn_status gn_create(gn_handle* out, void* stream) {
         delete h;
         return GN_ERR_CUDA;
     }
-    if (cudaMemsetAsync(h->dstatus, 0, 64, h->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(h->dstatus, 0, 64, h->stream) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(h->dstatus);
+        delete h;
+        return GN_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(h->side);
         cudaFree(h->dstatus);
         delete h;
         return GN_ERR_CUDA;
@@ -221,6 +229,10 @@ gn_status gn_create(gn_handle* out, void* stream) {
 gn_status gn_destroy(gn_handle h) {
     if (!h) return GN_ERR_INVALID_ARG;
     cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->side);
+    cudaEventDestroy(h->ev_fork);
+    cudaEventDestroy(h->ev_join);
+    cudaStreamDestroy(h->side);
     cudaFree(h->dstatus);
     delete h;
     return GN_OK;
@@ -384,19 +396,30 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
         GN_TRY(tc_launch(h, &p));
         GN_TRY(sum3_f32_to_f64(h, c_hi, c_mid, c_lo, rl, r, r, core->C, r));
     }
-    // Householder QR of a copy of C.
+    // Householder QR of a copy of C: factor (R), then the thin Q.  In SGN / AUTO
+    // mode the Section 5.1.1/5.1.2 diagnostics on R run on the side stream
+    // while the main stream forms Q.
     GN_CUDA_TRY(cudaMemcpy2DAsync(W, r * sizeof(double), core->C, r * sizeof(double), r * sizeof(double), rl,
                                   cudaMemcpyDeviceToDevice, h->stream));
-    GN_TRY(householder_qr(h, W, rl, r, r, core->Q, r, core->R, r, inner, inner_bytes));
+    GN_TRY(qr_factor(h, W, rl, r, r, core->R, r, inner, inner_bytes));
     core->k = r;
     core->sgn = 0;
     core->rinv_est = 0.0;
     core->c_norm_est = 0.0;
     core->eps_abs = eps;
-    if (mode == GN_MODE_PLAIN) return GN_OK;
+    if (mode == GN_MODE_PLAIN) return qr_form_q(h, W, rl, r, r, core->Q, r, inner, inner_bytes);
 
-    GN_TRY(core_diagnostics(h, core->R, r, r, eps, eps_rel, 1, DIAG_ITERS, diag_d, k_d, zscr,
-                            sizeof(double) * 2 * std::max<long long>(r, 64)));
+    GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+    GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    {
+        gn_handle_s side = *h;
+        side.stream = h->side;
+        GN_TRY(core_diagnostics(&side, core->R, r, r, eps, eps_rel, 1, DIAG_ITERS, diag_d, k_d, zscr,
+                                sizeof(double) * 2 * std::max<long long>(r, 64)));
+    }
+    GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+    GN_TRY(qr_form_q(h, W, rl, r, r, core->Q, r, inner, inner_bytes));
+    GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     int k_h = 0;
     double diag_h[3] = {0.0, 0.0, 0.0};
     GN_CUDA_TRY(cudaMemcpyAsync(&k_h, k_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));

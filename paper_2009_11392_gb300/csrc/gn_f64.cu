@@ -16,6 +16,8 @@
 // skinny products) rather than at data movement.
 #include "gn_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 namespace gn {
@@ -56,33 +58,36 @@ __device__ __forceinline__ double load_ref(const ErrArgs& e, long long i, long l
     }
 }
 
-// C tile = alpha * op(A) op(B) (+ beta C); 64 x 64 tile, 256 threads, each a
-// 4 x 4 block of outputs at rows ty + 16 i and columns tx + 16 j.
-template <typename TA, typename TB_, int EPI>
+// C tile = alpha * op(A) op(B) (+ beta C); BM x BN tile, 256 threads as a
+// 16 x 16 grid, each thread a (BM/16) x (BN/16) block of outputs at rows
+// ty + 16 i and columns tx + 16 j.  BM = 16 serves the skinny (panel-width)
+// products of the WY updates without padding waste.
+template <int BM, int BN, typename TA, typename TB_, int EPI>
 __global__ void __launch_bounds__(GTHREADS) dgemm_kernel(
     int M, int N, int K, double alpha, const TA* __restrict__ A, long long lda, int ta,
     const TB_* __restrict__ B, long long ldb, int tb, double beta, double* C, long long ldc,
     double* part, int kchunk, ErrArgs err) {
-    __shared__ double As[GK][GT + 1];
-    __shared__ double Bs[GK][GT + 1];
+    constexpr int RI = BM / 16, RJ = BN / 16;
+    __shared__ double As[GK][BM + 1];
+    __shared__ double Bs[GK][BN + 1];
     __shared__ double red[GTHREADS / 32];
-    const int m0 = blockIdx.y * GT;
-    const int n0 = blockIdx.x * GT;
+    const int m0 = blockIdx.y * BM;
+    const int n0 = blockIdx.x * BN;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(K, kbeg + kchunk);
     const int tx = threadIdx.x & 15;
     const int ty = threadIdx.x >> 4;
-    double acc[4][4];
+    double acc[RI][RJ];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < RJ; ++j) acc[i][j] = 0.0;
 
     for (int k0 = kbeg; k0 < kend; k0 += GK) {
 #pragma unroll
-        for (int e = threadIdx.x; e < GT * GK; e += GTHREADS) {
+        for (int e = threadIdx.x; e < BM * GK; e += GTHREADS) {
             int mm, kk;
-            if (ta) { mm = e & 63; kk = e >> 6; } else { kk = e & 15; mm = e >> 4; }
+            if (ta) { mm = e % BM; kk = e / BM; } else { kk = e & 15; mm = e >> 4; }
             const int gm = m0 + mm, gk = k0 + kk;
             double v = 0.0;
             if (gm < M && gk < kend)
@@ -91,9 +96,9 @@ __global__ void __launch_bounds__(GTHREADS) dgemm_kernel(
             As[kk][mm] = v;
         }
 #pragma unroll
-        for (int e = threadIdx.x; e < GT * GK; e += GTHREADS) {
+        for (int e = threadIdx.x; e < BN * GK; e += GTHREADS) {
             int nn, kk;
-            if (tb) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
+            if (tb) { kk = e & 15; nn = e >> 4; } else { nn = e % BN; kk = e / BN; }
             const int gn_ = n0 + nn, gk = k0 + kk;
             double v = 0.0;
             if (gn_ < N && gk < kend)
@@ -104,15 +109,15 @@ __global__ void __launch_bounds__(GTHREADS) dgemm_kernel(
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            double a[4], b[4];
+            double a[RI], b[RJ];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < RI; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < RJ; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RI; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < RJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
@@ -120,9 +125,9 @@ __global__ void __launch_bounds__(GTHREADS) dgemm_kernel(
     if (EPI == EPI_ERR) {
         double s = 0.0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < RI; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < RJ; ++j) {
                 const int gm = m0 + ty + 16 * i, gn_ = n0 + tx + 16 * j;
                 if (gm < M && gn_ < N) {
                     const double d = load_ref(err, gm, gn_) - acc[i][j];
@@ -141,9 +146,9 @@ __global__ void __launch_bounds__(GTHREADS) dgemm_kernel(
         return;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RJ; ++j) {
             const int gm = m0 + ty + 16 * i, gn_ = n0 + tx + 16 * j;
             if (gm < M && gn_ < N) {
                 if (EPI == EPI_PARTIAL) {
@@ -184,25 +189,27 @@ __global__ void reduce_sum_kernel(const double* __restrict__ part, long long n, 
     }
 }
 
+// Tile shape: 16 x 128 or 32 x 128 for panel-width products (M <= 32), else 64 x 64.
+inline int tile_m(long long M) { return M <= 16 ? 16 : (M <= 32 ? 32 : GT); }
+
 int choose_splits(long long M, long long N, long long K, int sm_count) {
-    const long long tiles = ((M + GT - 1) / GT) * ((N + GT - 1) / GT);
-    if (tiles >= sm_count || K < 512) return 1;
+    const long long bm = tile_m(M), bn = bm < GT ? 128 : GT;
+    const long long tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+    if (tiles >= sm_count || K < 256) return 1;
     long long s = (2LL * sm_count + tiles - 1) / tiles;
-    s = std::min(s, K / 256);
+    s = std::min(s, K / 64);
     s = std::min<long long>(s, 64);
     return static_cast<int>(std::max<long long>(s, 1));
 }
 
-template <typename TA, typename TB_>
-gn_status dgemm_impl(gn_handle h, long long M, long long N, long long K, double alpha, const TA* A,
-                     long long lda, int ta, const TB_* B, long long ldb, int tb, double beta,
-                     double* C, long long ldc, double* ws, size_t ws_bytes) {
-    if (M <= 0 || N <= 0) return GN_OK;
-    if (K <= 0) {   // C = beta C
-        if (beta == 0.0) return set_zero_f64(h, C, M, N, ldc);
-        dim3 grid(static_cast<unsigned>((N + GT - 1) / GT), static_cast<unsigned>((M + GT - 1) / GT), 1);
-        ErrArgs e{};
-        dgemm_kernel<TA, TB_, EPI_STORE><<<grid, GTHREADS, 0, h->stream>>>(
+template <int BM, int BN, typename TA, typename TB_>
+gn_status dgemm_launch(gn_handle h, long long M, long long N, long long K, double alpha, const TA* A,
+                       long long lda, int ta, const TB_* B, long long ldb, int tb, double beta, double* C,
+                       long long ldc, double* ws, size_t ws_bytes) {
+    ErrArgs e{};
+    if (K <= 0) {
+        dim3 grid(static_cast<unsigned>((N + BN - 1) / BN), static_cast<unsigned>((M + BM - 1) / BM), 1);
+        dgemm_kernel<BM, BN, TA, TB_, EPI_STORE><<<grid, GTHREADS, 0, h->stream>>>(
             (int)M, (int)N, 0, 0.0, A, lda, ta, B, ldb, tb, beta, C, ldc, nullptr, 1, e); count_launch();
         GN_CUDA_TRY(cudaGetLastError());
         return GN_OK;
@@ -212,14 +219,13 @@ gn_status dgemm_impl(gn_handle h, long long M, long long N, long long K, double 
     if (ws == nullptr) splits = 1;
     int kchunk = static_cast<int>(((K + splits - 1) / splits + GK - 1) / GK * GK);
     splits = static_cast<int>((K + kchunk - 1) / kchunk);
-    dim3 grid(static_cast<unsigned>((N + GT - 1) / GT), static_cast<unsigned>((M + GT - 1) / GT),
+    dim3 grid(static_cast<unsigned>((N + BN - 1) / BN), static_cast<unsigned>((M + BM - 1) / BM),
               static_cast<unsigned>(splits));
-    ErrArgs e{};
     if (splits == 1) {
-        dgemm_kernel<TA, TB_, EPI_STORE><<<grid, GTHREADS, 0, h->stream>>>(
+        dgemm_kernel<BM, BN, TA, TB_, EPI_STORE><<<grid, GTHREADS, 0, h->stream>>>(
             (int)M, (int)N, (int)K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, nullptr, kchunk, e); count_launch();
     } else {
-        dgemm_kernel<TA, TB_, EPI_PARTIAL><<<grid, GTHREADS, 0, h->stream>>>(
+        dgemm_kernel<BM, BN, TA, TB_, EPI_PARTIAL><<<grid, GTHREADS, 0, h->stream>>>(
             (int)M, (int)N, (int)K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, ws, kchunk, e); count_launch();
         GN_CUDA_TRY(cudaGetLastError());
         const long long total = M * N;
@@ -230,13 +236,27 @@ gn_status dgemm_impl(gn_handle h, long long M, long long N, long long K, double 
     return GN_OK;
 }
 
+template <typename TA, typename TB_>
+gn_status dgemm_impl(gn_handle h, long long M, long long N, long long K, double alpha, const TA* A,
+                     long long lda, int ta, const TB_* B, long long ldb, int tb, double beta,
+                     double* C, long long ldc, double* ws, size_t ws_bytes) {
+    if (M <= 0 || N <= 0) return GN_OK;
+    if (K <= 0 && beta == 0.0) return set_zero_f64(h, C, M, N, ldc);
+    if (tile_m(M) == 16)
+        return dgemm_launch<16, 128, TA, TB_>(h, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, ws, ws_bytes);
+    if (tile_m(M) == 32)
+        return dgemm_launch<32, 128, TA, TB_>(h, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, ws, ws_bytes);
+    return dgemm_launch<GT, GT, TA, TB_>(h, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, ws, ws_bytes);
+}
+
 // --------------------------------------------------------------------------
 // Householder QR
 // --------------------------------------------------------------------------
 constexpr int QR_THREADS = 512;
 constexpr int QR_WARPS = QR_THREADS / 32;
-constexpr int QR_JB = 16;                 // panel width
-constexpr size_t QR_SMEM_PANEL_MAX = 196 * 1024;
+constexpr int QR_JB = 16;                 // panel width of the single-CTA panel kernel
+constexpr int QR_NB = 32;                 // widest panel (cluster kernel); sizes the T / Z storage
+constexpr size_t QR_SMEM_PANEL_MAX = 208 * 1024;
 
 // Sum of `n` per-thread values across the CTA; results in out[0..n).
 template <int NV>
@@ -278,11 +298,11 @@ __global__ void __launch_bounds__(QR_THREADS) qr_panel_kernel(double* W, long lo
     long long ldp;
     if (use_smem) {
         P = sh;
-        ldp = jb;
+        ldp = jb + 1;   // odd stride: column walks across rows avoid bank conflicts
         for (long long e = tid; e < static_cast<long long>(Mp) * jb; e += QR_THREADS) {
             const long long i = e / jb;
             const int c = static_cast<int>(e % jb);
-            P[e] = W[(j0 + i) * ld + j0 + c];
+            P[i * ldp + c] = W[(j0 + i) * ld + j0 + c];
         }
         __syncthreads();
     } else {
@@ -398,6 +418,203 @@ __global__ void __launch_bounds__(QR_THREADS) qr_panel_kernel(double* W, long lo
     }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster panel factorization.  The panel rows are split across the CTAs of a
+// thread-block cluster (each CTA keeps its rows in shared memory); the two
+// reductions per column (the norm of the column below the diagonal and the
+// vector w = v^T P of the rank-1 update) combine per-CTA partials read through
+// distributed shared memory, summed in rank order so every CTA derives the same
+// reflector.  Partials are double-buffered by column parity, so two cluster
+// barriers per column suffice.  Same outputs as qr_panel_kernel.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+constexpr int CP_THREADS = 256;
+constexpr int CP_WARPS = CP_THREADS / 32;
+
+__device__ __forceinline__ double warp_sum(double s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+template <int JB>
+__host__ __device__ constexpr size_t cluster_panel_smem(int rows_per) {
+    return sizeof(double) * (static_cast<size_t>(rows_per) * (JB + 1) + 4 + 2 * JB + JB * JB + JB + JB * JB);
+}
+
+template <int JB>
+__global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W, long long ld, int M, int j0,
+                                                                     int jb, double* V, long long ldv,
+                                                                     double* tau, double* T, int rows_per) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = static_cast<int>(cluster.num_blocks());
+    const int rank = static_cast<int>(cluster.block_rank());
+    extern __shared__ double sm[];
+    constexpr int LDP = JB + 1;
+    double* P = sm;
+    double* normp = P + static_cast<size_t>(rows_per) * LDP;   // [2] partial sums of squares
+    double* alphas = normp + 2;                                  // [2] diagonal entry (owner only)
+    double* wpart = alphas + 2;                                  // [2][JB] partial w
+    double* gram = wpart + 2 * JB;                               // [JB][JB] partial V^T V
+    double* wsum = gram + JB * JB;                               // [JB]
+    double* Ts = wsum + JB;                                      // [JB][JB]
+    __shared__ double taus[JB];
+    __shared__ double s_tau, s_beta, s_scale;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Mp = M - j0;
+    const int r0 = rank * rows_per;
+    const int nr = max(0, min(rows_per, Mp - r0));
+
+    for (int e = tid; e < nr * jb; e += CP_THREADS) {
+        const int i = e / jb, c = e - (e / jb) * jb;
+        P[i * LDP + c] = W[static_cast<long long>(j0 + r0 + i) * ld + j0 + c];
+    }
+    __syncthreads();
+
+    for (int c = 0; c < jb; ++c) {
+        const int par = c & 1;
+        if (warp == 0) {
+            double sq = 0.0;
+            for (int li = lane; li < nr; li += 32)
+                if (r0 + li > c) {
+                    const double x = P[li * LDP + c];
+                    sq = fma(x, x, sq);
+                }
+            sq = warp_sum(sq);
+            if (lane == 0) {
+                normp[par] = sq;
+                alphas[par] = (c >= r0 && c < r0 + nr) ? P[(c - r0) * LDP + c] : 0.0;
+            }
+        }
+        cluster.sync();
+        if (warp == 0) {
+            double pn = 0.0, pa = 0.0;
+            if (lane < cs) {
+                pn = cluster.map_shared_rank(normp, lane)[par];
+                pa = cluster.map_shared_rank(alphas, lane)[par];
+            }
+            // rank-ordered sum (identical in every CTA)
+            double tail = 0.0, alpha = 0.0;
+            for (int k = 0; k < cs; ++k) {
+                tail += __shfl_sync(0xffffffffu, pn, k);
+                alpha += __shfl_sync(0xffffffffu, pa, k);
+            }
+            if (lane == 0) {
+                if (tail == 0.0) {
+                    s_tau = 0.0;
+                    s_beta = alpha;
+                    s_scale = 0.0;
+                } else {
+                    const double nx = sqrt(fma(alpha, alpha, tail));
+                    const double beta = alpha >= 0.0 ? -nx : nx;
+                    s_tau = (beta - alpha) / beta;
+                    s_beta = beta;
+                    s_scale = 1.0 / (alpha - beta);
+                }
+            }
+        }
+        __syncthreads();
+        const double t = s_tau;
+        if (t != 0.0) {
+            const double sc = s_scale;
+            for (int li = tid; li < nr; li += CP_THREADS)
+                if (r0 + li > c) P[li * LDP + c] *= sc;
+            __syncthreads();
+            for (int q = c + 1 + warp; q < jb; q += CP_WARPS) {
+                double sw = 0.0;
+                for (int li = lane; li < nr; li += 32) {
+                    const int gi = r0 + li;
+                    if (gi >= c) {
+                        const double vi = (gi == c) ? 1.0 : P[li * LDP + c];
+                        sw = fma(vi, P[li * LDP + q], sw);
+                    }
+                }
+                sw = warp_sum(sw);
+                if (lane == 0) wpart[par * JB + q] = sw;
+            }
+        }
+        cluster.sync();
+        if (t != 0.0 && c + 1 < jb) {
+            if (tid > c && tid < jb) {
+                double sw = 0.0;
+                for (int k = 0; k < cs; ++k) sw += cluster.map_shared_rank(wpart, k)[par * JB + tid];
+                wsum[tid] = sw;
+            }
+            __syncthreads();
+            const int nq = jb - c - 1;
+            for (int e = tid; e < nr * nq; e += CP_THREADS) {
+                const int li = e / nq, q = c + 1 + (e - (e / nq) * nq);
+                const int gi = r0 + li;
+                if (gi >= c) {
+                    const double vi = (gi == c) ? 1.0 : P[li * LDP + c];
+                    P[li * LDP + q] = fma(-t * vi, wsum[q], P[li * LDP + q]);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (c >= r0 && c < r0 + nr) P[(c - r0) * LDP + c] = s_beta;
+            taus[c] = t;
+            if (rank == 0) tau[j0 + c] = t;
+        }
+        __syncthreads();
+    }
+
+    // write back the panel, the explicit reflectors, and the partial Gram V^T V
+    for (int e = tid; e < nr * jb; e += CP_THREADS) {
+        const int li = e / jb, c = e - (e / jb) * jb;
+        const int gi = r0 + li;
+        const double pv = P[li * LDP + c];
+        const double v = gi < c ? 0.0 : (gi == c ? 1.0 : (taus[c] == 0.0 ? 0.0 : pv));
+        V[static_cast<long long>(j0 + gi) * ldv + j0 + c] = v;
+        W[static_cast<long long>(j0 + gi) * ld + j0 + c] = pv;
+    }
+    for (int e = tid; e < jb * jb; e += CP_THREADS) {
+        const int q = e / jb, q2 = e - (e / jb) * jb;
+        double g = 0.0;
+        if (q2 < q) {
+            for (int li = 0; li < nr; ++li) {
+                const int gi = r0 + li;
+                if (gi < q) continue;   // v_q is zero above row q
+                const double vq = gi == q ? 1.0 : (taus[q] == 0.0 ? 0.0 : P[li * LDP + q]);
+                const double vq2 = gi == q2 ? 1.0 : (taus[q2] == 0.0 ? 0.0 : P[li * LDP + q2]);
+                g = fma(vq, vq2, g);
+            }
+        }
+        gram[q * JB + q2] = g;
+    }
+    cluster.sync();
+    if (rank == 0) {
+        // g_c[b] = v_b^T v_c (b < c), summed over ranks in order; T forward-columnwise
+        for (int e = tid; e < jb * jb; e += CP_THREADS) {
+            const int q = e / jb, q2 = e - (e / jb) * jb;
+            double g = 0.0;
+            if (q2 < q)
+                for (int k = 0; k < cs; ++k) g += cluster.map_shared_rank(gram, k)[q * JB + q2];
+            Ts[q * JB + q2] = g;   // temporarily the Gram, lower triangle
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // column c of T: T[a][c] = -tau_c sum_{b=a}^{c-1} T[a][b] g_c[b] for a < c.
+            // T's upper triangle overwrites the Gram's upper (unused) half.
+            for (int c = 0; c < jb; ++c) {
+                double val = 0.0;
+                if (lane < c) {
+                    for (int b = lane; b < c; ++b) val = fma(Ts[lane * JB + b], Ts[c * JB + b], val);
+                    val = -taus[c] * val;
+                }
+                __syncwarp();
+                if (lane < c) Ts[lane * JB + c] = val;
+                if (lane == c) Ts[c * JB + c] = taus[c];
+                __syncwarp();
+            }
+            for (int a = 0; a < jb; ++a)
+                for (int b = lane; b < jb; b += 32) T[a * jb + b] = b >= a ? Ts[a * JB + b] : 0.0;
+        }
+    }
+    cluster.sync();
+}
+
 __global__ void qr_init_q_kernel(double* Q, long long ldq, int M, int N) {
     const long long total = static_cast<long long>(M) * N;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
@@ -407,22 +624,24 @@ __global__ void qr_init_q_kernel(double* Q, long long ldq, int M, int N) {
     }
 }
 
-// R = sign-normalised upper triangle of W[0:N, 0:N]; flips the matching Q columns.
-__global__ void qr_finish_kernel(const double* W, long long ld, int M, int N, double* Q, long long ldq,
-                                 double* R, long long ldr) {
-    const long long totalR = static_cast<long long>(N) * N;
-    const long long totalQ = static_cast<long long>(M) * N;
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-         e < totalR + totalQ; e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        if (e < totalR) {
-            const long long i = e / N, j = e % N;
-            const double s = W[i * ld + i] < 0.0 ? -1.0 : 1.0;
-            R[i * ldr + j] = (j >= i) ? s * W[i * ld + j] : 0.0;
-        } else {
-            const long long f = e - totalR;
-            const long long i = f / N, j = f % N;
-            if (W[j * ld + j] < 0.0) Q[i * ldq + j] = -Q[i * ldq + j];
-        }
+// R = sign-normalised upper triangle of W[0:N, 0:N] (row i flipped when W_ii < 0).
+__global__ void qr_write_r_kernel(const double* W, long long ld, int N, double* R, long long ldr) {
+    const long long total = static_cast<long long>(N) * N;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / N, j = e % N;
+        const double s = W[i * ld + i] < 0.0 ? -1.0 : 1.0;
+        R[i * ldr + j] = (j >= i) ? s * W[i * ld + j] : 0.0;
+    }
+}
+
+// Flip column j of Q where W_jj < 0 (the matching sign normalisation of Q).
+__global__ void qr_flip_q_kernel(const double* W, long long ld, int M, int N, double* Q, long long ldq) {
+    const long long total = static_cast<long long>(M) * N;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / N, j = e % N;
+        if (W[j * ld + j] < 0.0) Q[i * ldq + j] = -Q[i * ldq + j];
     }
 }
 
@@ -749,69 +968,185 @@ gn_status set_zero_f64(gn_handle h, double* p, long long rows, long long cols, l
 // QR workspace: V (M x N), tau (N), T per panel (jb x jb), Z1, Z2 (jb x N), GEMM split-K.
 size_t qr_ws_bytes(long long M, long long N, int sm_count) {
     const long long panels = (N + QR_JB - 1) / QR_JB;
-    size_t b = sizeof(double) * (M * N + N + panels * QR_JB * QR_JB + 2 * QR_JB * N);
-    b += dgemm_ws_bytes(QR_JB, N, M, sm_count);
+    size_t b = sizeof(double) * (M * N + N + panels * QR_NB * QR_NB + 2 * QR_NB * N);
+    b += std::max(dgemm_ws_bytes(QR_NB, N, M, sm_count), dgemm_ws_bytes(QR_JB, N, M, sm_count));
     return b + 256;
 }
 
-gn_status householder_qr(gn_handle h, double* W, long long M, long long N, long long ld, double* Q,
-                         long long ldq, double* R, long long ldr, double* ws, size_t ws_bytes) {
+namespace {
+struct QrWs {
+    double *V, *tau, *Tall, *Z1, *Z2, *gws;
+    size_t gws_bytes;
+};
+
+QrWs qr_carve(long long M, long long N, double* ws, size_t ws_bytes) {
+    const long long panels = (N + QR_JB - 1) / QR_JB;
+    QrWs q;
+    q.V = ws;
+    q.tau = q.V + M * N;
+    q.Tall = q.tau + N;
+    q.Z1 = q.Tall + panels * QR_NB * QR_NB;
+    q.Z2 = q.Z1 + QR_NB * N;
+    q.gws = q.Z2 + QR_NB * N;
+    q.gws_bytes = ws_bytes - sizeof(double) * (q.gws - ws);
+    return q;
+}
+
+constexpr size_t CP_SMEM_MAX = 200 * 1024;
+
+// Panel scheme for an M x N factorization: the cluster kernel with 32- or
+// 16-wide panels when a panel's rows fit the cluster's shared memory, else the
+// single-CTA kernel (global-memory panel for tall inputs).
+struct PanelCfg {
+    int nb;
+    int cluster;
+    int cs;
+};
+
+int cluster_size(gn_handle h) {
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    cached = 0;
+    cudaFuncSetAttribute(qr_panel_cluster_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(CP_SMEM_MAX));
+    cudaFuncSetAttribute(qr_panel_cluster_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(CP_SMEM_MAX));
+    cudaFuncSetAttribute(qr_panel_cluster_kernel<32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(qr_panel_cluster_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int cs : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(CP_THREADS);
+        cfg.dynamicSmemBytes = CP_SMEM_MAX;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, qr_panel_cluster_kernel<32>, &cfg) == cudaSuccess && n >= 1 &&
+            cudaOccupancyMaxActiveClusters(&n, qr_panel_cluster_kernel<16>, &cfg) == cudaSuccess && n >= 1) {
+            cached = cs;
+            break;
+        }
+    }
+    cudaGetLastError();
+    (void)h;
+    return cached;
+}
+
+PanelCfg panel_cfg(gn_handle h, long long M) {
+    const int cs = cluster_size(h);
+    if (cs > 0) {
+        const int rp = static_cast<int>((M + cs - 1) / cs);
+        if (cluster_panel_smem<32>(rp) <= CP_SMEM_MAX) return {32, 1, cs};
+        if (cluster_panel_smem<16>(rp) <= CP_SMEM_MAX) return {16, 1, cs};
+    }
+    return {QR_JB, 0, 0};
+}
+
+gn_status launch_cluster_panel(gn_handle h, const PanelCfg& pc, double* W, long long ld, long long M,
+                               long long j0, int jb, double* V, long long ldv, double* tau, double* T) {
+    const long long Mp = M - j0;
+    const int rows_per = static_cast<int>((Mp + pc.cs - 1) / pc.cs);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pc.cs);
+    cfg.blockDim = dim3(CP_THREADS);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pc.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int Mi = static_cast<int>(M), j0i = static_cast<int>(j0);
+    if (pc.nb == 32) {
+        cfg.dynamicSmemBytes = cluster_panel_smem<32>(rows_per);
+        GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, qr_panel_cluster_kernel<32>, W, ld, Mi, j0i, jb, V, ldv, tau, T,
+                                       rows_per));
+    } else {
+        cfg.dynamicSmemBytes = cluster_panel_smem<16>(rows_per);
+        GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, qr_panel_cluster_kernel<16>, W, ld, Mi, j0i, jb, V, ldv, tau, T,
+                                       rows_per));
+    }
+    count_launch();
+    return GN_OK;
+}
+}  // namespace
+
+gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R, long long ldr,
+                    double* ws, size_t ws_bytes) {
     if (M < N || N <= 0) return GN_ERR_SHAPE;
     if (ws_bytes < qr_ws_bytes(M, N, h->sm_count)) return GN_ERR_WORKSPACE;
-    const long long panels = (N + QR_JB - 1) / QR_JB;
-    double* V = ws;
-    double* tau = V + M * N;
-    double* Tall = tau + N;
-    double* Z1 = Tall + panels * QR_JB * QR_JB;
-    double* Z2 = Z1 + QR_JB * N;
-    double* gws = Z2 + QR_JB * N;
-    const size_t gws_bytes = ws_bytes - sizeof(double) * (gws - ws);
-
+    QrWs q = qr_carve(M, N, ws, ws_bytes);
     static bool attr = false;
     if (!attr) {
         GN_CUDA_TRY(cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(QR_SMEM_PANEL_MAX)));
         attr = true;
     }
-    for (long long j0 = 0; j0 < N; j0 += QR_JB) {
-        const int jb = static_cast<int>(std::min<long long>(QR_JB, N - j0));
+    const PanelCfg pc = panel_cfg(h, M);
+    const int nb = pc.nb;
+    for (long long j0 = 0; j0 < N; j0 += nb) {
+        const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
         const long long Mp = M - j0;
-        const size_t panel_bytes = static_cast<size_t>(Mp) * jb * sizeof(double);
-        const int use_smem = panel_bytes <= QR_SMEM_PANEL_MAX ? 1 : 0;
-        double* T = Tall + (j0 / QR_JB) * QR_JB * QR_JB;
-        qr_panel_kernel<<<1, QR_THREADS, use_smem ? panel_bytes : 0, h->stream>>>(
-            W, ld, static_cast<int>(M), static_cast<int>(j0), jb, V, N, tau, T, use_smem); count_launch();
-        GN_CUDA_TRY(cudaGetLastError());
+        double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
+        if (pc.cluster) {
+            GN_TRY(launch_cluster_panel(h, pc, W, ld, M, j0, jb, q.V, N, q.tau, T));
+        } else {
+            const size_t panel_bytes = static_cast<size_t>(Mp) * (jb + 1) * sizeof(double);
+            const int use_smem = panel_bytes <= QR_SMEM_PANEL_MAX ? 1 : 0;
+            qr_panel_kernel<<<1, QR_THREADS, use_smem ? panel_bytes : 0, h->stream>>>(
+                W, ld, static_cast<int>(M), static_cast<int>(j0), jb, q.V, N, q.tau, T, use_smem); count_launch();
+            GN_CUDA_TRY(cudaGetLastError());
+        }
         const long long N2 = N - j0 - jb;
         if (N2 > 0) {
             double* W2 = W + j0 * ld + j0 + jb;
-            const double* Vb = V + j0 * N + j0;
+            const double* Vb = q.V + j0 * N + j0;
             // Z1 = V^T W2 ; Z2 = T^T Z1 ; W2 -= V Z2
-            GN_TRY(dgemm(h, jb, N2, Mp, 1.0, Vb, N, 1, W2, ld, 0, 0.0, Z1, N2, gws, gws_bytes));
-            GN_TRY(dgemm(h, jb, N2, jb, 1.0, T, jb, 1, Z1, N2, 0, 0.0, Z2, N2, gws, gws_bytes));
-            GN_TRY(dgemm(h, Mp, N2, jb, -1.0, Vb, N, 0, Z2, N2, 0, 1.0, W2, ld, gws, gws_bytes));
+            GN_TRY(dgemm(h, jb, N2, Mp, 1.0, Vb, N, 1, W2, ld, 0, 0.0, q.Z1, N2, q.gws, q.gws_bytes));
+            GN_TRY(dgemm(h, jb, N2, jb, 1.0, T, jb, 1, q.Z1, N2, 0, 0.0, q.Z2, N2, q.gws, q.gws_bytes));
+            GN_TRY(dgemm(h, Mp, N2, jb, -1.0, Vb, N, 0, q.Z2, N2, 0, 1.0, W2, ld, q.gws, q.gws_bytes));
         }
     }
+    qr_write_r_kernel<<<ew_blocks(h, N * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(N), R, ldr); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+gn_status qr_form_q(gn_handle h, const double* W, long long M, long long N, long long ld, double* Q,
+                    long long ldq, double* ws, size_t ws_bytes) {
+    QrWs q = qr_carve(M, N, ws, ws_bytes);
+    const int nb = panel_cfg(h, M).nb;   // the factorization's panel width
     // Q = H_0 ... H_{N-1} [I; 0], applied block by block from the last panel.
     qr_init_q_kernel<<<ew_blocks(h, M * N), 256, 0, h->stream>>>(Q, ldq, static_cast<int>(M),
                                                                   static_cast<int>(N)); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
-    for (long long j0 = ((N - 1) / QR_JB) * QR_JB; j0 >= 0; j0 -= QR_JB) {
-        const int jb = static_cast<int>(std::min<long long>(QR_JB, N - j0));
+    for (long long j0 = ((N - 1) / nb) * nb; j0 >= 0; j0 -= nb) {
+        const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
         const long long Mp = M - j0;
         const long long Nq = N - j0;
         double* Qs = Q + j0 * ldq + j0;
-        const double* Vb = V + j0 * N + j0;
-        const double* T = Tall + (j0 / QR_JB) * QR_JB * QR_JB;
-        GN_TRY(dgemm(h, jb, Nq, Mp, 1.0, Vb, N, 1, Qs, ldq, 0, 0.0, Z1, Nq, gws, gws_bytes));
-        GN_TRY(dgemm(h, jb, Nq, jb, 1.0, T, jb, 0, Z1, Nq, 0, 0.0, Z2, Nq, gws, gws_bytes));
-        GN_TRY(dgemm(h, Mp, Nq, jb, -1.0, Vb, N, 0, Z2, Nq, 0, 1.0, Qs, ldq, gws, gws_bytes));
+        const double* Vb = q.V + j0 * N + j0;
+        const double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
+        GN_TRY(dgemm(h, jb, Nq, Mp, 1.0, Vb, N, 1, Qs, ldq, 0, 0.0, q.Z1, Nq, q.gws, q.gws_bytes));
+        GN_TRY(dgemm(h, jb, Nq, jb, 1.0, T, jb, 0, q.Z1, Nq, 0, 0.0, q.Z2, Nq, q.gws, q.gws_bytes));
+        GN_TRY(dgemm(h, Mp, Nq, jb, -1.0, Vb, N, 0, q.Z2, Nq, 0, 1.0, Qs, ldq, q.gws, q.gws_bytes));
     }
-    qr_finish_kernel<<<ew_blocks(h, N * N + M * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(M),
-                                                                          static_cast<int>(N), Q, ldq,
-                                                                          R, ldr); count_launch();
+    qr_flip_q_kernel<<<ew_blocks(h, M * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(M),
+                                                                  static_cast<int>(N), Q, ldq); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     return GN_OK;
+}
+
+gn_status householder_qr(gn_handle h, double* W, long long M, long long N, long long ld, double* Q,
+                         long long ldq, double* R, long long ldr, double* ws, size_t ws_bytes) {
+    GN_TRY(qr_factor(h, W, M, N, ld, R, ldr, ws, ws_bytes));
+    return qr_form_q(h, W, M, N, ld, Q, ldq, ws, ws_bytes);
 }
 
 size_t trsm_ws_bytes(long long m, long long k, int sm_count) {
@@ -906,7 +1241,7 @@ gn_status error_fro2(gn_handle h, const void* A, int a_dtype, const void* A_lo, 
     dim3 grid(static_cast<unsigned>((n + GT - 1) / GT), static_cast<unsigned>((m + GT - 1) / GT), 1);
     ErrArgs e{A, A_lo, a_dtype, lda, ws};
     const int kk = static_cast<int>(k);
-    dgemm_kernel<double, double, EPI_ERR><<<grid, GTHREADS, 0, h->stream>>>(
+    dgemm_kernel<GT, GT, double, double, EPI_ERR><<<grid, GTHREADS, 0, h->stream>>>(
         (int)m, (int)n, kk, 1.0, F, ldf, 0, G, ldg, 0, 0.0, nullptr, 0, nullptr, kk > 0 ? kk : 1, e); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     reduce_sum_kernel<<<1, 1024, 0, h->stream>>>(ws, static_cast<long long>(grid.x) * grid.y, out); count_launch();

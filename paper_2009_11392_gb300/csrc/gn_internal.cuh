@@ -15,6 +15,8 @@ struct gn_handle_s {
     int device;
     int sm_count;
     cudaStream_t stream;
+    cudaStream_t side;         // second stream: work that overlaps the main sequence
+    cudaEvent_t ev_fork, ev_join;
     int32_t* dstatus;          // device: [0] latched gn_status, [1] where
     uint64_t wait_limit_ns;
 };
@@ -99,6 +101,12 @@ size_t qr_ws_bytes(long long M, long long N, int sm_count);
 gn_status householder_qr(gn_handle h, double* W, long long M, long long N, long long ld,
                          double* Q, long long ldq, double* R, long long ldr,
                          double* ws, size_t ws_bytes);
+// The two halves of householder_qr: the factorization (R written, reflectors
+// kept in ws) and the formation of the thin Q from them (same W and ws).
+gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R,
+                    long long ldr, double* ws, size_t ws_bytes);
+gn_status qr_form_q(gn_handle h, const double* W, long long M, long long N, long long ld, double* Q,
+                    long long ldq, double* ws, size_t ws_bytes);
 
 // Right triangular solves, FP64, in place on F (m x k):
 //   upper == 1, trans == 0: F <- F R^{-1}   (R upper, k x k)
