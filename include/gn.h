@@ -199,6 +199,26 @@ gn_status gn_approx(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat*
 gn_status gn_error_fro2(gn_handle h, const gn_mat* A, const gn_mat* F, const gn_mat* G,
                         double* out, void* ws, size_t ws_bytes);
 
+/* Allocation-free ||A - F G||_F^2, for callers that cannot allocate device
+ * memory: for example code that runs inside a host application whose memory
+ * manager owns the whole device and refuses further cudaMalloc calls, or a
+ * latency-critical loop that must not allocate.  The paper has no counterpart;
+ * this is a convenience of the library.
+ * Same arguments, arithmetic and result as gn_error_fro2, but no workspace: the
+ * per-tile partial sums live in one fixed array in device memory that every
+ * GPU loading the library holds until the process exits (128 KB).  Limit:
+ * ceil(m/64) * ceil(n/64) <= 16384 tiles (about 67 million elements of A, e.g.
+ * 8192 x 8192); larger sizes return GN_ERR_SHAPE before anything runs.  No
+ * device memory is allocated by this call.  The first call on a device looks
+ * up the array's device address (once per device, with that device made
+ * current); make that first call before any stream capture.  All calls share
+ * the one array and each overwrites every slot it reads, so its previous
+ * contents never matter -- but calls whose kernels overlap on the GPU (for
+ * example on two streams at once) race on the array and give wrong results;
+ * order them on one stream. */
+gn_status gn_error_fro2_noalloc(gn_handle h, const gn_mat* A, const gn_mat* F, const gn_mat* G,
+                                double* out);
+
 /* ---------------------------------------------------------------- Algorithm 1 */
 
 /* HMT range finder (Algorithm 1): AX, Householder QR AX = Q R_x, B = Q^T A.

@@ -36,7 +36,7 @@ ABI_SYMBOLS = (
     "gn_create", "gn_destroy", "gn_set_stream", "gn_sync_status", "gn_set_wait_limit",
     "gn_status_string", "gn_device_sm_count", "gn_workspace_size", "gn_quantize",
     "gn_sketch", "gn_core", "gn_factors", "gn_approx", "gn_error_fro2", "gn_hmt",
-    "gn_kernel_launches",
+    "gn_kernel_launches", "gn_error_fro2_noalloc",
 )
 
 
@@ -90,6 +90,7 @@ def _load():
         "gn_error_fro2": ([P, M, M, M, P, P, SZ], I32),
         "gn_hmt": ([P, M, M, M, M, P, SZ], I32),
         "gn_kernel_launches": ([], ctypes.c_uint64),
+        "gn_error_fro2_noalloc": ([P, M, M, M, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -262,6 +263,12 @@ class Handle:
         _check(lib.gn_error_fro2(self._h, ctypes.byref(mat(A, A_lo)), ctypes.byref(mat(F)), ctypes.byref(mat(G)),
                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel()),
                "gn_error_fro2")
+
+    def error_fro2_noalloc(self, A, F, G, out, A_lo=None):
+        """Like error_fro2 but without a workspace (fixed device array inside the library)."""
+        _check(lib.gn_error_fro2_noalloc(self._h, ctypes.byref(mat(A, A_lo)), ctypes.byref(mat(F)),
+                                         ctypes.byref(mat(G)), ctypes.c_void_p(out.data_ptr())),
+               "gn_error_fro2_noalloc")
 
     def hmt(self, A, X, Q, B, ws):
         _check(lib.gn_hmt(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Q)),
