@@ -344,12 +344,17 @@ def main():
         except Exception as ex:  # pragma: no cover
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
 
+    # DRAM bytes per launch from the committed ncu summary, valid only while the
+    # kernel source is the one the counters were taken on.
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         try:
+            import hashlib
             t = json.load(open(tp)).get(f"sketch_bf16_{m}x{n}_r{r}")
-            traffic = t
+            src = open(os.path.join(ROOT, "paper_2009_11392_gb300", "csrc", "gn_tc.cu"), "rb").read()
+            if t and hashlib.sha256(src).hexdigest()[:16] == t["kernel_sha256_16"]:
+                traffic = t["traffic_bytes"]
         except Exception:
             traffic = None
 

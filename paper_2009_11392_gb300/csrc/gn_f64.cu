@@ -493,12 +493,9 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
                 pn = cluster.map_shared_rank(normp, lane)[par];
                 pa = cluster.map_shared_rank(alphas, lane)[par];
             }
-            // rank-ordered sum (identical in every CTA)
-            double tail = 0.0, alpha = 0.0;
-            for (int k = 0; k < cs; ++k) {
-                tail += __shfl_sync(0xffffffffu, pn, k);
-                alpha += __shfl_sync(0xffffffffu, pa, k);
-            }
+            // fixed butterfly over the rank partials: the same sum in every CTA
+            const double tail = warp_sum(pn);
+            const double alpha = warp_sum(pa);
             if (lane == 0) {
                 if (tail == 0.0) {
                     s_tau = 0.0;
@@ -515,6 +512,11 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
         }
         __syncthreads();
         const double t = s_tau;
+        if (tid == 0) {   // R_cc = beta (its old value, alpha, is no longer read)
+            if (c >= r0 && c < r0 + nr) P[(c - r0) * LDP + c] = s_beta;
+            taus[c] = t;
+            if (rank == 0) tau[j0 + c] = t;
+        }
         if (t != 0.0) {
             const double sc = s_scale;
             for (int li = tid; li < nr; li += CP_THREADS)
@@ -535,10 +537,16 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
         }
         cluster.sync();
         if (t != 0.0 && c + 1 < jb) {
-            if (tid > c && tid < jb) {
-                double sw = 0.0;
-                for (int k = 0; k < cs; ++k) sw += cluster.map_shared_rank(wpart, k)[par * JB + tid];
-                wsum[tid] = sw;
+            // half-warp per column: lane (mod 16) = rank, fixed butterfly sum
+            const int half = lane >> 4, k = lane & 15;
+            const int iters = (jb - c - 1 + 2 * CP_WARPS - 1) / (2 * CP_WARPS);   // same in every lane
+            for (int it = 0; it < iters; ++it) {
+                const int q = c + 1 + 2 * CP_WARPS * it + 2 * warp + half;
+                const bool live = q < jb;
+                double sw = (live && k < cs) ? cluster.map_shared_rank(wpart, k)[par * JB + q] : 0.0;
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, o);
+                if (live && k == 0) wsum[q] = sw;
             }
             __syncthreads();
             const int nq = jb - c - 1;
@@ -550,12 +558,6 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
                     P[li * LDP + q] = fma(-t * vi, wsum[q], P[li * LDP + q]);
                 }
             }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            if (c >= r0 && c < r0 + nr) P[(c - r0) * LDP + c] = s_beta;
-            taus[c] = t;
-            if (rank == 0) tau[j0 + c] = t;
         }
         __syncthreads();
     }
