@@ -439,9 +439,16 @@ __device__ __forceinline__ double warp_sum(double s) {
 
 template <int JB>
 __host__ __device__ constexpr size_t cluster_panel_smem(int rows_per) {
-    return sizeof(double) * (static_cast<size_t>(rows_per) * (JB + 1) + 4 + 2 * JB + JB * JB + JB + JB * JB);
+    // P + exchange slots [2][2+2JB] + tv[rows_per] + dsum/prow/w [3][JB] + gram, T [2][JB*JB]
+    return sizeof(double) * (static_cast<size_t>(rows_per) * (JB + 1) + 2 * (2 + 2 * JB) + rows_per +
+                             3 * JB + 2 * JB * JB);
 }
 
+// One exchange per column: with x = P[c:, c], alpha = x_0, beta = -sign(alpha)||x||
+// and v = x / (alpha - beta) (v_0 = 1), the update vector is
+//     w_q = v^T P_q = (x^T P_q - beta P_cq) / (alpha - beta),
+// so ||x[1:]||^2, the dot products x^T P_q and the owner's row c are all the
+// per-CTA partials a column needs, and they are exchanged in one cluster round.
 template <int JB>
 __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W, long long ld, int M, int j0,
                                                                      int jb, double* V, long long ldv,
@@ -451,13 +458,15 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     const int rank = static_cast<int>(cluster.block_rank());
     extern __shared__ double sm[];
     constexpr int LDP = JB + 1;
+    constexpr int SLOT = 2 + 2 * JB;   // [tail, alpha, dots[JB], row_c[JB]]
     double* P = sm;
-    double* normp = P + static_cast<size_t>(rows_per) * LDP;   // [2] partial sums of squares
-    double* alphas = normp + 2;                                  // [2] diagonal entry (owner only)
-    double* wpart = alphas + 2;                                  // [2][JB] partial w
-    double* gram = wpart + 2 * JB;                               // [JB][JB] partial V^T V
-    double* wsum = gram + JB * JB;                               // [JB]
-    double* Ts = wsum + JB;                                      // [JB][JB]
+    double* xch = P + static_cast<size_t>(rows_per) * LDP;   // [2][SLOT]
+    double* tv = xch + 2 * SLOT;                             // [rows_per] tau * v_i
+    double* dsum = tv + rows_per;                            // [JB] x^T P_q summed over ranks
+    double* prow = dsum + JB;                                // [JB] row c of the panel
+    double* wv = prow + JB;                                  // [JB] w_q
+    double* gram = wv + JB;                                  // [JB][JB] partial V^T V
+    double* Ts = gram + JB * JB;                             // [JB][JB]
     __shared__ double taus[JB];
     __shared__ double s_tau, s_beta, s_scale;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -466,34 +475,43 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     const int nr = max(0, min(rows_per, Mp - r0));
 
     for (int e = tid; e < nr * jb; e += CP_THREADS) {
-        const int i = e / jb, c = e - (e / jb) * jb;
+        const int i = e / jb, c = e - i * jb;
         P[i * LDP + c] = W[static_cast<long long>(j0 + r0 + i) * ld + j0 + c];
     }
     __syncthreads();
 
     for (int c = 0; c < jb; ++c) {
-        const int par = c & 1;
+        double* slot = xch + (c & 1) * SLOT;
+        const int cl = c - r0;                       // local index of row c (owner iff 0 <= cl < nr)
+        const bool owner = cl >= 0 && cl < nr;
+        const int lo = max(0, cl);                   // first local row with panel row >= c
+        // ---- per-CTA partials
         if (warp == 0) {
             double sq = 0.0;
-            for (int li = lane; li < nr; li += 32)
-                if (r0 + li > c) {
-                    const double x = P[li * LDP + c];
-                    sq = fma(x, x, sq);
-                }
+            for (int li = max(0, cl + 1) + lane; li < nr; li += 32) {
+                const double x = P[li * LDP + c];
+                sq = fma(x, x, sq);
+            }
             sq = warp_sum(sq);
             if (lane == 0) {
-                normp[par] = sq;
-                alphas[par] = (c >= r0 && c < r0 + nr) ? P[(c - r0) * LDP + c] : 0.0;
+                slot[0] = sq;
+                slot[1] = owner ? P[cl * LDP + c] : 0.0;
+            }
+        }
+        for (int q = c + 1 + warp; q < jb; q += CP_WARPS) {
+            double d = 0.0;
+            for (int li = lo + lane; li < nr; li += 32) d = fma(P[li * LDP + c], P[li * LDP + q], d);
+            d = warp_sum(d);
+            if (lane == 0) {
+                slot[2 + q] = d;
+                slot[2 + JB + q] = owner ? P[cl * LDP + q] : 0.0;
             }
         }
         cluster.sync();
+        // ---- combine (rank order, fixed butterflies: identical in every CTA)
         if (warp == 0) {
-            double pn = 0.0, pa = 0.0;
-            if (lane < cs) {
-                pn = cluster.map_shared_rank(normp, lane)[par];
-                pa = cluster.map_shared_rank(alphas, lane)[par];
-            }
-            // fixed butterfly over the rank partials: the same sum in every CTA
+            const double pn = lane < cs ? cluster.map_shared_rank(slot, lane)[0] : 0.0;
+            const double pa = lane < cs ? cluster.map_shared_rank(slot, lane)[1] : 0.0;
             const double tail = warp_sum(pn);
             const double alpha = warp_sum(pa);
             if (lane == 0) {
@@ -510,52 +528,54 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
                 }
             }
         }
+        {
+            const int half = lane >> 4, k = lane & 15;
+            const int iters = (jb - c - 1 + 2 * CP_WARPS - 1) / (2 * CP_WARPS);
+            for (int it = 0; it < iters; ++it) {
+                const int q = c + 1 + 2 * CP_WARPS * it + 2 * warp + half;
+                const bool live = q < jb;
+                double d = 0.0, pr = 0.0;
+                if (live && k < cs) {
+                    const double* rs = cluster.map_shared_rank(slot, k);
+                    d = rs[2 + q];
+                    pr = rs[2 + JB + q];
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    d += __shfl_xor_sync(0xffffffffu, d, o);
+                    pr += __shfl_xor_sync(0xffffffffu, pr, o);
+                }
+                if (live && k == 0) {
+                    dsum[q] = d;
+                    prow[q] = pr;
+                }
+            }
+        }
         __syncthreads();
         const double t = s_tau;
-        if (tid == 0) {   // R_cc = beta (its old value, alpha, is no longer read)
-            if (c >= r0 && c < r0 + nr) P[(c - r0) * LDP + c] = s_beta;
+        if (tid == 0) {
+            if (owner) P[cl * LDP + c] = s_beta;
             taus[c] = t;
             if (rank == 0) tau[j0 + c] = t;
         }
         if (t != 0.0) {
-            const double sc = s_scale;
-            for (int li = tid; li < nr; li += CP_THREADS)
-                if (r0 + li > c) P[li * LDP + c] *= sc;
-            __syncthreads();
-            for (int q = c + 1 + warp; q < jb; q += CP_WARPS) {
-                double sw = 0.0;
-                for (int li = lane; li < nr; li += 32) {
-                    const int gi = r0 + li;
-                    if (gi >= c) {
-                        const double vi = (gi == c) ? 1.0 : P[li * LDP + c];
-                        sw = fma(vi, P[li * LDP + q], sw);
-                    }
+            const double sc = s_scale, beta = s_beta;
+            // v_i = x_i / (alpha - beta) for rows below c; tv_i = tau v_i (v_c = 1)
+            for (int li = lo + tid; li < nr; li += CP_THREADS) {
+                double vi = 1.0;
+                if (li != cl) {
+                    vi = P[li * LDP + c] * sc;
+                    P[li * LDP + c] = vi;
                 }
-                sw = warp_sum(sw);
-                if (lane == 0) wpart[par * JB + q] = sw;
+                tv[li] = t * vi;
             }
-        }
-        cluster.sync();
-        if (t != 0.0 && c + 1 < jb) {
-            // half-warp per column: lane (mod 16) = rank, fixed butterfly sum
-            const int half = lane >> 4, k = lane & 15;
-            const int iters = (jb - c - 1 + 2 * CP_WARPS - 1) / (2 * CP_WARPS);   // same in every lane
-            for (int it = 0; it < iters; ++it) {
-                const int q = c + 1 + 2 * CP_WARPS * it + 2 * warp + half;
-                const bool live = q < jb;
-                double sw = (live && k < cs) ? cluster.map_shared_rank(wpart, k)[par * JB + q] : 0.0;
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, o);
-                if (live && k == 0) wsum[q] = sw;
-            }
+            if (tid > c && tid < jb) wv[tid] = fma(-beta, prow[tid], dsum[tid]) * sc;
             __syncthreads();
             const int nq = jb - c - 1;
-            for (int e = tid; e < nr * nq; e += CP_THREADS) {
-                const int li = e / nq, q = c + 1 + (e - (e / nq) * nq);
-                const int gi = r0 + li;
-                if (gi >= c) {
-                    const double vi = (gi == c) ? 1.0 : P[li * LDP + c];
-                    P[li * LDP + q] = fma(-t * vi, wsum[q], P[li * LDP + q]);
+            if (nq > 0) {
+                for (int li = lo + warp; li < nr; li += CP_WARPS) {
+                    const double tvi = tv[li];
+                    for (int q = c + 1 + lane; q < jb; q += 32) P[li * LDP + q] = fma(-tvi, wv[q], P[li * LDP + q]);
                 }
             }
         }
@@ -564,7 +584,7 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
 
     // write back the panel, the explicit reflectors, and the partial Gram V^T V
     for (int e = tid; e < nr * jb; e += CP_THREADS) {
-        const int li = e / jb, c = e - (e / jb) * jb;
+        const int li = e / jb, c = e - li * jb;
         const int gi = r0 + li;
         const double pv = P[li * LDP + c];
         const double v = gi < c ? 0.0 : (gi == c ? 1.0 : (taus[c] == 0.0 ? 0.0 : pv));
@@ -572,12 +592,11 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
         W[static_cast<long long>(j0 + gi) * ld + j0 + c] = pv;
     }
     for (int e = tid; e < jb * jb; e += CP_THREADS) {
-        const int q = e / jb, q2 = e - (e / jb) * jb;
+        const int q = e / jb, q2 = e - q * jb;
         double g = 0.0;
         if (q2 < q) {
-            for (int li = 0; li < nr; ++li) {
+            for (int li = max(0, q - r0); li < nr; ++li) {   // v_q is zero above row q
                 const int gi = r0 + li;
-                if (gi < q) continue;   // v_q is zero above row q
                 const double vq = gi == q ? 1.0 : (taus[q] == 0.0 ? 0.0 : P[li * LDP + q]);
                 const double vq2 = gi == q2 ? 1.0 : (taus[q2] == 0.0 ? 0.0 : P[li * LDP + q2]);
                 g = fma(vq, vq2, g);
@@ -587,18 +606,16 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     }
     cluster.sync();
     if (rank == 0) {
-        // g_c[b] = v_b^T v_c (b < c), summed over ranks in order; T forward-columnwise
         for (int e = tid; e < jb * jb; e += CP_THREADS) {
-            const int q = e / jb, q2 = e - (e / jb) * jb;
+            const int q = e / jb, q2 = e - q * jb;
             double g = 0.0;
             if (q2 < q)
                 for (int k = 0; k < cs; ++k) g += cluster.map_shared_rank(gram, k)[q * JB + q2];
-            Ts[q * JB + q2] = g;   // temporarily the Gram, lower triangle
+            Ts[q * JB + q2] = g;   // the Gram in the strict lower triangle; zeros elsewhere
         }
         __syncthreads();
         if (warp == 0) {
-            // column c of T: T[a][c] = -tau_c sum_{b=a}^{c-1} T[a][b] g_c[b] for a < c.
-            // T's upper triangle overwrites the Gram's upper (unused) half.
+            // column c of T: T[a][c] = -tau_c sum_{b=a}^{c-1} T[a][b] g_c[b] for a < c
             for (int c = 0; c < jb; ++c) {
                 double val = 0.0;
                 if (lane < c) {
@@ -854,6 +871,228 @@ __global__ void __launch_bounds__(DG_THREADS) core_diag_kernel(const double* R, 
         __syncthreads();
     }
     if (threadIdx.x == 0) out[0] = est;
+}
+
+// Cluster version of the core diagnostics: rows of R are split over the CTAs of
+// a cluster.  The power iteration for ||R||_2 exchanges the matrix-vector
+// products through distributed shared memory; the blocked triangular solves of
+// the ||R^{-1}||_2 iteration are right-looking: the CTA owning a 32-row block
+// solves it with one warp, the block's solution is read by every CTA through
+// DSMEM (double-buffered by block parity, one cluster barrier per block), and
+// each CTA updates its own rows.  Same results as core_diag_kernel.
+constexpr int CD_THREADS = 512;
+constexpr int CD_WARPS = CD_THREADS / 32;
+constexpr int CD_MAX_R = 4096;
+
+__host__ __device__ inline int cd_rows_per(int r, int cs) { return ((r + cs - 1) / cs + 31) / 32 * 32; }
+__host__ __device__ inline size_t cd_smem(int r, int cs) {
+    return sizeof(double) * (2 * static_cast<size_t>(r) + cd_rows_per(r, cs) + 64 + 32 + 32 * 33 + 8);
+}
+
+__global__ void __launch_bounds__(CD_THREADS) core_diag_cluster_kernel(const double* R, long long ldr, int r,
+                                                                      double eps, int eps_relative,
+                                                                      int want_est, int iters, double* out,
+                                                                      int* k_out) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = static_cast<int>(cluster.num_blocks());
+    const int rank = static_cast<int>(cluster.block_rank());
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    extern __shared__ double sm[];
+    const int rp = cd_rows_per(r, cs);
+    double* v = sm;              // [r]  full iterate (identical in every CTA)
+    double* u = v + r;           // [r]  gathered R v
+    double* loc = u + r;         // [rp] own slice of the vector being solved
+    double* blk = loc + rp;      // [2][32] solved block, read by the other CTAs
+    double* ybuf = blk + 64;     // [32] local copy of the solved block
+    double* Rb = ybuf + 32;      // [32][33] diagonal block (owner)
+    double* part = Rb + 32 * 33; // [8] partial norms, double-buffered
+    __shared__ int s_kmin;
+    const int s0 = rank * rp;
+    const int s1 = min(r, s0 + rp);
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    const double inv = 1.0 / sqrt(static_cast<double>(r));
+
+    // ---- ||R||_2 (power iteration on R^T R from the all-ones vector)
+    double rn = 0.0;
+    if (eps_relative) {
+        for (int i = tid; i < r; i += CD_THREADS) v[i] = inv;
+        __syncthreads();
+        for (int it = 0; it < iters; ++it) {
+            const int par = it & 1;
+            for (int i = s0 + warp; i < s1; i += CD_WARPS) {   // u_i = (R v)_i, own rows
+                double acc = 0.0;
+                for (int j = i + lane; j < r; j += 32) acc = fma(R[static_cast<long long>(i) * ldr + j], v[j], acc);
+                acc = warp_sum(acc);
+                if (lane == 0) u[i] = acc;
+            }
+            cluster.sync();
+            for (int k = 0; k < cs; ++k) {   // gather the other slices of u
+                if (k == rank) continue;
+                const double* ru = cluster.map_shared_rank(u, k);
+                const int a = k * rp, b = min(r, a + rp);
+                for (int i = a + tid; i < b; i += CD_THREADS) u[i] = ru[i];
+            }
+            cluster.sync();
+            double ss = 0.0;
+            for (int j = s0 + tid; j < s1; j += CD_THREADS) {   // w_j = (R^T u)_j, own columns
+                double acc = 0.0;
+                for (int i = 0; i <= j; ++i) acc = fma(R[static_cast<long long>(i) * ldr + j], u[i], acc);
+                v[j] = acc;
+                ss = fma(acc, acc, ss);
+            }
+            ss = warp_sum(ss);
+            if (lane == 0) Rb[warp] = ss;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < CD_WARPS; ++w) t += Rb[w];
+                part[par] = t;
+            }
+            cluster.sync();
+            double nw2 = 0.0;
+            for (int k = 0; k < cs; ++k) nw2 += cluster.map_shared_rank(part, k)[par];
+            for (int k = 0; k < cs; ++k) {   // gather the other slices of w into v
+                if (k == rank) continue;
+                const double* rv = cluster.map_shared_rank(v, k);
+                const int a = k * rp, b = min(r, a + rp);
+                for (int i = a + tid; i < b; i += CD_THREADS) v[i] = rv[i];
+            }
+            const double nw = sqrt(nw2);
+            cluster.sync();   // every CTA has read my slice of v before it is rescaled
+            if (nw == 0.0 || !isfinite(nw)) {
+                rn = nw;
+                break;
+            }
+            rn = sqrt(nw);
+            const double sc = 1.0 / nw;
+            for (int i = tid; i < r; i += CD_THREADS) v[i] *= sc;
+            __syncthreads();
+        }
+        eps = eps * rn;
+    }
+
+    // ---- truncation rank (every CTA scans the diagonal; rank 0 reports)
+    if (tid == 0) s_kmin = r;
+    __syncthreads();
+    int zero_diag = 0;
+    for (int i = tid; i < r; i += CD_THREADS) {
+        const double d = R[static_cast<long long>(i) * ldr + i];
+        if (fabs(d) <= eps) atomicMin(&s_kmin, i);
+        if (d == 0.0) zero_diag = 1;
+    }
+    zero_diag = __syncthreads_or(zero_diag);
+    if (rank == 0 && tid == 0) {
+        *k_out = s_kmin;
+        out[1] = rn;
+        out[2] = eps;
+        out[0] = 0.0;
+    }
+    if (!want_est) {
+        cluster.sync();
+        return;
+    }
+    if (zero_diag) {
+        if (rank == 0 && tid == 0) out[0] = inf;
+        cluster.sync();
+        return;
+    }
+
+    // ---- ||R^{-1}||_2 (power iteration on R^{-1} R^{-T} from the all-ones vector)
+    const int nb = (r + 31) / 32;
+    for (int i = s0 + tid; i < s1; i += CD_THREADS) loc[i - s0] = inv;
+    __syncthreads();
+    double est = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        for (int pass = 0; pass < 2; ++pass) {   // pass 0: R^T y = z; pass 1: R w = y
+            for (int bi = 0; bi < nb; ++bi) {
+                const int b = pass == 0 ? bi : nb - 1 - bi;
+                const int j0 = b * 32, jb = min(32, r - j0);
+                const int owner = j0 / rp;
+                if (rank == owner && warp == 0) {
+#pragma unroll
+                    for (int a = 0; a < 32; ++a)   // 32 independent loads in flight
+                        Rb[a * 33 + lane] =
+                            (a < jb && lane < jb) ? R[static_cast<long long>(j0 + a) * ldr + j0 + lane] : 0.0;
+                    __syncwarp();
+                    const double rdl = lane < jb ? 1.0 / Rb[lane * 33 + lane] : 0.0;   // reciprocal diagonal
+                    double zl = lane < jb ? loc[j0 - s0 + lane] : 0.0;
+                    if (pass == 0) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            if (i < jb) {
+                                const double yi = __shfl_sync(0xffffffffu, zl, i) * __shfl_sync(0xffffffffu, rdl, i);
+                                if (lane == i) zl = yi;
+                                if (lane > i && lane < jb) zl = fma(-Rb[i * 33 + lane], yi, zl);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 31; i >= 0; --i) {
+                            if (i < jb) {
+                                const double wi = __shfl_sync(0xffffffffu, zl, i) * __shfl_sync(0xffffffffu, rdl, i);
+                                if (lane == i) zl = wi;
+                                if (lane < i) zl = fma(-Rb[lane * 33 + i], wi, zl);
+                            }
+                        }
+                    }
+                    // buffer alternates with (b + pass): consecutive blocks, including the
+                    // last block of one pass and the first of the next, never share a slot
+                    if (lane < jb) {
+                        loc[j0 - s0 + lane] = zl;
+                        blk[((b + pass) & 1) * 32 + lane] = zl;
+                    }
+                }
+                cluster.sync();
+                if (tid < jb) ybuf[tid] = cluster.map_shared_rank(blk, owner)[((b + pass) & 1) * 32 + tid];
+                __syncthreads();
+                if (pass == 0) {   // z_j -= sum_{i in block} R[i][j] y_i, own rows j after the block
+                    for (int j = max(s0, j0 + jb) + tid; j < s1; j += CD_THREADS) {
+                        double acc = loc[j - s0];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (i < jb) acc = fma(-R[static_cast<long long>(j0 + i) * ldr + j], ybuf[i], acc);
+                        loc[j - s0] = acc;
+                    }
+                } else {           // y_i -= sum_{j in block} R[i][j] w_j, own rows i before the block
+                    for (int i = s0 + tid; i < min(s1, j0); i += CD_THREADS) {
+                        double acc = loc[i - s0];
+                        const double* rr = R + static_cast<long long>(i) * ldr + j0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < jb) acc = fma(-rr[j], ybuf[j], acc);
+                        loc[i - s0] = acc;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        const int par = it & 1;
+        double ss = 0.0;
+        for (int i = s0 + tid; i < s1; i += CD_THREADS) ss = fma(loc[i - s0], loc[i - s0], ss);
+        ss = warp_sum(ss);
+        if (lane == 0) Rb[warp] = ss;   // Rb is free here (owner warps are done)
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < CD_WARPS; ++w) t += Rb[w];
+            part[2 + par] = t;
+        }
+        cluster.sync();
+        double nw2 = 0.0;
+        for (int k = 0; k < cs; ++k) nw2 += cluster.map_shared_rank(part, k)[2 + par];
+        const double nw = sqrt(nw2);
+        if (!isfinite(nw)) {
+            est = inf;
+            break;
+        }
+        est = sqrt(nw);
+        if (nw == 0.0) break;
+        const double sc = 1.0 / nw;
+        for (int i = s0 + tid; i < s1; i += CD_THREADS) loc[i - s0] *= sc;
+        __syncthreads();
+    }
+    if (rank == 0 && tid == 0) out[0] = est;
+    cluster.sync();
 }
 
 // --------------------------------------------------------------------------
@@ -1183,6 +1422,53 @@ gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, lon
 gn_status core_diagnostics(gn_handle h, const double* R, long long r, long long ldr, double eps,
                            int eps_relative, int want_estimate, int iters, double* out3, int* k_out,
                            double* ws, size_t ws_bytes) {
+    static int cd_cs = -1;
+    if (cd_cs < 0) {
+        cd_cs = 0;
+        const size_t smax = cd_smem(CD_MAX_R, 8);
+        if (cudaFuncSetAttribute(core_diag_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smax)) == cudaSuccess &&
+            cudaFuncSetAttribute(core_diag_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
+            for (int cs : {16, 8}) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(cs);
+                cfg.blockDim = dim3(CD_THREADS);
+                cfg.dynamicSmemBytes = smax;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = cs;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int n = 0;
+                if (cudaOccupancyMaxActiveClusters(&n, core_diag_cluster_kernel, &cfg) == cudaSuccess && n >= 1) {
+                    cd_cs = cs;
+                    break;
+                }
+            }
+        }
+        cudaGetLastError();
+    }
+    if (cd_cs > 0 && r <= CD_MAX_R && r >= 64) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cd_cs);
+        cfg.blockDim = dim3(CD_THREADS);
+        cfg.dynamicSmemBytes = cd_smem(static_cast<int>(r), cd_cs);
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cd_cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, core_diag_cluster_kernel, R, ldr, static_cast<int>(r), eps,
+                                       eps_relative, want_estimate, iters, out3, k_out));
+        count_launch();
+        return GN_OK;
+    }
     if (ws_bytes < 2 * static_cast<size_t>(r) * sizeof(double)) return GN_ERR_WORKSPACE;
     core_diag_kernel<<<1, DG_THREADS, 0, h->stream>>>(R, ldr, static_cast<int>(r), eps, eps_relative,
                                                       want_estimate, iters, ws, out3, k_out); count_launch();

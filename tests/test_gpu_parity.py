@@ -289,3 +289,40 @@ def test_relative_eps_and_auto_switch(gn, H):
     assert core.sgn == 1 and core.k == 7 and math.isinf(core.rinv_est)
     Ah = npy(F)[:, :7] @ npy(G)[:7]
     assert rel(Ah, Ahat) <= 1e-10
+
+
+@pytest.mark.parametrize("kind", ["wellcond", "rankdef"])
+def test_core_diagnostics_cluster_path(gn, H, kind):
+    """r >= 64 takes the clustered diagnostics kernel: est ||R^{-1}||, est ||C||
+    (relative eps) and the truncation rank against the oracle (6 iterations)."""
+    m, n, r, l = 700, 420, 100, 50
+    rng = np.random.default_rng(77)
+    if kind == "wellcond":
+        A = rng.standard_normal((m, n)) * (0.97 ** np.arange(n))[None, :]
+    else:
+        k0 = 70
+        U, _ = np.linalg.qr(rng.standard_normal((m, k0)))
+        V, _ = np.linalg.qr(rng.standard_normal((n, k0)))
+        A = (U * np.linspace(3.0, 1.0, k0)) @ V.T
+    X, Y = gn_synth.sketches(m, n, r, l, 78)
+    X, Y = X.numpy(), Y.numpy()
+    eps = 10 * O.U64 if kind == "wellcond" else 1e-9
+    md = gn.AUTO if kind == "wellcond" else gn.SGN
+    omd = O.AUTO if kind == "wellcond" else O.SGN
+    Ahat, o = O.gn(A, X, Y, eps, omd, eps_relative=True, diag_iters=6)
+    ws = H.workspace(m, n, r, l, gn.F64)
+    AX = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float64, device="cuda")
+    F = torch.zeros(m, r, dtype=torch.float64, device="cuda")
+    G = torch.zeros(r, n, dtype=torch.float64, device="cuda")
+    core = _core_tensors(gn, r, l)
+    H.approx(cu(A), cu(X), cu(Y), eps, md | gn.EPS_RELATIVE, AX, YtA, core, F, G, ws)
+    assert H.sync_status() == 0
+    assert abs(core.eps_abs - o["eps_abs"]) <= 1e-10 * o["eps_abs"]
+    assert core.k == o["k"] and core.sgn == int(o["sgn"])
+    if kind == "wellcond":
+        assert abs(core.rinv_est - o["rinv_est"]) <= 1e-8 * o["rinv_est"]
+    else:
+        assert core.k == 70
+    k = core.k
+    assert rel(npy(F)[:, :k] @ npy(G)[:k], Ahat) <= 1e-9
