@@ -219,6 +219,33 @@ gn_status gn_error_fro2(gn_handle h, const gn_mat* A, const gn_mat* F, const gn_
 gn_status gn_error_fro2_noalloc(gn_handle h, const gn_mat* A, const gn_mat* F, const gn_mat* G,
                                 double* out);
 
+/* ------------------------------------------------ adjoint of A -> A_hat (plain GN) */
+
+/* Scratch bytes for gn_backward / gn_forward_dense on an m x n input with
+ * sketch sizes r, l in `dtype` (GN_F64 or GN_F32). */
+gn_status gn_backward_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t dtype,
+                                     size_t* bytes);
+
+/* Gradient of L(A) = <Gup, A_hat(A)> for plain GN (eq. 2.1 evaluated as in
+ * eq. 5.1) with X, Y held fixed, for a core Y^T A X of full column rank:
+ *   dA = (S1 Q R^{-T} + Y K) X^T + Y (Q S2),   S1 = Gup (Y^T A)^T,
+ *   F = (AX) R^{-1},  S2 = F^T Gup,  W = F^T S1,
+ *   K = (I - Q Q^T) W^T R^{-T} - Q (W Q) R^{-T},
+ * derived from d(C^+) = -C^+ dC C^+ + (C^T C)^{-1} dC^T (I - C C^+) (the
+ * paper does not differentiate GN).  The core's pseudoinverse is never formed.
+ * A, X, Y, Gup, dA share one dtype: GN_F64 (every step in FP64) or GN_F32
+ * (the m x n contractions in FP32, the r-sized algebra in FP64).  A: m x n,
+ * X: n x r, Y: m x (r+l), Gup, dA: m x n (dA overwritten).  The sketches are
+ * recomputed from A (nothing is kept from a forward pass). */
+gn_status gn_backward(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,
+                      const gn_mat* Gup, gn_mat* dA, void* ws, size_t ws_bytes);
+
+/* The dense approximant A_hat = F G (m x n) of plain GN in the dtype of A
+ * (GN_F64 or GN_F32, same precision split as gn_backward); the forward value
+ * of the differentiable map whose adjoint gn_backward computes. */
+gn_status gn_forward_dense(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,
+                           gn_mat* Ahat, void* ws, size_t ws_bytes);
+
 /* ---------------------------------------------------------------- Algorithm 1 */
 
 /* HMT range finder (Algorithm 1): AX, Householder QR AX = Q R_x, B = Q^T A.

@@ -36,7 +36,8 @@ ABI_SYMBOLS = (
     "gn_create", "gn_destroy", "gn_set_stream", "gn_sync_status", "gn_set_wait_limit",
     "gn_status_string", "gn_device_sm_count", "gn_workspace_size", "gn_quantize",
     "gn_sketch", "gn_core", "gn_factors", "gn_approx", "gn_error_fro2", "gn_hmt",
-    "gn_kernel_launches", "gn_error_fro2_noalloc",
+    "gn_kernel_launches", "gn_error_fro2_noalloc", "gn_backward_workspace_size", "gn_backward",
+    "gn_forward_dense",
 )
 
 
@@ -91,6 +92,9 @@ def _load():
         "gn_hmt": ([P, M, M, M, M, P, SZ], I32),
         "gn_kernel_launches": ([], ctypes.c_uint64),
         "gn_error_fro2_noalloc": ([P, M, M, M, P], I32),
+        "gn_backward_workspace_size": ([I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
+        "gn_backward": ([P, M, M, M, M, M, P, SZ], I32),
+        "gn_forward_dense": ([P, M, M, M, M, P, SZ], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -270,6 +274,58 @@ class Handle:
                                          ctypes.byref(mat(G)), ctypes.c_void_p(out.data_ptr())),
                "gn_error_fro2_noalloc")
 
+    # ------------------------------------------------------------ adjoint
+    def backward_workspace(self, m, n, r, l, dtype) -> torch.Tensor:
+        b = ctypes.c_size_t()
+        _check(lib.gn_backward_workspace_size(m, n, r, l, dtype, ctypes.byref(b)), "gn_backward_workspace_size")
+        return torch.empty(int(b.value), dtype=torch.uint8, device="cuda")
+
+    def backward(self, A, X, Y, Gup, dA, ws):
+        _check(lib.gn_backward(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
+                               ctypes.byref(mat(Gup)), ctypes.byref(mat(dA)), ctypes.c_void_p(ws.data_ptr()),
+                               ws.numel()), "gn_backward")
+
+    def forward_dense(self, A, X, Y, Ahat, ws):
+        _check(lib.gn_forward_dense(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
+                                    ctypes.byref(mat(Ahat)), ctypes.c_void_p(ws.data_ptr()), ws.numel()),
+               "gn_forward_dense")
+
     def hmt(self, A, X, Q, B, ws):
         _check(lib.gn_hmt(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Q)),
                           ctypes.byref(mat(B)), ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_hmt")
+
+
+_DT = {torch.float64: F64, torch.float32: F32}
+
+
+class GNApprox(torch.autograd.Function):
+    """A -> A_hat = (AX)(Y^T A X)^+(Y^T A) (plain GN) with X, Y fixed, as a
+    differentiable torch op.  forward: gn_forward_dense; backward: gn_backward
+    (the hand-written adjoint), which recomputes the sketches from A instead of
+    keeping them from the forward pass."""
+
+    @staticmethod
+    def forward(ctx, A, X, Y, handle):
+        m, n = A.shape
+        r, l = X.shape[1], Y.shape[1] - X.shape[1]
+        ws = handle.backward_workspace(m, n, r, l, _DT[A.dtype])
+        Ahat = torch.empty_like(A)
+        handle.forward_dense(A, X, Y, Ahat, ws)
+        ctx.save_for_backward(A, X, Y)
+        ctx.handle = handle
+        return Ahat
+
+    @staticmethod
+    def backward(ctx, grad):
+        A, X, Y = ctx.saved_tensors
+        m, n = A.shape
+        r, l = X.shape[1], Y.shape[1] - X.shape[1]
+        ws = ctx.handle.backward_workspace(m, n, r, l, _DT[A.dtype])
+        dA = torch.empty_like(A)
+        ctx.handle.backward(A, X, Y, grad.contiguous(), dA, ws)
+        return dA, None, None, None
+
+
+def gn_approx_dense(A, X, Y, handle):
+    """Differentiable plain-GN approximant of A (FP64 or FP32 CUDA tensors)."""
+    return GNApprox.apply(A, X, Y, handle)

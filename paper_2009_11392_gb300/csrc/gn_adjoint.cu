@@ -1,0 +1,408 @@
+// Adjoint of the generalized Nystrom map A -> A_hat (plain GN, full-rank core).
+//
+// For L(A) = <G, A_hat(A)> with X, Y fixed and C = Y^T A X = QR of full column
+// rank, differentiating A_hat = AX C^+ Y^T A (d(C^+) = -C^+ dC C^+ +
+// (C^T C)^{-1} dC^T (I - C C^+)) gives
+//
+//     dL/dA = (S1 Q R^{-T} + Y K) X^T + Y (Q S2),
+//     S1 = G (Y^T A)^T,  F = AX R^{-1},  S2 = F^T G,  W = F^T S1,
+//     K  = (I - Q Q^T) W^T R^{-T} - Q (W Q) R^{-T}.
+//
+// Every C^+ enters through Q and triangular solves with R (the paper's
+// Section 5.1 rule: never form the core's inverse).  The m x n contractions
+// (the sketches, S1, S2 and the two rank-r products that form the gradient)
+// run in FP64 for FP64 inputs and in FP32 on the CUDA cores for FP32 inputs;
+// the r-sized algebra (C, QR, W, K, the solves) is always FP64.  Sketches are
+// recomputed from A in every call (nothing is kept from a forward pass).
+#include "gn_internal.cuh"
+
+#include <algorithm>
+#include <string.h>
+
+namespace gn {
+namespace {
+
+// ---------------------------------------------------------------- FP32 GEMM
+constexpr int ST = 128;   // tile (M and N)
+constexpr int SK = 8;     // K step
+constexpr int STHREADS = 256;
+
+// C = alpha op(A) op(B) + beta C, FP32, 128 x 128 tiles, 256 threads as 16 x 16,
+// each an 8 x 8 block of outputs at rows ty + 16 i, columns tx + 16 j.
+__global__ void __launch_bounds__(STHREADS) sgemm_kernel(int M, int N, int K, float alpha,
+                                                        const float* __restrict__ A, long long lda, int ta,
+                                                        const float* __restrict__ B, long long ldb, int tb,
+                                                        float beta, float* C, long long ldc) {
+    __shared__ float As[SK][ST + 4];
+    __shared__ float Bs[SK][ST + 4];
+    const int m0 = blockIdx.y * ST, n0 = blockIdx.x * ST;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += SK) {
+#pragma unroll
+        for (int e = threadIdx.x; e < ST * SK; e += STHREADS) {
+            int mm, kk;
+            if (ta) { mm = e & (ST - 1); kk = e >> 7; } else { kk = e & (SK - 1); mm = e >> 3; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            float v = 0.f;
+            if (gm < M && gk < K)
+                v = ta ? A[static_cast<long long>(gk) * lda + gm] : A[static_cast<long long>(gm) * lda + gk];
+            As[kk][mm] = v;
+        }
+#pragma unroll
+        for (int e = threadIdx.x; e < ST * SK; e += STHREADS) {
+            int nn, kk;
+            if (tb) { kk = e & (SK - 1); nn = e >> 3; } else { nn = e & (ST - 1); kk = e >> 7; }
+            const int gn_ = n0 + nn, gk = k0 + kk;
+            float v = 0.f;
+            if (gn_ < N && gk < K)
+                v = tb ? B[static_cast<long long>(gn_) * ldb + gk] : B[static_cast<long long>(gk) * ldb + gn_];
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < SK; ++kk) {
+            float a[8], b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gm = m0 + ty + 16 * i, gn_ = n0 + tx + 16 * j;
+            if (gm < M && gn_ < N) {
+                float* c = C + static_cast<long long>(gm) * ldc + gn_;
+                *c = beta == 0.f ? alpha * acc[i][j] : fmaf(beta, *c, alpha * acc[i][j]);
+            }
+        }
+}
+
+gn_status sgemm(gn_handle h, long long M, long long N, long long K, float alpha, const float* A, long long lda,
+                int ta, const float* B, long long ldb, int tb, float beta, float* C, long long ldc) {
+    if (M <= 0 || N <= 0) return GN_OK;
+    dim3 grid(static_cast<unsigned>((N + ST - 1) / ST), static_cast<unsigned>((M + ST - 1) / ST));
+    sgemm_kernel<<<grid, STHREADS, 0, h->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, ta, B, ldb, tb, beta, C,
+                                                   ldc);
+    count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+__global__ void cvt_kernel_d2f(const double* __restrict__ s, long long rows, long long cols, long long lds, float* d,
+                               long long ldd, int transpose) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e % cols;
+        const float v = static_cast<float>(s[i * lds + j]);
+        if (transpose) d[j * ldd + i] = v; else d[i * ldd + j] = v;
+    }
+}
+
+__global__ void copy_t_kernel(const double* __restrict__ s, long long rows, long long cols, long long lds, double* d,
+                              long long ldd) {
+    // d (cols x rows) = s^T
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e % cols;
+        d[j * ldd + i] = s[i * lds + j];
+    }
+}
+
+int ew(gn_handle h, long long total) {
+    return static_cast<int>(std::max<long long>(1, std::min<long long>((total + 255) / 256, 8LL * h->sm_count)));
+}
+
+gn_status d2f(gn_handle h, const double* s, long long rows, long long cols, long long lds, float* d, long long ldd,
+              int transpose) {
+    if (rows * cols == 0) return GN_OK;
+    cvt_kernel_d2f<<<ew(h, rows * cols), 256, 0, h->stream>>>(s, rows, cols, lds, d, ldd, transpose);
+    count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+gn_status transpose_f64(gn_handle h, const double* s, long long rows, long long cols, long long lds, double* d,
+                        long long ldd) {
+    if (rows * cols == 0) return GN_OK;
+    copy_t_kernel<<<ew(h, rows * cols), 256, 0, h->stream>>>(s, rows, cols, lds, d, ldd);
+    count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+
+struct Bump {
+    char* base;
+    size_t cap, off;
+    bool ok;
+    template <typename T>
+    T* take(size_t n) {
+        const size_t b = align256(n * sizeof(T));
+        if (off + b > cap) {
+            ok = false;
+            return nullptr;
+        }
+        T* p = reinterpret_cast<T*>(base + off);
+        off += b;
+        return p;
+    }
+};
+
+// Scratch of the adjoint; the QR / GEMM scratch is the tail after these.
+size_t backward_fixed(long long m, long long n, long long r, long long l, int f32) {
+    const long long rl = r + l;
+    size_t b = 0;
+    b += align256(8 * m * r) * 3;     // AX (f64), F, P
+    b += align256(8 * rl * n) * 2;    // Y^T A (f64), Q' = Q S2
+    b += align256(8 * rl * r) * 5;    // C, W (QR copy), Q, K1, scratch
+    b += align256(8 * r * r) * 3;     // R, QtZ, WQ
+    b += align256(8 * m * rl);        // S1
+    b += align256(8 * r * n);         // S2
+    b += align256(8 * r * rl) * 2;    // W, W^T
+    if (f32) {
+        b += align256(4 * m * r) * 2 + align256(4 * rl * n) * 2 + align256(4 * m * rl) + align256(4 * r * n);
+        b += align256(4 * n * r) + align256(4 * m * rl);   // X^T? (unused) and Y copies
+    }
+    return b + 4096;
+}
+
+}  // namespace
+}  // namespace gn
+
+using namespace gn;
+
+extern "C" gn_status gn_backward_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t dtype,
+                                                size_t* bytes) {
+    if (!bytes) return GN_ERR_INVALID_ARG;
+    if (m <= 0 || n <= 0 || r < 1 || l < 1 || r > std::min(m, n) || r + l > m) return GN_ERR_SHAPE;
+    if (dtype != GN_F64 && dtype != GN_F32) return GN_ERR_DTYPE;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t inner = std::max({qr_ws_bytes(r + l, r, sms), dgemm_ws_bytes(r + l, r, n, sms),
+                                   dgemm_ws_bytes(r, r + l, m, sms), trsm_ws_bytes(m, r, sms),
+                                   dgemm_ws_bytes(m, r, r + l, sms)});
+    *bytes = backward_fixed(m, n, r, l, dtype == GN_F32) + inner;
+    return GN_OK;
+}
+
+extern "C" gn_status gn_backward(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, const gn_mat* Gup,
+                                 gn_mat* dA, void* ws, size_t ws_bytes) {
+    if (!h || !A || !X || !Y || !Gup || !dA || !ws) return GN_ERR_INVALID_ARG;
+    const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols, l = rl - r;
+    if (m <= 0 || n <= 0 || r < 1 || l < 1 || r > std::min(m, n) || rl > m) return GN_ERR_SHAPE;
+    const gn_mat* mats[5] = {A, X, Y, Gup, dA};
+    const long long shp[5][2] = {{m, n}, {n, r}, {m, rl}, {m, n}, {m, n}};
+    for (int i = 0; i < 5; ++i) {
+        if (!mats[i]->data) return GN_ERR_INVALID_ARG;
+        if (mats[i]->rows != shp[i][0] || mats[i]->cols != shp[i][1]) return GN_ERR_SHAPE;
+        if (mats[i]->ld < mats[i]->cols) return GN_ERR_INVALID_ARG;
+        if (mats[i]->dtype != A->dtype) return GN_ERR_DTYPE;
+    }
+    const int f32 = A->dtype == GN_F32;
+    if (!f32 && A->dtype != GN_F64) return GN_ERR_DTYPE;
+    size_t need = 0;
+    GN_TRY(gn_backward_workspace_size(m, n, r, l, A->dtype, &need));
+    if (ws_bytes < need) return GN_ERR_WORKSPACE;
+
+    Bump b{static_cast<char*>(ws), ws_bytes, 0, true};
+    double* AX = b.take<double>(m * r);
+    double* F = b.take<double>(m * r);
+    double* P = b.take<double>(m * r);
+    double* YtA = b.take<double>(rl * n);
+    double* Qp = b.take<double>(rl * n);
+    double* C = b.take<double>(rl * r);
+    double* Wq = b.take<double>(rl * r);
+    double* Q = b.take<double>(rl * r);
+    double* K1 = b.take<double>(rl * r);
+    double* Wt = b.take<double>(rl * r);
+    double* R = b.take<double>(r * r);
+    double* QtZ = b.take<double>(r * r);
+    double* WQ = b.take<double>(r * r);
+    double* S1 = b.take<double>(m * rl);
+    double* S2 = b.take<double>(r * n);
+    double* W = b.take<double>(r * rl);
+    float *AX32 = nullptr, *P32 = nullptr, *YtA32 = nullptr, *Qp32 = nullptr, *S1_32 = nullptr, *S2_32 = nullptr,
+          *F32 = nullptr;
+    if (f32) {
+        AX32 = b.take<float>(m * r);
+        P32 = b.take<float>(m * r);
+        YtA32 = b.take<float>(rl * n);
+        Qp32 = b.take<float>(rl * n);
+        S1_32 = b.take<float>(m * rl);
+        S2_32 = b.take<float>(r * n);
+        F32 = b.take<float>(m * r);
+    }
+    if (!b.ok) return GN_ERR_WORKSPACE;
+    const size_t o = align256(b.off);
+    double* inner = reinterpret_cast<double*>(static_cast<char*>(ws) + o);
+    const size_t inner_bytes = ws_bytes > o ? ws_bytes - o : 0;
+
+    // ---- sketches and the core (Algorithm 2 step 2)
+    if (f32) {
+        const float* A32 = static_cast<const float*>(A->data);
+        GN_TRY(sgemm(h, m, r, n, 1.f, A32, A->ld, 0, static_cast<const float*>(X->data), X->ld, 0, 0.f, AX32, r));
+        GN_TRY(sgemm(h, rl, n, m, 1.f, static_cast<const float*>(Y->data), Y->ld, 1, A32, A->ld, 0, 0.f, YtA32, n));
+        GN_TRY(copy_f32_to_f64(h, AX32, m, r, r, AX, r));
+        GN_TRY(copy_f32_to_f64(h, YtA32, rl, n, n, YtA, n));
+        // C from the FP32 sketch and the FP32 X, accumulated in FP64
+        GN_TRY(dgemm_b32(h, rl, r, n, 1.0, YtA, n, 0, static_cast<const float*>(X->data), X->ld, 0, 0.0, C, r,
+                         inner, inner_bytes));
+    } else {
+        const double* A64 = static_cast<const double*>(A->data);
+        GN_TRY(dgemm(h, m, r, n, 1.0, A64, A->ld, 0, static_cast<const double*>(X->data), X->ld, 0, 0.0, AX, r,
+                     inner, inner_bytes));
+        GN_TRY(dgemm(h, rl, n, m, 1.0, static_cast<const double*>(Y->data), Y->ld, 1, A64, A->ld, 0, 0.0, YtA, n,
+                     inner, inner_bytes));
+        GN_TRY(dgemm(h, rl, r, n, 1.0, YtA, n, 0, static_cast<const double*>(X->data), X->ld, 0, 0.0, C, r, inner,
+                     inner_bytes));
+    }
+    GN_CUDA_TRY(cudaMemcpyAsync(Wq, C, sizeof(double) * rl * r, cudaMemcpyDeviceToDevice, h->stream));
+    GN_TRY(householder_qr(h, Wq, rl, r, r, Q, r, R, r, inner, inner_bytes));
+    // F = AX R^{-1}
+    GN_CUDA_TRY(cudaMemcpyAsync(F, AX, sizeof(double) * m * r, cudaMemcpyDeviceToDevice, h->stream));
+    GN_TRY(trsm_right_upper(h, F, m, r, r, R, r, 0, inner, inner_bytes));
+
+    // ---- S1 = G (Y^T A)^T (m x (r+l)), S2 = F^T G (r x n): the two contractions over G
+    if (f32) {
+        const float* G32 = static_cast<const float*>(Gup->data);
+        GN_TRY(sgemm(h, m, rl, n, 1.f, G32, Gup->ld, 0, YtA32, n, 1, 0.f, S1_32, rl));
+        GN_TRY(d2f(h, F, m, r, r, F32, r, 0));
+        GN_TRY(sgemm(h, r, n, m, 1.f, F32, r, 1, G32, Gup->ld, 0, 0.f, S2_32, n));
+        GN_TRY(copy_f32_to_f64(h, S1_32, m, rl, rl, S1, rl));
+        GN_TRY(copy_f32_to_f64(h, S2_32, r, n, n, S2, n));
+    } else {
+        const double* G64 = static_cast<const double*>(Gup->data);
+        GN_TRY(dgemm(h, m, rl, n, 1.0, G64, Gup->ld, 0, YtA, n, 1, 0.0, S1, rl, inner, inner_bytes));
+        GN_TRY(dgemm(h, r, n, m, 1.0, F, r, 1, G64, Gup->ld, 0, 0.0, S2, n, inner, inner_bytes));
+    }
+    // ---- the r-sized core terms (FP64)
+    // W = F^T S1 (r x (r+l))
+    GN_TRY(dgemm(h, r, rl, m, 1.0, F, r, 1, S1, rl, 0, 0.0, W, rl, inner, inner_bytes));
+    // K1 = W^T R^{-T} ((r+l) x r)
+    GN_TRY(transpose_f64(h, W, r, rl, rl, K1, r));
+    GN_TRY(trsm_right_upper(h, K1, rl, r, r, R, r, 1, inner, inner_bytes));
+    // K1 -= Q (Q^T K1)
+    GN_TRY(dgemm(h, r, r, rl, 1.0, Q, r, 1, K1, r, 0, 0.0, QtZ, r, inner, inner_bytes));
+    GN_TRY(dgemm(h, rl, r, r, -1.0, Q, r, 0, QtZ, r, 0, 1.0, K1, r, inner, inner_bytes));
+    // WQ = (W Q) R^{-T};  K = K1 - Q WQ   (stored in K1)
+    GN_TRY(dgemm(h, r, r, rl, 1.0, W, rl, 0, Q, r, 0, 0.0, WQ, r, inner, inner_bytes));
+    GN_TRY(trsm_right_upper(h, WQ, r, r, r, R, r, 1, inner, inner_bytes));
+    GN_TRY(dgemm(h, rl, r, r, -1.0, Q, r, 0, WQ, r, 0, 1.0, K1, r, inner, inner_bytes));
+    // P = (S1 Q) R^{-T} + Y K  (m x r)
+    GN_TRY(dgemm(h, m, r, rl, 1.0, S1, rl, 0, Q, r, 0, 0.0, P, r, inner, inner_bytes));
+    GN_TRY(trsm_right_upper(h, P, m, r, r, R, r, 1, inner, inner_bytes));
+    if (f32) {
+        GN_TRY(dgemm_a32(h, m, r, rl, 1.0, static_cast<const float*>(Y->data), Y->ld, 0, K1, r, 0, 1.0, P, r, inner,
+                         inner_bytes));
+    } else {
+        GN_TRY(dgemm(h, m, r, rl, 1.0, static_cast<const double*>(Y->data), Y->ld, 0, K1, r, 0, 1.0, P, r, inner,
+                     inner_bytes));
+    }
+    // Q' = Q S2 ((r+l) x n)
+    GN_TRY(dgemm(h, rl, n, r, 1.0, Q, r, 0, S2, n, 0, 0.0, Qp, n, inner, inner_bytes));
+
+    // ---- dA = P X^T + Y Q'
+    if (f32) {
+        float* dA32 = static_cast<float*>(dA->data);
+        GN_TRY(d2f(h, P, m, r, r, P32, r, 0));
+        GN_TRY(d2f(h, Qp, rl, n, n, Qp32, n, 0));
+        GN_TRY(sgemm(h, m, n, r, 1.f, P32, r, 0, static_cast<const float*>(X->data), X->ld, 1, 0.f, dA32, dA->ld));
+        GN_TRY(sgemm(h, m, n, rl, 1.f, static_cast<const float*>(Y->data), Y->ld, 0, Qp32, n, 0, 1.f, dA32, dA->ld));
+    } else {
+        double* dA64 = static_cast<double*>(dA->data);
+        GN_TRY(dgemm(h, m, n, r, 1.0, P, r, 0, static_cast<const double*>(X->data), X->ld, 1, 0.0, dA64, dA->ld,
+                     inner, inner_bytes));
+        GN_TRY(dgemm(h, m, n, rl, 1.0, static_cast<const double*>(Y->data), Y->ld, 0, Qp, n, 0, 1.0, dA64, dA->ld,
+                     inner, inner_bytes));
+    }
+    return GN_OK;
+}
+
+// Forward value A_hat = F G of plain GN in the precision of A (for the autograd
+// wrapper): A_hat (m x n) from A, X, Y.
+extern "C" gn_status gn_forward_dense(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* Ahat,
+                                      void* ws, size_t ws_bytes) {
+    if (!h || !A || !X || !Y || !Ahat || !ws) return GN_ERR_INVALID_ARG;
+    const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols, l = rl - r;
+    if (m <= 0 || n <= 0 || r < 1 || l < 1 || r > std::min(m, n) || rl > m) return GN_ERR_SHAPE;
+    const gn_mat* mats[4] = {A, X, Y, Ahat};
+    const long long shp[4][2] = {{m, n}, {n, r}, {m, rl}, {m, n}};
+    for (int i = 0; i < 4; ++i) {
+        if (!mats[i]->data) return GN_ERR_INVALID_ARG;
+        if (mats[i]->rows != shp[i][0] || mats[i]->cols != shp[i][1]) return GN_ERR_SHAPE;
+        if (mats[i]->ld < mats[i]->cols) return GN_ERR_INVALID_ARG;
+        if (mats[i]->dtype != A->dtype) return GN_ERR_DTYPE;
+    }
+    const int f32 = A->dtype == GN_F32;
+    if (!f32 && A->dtype != GN_F64) return GN_ERR_DTYPE;
+    size_t need = 0;
+    GN_TRY(gn_backward_workspace_size(m, n, r, l, A->dtype, &need));
+    if (ws_bytes < need) return GN_ERR_WORKSPACE;
+    Bump b{static_cast<char*>(ws), ws_bytes, 0, true};
+    double* AX = b.take<double>(m * r);
+    double* F = b.take<double>(m * r);
+    double* Gf = b.take<double>(rl * n);   // G factor = Q^T (Y^T A), first r rows used
+    double* YtA = b.take<double>(rl * n);
+    double* C = b.take<double>(rl * r);
+    double* Wq = b.take<double>(rl * r);
+    double* Q = b.take<double>(rl * r);
+    double* R = b.take<double>(r * r);
+    float *AX32 = nullptr, *YtA32 = nullptr, *F32 = nullptr, *G32 = nullptr;
+    if (f32) {
+        AX32 = b.take<float>(m * r);
+        YtA32 = b.take<float>(rl * n);
+        F32 = b.take<float>(m * r);
+        G32 = b.take<float>(r * n);
+    }
+    if (!b.ok) return GN_ERR_WORKSPACE;
+    const size_t o = align256(b.off);
+    double* inner = reinterpret_cast<double*>(static_cast<char*>(ws) + o);
+    const size_t inner_bytes = ws_bytes > o ? ws_bytes - o : 0;
+    if (f32) {
+        const float* A32 = static_cast<const float*>(A->data);
+        GN_TRY(sgemm(h, m, r, n, 1.f, A32, A->ld, 0, static_cast<const float*>(X->data), X->ld, 0, 0.f, AX32, r));
+        GN_TRY(sgemm(h, rl, n, m, 1.f, static_cast<const float*>(Y->data), Y->ld, 1, A32, A->ld, 0, 0.f, YtA32, n));
+        GN_TRY(copy_f32_to_f64(h, AX32, m, r, r, AX, r));
+        GN_TRY(copy_f32_to_f64(h, YtA32, rl, n, n, YtA, n));
+        GN_TRY(dgemm_b32(h, rl, r, n, 1.0, YtA, n, 0, static_cast<const float*>(X->data), X->ld, 0, 0.0, C, r,
+                         inner, inner_bytes));
+    } else {
+        const double* A64 = static_cast<const double*>(A->data);
+        GN_TRY(dgemm(h, m, r, n, 1.0, A64, A->ld, 0, static_cast<const double*>(X->data), X->ld, 0, 0.0, AX, r,
+                     inner, inner_bytes));
+        GN_TRY(dgemm(h, rl, n, m, 1.0, static_cast<const double*>(Y->data), Y->ld, 1, A64, A->ld, 0, 0.0, YtA, n,
+                     inner, inner_bytes));
+        GN_TRY(dgemm(h, rl, r, n, 1.0, YtA, n, 0, static_cast<const double*>(X->data), X->ld, 0, 0.0, C, r, inner,
+                     inner_bytes));
+    }
+    GN_CUDA_TRY(cudaMemcpyAsync(Wq, C, sizeof(double) * rl * r, cudaMemcpyDeviceToDevice, h->stream));
+    GN_TRY(householder_qr(h, Wq, rl, r, r, Q, r, R, r, inner, inner_bytes));
+    GN_CUDA_TRY(cudaMemcpyAsync(F, AX, sizeof(double) * m * r, cudaMemcpyDeviceToDevice, h->stream));
+    GN_TRY(trsm_right_upper(h, F, m, r, r, R, r, 0, inner, inner_bytes));
+    GN_TRY(dgemm(h, r, n, rl, 1.0, Q, r, 1, YtA, n, 0, 0.0, Gf, n, inner, inner_bytes));
+    if (f32) {
+        GN_TRY(d2f(h, F, m, r, r, F32, r, 0));
+        GN_TRY(d2f(h, Gf, r, n, n, G32, n, 0));
+        GN_TRY(sgemm(h, m, n, r, 1.f, F32, r, 0, G32, n, 0, 0.f, static_cast<float*>(Ahat->data), Ahat->ld));
+    } else {
+        GN_TRY(dgemm(h, m, n, r, 1.0, F, r, 0, Gf, n, 0, 0.0, static_cast<double*>(Ahat->data), Ahat->ld, inner,
+                     inner_bytes));
+    }
+    return GN_OK;
+}

@@ -439,9 +439,9 @@ __device__ __forceinline__ double warp_sum(double s) {
 
 template <int JB>
 __host__ __device__ constexpr size_t cluster_panel_smem(int rows_per) {
-    // P + exchange slots [2][2+2JB] + tv[rows_per] + dsum/prow/w [3][JB] + gram, T [2][JB*JB]
-    return sizeof(double) * (static_cast<size_t>(rows_per) * (JB + 1) + 2 * (2 + 2 * JB) + rows_per +
-                             3 * JB + 2 * JB * JB);
+    // P + exchange slots [2][2+2JB] + tv[max(rows_per, 256)] + dsum/prow/w [3][JB] + gram, T [2][JB*JB]
+    return sizeof(double) * (static_cast<size_t>(rows_per) * (JB + 1) + 2 * (2 + 2 * JB) +
+                             (rows_per > 256 ? rows_per : 256) + 3 * JB + 2 * JB * JB);
 }
 
 // One exchange per column: with x = P[c:, c], alpha = x_0, beta = -sign(alpha)||x||
@@ -461,8 +461,8 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     constexpr int SLOT = 2 + 2 * JB;   // [tail, alpha, dots[JB], row_c[JB]]
     double* P = sm;
     double* xch = P + static_cast<size_t>(rows_per) * LDP;   // [2][SLOT]
-    double* tv = xch + 2 * SLOT;                             // [rows_per] tau * v_i
-    double* dsum = tv + rows_per;                            // [JB] x^T P_q summed over ranks
+    double* tv = xch + 2 * SLOT;                             // [max(rows_per, 256)] tau * v_i
+    double* dsum = tv + (rows_per > 256 ? rows_per : 256);   // [JB] x^T P_q summed over ranks
     double* prow = dsum + JB;                                // [JB] row c of the panel
     double* wv = prow + JB;                                  // [JB] w_q
     double* gram = wv + JB;                                  // [JB][JB] partial V^T V
@@ -480,41 +480,60 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     }
     __syncthreads();
 
+    // Thread tile for the per-column sums and updates: column lane j = tid % 32
+    // (panel column index), row chunk k = tid / 32 (rows lo + k, lo + k + 8, ...).
+    // On GB300 one SM retires ~2 FP64 operations per clock, so partial sums are
+    // formed per (chunk, column) and combined once, not by warp butterflies.
+    const int cj = lane, ck = warp;
     for (int c = 0; c < jb; ++c) {
         double* slot = xch + (c & 1) * SLOT;
         const int cl = c - r0;                       // local index of row c (owner iff 0 <= cl < nr)
         const bool owner = cl >= 0 && cl < nr;
         const int lo = max(0, cl);                   // first local row with panel row >= c
-        // ---- per-CTA partials
-        if (warp == 0) {
-            double sq = 0.0;
-            for (int li = max(0, cl + 1) + lane; li < nr; li += 32) {
-                const double x = P[li * LDP + c];
-                sq = fma(x, x, sq);
+        // ---- per-CTA partials: tail = sum_{rows > c} x_i^2 (column lane c),
+        //      dots_j = sum_{rows >= c} x_i P_ij (column lanes j > c)
+        {
+            double acc = 0.0;
+            if (cj == c) {
+                for (int li = max(0, cl + 1) + ck; li < nr; li += CP_WARPS) {
+                    const double x = P[li * LDP + c];
+                    acc = fma(x, x, acc);
+                }
+            } else if (cj > c && cj < jb) {
+                for (int li = lo + ck; li < nr; li += CP_WARPS) acc = fma(P[li * LDP + c], P[li * LDP + cj], acc);
             }
-            sq = warp_sum(sq);
-            if (lane == 0) {
-                slot[0] = sq;
-                slot[1] = owner ? P[cl * LDP + c] : 0.0;
-            }
+            tv[ck * 32 + cj] = acc;   // tv doubles as the 8 x 32 partial table here
         }
-        for (int q = c + 1 + warp; q < jb; q += CP_WARPS) {
-            double d = 0.0;
-            for (int li = lo + lane; li < nr; li += 32) d = fma(P[li * LDP + c], P[li * LDP + q], d);
-            d = warp_sum(d);
-            if (lane == 0) {
-                slot[2 + q] = d;
-                slot[2 + JB + q] = owner ? P[cl * LDP + q] : 0.0;
+        __syncthreads();
+        if (warp == 0) {
+            if (cj >= c && cj < jb) {
+                double t8 = 0.0;
+#pragma unroll
+                for (int k = 0; k < CP_WARPS; ++k) t8 += tv[k * 32 + cj];
+                if (cj == c) {
+                    slot[0] = t8;
+                    slot[1] = owner ? P[cl * LDP + c] : 0.0;
+                } else {
+                    slot[2 + cj] = t8;
+                    slot[2 + JB + cj] = owner ? P[cl * LDP + cj] : 0.0;
+                }
             }
         }
         cluster.sync();
-        // ---- combine (rank order, fixed butterflies: identical in every CTA)
-        if (warp == 0) {
-            const double pn = lane < cs ? cluster.map_shared_rank(slot, lane)[0] : 0.0;
-            const double pa = lane < cs ? cluster.map_shared_rank(slot, lane)[1] : 0.0;
-            const double tail = warp_sum(pn);
-            const double alpha = warp_sum(pa);
-            if (lane == 0) {
+        // ---- combine over ranks in rank order (the same sums in every CTA)
+        if (warp == 0 && cj >= c && cj < jb) {
+            double a0 = 0.0, a1 = 0.0;
+            const int o0 = cj == c ? 0 : 2 + cj, o1 = cj == c ? 1 : 2 + JB + cj;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if (k < cs) {
+                    const double* rs = cluster.map_shared_rank(slot, k);
+                    a0 += rs[o0];
+                    a1 += rs[o1];
+                }
+            }
+            if (cj == c) {
+                const double tail = a0, alpha = a1;
                 if (tail == 0.0) {
                     s_tau = 0.0;
                     s_beta = alpha;
@@ -526,29 +545,9 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
                     s_beta = beta;
                     s_scale = 1.0 / (alpha - beta);
                 }
-            }
-        }
-        {
-            const int half = lane >> 4, k = lane & 15;
-            const int iters = (jb - c - 1 + 2 * CP_WARPS - 1) / (2 * CP_WARPS);
-            for (int it = 0; it < iters; ++it) {
-                const int q = c + 1 + 2 * CP_WARPS * it + 2 * warp + half;
-                const bool live = q < jb;
-                double d = 0.0, pr = 0.0;
-                if (live && k < cs) {
-                    const double* rs = cluster.map_shared_rank(slot, k);
-                    d = rs[2 + q];
-                    pr = rs[2 + JB + q];
-                }
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) {
-                    d += __shfl_xor_sync(0xffffffffu, d, o);
-                    pr += __shfl_xor_sync(0xffffffffu, pr, o);
-                }
-                if (live && k == 0) {
-                    dsum[q] = d;
-                    prow[q] = pr;
-                }
+            } else {
+                dsum[cj] = a0;
+                prow[cj] = a1;
             }
         }
         __syncthreads();
@@ -560,7 +559,7 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
         }
         if (t != 0.0) {
             const double sc = s_scale, beta = s_beta;
-            // v_i = x_i / (alpha - beta) for rows below c; tv_i = tau v_i (v_c = 1)
+            // v_i = x_i / (alpha - beta) below row c, v_c = 1; tv_i = tau v_i
             for (int li = lo + tid; li < nr; li += CP_THREADS) {
                 double vi = 1.0;
                 if (li != cl) {
@@ -571,12 +570,9 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
             }
             if (tid > c && tid < jb) wv[tid] = fma(-beta, prow[tid], dsum[tid]) * sc;
             __syncthreads();
-            const int nq = jb - c - 1;
-            if (nq > 0) {
-                for (int li = lo + warp; li < nr; li += CP_WARPS) {
-                    const double tvi = tv[li];
-                    for (int q = c + 1 + lane; q < jb; q += 32) P[li * LDP + q] = fma(-tvi, wv[q], P[li * LDP + q]);
-                }
+            if (cj > c && cj < jb) {
+                const double wj = wv[cj];
+                for (int li = lo + ck; li < nr; li += CP_WARPS) P[li * LDP + cj] = fma(-tv[li], wj, P[li * LDP + cj]);
             }
         }
         __syncthreads();
@@ -609,8 +605,11 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
         for (int e = tid; e < jb * jb; e += CP_THREADS) {
             const int q = e / jb, q2 = e - q * jb;
             double g = 0.0;
-            if (q2 < q)
-                for (int k = 0; k < cs; ++k) g += cluster.map_shared_rank(gram, k)[q * JB + q2];
+            if (q2 < q) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k < cs) g += cluster.map_shared_rank(gram, k)[q * JB + q2];
+            }
             Ts[q * JB + q2] = g;   // the Gram in the strict lower triangle; zeros elsewhere
         }
         __syncthreads();
