@@ -456,9 +456,33 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
                         "err": None}
     out["fp64_path"]["err"] = err_of(AX64, YtA64, c64)
     out["norm_A_fro"] = normA
+    out["adjoint"] = adjoint_measurement(gn, H, stream, dev)
     out["err_floor_note"] = ("errors are ||A - F G||_F against the FP64 A; the bf16 path's floor is the "
                              "bf16 storage of A, split bf16 and FP64 reach the sketch error itself")
     return out
+
+
+def adjoint_measurement(gn, H, stream, dev, m=4096, n=4096, r=256, l=128):
+    """Forward (dense A_hat) and hand-written adjoint of <G, A_hat> on the
+    4096 x 4096 FP32 case (sigma_i = i^-1.5 over 1024 modes + 1e-6 noise,
+    r = 256, l = 128), each timed with CUDA events after one warm-up."""
+    p, G = gn_synth.config4(device=dev, m=m, n=n, r=r, l=l, dtype=torch.float32)
+    A, X, Y = p.a, p.x, p.y
+    ws = H.backward_workspace(m, n, r, l, gn.F32)
+    Ah = torch.empty_like(A)
+    dA = torch.empty_like(A)
+    H.forward_dense(A, X, Y, Ah, ws)
+    H.backward(A, X, Y, G, dA, ws)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    H.forward_dense(A, X, Y, Ah, ws)
+    e[1].record(stream)
+    H.backward(A, X, Y, G, dA, ws)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    return {"workload": f"{m}x{n} FP32, r={r}, l={l}, loss <G, A_hat>", "fwd_ms": e[0].elapsed_time(e[1]),
+            "bwd_ms": e[1].elapsed_time(e[2]), "grad_norm": float(dA.norm().item())}
 
 
 if __name__ == "__main__":

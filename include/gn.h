@@ -246,6 +246,43 @@ gn_status gn_backward(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_ma
 gn_status gn_forward_dense(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,
                            gn_mat* Ahat, void* ws, size_t ws_bytes);
 
+/* ---------------------------------------------------------------- batched */
+
+/* One problem of a batch (uneven m, n, r, l allowed).  Inputs GN_BF16 (ld a
+ * multiple of 8, 16-byte aligned); outputs AX, YtA GN_F32; core buffers FP64
+ * device arrays: Q (r+l) x r, R, Q2, R2 r x r (all ld r); k: device int32 that
+ * receives the truncation rank (r unless the truncated branch was taken).
+ * Limits of the shared-memory core: r <= 128 and r + l <= 192. */
+typedef struct {
+    gn_mat A, X, Y;
+    gn_mat AX, YtA;
+    double* Q;
+    double* R;
+    double* Q2;
+    double* R2;
+    int32_t* k;
+} gn_problem;
+
+/* Workspace bytes for a batch (tables, tensor maps, slices of Y^T A). */
+gn_status gn_batched_workspace_size(int32_t count, const gn_problem* probs, size_t* bytes);
+
+/* Build and upload the batch's descriptors (GEMM tiles, TMA tensor maps,
+ * per-problem scratch layout) into `ws`.  Synchronous; call once per batch
+ * layout (pointers and shapes), before any capture of gn_batched_run. */
+gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs, void* ws,
+                             size_t ws_bytes);
+
+/* Algorithm 2 step 2 and the Section 5.1 core for every prepared problem, in
+ * four launches on the handle's stream: one grouped tensor-core launch for
+ * all sketches AX, Y^T A (BF16, FP32 accumulation), one split of every Y^T A
+ * into three BF16 slices, one grouped launch for the slice products of every
+ * core C = (Y^T A) X, and one kernel with a CTA per problem (FP64 Householder
+ * QR and Q in shared memory, diag(R) >= 0, the Section 5.1.2 detector and
+ * Section 5.1.1 truncation per `mode` / `eps` exactly as gn_core, second QR
+ * into Q2, R2 when truncated).  No host synchronisation and no allocation;
+ * `ws` must be the workspace given to gn_batched_prepare. */
+gn_status gn_batched_run(gn_handle h, double eps, int32_t mode, void* ws, size_t ws_bytes);
+
 /* ---------------------------------------------------------------- Algorithm 1 */
 
 /* HMT range finder (Algorithm 1): AX, Householder QR AX = Q R_x, B = Q^T A.

@@ -37,13 +37,19 @@ ABI_SYMBOLS = (
     "gn_status_string", "gn_device_sm_count", "gn_workspace_size", "gn_quantize",
     "gn_sketch", "gn_core", "gn_factors", "gn_approx", "gn_error_fro2", "gn_hmt",
     "gn_kernel_launches", "gn_error_fro2_noalloc", "gn_backward_workspace_size", "gn_backward",
-    "gn_forward_dense",
+    "gn_forward_dense", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
 )
 
 
 class GnMat(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("rows", ctypes.c_int64),
                 ("cols", ctypes.c_int64), ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32)]
+
+
+class GnProblem(ctypes.Structure):
+    _fields_ = [("A", GnMat), ("X", GnMat), ("Y", GnMat), ("AX", GnMat), ("YtA", GnMat),
+                ("Q", ctypes.c_void_p), ("R", ctypes.c_void_p), ("Q2", ctypes.c_void_p),
+                ("R2", ctypes.c_void_p), ("k", ctypes.c_void_p)]
 
 
 class GnCoreT(ctypes.Structure):
@@ -95,6 +101,9 @@ def _load():
         "gn_backward_workspace_size": ([I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
         "gn_backward": ([P, M, M, M, M, M, P, SZ], I32),
         "gn_forward_dense": ([P, M, M, M, M, P, SZ], I32),
+        "gn_batched_workspace_size": ([I32, ctypes.POINTER(GnProblem), ctypes.POINTER(SZ)], I32),
+        "gn_batched_prepare": ([P, I32, ctypes.POINTER(GnProblem), P, SZ], I32),
+        "gn_batched_run": ([P, D, I32, P, SZ], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -289,6 +298,27 @@ class Handle:
         _check(lib.gn_forward_dense(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
                                     ctypes.byref(mat(Ahat)), ctypes.c_void_p(ws.data_ptr()), ws.numel()),
                "gn_forward_dense")
+
+    # ------------------------------------------------------------ batched
+    def batched_prepare(self, problems):
+        """problems: list of dicts with A, X, Y (bf16), AX, YtA (f32), Q, R, Q2, R2 (f64), k (int32[1]).
+        Returns the workspace tensor that gn_batched_run needs (keep it alive)."""
+        arr = (GnProblem * len(problems))()
+        for i, p in enumerate(problems):
+            arr[i] = GnProblem(mat(p["A"]), mat(p["X"]), mat(p["Y"]), mat(p["AX"]), mat(p["YtA"]),
+                               p["Q"].data_ptr(), p["R"].data_ptr(), p["Q2"].data_ptr(), p["R2"].data_ptr(),
+                               p["k"].data_ptr())
+        b = ctypes.c_size_t()
+        _check(lib.gn_batched_workspace_size(len(problems), arr, ctypes.byref(b)), "gn_batched_workspace_size")
+        ws = torch.empty(int(b.value), dtype=torch.uint8, device="cuda")
+        _check(lib.gn_batched_prepare(self._h, len(problems), arr, ctypes.c_void_p(ws.data_ptr()), ws.numel()),
+               "gn_batched_prepare")
+        self._batched_arr = arr
+        return ws
+
+    def batched_run(self, eps, mode, ws):
+        _check(lib.gn_batched_run(self._h, float(eps), int(mode), ctypes.c_void_p(ws.data_ptr()), ws.numel()),
+               "gn_batched_run")
 
     def hmt(self, A, X, Q, B, ws):
         _check(lib.gn_hmt(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Q)),

@@ -19,6 +19,9 @@ struct gn_handle_s {
     cudaEvent_t ev_fork, ev_join;
     int32_t* dstatus;          // device: [0] latched gn_status, [1] where
     uint64_t wait_limit_ns;
+    // batched path: the tables gn_batched_prepare uploaded into batched_ws
+    void* batched_ws;
+    int batched_count, batched_sk_tiles, batched_c_tiles;
 };
 
 #define GN_CUDA_TRY(expr)                                   \
@@ -63,6 +66,8 @@ struct TcGemm {
 struct TcParams {
     CUtensorMap maps[TC_MAX_MAPS];
     TcGemm g[TC_MAX_GEMMS];
+    const TcGemm* gg;          // grouped mode: descriptors in device memory
+    const CUtensorMap* gmaps;  // grouped mode: tensor maps in device memory (64-B aligned)
     int ngemm;
     int total_tiles;
     int32_t* status;
@@ -73,6 +78,12 @@ struct TcParams {
 gn_status tc_make_map_bf16(CUtensorMap* map, const void* base, long long rows, long long cols,
                            long long ld, int box_cols, int box_rows);
 gn_status tc_launch(gn_handle h, TcParams* p);
+// Fill tiles_m / tiles_n / kblocks / tile_base / vec4 of one GEMM descriptor.
+gn_status tc_prepare_gemm(TcGemm* G, int tile_base);
+// Grouped launch: descriptors (tile_base ascending) and tensor maps already in
+// device memory; any number of GEMMs.
+gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, const CUtensorMap* dev_maps,
+                            int total_tiles);
 
 // --------------------------------------------------------------------------
 // FP64 / FP32 helper kernels (gn_f64.cu)

@@ -161,13 +161,35 @@ struct TileCoord {
     int g, tm, tn;
 };
 
+// GEMM descriptors and tensor maps live in the kernel parameters (up to four
+// GEMMs) or, in grouped mode, in device memory (any number of GEMMs; the
+// batched path).  Tiles are numbered GEMM after GEMM (tile_base ascending).
+template <bool GROUPED>
+__device__ __forceinline__ const TcGemm* gemm_of(const TcParams& p, int i) {
+    return GROUPED ? p.gg + i : p.g + i;
+}
+template <bool GROUPED>
+__device__ __forceinline__ const CUtensorMap* map_of(const TcParams& p, int i) {
+    return GROUPED ? p.gmaps + i : p.maps + i;
+}
+
+template <bool GROUPED>
 __device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t) {
     TileCoord c;
-    c.g = 0;
+    if (GROUPED) {   // last GEMM whose tile_base <= t
+        int lo = 0, hi = p.ngemm - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.gg[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+        }
+        c.g = lo;
+    } else {
+        c.g = 0;
 #pragma unroll 1
-    for (int i = 1; i < p.ngemm; ++i)
-        if (t >= p.g[i].tile_base) c.g = i;
-    const TcGemm& G = p.g[c.g];
+        for (int i = 1; i < p.ngemm; ++i)
+            if (t >= p.g[i].tile_base) c.g = i;
+    }
+    const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
     const int local = t - G.tile_base;
     if (G.a_mn) {   // A operand is the small sketch (Y^T): walk M fastest so the big B is shared
         c.tm = local % G.tiles_m;
@@ -184,6 +206,7 @@ __device__ void latch(int32_t* status, int code, int where, volatile int* abort_
     if (atomicCAS(&status[GN_DEV_STATUS], 0, code) == 0) status[GN_DEV_WHERE] = where;
 }
 
+template <bool GROUPED>
 __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __grid_constant__ TcParams p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -236,8 +259,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             uint32_t last_parity = 0;            // parity of the last armed phase per stage
             bool ok = true;
             for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
-                const TileCoord c = decode_tile(p, t);
-                const TcGemm& G = p.g[c.g];
+                const TileCoord c = decode_tile<GROUPED>(p, t);
+                const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
                 const uint32_t bytes = A_STAGE_BYTES + G.bn * BK * 2;
                 for (int kb = 0; kb < nkb; ++kb) {
@@ -248,8 +271,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     }
                     const int src = kb / G.kblocks;
                     const int kk = kb - src * G.kblocks;
-                    const CUtensorMap* ma = &p.maps[G.a_map[src]];
-                    const CUtensorMap* mb = &p.maps[G.b_map[src]];
+                    const CUtensorMap* ma = map_of<GROUPED>(p, G.a_map[src]);
+                    const CUtensorMap* mb = map_of<GROUPED>(p, G.b_map[src]);
+                    if (GROUPED && kk == 0) {   // maps written to device memory before the launch
+                        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                         reinterpret_cast<uint64_t>(ma))
+                                     : "memory");
+                        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                         reinterpret_cast<uint64_t>(mb))
+                                     : "memory");
+                    }
                     const uint32_t sa = base + stage * STAGE_BYTES;
                     const uint32_t sb = sa + A_STAGE_BYTES;
                     const uint32_t fb = full_bar(stage);
@@ -292,8 +323,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             bool ok = true;
             bool issued_any = false;
             for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
-                const TileCoord c = decode_tile(p, t);
-                const TcGemm& G = p.g[c.g];
+                const TileCoord c = decode_tile<GROUPED>(p, t);
+                const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
                 const uint32_t idesc = instr_desc_bf16(BM, G.bn, G.a_mn, G.b_mn);
                 if (!mbar_wait(tempty_bar(acc), aphase ^ 1u, limit, abort_flag)) {
@@ -347,8 +378,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
         int acc = 0;
         uint32_t aphase = 0;
         for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
-            const TileCoord c = decode_tile(p, t);
-            const TcGemm& G = p.g[c.g];
+            const TileCoord c = decode_tile<GROUPED>(p, t);
+            const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
             const bool got = mbar_wait(tfull_bar(acc), aphase, limit, abort_flag);
             if (!__all_sync(0xffffffffu, got)) {   // warp-uniform exit: tcgen05.ld is .sync.aligned
                 if (lane == 0) latch(p.status, GN_ERR_TIMEOUT, 6, abort_flag);
@@ -435,27 +466,56 @@ gn_status tc_make_map_bf16(CUtensorMap* map, const void* base, long long rows, l
 gn_status tc_launch(gn_handle h, TcParams* p) {
     static bool attr_set = false;
     if (!attr_set) {
-        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel,
+        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
         attr_set = true;
     }
     int total = 0;
     for (int i = 0; i < p->ngemm; ++i) {
-        TcGemm& G = p->g[i];
-        if (G.bn < 16 || G.bn > 256 || (G.b_mn && G.bn % 64) || G.bn % 16) return GN_ERR_INVALID_ARG;
-        G.tiles_m = static_cast<int>((G.M + BM - 1) / BM);
-        G.tiles_n = static_cast<int>((G.N + G.bn - 1) / G.bn);
-        G.kblocks = static_cast<int>((G.K + BK - 1) / BK);
-        G.tile_base = total;
-        G.vec4 = ((reinterpret_cast<uintptr_t>(G.D) & 15) == 0 && G.ldd % 4 == 0) ? 1 : 0;
-        total += G.tiles_m * G.tiles_n;
+        GN_TRY(tc_prepare_gemm(&p->g[i], total));
+        total += p->g[i].tiles_m * p->g[i].tiles_n;
     }
     p->total_tiles = total;
+    p->gg = nullptr;
+    p->gmaps = nullptr;
     p->status = h->dstatus;
     p->wait_limit_ns = h->wait_limit_ns;
     if (total == 0) return GN_OK;
     const int grid = total < h->sm_count ? total : h->sm_count;
-    tc_multigemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, h->stream>>>(*p); count_launch();
+    tc_multigemm_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, h->stream>>>(*p); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+gn_status tc_prepare_gemm(TcGemm* G, int tile_base) {
+    if (G->bn < 16 || G->bn > 256 || (G->b_mn && G->bn % 64) || G->bn % 16) return GN_ERR_INVALID_ARG;
+    G->tiles_m = static_cast<int>((G->M + BM - 1) / BM);
+    G->tiles_n = static_cast<int>((G->N + G->bn - 1) / G->bn);
+    G->kblocks = static_cast<int>((G->K + BK - 1) / BK);
+    G->tile_base = tile_base;
+    G->vec4 = ((reinterpret_cast<uintptr_t>(G->D) & 15) == 0 && G->ldd % 4 == 0) ? 1 : 0;
+    return GN_OK;
+}
+
+gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, const CUtensorMap* dev_maps,
+                            int total_tiles) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        attr_set = true;
+    }
+    if (total_tiles <= 0 || ngemm <= 0) return GN_OK;
+    TcParams p;
+    memset(&p, 0, sizeof(p));
+    p.gg = dev_gemms;
+    p.gmaps = dev_maps;
+    p.ngemm = ngemm;
+    p.total_tiles = total_tiles;
+    p.status = h->dstatus;
+    p.wait_limit_ns = h->wait_limit_ns;
+    const int grid = total_tiles < h->sm_count ? total_tiles : h->sm_count;
+    tc_multigemm_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, h->stream>>>(p); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     return GN_OK;
 }

@@ -1,0 +1,102 @@
+"""Batched path (one grouped sketch launch, one grouped core-product launch and
+one CTA per core) against the unbatched C-ABI calls and the oracle, on
+problems of uneven m, n, r."""
+import numpy as np
+import pytest
+import torch
+
+import gn_synth
+from oracle import gn_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(300, 200, 16), (520, 390, 40), (257, 129, 24), (700, 640, 64), (1024, 512, 100), (333, 333, 128)]
+
+
+@pytest.fixture(scope="module")
+def gn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2009_11392_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def H(gn):
+    return gn.Handle()
+
+
+def _problem(gn, i, m, n, r, rankdef=False):
+    l = r // 2
+    rng = np.random.default_rng(100 + i)
+    if rankdef:   # exactly rank r/2 and exactly representable in bf16 (small integers)
+        k0 = r // 2
+        U = rng.integers(-2, 3, (m, k0)).astype(float)
+        V = rng.integers(-1, 2, (n, k0)).astype(float)
+        A = U @ V.T
+    else:
+        A = rng.standard_normal((m, n)) * (0.97 ** np.arange(n))[None, :]
+    X, Y = rng.standard_normal((n, r)), rng.standard_normal((m, r + l))
+    q = lambda a: torch.from_numpy(O.quantize_bf16(a))
+    dev = {}
+    for name, a in (("A", A), ("X", X), ("Y", Y)):
+        t = gn.padded(a.shape[0], a.shape[1], torch.bfloat16, "cuda")
+        t.copy_(q(a).to(torch.bfloat16))
+        dev[name] = t
+    f32 = lambda a, b: torch.full((a, b), float("nan"), dtype=torch.float32, device="cuda")
+    f64 = lambda a, b: torch.full((a, b), float("nan"), dtype=torch.float64, device="cuda")
+    dev.update(AX=f32(m, r), YtA=f32(r + l, n), Q=f64(r + l, r), R=f64(r, r), Q2=f64(r, r), R2=f64(r, r),
+               k=torch.full((1,), -1, dtype=torch.int32, device="cuda"))
+    return dev
+
+
+def test_batched_matches_unbatched_and_oracle(gn, H):
+    probs = [_problem(gn, i, *s) for i, s in enumerate(SHAPES)]
+    ws = H.batched_prepare(probs)
+    H.batched_run(0.0, gn.PLAIN, ws)
+    torch.cuda.synchronize()
+    assert H.sync_status() == 0
+    for (m, n, r), p in zip(SHAPES, probs):
+        l = r // 2
+        # unbatched path on the same operands
+        wsu = H.workspace(m, n, r, l, gn.BF16)
+        AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+        YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+        H.sketch(p["A"], p["X"], p["Y"], AX, YtA, wsu)
+        core = gn.Core.empty(r, l, "cuda")
+        H.core(YtA, p["X"], 0.0, gn.PLAIN, core, wsu)
+        torch.cuda.synchronize()
+        assert torch.equal(p["AX"], AX) and torch.equal(p["YtA"], YtA)
+        assert int(p["k"].item()) == r
+        C = core.C.cpu().numpy()
+        Qb, Rb = p["Q"].cpu().numpy(), p["R"].cpu().numpy()
+        # Householder QR of the same core: C = QR, Q^T Q = I, diag(R) >= 0, and the unbatched factors
+        assert np.linalg.norm(C - Qb @ Rb) <= 1e-13 * np.linalg.norm(C)
+        assert np.linalg.norm(Qb.T @ Qb - np.eye(r)) <= 1e-12
+        assert np.all(np.diag(Rb) >= 0) and np.allclose(Rb, np.triu(Rb))
+        kappa = np.linalg.cond(Rb)
+        assert np.linalg.norm(Rb - core.R.cpu().numpy()) <= 1e-13 * kappa * np.linalg.norm(Rb)
+        # and the oracle's QR of that core
+        oq, orr = O.householder_qr(C)
+        assert np.linalg.norm(Rb - orr) <= 1e-13 * kappa * np.linalg.norm(orr)
+
+
+def test_batched_truncation_branch(gn, H):
+    shapes = [(400, 300, 32), (600, 500, 64)]
+    probs = [_problem(gn, 10 + i, *s, rankdef=True) for i, s in enumerate(shapes)]
+    ws = H.batched_prepare(probs)
+    eps = 1e-4
+    H.batched_run(eps, gn.SGN | gn.EPS_RELATIVE, ws)
+    torch.cuda.synchronize()
+    assert H.sync_status() == 0
+    for (m, n, r), p in zip(shapes, probs):
+        l = r // 2
+        wsu = H.workspace(m, n, r, l, gn.BF16)
+        core = gn.Core.empty(r, l, "cuda")
+        H.core(p["YtA"], p["X"], eps, gn.SGN | gn.EPS_RELATIVE, core, wsu)
+        k = int(p["k"].item())
+        assert k == core.k == r // 2
+        Rb2, Ru2 = p["R2"].cpu().numpy()[:k, :k], core.R2.cpu().numpy()[:k, :k]
+        assert np.linalg.norm(Rb2 - Ru2) <= 1e-9 * np.linalg.norm(Ru2)
+        Qb2, Qu2 = p["Q2"].cpu().numpy()[:, :k], core.Q2.cpu().numpy()[:, :k]
+        assert np.linalg.norm(Qb2 - Qu2) <= 1e-9 * np.linalg.norm(Qu2)
