@@ -457,6 +457,7 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
     out["fp64_path"]["err"] = err_of(AX64, YtA64, c64)
     out["norm_A_fro"] = normA
     out["adjoint"] = adjoint_measurement(gn, H, stream, dev)
+    out["batched"] = batched_measurement(gn, H, stream, dev, steps=max(3, a.steps))
     out["err_floor_note"] = ("errors are ||A - F G||_F against the FP64 A; the bf16 path's floor is the "
                              "bf16 storage of A, split bf16 and FP64 reach the sketch error itself")
     return out
@@ -483,6 +484,51 @@ def adjoint_measurement(gn, H, stream, dev, m=4096, n=4096, r=256, l=128):
     torch.cuda.synchronize()
     return {"workload": f"{m}x{n} FP32, r={r}, l={l}, loss <G, A_hat>", "fwd_ms": e[0].elapsed_time(e[1]),
             "bwd_ms": e[1].elapsed_time(e[2]), "grad_norm": float(dA.norm().item())}
+
+
+def batched_measurement(gn, H, stream, dev, count=512, steps=10):
+    """512 problems, m ~ U[256,4096], n ~ U[128,m], r ~ U{16..128}, l = r/2, each
+    W1 diag(2^(-i/10)) W2^T + 1e-8 N with its own seed, BF16 operands; the four
+    launches of gn_batched_run captured once in a CUDA graph and replayed."""
+    shapes = gn_synth.batched_shapes(count)
+    probs = []
+    a_bytes = 0
+    flops = 0.0
+    for i, (m, n, r, l) in enumerate(shapes):
+        p = gn_synth.config5_problem(i, (m, n, r, l), device=dev)
+        d = {"A": H.quantize(p.a), "X": H.quantize(p.x), "Y": H.quantize(p.y)}
+        del p
+        d["AX"] = torch.empty(m, r, dtype=torch.float32, device=dev)
+        d["YtA"] = torch.empty(r + l, n, dtype=torch.float32, device=dev)
+        for nm, (a, b) in (("Q", (r + l, r)), ("R", (r, r)), ("Q2", (r, r)), ("R2", (r, r))):
+            d[nm] = torch.empty(a, b, dtype=torch.float64, device=dev)
+        d["k"] = torch.empty(1, dtype=torch.int32, device=dev)
+        probs.append(d)
+        a_bytes += 2 * m * n
+        flops += 2.0 * m * n * (2 * r + l)
+    ws = H.batched_prepare(probs)
+    eps, mode = 10 * 2.0 ** -24, gn.AUTO | gn.EPS_RELATIVE
+    H.batched_run(eps, mode, ws)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        H.batched_run(eps, mode, ws)
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = gn.kernel_launches()
+    e0.record(stream)
+    for _ in range(steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ks = [int(d["k"].item()) for d in probs]
+    peaks, _ = measured_peaks()
+    return {"workload": f"{count} problems, m~U[256,4096], n~U[128,m], r~U{{16..128}}, l=r/2, BF16, mode AUTO",
+            "approx_per_s": count * 1e3 / ms, "ms_per_batch": ms, "cuda_graph": True, "launches_per_batch": 4,
+            "a_bytes": a_bytes, "hbm_floor_ms": a_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3,
+            "sketch_flops": flops, "truncated": sum(1 for k, (m, n, r, l) in zip(ks, shapes) if k < r)}
 
 
 if __name__ == "__main__":

@@ -203,26 +203,63 @@ __device__ void smem_form_q(const Smem& sm, int M, int N) {
     }
 }
 
-// Triangular solves on R (N x N upper, global, ld) for the power method.
-// lower: R^T y = z (forward); else R w = z (backward).  z in shared memory.
-__device__ void smem_tri_solve(const double* R, int ld, int N, double* z, int lower) {
-    const int tid = threadIdx.x;
-    if (lower) {
-        for (int i = 0; i < N; ++i) {
-            if (tid == 0) z[i] = z[i] / R[i * ld + i];
-            __syncthreads();
-            const double yi = z[i];
-            for (int jj = i + 1 + tid; jj < N; jj += BT) z[jj] = fma(-R[i * ld + jj], yi, z[jj]);
-            __syncthreads();
+// Triangular solves on R (N x N upper, global, ld) for the power method,
+// lower: R^T y = z (forward); else R w = z (backward); z in shared memory.
+// 32 x 32 diagonal blocks are solved by warp 0 from a shared-memory copy with
+// reciprocal diagonals; the other rows are updated by the whole CTA.
+__device__ void smem_tri_solve(const double* R, int ld, int N, double* z, int lower, double* Rb /*[32*33]*/) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nb = (N + 31) / 32;
+    for (int bi = 0; bi < nb; ++bi) {
+        const int b = lower ? bi : nb - 1 - bi;
+        const int j0 = b * 32, jb = min(32, N - j0);
+        for (int e = tid; e < 32 * 32; e += BT) {
+            const int a = e >> 5, c = e & 31;
+            Rb[a * 33 + c] = (a < jb && c < jb) ? R[(j0 + a) * ld + j0 + c] : 0.0;
         }
-    } else {
-        for (int i = N - 1; i >= 0; --i) {
-            if (tid == 0) z[i] = z[i] / R[i * ld + i];
-            __syncthreads();
-            const double wi = z[i];
-            for (int jj = tid; jj < i; jj += BT) z[jj] = fma(-R[jj * ld + i], wi, z[jj]);
-            __syncthreads();
+        __syncthreads();
+        if (warp == 0) {
+            const double rd = lane < jb ? 1.0 / Rb[lane * 33 + lane] : 0.0;
+            double zl = lane < jb ? z[j0 + lane] : 0.0;
+            if (lower) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (i < jb) {
+                        const double yi = __shfl_sync(0xffffffffu, zl, i) * __shfl_sync(0xffffffffu, rd, i);
+                        if (lane == i) zl = yi;
+                        if (lane > i && lane < jb) zl = fma(-Rb[i * 33 + lane], yi, zl);
+                    }
+            } else {
+#pragma unroll
+                for (int i = 31; i >= 0; --i)
+                    if (i < jb) {
+                        const double wi = __shfl_sync(0xffffffffu, zl, i) * __shfl_sync(0xffffffffu, rd, i);
+                        if (lane == i) zl = wi;
+                        if (lane < i) zl = fma(-Rb[lane * 33 + i], wi, zl);
+                    }
+            }
+            if (lane < jb) z[j0 + lane] = zl;
         }
+        __syncthreads();
+        if (lower) {
+            for (int jj = j0 + jb + tid; jj < N; jj += BT) {
+                double a = z[jj];
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (i < jb) a = fma(-R[(j0 + i) * ld + jj], z[j0 + i], a);
+                z[jj] = a;
+            }
+        } else {
+            for (int i = tid; i < j0; i += BT) {
+                double a = z[i];
+                const double* rr = R + i * ld + j0;
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj)
+                    if (jj < jb) a = fma(-rr[jj], z[j0 + jj], a);
+                z[i] = a;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -238,9 +275,9 @@ __device__ double block_sum512(double s, double* red) {
     return t;
 }
 
-__global__ void __launch_bounds__(BT) batched_core_kernel(const ProblemDev* __restrict__ PP, double eps, int eps_rel,
-                                                         int mode) {
-    const ProblemDev& p = PP[blockIdx.x];
+__global__ void __launch_bounds__(BT) batched_core_kernel(const ProblemDev* __restrict__ PP, const int* __restrict__ order,
+                                                         double eps, int eps_rel, int mode) {
+    const ProblemDev& p = PP[order[blockIdx.x]];   // largest cores first (longest-processing-time order)
     extern __shared__ double shm[];
     const int N = p.r, M = p.r + p.l, tid = threadIdx.x;
     Smem sm;
@@ -333,8 +370,8 @@ __global__ void __launch_bounds__(BT) batched_core_kernel(const ProblemDev* __re
             for (int i = tid; i < N; i += BT) z[i] = inv;
             __syncthreads();
             for (int it = 0; it < DIAG_ITERS_B; ++it) {
-                smem_tri_solve(p.R, N, N, z, 1);
-                smem_tri_solve(p.R, N, N, z, 0);
+                smem_tri_solve(p.R, N, N, z, 1, sm.red);
+                smem_tri_solve(p.R, N, N, z, 0, sm.red);
                 double ss = 0.0;
                 for (int i = tid; i < N; i += BT) ss = fma(z[i], z[i], ss);
                 const double nw = sqrt(block_sum512(ss, sm.red));
@@ -406,6 +443,7 @@ gn_status gn_batched_workspace_size(int32_t count, const gn_problem* probs, size
     size_t b = 4096;
     b += al(sizeof(CUtensorMap) * 7 * count);
     b += al(sizeof(TcGemm) * 2 * count) + al(sizeof(TcGemm) * 3 * count) + al(sizeof(ProblemDev) * count);
+    b += al(sizeof(int) * count);
     for (int i = 0; i < count; ++i) {
         const long long n = probs[i].A.cols, r = probs[i].X.cols, rl = probs[i].Y.cols;
         b += 3 * al(sizeof(__nv_bfloat16) * rl * r8(n)) + 3 * al(sizeof(float) * rl * r) + al(8 * 4);
@@ -429,6 +467,8 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
     off += al(sizeof(TcGemm) * 3 * count);
     const size_t o_p = off;
     off += al(sizeof(ProblemDev) * count);
+    const size_t o_ord = off;
+    off += al(sizeof(int) * count);
 
     std::vector<CUtensorMap> maps(7 * static_cast<size_t>(count));
     std::vector<TcGemm> sk(2 * static_cast<size_t>(count)), cg(3 * static_cast<size_t>(count));
@@ -536,6 +576,15 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
     GN_CUDA_TRY(cudaMemcpy(base + o_sk, sk.data(), sizeof(TcGemm) * sk.size(), cudaMemcpyHostToDevice));
     GN_CUDA_TRY(cudaMemcpy(base + o_c, cg.data(), sizeof(TcGemm) * cg.size(), cudaMemcpyHostToDevice));
     GN_CUDA_TRY(cudaMemcpy(base + o_p, pd.data(), sizeof(ProblemDev) * pd.size(), cudaMemcpyHostToDevice));
+    // core kernel order: decreasing (r + l) r^2, the FP64 work of a core
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b2) {
+        const double wa = double(pd[a].r + pd[a].l) * pd[a].r * pd[a].r;
+        const double wb = double(pd[b2].r + pd[b2].l) * pd[b2].r * pd[b2].r;
+        return wa > wb;
+    });
+    GN_CUDA_TRY(cudaMemcpy(base + o_ord, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
     // keep the host-side counts in the header's host mirror (the run call re-reads them)
     h->batched_count = count;
     h->batched_sk_tiles = sk_tiles;
@@ -556,6 +605,7 @@ gn_status gn_batched_run(gn_handle h, double eps, int32_t mode, void* ws, size_t
     const size_t o_sk = o_maps + al(sizeof(CUtensorMap) * 7 * count);
     const size_t o_c = o_sk + al(sizeof(TcGemm) * 2 * count);
     const size_t o_p = o_c + al(sizeof(TcGemm) * 3 * count);
+    const size_t o_ord = o_p + al(sizeof(ProblemDev) * count);
     (void)ws_bytes;
     const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(base + o_maps);
     GN_TRY(tc_launch_grouped(h, reinterpret_cast<const TcGemm*>(base + o_sk), 2 * count, maps, h->batched_sk_tiles));
@@ -570,7 +620,8 @@ gn_status gn_batched_run(gn_handle h, double eps, int32_t mode, void* ws, size_t
                                          static_cast<int>(core_smem_bytes())));
         attr = true;
     }
-    batched_core_kernel<<<count, BT, core_smem_bytes(), h->stream>>>(pd, eps, eps_rel, mode);
+    batched_core_kernel<<<count, BT, core_smem_bytes(), h->stream>>>(
+        pd, reinterpret_cast<const int*>(base + o_ord), eps, eps_rel, mode);
     count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     return GN_OK;

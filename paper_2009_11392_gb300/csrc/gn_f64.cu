@@ -520,18 +520,27 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
             }
         }
         cluster.sync();
-        // ---- combine over ranks in rank order (the same sums in every CTA)
-        if (warp == 0 && cj >= c && cj < jb) {
+        // ---- combine over ranks (the same order in every CTA): warps 0-3 each sum
+        //      four ranks' partials for every column, warp 0 adds the four sums
+        if (warp < 4 && cj >= c && cj < jb) {
             double a0 = 0.0, a1 = 0.0;
             const int o0 = cj == c ? 0 : 2 + cj, o1 = cj == c ? 1 : 2 + JB + cj;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
+            for (int kk = 0; kk < 4; ++kk) {
+                const int k = 4 * warp + kk;
                 if (k < cs) {
                     const double* rs = cluster.map_shared_rank(slot, k);
                     a0 += rs[o0];
                     a1 += rs[o1];
                 }
             }
+            tv[warp * 64 + cj] = a0;        // tv is free here: 4 x 2 x 32 partial sums
+            tv[warp * 64 + 32 + cj] = a1;
+        }
+        __syncthreads();
+        if (warp == 0 && cj >= c && cj < jb) {
+            const double a0 = (tv[cj] + tv[64 + cj]) + (tv[128 + cj] + tv[192 + cj]);
+            const double a1 = (tv[32 + cj] + tv[96 + cj]) + (tv[160 + cj] + tv[224 + cj]);
             if (cj == c) {
                 const double tail = a0, alpha = a1;
                 if (tail == 0.0) {
@@ -541,9 +550,12 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
                 } else {
                     const double nx = sqrt(fma(alpha, alpha, tail));
                     const double beta = alpha >= 0.0 ? -nx : nx;
-                    s_tau = (beta - alpha) / beta;
+                    // one division: d = 1 / (beta (alpha - beta)) gives both 1/beta and 1/(alpha - beta)
+                    const double amb = alpha - beta;
+                    const double d = 1.0 / (beta * amb);
+                    s_tau = (beta - alpha) * (amb * d);
                     s_beta = beta;
-                    s_scale = 1.0 / (alpha - beta);
+                    s_scale = beta * d;
                 }
             } else {
                 dsum[cj] = a0;
