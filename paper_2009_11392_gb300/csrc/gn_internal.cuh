@@ -79,7 +79,7 @@ gn_status tc_make_map_bf16(CUtensorMap* map, const void* base, long long rows, l
                            long long ld, int box_cols, int box_rows);
 gn_status tc_launch(gn_handle h, TcParams* p);
 // Fill tiles_m / tiles_n / kblocks / tile_base / vec4 of one GEMM descriptor.
-gn_status tc_prepare_gemm(TcGemm* G, int tile_base);
+gn_status tc_prepare_gemm(TcGemm* G, int tile_base, int mt = 1);
 // Grouped launch: descriptors (tile_base ascending) and tensor maps already in
 // device memory; any number of GEMMs.
 gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, const CUtensorMap* dev_maps,

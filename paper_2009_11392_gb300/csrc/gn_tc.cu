@@ -27,16 +27,27 @@
 namespace gn {
 namespace {
 
-constexpr int BM = 128;                          // M tile (tcgen05 M)
+constexpr int BM = 128;                          // M of one tcgen05 MMA
 constexpr int BK = 64;                           // K per stage: 64 bf16 = one 128B swizzle row
-constexpr int STAGES = 4;
-constexpr int A_STAGE_BYTES = BM * BK * 2;       // 16 KB
 constexpr int B_STAGE_BYTES = 256 * BK * 2;      // 32 KB (bn <= 256)
-constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
-constexpr int ACC_COLS = 256;
 constexpr int TMEM_COLS = 512;
 constexpr int NUM_THREADS = 192;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+// MT = number of 128-row M halves per tile.  MT = 1: 128 x bn tiles, 4 stages of
+// 48 KB, two TMEM accumulator buffers (the epilogue of a tile overlaps the next
+// main loop).  MT = 2: 256 x bn tiles whose two MMAs share each B stage (a third
+// fewer operand bytes per flop), 3 stages of 64 KB, one accumulator buffer of
+// 2 x 256 columns.
+template <int MT>
+struct Cfg {
+    static constexpr int STG = MT == 2 ? 3 : 4;
+    static constexpr int A_BYTES = MT * BM * BK * 2;
+    static constexpr int STAGE = A_BYTES + B_STAGE_BYTES;
+    static constexpr int NACC = MT == 2 ? 1 : 2;
+    static constexpr int TM = BM * MT;
+    static constexpr int SMEM = STG * STAGE + 1024 + 256;
+};
+constexpr int SMEM_BYTES = Cfg<1>::SMEM > Cfg<2>::SMEM ? Cfg<1>::SMEM : Cfg<2>::SMEM;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -96,6 +107,27 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// Multicast variant: the box lands at the same shared-memory offset in every CTA
+// of `mask` (cluster ranks) and completes bytes on each CTA's barrier at `bar`'s offset.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -106,6 +138,16 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+// Arrive (once the prior MMAs complete) on the barrier at `bar`'s offset in every
+// CTA of `mask`.
+__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(mask)
         : "memory");
 }
 
@@ -173,8 +215,9 @@ __device__ __forceinline__ const CUtensorMap* map_of(const TcParams& p, int i) {
     return GROUPED ? p.gmaps + i : p.maps + i;
 }
 
-template <bool GROUPED>
-__device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t) {
+template <bool GROUPED, int CL>
+__device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t, int crank) {
+    // tiles_m / tiles_n / tile_base are in units of this launch's tile shape
     TileCoord c;
     if (GROUPED) {   // last GEMM whose tile_base <= t
         int lo = 0, hi = p.ngemm - 1;
@@ -191,13 +234,16 @@ __device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t) {
     }
     const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
     const int local = t - G.tile_base;
+    const int ctm_n = (G.tiles_m + CL - 1) / CL;   // cluster tiles along M
+    int ctm;
     if (G.a_mn) {   // A operand is the small sketch (Y^T): walk M fastest so the big B is shared
-        c.tm = local % G.tiles_m;
-        c.tn = local / G.tiles_m;
+        ctm = local % ctm_n;
+        c.tn = local / ctm_n;
     } else {        // walk N fastest so the big A row panel is shared
-        c.tm = local / G.tiles_n;
+        ctm = local / G.tiles_n;
         c.tn = local % G.tiles_n;
     }
+    c.tm = ctm * CL + crank;   // the CL CTAs of a cluster take consecutive M tiles of one N tile
     return c;
 }
 
@@ -206,8 +252,16 @@ __device__ void latch(int32_t* status, int code, int where, volatile int* abort_
     if (atomicCAS(&status[GN_DEV_STATUS], 0, code) == 0) status[GN_DEV_WHERE] = where;
 }
 
-template <bool GROUPED>
+// CL > 1: thread-block clusters of CL CTAs along M; the B tile (shared by the
+// CL M tiles of one N tile) is split into 64-column boxes, each loaded by one
+// CTA and multicast to all CL; a stage is refilled only after every CTA of the
+// cluster has consumed it (each MMA commit arrives on all CL empty barriers).
+template <bool GROUPED, int CL, int MT>
 __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __grid_constant__ TcParams p) {
+    using K = Cfg<MT>;
+    constexpr int STAGES = K::STG;
+    constexpr int STAGE_BYTES = K::STAGE;
+    constexpr int A_STAGE_BYTES = K::A_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;            // 1024-aligned stage ring
@@ -228,9 +282,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full_bar(s), 1);
-            mbar_init(empty_bar(s), 1);
+            mbar_init(empty_bar(s), CL);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < K::NACC; ++a) {
             mbar_init(tfull_bar(a), 1);
             mbar_init(tempty_bar(a), 128);
         }
@@ -247,8 +301,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
     }
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    const int crank = CL > 1 ? static_cast<int>(cluster_rank()) : 0;
+    const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+    const uint16_t cmask = static_cast<uint16_t>((1u << CL) - 1u);
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
@@ -258,8 +316,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             uint32_t issued_mask = 0;            // stages that ever received a load
             uint32_t last_parity = 0;            // parity of the last armed phase per stage
             bool ok = true;
-            for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
-                const TileCoord c = decode_tile<GROUPED>(p, t);
+            for (int t = cid; t < p.total_tiles && ok; t += ncl) {
+                const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
                 const uint32_t bytes = A_STAGE_BYTES + G.bn * BK * 2;
@@ -287,13 +345,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     mbar_arrive_expect_tx(fb, bytes);
                     issued_mask |= 1u << stage;
                     last_parity = (last_parity & ~(1u << stage)) | (ephase << stage);
-                    if (G.a_mn) {
-                        tma_load_2d(sa, ma, fb, c.tm * BM, kk * BK);
-                        tma_load_2d(sa + 8192, ma, fb, c.tm * BM + 64, kk * BK);
-                    } else {
-                        tma_load_2d(sa, ma, fb, kk * BK, c.tm * BM);
+#pragma unroll
+                    for (int hh = 0; hh < MT; ++hh) {
+                        const int m0 = c.tm * K::TM + hh * BM;
+                        if (G.a_mn) {
+                            tma_load_2d(sa + hh * 16384, ma, fb, m0, kk * BK);
+                            tma_load_2d(sa + hh * 16384 + 8192, ma, fb, m0 + 64, kk * BK);
+                        } else {
+                            tma_load_2d(sa + hh * 16384, ma, fb, kk * BK, m0);
+                        }
                     }
-                    if (G.b_mn) {
+                    if (CL > 1) {   // B boxes: box j from cluster rank j % CL, multicast to all
+                        if (G.b_mn) {
+                            for (int j = crank; j < G.bn / 64; j += CL)
+                                tma_load_2d_mc(sb + 8192 * j, mb, fb, c.tn * G.bn + 64 * j, kk * BK, cmask);
+                        } else if (crank == 0) {
+                            tma_load_2d_mc(sb, mb, fb, kk * BK, c.tn * G.bn, cmask);
+                        }
+                    } else if (G.b_mn) {
                         for (int j = 0; j < G.bn / 64; ++j)
                             tma_load_2d(sb + 8192 * j, mb, fb, c.tn * G.bn + 64 * j, kk * BK);
                     } else {
@@ -322,8 +391,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             uint32_t aphase = 0;
             bool ok = true;
             bool issued_any = false;
-            for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
-                const TileCoord c = decode_tile<GROUPED>(p, t);
+            for (int t = cid; t < p.total_tiles && ok; t += ncl) {
+                const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
                 const uint32_t idesc = instr_desc_bf16(BM, G.bn, G.a_mn, G.b_mn);
@@ -332,7 +401,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
+                const uint32_t d_tmem = tmem_base + acc * MT * 256;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(full_bar(stage), fphase, limit, abort_flag)) {
                         latch(p.status, GN_ERR_TIMEOUT, 4, abort_flag);
@@ -344,14 +413,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     const uint32_t sb = sa + A_STAGE_BYTES;
 #pragma unroll
                     for (int k = 0; k < BK / 16; ++k) {
-                        const uint64_t ad = G.a_mn ? smem_desc(sa + 2048u * k, 8192u, 1024u)
-                                                   : smem_desc(sa + 32u * k, 16u, 1024u);
                         const uint64_t bd = G.b_mn ? smem_desc(sb + 2048u * k, 8192u, 1024u)
                                                    : smem_desc(sb + 32u * k, 16u, 1024u);
-                        tc_mma_bf16(d_tmem, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+#pragma unroll
+                        for (int hh = 0; hh < MT; ++hh) {
+                            const uint32_t sah = sa + 16384u * hh;
+                            const uint64_t ad = G.a_mn ? smem_desc(sah + 2048u * k, 8192u, 1024u)
+                                                       : smem_desc(sah + 32u * k, 16u, 1024u);
+                            tc_mma_bf16(d_tmem + 256u * hh, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                        }
                     }
                     issued_any = true;
-                    tc_commit(empty_bar(stage));
+                    if (CL > 1) tc_commit_mc(empty_bar(stage), cmask); else tc_commit(empty_bar(stage));
                     if (++stage == STAGES) {
                         stage = 0;
                         fphase ^= 1u;
@@ -359,7 +432,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                 }
                 if (!ok) break;
                 tc_commit(tfull_bar(acc));
-                if (++acc == 2) {
+                if (++acc == K::NACC) {
                     acc = 0;
                     aphase ^= 1u;
                 }
@@ -377,8 +450,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
         const int q = warp & 3;   // TMEM lane quarter this warp may access
         int acc = 0;
         uint32_t aphase = 0;
-        for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
-            const TileCoord c = decode_tile<GROUPED>(p, t);
+        for (int t = cid; t < p.total_tiles; t += ncl) {
+            const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
             const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
             const bool got = mbar_wait(tfull_bar(acc), aphase, limit, abort_flag);
             if (!__all_sync(0xffffffffu, got)) {   // warp-uniform exit: tcgen05.ld is .sync.aligned
@@ -386,30 +459,32 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                 break;
             }
             tc_fence_after();
-            const int row = c.tm * BM + q * 32 + lane;
-            const bool row_ok = row < G.M;
-            float* drow = G.D + static_cast<long long>(row_ok ? row : 0) * G.ldd;
-            for (int c0 = 0; c0 < G.bn; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + acc * ACC_COLS + c0, v);
-                const int col0 = c.tn * G.bn + c0;
-                if (!row_ok || col0 >= G.N) continue;
-                if (G.vec4 && col0 + 32 <= G.N) {
-                    float4* dst = reinterpret_cast<float4*>(drow + col0);
+#pragma unroll 1
+            for (int hh = 0; hh < MT; ++hh) {
+                const int row = c.tm * K::TM + hh * BM + q * 32 + lane;
+                const bool row_ok = row < G.M;
+                float* drow = G.D + static_cast<long long>(row_ok ? row : 0) * G.ldd;
+                for (int c0 = 0; c0 < G.bn; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + (acc * MT + hh) * 256 + c0, v);
+                    const int col0 = c.tn * G.bn + c0;
+                    if (!row_ok || col0 >= G.N) continue;
+                    if (G.vec4 && col0 + 32 <= G.N) {
+                        float4* dst = reinterpret_cast<float4*>(drow + col0);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                             __uint_as_float(v[4 * j + 2]),
-                                             __uint_as_float(v[4 * j + 3]));
-                } else {
+                        for (int j = 0; j < 8; ++j)
+                            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+                    } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (col0 + j < G.N) drow[col0 + j] = __uint_as_float(v[j]);
+                        for (int j = 0; j < 32; ++j)
+                            if (col0 + j < G.N) drow[col0 + j] = __uint_as_float(v[j]);
+                    }
                 }
             }
             tc_fence_before();
             mbar_arrive(tempty_bar(acc));
-            if (++acc == 2) {
+            if (++acc == K::NACC) {
                 acc = 0;
                 aphase ^= 1u;
             }
@@ -418,6 +493,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
 
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync_all();   // no CTA leaves while peers may still write its barriers
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -463,17 +539,60 @@ gn_status tc_make_map_bf16(CUtensorMap* map, const void* base, long long rows, l
     return r == CUDA_SUCCESS ? GN_OK : GN_ERR_CUDA;
 }
 
-gn_status tc_launch(gn_handle h, TcParams* p) {
+template <bool GROUPED, int CL, int MT>
+gn_status launch_cfg(gn_handle h, const TcParams& p, int total_ctiles) {
     static bool attr_set = false;
     if (!attr_set) {
-        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel<GROUPED, CL, MT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MT>::SMEM));
         attr_set = true;
     }
+    const int max_clusters = h->sm_count / CL;
+    const int clusters = total_ctiles < max_clusters ? total_ctiles : max_clusters;
+    if (CL == 1) {
+        tc_multigemm_kernel<GROUPED, CL, MT><<<clusters, NUM_THREADS, Cfg<MT>::SMEM, h->stream>>>(p);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(clusters * CL);
+        cfg.blockDim = dim3(NUM_THREADS);
+        cfg.dynamicSmemBytes = Cfg<MT>::SMEM;
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_multigemm_kernel<GROUPED, CL, MT>, p));
+    }
+    count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+// Tile shape: 256-row tiles (two MMAs sharing each B stage) when every GEMM has
+// at least 256 rows, else 128-row tiles.  B multicast across a 4-CTA cluster
+// (CL = 4) is implemented but not selected: measured slower, the lockstep of the
+// cluster costs more than the L2 traffic it saves.
+int pick_mt(const TcGemm* g, int ngemm, int sm_count) {
+    long long tiles2 = 0;
+    for (int i = 0; i < ngemm; ++i) {
+        if (g[i].M < 2 * BM) return 1;
+        tiles2 += ((g[i].M + 2 * BM - 1) / (2 * BM)) * ((g[i].N + g[i].bn - 1) / g[i].bn);
+    }
+    return tiles2 >= 4LL * sm_count ? 2 : 1;   // keep enough tiles to fill the GPU
+}
+
+gn_status tc_launch(gn_handle h, TcParams* p) {
+    const int MT = pick_mt(p->g, p->ngemm, h->sm_count);
+    for (int i = 0; i < p->ngemm; ++i) GN_TRY(tc_prepare_gemm(&p->g[i], 0, MT));
+    const int CL = 1;
     int total = 0;
     for (int i = 0; i < p->ngemm; ++i) {
-        GN_TRY(tc_prepare_gemm(&p->g[i], total));
-        total += p->g[i].tiles_m * p->g[i].tiles_n;
+        TcGemm& G = p->g[i];
+        G.tile_base = total;
+        total += ((G.tiles_m + CL - 1) / CL) * G.tiles_n;
     }
     p->total_tiles = total;
     p->gg = nullptr;
@@ -481,15 +600,12 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
     p->status = h->dstatus;
     p->wait_limit_ns = h->wait_limit_ns;
     if (total == 0) return GN_OK;
-    const int grid = total < h->sm_count ? total : h->sm_count;
-    tc_multigemm_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, h->stream>>>(*p); count_launch();
-    GN_CUDA_TRY(cudaGetLastError());
-    return GN_OK;
+    return MT == 2 ? launch_cfg<false, 1, 2>(h, *p, total) : launch_cfg<false, 1, 1>(h, *p, total);
 }
 
-gn_status tc_prepare_gemm(TcGemm* G, int tile_base) {
+gn_status tc_prepare_gemm(TcGemm* G, int tile_base, int mt) {
     if (G->bn < 16 || G->bn > 256 || (G->b_mn && G->bn % 64) || G->bn % 16) return GN_ERR_INVALID_ARG;
-    G->tiles_m = static_cast<int>((G->M + BM - 1) / BM);
+    G->tiles_m = static_cast<int>((G->M + BM * mt - 1) / (BM * mt));
     G->tiles_n = static_cast<int>((G->N + G->bn - 1) / G->bn);
     G->kblocks = static_cast<int>((G->K + BK - 1) / BK);
     G->tile_base = tile_base;
@@ -499,12 +615,6 @@ gn_status tc_prepare_gemm(TcGemm* G, int tile_base) {
 
 gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, const CUtensorMap* dev_maps,
                             int total_tiles) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-        attr_set = true;
-    }
     if (total_tiles <= 0 || ngemm <= 0) return GN_OK;
     TcParams p;
     memset(&p, 0, sizeof(p));
@@ -514,10 +624,7 @@ gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, con
     p.total_tiles = total_tiles;
     p.status = h->dstatus;
     p.wait_limit_ns = h->wait_limit_ns;
-    const int grid = total_tiles < h->sm_count ? total_tiles : h->sm_count;
-    tc_multigemm_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, h->stream>>>(p); count_launch();
-    GN_CUDA_TRY(cudaGetLastError());
-    return GN_OK;
+    return launch_cfg<true, 1, 1>(h, p, total_tiles);
 }
 
 }  // namespace gn
