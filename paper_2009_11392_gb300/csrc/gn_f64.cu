@@ -645,6 +645,121 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     cluster.sync();
 }
 
+// ---------------------------------------------------------------------------
+// Compact-WY application W <- W - V op(T) (V^T W) for one panel, in one launch:
+// clusters of CS CTAs, one cluster per 64-column block of W, each CTA owning a
+// slice of rows (its rows of V and of the W block stay in shared memory for
+// both products).  Z = V^T W_blk is reduced over the cluster through DSMEM
+// (reduce-scatter by rows, all-gather), each CTA forms its share of
+// op(T) Z, and the shares are gathered again.  op(T) = T^T for the trailing
+// update of the factorization, T for the formation of Q.
+// ---------------------------------------------------------------------------
+constexpr int WY_THREADS = 256;
+constexpr int WY_BN = 64;
+constexpr int WY_JB = 32;
+constexpr int WY_MAX_ROWS = 188;   // rows per CTA that fit in shared memory
+
+__host__ __device__ inline size_t wy_smem(int rp) {
+    return sizeof(double) * (static_cast<size_t>(rp) * (WY_JB + 1 + WY_BN + 1) + 3 * WY_JB * WY_BN + WY_JB * WY_JB);
+}
+
+__global__ void __launch_bounds__(WY_THREADS) qr_wy_apply_kernel(double* W, long long ldw, int Mp, int Nw,
+                                                                const double* V, long long ldv, int jb,
+                                                                const double* T, int transT, int rp) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = static_cast<int>(cluster.num_blocks());
+    const int rank = static_cast<int>(cluster.block_rank());
+    const int blk = blockIdx.x / cs;
+    const int c0 = blk * WY_BN;
+    const int nbw = min(WY_BN, Nw - c0);
+    const int r0 = rank * rp;
+    const int nr = max(0, min(rp, Mp - r0));
+    extern __shared__ double sm[];
+    double* Vs = sm;                                   // [rp][JB+1]
+    double* Ws = Vs + static_cast<size_t>(rp) * (WY_JB + 1);   // [rp][BN+1]
+    double* Zp = Ws + static_cast<size_t>(rp) * (WY_BN + 1);   // [JB][BN] partial V^T W (read remotely)
+    double* Z = Zp + WY_JB * WY_BN;                    // [JB][BN] reduced Z, then op(T) Z
+    double* Zt = Z + WY_JB * WY_BN;                    // [JB][BN] own rows of op(T) Z (read remotely)
+    double* Ts = Zt + WY_JB * WY_BN;                   // [JB][JB] op(T)
+    const int tid = threadIdx.x;
+
+    for (int e = tid; e < nr * WY_JB; e += WY_THREADS) {
+        const int i = e >> 5, a = e & 31;
+        Vs[i * (WY_JB + 1) + a] = a < jb ? V[static_cast<long long>(r0 + i) * ldv + a] : 0.0;
+    }
+    for (int e = tid; e < nr * WY_BN; e += WY_THREADS) {
+        const int i = e >> 6, b = e & 63;
+        Ws[i * (WY_BN + 1) + b] = b < nbw ? W[static_cast<long long>(r0 + i) * ldw + c0 + b] : 0.0;
+    }
+    for (int e = tid; e < WY_JB * WY_JB; e += WY_THREADS) {
+        const int a = e >> 5, c = e & 31;
+        double v = 0.0;
+        if (a < jb && c < jb) v = transT ? T[c * jb + a] : T[a * jb + c];
+        Ts[e] = v;
+    }
+    __syncthreads();
+    // ---- Zp = V_rows^T W_rows,blk: thread -> column b, 8 consecutive a
+    const int b = tid & 63, ag = tid >> 6;
+    {
+        double acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+        for (int i = 0; i < nr; ++i) {
+            const double w = Ws[i * (WY_BN + 1) + b];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = fma(Vs[i * (WY_JB + 1) + ag * 8 + u], w, acc[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) Zp[(ag * 8 + u) * WY_BN + b] = acc[u];
+    }
+    cluster.sync();
+    // ---- reduce-scatter: rank k sums rows a in its share of Z over all ranks (rank order)
+    const int rows_per_rank = (WY_JB + cs - 1) / cs;
+    const int a0 = rank * rows_per_rank, a1 = min(WY_JB, a0 + rows_per_rank);
+    for (int e = tid; e < (a1 - a0) * WY_BN; e += WY_THREADS) {
+        const int a = a0 + e / WY_BN, bb = e % WY_BN;
+        double z = 0.0;
+        for (int k = 0; k < cs; ++k) z += cluster.map_shared_rank(Zp, k)[a * WY_BN + bb];
+        Z[a * WY_BN + bb] = z;
+    }
+    cluster.sync();
+    // ---- all-gather Z
+    for (int e = tid; e < WY_JB * WY_BN; e += WY_THREADS) {
+        const int a = e / WY_BN;
+        const int owner = a / rows_per_rank;
+        if (owner != rank) Z[e] = cluster.map_shared_rank(Z, owner)[e];
+    }
+    __syncthreads();
+    // ---- own rows of op(T) Z
+    for (int e = tid; e < (a1 - a0) * WY_BN; e += WY_THREADS) {
+        const int a = a0 + e / WY_BN, bb = e % WY_BN;
+        double z = 0.0;
+        for (int c = 0; c < WY_JB; ++c) z = fma(Ts[a * WY_JB + c], Z[c * WY_BN + bb], z);
+        Zt[a * WY_BN + bb] = z;
+    }
+    cluster.sync();
+    // ---- all-gather op(T) Z into Z (Z itself is no longer read by anyone after the sync)
+    for (int e = tid; e < WY_JB * WY_BN; e += WY_THREADS) {
+        const int a = e / WY_BN;
+        const int owner = a / rows_per_rank;
+        Z[e] = owner == rank ? Zt[e] : cluster.map_shared_rank(Zt, owner)[e];
+    }
+    __syncthreads();
+    // ---- W_rows,blk -= V_rows (op(T) Z): thread -> column b, rows ag, ag + 4, ...
+    {
+        double zc[WY_JB];
+#pragma unroll
+        for (int a = 0; a < WY_JB; ++a) zc[a] = Z[a * WY_BN + b];
+        for (int i = ag; i < nr; i += 4) {
+            double w = Ws[i * (WY_BN + 1) + b];
+#pragma unroll
+            for (int a = 0; a < WY_JB; ++a) w = fma(-Vs[i * (WY_JB + 1) + a], zc[a], w);
+            if (b < nbw) W[static_cast<long long>(r0 + i) * ldw + c0 + b] = w;
+        }
+    }
+    cluster.sync();   // peers may still read this CTA's Zt / Z slices
+}
+
 __global__ void qr_init_q_kernel(double* Q, long long ldq, int M, int N) {
     const long long total = static_cast<long long>(M) * N;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
@@ -1329,6 +1444,79 @@ gn_status launch_cluster_panel(gn_handle h, const PanelCfg& pc, double* W, long 
 }
 }  // namespace
 
+// Largest cluster size the WY kernel can launch with (0: none).
+int wy_cluster_max() {
+    static int cs_max = -1;
+    if (cs_max < 0) {
+        cs_max = 0;
+        if (cudaFuncSetAttribute(qr_wy_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(wy_smem(WY_MAX_ROWS))) == cudaSuccess &&
+            cudaFuncSetAttribute(qr_wy_apply_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
+            for (int cs : {16, 8}) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(cs);
+                cfg.blockDim = dim3(WY_THREADS);
+                cfg.dynamicSmemBytes = wy_smem(WY_MAX_ROWS);
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = cs;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int n = 0;
+                if (cudaOccupancyMaxActiveClusters(&n, qr_wy_apply_kernel, &cfg) == cudaSuccess && n >= 1) {
+                    cs_max = cs;
+                    break;
+                }
+            }
+        }
+        cudaGetLastError();
+    }
+    return cs_max;
+}
+
+// Whether wy_apply can handle panels with up to Mp rows.
+bool wy_usable(long long Mp) {
+    const int cm = wy_cluster_max();
+    return cm > 0 && (Mp + cm - 1) / cm <= WY_MAX_ROWS;
+}
+
+// One-launch compact-WY application when a row slice of the panel fits a CTA's
+// shared memory; returns GN_ERR_UNSUPPORTED otherwise (the caller then uses the
+// GEMM sequence).
+gn_status wy_apply(gn_handle h, double* W, long long ldw, long long Mp, long long Nw, const double* V, long long ldv,
+                   int jb, const double* T, int transT) {
+    const int cs_max = wy_cluster_max();
+    if (cs_max == 0 || jb > WY_JB || Mp <= 0 || Nw <= 0) return GN_ERR_UNSUPPORTED;
+    const long long nblk = (Nw + WY_BN - 1) / WY_BN;
+    int cs = 8;
+    if (nblk * 8 < h->sm_count / 2 && cs_max >= 16) cs = 16;   // few column blocks: split rows finer
+    long long rp = (Mp + cs - 1) / cs;
+    if (rp > WY_MAX_ROWS && cs_max >= 16) {
+        cs = 16;
+        rp = (Mp + cs - 1) / cs;
+    }
+    if (rp > WY_MAX_ROWS) return GN_ERR_UNSUPPORTED;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(nblk * cs));
+    cfg.blockDim = dim3(WY_THREADS);
+    cfg.dynamicSmemBytes = wy_smem(static_cast<int>(rp));
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, qr_wy_apply_kernel, W, ldw, static_cast<int>(Mp), static_cast<int>(Nw), V,
+                                   ldv, jb, T, transT, static_cast<int>(rp)));
+    count_launch();
+    return GN_OK;
+}
+
 gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R, long long ldr,
                     double* ws, size_t ws_bytes) {
     if (M < N || N <= 0) return GN_ERR_SHAPE;
@@ -1342,28 +1530,56 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
     }
     const PanelCfg pc = panel_cfg(h, M);
     const int nb = pc.nb;
-    for (long long j0 = 0; j0 < N; j0 += nb) {
+    auto factor_panel = [&](long long j0) -> gn_status {
         const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
         const long long Mp = M - j0;
         double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
-        if (pc.cluster) {
-            GN_TRY(launch_cluster_panel(h, pc, W, ld, M, j0, jb, q.V, N, q.tau, T));
-        } else {
-            const size_t panel_bytes = static_cast<size_t>(Mp) * (jb + 1) * sizeof(double);
-            const int use_smem = panel_bytes <= QR_SMEM_PANEL_MAX ? 1 : 0;
-            qr_panel_kernel<<<1, QR_THREADS, use_smem ? panel_bytes : 0, h->stream>>>(
-                W, ld, static_cast<int>(M), static_cast<int>(j0), jb, q.V, N, q.tau, T, use_smem); count_launch();
-            GN_CUDA_TRY(cudaGetLastError());
-        }
+        if (pc.cluster) return launch_cluster_panel(h, pc, W, ld, M, j0, jb, q.V, N, q.tau, T);
+        const size_t panel_bytes = static_cast<size_t>(Mp) * (jb + 1) * sizeof(double);
+        const int use_smem = panel_bytes <= QR_SMEM_PANEL_MAX ? 1 : 0;
+        qr_panel_kernel<<<1, QR_THREADS, use_smem ? panel_bytes : 0, h->stream>>>(
+            W, ld, static_cast<int>(M), static_cast<int>(j0), jb, q.V, N, q.tau, T, use_smem); count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        return GN_OK;
+    };
+    // Look-ahead: after panel j only panel j+1's columns are updated on the main
+    // stream; panel j+1 is then factored (16-SM cluster) while the rest of the
+    // trailing update runs on the side stream.  Requires the one-launch WY path.
+    const bool lookahead = pc.cluster && h->side != nullptr && wy_usable(M);
+    GN_TRY(factor_panel(0));
+    for (long long j0 = 0; j0 < N; j0 += nb) {
+        const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
+        const long long Mp = M - j0;
         const long long N2 = N - j0 - jb;
-        if (N2 > 0) {
-            double* W2 = W + j0 * ld + j0 + jb;
-            const double* Vb = q.V + j0 * N + j0;
-            // Z1 = V^T W2 ; Z2 = T^T Z1 ; W2 -= V Z2
+        if (N2 <= 0) break;
+        double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
+        double* W2 = W + j0 * ld + j0 + jb;
+        const double* Vb = q.V + j0 * N + j0;
+        if (lookahead) {
+            // W2 <- (I - V T V^T)^T W2 = W2 - V T^T (V^T W2), split at the next panel
+            const long long nnext = std::min<long long>(nb, N2);
+            GN_TRY(wy_apply(h, W2, ld, Mp, nnext, Vb, N, jb, T, 1));
+            if (N2 > nnext) {
+                GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+                GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+                gn_handle_s side = *h;
+                side.stream = h->side;
+                GN_TRY(wy_apply(&side, W2 + nnext, ld, Mp, N2 - nnext, Vb, N, jb, T, 1));
+                GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+            }
+            GN_TRY(factor_panel(j0 + jb));
+            if (N2 > nnext) GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+            continue;
+        }
+        const gn_status st = wy_apply(h, W2, ld, Mp, N2, Vb, N, jb, T, 1);
+        if (st == GN_ERR_UNSUPPORTED) {
             GN_TRY(dgemm(h, jb, N2, Mp, 1.0, Vb, N, 1, W2, ld, 0, 0.0, q.Z1, N2, q.gws, q.gws_bytes));
             GN_TRY(dgemm(h, jb, N2, jb, 1.0, T, jb, 1, q.Z1, N2, 0, 0.0, q.Z2, N2, q.gws, q.gws_bytes));
             GN_TRY(dgemm(h, Mp, N2, jb, -1.0, Vb, N, 0, q.Z2, N2, 0, 1.0, W2, ld, q.gws, q.gws_bytes));
+        } else {
+            GN_TRY(st);
         }
+        GN_TRY(factor_panel(j0 + jb));
     }
     qr_write_r_kernel<<<ew_blocks(h, N * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(N), R, ldr); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
@@ -1385,9 +1601,15 @@ gn_status qr_form_q(gn_handle h, const double* W, long long M, long long N, long
         double* Qs = Q + j0 * ldq + j0;
         const double* Vb = q.V + j0 * N + j0;
         const double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
-        GN_TRY(dgemm(h, jb, Nq, Mp, 1.0, Vb, N, 1, Qs, ldq, 0, 0.0, q.Z1, Nq, q.gws, q.gws_bytes));
-        GN_TRY(dgemm(h, jb, Nq, jb, 1.0, T, jb, 0, q.Z1, Nq, 0, 0.0, q.Z2, Nq, q.gws, q.gws_bytes));
-        GN_TRY(dgemm(h, Mp, Nq, jb, -1.0, Vb, N, 0, q.Z2, Nq, 0, 1.0, Qs, ldq, q.gws, q.gws_bytes));
+        // Q_s <- (I - V T V^T) Q_s
+        const gn_status st = wy_apply(h, Qs, ldq, Mp, Nq, Vb, N, jb, T, 0);
+        if (st == GN_ERR_UNSUPPORTED) {
+            GN_TRY(dgemm(h, jb, Nq, Mp, 1.0, Vb, N, 1, Qs, ldq, 0, 0.0, q.Z1, Nq, q.gws, q.gws_bytes));
+            GN_TRY(dgemm(h, jb, Nq, jb, 1.0, T, jb, 0, q.Z1, Nq, 0, 0.0, q.Z2, Nq, q.gws, q.gws_bytes));
+            GN_TRY(dgemm(h, Mp, Nq, jb, -1.0, Vb, N, 0, q.Z2, Nq, 0, 1.0, Qs, ldq, q.gws, q.gws_bytes));
+        } else {
+            GN_TRY(st);
+        }
     }
     qr_flip_q_kernel<<<ew_blocks(h, M * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(M),
                                                                   static_cast<int>(N), Q, ldq); count_launch();
