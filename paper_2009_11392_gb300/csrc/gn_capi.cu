@@ -217,8 +217,19 @@ gn_status gn_create(gn_handle* out, void* stream) {
         delete h;
         return GN_ERR_CUDA;
     }
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->crit, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
+        cudaStreamDestroy(h->side);
+        cudaFree(h->dstatus);
+        delete h;
+        return GN_ERR_CUDA;
+    }
     if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_crit0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_crit1, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(h->crit);
         cudaStreamDestroy(h->side);
         cudaFree(h->dstatus);
         delete h;
@@ -232,8 +243,12 @@ gn_status gn_destroy(gn_handle h) {
     if (!h) return GN_ERR_INVALID_ARG;
     cudaStreamSynchronize(h->stream);
     cudaStreamSynchronize(h->side);
+    cudaStreamSynchronize(h->crit);
     cudaEventDestroy(h->ev_fork);
     cudaEventDestroy(h->ev_join);
+    cudaEventDestroy(h->ev_crit0);
+    cudaEventDestroy(h->ev_crit1);
+    cudaStreamDestroy(h->crit);
     cudaStreamDestroy(h->side);
     cudaFree(h->dstatus);
     delete h;

@@ -655,41 +655,46 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
 // update of the factorization, T for the formation of Q.
 // ---------------------------------------------------------------------------
 constexpr int WY_THREADS = 256;
-constexpr int WY_BN = 64;
 constexpr int WY_JB = 32;
-constexpr int WY_MAX_ROWS = 188;   // rows per CTA that fit in shared memory
+constexpr int WY_MAX_ROWS = 188;   // rows per CTA that fit in shared memory (BN = 64)
 
-__host__ __device__ inline size_t wy_smem(int rp) {
-    return sizeof(double) * (static_cast<size_t>(rp) * (WY_JB + 1 + WY_BN + 1) + 3 * WY_JB * WY_BN + WY_JB * WY_JB);
+__host__ __device__ inline size_t wy_smem(int rp, int bn) {
+    return sizeof(double) * (static_cast<size_t>(rp) * (WY_JB + 1 + bn + 1) + 3 * WY_JB * bn + WY_JB * WY_JB);
 }
 
+// BN: columns of W per cluster (8, 16, 32 or 64).  Narrow blocks spread a
+// narrow update over more SMs: the kernel is bound by the SM's FP64 rate.
+template <int BN>
 __global__ void __launch_bounds__(WY_THREADS) qr_wy_apply_kernel(double* W, long long ldw, int Mp, int Nw,
                                                                 const double* V, long long ldv, int jb,
                                                                 const double* T, int transT, int rp) {
+    constexpr int G = WY_THREADS / BN;    // thread groups per column
+    constexpr int AU = WY_JB / G;         // rows of Z per thread
+    static_assert(AU >= 1 && AU * G == WY_JB, "BN must be 8, 16, 32 or 64");
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = static_cast<int>(cluster.num_blocks());
     const int rank = static_cast<int>(cluster.block_rank());
     const int blk = blockIdx.x / cs;
-    const int c0 = blk * WY_BN;
-    const int nbw = min(WY_BN, Nw - c0);
+    const int c0 = blk * BN;
+    const int nbw = min(BN, Nw - c0);
     const int r0 = rank * rp;
     const int nr = max(0, min(rp, Mp - r0));
     extern __shared__ double sm[];
     double* Vs = sm;                                   // [rp][JB+1]
     double* Ws = Vs + static_cast<size_t>(rp) * (WY_JB + 1);   // [rp][BN+1]
-    double* Zp = Ws + static_cast<size_t>(rp) * (WY_BN + 1);   // [JB][BN] partial V^T W (read remotely)
-    double* Z = Zp + WY_JB * WY_BN;                    // [JB][BN] reduced Z, then op(T) Z
-    double* Zt = Z + WY_JB * WY_BN;                    // [JB][BN] own rows of op(T) Z (read remotely)
-    double* Ts = Zt + WY_JB * WY_BN;                   // [JB][JB] op(T)
+    double* Zp = Ws + static_cast<size_t>(rp) * (BN + 1);      // [JB][BN] partial V^T W (read remotely)
+    double* Z = Zp + WY_JB * BN;                       // [JB][BN] reduced Z, then op(T) Z
+    double* Zt = Z + WY_JB * BN;                       // [JB][BN] own rows of op(T) Z (read remotely)
+    double* Ts = Zt + WY_JB * BN;                      // [JB][JB] op(T)
     const int tid = threadIdx.x;
 
     for (int e = tid; e < nr * WY_JB; e += WY_THREADS) {
         const int i = e >> 5, a = e & 31;
         Vs[i * (WY_JB + 1) + a] = a < jb ? V[static_cast<long long>(r0 + i) * ldv + a] : 0.0;
     }
-    for (int e = tid; e < nr * WY_BN; e += WY_THREADS) {
-        const int i = e >> 6, b = e & 63;
-        Ws[i * (WY_BN + 1) + b] = b < nbw ? W[static_cast<long long>(r0 + i) * ldw + c0 + b] : 0.0;
+    for (int e = tid; e < nr * BN; e += WY_THREADS) {
+        const int i = e / BN, b = e % BN;
+        Ws[i * (BN + 1) + b] = b < nbw ? W[static_cast<long long>(r0 + i) * ldw + c0 + b] : 0.0;
     }
     for (int e = tid; e < WY_JB * WY_JB; e += WY_THREADS) {
         const int a = e >> 5, c = e & 31;
@@ -698,60 +703,60 @@ __global__ void __launch_bounds__(WY_THREADS) qr_wy_apply_kernel(double* W, long
         Ts[e] = v;
     }
     __syncthreads();
-    // ---- Zp = V_rows^T W_rows,blk: thread -> column b, 8 consecutive a
-    const int b = tid & 63, ag = tid >> 6;
+    // ---- Zp = V_rows^T W_rows,blk: thread -> column b, AU consecutive a
+    const int b = tid % BN, ag = tid / BN;
     {
-        double acc[8];
+        double acc[AU];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+        for (int u = 0; u < AU; ++u) acc[u] = 0.0;
         for (int i = 0; i < nr; ++i) {
-            const double w = Ws[i * (WY_BN + 1) + b];
+            const double w = Ws[i * (BN + 1) + b];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] = fma(Vs[i * (WY_JB + 1) + ag * 8 + u], w, acc[u]);
+            for (int u = 0; u < AU; ++u) acc[u] = fma(Vs[i * (WY_JB + 1) + ag * AU + u], w, acc[u]);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) Zp[(ag * 8 + u) * WY_BN + b] = acc[u];
+        for (int u = 0; u < AU; ++u) Zp[(ag * AU + u) * BN + b] = acc[u];
     }
     cluster.sync();
     // ---- reduce-scatter: rank k sums rows a in its share of Z over all ranks (rank order)
     const int rows_per_rank = (WY_JB + cs - 1) / cs;
     const int a0 = rank * rows_per_rank, a1 = min(WY_JB, a0 + rows_per_rank);
-    for (int e = tid; e < (a1 - a0) * WY_BN; e += WY_THREADS) {
-        const int a = a0 + e / WY_BN, bb = e % WY_BN;
+    for (int e = tid; e < (a1 - a0) * BN; e += WY_THREADS) {
+        const int a = a0 + e / BN, bb = e % BN;
         double z = 0.0;
-        for (int k = 0; k < cs; ++k) z += cluster.map_shared_rank(Zp, k)[a * WY_BN + bb];
-        Z[a * WY_BN + bb] = z;
+        for (int k = 0; k < cs; ++k) z += cluster.map_shared_rank(Zp, k)[a * BN + bb];
+        Z[a * BN + bb] = z;
     }
     cluster.sync();
     // ---- all-gather Z
-    for (int e = tid; e < WY_JB * WY_BN; e += WY_THREADS) {
-        const int a = e / WY_BN;
+    for (int e = tid; e < WY_JB * BN; e += WY_THREADS) {
+        const int a = e / BN;
         const int owner = a / rows_per_rank;
         if (owner != rank) Z[e] = cluster.map_shared_rank(Z, owner)[e];
     }
     __syncthreads();
     // ---- own rows of op(T) Z
-    for (int e = tid; e < (a1 - a0) * WY_BN; e += WY_THREADS) {
-        const int a = a0 + e / WY_BN, bb = e % WY_BN;
+    for (int e = tid; e < (a1 - a0) * BN; e += WY_THREADS) {
+        const int a = a0 + e / BN, bb = e % BN;
         double z = 0.0;
-        for (int c = 0; c < WY_JB; ++c) z = fma(Ts[a * WY_JB + c], Z[c * WY_BN + bb], z);
-        Zt[a * WY_BN + bb] = z;
+        for (int c = 0; c < WY_JB; ++c) z = fma(Ts[a * WY_JB + c], Z[c * BN + bb], z);
+        Zt[a * BN + bb] = z;
     }
     cluster.sync();
     // ---- all-gather op(T) Z into Z (Z itself is no longer read by anyone after the sync)
-    for (int e = tid; e < WY_JB * WY_BN; e += WY_THREADS) {
-        const int a = e / WY_BN;
+    for (int e = tid; e < WY_JB * BN; e += WY_THREADS) {
+        const int a = e / BN;
         const int owner = a / rows_per_rank;
         Z[e] = owner == rank ? Zt[e] : cluster.map_shared_rank(Zt, owner)[e];
     }
     __syncthreads();
-    // ---- W_rows,blk -= V_rows (op(T) Z): thread -> column b, rows ag, ag + 4, ...
+    // ---- W_rows,blk -= V_rows (op(T) Z): thread -> column b, rows ag, ag + G, ...
     {
         double zc[WY_JB];
 #pragma unroll
-        for (int a = 0; a < WY_JB; ++a) zc[a] = Z[a * WY_BN + b];
-        for (int i = ag; i < nr; i += 4) {
-            double w = Ws[i * (WY_BN + 1) + b];
+        for (int a = 0; a < WY_JB; ++a) zc[a] = Z[a * BN + b];
+        for (int i = ag; i < nr; i += G) {
+            double w = Ws[i * (BN + 1) + b];
 #pragma unroll
             for (int a = 0; a < WY_JB; ++a) w = fma(-Vs[i * (WY_JB + 1) + a], zc[a], w);
             if (b < nbw) W[static_cast<long long>(r0 + i) * ldw + c0 + b] = w;
@@ -1444,20 +1449,25 @@ gn_status launch_cluster_panel(gn_handle h, const PanelCfg& pc, double* W, long 
 }
 }  // namespace
 
+template <int BN>
+bool wy_attrs() {
+    return cudaFuncSetAttribute(qr_wy_apply_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(wy_smem(WY_MAX_ROWS, BN))) == cudaSuccess &&
+           cudaFuncSetAttribute(qr_wy_apply_kernel<BN>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+               cudaSuccess;
+}
+
 // Largest cluster size the WY kernel can launch with (0: none).
 int wy_cluster_max() {
     static int cs_max = -1;
     if (cs_max < 0) {
         cs_max = 0;
-        if (cudaFuncSetAttribute(qr_wy_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(wy_smem(WY_MAX_ROWS))) == cudaSuccess &&
-            cudaFuncSetAttribute(qr_wy_apply_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                cudaSuccess) {
+        if (wy_attrs<64>() && wy_attrs<32>() && wy_attrs<16>() && wy_attrs<8>()) {
             for (int cs : {16, 8}) {
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3(cs);
                 cfg.blockDim = dim3(WY_THREADS);
-                cfg.dynamicSmemBytes = wy_smem(WY_MAX_ROWS);
+                cfg.dynamicSmemBytes = wy_smem(WY_MAX_ROWS, 64);
                 cudaLaunchAttribute attr[1];
                 attr[0].id = cudaLaunchAttributeClusterDimension;
                 attr[0].val.clusterDim.x = cs;
@@ -1466,7 +1476,7 @@ int wy_cluster_max() {
                 cfg.attrs = attr;
                 cfg.numAttrs = 1;
                 int n = 0;
-                if (cudaOccupancyMaxActiveClusters(&n, qr_wy_apply_kernel, &cfg) == cudaSuccess && n >= 1) {
+                if (cudaOccupancyMaxActiveClusters(&n, qr_wy_apply_kernel<64>, &cfg) == cudaSuccess && n >= 1) {
                     cs_max = cs;
                     break;
                 }
@@ -1475,6 +1485,31 @@ int wy_cluster_max() {
         cudaGetLastError();
     }
     return cs_max;
+}
+
+// Clusters of cs CTAs that fit at once with one CTA per SM (cached per size).
+int wy_cluster_capacity(int cs, int sm_count) {
+    static int cap[17] = {0};
+    if (cs < 1 || cs > 16) return 1;
+    if (cap[cs] == 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(WY_THREADS);
+        cfg.dynamicSmemBytes = wy_smem(WY_MAX_ROWS, 64);   // > half an SM's shared memory
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, qr_wy_apply_kernel<64>, &cfg) != cudaSuccess || n < 1)
+            n = sm_count / cs > 0 ? sm_count / cs : 1;
+        cudaGetLastError();
+        cap[cs] = n;
+    }
+    return cap[cs];
 }
 
 // Whether wy_apply can handle panels with up to Mp rows.
@@ -1490,19 +1525,34 @@ gn_status wy_apply(gn_handle h, double* W, long long ldw, long long Mp, long lon
                    int jb, const double* T, int transT) {
     const int cs_max = wy_cluster_max();
     if (cs_max == 0 || jb > WY_JB || Mp <= 0 || Nw <= 0) return GN_ERR_UNSUPPORTED;
-    const long long nblk = (Nw + WY_BN - 1) / WY_BN;
-    int cs = 8;
-    if (nblk * 8 < h->sm_count / 2 && cs_max >= 16) cs = 16;   // few column blocks: split rows finer
-    long long rp = (Mp + cs - 1) / cs;
-    if (rp > WY_MAX_ROWS && cs_max >= 16) {
-        cs = 16;
-        rp = (Mp + cs - 1) / cs;
+    // Cluster size (rows per CTA) and column block width: the kernel is bound by
+    // each SM's FP64 rate, so its time is ~ waves x rows per CTA x (bn + a fixed
+    // cost of about 8 columns' work), a wave being the clusters that fit at once
+    // with one CTA per SM.
+    int cs = 0, bn = 64;
+    long long rp = 0, best = -1;
+    for (int c : {8, 16}) {
+        if (c > cs_max) continue;
+        const long long rpc = (Mp + c - 1) / c;
+        if (rpc > WY_MAX_ROWS) continue;
+        const long long capc = wy_cluster_capacity(c, h->sm_count);
+        for (int cand : {64, 32, 16, 8}) {
+            const long long waves = ((Nw + cand - 1) / cand + capc - 1) / capc;
+            const long long cost = waves * rpc * (cand + 8);
+            if (best < 0 || cost < best) {
+                best = cost;
+                cs = c;
+                bn = cand;
+                rp = rpc;
+            }
+        }
     }
-    if (rp > WY_MAX_ROWS) return GN_ERR_UNSUPPORTED;
+    if (cs == 0) return GN_ERR_UNSUPPORTED;
+    const long long nblk = (Nw + bn - 1) / bn;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(nblk * cs));
     cfg.blockDim = dim3(WY_THREADS);
-    cfg.dynamicSmemBytes = wy_smem(static_cast<int>(rp));
+    cfg.dynamicSmemBytes = wy_smem(static_cast<int>(rp), bn);
     cfg.stream = h->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1511,8 +1561,13 @@ gn_status wy_apply(gn_handle h, double* W, long long ldw, long long Mp, long lon
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, qr_wy_apply_kernel, W, ldw, static_cast<int>(Mp), static_cast<int>(Nw), V,
-                                   ldv, jb, T, transT, static_cast<int>(rp)));
+    const int mpi = static_cast<int>(Mp), nwi = static_cast<int>(Nw), rpi = static_cast<int>(rp);
+    switch (bn) {
+        case 64: GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, qr_wy_apply_kernel<64>, W, ldw, mpi, nwi, V, ldv, jb, T, transT, rpi)); break;
+        case 32: GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, qr_wy_apply_kernel<32>, W, ldw, mpi, nwi, V, ldv, jb, T, transT, rpi)); break;
+        case 16: GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, qr_wy_apply_kernel<16>, W, ldw, mpi, nwi, V, ldv, jb, T, transT, rpi)); break;
+        default: GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, qr_wy_apply_kernel<8>, W, ldw, mpi, nwi, V, ldv, jb, T, transT, rpi)); break;
+    }
     count_launch();
     return GN_OK;
 }
@@ -1545,7 +1600,18 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
     // Look-ahead: after panel j only panel j+1's columns are updated on the main
     // stream; panel j+1 is then factored (16-SM cluster) while the rest of the
     // trailing update runs on the side stream.  Requires the one-launch WY path.
-    const bool lookahead = pc.cluster && h->side != nullptr && wy_usable(M);
+    const bool lookahead = pc.cluster && h->side != nullptr && h->crit != nullptr && wy_usable(M);
+    // The look-ahead chain (next-block updates and panels) runs on a
+    // high-priority stream so the block scheduler places its clusters ahead of
+    // the trailing updates queued on the side stream.
+    const gn_handle h0 = h;
+    gn_handle_s crit = *h;
+    if (lookahead) {
+        crit.stream = h->crit;
+        GN_CUDA_TRY(cudaEventRecord(h->ev_crit0, h->stream));
+        GN_CUDA_TRY(cudaStreamWaitEvent(h->crit, h->ev_crit0, 0));
+        h = &crit;
+    }
     GN_TRY(factor_panel(0));
     for (long long j0 = 0; j0 < N; j0 += nb) {
         const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
@@ -1583,6 +1649,10 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
     }
     qr_write_r_kernel<<<ew_blocks(h, N * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(N), R, ldr); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
+    if (h != h0) {   // join the high-priority chain back into the caller's stream
+        GN_CUDA_TRY(cudaEventRecord(h0->ev_crit1, h->stream));
+        GN_CUDA_TRY(cudaStreamWaitEvent(h0->stream, h0->ev_crit1, 0));
+    }
     return GN_OK;
 }
 

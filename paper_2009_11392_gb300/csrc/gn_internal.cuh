@@ -17,6 +17,8 @@ struct gn_handle_s {
     cudaStream_t stream;
     cudaStream_t side;         // second stream: work that overlaps the main sequence
     cudaEvent_t ev_fork, ev_join;
+    cudaStream_t crit;         // high-priority stream for the QR's panel chain
+    cudaEvent_t ev_crit0, ev_crit1;
     int32_t* dstatus;          // device: [0] latched gn_status, [1] where
     uint64_t wait_limit_ns;
     // batched path: the tables gn_batched_prepare uploaded into batched_ws
