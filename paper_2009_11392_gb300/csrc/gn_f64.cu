@@ -480,48 +480,59 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     }
     __syncthreads();
 
-    // Thread tile for the per-column sums and updates: column lane j = tid % 32
-    // (panel column index), row chunk k = tid / 32 (rows lo + k, lo + k + 8, ...).
-    // On GB300 one SM retires ~2 FP64 operations per clock, so partial sums are
-    // formed per (chunk, column) and combined once, not by warp butterflies.
-    const int cj = lane, ck = warp;
+    for (int e = tid; e < JB; e += CP_THREADS) taus[e] = 0.0;
+    // Per-column thread tiles cover only the live columns: with na live columns
+    // (padded to np, a power of two), lane = sub * np + column offset and the
+    // 8 * 32 / np row chunks split the rows.  On GB300 each FP64 warp
+    // instruction holds the SM's FP64 pipe for ~16 cycles whatever its mask,
+    // so idle lanes are what this avoids.
     for (int c = 0; c < jb; ++c) {
         double* slot = xch + (c & 1) * SLOT;
         const int cl = c - r0;                       // local index of row c (owner iff 0 <= cl < nr)
         const bool owner = cl >= 0 && cl < nr;
         const int lo = max(0, cl);                   // first local row with panel row >= c
-        // ---- per-CTA partials: tail = sum_{rows > c} x_i^2 (column lane c),
-        //      dots_j = sum_{rows >= c} x_i P_ij (column lanes j > c)
+        // ---- per-CTA partials: tail = sum_{rows > c} x_i^2 (column c),
+        //      dots_j = sum_{rows >= c} x_i P_ij (columns j > c)
         {
+            const int na = jb - c;
+            const int np = na > 16 ? 32 : na > 8 ? 16 : na > 4 ? 8 : na > 2 ? 4 : na > 1 ? 2 : 1;
+            const int off = lane & (np - 1), sub = lane / np;
+            const int nchunk = CP_WARPS * (32 / np);
+            const int chunk = warp * (32 / np) + sub;
+            const int j = c + off;
             double acc = 0.0;
-            if (cj == c) {
-                for (int li = max(0, cl + 1) + ck; li < nr; li += CP_WARPS) {
-                    const double x = P[li * LDP + c];
-                    acc = fma(x, x, acc);
+            if (off < na) {
+                if (off == 0) {
+                    for (int li = max(0, cl + 1) + chunk; li < nr; li += nchunk) {
+                        const double x = P[li * LDP + c];
+                        acc = fma(x, x, acc);
+                    }
+                } else {
+                    for (int li = lo + chunk; li < nr; li += nchunk) acc = fma(P[li * LDP + c], P[li * LDP + j], acc);
                 }
-            } else if (cj > c && cj < jb) {
-                for (int li = lo + ck; li < nr; li += CP_WARPS) acc = fma(P[li * LDP + c], P[li * LDP + cj], acc);
             }
-            tv[ck * 32 + cj] = acc;   // tv doubles as the 8 x 32 partial table here
+            for (int o = np; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (sub == 0) tv[warp * 32 + off] = acc;   // tv doubles as the 8 x 32 partial table here
         }
         __syncthreads();
         if (warp == 0) {
-            if (cj >= c && cj < jb) {
-                double t8 = 0.0;
-#pragma unroll
-                for (int k = 0; k < CP_WARPS; ++k) t8 += tv[k * 32 + cj];
-                if (cj == c) {
+            const int j = c + lane;
+            if (j < jb) {
+                const double t8 = ((tv[lane] + tv[32 + lane]) + (tv[64 + lane] + tv[96 + lane])) +
+                                  ((tv[128 + lane] + tv[160 + lane]) + (tv[192 + lane] + tv[224 + lane]));
+                if (lane == 0) {
                     slot[0] = t8;
                     slot[1] = owner ? P[cl * LDP + c] : 0.0;
                 } else {
-                    slot[2 + cj] = t8;
-                    slot[2 + JB + cj] = owner ? P[cl * LDP + cj] : 0.0;
+                    slot[2 + j] = t8;
+                    slot[2 + JB + j] = owner ? P[cl * LDP + j] : 0.0;
                 }
             }
         }
         cluster.sync();
         // ---- combine over ranks (the same order in every CTA): warps 0-3 each sum
         //      four ranks' partials for every column, warp 0 adds the four sums
+        const int cj = lane;
         if (warp < 4 && cj >= c && cj < jb) {
             double a0 = 0.0, a1 = 0.0;
             const int o0 = cj == c ? 0 : 2 + cj, o1 = cj == c ? 1 : 2 + JB + cj;
@@ -582,64 +593,94 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
             }
             if (tid > c && tid < jb) wv[tid] = fma(-beta, prow[tid], dsum[tid]) * sc;
             __syncthreads();
-            if (cj > c && cj < jb) {
-                const double wj = wv[cj];
-                for (int li = lo + ck; li < nr; li += CP_WARPS) P[li * LDP + cj] = fma(-tv[li], wj, P[li * LDP + cj]);
+            const int na = jb - c - 1;   // columns c+1 .. jb-1
+            if (na > 0) {
+                const int np = na > 16 ? 32 : na > 8 ? 16 : na > 4 ? 8 : na > 2 ? 4 : na > 1 ? 2 : 1;
+                const int off = lane & (np - 1);
+                const int nchunk = CP_WARPS * (32 / np);
+                const int chunk = warp * (32 / np) + lane / np;
+                if (off < na) {
+                    const int j = c + 1 + off;
+                    const double wj = wv[j];
+                    for (int li = lo + chunk; li < nr; li += nchunk) P[li * LDP + j] = fma(-tv[li], wj, P[li * LDP + j]);
+                }
             }
         }
         __syncthreads();
     }
 
-    // write back the panel, the explicit reflectors, and the partial Gram V^T V
+    // write back the panel and the explicit reflectors
     for (int e = tid; e < nr * jb; e += CP_THREADS) {
         const int li = e / jb, c = e - li * jb;
         const int gi = r0 + li;
         const double pv = P[li * LDP + c];
-        const double v = gi < c ? 0.0 : (gi == c ? 1.0 : (taus[c] == 0.0 ? 0.0 : pv));
+        const bool live = taus[c] != 0.0;
+        const double v = gi < c ? 0.0 : (gi == c ? 1.0 : (live ? pv : 0.0));
         V[static_cast<long long>(j0 + gi) * ldv + j0 + c] = v;
         W[static_cast<long long>(j0 + gi) * ld + j0 + c] = pv;
     }
-    for (int e = tid; e < jb * jb; e += CP_THREADS) {
-        const int q = e / jb, q2 = e - q * jb;
-        double g = 0.0;
-        if (q2 < q) {
-            for (int li = max(0, q - r0); li < nr; ++li) {   // v_q is zero above row q
-                const int gi = r0 + li;
-                const double vq = gi == q ? 1.0 : (taus[q] == 0.0 ? 0.0 : P[li * LDP + q]);
-                const double vq2 = gi == q2 ? 1.0 : (taus[q2] == 0.0 ? 0.0 : P[li * LDP + q2]);
-                g = fma(vq, vq2, g);
-            }
+    // partial Gram of the reflectors over this CTA's rows: for q2 < q,
+    //   g(q, q2) = v_q^T v_q2 = P[q][q2] + sum_{rows i > q} P[i][q] P[i][q2]
+    // (v_q is zero above row q and 1 at row q); pairs enumerated compactly.
+    for (int e = tid; e < JB * (JB - 1) / 2; e += CP_THREADS) {
+        int q = 1, q2 = e;
+        while (q2 >= q) {
+            q2 -= q;
+            ++q;
         }
-        gram[q * JB + q2] = g;
+        double g = 0.0;
+        if (q < jb) {
+            const int lq = q - r0;
+            if (lq >= 0 && lq < nr) g = P[lq * LDP + q2];
+            for (int li = max(0, lq + 1); li < nr; ++li) g = fma(P[li * LDP + q], P[li * LDP + q2], g);
+        }
+        gram[e] = g;
     }
     cluster.sync();
     if (rank == 0) {
-        for (int e = tid; e < jb * jb; e += CP_THREADS) {
-            const int q = e / jb, q2 = e - q * jb;
+        // Ts: the Gram in the strict lower triangle (zero for dropped reflectors and
+        // padding), tau on the diagonal; T is built in the upper triangle.
+        for (int e = tid; e < JB * JB; e += CP_THREADS) {
+            const int q = e / JB, q2 = e - q * JB;
             double g = 0.0;
             if (q2 < q) {
+                const int pe = q * (q - 1) / 2 + q2;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    if (k < cs) g += cluster.map_shared_rank(gram, k)[q * JB + q2];
+                    if (k < cs) g += cluster.map_shared_rank(gram, k)[pe];
+                if (taus[q] == 0.0 || taus[q2] == 0.0) g = 0.0;
+            } else if (q2 == q) {
+                g = taus[q];
             }
-            Ts[q * JB + q2] = g;   // the Gram in the strict lower triangle; zeros elsewhere
+            Ts[e] = g;
         }
         __syncthreads();
-        if (warp == 0) {
-            // column c of T: T[a][c] = -tau_c sum_{b=a}^{c-1} T[a][b] g_c[b] for a < c
-            for (int c = 0; c < jb; ++c) {
-                double val = 0.0;
-                if (lane < c) {
-                    for (int b = lane; b < c; ++b) val = fma(Ts[lane * JB + b], Ts[c * JB + b], val);
-                    val = -taus[c] * val;
-                }
-                __syncwarp();
-                if (lane < c) Ts[lane * JB + c] = val;
-                if (lane == c) Ts[c * JB + c] = taus[c];
-                __syncwarp();
+        // T by recursive doubling: for adjacent diagonal blocks T1 (rows o..o+s) and
+        // T2 (o+s..o+2s), the off-diagonal block is -T1 (V1^T V2) T2, where
+        // (V1^T V2)[a][b] = g(o+s+b, o+a).  Mt holds (V1^T V2) T2 for every pair.
+        double* Mt = tv;
+        for (int sz = 1; sz < JB; sz <<= 1) {
+            const int items = (JB / (2 * sz)) * sz * sz;
+            for (int e = tid; e < items; e += CP_THREADS) {
+                const int pr = e / (sz * sz), rem = e - pr * sz * sz, a = rem / sz, b = rem - a * sz;
+                const int o = pr * 2 * sz;
+                double m = 0.0;
+                for (int k = 0; k <= b; ++k) m = fma(Ts[(o + sz + k) * JB + o + a], Ts[(o + sz + k) * JB + o + sz + b], m);
+                Mt[e] = m;
             }
-            for (int a = 0; a < jb; ++a)
-                for (int b = lane; b < jb; b += 32) T[a * jb + b] = b >= a ? Ts[a * JB + b] : 0.0;
+            __syncthreads();
+            for (int e = tid; e < items; e += CP_THREADS) {
+                const int pr = e / (sz * sz), rem = e - pr * sz * sz, a = rem / sz, b = rem - a * sz;
+                const int o = pr * 2 * sz;
+                double v = 0.0;
+                for (int k = a; k < sz; ++k) v = fma(Ts[(o + a) * JB + o + k], Mt[pr * sz * sz + k * sz + b], v);
+                Ts[(o + a) * JB + o + sz + b] = -v;
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < jb * jb; e += CP_THREADS) {
+            const int a = e / jb, b = e - a * jb;
+            T[e] = b >= a ? Ts[a * JB + b] : 0.0;
         }
     }
     cluster.sync();
