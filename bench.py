@@ -332,6 +332,9 @@ def main():
     peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
     roof_ms = max(2.0 * m * n / (peaks["hbm_gbs"] * 1e9), flops / (peak * 1e12)) * 1e3
 
+    # the timed path's core summary, before the side measurements reuse `core`
+    core_info = {"eps_rel": eps, "eps_abs": core.eps_abs, "c_norm_est": core.c_norm_est,
+                 "k": core.k, "sgn": core.sgn, "rinv_est": core.rinv_est}
     extras = {}
     if not a.no_extras and rank == 0:
         extras = side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mode, ws, AX, YtA, core, peaks)
@@ -376,9 +379,8 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks,
             "quantize_ms": quantize_ms,
-            "eps_rel": eps, "eps_abs": core.eps_abs, "c_norm_est": core.c_norm_est,
-            "k": core.k, "sgn": core.sgn, "rinv_est": core.rinv_est,
         }
+        line.update(core_info)
         line.update(extras)
         print(json.dumps(line), flush=True)
     if dist:

@@ -1058,7 +1058,8 @@ constexpr int CD_MAX_R = 4096;
 
 __host__ __device__ inline int cd_rows_per(int r, int cs) { return ((r + cs - 1) / cs + 31) / 32 * 32; }
 __host__ __device__ inline size_t cd_smem(int r, int cs) {
-    return sizeof(double) * (2 * static_cast<size_t>(r) + cd_rows_per(r, cs) + 64 + 32 + 32 * 33 + 8);
+    const size_t rp = cd_rows_per(r, cs);
+    return sizeof(double) * (2 * static_cast<size_t>(r) + rp + 64 + 32 + 32 * 33 + 8 + (rp / 32) * 32 * 33);
 }
 
 __global__ void __launch_bounds__(CD_THREADS) core_diag_cluster_kernel(const double* R, long long ldr, int r,
@@ -1078,6 +1079,7 @@ __global__ void __launch_bounds__(CD_THREADS) core_diag_cluster_kernel(const dou
     double* ybuf = blk + 64;     // [32] local copy of the solved block
     double* Rb = ybuf + 32;      // [32][33] diagonal block (owner)
     double* part = Rb + 32 * 33; // [8] partial norms, double-buffered
+    double* Xinv = part + 8;     // [rp/32][32][33] inverses of the owned diagonal blocks
     __shared__ int s_kmin;
     const int s0 = rank * rp;
     const int s1 = min(r, s0 + rp);
@@ -1170,69 +1172,95 @@ __global__ void __launch_bounds__(CD_THREADS) core_diag_cluster_kernel(const dou
     }
 
     // ---- ||R^{-1}||_2 (power iteration on R^{-1} R^{-T} from the all-ones vector)
+    // Blocked substitution over 32-row blocks.  Each CTA first inverts the
+    // diagonal blocks it owns (once, in shared memory), so a block step is a
+    // 32 x 32 matrix-vector product instead of a 32-step dependent chain.
     const int nb = (r + 31) / 32;
+    for (int ob = warp; ob * 32 < s1 - s0; ob += CD_WARPS) {
+        const int j0 = s0 + ob * 32, jb = min(32, r - j0);
+        double* X = Xinv + ob * 32 * 33;
+        // load D (identity padding beyond jb), then invert in place: rows from the
+        // bottom, X[i][j] = (delta_ij - sum_{i<k<=j} D[i][k] X[k][j]) / D[i][i]
+#pragma unroll 4
+        for (int a = 0; a < 32; ++a)
+            X[a * 33 + lane] = (a < jb && lane < jb) ? (lane >= a ? R[static_cast<long long>(j0 + a) * ldr + j0 + lane] : 0.0)
+                                                     : (a == lane ? 1.0 : 0.0);
+        __syncwarp();
+        const double rdl = 1.0 / X[lane * 33 + lane];
+        for (int i = 31; i >= 0; --i) {
+            double acc = lane == i ? 1.0 : 0.0;
+            for (int k = i + 1; k <= lane; ++k) acc = fma(-X[i * 33 + k], X[k * 33 + lane], acc);
+            const double rdi = __shfl_sync(0xffffffffu, rdl, i);   // every lane takes part
+            const double xi = lane >= i ? acc * rdi : 0.0;
+            __syncwarp();
+            X[i * 33 + lane] = xi;
+            __syncwarp();
+        }
+    }
     for (int i = s0 + tid; i < s1; i += CD_THREADS) loc[i - s0] = inv;
     __syncthreads();
     double est = 0.0;
+    const int ra = tid >> 4, rpart = tid & 15;   // block product: row ra, k = rpart, rpart + 16
+    const int urow = tid >> 2, uq = tid & 3;      // updates: 4 lanes per row, 8 terms each
     for (int it = 0; it < iters; ++it) {
         for (int pass = 0; pass < 2; ++pass) {   // pass 0: R^T y = z; pass 1: R w = y
             for (int bi = 0; bi < nb; ++bi) {
                 const int b = pass == 0 ? bi : nb - 1 - bi;
                 const int j0 = b * 32, jb = min(32, r - j0);
                 const int owner = j0 / rp;
-                if (rank == owner && warp == 0) {
+                if (rank == owner) {
+                    const double* X = Xinv + ((j0 - s0) >> 5) * 32 * 33;
+                    const int k0 = rpart, k1 = rpart + 16;
+                    const double z0 = k0 < jb ? loc[j0 - s0 + k0] : 0.0;
+                    const double z1 = k1 < jb ? loc[j0 - s0 + k1] : 0.0;
+                    // pass 0: y = X^T z (X upper); pass 1: w = X y
+                    double acc = pass == 0 ? fma(X[k0 * 33 + ra], z0, X[k1 * 33 + ra] * z1)
+                                           : fma(X[ra * 33 + k0], z0, X[ra * 33 + k1] * z1);
 #pragma unroll
-                    for (int a = 0; a < 32; ++a)   // 32 independent loads in flight
-                        Rb[a * 33 + lane] =
-                            (a < jb && lane < jb) ? R[static_cast<long long>(j0 + a) * ldr + j0 + lane] : 0.0;
-                    __syncwarp();
-                    const double rdl = lane < jb ? 1.0 / Rb[lane * 33 + lane] : 0.0;   // reciprocal diagonal
-                    double zl = lane < jb ? loc[j0 - s0 + lane] : 0.0;
-                    if (pass == 0) {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            if (i < jb) {
-                                const double yi = __shfl_sync(0xffffffffu, zl, i) * __shfl_sync(0xffffffffu, rdl, i);
-                                if (lane == i) zl = yi;
-                                if (lane > i && lane < jb) zl = fma(-Rb[i * 33 + lane], yi, zl);
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 31; i >= 0; --i) {
-                            if (i < jb) {
-                                const double wi = __shfl_sync(0xffffffffu, zl, i) * __shfl_sync(0xffffffffu, rdl, i);
-                                if (lane == i) zl = wi;
-                                if (lane < i) zl = fma(-Rb[lane * 33 + i], wi, zl);
-                            }
-                        }
-                    }
+                    for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    __syncthreads();   // every block-product read of loc is done
                     // buffer alternates with (b + pass): consecutive blocks, including the
                     // last block of one pass and the first of the next, never share a slot
-                    if (lane < jb) {
-                        loc[j0 - s0 + lane] = zl;
-                        blk[((b + pass) & 1) * 32 + lane] = zl;
+                    if (rpart == 0 && ra < jb) {
+                        loc[j0 - s0 + ra] = acc;
+                        blk[((b + pass) & 1) * 32 + ra] = acc;
                     }
                 }
                 cluster.sync();
                 if (tid < jb) ybuf[tid] = cluster.map_shared_rank(blk, owner)[((b + pass) & 1) * 32 + tid];
                 __syncthreads();
                 if (pass == 0) {   // z_j -= sum_{i in block} R[i][j] y_i, own rows j after the block
-                    for (int j = max(s0, j0 + jb) + tid; j < s1; j += CD_THREADS) {
-                        double acc = loc[j - s0];
+                    const int jlo = max(s0, j0 + jb);
+                    for (int base = jlo; base < s1; base += CD_THREADS / 4) {
+                        const int j = base + urow;
+                        double acc = 0.0;
+                        if (j < s1) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            if (i < jb) acc = fma(-R[static_cast<long long>(j0 + i) * ldr + j], ybuf[i], acc);
-                        loc[j - s0] = acc;
+                            for (int t = 0; t < 8; ++t) {
+                                const int i = uq * 8 + t;
+                                if (i < jb) acc = fma(R[static_cast<long long>(j0 + i) * ldr + j], ybuf[i], acc);
+                            }
+                        }
+                        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                        if (j < s1 && uq == 0) loc[j - s0] -= acc;
                     }
                 } else {           // y_i -= sum_{j in block} R[i][j] w_j, own rows i before the block
-                    for (int i = s0 + tid; i < min(s1, j0); i += CD_THREADS) {
-                        double acc = loc[i - s0];
-                        const double* rr = R + static_cast<long long>(i) * ldr + j0;
+                    const int ihi = min(s1, j0);
+                    for (int base = s0; base < ihi; base += CD_THREADS / 4) {
+                        const int i = base + urow;
+                        double acc = 0.0;
+                        if (i < ihi) {
+                            const double* rr = R + static_cast<long long>(i) * ldr + j0;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j < jb) acc = fma(-rr[j], ybuf[j], acc);
-                        loc[i - s0] = acc;
+                            for (int t = 0; t < 8; ++t) {
+                                const int j = uq * 8 + t;
+                                if (j < jb) acc = fma(rr[j], ybuf[j], acc);
+                            }
+                        }
+                        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                        if (i < ihi && uq == 0) loc[i - s0] -= acc;
                     }
                 }
                 __syncthreads();
