@@ -353,6 +353,61 @@ def split_bf16(x):
     return hi, lo
 
 
+E4M3_MAX = 448.0        # largest finite e4m3 value: (1 + 6/8) * 2^8
+E4M3_TILE = 128         # edge of the square tiles that share one scale
+
+
+def e4m3_round(y):
+    """Round FP32 values to the nearest e4m3 value, ties to even, saturating at
+    +-448; returns the exact FP64 values.
+
+    e4m3: 1 sign bit, 4 exponent bits (bias 7), 3 mantissa bits, no infinities.
+    Normal values |v| >= 2^-6 are spaced 2^(floor(log2 |v|) - 3) apart, the
+    subnormals below 2^-6 are multiples of 2^-9.  Rounding is done on the
+    magnitude divided by that spacing (an exact power-of-two division), with
+    numpy's round-half-to-even."""
+    y = np.asarray(y, np.float32).astype(np.float64)
+    a = np.abs(y)
+    _, E = np.frexp(a)                         # a = m 2^E, m in [0.5, 1): floor(log2 a) = E - 1
+    qexp = np.maximum(E - 1, -6) - 3
+    q = np.ldexp(1.0, qexp)
+    v = np.minimum(np.round(a / q) * q, E4M3_MAX)
+    return np.where(y < 0, -v, v)
+
+
+def e4m3_tile_exponent(amax):
+    """Power-of-two scale of a tile: the smallest integer e with amax <= 448 * 2^e
+    (0 for an all-zero tile), kept within the UE8M0 range [-127, 127].  With
+    amax = m 2^E, m in [0.5, 1), and 448 = 0.875 * 2^9 this is E - 9 when
+    m <= 0.875, else E - 8."""
+    amax = np.asarray(amax, np.float64)
+    m, E = np.frexp(amax)
+    e = np.clip(np.where(m <= 0.875, E - 9, E - 8), -127, 127)   # the UE8M0 range
+    return np.where(amax > 0, e, 0).astype(np.int64)
+
+
+def quantize_e4m3_tiles(x, tile=E4M3_TILE):
+    """e4m3 storage with one power-of-two scale per tile x tile block.
+
+    x -> FP32 (round to nearest even) -> per tile e = e4m3_tile_exponent(max |x32|)
+    -> y = x32 * 2^-e in FP32 -> e4m3_round(y).  Returns (values, exps): the exact
+    FP64 values code * 2^e the tensor cores multiply, and the integer exponent of
+    every tile (row-major over tiles; the UE8M0 byte is e + 127)."""
+    x32 = np.asarray(x, np.float64).astype(np.float32)
+    rows, cols = x32.shape
+    tr, tc = -(-rows // tile), -(-cols // tile)
+    exps = np.zeros((tr, tc), np.int64)
+    out = np.zeros((rows, cols), np.float64)
+    for i in range(tr):
+        for j in range(tc):
+            blk = x32[i * tile:(i + 1) * tile, j * tile:(j + 1) * tile]
+            e = int(e4m3_tile_exponent(np.max(np.abs(blk).astype(np.float64))) if blk.size else 0)
+            exps[i, j] = e
+            y = (blk * np.float32(2.0 ** -e)).astype(np.float32)
+            out[i * tile:(i + 1) * tile, j * tile:(j + 1) * tile] = e4m3_round(y) * 2.0 ** e
+    return out, exps
+
+
 def scale_eps(A_norm2, X_norm2, Y_norm2, u):
     """eps = 10 u ||A|| ||X|| ||Y||, the scale-consistent threshold (Section 4.1's
     'eps = 10u' for ||A|| = 1 and O(1) sketches, rescaled to the actual norms)."""

@@ -150,6 +150,32 @@ def test_fp64_core_qr_parity(gn, H):
     assert core.k == r and core.sgn == 0
 
 
+def test_fp64_core_full_size(gn, H):
+    """The bench's core shape, (r+l) x r = 1500 x 1000 in FP64, mode AUTO with
+    relative eps: Q, R against the oracle's Householder QR (31 panels with
+    look-ahead, WY updates of every width); the detector's ||R^{-1}|| and ||C||
+    estimates against the oracle's power iterations on the same R (two 32-row
+    blocks per CTA in the clustered detector)."""
+    r, l, n = 1000, 500, 1100
+    rng = np.random.default_rng(11)
+    YtA = rng.standard_normal((r + l, n))
+    X = rng.standard_normal((n, r)) * (0.996 ** np.arange(r))[None, :]
+    c = O.core(YtA, X, 10 * O.U64, O.AUTO, eps_relative=True, diag_iters=6)
+    ws = H.workspace(r + l, n, r, l, gn.F64)
+    core = _core_tensors(gn, r, l)
+    H.core(cu(YtA), cu(X), 10 * O.U64, gn.AUTO | gn.EPS_RELATIVE, core, ws)
+    assert H.sync_status() == 0
+    assert rel(npy(core.C), c["C"]) <= 1e-13
+    kappa = np.linalg.cond(c["R"])
+    tol = max(1e-11, 50 * kappa * 1.1e-16)
+    assert rel(npy(core.R), c["R"]) <= tol
+    assert rel(npy(core.Q), c["Q"]) <= tol
+    Rg = npy(core.R)
+    assert abs(core.rinv_est - O.rinv_norm_estimate(Rg, iters=6)) <= 1e-8 * core.rinv_est
+    assert abs(core.c_norm_est - O.norm2_estimate(Rg, iters=6)) <= 1e-10 * core.c_norm_est
+    assert core.k == c["k"] == r and core.sgn == int(c["sgn"]) == 0
+
+
 @pytest.mark.parametrize("mode", ["plain", "auto"])
 def test_fp64_gn_config1(gn, H, mode):
     """The 1000 x 500 geometric case: factors and A_hat at 1e-10."""

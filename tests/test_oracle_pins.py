@@ -387,3 +387,74 @@ def test_split_bf16_is_accurate_to_16_bits():
     assert np.all(np.abs(hi + lo - f) <= 2.0 ** -16 * np.abs(f) + 1e-300)
     assert np.array_equal(O.quantize_bf16(hi), hi)
     assert np.array_equal(O.quantize_bf16(lo), lo)
+
+
+def _e4m3_values():
+    """Every non-negative finite e4m3 value, built from the format's fields:
+    exponent field f (bias 7), mantissa field t; f = 0 is subnormal (t/8 2^-6);
+    f = 15, t = 7 is NaN."""
+    vals = []
+    for f in range(16):
+        for t in range(8):
+            if f == 15 and t == 7:
+                continue
+            vals.append((t / 8.0) * 2.0 ** -6 if f == 0 else (1 + t / 8.0) * 2.0 ** (f - 7))
+    return np.array(vals)
+
+
+def test_e4m3_round_fixed_points_and_ties():
+    """Representable values round to themselves; midpoints go to the neighbour
+    with the even mantissa field; anything off the midpoint goes to the nearer."""
+    v = _e4m3_values()
+    assert v.max() == O.E4M3_MAX and len(v) == 127
+    assert np.array_equal(O.e4m3_round(v), v)
+    assert np.array_equal(O.e4m3_round(-v), -v)
+    lo, hi = v[:-1], v[1:]
+    mid = (lo + hi) / 2
+    even_is_lo = (np.arange(len(lo)) % 2) == 0      # codes 0, 1, 2 ...: mantissa parity follows the index
+    assert np.array_equal(O.e4m3_round(mid), np.where(even_is_lo, lo, hi))
+    gap = hi - lo
+    assert np.array_equal(O.e4m3_round(mid - gap / 64), lo)
+    assert np.array_equal(O.e4m3_round(mid + gap / 64), hi)
+    assert O.e4m3_round(np.float32(460.0)) == 448.0       # below the 464 midpoint
+    assert O.e4m3_round(np.float32(470.0)) == 448.0       # would round to 480: saturates
+    assert O.e4m3_round(np.float32(-1e6)) == -448.0
+    assert O.e4m3_round(np.float32(2.0 ** -11)) == 0.0    # below half the smallest subnormal
+
+
+def test_e4m3_round_against_torch():
+    """An independent implementation: torch's float8_e4m3fn cast (round to
+    nearest even) on in-range FP32 values."""
+    import torch
+    rng = np.random.default_rng(8)
+    y = np.concatenate([rng.uniform(-448, 448, 20000), rng.standard_normal(20000) * 0.01]).astype(np.float32)
+    ref = torch.tensor(y).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(O.e4m3_round(y), ref)
+
+
+def test_e4m3_tile_scale_rule():
+    """The scale is the smallest power of two that brings the tile maximum to at
+    most 448; every stored value is then an e4m3 value times 2^e."""
+    assert int(O.e4m3_tile_exponent(448.0)) == 0
+    assert int(O.e4m3_tile_exponent(448.0 * (1 + 2.0 ** -20))) == 1
+    assert int(O.e4m3_tile_exponent(449.0)) == 1
+    assert int(O.e4m3_tile_exponent(224.0)) == -1
+    assert int(O.e4m3_tile_exponent(448.0 * 2.0 ** -30)) == -30
+    assert int(O.e4m3_tile_exponent(0.0)) == 0
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((300, 260)) * np.exp(rng.uniform(-8, 8, (300, 1)))
+    q, e = O.quantize_e4m3_tiles(x)
+    assert e.shape == (3, 3)
+    vals = set(_e4m3_values().tolist())
+    x32 = x.astype(np.float32).astype(np.float64)
+    for i in range(3):
+        for j in range(3):
+            blk = q[i * 128:(i + 1) * 128, j * 128:(j + 1) * 128] / 2.0 ** e[i, j]
+            assert set(np.abs(blk).ravel().tolist()) <= vals
+            amax = np.abs(x32[i * 128:(i + 1) * 128, j * 128:(j + 1) * 128]).max()
+            assert amax <= 448.0 * 2.0 ** e[i, j] and amax > 448.0 * 2.0 ** (e[i, j] - 1)
+            # half a quantum: 2^-4 relative in the normal range, 2^-10 2^e below it
+            err = np.abs(q[i * 128:(i + 1) * 128, j * 128:(j + 1) * 128] - x32[i * 128:(i + 1) * 128, j * 128:(j + 1) * 128])
+            bound = np.maximum(2.0 ** -4 * np.abs(x32[i * 128:(i + 1) * 128, j * 128:(j + 1) * 128]),
+                               2.0 ** (e[i, j] - 10))
+            assert np.all(err <= bound)
