@@ -439,6 +439,37 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
                          "err": err_of(AX, YtA, core)}
     del Ahi, Alo
 
+    # e4m3 path: one power-of-two scale per 128 x 128 tile, block-scaled MMAs
+    q0, q1 = ev(), ev()
+    q0.record(stream)
+    A8 = H.quantize_e4m3(A64)
+    X8 = H.quantize_e4m3(X64, data=False)
+    Y8 = H.quantize_e4m3(Y64, data=False)
+    q1.record(stream)
+    ws8 = H.workspace(m, n, r, l, gn.E4M3)
+    H.sketch(A8, X8, Y8, AX, YtA, ws8)
+    H.core(YtA, X8, eps, mode, core, ws8)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for _ in range(reps):
+        k0.record(stream)
+        H.sketch(A8, X8, Y8, AX, YtA, ws8)
+        k1.record(stream)
+        H.core(YtA, X8, eps, mode, core, ws8)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f8_ms = e0.elapsed_time(e1) / reps
+    f8_sketch_ms = k0.elapsed_time(k1)
+    fl = 2.0 * m * n * (2 * r + l)
+    peak8 = 2.0 * peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])   # nominal e4m3 / bf16 ratio
+    out["fp8_e4m3"] = {"approx_per_s": 1e3 / f8_ms, "ms_per_step": f8_ms, "sketch_ms": f8_sketch_ms,
+                       "sketch_tflops": fl / (f8_sketch_ms / 1e3) / 1e12,
+                       "sketch_frac": fl / (f8_sketch_ms / 1e3) / 1e12 / peak8,
+                       "peak_tflops": peak8, "peak_kind": "2 x measured bf16 sustained (nominal ratio)",
+                       "quantize_ms": q0.elapsed_time(q1), "k": core.k, "err": err_of(AX, YtA, core)}
+    del A8, X8, Y8, ws8
+
     # plain FP64 GPU path on the same matrix (one step)
     AX64 = torch.empty(m, r, dtype=torch.float64, device=dev)
     YtA64 = torch.empty(r + l, n, dtype=torch.float64, device=dev)

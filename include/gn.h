@@ -55,7 +55,9 @@ typedef enum {
     GN_F64 = 0,     /* double */
     GN_F32 = 1,     /* float */
     GN_BF16 = 2,    /* bfloat16 (2 bytes) */
-    GN_BF16X2 = 3   /* split bfloat16: value = data + lo, both bf16, same layout */
+    GN_BF16X2 = 3,  /* split bfloat16: value = data + lo, both bf16, same layout */
+    GN_E4M3 = 4     /* FP8 e4m3 (1 byte) with one power-of-two scale per 128 x 128
+                       tile: value = e4m3(data) * 2^(scale byte - 127) (gn_mat.scale) */
 } gn_dtype;
 
 typedef enum {
@@ -75,6 +77,16 @@ typedef struct {
     int64_t cols;
     int64_t ld;      /* leading dimension in elements, >= cols */
     int32_t dtype;   /* gn_dtype */
+    /* GN_E4M3 only (NULL / 0 otherwise):
+     *   scale : device, ceil(rows/128) x ceil(cols/128) bytes, row-major over
+     *           tiles; byte = e + 127 (UE8M0) for the tile's scale 2^e.
+     *   data_t: device, the transpose (cols x rows, e4m3, leading dimension
+     *           ld_t) under the same scales (its tile (j, i) is tile (i, j)).
+     * The tensor cores read every e4m3 operand K-major, so the sketch uses
+     * A.data and A.data_t, X.data_t (r x n) and Y.data_t ((r+l) x m). */
+    uint8_t* scale;
+    void* data_t;
+    int64_t ld_t;
 } gn_mat;
 
 /* The small core produced by gn_core().  Q, R, Q2, R2, C are caller-allocated
@@ -149,7 +161,14 @@ gn_status gn_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l,
  * src: GN_F64 or GN_F32 matrix; dst: same rows/cols, dtype GN_BF16 (round to
  * nearest even via FP32) or GN_BF16X2 (dst.data = bf16(x32), dst.lo =
  * bf16(x32 - hi), x32 = fp32(x)).  dst.ld must be a multiple of 8 and the
- * data (and lo) pointers 16-byte aligned, the layout TMA needs. */
+ * data (and lo) pointers 16-byte aligned, the layout TMA needs.
+ * dst GN_E4M3: per 128 x 128 tile, e = the smallest integer with
+ * max|x32| <= 448 * 2^e (0 for a zero tile, clamped to [-127, 127]), and each
+ * element becomes e4m3(x32 * 2^-e), rounded to nearest even, saturating.
+ * Writes dst.scale (required) and dst.data and / or dst.data_t (either may be
+ * NULL); ld and ld_t multiples of 16, pointers 16-byte aligned.  The paper
+ * fixes no precision for the sketches (any well-conditioned O(1) sketch
+ * works, Section 4); the per-tile scaling is this library's. */
 gn_status gn_quantize(gn_handle h, const gn_mat* src, gn_mat* dst);
 
 /* The two sketches of Algorithm 2, step 2: AX (m x r) and Y^T A ((r+l) x n).
@@ -158,6 +177,9 @@ gn_status gn_quantize(gn_handle h, const gn_mat* src, gn_mat* dst);
  *   GN_BF16 / GN_BF16X2 A with GN_BF16 X, Y: one launch of the tcgen05
  *     tensor-core kernel, FP32 accumulation; AX, YtA are GN_F32.  Operand
  *     ld must be a multiple of 8, bases 16-byte aligned (GN_ERR_ALIGNMENT).
+ *   GN_E4M3 A, X, Y (with data_t and scale as described at gn_mat): block-
+ *     scaled e4m3 tensor-core MMAs (the tile scales as UE8M0 scale factors),
+ *     FP32 accumulation; AX, YtA are GN_F32; ld / ld_t multiples of 16.
  * Outputs are overwritten (no accumulation into them). */
 gn_status gn_sketch(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,
                     gn_mat* AX, gn_mat* YtA, void* ws, size_t ws_bytes);

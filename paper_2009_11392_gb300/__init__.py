@@ -27,7 +27,7 @@ __all__ = [
     "PLAIN", "SGN", "AUTO", "EPS_RELATIVE", "ABI_SYMBOLS", "mat", "round8", "padded",
 ]
 
-F64, F32, BF16, BF16X2 = 0, 1, 2, 3
+F64, F32, BF16, BF16X2, E4M3 = 0, 1, 2, 3, 4
 PLAIN, SGN, AUTO = 0, 1, 2
 EPS_RELATIVE = 0x100
 
@@ -43,7 +43,8 @@ ABI_SYMBOLS = (
 
 class GnMat(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("rows", ctypes.c_int64),
-                ("cols", ctypes.c_int64), ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32)]
+                ("cols", ctypes.c_int64), ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("scale", ctypes.c_void_p), ("data_t", ctypes.c_void_p), ("ld_t", ctypes.c_int64)]
 
 
 class GnProblem(ctypes.Structure):
@@ -134,8 +135,11 @@ def round8(x: int) -> int:
     return (x + 7) // 8 * 8
 
 
-def mat(t: torch.Tensor, lo: torch.Tensor | None = None) -> GnMat:
-    """gn_mat for a row-major 2-D CUDA tensor (stride (ld, 1)); ``lo`` makes it split bf16."""
+def mat(t, lo: torch.Tensor | None = None) -> GnMat:
+    """gn_mat for a row-major 2-D CUDA tensor (stride (ld, 1)); ``lo`` makes it
+    split bf16; an E4M3Mat maps to its e4m3 description."""
+    if isinstance(t, E4M3Mat):
+        return t.gnmat()
     if t.dim() != 2 or t.stride(1) != 1:
         raise ValueError("operands must be 2-D row-major (stride(1) == 1)")
     if not t.is_cuda:
@@ -151,6 +155,42 @@ def mat(t: torch.Tensor, lo: torch.Tensor | None = None) -> GnMat:
         m.lo = lo.data_ptr()
         m.dtype = BF16X2
     return m
+
+
+@dataclass
+class E4M3Mat:
+    """An e4m3 operand with one power-of-two scale per 128 x 128 tile.
+
+    ``data`` (rows x cols) and ``data_t`` (cols x rows) hold the codes as uint8
+    views with leading dimensions that are multiples of 16 (either may be None);
+    ``scale`` holds one UE8M0 byte (exponent + 127) per tile, row-major over the
+    tiles of the rows x cols matrix."""
+    rows: int
+    cols: int
+    scale: torch.Tensor
+    data: torch.Tensor | None = None
+    data_t: torch.Tensor | None = None
+
+    def gnmat(self) -> "GnMat":
+        m = GnMat(self.data.data_ptr() if self.data is not None else 0, 0, self.rows, self.cols,
+                  self.data.stride(0) if self.data is not None else 0, E4M3)
+        m.scale = self.scale.data_ptr()
+        if self.data_t is not None:
+            m.data_t = self.data_t.data_ptr()
+            m.ld_t = self.data_t.stride(0)
+        return m
+
+    def values(self) -> torch.Tensor:
+        """The FP64 values code * 2^e (rows x cols) on the device, from ``data``
+        or ``data_t``."""
+        # 2^e exactly, from the FP64 bit pattern (a power function need not be exact)
+        sc = ((self.scale.to(torch.int64) - 127 + 1023) << 52).view(torch.float64)
+        sc = sc.repeat_interleave(128, 0).repeat_interleave(128, 1)[: self.rows, : self.cols]
+        if self.data is not None:
+            v = self.data.view(torch.float8_e4m3fn).to(torch.float64)
+        else:
+            v = self.data_t.view(torch.float8_e4m3fn).to(torch.float64).t()
+        return v * sc
 
 
 def padded(rows: int, cols: int, dtype, device) -> torch.Tensor:
@@ -243,6 +283,19 @@ class Handle:
         d = mat(hi, lo)
         _check(lib.gn_quantize(self._h, ctypes.byref(mat(src)), ctypes.byref(d)), "gn_quantize")
         return (hi, lo) if split else hi
+
+    def quantize_e4m3(self, src: torch.Tensor, data: bool = True, transposed: bool = True) -> E4M3Mat:
+        """FP64/FP32 -> e4m3 with one power-of-two scale per 128 x 128 tile,
+        row-major (``data``) and / or transposed (``data_t``) codes."""
+        rows, cols = src.shape
+        r16 = lambda x: (x + 15) // 16 * 16
+        sc = torch.empty((rows + 127) // 128, (cols + 127) // 128, dtype=torch.uint8, device=src.device)
+        d = torch.empty(rows, r16(cols), dtype=torch.uint8, device=src.device)[:, :cols] if data else None
+        dt = torch.empty(cols, r16(rows), dtype=torch.uint8, device=src.device)[:, :rows] if transposed else None
+        q = E4M3Mat(rows, cols, sc, d, dt)
+        dst = q.gnmat()
+        _check(lib.gn_quantize(self._h, ctypes.byref(mat(src)), ctypes.byref(dst)), "gn_quantize")
+        return q
 
     def sketch(self, A, X, Y, AX, YtA, ws, A_lo=None):
         _check(lib.gn_sketch(self._h, ctypes.byref(mat(A, A_lo)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),

@@ -24,12 +24,27 @@ constexpr int DIAG_ITERS = 6;
 
 bool valid_dtype(int32_t d) { return d >= GN_F64 && d <= GN_BF16X2; }
 
+long long tiles128(long long x) { return (x + 127) / 128; }
+
 size_t elem_size(int32_t d) {
     switch (d) {
         case GN_F64: return 8;
         case GN_F32: return 4;
         default: return 2;
     }
+}
+
+// An e4m3 operand: scales and at least one orientation, TMA-aligned.
+gn_status check_e4m3(const gn_mat* a, long long rows, long long cols, bool need_data, bool need_t) {
+    if (!a) return GN_ERR_INVALID_ARG;
+    if (a->dtype != GN_E4M3) return GN_ERR_DTYPE;
+    if (a->rows != rows || a->cols != cols) return GN_ERR_SHAPE;
+    if (!a->scale || (need_data && !a->data) || (need_t && !a->data_t) || (!a->data && !a->data_t))
+        return GN_ERR_INVALID_ARG;
+    if (a->data && ((reinterpret_cast<uintptr_t>(a->data) & 15) || a->ld < cols || a->ld % 16)) return GN_ERR_ALIGNMENT;
+    if (a->data_t && ((reinterpret_cast<uintptr_t>(a->data_t) & 15) || a->ld_t < rows || a->ld_t % 16))
+        return GN_ERR_ALIGNMENT;
+    return GN_OK;
 }
 
 gn_status check_mat(const gn_mat* a, long long rows, long long cols) {
@@ -97,6 +112,16 @@ size_t core_ws(long long n, long long r, long long l, int mixed, int sms) {
     size_t inner = std::max(qr_ws_bytes(rl, r, sms), dgemm_ws_bytes(rl, r, n, sms));
     return b + inner + 1024;
 }
+
+// e4m3 sketch: the scale-factor images of A, X and Y (512 bytes per tile).
+size_t sketch_e4m3_ws(long long m, long long n, long long r, long long l) {
+    return align256(512 * static_cast<size_t>(tiles128(m) * tiles128(n))) +
+           align256(512 * static_cast<size_t>(tiles128(n) * tiles128(r))) +
+           align256(512 * static_cast<size_t>(tiles128(m) * tiles128(r + l))) + 1024;
+}
+
+// e4m3 X in the core product: an exact BF16 copy of X^T (r x n) ahead of the core workspace.
+size_t core_e4m3_ws(long long n, long long r) { return align256(sizeof(__nv_bfloat16) * r * round8(n)) + 256; }
 
 size_t factors_ws(long long m, long long r, int sms) { return trsm_ws_bytes(m, r, sms) + dgemm_ws_bytes(m, r, r, sms) + 1024; }
 
@@ -168,6 +193,73 @@ gn_status launch_sketch_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const 
         p.g[1] = t;
     }
     p.ngemm = 2;
+    return tc_launch(h, &p);
+}
+
+// e4m3 sketch: both products from K-major operands in one block-scaled launch.
+//   AX   = A (m x n) . (X^T)^T     : A operand A.data, B operand X.data_t (r x n)
+//   Y^T A = (Y^T) . (A^T)^T        : A operand Y.data_t ((r+l) x m), B operand A.data_t (n x m)
+gn_status launch_sketch_e4m3(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* AX,
+                             gn_mat* YtA, void* ws, size_t ws_bytes) {
+    const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols;
+    Carve cv{static_cast<char*>(ws), ws_bytes, 0, true};
+    const long long tA = tiles128(m) * tiles128(n), tX = tiles128(n) * tiles128(r), tY = tiles128(m) * tiles128(rl);
+    uint8_t* imA = cv.take<uint8_t>(512 * tA);
+    uint8_t* imX = cv.take<uint8_t>(512 * tX);
+    uint8_t* imY = cv.take<uint8_t>(512 * tY);
+    if (!cv.ok) return GN_ERR_WORKSPACE;
+    GN_TRY(e4m3_sf_image(h, A->scale, tA, imA));
+    GN_TRY(e4m3_sf_image(h, X->scale, tX, imX));
+    GN_TRY(e4m3_sf_image(h, Y->scale, tY, imY));
+    TcParams p;
+    memset(&p, 0, sizeof(p));
+    GN_TRY(tc_make_map_e4m3(&p.maps[0], A->data, m, n, A->ld, 128));
+    GN_TRY(tc_make_map_e4m3(&p.maps[1], X->data_t, r, n, X->ld_t, 128));
+    GN_TRY(tc_make_map_e4m3(&p.maps[2], Y->data_t, rl, m, Y->ld_t, 128));
+    GN_TRY(tc_make_map_e4m3(&p.maps[3], A->data_t, n, m, A->ld_t, 128));
+    TcGemm& g0 = p.g[0];
+    g0.M = static_cast<int>(m);
+    g0.N = static_cast<int>(r);
+    g0.K = static_cast<int>(n);
+    g0.bn = 128;
+    g0.nsrc = 1;
+    g0.a_map[0] = 0;
+    g0.b_map[0] = 1;
+    g0.D = static_cast<float*>(AX->data);
+    g0.ldd = AX->ld;
+    g0.sfa = imA;                               // A tile (rb, kb): image (rb, kb)
+    g0.sfa_ld = static_cast<int>(tiles128(n));
+    g0.sfa_tr = 0;
+    g0.sfa_rows = static_cast<int>(tiles128(m));
+    g0.sfb = imX;                               // X^T tile (rb, kb) is X tile (kb, rb)
+    g0.sfb_ld = static_cast<int>(tiles128(r));
+    g0.sfb_tr = 1;
+    g0.sfb_rows = static_cast<int>(tiles128(r));
+    TcGemm& g1 = p.g[1];
+    g1.M = static_cast<int>(rl);
+    g1.N = static_cast<int>(n);
+    g1.K = static_cast<int>(m);
+    g1.bn = 128;
+    g1.nsrc = 1;
+    g1.a_map[0] = 2;
+    g1.b_map[0] = 3;
+    g1.D = static_cast<float*>(YtA->data);
+    g1.ldd = YtA->ld;
+    g1.sfa = imY;                               // Y^T tile (rb, kb) is Y tile (kb, rb)
+    g1.sfa_ld = static_cast<int>(tiles128(rl));
+    g1.sfa_tr = 1;
+    g1.sfa_rows = static_cast<int>(tiles128(rl));
+    g1.sfb = imA;                               // A^T tile (rb, kb) is A tile (kb, rb)
+    g1.sfb_ld = static_cast<int>(tiles128(n));
+    g1.sfb_tr = 1;
+    g1.sfb_rows = static_cast<int>(tiles128(n));
+    if (m >= n) {   // the longer-K GEMM first
+        TcGemm t = p.g[0];
+        p.g[0] = p.g[1];
+        p.g[1] = t;
+    }
+    p.ngemm = 2;
+    p.f8 = 1;
     return tc_launch(h, &p);
 }
 
@@ -283,11 +375,13 @@ gn_status gn_sync_status(gn_handle h) {
 gn_status gn_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t op_dtype, size_t* bytes) {
     if (!bytes) return GN_ERR_INVALID_ARG;
     GN_TRY(check_sizes(m, n, r, l));
-    if (op_dtype != GN_F64 && op_dtype != GN_BF16 && op_dtype != GN_BF16X2) return GN_ERR_DTYPE;
+    if (op_dtype != GN_F64 && op_dtype != GN_BF16 && op_dtype != GN_BF16X2 && op_dtype != GN_E4M3)
+        return GN_ERR_DTYPE;
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int mixed = op_dtype != GN_F64;
-    size_t b = core_ws(n, r, l, mixed, sms);
+    size_t b = core_ws(n, r, l, mixed, sms) + (op_dtype == GN_E4M3 ? core_e4m3_ws(n, r) : 0);
+    if (op_dtype == GN_E4M3) b = std::max(b, sketch_e4m3_ws(m, n, r, l));
     b = std::max(b, factors_ws(m, r, sms));
     b = std::max(b, hmt_ws(m, n, r, sms));
     b = std::max(b, error_ws_bytes(m, n, sms));
@@ -298,6 +392,13 @@ gn_status gn_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t 
 gn_status gn_quantize(gn_handle h, const gn_mat* src, gn_mat* dst) {
     if (!h || !src || !dst) return GN_ERR_INVALID_ARG;
     GN_TRY(check_mat(src, src->rows, src->cols));
+    if (dst->dtype == GN_E4M3) {
+        if (src->dtype != GN_F64 && src->dtype != GN_F32) return GN_ERR_DTYPE;
+        GN_TRY(check_e4m3(dst, src->rows, src->cols, false, false));
+        return quantize_e4m3(h, src->data, src->dtype == GN_F64, src->rows, src->cols, src->ld,
+                             static_cast<uint8_t*>(dst->data), dst->ld, static_cast<uint8_t*>(dst->data_t),
+                             dst->ld_t, dst->scale);
+    }
     GN_TRY(check_mat(dst, src->rows, src->cols));
     if (src->dtype != GN_F64 && src->dtype != GN_F32) return GN_ERR_DTYPE;
     if (dst->dtype != GN_BF16 && dst->dtype != GN_BF16X2) return GN_ERR_DTYPE;
@@ -314,6 +415,16 @@ gn_status gn_sketch(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat*
     if (!Y) return GN_ERR_INVALID_ARG;
     const long long l = Y->cols - r;
     GN_TRY(check_sizes(m, n, r, l));
+    if (A->dtype == GN_E4M3) {
+        GN_TRY(check_e4m3(A, m, n, true, true));
+        GN_TRY(check_e4m3(X, n, r, false, true));
+        GN_TRY(check_e4m3(Y, m, r + l, false, true));
+        GN_TRY(check_mat(AX, m, r));
+        GN_TRY(check_mat(YtA, r + l, n));
+        if (AX->dtype != GN_F32 || YtA->dtype != GN_F32) return GN_ERR_DTYPE;
+        if (!ws || ws_bytes < sketch_e4m3_ws(m, n, r, l)) return GN_ERR_WORKSPACE;
+        return launch_sketch_e4m3(h, A, X, Y, AX, YtA, ws, ws_bytes);
+    }
     GN_TRY(check_mat(A, m, n));
     GN_TRY(check_mat(X, n, r));
     GN_TRY(check_mat(Y, m, r + l));
@@ -351,12 +462,24 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     const long long n = X->rows, r = X->cols, rl = YtA->rows, l = rl - r;
     if (r < 1 || l < 1 || n < r) return GN_ERR_SHAPE;
     GN_TRY(check_mat(YtA, rl, n));
-    GN_TRY(check_mat(X, n, r));
+    const int x8 = X->dtype == GN_E4M3;
+    if (x8) GN_TRY(check_e4m3(X, n, r, false, true));
+    else GN_TRY(check_mat(X, n, r));
     if (!core->Q || !core->R || !core->C || ((mode != GN_MODE_PLAIN) && (!core->Q2 || !core->R2)))
         return GN_ERR_INVALID_ARG;
-    const int mixed = (YtA->dtype == GN_F32 && X->dtype == GN_BF16);
+    const int mixed = (YtA->dtype == GN_F32 && (X->dtype == GN_BF16 || x8));
     const int fp64 = (YtA->dtype == GN_F64 && X->dtype == GN_F64);
     if (!mixed && !fp64) return GN_ERR_DTYPE;
+    // e4m3 X: its exact BF16 transpose (r x n) takes the front of the workspace
+    __nv_bfloat16* xt16 = nullptr;
+    const long long ldx16 = round8(n);
+    if (x8) {
+        const size_t front = core_e4m3_ws(n, r);
+        if (ws_bytes < front) return GN_ERR_WORKSPACE;
+        xt16 = static_cast<__nv_bfloat16*>(ws);
+        ws = static_cast<char*>(ws) + front;
+        ws_bytes -= front;
+    }
     if (ws_bytes < core_ws(n, r, l, mixed, h->sm_count)) return GN_ERR_WORKSPACE;
     core->r = r;
     core->l = l;
@@ -387,14 +510,19 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
         GN_TRY(dgemm(h, rl, r, n, 1.0, static_cast<const double*>(YtA->data), YtA->ld, 0,
                      static_cast<const double*>(X->data), X->ld, 0, 0.0, core->C, r, inner, inner_bytes));
     } else {
-        GN_TRY(check_tma_operand(X));
+        if (!x8) GN_TRY(check_tma_operand(X));
         GN_TRY(split3_bf16(h, static_cast<const float*>(YtA->data), rl, n, YtA->ld, s_hi, s_mid, s_lo, lds));
         TcParams p;
         memset(&p, 0, sizeof(p));
         __nv_bfloat16* sl[3] = {s_hi, s_mid, s_lo};
         float* cl[3] = {c_hi, c_mid, c_lo};
         for (int s = 0; s < 3; ++s) GN_TRY(tc_make_map_bf16(&p.maps[s], sl[s], rl, n, lds, 64, 128));
-        GN_TRY(tc_make_map_bf16(&p.maps[3], X->data, n, r, X->ld, 64, 64));
+        if (x8) {   // X^T in BF16 as a K-major B operand
+            GN_TRY(e4m3_t_to_bf16(h, static_cast<const uint8_t*>(X->data_t), X->ld_t, X->scale, n, r, xt16, ldx16));
+            GN_TRY(tc_make_map_bf16(&p.maps[3], xt16, r, n, ldx16, 64, static_cast<int>(std::min<long long>(256, (r + 63) / 64 * 64))));
+        } else {
+            GN_TRY(tc_make_map_bf16(&p.maps[3], X->data, n, r, X->ld, 64, 64));
+        }
         for (int s = 0; s < 3; ++s) {
             TcGemm& g = p.g[s];
             g.M = static_cast<int>(rl);
@@ -402,7 +530,7 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
             g.K = static_cast<int>(n);
             g.bn = static_cast<int>(std::min<long long>(256, (r + 63) / 64 * 64));
             g.a_mn = 0;
-            g.b_mn = 1;
+            g.b_mn = x8 ? 0 : 1;
             g.nsrc = 1;
             g.a_map[0] = s;
             g.b_map[0] = 3;

@@ -63,6 +63,13 @@ struct TcGemm {
     float* D;
     long long ldd;
     int vec4;                // D rows 16-byte aligned -> float4 stores
+    // e4m3 launches (TcParams::f8): scale-factor images, 512 bytes of the tile's
+    // UE8M0 byte per 128 x 128 tile of the original matrix, row-major over tiles.
+    const uint8_t* sfa;
+    const uint8_t* sfb;
+    int sfa_ld, sfb_ld;      // tiles per row of the image's tile grid
+    int sfa_tr, sfb_tr;      // 1: operand tile (row block rb, k block kb) is image tile (kb, rb)
+    int sfa_rows, sfb_rows;  // operand row blocks (ragged tiles clamp to the last)
 };
 
 struct TcParams {
@@ -74,14 +81,30 @@ struct TcParams {
     int total_tiles;
     int32_t* status;
     unsigned long long wait_limit_ns;
+    int f8;                    // 1: e4m3 operands (K-major, block-scaled MMA, bn = 128)
 };
 
 // Host helpers (gn_tc.cu).
 gn_status tc_make_map_bf16(CUtensorMap* map, const void* base, long long rows, long long cols,
                            long long ld, int box_cols, int box_rows);
+// e4m3 operand: rows x cols bytes, leading dimension ld bytes, 128-byte boxes.
+gn_status tc_make_map_e4m3(CUtensorMap* map, const void* base, long long rows, long long cols,
+                           long long ld, int box_rows);
 gn_status tc_launch(gn_handle h, TcParams* p);
 // Fill tiles_m / tiles_n / kblocks / tile_base / vec4 of one GEMM descriptor.
-gn_status tc_prepare_gemm(TcGemm* G, int tile_base, int mt = 1);
+gn_status tc_prepare_gemm(TcGemm* G, int tile_base, int mt = 1, int f8 = 0);
+
+// e4m3 helpers (gn_fp8.cu).
+// Per 128 x 128 tile of src (FP64 or FP32, rows x cols): scale byte, and the
+// codes row-major (dst, ld) and / or transposed (dst_t, ld_t); either may be null.
+gn_status quantize_e4m3(gn_handle h, const void* src, int src_f64, long long rows, long long cols, long long lds,
+                        uint8_t* dst, long long ld, uint8_t* dst_t, long long ld_t, uint8_t* scale);
+// 512-byte scale-factor image of every tile from its scale byte.
+gn_status e4m3_sf_image(gn_handle h, const uint8_t* scale, long long tiles, uint8_t* image);
+// BF16 copy of the transposed e4m3 operand data_t (cols x rows of the original
+// rows x cols matrix) with the scales applied: exact (3 mantissa bits fit in 8).
+gn_status e4m3_t_to_bf16(gn_handle h, const uint8_t* data_t, long long ld_t, const uint8_t* scale,
+                         long long rows, long long cols, __nv_bfloat16* out, long long ldo);
 // Grouped launch: descriptors (tile_base ascending) and tensor maps already in
 // device memory; any number of GEMMs.
 gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, const CUtensorMap* dev_maps,

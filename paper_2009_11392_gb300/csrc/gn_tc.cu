@@ -38,16 +38,27 @@ constexpr int NUM_THREADS = 192;
 // main loop).  MT = 2: 256 x bn tiles whose two MMAs share each B stage (a third
 // fewer operand bytes per flop), 3 stages of 64 KB, one accumulator buffer of
 // 2 x 256 columns.
-template <int MT>
+//
+// F8: e4m3 operands, both K-major, 128 elements (128 bytes) per stage row; the
+// MMAs are block-scaled (kind::mxf8f6f4, one UE8M0 scale per 32 K-elements of a
+// row or column), bn = 128 so that every MMA covers whole 128 x 128 scale
+// tiles.  Each stage also carries the scale-factor images of its operand tiles
+// (512 bytes each: the A tile of every M half, then the B tile), copied into
+// tensor memory with tcgen05.cp before the stage's MMAs.  Because each image
+// holds one byte value, every scale-factor cell an MMA reads holds the tile's
+// scale whatever cell it reads.  Accumulators use columns [0, 128) and
+// [256, 384); the scale factors of stage s sit at columns 384 + 16 s.
+template <int MT, bool F8 = false>
 struct Cfg {
     static constexpr int STG = MT == 2 ? 3 : 4;
     static constexpr int A_BYTES = MT * BM * BK * 2;
     static constexpr int STAGE = A_BYTES + B_STAGE_BYTES;
     static constexpr int NACC = MT == 2 ? 1 : 2;
     static constexpr int TM = BM * MT;
-    static constexpr int SMEM = STG * STAGE + 1024 + 256;
+    static constexpr int SF_STAGE = F8 ? (MT + 1) * 512 : 0;
+    static constexpr int SMEM = STG * STAGE + 1024 + (F8 ? 1024 + STG * SF_STAGE : 256);
 };
-constexpr int SMEM_BYTES = Cfg<1>::SMEM > Cfg<2>::SMEM ? Cfg<1>::SMEM : Cfg<2>::SMEM;
+constexpr uint32_t SF_TMEM_COL = 384;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -161,6 +172,33 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uin
         : "memory");
 }
 
+// Block-scaled e4m3 MMA: scale factors (UE8M0) for A rows and B columns in
+// tensor memory at sfa / sfb.
+__device__ __forceinline__ void tc_mma_mxf8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%5], [%6], p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(sfa), "r"(sfb)
+        : "memory");
+}
+
+// 32 rows x 16 bytes of shared memory (no swizzle) into tensor-memory columns
+// [taddr, taddr + 4) of all four 32-lane groups.
+__device__ __forceinline__ void tc_cp_32x128b_x4(uint32_t taddr, uint64_t sdesc) {
+    asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
+// Non-tensor bulk copy global -> shared, completing bytes on an mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -186,6 +224,28 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t start, uint32_t lbo, uint
     d |= static_cast<uint64_t>(1) << 46;   // descriptor version for tcgen05
     d |= static_cast<uint64_t>(2) << 61;   // SWIZZLE_128B
     return d;
+}
+
+// No-swizzle descriptor of a 32-row x 16-byte block (8-row core matrices of
+// 128 contiguous bytes, 128 bytes apart).
+__device__ __forceinline__ uint64_t smem_desc_plain(uint32_t start) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((start & 0x3FFFF) >> 4);
+    d |= static_cast<uint64_t>(128 >> 4) << 16;
+    d |= static_cast<uint64_t>(128 >> 4) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    return d;   // layout type 0: no swizzle
+}
+
+// Instruction descriptor, kind::mxf8f6f4 (block-scaled): e4m3 A and B (format
+// code 0), K-major, FP32 accumulator, UE8M0 scale factors; sf ids pick the
+// byte of each 32-bit scale-factor cell.
+__device__ __forceinline__ uint32_t instr_desc_mxf8(int m, int n, int sfa_id, int sfb_id) {
+    return (static_cast<uint32_t>(sfb_id) << 4)     // B scale-factor id
+           | (static_cast<uint32_t>(n >> 3) << 17)   // N / 8
+           | (1u << 23)                              // scale type UE8M0
+           | (static_cast<uint32_t>(m >> 4) << 24)   // M / 16
+           | (static_cast<uint32_t>(sfa_id) << 29);  // A scale-factor id
 }
 
 // Instruction descriptor, kind::f16 with BF16 inputs and an FP32 accumulator.
@@ -256,9 +316,10 @@ __device__ void latch(int32_t* status, int code, int where, volatile int* abort_
 // CL M tiles of one N tile) is split into 64-column boxes, each loaded by one
 // CTA and multicast to all CL; a stage is refilled only after every CTA of the
 // cluster has consumed it (each MMA commit arrives on all CL empty barriers).
-template <bool GROUPED, int CL, int MT>
+template <bool GROUPED, int CL, int MT, bool F8>
 __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __grid_constant__ TcParams p) {
-    using K = Cfg<MT>;
+    using K = Cfg<MT, F8>;
+    constexpr int KE = F8 ? 128 : BK;                     // K elements per stage (128 bytes per row)
     constexpr int STAGES = K::STG;
     constexpr int STAGE_BYTES = K::STAGE;
     constexpr int A_STAGE_BYTES = K::A_BYTES;
@@ -267,6 +328,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
     const uint32_t base = (raw + 1023u) & ~1023u;            // 1024-aligned stage ring
     uint8_t* base_ptr = smem_raw + (base - raw);
     const uint32_t bars = base + STAGES * STAGE_BYTES;        // barrier block
+    const uint32_t sfs = bars + 1024;                         // F8: scale-factor images per stage
     auto full_bar = [&](int s) { return bars + 8u * s; };
     auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
     auto tfull_bar = [&](int a) { return bars + 8u * (2 * STAGES + a); };
@@ -320,7 +382,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                 const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
-                const uint32_t bytes = A_STAGE_BYTES + G.bn * BK * 2;
+                const uint32_t bytes = A_STAGE_BYTES + G.bn * BK * 2 + K::SF_STAGE;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(empty_bar(stage), ephase ^ 1u, limit, abort_flag)) {
                         latch(p.status, GN_ERR_TIMEOUT, 1, abort_flag);
@@ -348,12 +410,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
 #pragma unroll
                     for (int hh = 0; hh < MT; ++hh) {
                         const int m0 = c.tm * K::TM + hh * BM;
-                        if (G.a_mn) {
+                        if (!F8 && G.a_mn) {
                             tma_load_2d(sa + hh * 16384, ma, fb, m0, kk * BK);
                             tma_load_2d(sa + hh * 16384 + 8192, ma, fb, m0 + 64, kk * BK);
                         } else {
-                            tma_load_2d(sa + hh * 16384, ma, fb, kk * BK, m0);
+                            tma_load_2d(sa + hh * 16384, ma, fb, kk * KE, m0);
                         }
+                        if (F8) {   // scale-factor image of this A tile
+                            const int rb = min(m0 / BM, G.sfa_rows - 1);
+                            const long long ti = G.sfa_tr ? static_cast<long long>(kk) * G.sfa_ld + rb
+                                                          : static_cast<long long>(rb) * G.sfa_ld + kk;
+                            bulk_load(sfs + stage * K::SF_STAGE + hh * 512, G.sfa + ti * 512, 512, fb);
+                        }
+                    }
+                    if (F8) {       // and of the B tile (bn = 128: one tile)
+                        const int rb = min(c.tn * G.bn / BM, G.sfb_rows - 1);
+                        const long long ti = G.sfb_tr ? static_cast<long long>(kk) * G.sfb_ld + rb
+                                                      : static_cast<long long>(rb) * G.sfb_ld + kk;
+                        bulk_load(sfs + stage * K::SF_STAGE + MT * 512, G.sfb + ti * 512, 512, fb);
                     }
                     if (CL > 1) {   // B boxes: box j from cluster rank j % CL, multicast to all
                         if (G.b_mn) {
@@ -366,7 +440,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                         for (int j = 0; j < G.bn / 64; ++j)
                             tma_load_2d(sb + 8192 * j, mb, fb, c.tn * G.bn + 64 * j, kk * BK);
                     } else {
-                        tma_load_2d(sb, mb, fb, kk * BK, c.tn * G.bn);
+                        tma_load_2d(sb, mb, fb, kk * KE, c.tn * G.bn);
                     }
                     if (++stage == STAGES) {
                         stage = 0;
@@ -395,7 +469,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                 const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
-                const uint32_t idesc = instr_desc_bf16(BM, G.bn, G.a_mn, G.b_mn);
+                const uint32_t idesc = F8 ? 0u : instr_desc_bf16(BM, G.bn, G.a_mn, G.b_mn);
                 if (!mbar_wait(tempty_bar(acc), aphase ^ 1u, limit, abort_flag)) {
                     latch(p.status, GN_ERR_TIMEOUT, 3, abort_flag);
                     break;
@@ -411,16 +485,36 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     tc_fence_after();
                     const uint32_t sa = base + stage * STAGE_BYTES;
                     const uint32_t sb = sa + A_STAGE_BYTES;
+                    if (F8) {
+                        // scale factors of this stage into tensor memory (ordered
+                        // before the MMAs below: same issuing thread), then
+                        // 4 K-steps of 32 e4m3 (32 bytes) per M half
+                        const uint32_t sfs_s = sfs + stage * K::SF_STAGE;
+                        const uint32_t tsf = tmem_base + SF_TMEM_COL + 16u * stage;
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k) {
-                        const uint64_t bd = G.b_mn ? smem_desc(sb + 2048u * k, 8192u, 1024u)
-                                                   : smem_desc(sb + 32u * k, 16u, 1024u);
+                        for (int hh = 0; hh < MT; ++hh) tc_cp_32x128b_x4(tsf + 4u * hh, smem_desc_plain(sfs_s + 512u * hh));
+                        tc_cp_32x128b_x4(tsf + 8u, smem_desc_plain(sfs_s + 512u * MT));
 #pragma unroll
-                        for (int hh = 0; hh < MT; ++hh) {
-                            const uint32_t sah = sa + 16384u * hh;
-                            const uint64_t ad = G.a_mn ? smem_desc(sah + 2048u * k, 8192u, 1024u)
-                                                       : smem_desc(sah + 32u * k, 16u, 1024u);
-                            tc_mma_bf16(d_tmem + 256u * hh, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                        for (int k = 0; k < 4; ++k) {
+                            const uint64_t bd = smem_desc(sb + 32u * k, 16u, 1024u);
+                            const uint32_t id = instr_desc_mxf8(BM, G.bn, k, k);
+#pragma unroll
+                            for (int hh = 0; hh < MT; ++hh)
+                                tc_mma_mxf8(d_tmem + 256u * hh, smem_desc(sa + 16384u * hh + 32u * k, 16u, 1024u), bd, id,
+                                            tsf + 4u * hh, tsf + 8u, (kb | k) != 0 ? 1u : 0u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < BK / 16; ++k) {
+                            const uint64_t bd = G.b_mn ? smem_desc(sb + 2048u * k, 8192u, 1024u)
+                                                       : smem_desc(sb + 32u * k, 16u, 1024u);
+#pragma unroll
+                            for (int hh = 0; hh < MT; ++hh) {
+                                const uint32_t sah = sa + 16384u * hh;
+                                const uint64_t ad = G.a_mn ? smem_desc(sah + 2048u * k, 8192u, 1024u)
+                                                           : smem_desc(sah + 32u * k, 16u, 1024u);
+                                tc_mma_bf16(d_tmem + 256u * hh, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                            }
                         }
                     }
                     issued_any = true;
@@ -539,23 +633,39 @@ gn_status tc_make_map_bf16(CUtensorMap* map, const void* base, long long rows, l
     return r == CUDA_SUCCESS ? GN_OK : GN_ERR_CUDA;
 }
 
-template <bool GROUPED, int CL, int MT>
+gn_status tc_make_map_e4m3(CUtensorMap* map, const void* base, long long rows, long long cols, long long ld,
+                           int box_rows) {
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || ld % 16 != 0) return GN_ERR_ALIGNMENT;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return GN_ERR_CUDA;
+    memset(map, 0, sizeof(*map));
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld)};
+    cuuint32_t box[2] = {128u, static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GN_OK : GN_ERR_CUDA;
+}
+
+template <bool GROUPED, int CL, int MT, bool F8 = false>
 gn_status launch_cfg(gn_handle h, const TcParams& p, int total_ctiles) {
     static bool attr_set = false;
     if (!attr_set) {
-        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel<GROUPED, CL, MT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MT>::SMEM));
+        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel<GROUPED, CL, MT, F8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MT, F8>::SMEM));
         attr_set = true;
     }
     const int max_clusters = h->sm_count / CL;
     const int clusters = total_ctiles < max_clusters ? total_ctiles : max_clusters;
     if (CL == 1) {
-        tc_multigemm_kernel<GROUPED, CL, MT><<<clusters, NUM_THREADS, Cfg<MT>::SMEM, h->stream>>>(p);
+        tc_multigemm_kernel<GROUPED, CL, MT, F8><<<clusters, NUM_THREADS, Cfg<MT, F8>::SMEM, h->stream>>>(p);
     } else {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(clusters * CL);
         cfg.blockDim = dim3(NUM_THREADS);
-        cfg.dynamicSmemBytes = Cfg<MT>::SMEM;
+        cfg.dynamicSmemBytes = Cfg<MT, F8>::SMEM;
         cfg.stream = h->stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -564,7 +674,7 @@ gn_status launch_cfg(gn_handle h, const TcParams& p, int total_ctiles) {
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_multigemm_kernel<GROUPED, CL, MT>, p));
+        GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_multigemm_kernel<GROUPED, CL, MT, F8>, p));
     }
     count_launch();
     GN_CUDA_TRY(cudaGetLastError());
@@ -586,7 +696,12 @@ int pick_mt(const TcGemm* g, int ngemm, int sm_count) {
 
 gn_status tc_launch(gn_handle h, TcParams* p) {
     const int MT = pick_mt(p->g, p->ngemm, h->sm_count);
-    for (int i = 0; i < p->ngemm; ++i) GN_TRY(tc_prepare_gemm(&p->g[i], 0, MT));
+    for (int i = 0; i < p->ngemm; ++i) {
+        if (p->f8 && (p->g[i].a_mn || p->g[i].b_mn || p->g[i].bn != 128 || p->g[i].nsrc != 1 || !p->g[i].sfa ||
+                      !p->g[i].sfb || p->g[i].sfa_rows < 1 || p->g[i].sfb_rows < 1))
+            return GN_ERR_INVALID_ARG;
+        GN_TRY(tc_prepare_gemm(&p->g[i], 0, MT, p->f8));
+    }
     const int CL = 1;
     int total = 0;
     for (int i = 0; i < p->ngemm; ++i) {
@@ -600,14 +715,16 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
     p->status = h->dstatus;
     p->wait_limit_ns = h->wait_limit_ns;
     if (total == 0) return GN_OK;
+    if (p->f8) return MT == 2 ? launch_cfg<false, 1, 2, true>(h, *p, total) : launch_cfg<false, 1, 1, true>(h, *p, total);
     return MT == 2 ? launch_cfg<false, 1, 2>(h, *p, total) : launch_cfg<false, 1, 1>(h, *p, total);
 }
 
-gn_status tc_prepare_gemm(TcGemm* G, int tile_base, int mt) {
+gn_status tc_prepare_gemm(TcGemm* G, int tile_base, int mt, int f8) {
     if (G->bn < 16 || G->bn > 256 || (G->b_mn && G->bn % 64) || G->bn % 16) return GN_ERR_INVALID_ARG;
+    const int ke = f8 ? 128 : BK;
     G->tiles_m = static_cast<int>((G->M + BM * mt - 1) / (BM * mt));
     G->tiles_n = static_cast<int>((G->N + G->bn - 1) / G->bn);
-    G->kblocks = static_cast<int>((G->K + BK - 1) / BK);
+    G->kblocks = static_cast<int>((G->K + ke - 1) / ke);
     G->tile_base = tile_base;
     G->vec4 = ((reinterpret_cast<uintptr_t>(G->D) & 15) == 0 && G->ldd % 4 == 0) ? 1 : 0;
     return GN_OK;
