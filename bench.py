@@ -52,10 +52,13 @@ def parse():
     ap.add_argument("--r", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="skip split/FP64/error/CPU side measurements")
     ap.add_argument("--cpu-rows", type=int, default=512, help="row sample of the CPU-oracle baseline")
+    ap.add_argument("--op", default="bf16", choices=["bf16", "e4m3"],
+                    help="sketch operand type of the timed step (e4m3: per-128x128-tile scales)")
     return ap.parse_args()
 
 
-def config_dict(a, precision="bf16"):
+def config_dict(a, precision=None):
+    precision = precision or getattr(a, "op", "bf16")
     return {
         "workload": f"GN dense {a.m}x{a.n} low-rank+noise (i^-2, 2000 modes, 1e-8 noise), r={a.r}, "
                     f"l={a.r // 2}, Gaussian sketches, {precision} operands, FP64 core, mode AUTO",
@@ -237,10 +240,17 @@ def main():
     Ab = H.quantize(A64)
     q1.record(stream)
     Xb, Yb = H.quantize(X64), H.quantize(Y64)
+    if a.op == "e4m3":   # the timed step's operands; the BF16 ones serve the side measurements
+        q0.record(stream)
+        Aop = H.quantize_e4m3(A64)
+        q1.record(stream)
+        Xop, Yop = H.quantize_e4m3(X64, data=False), H.quantize_e4m3(Y64, data=False)
+    else:
+        Aop, Xop, Yop = Ab, Xb, Yb
     torch.cuda.synchronize()
     quantize_ms = q0.elapsed_time(q1)
 
-    ws = H.workspace(m, n, r, l, gn.BF16X2)
+    ws = H.workspace(m, n, r, l, gn.E4M3 if a.op == "e4m3" else gn.BF16X2)
     AX = torch.empty(m, r, dtype=torch.float32, device=dev)
     YtA = torch.empty(r + l, n, dtype=torch.float32, device=dev)
     core = gn.Core.empty(r, l, dev)
@@ -248,13 +258,13 @@ def main():
     def step(A_op, A_lo=None, ev=None):
         if ev is not None:
             ev[0].record(stream)
-        H.sketch(A_op, Xb, Yb, AX, YtA, ws, A_lo=A_lo)
+        H.sketch(A_op, Xop, Yop, AX, YtA, ws, A_lo=A_lo)
         if ev is not None:
             ev[1].record(stream)
-        H.core(YtA, Xb, eps, mode, core, ws)
+        H.core(YtA, Xop, eps, mode, core, ws)
 
     for _ in range(a.warmup):
-        step(Ab)
+        step(Aop)
     torch.cuda.synchronize()
     if H.sync_status() != 0:
         raise RuntimeError("device status after warm-up")
@@ -271,7 +281,7 @@ def main():
     launches0 = gn.kernel_launches()
     t0.record(stream)
     for i in range(a.steps):
-        step(Ab, ev=evs[i])
+        step(Aop, ev=evs[i])
     t1.record(stream)
     torch.cuda.synchronize()
     launches = gn.kernel_launches() - launches0
@@ -288,26 +298,30 @@ def main():
     value = world * a.steps / (elapsed_ms / 1e3)
 
     # ---- end to end through the API with host buffers (H2D inputs, D2H outputs)
-    Ah = torch.empty(m, n, dtype=torch.bfloat16, pin_memory=True)
-    Ah.copy_(Ab)
-    Xh = torch.empty(Xb.shape, dtype=torch.bfloat16, pin_memory=True)
-    Xh.copy_(Xb)
-    Yh = torch.empty(Yb.shape, dtype=torch.bfloat16, pin_memory=True)
-    Yh.copy_(Yb)
     outs = [torch.empty(AX.shape, dtype=torch.float32, pin_memory=True),
             torch.empty(YtA.shape, dtype=torch.float32, pin_memory=True),
             torch.empty(core.Q.shape, dtype=torch.float64, pin_memory=True),
             torch.empty(core.R.shape, dtype=torch.float64, pin_memory=True)]
-    h2d = Ah.numel() * 2 + Xh.numel() * 2 + Yh.numel() * 2
     d2h = sum(o.numel() * o.element_size() for o in outs)
-    Ad = gn.padded(m, n, torch.bfloat16, dev)
-    Xd = gn.padded(n, r, torch.bfloat16, dev)
-    Yd = gn.padded(m, r + l, torch.bfloat16, dev)
+    if a.op == "e4m3":
+        # the e4m3 codes (A in both orientations, X^T, Y^T) and the tile scales
+        srcs = [Aop.data, Aop.data_t, Xop.data_t, Yop.data_t, Aop.scale, Xop.scale, Yop.scale]
+        hosts = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in srcs]
+        devs = [torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=dev) for t in srcs]
+        Ad = gn.E4M3Mat(m, n, devs[4], devs[0], devs[1])
+        Xd = gn.E4M3Mat(n, r, devs[5], None, devs[2])
+        Yd = gn.E4M3Mat(m, r + l, devs[6], None, devs[3])
+    else:
+        srcs = [Ab, Xb, Yb]
+        hosts = [torch.empty(t.shape, dtype=torch.bfloat16, pin_memory=True).copy_(t) for t in srcs]
+        devs = [gn.padded(m, n, torch.bfloat16, dev), gn.padded(n, r, torch.bfloat16, dev),
+                gn.padded(m, r + l, torch.bfloat16, dev)]
+        Ad, Xd, Yd = devs
+    h2d = sum(t.numel() * t.element_size() for t in hosts)
 
     def e2e_step():
-        Ad.copy_(Ah, non_blocking=True)
-        Xd.copy_(Xh, non_blocking=True)
-        Yd.copy_(Yh, non_blocking=True)
+        for d_, h_ in zip(devs, hosts):
+            d_.copy_(h_, non_blocking=True)
         H.sketch(Ad, Xd, Yd, AX, YtA, ws)
         H.core(YtA, Xd, eps, mode, core, ws)
         for o, s in zip(outs, (AX, YtA, core.Q, core.R)):
@@ -324,13 +338,14 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / a.steps
-    del Ad, Xd, Yd
+    del Ad, Xd, Yd, devs, hosts
 
     peaks, peak_kind = measured_peaks()
     flops = 2.0 * m * n * (2 * r + l)
     achieved = flops / (sketch_ms / 1e3) / 1e12
-    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-    roof_ms = max(2.0 * m * n / (peaks["hbm_gbs"] * 1e9), flops / (peak * 1e12)) * 1e3
+    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (2.0 if a.op == "e4m3" else 1.0)
+    a_bytes = m * n * (1 if a.op == "e4m3" else 2)
+    roof_ms = max(a_bytes / (peaks["hbm_gbs"] * 1e9), flops / (peak * 1e12)) * 1e3
 
     # the timed path's core summary, before the side measurements reuse `core`
     core_info = {"eps_rel": eps, "eps_abs": core.eps_abs, "c_norm_est": core.c_norm_est,
@@ -354,7 +369,7 @@ def main():
     if os.path.exists(tp):
         try:
             import hashlib
-            t = json.load(open(tp)).get(f"sketch_bf16_{m}x{n}_r{r}")
+            t = json.load(open(tp)).get(f"sketch_{a.op}_{m}x{n}_r{r}")
             src = open(os.path.join(ROOT, "paper_2009_11392_gb300", "csrc", "gn_tc.cu"), "rb").read()
             if t and hashlib.sha256(src).hexdigest()[:16] == t["kernel_sha256_16"]:
                 traffic = t["traffic_bytes"]
@@ -363,15 +378,17 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "metric": METRIC if a.op == "bf16" else METRIC.replace("BF16", "e4m3 block-scaled"),
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded low-rank + noise, Gaussian sketches)",
+            "vs_baseline": None, "dtype": a.op, "data": "synthetic (seeded low-rank + noise, Gaussian sketches)",
             "config": config_dict(a),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "tc_multigemm_kernel (fused AX + Y^T A sketch launch)",
                          "kernel_ms": sketch_ms, "algorithmic_flops": flops,
-                         "peak_kind": f"bf16 sustained, {peak_kind}",
+                         "peak_kind": (f"bf16 sustained, {peak_kind}" if a.op == "bf16" else
+                                       f"2 x bf16 sustained ({peak_kind}; nominal e4m3 / bf16 ratio)"),
                          "step_roofline_ms": roof_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": h2d,
