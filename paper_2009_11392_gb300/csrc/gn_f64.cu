@@ -703,8 +703,9 @@ __host__ __device__ inline size_t wy_smem(int rp, int bn) {
     return sizeof(double) * (static_cast<size_t>(rp) * (WY_JB + 1 + bn + 1) + 3 * WY_JB * bn + WY_JB * WY_JB);
 }
 
-// BN: columns of W per cluster (8, 16, 32 or 64).  Narrow blocks spread a
-// narrow update over more SMs: the kernel is bound by the SM's FP64 rate.
+// BN: columns of W per block (8, 16, 32 or 64).  The grid holds one wave of
+// clusters; cluster c takes column blocks c, c + ncl, ... (its rows of V and
+// op(T) are loaded once).  The kernel is bound by each SM's FP64 rate.
 template <int BN>
 __global__ void __launch_bounds__(WY_THREADS) qr_wy_apply_kernel(double* W, long long ldw, int Mp, int Nw,
                                                                 const double* V, long long ldv, int jb,
@@ -715,9 +716,8 @@ __global__ void __launch_bounds__(WY_THREADS) qr_wy_apply_kernel(double* W, long
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = static_cast<int>(cluster.num_blocks());
     const int rank = static_cast<int>(cluster.block_rank());
-    const int blk = blockIdx.x / cs;
-    const int c0 = blk * BN;
-    const int nbw = min(BN, Nw - c0);
+    const int cid = blockIdx.x / cs, ncl = gridDim.x / cs;
+    const int nblk = (Nw + BN - 1) / BN;
     const int r0 = rank * rp;
     const int nr = max(0, min(rp, Mp - r0));
     extern __shared__ double sm[];
@@ -733,77 +733,81 @@ __global__ void __launch_bounds__(WY_THREADS) qr_wy_apply_kernel(double* W, long
         const int i = e >> 5, a = e & 31;
         Vs[i * (WY_JB + 1) + a] = a < jb ? V[static_cast<long long>(r0 + i) * ldv + a] : 0.0;
     }
-    for (int e = tid; e < nr * BN; e += WY_THREADS) {
-        const int i = e / BN, b = e % BN;
-        Ws[i * (BN + 1) + b] = b < nbw ? W[static_cast<long long>(r0 + i) * ldw + c0 + b] : 0.0;
-    }
     for (int e = tid; e < WY_JB * WY_JB; e += WY_THREADS) {
         const int a = e >> 5, c = e & 31;
         double v = 0.0;
         if (a < jb && c < jb) v = transT ? T[c * jb + a] : T[a * jb + c];
         Ts[e] = v;
     }
-    __syncthreads();
-    // ---- Zp = V_rows^T W_rows,blk: thread -> column b, AU consecutive a
     const int b = tid % BN, ag = tid / BN;
-    {
-        double acc[AU];
-#pragma unroll
-        for (int u = 0; u < AU; ++u) acc[u] = 0.0;
-        for (int i = 0; i < nr; ++i) {
-            const double w = Ws[i * (BN + 1) + b];
-#pragma unroll
-            for (int u = 0; u < AU; ++u) acc[u] = fma(Vs[i * (WY_JB + 1) + ag * AU + u], w, acc[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < AU; ++u) Zp[(ag * AU + u) * BN + b] = acc[u];
-    }
-    cluster.sync();
-    // ---- reduce-scatter: rank k sums rows a in its share of Z over all ranks (rank order)
     const int rows_per_rank = (WY_JB + cs - 1) / cs;
     const int a0 = rank * rows_per_rank, a1 = min(WY_JB, a0 + rows_per_rank);
-    for (int e = tid; e < (a1 - a0) * BN; e += WY_THREADS) {
-        const int a = a0 + e / BN, bb = e % BN;
-        double z = 0.0;
-        for (int k = 0; k < cs; ++k) z += cluster.map_shared_rank(Zp, k)[a * BN + bb];
-        Z[a * BN + bb] = z;
-    }
-    cluster.sync();
-    // ---- all-gather Z
-    for (int e = tid; e < WY_JB * BN; e += WY_THREADS) {
-        const int a = e / BN;
-        const int owner = a / rows_per_rank;
-        if (owner != rank) Z[e] = cluster.map_shared_rank(Z, owner)[e];
-    }
-    __syncthreads();
-    // ---- own rows of op(T) Z
-    for (int e = tid; e < (a1 - a0) * BN; e += WY_THREADS) {
-        const int a = a0 + e / BN, bb = e % BN;
-        double z = 0.0;
-        for (int c = 0; c < WY_JB; ++c) z = fma(Ts[a * WY_JB + c], Z[c * BN + bb], z);
-        Zt[a * BN + bb] = z;
-    }
-    cluster.sync();
-    // ---- all-gather op(T) Z into Z (Z itself is no longer read by anyone after the sync)
-    for (int e = tid; e < WY_JB * BN; e += WY_THREADS) {
-        const int a = e / BN;
-        const int owner = a / rows_per_rank;
-        Z[e] = owner == rank ? Zt[e] : cluster.map_shared_rank(Zt, owner)[e];
-    }
-    __syncthreads();
-    // ---- W_rows,blk -= V_rows (op(T) Z): thread -> column b, rows ag, ag + G, ...
-    {
-        double zc[WY_JB];
-#pragma unroll
-        for (int a = 0; a < WY_JB; ++a) zc[a] = Z[a * BN + b];
-        for (int i = ag; i < nr; i += G) {
-            double w = Ws[i * (BN + 1) + b];
-#pragma unroll
-            for (int a = 0; a < WY_JB; ++a) w = fma(-Vs[i * (WY_JB + 1) + a], zc[a], w);
-            if (b < nbw) W[static_cast<long long>(r0 + i) * ldw + c0 + b] = w;
+    for (int blk = cid; blk < nblk; blk += ncl) {
+        const int c0 = blk * BN;
+        const int nbw = min(BN, Nw - c0);
+        for (int e = tid; e < nr * BN; e += WY_THREADS) {
+            const int i = e / BN, bb = e % BN;
+            Ws[i * (BN + 1) + bb] = bb < nbw ? W[static_cast<long long>(r0 + i) * ldw + c0 + bb] : 0.0;
         }
+        __syncthreads();
+        // ---- Zp = V_rows^T W_rows,blk: thread -> column b, AU consecutive a
+        {
+            double acc[AU];
+#pragma unroll
+            for (int u = 0; u < AU; ++u) acc[u] = 0.0;
+            for (int i = 0; i < nr; ++i) {
+                const double w = Ws[i * (BN + 1) + b];
+#pragma unroll
+                for (int u = 0; u < AU; ++u) acc[u] = fma(Vs[i * (WY_JB + 1) + ag * AU + u], w, acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < AU; ++u) Zp[(ag * AU + u) * BN + b] = acc[u];
+        }
+        cluster.sync();
+        // ---- reduce-scatter: rank k sums rows a in its share of Z over all ranks (rank order)
+        for (int e = tid; e < (a1 - a0) * BN; e += WY_THREADS) {
+            const int a = a0 + e / BN, bb = e % BN;
+            double z = 0.0;
+            for (int k = 0; k < cs; ++k) z += cluster.map_shared_rank(Zp, k)[a * BN + bb];
+            Z[a * BN + bb] = z;
+        }
+        cluster.sync();
+        // ---- all-gather Z
+        for (int e = tid; e < WY_JB * BN; e += WY_THREADS) {
+            const int a = e / BN;
+            const int owner = a / rows_per_rank;
+            if (owner != rank) Z[e] = cluster.map_shared_rank(Z, owner)[e];
+        }
+        __syncthreads();
+        // ---- own rows of op(T) Z
+        for (int e = tid; e < (a1 - a0) * BN; e += WY_THREADS) {
+            const int a = a0 + e / BN, bb = e % BN;
+            double z = 0.0;
+            for (int c = 0; c < WY_JB; ++c) z = fma(Ts[a * WY_JB + c], Z[c * BN + bb], z);
+            Zt[a * BN + bb] = z;
+        }
+        cluster.sync();
+        // ---- all-gather op(T) Z into Z (Z itself is no longer read by anyone after the sync)
+        for (int e = tid; e < WY_JB * BN; e += WY_THREADS) {
+            const int a = e / BN;
+            const int owner = a / rows_per_rank;
+            Z[e] = owner == rank ? Zt[e] : cluster.map_shared_rank(Zt, owner)[e];
+        }
+        __syncthreads();
+        // ---- W_rows,blk -= V_rows (op(T) Z): thread -> column b, rows ag, ag + G, ...
+        {
+            double zc[WY_JB];
+#pragma unroll
+            for (int a = 0; a < WY_JB; ++a) zc[a] = Z[a * BN + b];
+            for (int i = ag; i < nr; i += G) {
+                double w = Ws[i * (BN + 1) + b];
+#pragma unroll
+                for (int a = 0; a < WY_JB; ++a) w = fma(-Vs[i * (WY_JB + 1) + a], zc[a], w);
+                if (b < nbw) W[static_cast<long long>(r0 + i) * ldw + c0 + b] = w;
+            }
+        }
+        cluster.sync();   // peers may still read this CTA's Zt / Z slices; Ws / Zp are reused next
     }
-    cluster.sync();   // peers may still read this CTA's Zt / Z slices
 }
 
 __global__ void qr_init_q_kernel(double* Q, long long ldq, int M, int N) {
@@ -1589,37 +1593,39 @@ bool wy_usable(long long Mp) {
 
 // One-launch compact-WY application when a row slice of the panel fits a CTA's
 // shared memory; returns GN_ERR_UNSUPPORTED otherwise (the caller then uses the
-// GEMM sequence).
+// GEMM sequence).  reserve: another 16-CTA cluster runs alongside (a panel or
+// the diagnostics), so one cluster slot of 16 SMs is left free.
 gn_status wy_apply(gn_handle h, double* W, long long ldw, long long Mp, long long Nw, const double* V, long long ldv,
-                   int jb, const double* T, int transT) {
+                   int jb, const double* T, int transT, int reserve) {
     const int cs_max = wy_cluster_max();
     if (cs_max == 0 || jb > WY_JB || Mp <= 0 || Nw <= 0) return GN_ERR_UNSUPPORTED;
     // Cluster size (rows per CTA) and column block width: the kernel is bound by
-    // each SM's FP64 rate, so its time is ~ waves x rows per CTA x (bn + a fixed
-    // cost of about 8 columns' work), a wave being the clusters that fit at once
-    // with one CTA per SM.
+    // each SM's FP64 rate and its clusters loop over the blocks, so its time is
+    // ~ ceil(blocks / clusters) x rows per CTA x (bn + a fixed cost of about 8
+    // columns' work per block).
     int cs = 0, bn = 64;
-    long long rp = 0, best = -1;
+    long long rp = 0, best = -1, ncl = 1;
     for (int c : {8, 16}) {
         if (c > cs_max) continue;
         const long long rpc = (Mp + c - 1) / c;
         if (rpc > WY_MAX_ROWS) continue;
-        const long long capc = wy_cluster_capacity(c, h->sm_count);
+        const long long capc = std::max<long long>(1, wy_cluster_capacity(c, h->sm_count) - (reserve ? 16 / c : 0));
         for (int cand : {64, 32, 16, 8}) {
-            const long long waves = ((Nw + cand - 1) / cand + capc - 1) / capc;
-            const long long cost = waves * rpc * (cand + 8);
+            const long long nb = (Nw + cand - 1) / cand;
+            const long long per = (nb + capc - 1) / capc;   // blocks per cluster
+            const long long cost = per * rpc * (cand + 8);
             if (best < 0 || cost < best) {
                 best = cost;
                 cs = c;
                 bn = cand;
                 rp = rpc;
+                ncl = std::min<long long>(nb, capc);
             }
         }
     }
     if (cs == 0) return GN_ERR_UNSUPPORTED;
-    const long long nblk = (Nw + bn - 1) / bn;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(static_cast<unsigned>(nblk * cs));
+    cfg.gridDim = dim3(static_cast<unsigned>(ncl * cs));
     cfg.blockDim = dim3(WY_THREADS);
     cfg.dynamicSmemBytes = wy_smem(static_cast<int>(rp), bn);
     cfg.stream = h->stream;
@@ -1682,6 +1688,7 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
         h = &crit;
     }
     GN_TRY(factor_panel(0));
+    bool had_second = false, side_used = false;
     for (long long j0 = 0; j0 < N; j0 += nb) {
         const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
         const long long Mp = M - j0;
@@ -1691,22 +1698,33 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
         double* W2 = W + j0 * ld + j0 + jb;
         const double* Vb = q.V + j0 * N + j0;
         if (lookahead) {
-            // W2 <- (I - V T V^T)^T W2 = W2 - V T^T (V^T W2), split at the next panel
+            // W2 <- (I - V T V^T)^T W2 = W2 - V T^T (V^T W2), in three column ranges:
+            //   next panel (main stream, before it is factored);
+            //   the panel after it (side stream, then ev_join marks it done);
+            //   everything further right (side stream, may lag behind the panels).
+            // Each column range receives the panels' updates in order: the side
+            // stream is in order, and the main stream's next-panel update waits for
+            // the side stream's update of the same columns by the previous panel.
             const long long nnext = std::min<long long>(nb, N2);
-            GN_TRY(wy_apply(h, W2, ld, Mp, nnext, Vb, N, jb, T, 1));
-            if (N2 > nnext) {
-                GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+            const long long nsec = std::min<long long>(nb, N2 - nnext);
+            const long long nrest = N2 - nnext - nsec;
+            if (j0 > 0 && had_second) GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+            if (nsec > 0) {
+                GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));   // panel j0 factored
                 GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
                 gn_handle_s side = *h;
                 side.stream = h->side;
-                GN_TRY(wy_apply(&side, W2 + nnext, ld, Mp, N2 - nnext, Vb, N, jb, T, 1));
+                GN_TRY(wy_apply(&side, W2 + nnext, ld, Mp, nsec, Vb, N, jb, T, 1, 1));
                 GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+                if (nrest > 0) GN_TRY(wy_apply(&side, W2 + nnext + nsec, ld, Mp, nrest, Vb, N, jb, T, 1, 1));
+                side_used = true;
             }
+            had_second = nsec > 0;
+            GN_TRY(wy_apply(h, W2, ld, Mp, nnext, Vb, N, jb, T, 1, 0));
             GN_TRY(factor_panel(j0 + jb));
-            if (N2 > nnext) GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
             continue;
         }
-        const gn_status st = wy_apply(h, W2, ld, Mp, N2, Vb, N, jb, T, 1);
+        const gn_status st = wy_apply(h, W2, ld, Mp, N2, Vb, N, jb, T, 1, 0);
         if (st == GN_ERR_UNSUPPORTED) {
             GN_TRY(dgemm(h, jb, N2, Mp, 1.0, Vb, N, 1, W2, ld, 0, 0.0, q.Z1, N2, q.gws, q.gws_bytes));
             GN_TRY(dgemm(h, jb, N2, jb, 1.0, T, jb, 1, q.Z1, N2, 0, 0.0, q.Z2, N2, q.gws, q.gws_bytes));
@@ -1715,6 +1733,10 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
             GN_TRY(st);
         }
         GN_TRY(factor_panel(j0 + jb));
+    }
+    if (side_used) {   // every lagging update is done before R and the reflectors are used
+        GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+        GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     }
     qr_write_r_kernel<<<ew_blocks(h, N * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(N), R, ldr); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
@@ -1741,7 +1763,7 @@ gn_status qr_form_q(gn_handle h, const double* W, long long M, long long N, long
         const double* Vb = q.V + j0 * N + j0;
         const double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
         // Q_s <- (I - V T V^T) Q_s
-        const gn_status st = wy_apply(h, Qs, ldq, Mp, Nq, Vb, N, jb, T, 0);
+        const gn_status st = wy_apply(h, Qs, ldq, Mp, Nq, Vb, N, jb, T, 0, 1);
         if (st == GN_ERR_UNSUPPORTED) {
             GN_TRY(dgemm(h, jb, Nq, Mp, 1.0, Vb, N, 1, Qs, ldq, 0, 0.0, q.Z1, Nq, q.gws, q.gws_bytes));
             GN_TRY(dgemm(h, jb, Nq, jb, 1.0, T, jb, 0, q.Z1, Nq, 0, 0.0, q.Z2, Nq, q.gws, q.gws_bytes));
