@@ -506,10 +506,47 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
                         "err": None}
     out["fp64_path"]["err"] = err_of(AX64, YtA64, c64)
     out["norm_A_fro"] = normA
+    out["r2000"] = r2000_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode)
     out["adjoint"] = adjoint_measurement(gn, H, stream, dev)
     out["batched"] = batched_measurement(gn, H, stream, dev, steps=max(3, a.steps))
     out["err_floor_note"] = ("errors are ||A - F G||_F against the FP64 A; the bf16 path's floor is the "
                              "bf16 storage of A, split bf16 and FP64 reach the sketch error itself")
+    return out
+
+
+def r2000_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode, r=2000):
+    """The same matrix with the larger sketch size, r = 2000, l = 1000 (BF16
+    sketch + FP64 core of 3000 x 2000): approximations/s and the sketch rate."""
+    m, n = a.m, a.n
+    l = r // 2
+    X64, Y64 = gn_synth.sketches(m, n, r, l, gn_synth.DEFAULT_SEED + 2, device=dev)
+    Xb, Yb = H.quantize(X64), H.quantize(Y64)
+    del X64, Y64
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    AX = torch.empty(m, r, dtype=torch.float32, device=dev)
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device=dev)
+    core = gn.Core.empty(r, l, dev)
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    H.core(YtA, Xb, eps, mode, core, ws)
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1, k0, k1 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+    e0.record(stream)
+    for _ in range(reps):
+        k0.record(stream)
+        H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+        k1.record(stream)
+        H.core(YtA, Xb, eps, mode, core, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    sk = k0.elapsed_time(k1)
+    fl = 2.0 * m * n * (2 * r + l)
+    out = {"workload": f"{m}x{n}, r={r}, l={l}, bf16 operands, FP64 core, mode AUTO",
+           "approx_per_s": 1e3 / ms, "ms_per_step": ms, "sketch_ms": sk,
+           "sketch_tflops": fl / (sk / 1e3) / 1e12, "k": core.k}
+    del Xb, Yb, ws, AX, YtA, core
+    torch.cuda.empty_cache()
     return out
 
 
@@ -560,6 +597,15 @@ def batched_measurement(gn, H, stream, dev, count=512, steps=10):
     eps, mode = 10 * 2.0 ** -24, gn.AUTO | gn.EPS_RELATIVE
     H.batched_run(eps, mode, ws)
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        H.batched_run(eps, mode, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fixed_ms = e0.elapsed_time(e1) / 3
+    policy, tuned_ms = H.batched_tune(eps, mode, ws)   # re-prepares with the fastest tile policy
+    torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         H.batched_run(eps, mode, ws)
@@ -577,6 +623,7 @@ def batched_measurement(gn, H, stream, dev, count=512, steps=10):
     peaks, _ = measured_peaks()
     return {"workload": f"{count} problems, m~U[256,4096], n~U[128,m], r~U{{16..128}}, l=r/2, BF16, mode AUTO",
             "approx_per_s": count * 1e3 / ms, "ms_per_batch": ms, "cuda_graph": True, "launches_per_batch": 4,
+            "tile_policy": policy, "tuned_ms_no_graph": tuned_ms, "fixed_rule_ms_no_graph": fixed_ms,
             "a_bytes": a_bytes, "hbm_floor_ms": a_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3,
             "sketch_flops": flops, "truncated": sum(1 for k, (m, n, r, l) in zip(ks, shapes) if k < r)}
 

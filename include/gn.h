@@ -294,6 +294,23 @@ gn_status gn_batched_workspace_size(int32_t count, const gn_problem* probs, size
 gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs, void* ws,
                              size_t ws_bytes);
 
+/* Tile policy of the batch's tensor-core launches, used by the next
+ * gn_batched_prepare (bit field; 0 = the fixed rule):
+ *   bits 0-1: N tile of every Y^T A product: 0 -> 128, 1 -> 64, 2 -> 256
+ *   bit 2   : N tile 64 for AX when 64 < r (two tiles instead of one)
+ *   bit 3   : problems ordered by decreasing sketch work in the tile list
+ * The paper has no batched mode; the policy is this library's. */
+#define GN_BATCHED_POLICIES 12
+gn_status gn_batched_set_policy(gn_handle h, int32_t policy);
+
+/* Autotuner: for each of the GN_BATCHED_POLICIES policies, prepare the batch
+ * and time gn_batched_run (one warm-up, three timed runs, CUDA events on the
+ * handle's stream); then prepare it again with the fastest, which stays set
+ * on the handle and is written to *best (ms per run to *best_ms if non-null).
+ * Synchronous; overwrites the problems' outputs. */
+gn_status gn_batched_tune(gn_handle h, int32_t count, const gn_problem* probs, void* ws, size_t ws_bytes,
+                          double eps, int32_t mode, int32_t* best, double* best_ms);
+
 /* Algorithm 2 step 2 and the Section 5.1 core for every prepared problem, in
  * four launches on the handle's stream: one grouped tensor-core launch for
  * all sketches AX, Y^T A (BF16, FP32 accumulation), one split of every Y^T A

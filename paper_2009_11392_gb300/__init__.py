@@ -38,6 +38,7 @@ ABI_SYMBOLS = (
     "gn_sketch", "gn_core", "gn_factors", "gn_approx", "gn_error_fro2", "gn_hmt",
     "gn_kernel_launches", "gn_error_fro2_noalloc", "gn_backward_workspace_size", "gn_backward",
     "gn_forward_dense", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
+    "gn_batched_set_policy", "gn_batched_tune",
 )
 
 
@@ -105,6 +106,9 @@ def _load():
         "gn_batched_workspace_size": ([I32, ctypes.POINTER(GnProblem), ctypes.POINTER(SZ)], I32),
         "gn_batched_prepare": ([P, I32, ctypes.POINTER(GnProblem), P, SZ], I32),
         "gn_batched_run": ([P, D, I32, P, SZ], I32),
+        "gn_batched_set_policy": ([P, I32], I32),
+        "gn_batched_tune": ([P, I32, ctypes.POINTER(GnProblem), P, SZ, D, I32, ctypes.POINTER(I32),
+                             ctypes.POINTER(D)], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -368,6 +372,19 @@ class Handle:
                "gn_batched_prepare")
         self._batched_arr = arr
         return ws
+
+    def batched_set_policy(self, policy: int):
+        _check(lib.gn_batched_set_policy(self._h, int(policy)), "gn_batched_set_policy")
+
+    def batched_tune(self, eps, mode, ws):
+        """Time every tile policy on the prepared batch, keep the fastest;
+        returns (policy, ms per run)."""
+        arr = self._batched_arr
+        best = ctypes.c_int32()
+        ms = ctypes.c_double()
+        _check(lib.gn_batched_tune(self._h, len(arr), arr, ctypes.c_void_p(ws.data_ptr()), ws.numel(), float(eps),
+                                   int(mode), ctypes.byref(best), ctypes.byref(ms)), "gn_batched_tune")
+        return int(best.value), float(ms.value)
 
     def batched_run(self, eps, mode, ws):
         _check(lib.gn_batched_run(self._h, float(eps), int(mode), ctypes.c_void_p(ws.data_ptr()), ws.numel()),

@@ -474,6 +474,23 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
     std::vector<TcGemm> sk(2 * static_cast<size_t>(count)), cg(3 * static_cast<size_t>(count));
     std::vector<ProblemDev> pd(count);
     int sk_tiles = 0, c_tiles = 0;
+    const int policy = h->batched_policy;
+    const int bn_yta = (policy & 3) == 1 ? 64 : ((policy & 3) == 2 ? 256 : 128);
+    // position of each problem's two sketch GEMMs in the tile list
+    std::vector<int> slot(count);
+    {
+        std::vector<int> ord(count);
+        for (int i = 0; i < count; ++i) ord[i] = i;
+        if (policy & 8) {
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b2) {
+                const auto w = [&](int i) {
+                    return double(probs[i].A.rows) * probs[i].A.cols * (2.0 * probs[i].X.cols + probs[i].Y.cols);
+                };
+                return w(a) > w(b2);
+            });
+        }
+        for (int pos = 0; pos < count; ++pos) slot[ord[pos]] = pos;
+    }
     for (int i = 0; i < count; ++i) {
         const gn_problem& q = probs[i];
         const long long m = q.A.rows, n = q.A.cols, r = q.X.cols, rl = q.Y.cols, l = rl - r;
@@ -523,24 +540,24 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
         for (int s = 0; s < 3; ++s) GN_TRY(tc_make_map_bf16(&mp[4 + s], d.s[s], rl, n, d.lds, 64, 128));
         // sketch GEMMs: AX (A K-major, X MN-major), Y^T A (Y MN-major, A MN-major)
         const int mi = 7 * i;
-        TcGemm& g0 = sk[2 * i];
+        TcGemm& g0 = sk[2 * slot[i]];
         memset(&g0, 0, sizeof(g0));
         g0.M = static_cast<int>(m);
         g0.N = static_cast<int>(r);
         g0.K = static_cast<int>(n);
-        g0.bn = static_cast<int>(std::min<long long>(256, (r + 63) / 64 * 64));
+        g0.bn = (policy & 4) && r > 64 ? 64 : static_cast<int>(std::min<long long>(256, (r + 63) / 64 * 64));
         g0.b_mn = 1;
         g0.nsrc = 1;
         g0.a_map[0] = mi + 0;
         g0.b_map[0] = mi + 2;
         g0.D = static_cast<float*>(q.AX.data);
         g0.ldd = q.AX.ld;
-        TcGemm& g1 = sk[2 * i + 1];
+        TcGemm& g1 = sk[2 * slot[i] + 1];
         memset(&g1, 0, sizeof(g1));
         g1.M = static_cast<int>(rl);
         g1.N = static_cast<int>(n);
         g1.K = static_cast<int>(m);
-        g1.bn = 128;
+        g1.bn = bn_yta;
         g1.a_mn = 1;
         g1.b_mn = 1;
         g1.nsrc = 1;
@@ -548,10 +565,6 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
         g1.b_map[0] = mi + 1;
         g1.D = static_cast<float*>(q.YtA.data);
         g1.ldd = q.YtA.ld;
-        GN_TRY(tc_prepare_gemm(&g0, sk_tiles));
-        sk_tiles += g0.tiles_m * g0.tiles_n;
-        GN_TRY(tc_prepare_gemm(&g1, sk_tiles));
-        sk_tiles += g1.tiles_m * g1.tiles_n;
         for (int s = 0; s < 3; ++s) {
             TcGemm& g = cg[3 * i + s];
             memset(&g, 0, sizeof(g));
@@ -568,6 +581,10 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
             GN_TRY(tc_prepare_gemm(&g, c_tiles));
             c_tiles += g.tiles_m * g.tiles_n;
         }
+    }
+    for (int pos = 0; pos < 2 * count; ++pos) {   // tile bases in list order
+        GN_TRY(tc_prepare_gemm(&sk[pos], sk_tiles));
+        sk_tiles += sk[pos].tiles_m * sk[pos].tiles_n;
     }
     if (off > ws_bytes) return GN_ERR_WORKSPACE;
     int header[4] = {count, sk_tiles, c_tiles, 0};
@@ -590,6 +607,54 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
     h->batched_sk_tiles = sk_tiles;
     h->batched_c_tiles = c_tiles;
     h->batched_ws = ws;
+    return GN_OK;
+}
+
+gn_status gn_batched_set_policy(gn_handle h, int32_t policy) {
+    if (!h || policy < 0 || policy >= 16 || (policy & 3) == 3) return GN_ERR_INVALID_ARG;
+    h->batched_policy = policy;
+    return GN_OK;
+}
+
+gn_status gn_batched_tune(gn_handle h, int32_t count, const gn_problem* probs, void* ws, size_t ws_bytes,
+                          double eps, int32_t mode, int32_t* best, double* best_ms) {
+    if (!h || !best) return GN_ERR_INVALID_ARG;
+    static const int kPolicies[GN_BATCHED_POLICIES] = {0, 1, 2, 4, 5, 6, 8, 9, 10, 12, 13, 14};
+    cudaEvent_t e0, e1;
+    GN_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return GN_ERR_CUDA;
+    }
+    int best_p = -1;
+    float best_t = 0.0f;
+    gn_status st = GN_OK;
+    for (int c = 0; c < GN_BATCHED_POLICIES && st == GN_OK; ++c) {
+        h->batched_policy = kPolicies[c];
+        st = gn_batched_prepare(h, count, probs, ws, ws_bytes);
+        if (st == GN_OK) st = gn_batched_run(h, eps, mode, ws, ws_bytes);   // warm-up
+        if (st != GN_OK) break;
+        if (cudaEventRecord(e0, h->stream) != cudaSuccess) { st = GN_ERR_CUDA; break; }
+        for (int rep = 0; rep < 3 && st == GN_OK; ++rep) st = gn_batched_run(h, eps, mode, ws, ws_bytes);
+        if (st != GN_OK) break;
+        float ms = 0.0f;
+        if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            st = GN_ERR_CUDA;
+            break;
+        }
+        if (best_p < 0 || ms < best_t) {
+            best_p = kPolicies[c];
+            best_t = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GN_OK) return st;
+    h->batched_policy = best_p;
+    GN_TRY(gn_batched_prepare(h, count, probs, ws, ws_bytes));
+    *best = best_p;
+    if (best_ms) *best_ms = best_t / 3.0;
     return GN_OK;
 }
 

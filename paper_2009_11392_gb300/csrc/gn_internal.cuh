@@ -24,6 +24,7 @@ struct gn_handle_s {
     // batched path: the tables gn_batched_prepare uploaded into batched_ws
     void* batched_ws;
     int batched_count, batched_sk_tiles, batched_c_tiles;
+    int batched_policy;        // tile policy of the next gn_batched_prepare
 };
 
 #define GN_CUDA_TRY(expr)                                   \

@@ -100,3 +100,42 @@ def test_batched_truncation_branch(gn, H):
         assert np.linalg.norm(Rb2 - Ru2) <= 1e-9 * np.linalg.norm(Ru2)
         Qb2, Qu2 = p["Q2"].cpu().numpy()[:, :k], core.Q2.cpu().numpy()[:, :k]
         assert np.linalg.norm(Qb2 - Qu2) <= 1e-9 * np.linalg.norm(Qu2)
+
+
+def test_batched_autotuner_keeps_results(gn, H):
+    """The autotuner times every tile policy and keeps the fastest; the tile
+    shape changes only the schedule, so the sketches stay bitwise equal to
+    the unbatched path and the cores are unchanged."""
+    probs = [_problem(gn, 20 + i, *s) for i, s in enumerate(SHAPES)]
+    ws = H.batched_prepare(probs)
+    best, ms = H.batched_tune(0.0, gn.PLAIN, ws)
+    assert best in (0, 1, 2, 4, 5, 6, 8, 9, 10, 12, 13, 14) and ms > 0
+    for p in probs:
+        p["AX"].fill_(float("nan"))
+        p["YtA"].fill_(float("nan"))
+    H.batched_run(0.0, gn.PLAIN, ws)
+    torch.cuda.synchronize()
+    assert H.sync_status() == 0
+    for (m, n, r), p in zip(SHAPES, probs):
+        l = r // 2
+        wsu = H.workspace(m, n, r, l, gn.BF16)
+        AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+        YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+        H.sketch(p["A"], p["X"], p["Y"], AX, YtA, wsu)
+        torch.cuda.synchronize()
+        assert torch.equal(p["AX"], AX) and torch.equal(p["YtA"], YtA)
+        assert int(p["k"].item()) == r
+    for pol in (1, 2, 4, 8, 14):   # every policy gives the same sketches
+        H.batched_set_policy(pol)
+        ws2 = H.batched_prepare(probs)
+        H.batched_run(0.0, gn.PLAIN, ws2)
+        torch.cuda.synchronize()
+        for (m, n, r), p in zip(SHAPES, probs):
+            l = r // 2
+            wsu = H.workspace(m, n, r, l, gn.BF16)
+            AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+            YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+            H.sketch(p["A"], p["X"], p["Y"], AX, YtA, wsu)
+            torch.cuda.synchronize()
+            assert torch.equal(p["AX"], AX) and torch.equal(p["YtA"], YtA)
+    H.batched_set_policy(0)

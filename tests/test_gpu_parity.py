@@ -176,6 +176,31 @@ def test_fp64_core_full_size(gn, H):
     assert core.k == c["k"] == r and core.sgn == int(c["sgn"]) == 0
 
 
+def test_fp64_core_r2000_properties(gn, H):
+    """r = 2000, l = 1000 (the larger core of the bench shape, 3000 x 2000, 63
+    panels): properties that hold at any size -- Householder backward error
+    ||C - QR|| and orthogonality ||Q^T Q - I|| at the FP64 rounding level,
+    R upper triangular with a non-negative diagonal -- and the detector's
+    estimates against the oracle's power iterations on the same R."""
+    r, l, n = 2000, 1000, 2200
+    rng = np.random.default_rng(12)
+    YtA = rng.standard_normal((r + l, n))
+    X = rng.standard_normal((n, r)) * (0.998 ** np.arange(r))[None, :]
+    ws = H.workspace(r + l, n, r, l, gn.F64)
+    core = _core_tensors(gn, r, l)
+    H.core(cu(YtA), cu(X), 10 * O.U64, gn.AUTO | gn.EPS_RELATIVE, core, ws)
+    assert H.sync_status() == 0
+    C, Q, R = npy(core.C), npy(core.Q), npy(core.R)
+    assert rel(C, YtA @ X) <= 1e-13
+    u = O.U64
+    assert np.linalg.norm(C - Q @ R) <= 50 * r * u * np.linalg.norm(C)
+    assert np.linalg.norm(Q.T @ Q - np.eye(r)) <= 50 * r * u
+    assert np.array_equal(np.triu(R), R) and np.all(np.diag(R) >= 0)
+    assert abs(core.rinv_est - O.rinv_norm_estimate(R, iters=6)) <= 1e-8 * core.rinv_est
+    assert abs(core.c_norm_est - O.norm2_estimate(R, iters=6)) <= 1e-10 * core.c_norm_est
+    assert core.k == r and core.sgn == 0
+
+
 @pytest.mark.parametrize("mode", ["plain", "auto"])
 def test_fp64_gn_config1(gn, H, mode):
     """The 1000 x 500 geometric case: factors and A_hat at 1e-10."""
