@@ -297,48 +297,82 @@ def main():
     per_step_ms = elapsed_ms / a.steps
     value = world * a.steps / (elapsed_ms / 1e3)
 
-    # ---- end to end through the API with host buffers (H2D inputs, D2H outputs)
-    outs = [torch.empty(AX.shape, dtype=torch.float32, pin_memory=True),
-            torch.empty(YtA.shape, dtype=torch.float32, pin_memory=True),
-            torch.empty(core.Q.shape, dtype=torch.float64, pin_memory=True),
-            torch.empty(core.R.shape, dtype=torch.float64, pin_memory=True)]
-    d2h = sum(o.numel() * o.element_size() for o in outs)
+    # ---- end to end through the API with host buffers (H2D inputs, D2H outputs).
+    # Every step copies its own inputs in from pinned host memory and its results
+    # out; two device buffer sets let the copies of one step run on a copy stream
+    # while the previous step computes.
+    nset = 2
     if a.op == "e4m3":
         # the e4m3 codes (A in both orientations, X^T, Y^T) and the tile scales
         srcs = [Aop.data, Aop.data_t, Xop.data_t, Yop.data_t, Aop.scale, Xop.scale, Yop.scale]
         hosts = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in srcs]
-        devs = [torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=dev) for t in srcs]
-        Ad = gn.E4M3Mat(m, n, devs[4], devs[0], devs[1])
-        Xd = gn.E4M3Mat(n, r, devs[5], None, devs[2])
-        Yd = gn.E4M3Mat(m, r + l, devs[6], None, devs[3])
+
+        def make_in():
+            d = [torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=dev) for t in srcs]
+            return d, (gn.E4M3Mat(m, n, d[4], d[0], d[1]), gn.E4M3Mat(n, r, d[5], None, d[2]),
+                       gn.E4M3Mat(m, r + l, d[6], None, d[3]))
     else:
         srcs = [Ab, Xb, Yb]
         hosts = [torch.empty(t.shape, dtype=torch.bfloat16, pin_memory=True).copy_(t) for t in srcs]
-        devs = [gn.padded(m, n, torch.bfloat16, dev), gn.padded(n, r, torch.bfloat16, dev),
-                gn.padded(m, r + l, torch.bfloat16, dev)]
-        Ad, Xd, Yd = devs
+
+        def make_in():
+            d = [gn.padded(m, n, torch.bfloat16, dev), gn.padded(n, r, torch.bfloat16, dev),
+                 gn.padded(m, r + l, torch.bfloat16, dev)]
+            return d, tuple(d)
+    ins = [make_in() for _ in range(nset)]
+    outd = [(torch.empty(m, r, dtype=torch.float32, device=dev), torch.empty(r + l, n, dtype=torch.float32, device=dev),
+             gn.Core.empty(r, l, dev)) for _ in range(nset)]
+    outh = [[torch.empty(AX.shape, dtype=torch.float32, pin_memory=True),
+             torch.empty(YtA.shape, dtype=torch.float32, pin_memory=True),
+             torch.empty(core.Q.shape, dtype=torch.float64, pin_memory=True),
+             torch.empty(core.R.shape, dtype=torch.float64, pin_memory=True)] for _ in range(nset)]
     h2d = sum(t.numel() * t.element_size() for t in hosts)
+    d2h = sum(o.numel() * o.element_size() for o in outh[0])
+    cstream = torch.cuda.Stream(device=dev)
+    ev_in = [torch.cuda.Event() for _ in range(nset)]    # inputs of the set landed
+    ev_done = [torch.cuda.Event() for _ in range(nset)]  # compute on the set finished
+    ev_out = [torch.cuda.Event() for _ in range(nset)]   # results of the set copied out
 
-    def e2e_step():
-        for d_, h_ in zip(devs, hosts):
-            d_.copy_(h_, non_blocking=True)
-        H.sketch(Ad, Xd, Yd, AX, YtA, ws)
-        H.core(YtA, Xd, eps, mode, core, ws)
-        for o, s in zip(outs, (AX, YtA, core.Q, core.R)):
-            o.copy_(s, non_blocking=True)
+    def prefetch(i):
+        b = i % nset
+        cstream.wait_event(ev_done[b])            # the set's previous step has finished computing
+        with torch.cuda.stream(cstream):
+            for d_, h_ in zip(ins[b][0], hosts):
+                d_.copy_(h_, non_blocking=True)
+        ev_in[b].record(cstream)
 
-    for _ in range(max(1, a.warmup)):
-        e2e_step()
+    def compute(i):
+        b = i % nset
+        Ad, Xd, Yd = ins[b][1]
+        AXd, YtAd, cd = outd[b]
+        stream.wait_event(ev_in[b])
+        stream.wait_event(ev_out[b])              # the set's previous results are out
+        H.sketch(Ad, Xd, Yd, AXd, YtAd, ws)
+        H.core(YtAd, Xd, eps, mode, cd, ws)
+        ev_done[b].record(stream)
+        cstream.wait_event(ev_done[b])
+        with torch.cuda.stream(cstream):
+            for o, s_ in zip(outh[b], (AXd, YtAd, cd.Q, cd.R)):
+                o.copy_(s_, non_blocking=True)
+        ev_out[b].record(cstream)
+
+    def e2e_run(k):
+        prefetch(0)
+        for i in range(k):
+            if i + 1 < k:
+                prefetch(i + 1)
+            compute(i)
+
+    e2e_run(max(1, a.warmup))
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        e2e_step()
-    e1.record(stream)
+    e0.record(cstream)
+    e2e_run(a.steps)
+    e1.record(cstream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / a.steps
-    del Ad, Xd, Yd, devs, hosts
+    del ins, outd, outh, hosts
 
     peaks, peak_kind = measured_peaks()
     flops = 2.0 * m * n * (2 * r + l)
