@@ -102,6 +102,33 @@ def test_tc_sketch_exact_on_integer_inputs(gn, H, m, n, r, l):
     assert np.array_equal(npy(YtA), oYtA)
 
 
+def test_tc_sketch_large_sampled(gn, H):
+    """16384 x 8192, r = 1000, l = 500: enough tiles for the 256-row tile shape
+    (CTA pairs sharing the B stage by multicast).  Integer inputs drawn on the
+    device; 64 sampled rows of AX and 64 sampled columns of Y^T A against the
+    oracle's products, bitwise."""
+    m, n, r, l = 16384, 8192, 1000, 500
+    g = torch.Generator(device="cuda").manual_seed(78)
+    def draw(rows, cols):
+        return torch.randint(-3, 4, (rows, cols), generator=g, device="cuda", dtype=torch.int8).double()
+    A, X, Y = draw(m, n), draw(n, r), draw(m, r + l)
+    Ab, Xb, Yb = H.quantize(A), H.quantize(X), H.quantize(Y)
+    AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    assert H.sync_status() == 0
+    rng = np.random.default_rng(6)
+    rows = np.sort(rng.choice(m, 64, replace=False))
+    cols = np.sort(rng.choice(n, 64, replace=False))
+    oAX = A[torch.from_numpy(rows).cuda()].cpu().numpy() @ X.cpu().numpy()
+    oYtA = Y.cpu().numpy().T @ A[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+    assert np.array_equal(npy(AX)[rows], oAX)
+    assert np.array_equal(npy(YtA)[:, cols], oYtA)
+    del A, X, Y, Ab, Xb, Yb, AX, YtA, ws
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("split", [False, True])
 def test_tc_sketch_fp32_accumulation_bound(gn, H, split):
     m, n, r, l = 700, 450, 100, 50
