@@ -439,9 +439,10 @@ __device__ __forceinline__ double warp_sum(double s) {
 
 template <int JB>
 __host__ __device__ constexpr size_t cluster_panel_smem(int rows_per) {
-    // P + exchange slots [2][2+2JB] + tv[max(rows_per, 256)] + dsum/prow/w [3][JB] + gram, T [2][JB*JB]
+    // P + exchange slots [2][2+2JB] + tv[max(rows_per, 256)] + dsum/prow/g [3][JB] + gram, T [2][JB*JB]
+    // + per-warp Gram partials [7][JB(JB-1)/2]
     return sizeof(double) * (static_cast<size_t>(rows_per) * (JB + 1) + 2 * (2 + 2 * JB) +
-                             (rows_per > 256 ? rows_per : 256) + 3 * JB + 2 * JB * JB);
+                             (rows_per > 256 ? rows_per : 256) + 3 * JB + 2 * JB * JB + 7 * (JB * (JB - 1) / 2));
 }
 
 // One exchange per column: with x = P[c:, c], alpha = x_0, beta = -sign(alpha)||x||
@@ -449,6 +450,12 @@ __host__ __device__ constexpr size_t cluster_panel_smem(int rows_per) {
 //     w_q = v^T P_q = (x^T P_q - beta P_cq) / (alpha - beta),
 // so ||x[1:]||^2, the dot products x^T P_q and the owner's row c are all the
 // per-CTA partials a column needs, and they are exchanged in one cluster round.
+// With d = 1 / (beta (alpha - beta)) the update P_q -= tau v w_q is
+//     P_iq += xt_i g_q,   g_q = d (x^T P_q - beta P_cq),
+// where xt = x below row c and xt_c = alpha - beta: it uses the column as it
+// stands, so the reflectors are normalised (v = xt / (alpha - beta)) once,
+// after the last column.  The Gram V^T V that T needs is formed column by
+// column by warps 1-7 while warp 0 computes the next reflector's scalars.
 template <int JB>
 __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W, long long ld, int M, int j0,
                                                                      int jb, double* V, long long ldv,
@@ -464,11 +471,13 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     double* tv = xch + 2 * SLOT;                             // [max(rows_per, 256)] tau * v_i
     double* dsum = tv + (rows_per > 256 ? rows_per : 256);   // [JB] x^T P_q summed over ranks
     double* prow = dsum + JB;                                // [JB] row c of the panel
-    double* wv = prow + JB;                                  // [JB] w_q
+    double* wv = prow + JB;                                  // [JB] g_q
     double* gram = wv + JB;                                  // [JB][JB] partial V^T V
     double* Ts = gram + JB * JB;                             // [JB][JB]
-    __shared__ double taus[JB];
-    __shared__ double s_tau, s_beta, s_scale;
+    constexpr int NPAIR = JB * (JB - 1) / 2;
+    double* gpart = Ts + JB * JB;                            // [7][NPAIR] Gram partials of warps 1-7
+    __shared__ double taus[JB], sc_col[JB], amb_col[JB];
+    __shared__ double s_tau, s_beta, s_amb;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Mp = M - j0;
     const int r0 = rank * rows_per;
@@ -480,7 +489,26 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     }
     __syncthreads();
 
-    for (int e = tid; e < JB; e += CP_THREADS) taus[e] = 0.0;
+    for (int e = tid; e < JB; e += CP_THREADS) {
+        taus[e] = 0.0;
+        sc_col[e] = 0.0;
+        amb_col[e] = 0.0;
+    }
+    // Warps 1-7: partial Gram of reflector a with reflectors q < a over this CTA's
+    // rows below row a, from the unnormalised columns (xt_a = alpha - beta at row a).
+    auto gram_partial = [&](int a) {
+        const int np = a > 16 ? 32 : a > 8 ? 16 : a > 4 ? 8 : a > 2 ? 4 : a > 1 ? 2 : 1;
+        const int q = lane & (np - 1), sub = lane / np, nsub = 32 / np;
+        const int cla = a - r0;
+        double acc = 0.0;
+        if (q < a)
+            for (int li = max(0, cla) + (warp - 1) * nsub + sub; li < nr; li += (CP_WARPS - 1) * nsub) {
+                const double xa = li == cla ? amb_col[a] : P[li * LDP + a];
+                acc = fma(xa, P[li * LDP + q], acc);
+            }
+        for (int o = np; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (sub == 0 && q < a) gpart[(warp - 1) * NPAIR + a * (a - 1) / 2 + q] = acc;
+    };
     // Per-column thread tiles cover only the live columns: with na live columns
     // (padded to np, a power of two), lane = sub * np + column offset and the
     // 8 * 32 / np row chunks split the rows.  On GB300 each FP64 warp
@@ -549,15 +577,18 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
             tv[warp * 64 + 32 + cj] = a1;
         }
         __syncthreads();
-        if (warp == 0 && cj >= c && cj < jb) {
-            const double a0 = (tv[cj] + tv[64 + cj]) + (tv[128 + cj] + tv[192 + cj]);
-            const double a1 = (tv[32 + cj] + tv[96 + cj]) + (tv[160 + cj] + tv[224 + cj]);
+        if (warp == 0) {
+            double a0 = 0.0, a1 = 0.0, beta_l = 0.0, d_l = 0.0;
+            if (cj >= c && cj < jb) {
+                a0 = (tv[cj] + tv[64 + cj]) + (tv[128 + cj] + tv[192 + cj]);
+                a1 = (tv[32 + cj] + tv[96 + cj]) + (tv[160 + cj] + tv[224 + cj]);
+            }
             if (cj == c) {
                 const double tail = a0, alpha = a1;
                 if (tail == 0.0) {
                     s_tau = 0.0;
                     s_beta = alpha;
-                    s_scale = 0.0;
+                    s_amb = 0.0;
                 } else {
                     const double nx = sqrt(fma(alpha, alpha, tail));
                     const double beta = alpha >= 0.0 ? -nx : nx;
@@ -566,12 +597,21 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
                     const double d = 1.0 / (beta * amb);
                     s_tau = (beta - alpha) * (amb * d);
                     s_beta = beta;
-                    s_scale = beta * d;
+                    s_amb = amb;
+                    sc_col[c] = beta * d;   // 1 / (alpha - beta)
+                    amb_col[c] = amb;
+                    beta_l = beta;
+                    d_l = d;
                 }
-            } else {
-                dsum[cj] = a0;
-                prow[cj] = a1;
             }
+            const double beta = __shfl_sync(0xffffffffu, beta_l, c);
+            const double d = __shfl_sync(0xffffffffu, d_l, c);
+            if (cj > c && cj < jb) wv[cj] = d * fma(-beta, a1, a0);
+        } else if (c >= 2) {
+            // Gram of reflector a = c - 1 with reflectors q < a over this CTA's rows
+            // (unnormalised columns; scaled by both normalisations at the end).
+            // Lanes cover only the live pairs: lane = sub * np + q.
+            gram_partial(c - 1);
         }
         __syncthreads();
         const double t = s_tau;
@@ -581,18 +621,7 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
             if (rank == 0) tau[j0 + c] = t;
         }
         if (t != 0.0) {
-            const double sc = s_scale, beta = s_beta;
-            // v_i = x_i / (alpha - beta) below row c, v_c = 1; tv_i = tau v_i
-            for (int li = lo + tid; li < nr; li += CP_THREADS) {
-                double vi = 1.0;
-                if (li != cl) {
-                    vi = P[li * LDP + c] * sc;
-                    P[li * LDP + c] = vi;
-                }
-                tv[li] = t * vi;
-            }
-            if (tid > c && tid < jb) wv[tid] = fma(-beta, prow[tid], dsum[tid]) * sc;
-            __syncthreads();
+            const double amb = s_amb;
             const int na = jb - c - 1;   // columns c+1 .. jb-1
             if (na > 0) {
                 const int np = na > 16 ? 32 : na > 8 ? 16 : na > 4 ? 8 : na > 2 ? 4 : na > 1 ? 2 : 1;
@@ -601,13 +630,41 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
                 const int chunk = warp * (32 / np) + lane / np;
                 if (off < na) {
                     const int j = c + 1 + off;
-                    const double wj = wv[j];
-                    for (int li = lo + chunk; li < nr; li += nchunk) P[li * LDP + j] = fma(-tv[li], wj, P[li * LDP + j]);
+                    const double gj = wv[j];
+                    for (int li = lo + chunk; li < nr; li += nchunk) {
+                        const double x = li == cl ? amb : P[li * LDP + c];
+                        P[li * LDP + j] = fma(x, gj, P[li * LDP + j]);
+                    }
                 }
             }
         }
         __syncthreads();
     }
+
+    // Gram of the last reflector (raw columns), then every partial scaled by the
+    // two normalisations: g(a, q) = sc_a sc_q xt_a^T xt_q
+    if (jb >= 2 && warp >= 1) gram_partial(jb - 1);
+    __syncthreads();
+    for (int e = tid; e < NPAIR; e += CP_THREADS) {
+        int q = 1, q2 = e;
+        while (q2 >= q) {
+            q2 -= q;
+            ++q;
+        }
+        double g = 0.0;
+        if (q < jb) {
+#pragma unroll
+            for (int w = 0; w < CP_WARPS - 1; ++w) g += gpart[w * NPAIR + e];
+            g *= sc_col[q] * sc_col[q2];
+        }
+        gram[e] = g;
+    }
+    // normalise the reflectors below the diagonal: v = xt / (alpha - beta)
+    for (int e = tid; e < nr * jb; e += CP_THREADS) {
+        const int li = e / jb, c = e - li * jb;
+        if (r0 + li > c) P[li * LDP + c] *= sc_col[c];
+    }
+    __syncthreads();
 
     // write back the panel and the explicit reflectors
     for (int e = tid; e < nr * jb; e += CP_THREADS) {
@@ -618,23 +675,6 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
         const double v = gi < c ? 0.0 : (gi == c ? 1.0 : (live ? pv : 0.0));
         V[static_cast<long long>(j0 + gi) * ldv + j0 + c] = v;
         W[static_cast<long long>(j0 + gi) * ld + j0 + c] = pv;
-    }
-    // partial Gram of the reflectors over this CTA's rows: for q2 < q,
-    //   g(q, q2) = v_q^T v_q2 = P[q][q2] + sum_{rows i > q} P[i][q] P[i][q2]
-    // (v_q is zero above row q and 1 at row q); pairs enumerated compactly.
-    for (int e = tid; e < JB * (JB - 1) / 2; e += CP_THREADS) {
-        int q = 1, q2 = e;
-        while (q2 >= q) {
-            q2 -= q;
-            ++q;
-        }
-        double g = 0.0;
-        if (q < jb) {
-            const int lq = q - r0;
-            if (lq >= 0 && lq < nr) g = P[lq * LDP + q2];
-            for (int li = max(0, lq + 1); li < nr; ++li) g = fma(P[li * LDP + q], P[li * LDP + q2], g);
-        }
-        gram[e] = g;
     }
     cluster.sync();
     if (rank == 0) {
