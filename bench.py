@@ -433,6 +433,9 @@ def main():
         }
         line.update(core_info)
         line.update(extras)
+        if "factors_ms" in extras:   # sketch + core + factors F (FP64 solve) and G
+            line["all_in"] = {"approx_per_s": 1e3 / (per_step_ms + extras["factors_ms"]),
+                              "ms": per_step_ms + extras["factors_ms"]}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -484,10 +487,12 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
     torch.cuda.synchronize()
     split_ms = s0.elapsed_time(s1) / reps
     split_sketch_ms = k0.elapsed_time(k1)
+    H.set_fp64_g(True)   # split BF16 aims at the FP64 path's error: G in FP64 too
     fl2 = 2 * 2.0 * m * n * (2 * r + l)
     out["split_bf16"] = {"approx_per_s": 1e3 / split_ms, "ms_per_step": split_ms, "sketch_ms": split_sketch_ms,
                          "sketch_tflops": fl2 / (split_sketch_ms / 1e3) / 1e12,
-                         "err": err_of(AX, YtA, core)}
+                         "err": err_of(AX, YtA, core), "g_fp64": True}
+    H.set_fp64_g(False)
     del Ahi, Alo
 
     # e4m3 path: one power-of-two scale per 128 x 128 tile, block-scaled MMAs

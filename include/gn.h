@@ -136,6 +136,15 @@ gn_status gn_sync_status(gn_handle h);
  * kernel drains its in-flight copies, frees its tensor memory and returns. */
 gn_status gn_set_wait_limit(gn_handle h, uint64_t ns);
 
+/* Precision of the factor G = Q_1^T (Y^T A) in gn_factors / gn_approx when
+ * Y^T A is GN_F32 (the tensor-core sketches).  0 (default): on the tensor
+ * cores from three BF16 slices of each factor with FP32 accumulation, i.e. at
+ * the precision of an FP32-accumulated Y^T A; 1: an FP64 product, for callers
+ * whose sketch reaches beyond FP32 accumulation error (split BF16 aiming at
+ * the FP64 path's error).  The triangular solve for F is FP64 either way
+ * (eq. 5.1: it carries the conditioning of R). */
+gn_status gn_set_fp64_g(gn_handle h, int32_t fp64_g);
+
 const char* gn_status_string(gn_status s);
 
 /* Number of SMs of the handle's device (the persistent grids use it). */

@@ -33,7 +33,7 @@ EPS_RELATIVE = 0x100
 
 # Every symbol declared in include/gn.h.
 ABI_SYMBOLS = (
-    "gn_create", "gn_destroy", "gn_set_stream", "gn_sync_status", "gn_set_wait_limit",
+    "gn_create", "gn_destroy", "gn_set_stream", "gn_sync_status", "gn_set_wait_limit", "gn_set_fp64_g",
     "gn_status_string", "gn_device_sm_count", "gn_workspace_size", "gn_quantize",
     "gn_sketch", "gn_core", "gn_factors", "gn_approx", "gn_error_fro2", "gn_hmt",
     "gn_kernel_launches", "gn_error_fro2_noalloc", "gn_backward_workspace_size", "gn_backward",
@@ -88,6 +88,7 @@ def _load():
         "gn_set_stream": ([P, P], I32),
         "gn_sync_status": ([P], I32),
         "gn_set_wait_limit": ([P, ctypes.c_uint64], I32),
+        "gn_set_fp64_g": ([P, I32], I32),
         "gn_status_string": ([I32], ctypes.c_char_p),
         "gn_device_sm_count": ([P], ctypes.c_int),
         "gn_workspace_size": ([I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
@@ -267,6 +268,10 @@ class Handle:
 
     def set_wait_limit(self, ns: int):
         _check(lib.gn_set_wait_limit(self._h, int(ns)), "gn_set_wait_limit")
+
+    def set_fp64_g(self, on: bool):
+        """G = Q_1^T (Y^T A) in FP64 (True) or on the tensor cores (False, default) for FP32 Y^T A."""
+        _check(lib.gn_set_fp64_g(self._h, 1 if on else 0), "gn_set_fp64_g")
 
     # ---------------------------------------------------------------- sizing
     @staticmethod

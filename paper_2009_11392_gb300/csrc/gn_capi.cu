@@ -123,7 +123,15 @@ size_t sketch_e4m3_ws(long long m, long long n, long long r, long long l) {
 // e4m3 X in the core product: an exact BF16 copy of X^T (r x n) ahead of the core workspace.
 size_t core_e4m3_ws(long long n, long long r) { return align256(sizeof(__nv_bfloat16) * r * round8(n)) + 256; }
 
-size_t factors_ws(long long m, long long r, int sms) { return trsm_ws_bytes(m, r, sms) + dgemm_ws_bytes(m, r, r, sms) + 1024; }
+// Factors: the FP64 solves' scratch, plus (FP32 Y^T A) the BF16 slices of Y^T A
+// and Q_1 and the FP32 product G.
+size_t factors_ws(long long m, long long n, long long r, long long l, int mixed, int sms) {
+    size_t b = trsm_ws_bytes(m, r, sms) + dgemm_ws_bytes(m, r, r, sms) + 1024;
+    if (mixed)
+        b += 3 * align256(sizeof(__nv_bfloat16) * (r + l) * round8(n)) +
+             3 * align256(sizeof(__nv_bfloat16) * (r + l) * round8(r)) + align256(sizeof(float) * r * round8(n));
+    return b;
+}
 
 size_t hmt_ws(long long m, long long n, long long r, int sms) {
     return align256(sizeof(double) * m * r) + align256(sizeof(double) * r * r) + qr_ws_bytes(m, r, sms) +
@@ -300,6 +308,7 @@ gn_status gn_create(gn_handle* out, void* stream) {
     h->batched_ws = nullptr;
     h->batched_count = h->batched_sk_tiles = h->batched_c_tiles = 0;
     h->batched_policy = 0;
+    h->fp64_g = 0;
     if (cudaMalloc(&h->dstatus, 64) != cudaSuccess) {
         delete h;
         return GN_ERR_CUDA;
@@ -354,6 +363,12 @@ gn_status gn_set_stream(gn_handle h, void* stream) {
     return GN_OK;
 }
 
+gn_status gn_set_fp64_g(gn_handle h, int32_t fp64_g) {
+    if (!h || (fp64_g != 0 && fp64_g != 1)) return GN_ERR_INVALID_ARG;
+    h->fp64_g = fp64_g;
+    return GN_OK;
+}
+
 gn_status gn_set_wait_limit(gn_handle h, uint64_t ns) {
     if (!h || ns == 0) return GN_ERR_INVALID_ARG;
     h->wait_limit_ns = ns;
@@ -383,7 +398,7 @@ gn_status gn_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t 
     const int mixed = op_dtype != GN_F64;
     size_t b = core_ws(n, r, l, mixed, sms) + (op_dtype == GN_E4M3 ? core_e4m3_ws(n, r) : 0);
     if (op_dtype == GN_E4M3) b = std::max(b, sketch_e4m3_ws(m, n, r, l));
-    b = std::max(b, factors_ws(m, r, sms));
+    b = std::max(b, factors_ws(m, n, r, l, mixed, sms));
     b = std::max(b, hmt_ws(m, n, r, sms));
     b = std::max(b, error_ws_bytes(m, n, sms));
     *bytes = b;
@@ -600,10 +615,26 @@ gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_
         return GN_ERR_SHAPE;
     if (AX->dtype != GN_F64 && AX->dtype != GN_F32) return GN_ERR_DTYPE;
     if (YtA->dtype != GN_F64 && YtA->dtype != GN_F32) return GN_ERR_DTYPE;
-    if (ws_bytes < factors_ws(m, r, h->sm_count)) return GN_ERR_WORKSPACE;
+    const int tc_g = YtA->dtype == GN_F32 && !h->fp64_g;
+    if (ws_bytes < factors_ws(m, n, r, l, tc_g, h->sm_count)) return GN_ERR_WORKSPACE;
     double* Fd = static_cast<double*>(F->data);
     double* Gd = static_cast<double*>(G->data);
-    double* gws = static_cast<double*>(ws);
+    // FP32 Y^T A: G = Q_1^T (Y^T A) on the tensor cores from three BF16 slices of
+    // each factor (the six slice products of order <= 2: FP32-level accuracy,
+    // below the sketch's own error); the FP64 path keeps an FP64 product.
+    Carve cv{static_cast<char*>(ws), ws_bytes, 0, true};
+    const long long rl = r + l, lds = round8(n), ldq = round8(k);
+    __nv_bfloat16 *sl[3] = {nullptr, nullptr, nullptr}, *ql[3] = {nullptr, nullptr, nullptr};
+    float* g32 = nullptr;
+    if (tc_g) {
+        for (int i = 0; i < 3; ++i) sl[i] = cv.take<__nv_bfloat16>(rl * lds);
+        for (int i = 0; i < 3; ++i) ql[i] = cv.take<__nv_bfloat16>(rl * ldq);
+        g32 = cv.take<float>(k * lds);
+        if (!cv.ok) return GN_ERR_WORKSPACE;
+    }
+    size_t gws_bytes = 0;
+    double* gws = cv.rest(&gws_bytes);
+    ws_bytes = gws_bytes;
     const bool truncated = core->sgn && k < r;
     if (!truncated) {
         // F = AX R^{-1}
@@ -625,10 +656,37 @@ gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_
         GN_TRY(trsm_right_upper(h, Fd, m, k, F->ld, core->R2, r, 1, gws, ws_bytes));
     }
     // G = Q_1^T (Y^T A)
-    if (YtA->dtype == GN_F32)
+    if (YtA->dtype == GN_F32 && !tc_g) {
         GN_TRY(dgemm_b32(h, k, n, r + l, 1.0, core->Q, r, 1, static_cast<const float*>(YtA->data), YtA->ld, 0,
                          0.0, Gd, G->ld, gws, ws_bytes));
-    else
+    } else if (tc_g) {
+        GN_TRY(split3_bf16(h, static_cast<const float*>(YtA->data), rl, n, YtA->ld, sl[0], sl[1], sl[2], lds));
+        GN_TRY(split3_f64_bf16(h, core->Q, rl, k, r, ql[0], ql[1], ql[2], ldq));
+        TcParams p;
+        memset(&p, 0, sizeof(p));
+        for (int i = 0; i < 3; ++i) {
+            GN_TRY(tc_make_map_bf16(&p.maps[i], ql[i], rl, k, ldq, 64, 64));       // Q_1^T: MN-major A operand
+            GN_TRY(tc_make_map_bf16(&p.maps[3 + i], sl[i], rl, n, lds, 64, 64));   // slices: MN-major B operand
+        }
+        TcGemm& g = p.g[0];
+        g.M = static_cast<int>(k);
+        g.N = static_cast<int>(n);
+        g.K = static_cast<int>(rl);
+        g.bn = 256;
+        g.a_mn = 1;
+        g.b_mn = 1;
+        g.nsrc = 6;
+        const int am[6] = {0, 0, 1, 0, 1, 2}, bm[6] = {3, 4, 3, 5, 4, 3};   // slice orders 0, 1, 1, 2, 2, 2
+        for (int i = 0; i < 6; ++i) {
+            g.a_map[i] = am[i];
+            g.b_map[i] = bm[i];
+        }
+        g.D = g32;
+        g.ldd = lds;
+        p.ngemm = 1;
+        GN_TRY(tc_launch(h, &p));
+        GN_TRY(copy_f32_to_f64(h, g32, k, n, lds, Gd, G->ld));
+    } else
         GN_TRY(dgemm(h, k, n, r + l, 1.0, core->Q, r, 1, static_cast<const double*>(YtA->data), YtA->ld, 0, 0.0,
                      Gd, G->ld, gws, ws_bytes));
     return GN_OK;

@@ -1831,24 +1831,41 @@ size_t trsm_ws_bytes(long long m, long long k, int sm_count) {
 gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, long long ldf,
                            const double* R, long long ldr, int trans, double* ws, size_t ws_bytes) {
     if (m <= 0 || k <= 0) return GN_OK;
-    const long long nb = (k + TB - 1) / TB;
+    // Two levels of blocking: 128-column outer blocks take the bulk of the
+    // update as one wide FP64 GEMM each; inside, 32-column blocks take a narrow
+    // GEMM over the outer block and the per-row triangular solve.
+    constexpr long long OB = 128;
+    const long long nob = (k + OB - 1) / OB;
     const int blocks = static_cast<int>((m + 127) / 128);
-    for (long long bi = 0; bi < nb; ++bi) {
-        const long long b = trans ? nb - 1 - bi : bi;
-        const long long j0 = b * TB;
-        const int jb = static_cast<int>(std::min<long long>(TB, k - j0));
-        if (!trans && j0 > 0) {
-            // F[:, J] -= F[:, 0:j0] R[0:j0, J]
-            GN_TRY(dgemm(h, m, jb, j0, -1.0, F, ldf, 0, R + j0, ldr, 0, 1.0, F + j0, ldf, ws, ws_bytes));
+    for (long long obi = 0; obi < nob; ++obi) {
+        const long long ob = trans ? nob - 1 - obi : obi;
+        const long long J0 = ob * OB, JB = std::min<long long>(OB, k - J0);
+        if (!trans && J0 > 0)   // F[:, J] -= F[:, 0:J0] R[0:J0, J]
+            GN_TRY(dgemm(h, m, JB, J0, -1.0, F, ldf, 0, R + J0, ldr, 0, 1.0, F + J0, ldf, ws, ws_bytes));
+        if (trans && J0 + JB < k) {   // F[:, J] -= F[:, J+] R[J, J+]^T
+            const long long kk = k - J0 - JB;
+            GN_TRY(dgemm(h, m, JB, kk, -1.0, F + J0 + JB, ldf, 0, R + J0 * ldr + J0 + JB, ldr, 1, 1.0, F + J0, ldf,
+                         ws, ws_bytes));
         }
-        if (trans && j0 + jb < k) {
-            // F[:, J] -= F[:, J+] R[J, J+]^T
-            const long long kk = k - j0 - jb;
-            GN_TRY(dgemm(h, m, jb, kk, -1.0, F + j0 + jb, ldf, 0, R + j0 * ldr + j0 + jb, ldr, 1, 1.0,
-                         F + j0, ldf, ws, ws_bytes));
+        const long long nb = (JB + TB - 1) / TB;
+        for (long long bi = 0; bi < nb; ++bi) {
+            const long long b = trans ? nb - 1 - bi : bi;
+            const long long j0 = J0 + b * TB;
+            const int jb = static_cast<int>(std::min<long long>(TB, J0 + JB - j0));
+            if (!trans && j0 > J0) {
+                // F[:, j] -= F[:, J0:j0] R[J0:j0, j]
+                GN_TRY(dgemm(h, m, jb, j0 - J0, -1.0, F + J0, ldf, 0, R + J0 * ldr + j0, ldr, 0, 1.0, F + j0, ldf, ws,
+                             ws_bytes));
+            }
+            if (trans && j0 + jb < J0 + JB) {
+                // F[:, j] -= F[:, j+ .. J0+JB] R[j, j+ ..]^T
+                const long long kk = J0 + JB - j0 - jb;
+                GN_TRY(dgemm(h, m, jb, kk, -1.0, F + j0 + jb, ldf, 0, R + j0 * ldr + j0 + jb, ldr, 1, 1.0, F + j0, ldf,
+                             ws, ws_bytes));
+            }
+            trsm_diag_kernel<<<blocks, 128, 0, h->stream>>>(F, m, ldf, static_cast<int>(j0), jb, R, ldr, trans); count_launch();
+            GN_CUDA_TRY(cudaGetLastError());
         }
-        trsm_diag_kernel<<<blocks, 128, 0, h->stream>>>(F, m, ldf, static_cast<int>(j0), jb, R, ldr, trans); count_launch();
-        GN_CUDA_TRY(cudaGetLastError());
     }
     return GN_OK;
 }
@@ -1914,6 +1931,31 @@ gn_status copy_f32_to_f64(gn_handle h, const float* src, long long rows, long lo
                           double* dst, long long ldd) {
     if (rows * cols == 0) return GN_OK;
     copy_f32_f64_kernel<<<ew_blocks(h, rows * cols), 256, 0, h->stream>>>(src, rows, cols, lds, dst, ldd); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+__global__ void split3_f64_kernel(const double* __restrict__ s, long long rows, long long cols, long long lds,
+                                  __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* lo, long long ldd) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e % cols;
+        const double x = s[i * lds + j];
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        const double r1 = x - static_cast<double>(__bfloat162float(h));
+        const __nv_bfloat16 m = __double2bfloat16(r1);
+        const double r2 = r1 - static_cast<double>(__bfloat162float(m));
+        hi[i * ldd + j] = h;
+        mid[i * ldd + j] = m;
+        lo[i * ldd + j] = __double2bfloat16(r2);
+    }
+}
+
+gn_status split3_f64_bf16(gn_handle h, const double* src, long long rows, long long cols, long long lds,
+                          __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* lo, long long ldd) {
+    if (rows * cols == 0) return GN_OK;
+    split3_f64_kernel<<<ew_blocks(h, rows * cols), 256, 0, h->stream>>>(src, rows, cols, lds, hi, mid, lo, ldd); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     return GN_OK;
 }

@@ -25,6 +25,7 @@ struct gn_handle_s {
     void* batched_ws;
     int batched_count, batched_sk_tiles, batched_c_tiles;
     int batched_policy;        // tile policy of the next gn_batched_prepare
+    int fp64_g;                // gn_factors: FP64 G even for FP32 Y^T A
 };
 
 #define GN_CUDA_TRY(expr)                                   \
@@ -50,7 +51,7 @@ void count_launch();
 
 constexpr int TC_MAX_MAPS = 12;
 constexpr int TC_MAX_GEMMS = 4;
-constexpr int TC_MAX_SRC = 3;
+constexpr int TC_MAX_SRC = 6;
 
 struct TcGemm {
     int M, N, K;             // D is M x N, contraction length K
@@ -162,6 +163,9 @@ gn_status core_diagnostics(gn_handle h, const double* R, long long r, long long 
 
 gn_status copy_f32_to_f64(gn_handle h, const float* src, long long rows, long long cols,
                           long long lds, double* dst, long long ldd);
+// FP64 -> three BF16 slices hi + mid + lo (residuals taken in FP64).
+gn_status split3_f64_bf16(gn_handle h, const double* src, long long rows, long long cols, long long lds,
+                          __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* lo, long long ldd);
 gn_status split3_bf16(gn_handle h, const float* src, long long rows, long long cols, long long lds,
                       __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* lo, long long ldd);
 gn_status sum3_f32_to_f64(gn_handle h, const float* a, const float* b, const float* c,

@@ -228,6 +228,37 @@ def test_fp64_core_r2000_properties(gn, H):
     assert core.k == r and core.sgn == 0
 
 
+def test_factor_g_tensor_core_vs_fp64(gn, H):
+    """For FP32 Y^T A the factor G = Q_1^T (Y^T A) is formed on the tensor cores
+    from three BF16 slices of each operand; against the FP64 product (the
+    gn_set_fp64_g path) it agrees to FP32 accumulation accuracy, and F (the
+    FP64 triangular solve) is identical."""
+    m, n, r, l = 900, 700, 60, 30
+    A = gn_synth.gaussian((m, n), 41, 0) * torch.pow(0.97, torch.arange(n, dtype=torch.float64))
+    X, Y = gn_synth.sketches(m, n, r, l, 42)
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+    H.sketch(bf16_operand(gn, A), bf16_operand(gn, X), bf16_operand(gn, Y), AX, YtA, ws)
+    core = _core_tensors(gn, r, l)
+    H.core(YtA, bf16_operand(gn, X), 10 * O.U32, gn.PLAIN, core, ws)
+    F1 = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    G1 = torch.empty(r, n, dtype=torch.float64, device="cuda")
+    F2, G2 = torch.empty_like(F1), torch.empty_like(G1)
+    H.factors(AX, YtA, core, F1, G1, ws)
+    H.set_fp64_g(True)
+    try:
+        H.factors(AX, YtA, core, F2, G2, ws)
+    finally:
+        H.set_fp64_g(False)
+    assert H.sync_status() == 0
+    assert torch.equal(F1, F2)
+    Q, S = npy(core.Q), npy(YtA)
+    bound = 4 * (r + l) * O.U32 * (np.abs(Q).T @ np.abs(S))
+    assert np.all(np.abs(npy(G1) - npy(G2)) <= bound)
+    assert rel(npy(G2), Q.T @ S) <= 1e-12
+
+
 @pytest.mark.parametrize("mode", ["plain", "auto"])
 def test_fp64_gn_config1(gn, H, mode):
     """The 1000 x 500 geometric case: factors and A_hat at 1e-10."""
