@@ -84,6 +84,10 @@ struct TcParams {
     int32_t* status;
     unsigned long long wait_limit_ns;
     int f8;                    // 1: e4m3 operands (K-major, block-scaled MMA, bn = 128)
+    // Balanced last round: cluster tiles [split_base, split_base + nsplit) run
+    // as two halves of their K range each (work items split_base + 2u, + 2u + 1),
+    // adding into a pre-zeroed D.
+    int split_base, nsplit;
 };
 
 // Host helpers (gn_tc.cu).

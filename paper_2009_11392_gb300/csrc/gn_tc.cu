@@ -261,6 +261,7 @@ __device__ __forceinline__ uint32_t instr_desc_bf16(int m, int n, int a_mn, int 
 
 struct TileCoord {
     int g, tm, tn;
+    int half;   // 0: whole K range; 1, 2: first / second half (adds into D)
 };
 
 // GEMM descriptors and tensor maps live in the kernel parameters (up to four
@@ -279,6 +280,12 @@ template <bool GROUPED, int CL>
 __device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t, int crank) {
     // tiles_m / tiles_n / tile_base are in units of this launch's tile shape
     TileCoord c;
+    c.half = 0;
+    if (!GROUPED && p.nsplit > 0 && t >= p.split_base) {
+        const int u = t - p.split_base;
+        c.half = 1 + (u & 1);
+        t = p.split_base + (u >> 1);
+    }
     if (GROUPED) {   // last GEMM whose tile_base <= t
         int lo = 0, hi = p.ngemm - 1;
         while (lo < hi) {
@@ -382,8 +389,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                 const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
+                const int kb0 = c.half == 2 ? nkb / 2 : 0, kb1 = c.half == 1 ? nkb / 2 : nkb;
                 const uint32_t bytes = A_STAGE_BYTES + G.bn * BK * 2 + K::SF_STAGE;
-                for (int kb = 0; kb < nkb; ++kb) {
+                for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(empty_bar(stage), ephase ^ 1u, limit, abort_flag)) {
                         latch(p.status, GN_ERR_TIMEOUT, 1, abort_flag);
                         ok = false;
@@ -469,6 +477,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                 const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
+                const int kb0 = c.half == 2 ? nkb / 2 : 0, kb1 = c.half == 1 ? nkb / 2 : nkb;
                 const uint32_t idesc = F8 ? 0u : instr_desc_bf16(BM, G.bn, G.a_mn, G.b_mn);
                 if (!mbar_wait(tempty_bar(acc), aphase ^ 1u, limit, abort_flag)) {
                     latch(p.status, GN_ERR_TIMEOUT, 3, abort_flag);
@@ -476,7 +485,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + acc * MT * 256;
-                for (int kb = 0; kb < nkb; ++kb) {
+                for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(full_bar(stage), fphase, limit, abort_flag)) {
                         latch(p.status, GN_ERR_TIMEOUT, 4, abort_flag);
                         ok = false;
@@ -501,7 +510,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
 #pragma unroll
                             for (int hh = 0; hh < MT; ++hh)
                                 tc_mma_mxf8(d_tmem + 256u * hh, smem_desc(sa + 16384u * hh + 32u * k, 16u, 1024u), bd, id,
-                                            tsf + 4u * hh, tsf + 8u, (kb | k) != 0 ? 1u : 0u);
+                                            tsf + 4u * hh, tsf + 8u, (kb != kb0 || k != 0) ? 1u : 0u);
                         }
                     } else {
 #pragma unroll
@@ -513,7 +522,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                                 const uint32_t sah = sa + 16384u * hh;
                                 const uint64_t ad = G.a_mn ? smem_desc(sah + 2048u * k, 8192u, 1024u)
                                                            : smem_desc(sah + 32u * k, 16u, 1024u);
-                                tc_mma_bf16(d_tmem + 256u * hh, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                                tc_mma_bf16(d_tmem + 256u * hh, ad, bd, idesc, (kb != kb0 || k != 0) ? 1u : 0u);
                             }
                         }
                     }
@@ -563,7 +572,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + (acc * MT + hh) * 256 + c0, v);
                     const int col0 = c.tn * G.bn + c0;
                     if (!row_ok || col0 >= G.N) continue;
-                    if (G.vec4 && col0 + 32 <= G.N) {
+                    if (c.half) {   // half of the K range: add into the pre-zeroed D
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (col0 + j < G.N) atomicAdd(drow + col0 + j, __uint_as_float(v[j]));
+                    } else if (G.vec4 && col0 + 32 <= G.N) {
                         float4* dst = reinterpret_cast<float4*>(drow + col0);
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
@@ -712,6 +725,29 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
         TcGemm& G = p->g[i];
         G.tile_base = total;
         total += ((G.tiles_m + CL - 1) / CL) * G.tiles_n;
+    }
+    // Balance the last round: when the cluster tiles leave a partial round of R
+    // tiles (R <= half the clusters) that are whole rows of cluster tiles of the
+    // last GEMM with A K-major (a contiguous row range of its D), those R tiles
+    // run as 2R half-K items adding into D, zeroed first; the last round then
+    // costs half a tile.
+    p->split_base = 0;
+    p->nsplit = 0;
+    if (!p->f8 && total > 0) {
+        const int ncl = std::min(total, h->sm_count / CL);
+        const int R = total % ncl;
+        const TcGemm& G = p->g[p->ngemm - 1];
+        if (total > ncl && R > 0 && 2 * R <= ncl && !G.a_mn && R % G.tiles_n == 0 && G.nsrc * G.kblocks >= 8) {
+            const int ctm_n = (G.tiles_m + CL - 1) / CL;
+            const long long row0 = static_cast<long long>(ctm_n - R / G.tiles_n) * CL * BM * MT;
+            if (row0 >= 0 && row0 < G.M) {
+                GN_CUDA_TRY(cudaMemset2DAsync(G.D + row0 * G.ldd, sizeof(float) * G.ldd, 0, sizeof(float) * G.N,
+                                              G.M - row0, h->stream));
+                p->split_base = total - R;
+                p->nsplit = R;
+                total += R;
+            }
+        }
     }
     p->total_tiles = total;
     p->gg = nullptr;
