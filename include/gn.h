@@ -308,8 +308,9 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
  *   bits 0-1: N tile of every Y^T A product: 0 -> 128, 1 -> 64, 2 -> 256
  *   bit 2   : N tile 64 for AX when 64 < r (two tiles instead of one)
  *   bit 3   : problems ordered by decreasing sketch work in the tile list
+ *   bit 4   : 256-row sketch tiles (two M halves share each B stage)
  * The paper has no batched mode; the policy is this library's. */
-#define GN_BATCHED_POLICIES 12
+#define GN_BATCHED_POLICIES 24
 gn_status gn_batched_set_policy(gn_handle h, int32_t policy);
 
 /* Autotuner: for each of the GN_BATCHED_POLICIES policies, prepare the batch

@@ -475,6 +475,7 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
     std::vector<ProblemDev> pd(count);
     int sk_tiles = 0, c_tiles = 0;
     const int policy = h->batched_policy;
+    const int sk_mt = (policy & 16) ? 2 : 1;
     const int bn_yta = (policy & 3) == 1 ? 64 : ((policy & 3) == 2 ? 256 : 128);
     // position of each problem's two sketch GEMMs in the tile list
     std::vector<int> slot(count);
@@ -583,7 +584,7 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
         }
     }
     for (int pos = 0; pos < 2 * count; ++pos) {   // tile bases in list order
-        GN_TRY(tc_prepare_gemm(&sk[pos], sk_tiles));
+        GN_TRY(tc_prepare_gemm(&sk[pos], sk_tiles, sk_mt));
         sk_tiles += sk[pos].tiles_m * sk[pos].tiles_n;
     }
     if (off > ws_bytes) return GN_ERR_WORKSPACE;
@@ -605,13 +606,14 @@ gn_status gn_batched_prepare(gn_handle h, int32_t count, const gn_problem* probs
     // keep the host-side counts in the header's host mirror (the run call re-reads them)
     h->batched_count = count;
     h->batched_sk_tiles = sk_tiles;
+    h->batched_mt = sk_mt;
     h->batched_c_tiles = c_tiles;
     h->batched_ws = ws;
     return GN_OK;
 }
 
 gn_status gn_batched_set_policy(gn_handle h, int32_t policy) {
-    if (!h || policy < 0 || policy >= 16 || (policy & 3) == 3) return GN_ERR_INVALID_ARG;
+    if (!h || policy < 0 || policy >= 32 || (policy & 3) == 3) return GN_ERR_INVALID_ARG;
     h->batched_policy = policy;
     return GN_OK;
 }
@@ -619,7 +621,8 @@ gn_status gn_batched_set_policy(gn_handle h, int32_t policy) {
 gn_status gn_batched_tune(gn_handle h, int32_t count, const gn_problem* probs, void* ws, size_t ws_bytes,
                           double eps, int32_t mode, int32_t* best, double* best_ms) {
     if (!h || !best) return GN_ERR_INVALID_ARG;
-    static const int kPolicies[GN_BATCHED_POLICIES] = {0, 1, 2, 4, 5, 6, 8, 9, 10, 12, 13, 14};
+    static const int kPolicies[GN_BATCHED_POLICIES] = {0,  1,  2,  4,  5,  6,  8,  9,  10, 12, 13, 14,
+                                                       16, 17, 18, 20, 21, 22, 24, 25, 26, 28, 29, 30};
     cudaEvent_t e0, e1;
     GN_CUDA_TRY(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -673,7 +676,8 @@ gn_status gn_batched_run(gn_handle h, double eps, int32_t mode, void* ws, size_t
     const size_t o_ord = o_p + al(sizeof(ProblemDev) * count);
     (void)ws_bytes;
     const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(base + o_maps);
-    GN_TRY(tc_launch_grouped(h, reinterpret_cast<const TcGemm*>(base + o_sk), 2 * count, maps, h->batched_sk_tiles));
+    GN_TRY(tc_launch_grouped(h, reinterpret_cast<const TcGemm*>(base + o_sk), 2 * count, maps, h->batched_sk_tiles,
+                             h->batched_mt));
     const ProblemDev* pd = reinterpret_cast<const ProblemDev*>(base + o_p);
     batched_split3_kernel<<<dim3(16, count), 256, 0, h->stream>>>(pd);
     count_launch();

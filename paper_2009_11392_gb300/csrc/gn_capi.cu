@@ -307,6 +307,7 @@ gn_status gn_create(gn_handle* out, void* stream) {
     h->wait_limit_ns = 2000000000ULL;
     h->batched_ws = nullptr;
     h->batched_count = h->batched_sk_tiles = h->batched_c_tiles = 0;
+    h->batched_mt = 1;
     h->batched_policy = 0;
     h->fp64_g = 0;
     if (cudaMalloc(&h->dstatus, 64) != cudaSuccess) {

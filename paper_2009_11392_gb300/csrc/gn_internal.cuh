@@ -23,7 +23,7 @@ struct gn_handle_s {
     uint64_t wait_limit_ns;
     // batched path: the tables gn_batched_prepare uploaded into batched_ws
     void* batched_ws;
-    int batched_count, batched_sk_tiles, batched_c_tiles;
+    int batched_count, batched_sk_tiles, batched_c_tiles, batched_mt;
     int batched_policy;        // tile policy of the next gn_batched_prepare
     int fp64_g;                // gn_factors: FP64 G even for FP32 Y^T A
 };
@@ -114,7 +114,7 @@ gn_status e4m3_t_to_bf16(gn_handle h, const uint8_t* data_t, long long ld_t, con
 // Grouped launch: descriptors (tile_base ascending) and tensor maps already in
 // device memory; any number of GEMMs.
 gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, const CUtensorMap* dev_maps,
-                            int total_tiles);
+                            int total_tiles, int mt = 1);
 
 // --------------------------------------------------------------------------
 // FP64 / FP32 helper kernels (gn_f64.cu)

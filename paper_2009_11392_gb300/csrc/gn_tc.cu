@@ -771,7 +771,7 @@ gn_status tc_prepare_gemm(TcGemm* G, int tile_base, int mt, int f8) {
 }
 
 gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, const CUtensorMap* dev_maps,
-                            int total_tiles) {
+                            int total_tiles, int mt) {
     if (total_tiles <= 0 || ngemm <= 0) return GN_OK;
     TcParams p;
     memset(&p, 0, sizeof(p));
@@ -781,7 +781,7 @@ gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, con
     p.total_tiles = total_tiles;
     p.status = h->dstatus;
     p.wait_limit_ns = h->wait_limit_ns;
-    return launch_cfg<true, 1, 1>(h, p, total_tiles);
+    return mt == 2 ? launch_cfg<true, 1, 2>(h, p, total_tiles) : launch_cfg<true, 1, 1>(h, p, total_tiles);
 }
 
 }  // namespace gn

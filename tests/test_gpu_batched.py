@@ -109,7 +109,7 @@ def test_batched_autotuner_keeps_results(gn, H):
     probs = [_problem(gn, 20 + i, *s) for i, s in enumerate(SHAPES)]
     ws = H.batched_prepare(probs)
     best, ms = H.batched_tune(0.0, gn.PLAIN, ws)
-    assert best in (0, 1, 2, 4, 5, 6, 8, 9, 10, 12, 13, 14) and ms > 0
+    assert best in (0, 1, 2, 4, 5, 6, 8, 9, 10, 12, 13, 14, 16, 17, 18, 20, 21, 22, 24, 25, 26, 28, 29, 30) and ms > 0
     for p in probs:
         p["AX"].fill_(float("nan"))
         p["YtA"].fill_(float("nan"))
@@ -125,7 +125,7 @@ def test_batched_autotuner_keeps_results(gn, H):
         torch.cuda.synchronize()
         assert torch.equal(p["AX"], AX) and torch.equal(p["YtA"], YtA)
         assert int(p["k"].item()) == r
-    for pol in (1, 2, 4, 8, 14):   # every policy gives the same sketches
+    for pol in (1, 2, 4, 8, 14, 16, 30):   # every policy gives the same sketches
         H.batched_set_policy(pol)
         ws2 = H.batched_prepare(probs)
         H.batched_run(0.0, gn.PLAIN, ws2)
