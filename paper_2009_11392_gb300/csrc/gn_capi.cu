@@ -181,8 +181,11 @@ gn_status launch_sketch_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const 
     g1.M = static_cast<int>(rl);
     g1.N = static_cast<int>(n);
     g1.K = static_cast<int>(m);
-    // Per-tile cost ~ bn * K: halve the N tile when K is twice the other GEMM's.
-    g1.bn = (m >= 2 * n) ? 128 : 256;
+    // Per-tile cost ~ bn * K.  When K = m is much longer than the other GEMM's,
+    // the tiles keep bn = 256 (the fewest L2 bytes per flop) and run as two
+    // half-K items each, so that every item costs about the same.
+    g1.bn = 256;
+    g1.ksplit = (2 * 256LL * m >= 3LL * g0.bn * n) ? 2 : 1;
     g1.a_mn = 1;
     g1.b_mn = 1;
     g1.nsrc = nsrc;

@@ -65,6 +65,8 @@ struct TcGemm {
     float* D;
     long long ldd;
     int vec4;                // D rows 16-byte aligned -> float4 stores
+    int ksplit;              // 2: every tile runs as two half-K items adding into a pre-zeroed D
+                             // (single launches only; 0 or 1: whole K)
     // e4m3 launches (TcParams::f8): scale-factor images, 512 bytes of the tile's
     // UE8M0 byte per 128 x 128 tile of the original matrix, row-major over tiles.
     const uint8_t* sfa;

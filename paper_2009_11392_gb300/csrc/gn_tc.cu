@@ -303,7 +303,21 @@ __device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t, int c
     const int local = t - G.tile_base;
     const int ctm_n = (G.tiles_m + CL - 1) / CL;   // cluster tiles along M
     int ctm;
-    if (G.a_mn) {   // A operand is the small sketch (Y^T): walk M fastest so the big B is shared
+    if (!GROUPED && G.ksplit == 2) {
+        // the two K halves of a tile are separate items; the items that share an
+        // operand panel (same half) stay consecutive
+        if (G.a_mn) {
+            ctm = local % ctm_n;
+            const int v = local / ctm_n;
+            c.half = 1 + (v & 1);
+            c.tn = v >> 1;
+        } else {
+            c.tn = local % G.tiles_n;
+            const int v = local / G.tiles_n;
+            c.half = 1 + (v & 1);
+            ctm = v >> 1;
+        }
+    } else if (G.a_mn) {   // A operand is the small sketch (Y^T): walk M fastest so the big B is shared
         ctm = local % ctm_n;
         c.tn = local / ctm_n;
     } else {        // walk N fastest so the big A row panel is shared
@@ -573,9 +587,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     const int col0 = c.tn * G.bn + c0;
                     if (!row_ok || col0 >= G.N) continue;
                     if (c.half) {   // half of the K range: add into the pre-zeroed D
+                        if (G.vec4 && col0 + 32 <= G.N) {
+                            float4* dst = reinterpret_cast<float4*>(drow + col0);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (col0 + j < G.N) atomicAdd(drow + col0 + j, __uint_as_float(v[j]));
+                            for (int j = 0; j < 8; ++j)
+                                atomicAdd(dst + j, make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                                               __uint_as_float(v[4 * j + 2]),
+                                                               __uint_as_float(v[4 * j + 3])));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (col0 + j < G.N) atomicAdd(drow + col0 + j, __uint_as_float(v[j]));
+                        }
                     } else if (G.vec4 && col0 + 32 <= G.N) {
                         float4* dst = reinterpret_cast<float4*>(drow + col0);
 #pragma unroll
@@ -723,8 +746,11 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
     int total = 0;
     for (int i = 0; i < p->ngemm; ++i) {
         TcGemm& G = p->g[i];
+        if (G.ksplit == 2 && (p->f8 || G.nsrc * G.kblocks < 8)) G.ksplit = 1;
         G.tile_base = total;
-        total += ((G.tiles_m + CL - 1) / CL) * G.tiles_n;
+        total += ((G.tiles_m + CL - 1) / CL) * G.tiles_n * (G.ksplit == 2 ? 2 : 1);
+        if (G.ksplit == 2)   // both halves add into D
+            GN_CUDA_TRY(cudaMemset2DAsync(G.D, sizeof(float) * G.ldd, 0, sizeof(float) * G.N, G.M, h->stream));
     }
     // Balance the last round: when the cluster tiles leave a partial round of R
     // tiles (R <= half the clusters) that are whole rows of cluster tiles of the
@@ -737,7 +763,8 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
         const int ncl = std::min(total, h->sm_count / CL);
         const int R = total % ncl;
         const TcGemm& G = p->g[p->ngemm - 1];
-        if (total > ncl && R > 0 && 2 * R <= ncl && !G.a_mn && R % G.tiles_n == 0 && G.nsrc * G.kblocks >= 8) {
+        if (total > ncl && R > 0 && 2 * R <= ncl && !G.a_mn && G.ksplit != 2 && R % G.tiles_n == 0 &&
+            G.nsrc * G.kblocks >= 8) {
             const int ctm_n = (G.tiles_m + CL - 1) / CL;
             const long long row0 = static_cast<long long>(ctm_n - R / G.tiles_n) * CL * BM * MT;
             if (row0 >= 0 && row0 < G.M) {

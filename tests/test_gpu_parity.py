@@ -84,7 +84,7 @@ def test_fp64_sketch_parity(gn, H, m, n, r, l):
 
 
 # --------------------------------------------------------- tensor-core sketches
-@pytest.mark.parametrize("m,n,r,l", [(300, 200, 70, 35), (128, 64, 16, 8), (520, 390, 130, 65)])
+@pytest.mark.parametrize("m,n,r,l", [(300, 200, 70, 35), (128, 64, 16, 8), (520, 390, 130, 65), (1100, 300, 70, 35)])
 def test_tc_sketch_exact_on_integer_inputs(gn, H, m, n, r, l):
     """Small integers are exact in bf16, and every partial sum stays an
     integer below 2^24, so FP32 accumulation is exact: bitwise parity."""
