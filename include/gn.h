@@ -145,6 +145,34 @@ gn_status gn_set_wait_limit(gn_handle h, uint64_t ns);
  * (eq. 5.1: it carries the conditioning of R). */
 gn_status gn_set_fp64_g(gn_handle h, int32_t fp64_g);
 
+/* How gn_factors / gn_approx compute the large FP64 products of the solve for
+ * F when AX is GN_F32 (the tensor-core sketches): the outer-block updates of
+ * the triangular solve F R = AX (eq. 5.1) and, after a truncation, AX Q_2.
+ * 1 (default): on the BF16 tensor cores by exact digit slicing (gn_dgemm_tc;
+ * FP64-level accuracy); 0: on the FP64 units.  The small diagonal-block solves
+ * stay in FP64 either way; FP64 sketches always use the FP64 units. */
+gn_status gn_set_fp64_tc(gn_handle h, int32_t on);
+
+/* C = alpha op(A) op(B) + beta C, FP64 (A may be FP32), computed on the BF16
+ * tensor cores by exact digit slicing (the error-free splitting of Ozaki,
+ * Ogita, Oishi and Rump, 2012).  Row-major; op(A) is M x K (ta = 0: A[i*lda +
+ * k]; ta = 1: A[k*lda + i]), op(B) is K x N (tb = 0: B[k*ldb + j]; tb = 1:
+ * B[j*ldb + k]), C is M x N with leading dimension ldc.  Every row of op(A)
+ * and column of op(B) is scaled by a power of two and cut into signed 7-bit
+ * digits held exactly in BF16 (7 digits per operand); the slice
+ * products of each order are summed in FP32 accumulators, exactly for the
+ * four leading orders, in passes of at most 1024 of K, and combined in FP64.
+ * Error per element about 2^-46 K max_k |op(A)_ik| max_k |op(B)_kj|.
+ * Device pointers; ws (device, 256-byte aligned, >= gn_dgemm_tc_workspace_size)
+ * is scratch owned by the caller.  GN_ERR_INVALID_ARG for K < 1 or null
+ * pointers, GN_ERR_SHAPE for leading dimensions shorter than a row,
+ * GN_ERR_ALIGNMENT for an unaligned ws, GN_ERR_WORKSPACE if ws is short.
+ * Asynchronous on the handle's stream. */
+gn_status gn_dgemm_tc_workspace_size(int64_t M, int64_t N, int64_t K, int32_t a_f32, size_t* bytes);
+gn_status gn_dgemm_tc(gn_handle h, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int32_t a_f32,
+                      int64_t lda, int32_t ta, const double* B, int64_t ldb, int32_t tb, double beta, double* C,
+                      int64_t ldc, void* ws, size_t ws_bytes);
+
 const char* gn_status_string(gn_status s);
 
 /* Number of SMs of the handle's device (the persistent grids use it). */

@@ -38,7 +38,7 @@ ABI_SYMBOLS = (
     "gn_sketch", "gn_core", "gn_factors", "gn_approx", "gn_error_fro2", "gn_hmt",
     "gn_kernel_launches", "gn_error_fro2_noalloc", "gn_backward_workspace_size", "gn_backward",
     "gn_forward_dense", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
-    "gn_batched_set_policy", "gn_batched_tune",
+    "gn_batched_set_policy", "gn_batched_tune", "gn_set_fp64_tc", "gn_dgemm_tc_workspace_size", "gn_dgemm_tc",
 )
 
 
@@ -108,6 +108,9 @@ def _load():
         "gn_batched_prepare": ([P, I32, ctypes.POINTER(GnProblem), P, SZ], I32),
         "gn_batched_run": ([P, D, I32, P, SZ], I32),
         "gn_batched_set_policy": ([P, I32], I32),
+        "gn_set_fp64_tc": ([P, I32], I32),
+        "gn_dgemm_tc_workspace_size": ([I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
+        "gn_dgemm_tc": ([P, I64, I64, I64, D, P, I32, I64, I32, P, I64, I32, D, P, I64, P, SZ], I32),
         "gn_batched_tune": ([P, I32, ctypes.POINTER(GnProblem), P, SZ, D, I32, ctypes.POINTER(I32),
                              ctypes.POINTER(D)], I32),
     }
@@ -272,6 +275,35 @@ class Handle:
     def set_fp64_g(self, on: bool):
         """G = Q_1^T (Y^T A) in FP64 (True) or on the tensor cores (False, default) for FP32 Y^T A."""
         _check(lib.gn_set_fp64_g(self._h, 1 if on else 0), "gn_set_fp64_g")
+
+    def set_fp64_tc(self, on: bool):
+        """The factors' large FP64 products (FP32 AX) on the tensor cores by exact
+        digit slicing (True, default) or on the FP64 units (False)."""
+        _check(lib.gn_set_fp64_tc(self._h, 1 if on else 0), "gn_set_fp64_tc")
+
+    def dgemm_tc(self, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor = None, alpha: float = 1.0,
+                 beta: float = 0.0, ta: bool = False, tb: bool = False) -> torch.Tensor:
+        """C = alpha op(A) op(B) + beta C in FP64 on the tensor cores (digit slicing).
+        A: FP64 or FP32, B and C: FP64, all row-major with unit column stride."""
+        if A.dtype not in (torch.float64, torch.float32) or B.dtype != torch.float64:
+            raise TypeError("dgemm_tc: A FP64 or FP32, B FP64")
+        if A.stride(1) != 1 or B.stride(1) != 1:
+            raise ValueError("dgemm_tc: unit column stride required")
+        M, K = (A.shape[1], A.shape[0]) if ta else (A.shape[0], A.shape[1])
+        K2, N = (B.shape[1], B.shape[0]) if tb else (B.shape[0], B.shape[1])
+        if K != K2:
+            raise ValueError("dgemm_tc: inner dimensions differ")
+        if C is None:
+            C = torch.zeros(M, N, dtype=torch.float64, device=A.device)
+        a32 = 1 if A.dtype == torch.float32 else 0
+        b = ctypes.c_size_t()
+        _check(lib.gn_dgemm_tc_workspace_size(M, N, K, a32, ctypes.byref(b)), "gn_dgemm_tc_workspace_size")
+        with torch.cuda.stream(self.stream):   # freed in order with the handle's stream
+            ws = torch.empty(int(b.value), dtype=torch.uint8, device=A.device)
+        _check(lib.gn_dgemm_tc(self._h, M, N, K, float(alpha), A.data_ptr(), a32, A.stride(0), 1 if ta else 0,
+                               B.data_ptr(), B.stride(0), 1 if tb else 0, float(beta), C.data_ptr(), C.stride(0),
+                               ws.data_ptr(), ws.numel()), "gn_dgemm_tc")
+        return C
 
     # ---------------------------------------------------------------- sizing
     @staticmethod

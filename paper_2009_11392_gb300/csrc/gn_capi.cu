@@ -123,13 +123,20 @@ size_t sketch_e4m3_ws(long long m, long long n, long long r, long long l) {
 // e4m3 X in the core product: an exact BF16 copy of X^T (r x n) ahead of the core workspace.
 size_t core_e4m3_ws(long long n, long long r) { return align256(sizeof(__nv_bfloat16) * r * round8(n)) + 256; }
 
+// Digit-sliced tensor-core FP64 products of the factors (FP32 AX): the solve's
+// outer-block updates (N = 128, K < r) and AX Q_2 (FP32 A, N = k <= r, K = r).
+size_t factors_oz_ws(long long m, long long r) {
+    return std::max(oz_ws_bytes(m, 128, r, 0), oz_ws_bytes(m, r, r, 1));
+}
+
 // Factors: the FP64 solves' scratch, plus (FP32 Y^T A) the BF16 slices of Y^T A
 // and Q_1 and the FP32 product G.
 size_t factors_ws(long long m, long long n, long long r, long long l, int mixed, int sms) {
     size_t b = trsm_ws_bytes(m, r, sms) + dgemm_ws_bytes(m, r, r, sms) + 1024;
     if (mixed)
         b += 3 * align256(sizeof(__nv_bfloat16) * (r + l) * round8(n)) +
-             3 * align256(sizeof(__nv_bfloat16) * (r + l) * round8(r)) + align256(sizeof(float) * r * round8(n));
+             3 * align256(sizeof(__nv_bfloat16) * (r + l) * round8(r)) + align256(sizeof(float) * r * round8(n)) +
+             factors_oz_ws(m, r);
     return b;
 }
 
@@ -313,6 +320,7 @@ gn_status gn_create(gn_handle* out, void* stream) {
     h->batched_mt = 1;
     h->batched_policy = 0;
     h->fp64_g = 0;
+    h->fp64_tc = 1;
     if (cudaMalloc(&h->dstatus, 64) != cudaSuccess) {
         delete h;
         return GN_ERR_CUDA;
@@ -371,6 +379,29 @@ gn_status gn_set_fp64_g(gn_handle h, int32_t fp64_g) {
     if (!h || (fp64_g != 0 && fp64_g != 1)) return GN_ERR_INVALID_ARG;
     h->fp64_g = fp64_g;
     return GN_OK;
+}
+
+gn_status gn_set_fp64_tc(gn_handle h, int32_t on) {
+    if (!h || (on != 0 && on != 1)) return GN_ERR_INVALID_ARG;
+    h->fp64_tc = on;
+    return GN_OK;
+}
+
+gn_status gn_dgemm_tc_workspace_size(int64_t M, int64_t N, int64_t K, int32_t a_f32, size_t* bytes) {
+    if (!bytes || M < 0 || N < 0 || K < 1) return GN_ERR_INVALID_ARG;
+    *bytes = oz_ws_bytes(M, N, K, a_f32 ? 1 : 0);
+    return GN_OK;
+}
+
+gn_status gn_dgemm_tc(gn_handle h, int64_t M, int64_t N, int64_t K, double alpha, const void* A, int32_t a_f32,
+                      int64_t lda, int32_t ta, const double* B, int64_t ldb, int32_t tb, double beta, double* C,
+                      int64_t ldc, void* ws, size_t ws_bytes) {
+    if (!h || M < 0 || N < 0 || K < 1 || !A || !B || !C || !ws) return GN_ERR_INVALID_ARG;
+    if (lda < (ta ? M : K) || ldb < (tb ? K : N) || ldc < N) return GN_ERR_SHAPE;
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return GN_ERR_ALIGNMENT;
+    if (ws_bytes < oz_ws_bytes(M, N, K, a_f32 ? 1 : 0)) return GN_ERR_WORKSPACE;
+    return oz_dgemm(h, M, N, K, alpha, A, a_f32 ? 1 : 0, lda, ta ? 1 : 0, B, ldb, tb ? 1 : 0, beta, C, ldc, ws,
+                    ws_bytes);
 }
 
 gn_status gn_set_wait_limit(gn_handle h, uint64_t ns) {
@@ -620,7 +651,8 @@ gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_
     if (AX->dtype != GN_F64 && AX->dtype != GN_F32) return GN_ERR_DTYPE;
     if (YtA->dtype != GN_F64 && YtA->dtype != GN_F32) return GN_ERR_DTYPE;
     const int tc_g = YtA->dtype == GN_F32 && !h->fp64_g;
-    if (ws_bytes < factors_ws(m, n, r, l, tc_g, h->sm_count)) return GN_ERR_WORKSPACE;
+    const int mixed = AX->dtype == GN_F32 || YtA->dtype == GN_F32;
+    if (ws_bytes < factors_ws(m, n, r, l, mixed, h->sm_count)) return GN_ERR_WORKSPACE;
     double* Fd = static_cast<double*>(F->data);
     double* Gd = static_cast<double*>(G->data);
     // FP32 Y^T A: G = Q_1^T (Y^T A) on the tensor cores from three BF16 slices of
@@ -630,10 +662,18 @@ gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_
     const long long rl = r + l, lds = round8(n), ldq = round8(k);
     __nv_bfloat16 *sl[3] = {nullptr, nullptr, nullptr}, *ql[3] = {nullptr, nullptr, nullptr};
     float* g32 = nullptr;
+    // FP32 AX: the solve's large products on the tensor cores (digit slicing)
+    const bool oz_on = AX->dtype == GN_F32 && h->fp64_tc && m >= 1024;
+    void* oz = nullptr;
+    const size_t oz_bytes = oz_on ? factors_oz_ws(m, r) : 0;
     if (tc_g) {
         for (int i = 0; i < 3; ++i) sl[i] = cv.take<__nv_bfloat16>(rl * lds);
         for (int i = 0; i < 3; ++i) ql[i] = cv.take<__nv_bfloat16>(rl * ldq);
         g32 = cv.take<float>(k * lds);
+        if (!cv.ok) return GN_ERR_WORKSPACE;
+    }
+    if (oz_on) {
+        oz = cv.take<char>(oz_bytes);
         if (!cv.ok) return GN_ERR_WORKSPACE;
     }
     size_t gws_bytes = 0;
@@ -648,16 +688,18 @@ gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_
             GN_CUDA_TRY(cudaMemcpy2DAsync(Fd, F->ld * 8, AX->data, AX->ld * 8, r * 8, m, cudaMemcpyDeviceToDevice,
                                           h->stream));
         }
-        GN_TRY(trsm_right_upper(h, Fd, m, r, F->ld, core->R, r, 0, gws, ws_bytes));
+        GN_TRY(trsm_right_upper(h, Fd, m, r, F->ld, core->R, r, 0, gws, ws_bytes, oz, oz_bytes));
     } else {
         // F = (AX Q_2) R_2^{-T}
-        if (AX->dtype == GN_F32)
+        if (oz)
+            GN_TRY(oz_dgemm(h, m, k, r, 1.0, AX->data, 1, AX->ld, 0, core->Q2, r, 0, 0.0, Fd, F->ld, oz, oz_bytes));
+        else if (AX->dtype == GN_F32)
             GN_TRY(dgemm_a32(h, m, k, r, 1.0, static_cast<const float*>(AX->data), AX->ld, 0, core->Q2, r, 0,
                              0.0, Fd, F->ld, gws, ws_bytes));
         else
             GN_TRY(dgemm(h, m, k, r, 1.0, static_cast<const double*>(AX->data), AX->ld, 0, core->Q2, r, 0, 0.0,
                          Fd, F->ld, gws, ws_bytes));
-        GN_TRY(trsm_right_upper(h, Fd, m, k, F->ld, core->R2, r, 1, gws, ws_bytes));
+        GN_TRY(trsm_right_upper(h, Fd, m, k, F->ld, core->R2, r, 1, gws, ws_bytes, oz, oz_bytes));
     }
     // G = Q_1^T (Y^T A)
     if (YtA->dtype == GN_F32 && !tc_g) {

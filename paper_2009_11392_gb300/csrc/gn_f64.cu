@@ -890,10 +890,13 @@ constexpr int TB = 32;
 __global__ void trsm_diag_kernel(double* F, long long m, long long ldf, int j0, int jb,
                                  const double* R, long long ldr, int trans) {
     __shared__ double Rs[TB][TB + 1];
+    __shared__ double rdiag[TB];   // 1 / R_jj: one division per column and block, not per row
     for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
         const int a = e / TB, b = e % TB;
         Rs[a][b] = (a < jb && b < jb) ? R[static_cast<long long>(j0 + a) * ldr + j0 + b] : 0.0;
     }
+    if (threadIdx.x < TB)
+        rdiag[threadIdx.x] = threadIdx.x < jb ? 1.0 / R[static_cast<long long>(j0 + threadIdx.x) * (ldr + 1)] : 0.0;
     __syncthreads();
     const long long row = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (row >= m) return;
@@ -909,7 +912,7 @@ __global__ void trsm_diag_kernel(double* F, long long m, long long ldf, int j0, 
 #pragma unroll
                 for (int i = 0; i < TB; ++i)
                     if (i < j) s = fma(-x[i], Rs[i][j], s);
-                x[j] = s / Rs[j][j];
+                x[j] = s * rdiag[j];
             }
         }
     } else {
@@ -920,7 +923,7 @@ __global__ void trsm_diag_kernel(double* F, long long m, long long ldf, int j0, 
 #pragma unroll
                 for (int i = 0; i < TB; ++i)
                     if (i > j && i < jb) s = fma(-x[i], Rs[j][i], s);
-                x[j] = s / Rs[j][j];
+                x[j] = s * rdiag[j];
             }
         }
     }
@@ -1829,7 +1832,8 @@ size_t trsm_ws_bytes(long long m, long long k, int sm_count) {
 }
 
 gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, long long ldf,
-                           const double* R, long long ldr, int trans, double* ws, size_t ws_bytes) {
+                           const double* R, long long ldr, int trans, double* ws, size_t ws_bytes, void* oz,
+                           size_t oz_bytes) {
     if (m <= 0 || k <= 0) return GN_OK;
     // Two levels of blocking: 128-column outer blocks take the bulk of the
     // update as one wide FP64 GEMM each; inside, 32-column blocks take a narrow
@@ -1840,12 +1844,21 @@ gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, lon
     for (long long obi = 0; obi < nob; ++obi) {
         const long long ob = trans ? nob - 1 - obi : obi;
         const long long J0 = ob * OB, JB = std::min<long long>(OB, k - J0);
-        if (!trans && J0 > 0)   // F[:, J] -= F[:, 0:J0] R[0:J0, J]
-            GN_TRY(dgemm(h, m, JB, J0, -1.0, F, ldf, 0, R + J0, ldr, 0, 1.0, F + J0, ldf, ws, ws_bytes));
+        // (oz: these and the inner updates below on the tensor cores by exact digit slicing)
+        if (!trans && J0 > 0) {   // F[:, J] -= F[:, 0:J0] R[0:J0, J]
+            if (oz)
+                GN_TRY(oz_dgemm(h, m, JB, J0, -1.0, F, 0, ldf, 0, R + J0, ldr, 0, 1.0, F + J0, ldf, oz, oz_bytes));
+            else
+                GN_TRY(dgemm(h, m, JB, J0, -1.0, F, ldf, 0, R + J0, ldr, 0, 1.0, F + J0, ldf, ws, ws_bytes));
+        }
         if (trans && J0 + JB < k) {   // F[:, J] -= F[:, J+] R[J, J+]^T
             const long long kk = k - J0 - JB;
-            GN_TRY(dgemm(h, m, JB, kk, -1.0, F + J0 + JB, ldf, 0, R + J0 * ldr + J0 + JB, ldr, 1, 1.0, F + J0, ldf,
-                         ws, ws_bytes));
+            if (oz)
+                GN_TRY(oz_dgemm(h, m, JB, kk, -1.0, F + J0 + JB, 0, ldf, 0, R + J0 * ldr + J0 + JB, ldr, 1, 1.0,
+                                F + J0, ldf, oz, oz_bytes));
+            else
+                GN_TRY(dgemm(h, m, JB, kk, -1.0, F + J0 + JB, ldf, 0, R + J0 * ldr + J0 + JB, ldr, 1, 1.0, F + J0,
+                             ldf, ws, ws_bytes));
         }
         const long long nb = (JB + TB - 1) / TB;
         for (long long bi = 0; bi < nb; ++bi) {
@@ -1854,14 +1867,22 @@ gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, lon
             const int jb = static_cast<int>(std::min<long long>(TB, J0 + JB - j0));
             if (!trans && j0 > J0) {
                 // F[:, j] -= F[:, J0:j0] R[J0:j0, j]
-                GN_TRY(dgemm(h, m, jb, j0 - J0, -1.0, F + J0, ldf, 0, R + J0 * ldr + j0, ldr, 0, 1.0, F + j0, ldf, ws,
-                             ws_bytes));
+                if (oz)
+                    GN_TRY(oz_dgemm(h, m, jb, j0 - J0, -1.0, F + J0, 0, ldf, 0, R + J0 * ldr + j0, ldr, 0, 1.0,
+                                    F + j0, ldf, oz, oz_bytes));
+                else
+                    GN_TRY(dgemm(h, m, jb, j0 - J0, -1.0, F + J0, ldf, 0, R + J0 * ldr + j0, ldr, 0, 1.0, F + j0, ldf,
+                                 ws, ws_bytes));
             }
             if (trans && j0 + jb < J0 + JB) {
                 // F[:, j] -= F[:, j+ .. J0+JB] R[j, j+ ..]^T
                 const long long kk = J0 + JB - j0 - jb;
-                GN_TRY(dgemm(h, m, jb, kk, -1.0, F + j0 + jb, ldf, 0, R + j0 * ldr + j0 + jb, ldr, 1, 1.0, F + j0, ldf,
-                             ws, ws_bytes));
+                if (oz)
+                    GN_TRY(oz_dgemm(h, m, jb, kk, -1.0, F + j0 + jb, 0, ldf, 0, R + j0 * ldr + j0 + jb, ldr, 1, 1.0,
+                                    F + j0, ldf, oz, oz_bytes));
+                else
+                    GN_TRY(dgemm(h, m, jb, kk, -1.0, F + j0 + jb, ldf, 0, R + j0 * ldr + j0 + jb, ldr, 1, 1.0, F + j0,
+                                 ldf, ws, ws_bytes));
             }
             trsm_diag_kernel<<<blocks, 128, 0, h->stream>>>(F, m, ldf, static_cast<int>(j0), jb, R, ldr, trans); count_launch();
             GN_CUDA_TRY(cudaGetLastError());

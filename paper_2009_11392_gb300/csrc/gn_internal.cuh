@@ -26,6 +26,7 @@ struct gn_handle_s {
     int batched_count, batched_sk_tiles, batched_c_tiles, batched_mt;
     int batched_policy;        // tile policy of the next gn_batched_prepare
     int fp64_g;                // gn_factors: FP64 G even for FP32 Y^T A
+    int fp64_tc;               // gn_factors: digit-sliced tensor-core FP64 products (FP32 AX)
 };
 
 #define GN_CUDA_TRY(expr)                                   \
@@ -49,9 +50,9 @@ namespace gn {
 unsigned long long launch_count();
 void count_launch();
 
-constexpr int TC_MAX_MAPS = 12;
-constexpr int TC_MAX_GEMMS = 4;
-constexpr int TC_MAX_SRC = 6;
+constexpr int TC_MAX_MAPS = 14;
+constexpr int TC_MAX_GEMMS = 7;
+constexpr int TC_MAX_SRC = 7;
 
 struct TcGemm {
     int M, N, K;             // D is M x N, contraction length K
@@ -155,9 +156,19 @@ gn_status qr_form_q(gn_handle h, const double* W, long long M, long long N, long
 // Right triangular solves, FP64, in place on F (m x k):
 //   upper == 1, trans == 0: F <- F R^{-1}   (R upper, k x k)
 //   upper == 1, trans == 1: F <- F R^{-T}
+// oz (optional): workspace of oz_dgemm for the outer-block updates (>= oz_ws_bytes(m,
+// 128, k, 0)); null keeps every update on the FP64 units.
 size_t trsm_ws_bytes(long long m, long long k, int sm_count);
 gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, long long ldf,
-                           const double* R, long long ldr, int trans, double* ws, size_t ws_bytes);
+                           const double* R, long long ldr, int trans, double* ws, size_t ws_bytes,
+                           void* oz = nullptr, size_t oz_bytes = 0);
+
+// FP64 product on the BF16 tensor cores by exact digit slicing (gn_ozaki.cu);
+// same operand conventions as dgemm, A FP64 or (a_f32) FP32.
+size_t oz_ws_bytes(long long M, long long N, long long K, int a_f32);
+gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double alpha, const void* A, int a_f32,
+                   long long lda, int ta, const double* B, long long ldb, int tb, double beta, double* C,
+                   long long ldc, void* ws, size_t ws_bytes);
 
 // Core diagnostics (one CTA): out3[0] = est ||R^{-1}||_2 (if want_estimate),
 // out3[1] = est ||R||_2 (if eps_relative), out3[2] = the absolute threshold

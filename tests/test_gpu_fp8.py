@@ -70,7 +70,7 @@ def e4m3_operands(H, A, X, Y):
             H.quantize_e4m3(Y.cuda(), data=False, transposed=True))
 
 
-@pytest.mark.parametrize("m,n,r,l", [(300, 200, 70, 35), (520, 390, 130, 65), (256, 128, 16, 8)])
+@pytest.mark.parametrize("m,n,r,l", [(300, 200, 70, 35), (520, 390, 130, 65), (256, 128, 16, 8), (1100, 300, 70, 35)])
 def test_e4m3_sketch_exact_on_integer_inputs(gn, H, m, n, r, l):
     A, X, Y = integer_tiled(m, n, 1), integer_tiled(n, r, 2), integer_tiled(m, r + l, 3)
     for t in (A, X, Y):   # the quantization is exact on these inputs
