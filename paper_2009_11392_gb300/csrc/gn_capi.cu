@@ -108,6 +108,7 @@ size_t core_ws(long long n, long long r, long long l, int mixed, int sms) {
     if (mixed) {
         b += 3 * align256(sizeof(__nv_bfloat16) * rl * round8(n));
         b += 3 * align256(sizeof(float) * rl * r);
+        b += align256(qr_oz_ws_bytes(rl, r));          // tensor-core formation of Q
     }
     size_t inner = std::max(qr_ws_bytes(rl, r, sms), dgemm_ws_bytes(rl, r, n, sms));
     return b + inner + 1024;
@@ -552,6 +553,13 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
         c_mid = cv.take<float>(rl * r);
         c_lo = cv.take<float>(rl * r);
     }
+    // FP32 sketches: Q formed with its large products on the tensor cores
+    void* qoz = nullptr;
+    size_t qoz_bytes = 0;
+    if (mixed && h->fp64_tc) {
+        qoz_bytes = qr_oz_ws_bytes(rl, r);
+        qoz = cv.take<char>(qoz_bytes);
+    }
     size_t inner_bytes = 0;
     double* inner = cv.rest(&inner_bytes);
     if (!cv.ok) return GN_ERR_WORKSPACE;
@@ -603,7 +611,7 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     core->rinv_est = 0.0;
     core->c_norm_est = 0.0;
     core->eps_abs = eps;
-    if (mode == GN_MODE_PLAIN) return qr_form_q(h, W, rl, r, r, core->Q, r, inner, inner_bytes);
+    if (mode == GN_MODE_PLAIN) return qr_form_q(h, W, rl, r, r, core->Q, r, inner, inner_bytes, qoz, qoz_bytes);
 
     GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
     GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
@@ -614,7 +622,7 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
                                 sizeof(double) * 2 * std::max<long long>(r, 64)));
     }
     GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
-    GN_TRY(qr_form_q(h, W, rl, r, r, core->Q, r, inner, inner_bytes));
+    GN_TRY(qr_form_q(h, W, rl, r, r, core->Q, r, inner, inner_bytes, qoz, qoz_bytes));
     GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     int k_h = 0;
     double diag_h[3] = {0.0, 0.0, 0.0};

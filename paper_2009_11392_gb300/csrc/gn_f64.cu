@@ -1790,9 +1790,118 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
     return GN_OK;
 }
 
+namespace {
+
+// X <- S^{-1} X for S = striu(G) + diag(1 / tau) (n x n upper triangular, n <=
+// QR_SB): the UT transform of a block of reflectors, T = S^{-1}, so that
+// H_0 ... H_{n-1} = I - V T V^T with G = V^T V (Puglisi 1992; Joffrain et al.
+// 2006).  Back substitution x_i = tau_i (x_i - sum_{k>i} G_ik x_k); a dropped
+// reflector (tau_i = 0) gets x_i = 0.  One warp per column of X.
+constexpr int QR_SB = 256;   // reflectors per block of the tensor-core Q formation
+
+__global__ void ut_solve_kernel(const double* __restrict__ G, long long ldg, const double* __restrict__ tau, int n,
+                                double* __restrict__ X, long long ldx, int cols) {
+    const long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= cols) return;   // warp-uniform
+    constexpr int NT = QR_SB / 32;
+    double x[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int k = lane + 32 * t;
+        x[t] = k < n ? X[k * ldx + w] : 0.0;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        const double* gi = G + static_cast<long long>(i) * ldg;
+        double acc = 0.0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int k = lane + 32 * t;
+            if (32 * t + 31 > i && k > i && k < n) acc = fma(gi[k], x[t], acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const int ti = i >> 5;
+        if (lane == (i & 31)) {
+            const double ta = tau[i];
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+                if (t == ti) x[t] = ta * (x[t] - acc);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int k = lane + 32 * t;
+        if (k < n) X[k * ldx + w] = x[t];
+    }
+}
+
+// Zero V above the diagonal inside each block of QR_SB reflectors: a panel
+// writes its reflectors from its own first row down, so rows of the block's
+// earlier panels are left unwritten in its columns.
+__global__ void v_zero_upper_kernel(double* V, long long ldv, int N) {
+    const long long total = static_cast<long long>(N) * QR_SB;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int c = static_cast<int>(e / QR_SB), i = (c / QR_SB) * QR_SB + static_cast<int>(e % QR_SB);
+        if (i < c) V[static_cast<long long>(i) * ldv + c] = 0.0;
+    }
+}
+
+}  // namespace
+
+size_t qr_oz_ws_bytes(long long M, long long N) {
+    return oz_ws_bytes(std::max<long long>(M, QR_SB), N, M, 0) + sizeof(double) * (QR_SB * QR_SB + QR_SB * N) +
+           1024;
+}
+
+namespace {
+
+// Q = H_0 ... H_{N-1} [I; 0] in blocks of QR_SB reflectors from the last block:
+// Q_s <- Q_s - V_b T_b (V_b^T Q_s), with G_b = V_b^T V_b, V_b^T Q_s and the update
+// on the tensor cores (oz_dgemm, FP64 accuracy) and T_b applied by ut_solve.
+gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double* Q, long long ldq, void* oz,
+                    size_t oz_bytes) {
+    char* base = static_cast<char*>(oz);
+    double* G = reinterpret_cast<double*>(base);
+    const size_t g_bytes = (sizeof(double) * QR_SB * QR_SB + 255) & ~static_cast<size_t>(255);
+    double* Wb = reinterpret_cast<double*>(base + g_bytes);
+    const size_t w_bytes = (sizeof(double) * QR_SB * N + 255) & ~static_cast<size_t>(255);
+    if (g_bytes + w_bytes >= oz_bytes) return GN_ERR_WORKSPACE;
+    void* ozw = base + g_bytes + w_bytes;
+    const size_t ozw_bytes = oz_bytes - g_bytes - w_bytes;
+    v_zero_upper_kernel<<<ew_blocks(h, N * QR_SB), 256, 0, h->stream>>>(q.V, N, static_cast<int>(N)); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    for (long long j0 = ((N - 1) / QR_SB) * QR_SB; j0 >= 0; j0 -= QR_SB) {
+        const long long nbb = std::min<long long>(QR_SB, N - j0), Mp = M - j0, Nq = N - j0;
+        const double* Vb = q.V + j0 * N + j0;   // Mp x nbb, ld N (explicit unit diagonal, zeros above)
+        double* Qs = Q + j0 * ldq + j0;
+        GN_TRY(oz_dgemm(h, nbb, nbb, Mp, 1.0, Vb, 0, N, 1, Vb, N, 0, 0.0, G, QR_SB, ozw, ozw_bytes));
+        GN_TRY(oz_dgemm(h, nbb, Nq, Mp, 1.0, Vb, 0, N, 1, Qs, ldq, 0, 0.0, Wb, Nq, ozw, ozw_bytes));
+        const long long threads = Nq * 32;
+        ut_solve_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, h->stream>>>(
+            G, QR_SB, q.tau + j0, static_cast<int>(nbb), Wb, Nq, static_cast<int>(Nq)); count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        GN_TRY(oz_dgemm(h, Mp, Nq, nbb, -1.0, Vb, 0, N, 0, Wb, Nq, 0, 1.0, Qs, ldq, ozw, ozw_bytes));
+    }
+    return GN_OK;
+}
+
+}  // namespace
+
 gn_status qr_form_q(gn_handle h, const double* W, long long M, long long N, long long ld, double* Q,
-                    long long ldq, double* ws, size_t ws_bytes) {
+                    long long ldq, double* ws, size_t ws_bytes, void* oz, size_t oz_bytes) {
     QrWs q = qr_carve(M, N, ws, ws_bytes);
+    if (oz) {
+        qr_init_q_kernel<<<ew_blocks(h, M * N), 256, 0, h->stream>>>(Q, ldq, static_cast<int>(M),
+                                                                      static_cast<int>(N)); count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        GN_TRY(form_q_tc(h, q, M, N, Q, ldq, oz, oz_bytes));
+        qr_flip_q_kernel<<<ew_blocks(h, M * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(M),
+                                                                      static_cast<int>(N), Q, ldq); count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        return GN_OK;
+    }
     const int nb = panel_cfg(h, M).nb;   // the factorization's panel width
     // Q = H_0 ... H_{N-1} [I; 0], applied block by block from the last panel.
     qr_init_q_kernel<<<ew_blocks(h, M * N), 256, 0, h->stream>>>(Q, ldq, static_cast<int>(M),

@@ -150,8 +150,11 @@ gn_status householder_qr(gn_handle h, double* W, long long M, long long N, long 
 // kept in ws) and the formation of the thin Q from them (same W and ws).
 gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R,
                     long long ldr, double* ws, size_t ws_bytes);
+// oz (optional, >= qr_oz_ws_bytes(M, N)): form Q in blocks of 256 reflectors with
+// the large products on the tensor cores (oz_dgemm); null: FP64 units only.
 gn_status qr_form_q(gn_handle h, const double* W, long long M, long long N, long long ld, double* Q,
-                    long long ldq, double* ws, size_t ws_bytes);
+                    long long ldq, double* ws, size_t ws_bytes, void* oz = nullptr, size_t oz_bytes = 0);
+size_t qr_oz_ws_bytes(long long M, long long N);
 
 // Right triangular solves, FP64, in place on F (m x k):
 //   upper == 1, trans == 0: F <- F R^{-1}   (R upper, k x k)

@@ -135,3 +135,30 @@ def test_factors_tensor_core_truncated_branch(gn, H):
     F0, c0 = _mixed_factors(gn, H, A, X, Y, eps, mode, False)
     assert c1.sgn == c0.sgn == 1 and c1.k == c0.k == 200
     assert np.linalg.norm(F1 - F0) <= 1e-11 * np.linalg.norm(F0)
+
+
+@pytest.mark.parametrize("n,r,l", [(2048, 600, 300), (700, 96, 48)])
+def test_core_q_tensor_core_vs_fp64_units(gn, H, n, r, l):
+    """The thin Q of the core's Householder QR formed in 256-reflector blocks with
+    the products on the tensor cores: equal to the FP64-unit formation to
+    1e-11 (each digit-sliced product errs by ~1e-13 of |A||B| per element,
+    three blocks deep) and orthonormal to 1e-12 r; R untouched (the same
+    factorization)."""
+    g = torch.Generator(device="cuda").manual_seed(n + r)
+    YtA = torch.randn(r + l, n, generator=g, device="cuda", dtype=torch.float32)
+    X = H.quantize(torch.randn(n, r, generator=g, device="cuda", dtype=torch.float64))
+    ws = H.workspace(4096, n, r, l, gn.BF16)
+    out = []
+    for tc in (True, False):
+        core = gn.Core.empty(r, l, "cuda")
+        H.set_fp64_tc(tc)
+        try:
+            H.core(YtA, X, 0.0, gn.PLAIN, core, ws)
+            assert H.sync_status() == 0
+        finally:
+            H.set_fp64_tc(True)
+        out.append((npy(core.Q), npy(core.R)))
+    (Q1, R1), (Q0, R0) = out
+    assert np.array_equal(R1, R0)
+    assert np.linalg.norm(Q1 - Q0) <= 1e-11 * np.linalg.norm(Q0)
+    assert np.linalg.norm(Q1.T @ Q1 - np.eye(r)) <= 1e-12 * r
