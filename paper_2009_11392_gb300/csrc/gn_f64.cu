@@ -1792,42 +1792,62 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
 
 namespace {
 
-// X <- S^{-1} X for S = striu(G) + diag(1 / tau) (n x n upper triangular, n <=
-// QR_SB): the UT transform of a block of reflectors, T = S^{-1}, so that
-// H_0 ... H_{n-1} = I - V T V^T with G = V^T V (Puglisi 1992; Joffrain et al.
-// 2006).  Back substitution x_i = tau_i (x_i - sum_{k>i} G_ik x_k); a dropped
-// reflector (tau_i = 0) gets x_i = 0.  One warp per column of X.
+// T = S^{-1} for S = striu(G) + diag(1 / tau) (n x n upper triangular, n <=
+// QR_SB): the UT transform of a block of reflectors, H_0 ... H_{n-1} = I - V T V^T
+// with G = V^T V (Puglisi 1992; Joffrain et al. 2006).  Column w of T solves
+// S x = e_w by back substitution x_i = tau_i (x_i - sum_{k>i} G_ik x_k), from
+// i = w up (x_i = 0 below w); a dropped reflector (tau_i = 0) gets x_i = 0.
+// One warp per column.
 constexpr int QR_SB = 256;   // reflectors per block of the tensor-core Q formation
 
-__global__ void ut_solve_kernel(const double* __restrict__ G, long long ldg, const double* __restrict__ tau, int n,
-                                double* __restrict__ X, long long ldx, int cols) {
+__global__ void ut_inverse_kernel(const double* __restrict__ G, long long ldg, const double* __restrict__ tau, int n,
+                                  double* __restrict__ X, long long ldx) {
     const long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (w >= cols) return;   // warp-uniform
+    if (w >= n) return;   // warp-uniform
     constexpr int NT = QR_SB / 32;
+    // Right-looking form: once x_i is final, x_k -= G_ki x_i for every k < i,
+    // reading row i of the symmetric G (coalesced); rows arrive through a ring
+    // of four prefetched rows.
     double x[NT];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        const int k = lane + 32 * t;
-        x[t] = k < n ? X[k * ldx + w] : 0.0;
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        const double* gi = G + static_cast<long long>(i) * ldg;
-        double acc = 0.0;
+    for (int t = 0; t < NT; ++t) x[t] = (lane + 32 * t == w) ? 1.0 : 0.0;
+    double g0[NT], g1[NT], g2[NT], g3[NT];
+    double ta0, ta1, ta2, ta3;   // tau of the ring's rows
+    auto load_row = [&](int i, double* dst, double& ta) {
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const int k = lane + 32 * t;
-            if (32 * t + 31 > i && k > i && k < n) acc = fma(gi[k], x[t], acc);
+            dst[t] = (i > 0 && k < i) ? G[static_cast<long long>(i) * ldg + k] : 0.0;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        ta = i >= 0 ? tau[i] : 0.0;
+    };
+    auto step = [&](int i, double* gr, double& ta) {
+        if (i < 0) return;
         const int ti = i >> 5;
-        if (lane == (i & 31)) {
-            const double ta = tau[i];
+        double xs = x[0];
 #pragma unroll
-            for (int t = 0; t < NT; ++t)
-                if (t == ti) x[t] = ta * (x[t] - acc);
+        for (int t = 1; t < NT; ++t)
+            if (t == ti) xs = x[t];   // a move; the owner lane's value is the one broadcast
+        const double xi = __shfl_sync(0xffffffffu, xs * ta, i & 31);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            if (32 * t > i) continue;   // warp-uniform: rows k >= i take no update
+            const bool own = (t == ti) && lane == (i & 31);
+            x[t] = own ? xi : fma(-gr[t], xi, x[t]);   // gr[t] = 0 for k >= i
         }
+        load_row(i - 4, gr, ta);                        // the row four steps on
+    };
+    const int wi = static_cast<int>(w);
+    load_row(wi, g0, ta0);
+    load_row(wi - 1, g1, ta1);
+    load_row(wi - 2, g2, ta2);
+    load_row(wi - 3, g3, ta3);
+    for (int i = wi; i >= 0; i -= 4) {
+        step(i, g0, ta0);
+        step(i - 1, g1, ta1);
+        step(i - 2, g2, ta2);
+        step(i - 3, g3, ta3);
     }
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
@@ -1851,25 +1871,28 @@ __global__ void v_zero_upper_kernel(double* V, long long ldv, int N) {
 }  // namespace
 
 size_t qr_oz_ws_bytes(long long M, long long N) {
-    return oz_ws_bytes(std::max<long long>(M, QR_SB), N, M, 0) + sizeof(double) * (QR_SB * QR_SB + QR_SB * N) +
-           1024;
+    return oz_ws_bytes(std::max<long long>(M, QR_SB), std::max<long long>(N, QR_SB), M, 0) +
+           sizeof(double) * (2 * QR_SB * QR_SB + 2 * QR_SB * N) + 2048;
 }
 
 namespace {
 
 // Q = H_0 ... H_{N-1} [I; 0] in blocks of QR_SB reflectors from the last block:
-// Q_s <- Q_s - V_b T_b (V_b^T Q_s), with G_b = V_b^T V_b, V_b^T Q_s and the update
-// on the tensor cores (oz_dgemm, FP64 accuracy) and T_b applied by ut_solve.
+// Q_s <- Q_s - V_b T_b (V_b^T Q_s), with G_b = V_b^T V_b, V_b^T Q_s, T_b (.) and the
+// update on the tensor cores (oz_dgemm, FP64 accuracy); T_b from G_b by
+// ut_inverse.
 gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double* Q, long long ldq, void* oz,
                     size_t oz_bytes) {
     char* base = static_cast<char*>(oz);
-    double* G = reinterpret_cast<double*>(base);
     const size_t g_bytes = (sizeof(double) * QR_SB * QR_SB + 255) & ~static_cast<size_t>(255);
-    double* Wb = reinterpret_cast<double*>(base + g_bytes);
     const size_t w_bytes = (sizeof(double) * QR_SB * N + 255) & ~static_cast<size_t>(255);
-    if (g_bytes + w_bytes >= oz_bytes) return GN_ERR_WORKSPACE;
-    void* ozw = base + g_bytes + w_bytes;
-    const size_t ozw_bytes = oz_bytes - g_bytes - w_bytes;
+    double* G = reinterpret_cast<double*>(base);
+    double* Tb = reinterpret_cast<double*>(base + g_bytes);
+    double* Wb = reinterpret_cast<double*>(base + 2 * g_bytes);
+    double* Wb2 = reinterpret_cast<double*>(base + 2 * g_bytes + w_bytes);
+    if (2 * (g_bytes + w_bytes) >= oz_bytes) return GN_ERR_WORKSPACE;
+    void* ozw = base + 2 * (g_bytes + w_bytes);
+    const size_t ozw_bytes = oz_bytes - 2 * (g_bytes + w_bytes);
     v_zero_upper_kernel<<<ew_blocks(h, N * QR_SB), 256, 0, h->stream>>>(q.V, N, static_cast<int>(N)); count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     for (long long j0 = ((N - 1) / QR_SB) * QR_SB; j0 >= 0; j0 -= QR_SB) {
@@ -1877,12 +1900,12 @@ gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double
         const double* Vb = q.V + j0 * N + j0;   // Mp x nbb, ld N (explicit unit diagonal, zeros above)
         double* Qs = Q + j0 * ldq + j0;
         GN_TRY(oz_dgemm(h, nbb, nbb, Mp, 1.0, Vb, 0, N, 1, Vb, N, 0, 0.0, G, QR_SB, ozw, ozw_bytes));
-        GN_TRY(oz_dgemm(h, nbb, Nq, Mp, 1.0, Vb, 0, N, 1, Qs, ldq, 0, 0.0, Wb, Nq, ozw, ozw_bytes));
-        const long long threads = Nq * 32;
-        ut_solve_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, h->stream>>>(
-            G, QR_SB, q.tau + j0, static_cast<int>(nbb), Wb, Nq, static_cast<int>(Nq)); count_launch();
+        ut_inverse_kernel<<<static_cast<unsigned>(nbb), 32, 0, h->stream>>>(   // a warp per block: all SMs
+            G, QR_SB, q.tau + j0, static_cast<int>(nbb), Tb, QR_SB); count_launch();
         GN_CUDA_TRY(cudaGetLastError());
-        GN_TRY(oz_dgemm(h, Mp, Nq, nbb, -1.0, Vb, 0, N, 0, Wb, Nq, 0, 1.0, Qs, ldq, ozw, ozw_bytes));
+        GN_TRY(oz_dgemm(h, nbb, Nq, Mp, 1.0, Vb, 0, N, 1, Qs, ldq, 0, 0.0, Wb, Nq, ozw, ozw_bytes));
+        GN_TRY(oz_dgemm(h, nbb, Nq, nbb, 1.0, Tb, 0, QR_SB, 0, Wb, Nq, 0, 0.0, Wb2, Nq, ozw, ozw_bytes));
+        GN_TRY(oz_dgemm(h, Mp, Nq, nbb, -1.0, Vb, 0, N, 0, Wb2, Nq, 0, 1.0, Qs, ldq, ozw, ozw_bytes));
     }
     return GN_OK;
 }

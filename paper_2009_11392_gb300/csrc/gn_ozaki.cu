@@ -27,10 +27,18 @@ namespace gn {
 namespace {
 
 constexpr int OZ_KPASS = 1024;   // K per pass (exactness of the orders <= 3)
-constexpr int OZ_NPANEL = 256;   // N per GEMM launch (bounds the FP32 outputs)
+constexpr int OZ_NPANEL = 256;   // least N per GEMM launch (oz_npanel bounds the FP32 outputs)
 constexpr int OZ_MAX_DIGITS = 7;
 
 size_t al256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+
+// Columns of C per GEMM launch: at least 256, more while the FP32 outputs of all
+// orders stay within 64 MB (short, wide products in one launch).
+long long oz_npanel(long long M, long long N) {
+    long long np = (64LL << 20) / (4LL * OZ_MAX_DIGITS * std::max<long long>(M, 1));
+    np = std::max<long long>(np, OZ_NPANEL) / 16 * 16;
+    return std::min<long long>(N, np);
+}
 long long r8(long long x) { return (x + 7) / 8 * 8; }
 long long r4(long long x) { return (x + 3) / 4 * 4; }
 
@@ -96,57 +104,77 @@ __device__ __forceinline__ void write_digits(long long Y, int S, __nv_bfloat16* 
     }
 }
 
-// Largest |entry| of every operand row: a warp per row when the row is
-// contiguous (s_k == 1), else 32 rows per block with K split over its warps
-// (rows contiguous, s_row == 1).
+// Largest |entry| of every operand row, as the bits of |x|.  Rows contiguous
+// along K (s_k == 1): a warp per row.
 template <typename T>
-__global__ void oz_rowmax_kernel(const T* __restrict__ src, long long s_row, long long s_k, int rows, int K,
-                                 int* __restrict__ ex) {
-    if (s_k == 1) {
-        const long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-        const int lane = threadIdx.x & 31;
-        if (w >= rows) return;   // warp-uniform
-        const T* row = src + w * s_row;
-        unsigned long long mx = 0;
-        for (int k = lane; k < K; k += 32) mx = max(mx, abs_bits(row[k]));
+__global__ void oz_rowmax_rows_kernel(const T* __restrict__ src, long long s_row, int rows, int K,
+                                      unsigned long long* __restrict__ mx) {
+    const long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= rows) return;   // warp-uniform
+    const T* row = src + w * s_row;
+    unsigned long long m = 0;
+    for (int k = lane; k < K; k += 32) m = max(m, abs_bits(row[k]));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) ex[w] = row_exponent<T>(mx);
-    } else {   // 32 rows per block, the 8 warps split K
-        __shared__ unsigned long long part[8][32];
-        const int lane = threadIdx.x & 31, kg = threadIdx.x >> 5;
-        const long long i = static_cast<long long>(blockIdx.x) * 32 + lane;
-        unsigned long long mx = 0;
-        if (i < rows)
-            for (int k = kg; k < K; k += 8) mx = max(mx, abs_bits(src[i + k * s_k]));
-        part[kg][lane] = mx;
-        __syncthreads();
-        if (kg == 0 && i < rows) {
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) mx[w] = m;
+}
+
+// Rows contiguous across rows (s_row == 1): blocks of 32 rows x one chunk of K,
+// the 8 warps striding the chunk; atomicMax into mx (zeroed before).
+template <typename T>
+__global__ void oz_rowmax_cols_kernel(const T* __restrict__ src, long long s_k, int rows, int K, int kchunk,
+                                      unsigned long long* __restrict__ mx) {
+    __shared__ unsigned long long part[8][32];
+    const int lane = threadIdx.x & 31, kg = threadIdx.x >> 5;
+    const long long i = static_cast<long long>(blockIdx.x) * 32 + lane;
+    const int k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
+    unsigned long long m = 0;
+    if (i < rows)
+        for (int k = k0 + kg; k < k1; k += 8) m = max(m, abs_bits(src[i + k * s_k]));
+    part[kg][lane] = m;
+    __syncthreads();
+    if (kg == 0 && i < rows) {
 #pragma unroll
-            for (int g = 1; g < 8; ++g) mx = max(mx, part[g][lane]);
-            ex[i] = row_exponent<T>(mx);
-        }
+        for (int g = 1; g < 8; ++g) m = max(m, part[g][lane]);
+        if (m) atomicMax(mx + i, m);
     }
 }
 
-// One thread per entry: k fastest when rows are contiguous along K, else the
-// row index fastest (coalesced reads of the source either way).
+// Digits, rows contiguous along K: one thread per entry, k fastest.
 template <typename T>
-__global__ void oz_digits_kernel(const T* __restrict__ src, long long s_row, long long s_k, int rows, int K, int S,
-                                 const int* __restrict__ ex, __nv_bfloat16* __restrict__ out, long long ldk,
-                                 long long slice_stride) {
+__global__ void oz_digits_rows_kernel(const T* __restrict__ src, long long s_row, int rows, int K, int S,
+                                      const unsigned long long* __restrict__ mx, __nv_bfloat16* __restrict__ out,
+                                      long long ldk, long long slice_stride) {
     const long long total = static_cast<long long>(rows) * K;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        long long i, k;
-        if (s_k == 1) {
-            i = e / K;
-            k = e % K;
-        } else {
-            k = e / rows;
-            i = e % rows;
-        }
-        write_digits(fixed49(src[i * s_row + k * s_k], ex[i]), S, out + i * ldk + k, slice_stride);
+        const long long i = e / K, k = e - i * K;
+        write_digits(fixed49(src[i * s_row + k], row_exponent<T>(mx[i])), S, out + i * ldk + k, slice_stride);
+    }
+}
+
+// Digits, rows contiguous across rows: 32 x 32 tiles through shared memory,
+// read along the rows, written along K.
+template <typename T>
+__global__ void oz_digits_cols_kernel(const T* __restrict__ src, long long s_k, int rows, int K, int S,
+                                      const unsigned long long* __restrict__ mx, __nv_bfloat16* __restrict__ out,
+                                      long long ldk, long long slice_stride) {
+    __shared__ long long ys[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads
+    const long long i0 = static_cast<long long>(blockIdx.x) * 32, k0 = static_cast<long long>(blockIdx.y) * 32;
+    const long long i = i0 + tx;
+    const int e = i < rows ? row_exponent<T>(mx[i]) : 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long k = k0 + ty + 8 * q;
+        ys[ty + 8 * q][tx] = (i < rows && k < K) ? fixed49(src[i + k * s_k], e) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long ii = i0 + ty + 8 * q, kk = k0 + tx;
+        if (ii < rows && kk < K) write_digits(ys[tx][ty + 8 * q], S, out + ii * ldk + kk, slice_stride);
     }
 }
 
@@ -154,12 +182,13 @@ __global__ void oz_digits_kernel(const T* __restrict__ src, long long s_row, lon
 // orders 0..3 are summed as integers in units of 2^-35 (one rounding), the
 // rounded orders 4.. in FP32 below them.
 __global__ void oz_combine_kernel(const float* __restrict__ D, long long d_stride, long long ldd, int norders,
-                                  int M, int N, const int* __restrict__ ea, const int* __restrict__ eb, double alpha,
-                                  double beta, double* __restrict__ C, long long ldc) {
+                                  int M, int N, const unsigned long long* __restrict__ mxa, int a_f32,
+                                  const unsigned long long* __restrict__ mxb, double alpha, double beta,
+                                  double* __restrict__ C, long long ldc) {
     const long long total = static_cast<long long>(M) * N;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long i = e / N, j = e % N;
+        const long long i = e / N, j = e - i * N;
         const float* d = D + i * ldd + j;
         long long acc = 0;
         const int nexact = norders < 4 ? norders : 4;
@@ -168,7 +197,8 @@ __global__ void oz_combine_kernel(const float* __restrict__ D, long long d_strid
         float low = 0.0f;
         for (int o = norders - 1; o >= 4; --o) low += d[o * d_stride];
         // times 2^(ea + eb - 35): a power of two built from its bits when normal
-        const int p = ea[i] + eb[j] - 35;
+        const int ea = a_f32 ? row_exponent<float>(mxa[i]) : row_exponent<double>(mxa[i]);
+        const int p = ea + row_exponent<double>(mxb[j]) - 35;
         const double x = fma(static_cast<double>(low), 34359738368.0, static_cast<double>(acc));
         const double v = (p >= -1022 && p <= 1023)
                              ? x * (alpha * __longlong_as_double(static_cast<long long>(p + 1023) << 52))
@@ -180,17 +210,30 @@ __global__ void oz_combine_kernel(const float* __restrict__ D, long long d_strid
 
 template <typename T>
 gn_status slice(gn_handle h, const T* src, long long s_row, long long s_k, long long rows, long long K, int S,
-                __nv_bfloat16* out, long long ldk, long long slice_stride, int* ex) {
-    if (s_k != 1 && s_row != 1) return GN_ERR_INVALID_ARG;
-    const long long blocks_r = s_k == 1 ? (rows * 32 + 255) / 256 : (rows + 31) / 32;
-    oz_rowmax_kernel<T><<<static_cast<unsigned>(blocks_r), 256, 0, h->stream>>>(
-        src, s_row, s_k, static_cast<int>(rows), static_cast<int>(K), ex);
-    count_launch();
-    GN_CUDA_TRY(cudaGetLastError());
-    const long long total = rows * K;
-    const long long blocks = std::min<long long>((total + 255) / 256, static_cast<long long>(h->sm_count) * 16);
-    oz_digits_kernel<T><<<static_cast<unsigned>(blocks), 256, 0, h->stream>>>(
-        src, s_row, s_k, static_cast<int>(rows), static_cast<int>(K), S, ex, out, ldk, slice_stride);
+                __nv_bfloat16* out, long long ldk, long long slice_stride, unsigned long long* mx) {
+    if (s_k == 1) {
+        oz_rowmax_rows_kernel<T><<<static_cast<unsigned>((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
+            src, s_row, static_cast<int>(rows), static_cast<int>(K), mx);
+        count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        const long long total = rows * K;
+        const long long blocks = std::min<long long>((total + 255) / 256, static_cast<long long>(h->sm_count) * 16);
+        oz_digits_rows_kernel<T><<<static_cast<unsigned>(blocks), 256, 0, h->stream>>>(
+            src, s_row, static_cast<int>(rows), static_cast<int>(K), S, mx, out, ldk, slice_stride);
+    } else if (s_row == 1) {
+        constexpr int KCHUNK = 64;
+        GN_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * rows, h->stream));
+        const dim3 g1(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((K + KCHUNK - 1) / KCHUNK));
+        oz_rowmax_cols_kernel<T><<<g1, 256, 0, h->stream>>>(src, s_k, static_cast<int>(rows), static_cast<int>(K),
+                                                            KCHUNK, mx);
+        count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        const dim3 g2(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((K + 31) / 32));
+        oz_digits_cols_kernel<T><<<g2, 256, 0, h->stream>>>(src, s_k, static_cast<int>(rows), static_cast<int>(K), S,
+                                                            mx, out, ldk, slice_stride);
+    } else {
+        return GN_ERR_INVALID_ARG;
+    }
     count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     return GN_OK;
@@ -199,12 +242,12 @@ gn_status slice(gn_handle h, const T* src, long long s_row, long long s_k, long 
 struct OzWs {
     __nv_bfloat16 *as, *bs;
     float* d;
-    int *ea, *eb;
+    unsigned long long *mxa, *mxb;
     long long ldk, ldd;
 };
 
 bool oz_carve(long long M, long long N, long long K, int sa, int sb, void* ws, size_t ws_bytes, OzWs* o) {
-    const long long kp = std::min<long long>(K, OZ_KPASS), np = std::min<long long>(N, OZ_NPANEL);
+    const long long kp = std::min<long long>(K, OZ_KPASS), np = oz_npanel(M, N);
     o->ldk = r8(kp);
     o->ldd = r4(np);
     char* p = static_cast<char*>(ws);
@@ -217,8 +260,8 @@ bool oz_carve(long long M, long long N, long long K, int sa, int sb, void* ws, s
     o->as = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * sa * M * o->ldk));
     o->bs = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * sb * N * o->ldk));
     o->d = reinterpret_cast<float*>(take(sizeof(float) * OZ_MAX_DIGITS * M * o->ldd));
-    o->ea = reinterpret_cast<int*>(take(sizeof(int) * M));
-    o->eb = reinterpret_cast<int*>(take(sizeof(int) * N));
+    o->mxa = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * M));
+    o->mxb = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * N));
     return off <= ws_bytes;
 }
 
@@ -228,10 +271,9 @@ size_t oz_ws_bytes(long long M, long long N, long long K, int a_f32) {
     (void)a_f32;
     const int sa = OZ_MAX_DIGITS, sb = OZ_MAX_DIGITS;
     const long long kp = std::min<long long>(std::max<long long>(K, 1), OZ_KPASS);
-    const long long np = std::min<long long>(std::max<long long>(N, 1), OZ_NPANEL);
+    const long long np = oz_npanel(M, std::max<long long>(N, 1));
     return al256(sizeof(__nv_bfloat16) * sa * M * r8(kp)) + al256(sizeof(__nv_bfloat16) * sb * N * r8(kp)) +
-           al256(sizeof(float) * OZ_MAX_DIGITS * M * r4(np)) + al256(sizeof(int) * M) + al256(sizeof(int) * N) +
-           256;
+           al256(sizeof(float) * OZ_MAX_DIGITS * M * r4(np)) + al256(8 * M) + al256(8 * N) + 256;
 }
 
 gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double alpha, const void* A, int a_f32,
@@ -265,17 +307,22 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
         const long long a_row = ta ? 1 : lda, a_k = ta ? lda : 1;
         const long long a_off = ta ? k0 * lda : k0;
         if (a_f32)
-            GN_TRY(slice(h, static_cast<const float*>(A) + a_off, a_row, a_k, M, kc, sa, o.as, o.ldk, as_stride, o.ea));
+            GN_TRY(slice(h, static_cast<const float*>(A) + a_off, a_row, a_k, M, kc, sa, o.as, o.ldk, as_stride, o.mxa));
         else
             GN_TRY(slice(h, static_cast<const double*>(A) + a_off, a_row, a_k, M, kc, sa, o.as, o.ldk, as_stride,
-                         o.ea));
+                         o.mxa));
         const long long b_row = tb ? ldb : 1, b_k = tb ? 1 : ldb;
         const long long b_off = tb ? k0 : k0 * ldb;
-        GN_TRY(slice(h, B + b_off, b_row, b_k, N, kc, sb, o.bs, o.ldk, bs_stride, o.eb));
+        GN_TRY(slice(h, B + b_off, b_row, b_k, N, kc, sb, o.bs, o.ldk, bs_stride, o.mxb));
         const double beta_pass = k0 == 0 ? beta : 1.0;
-        for (long long j0 = 0; j0 < N; j0 += OZ_NPANEL) {
-            const long long nb = std::min<long long>(OZ_NPANEL, N - j0);
-            const int bn = static_cast<int>(std::min<long long>(256, (nb + 15) / 16 * 16));
+        const long long npanel = oz_npanel(M, N);
+        for (long long j0 = 0; j0 < N; j0 += npanel) {
+            const long long nb = std::min<long long>(npanel, N - j0);
+            // N tile: the widest of 256 / 128 / 64 that still gives the GPU about
+            // two tiles per SM over the orders (small products are latency-bound)
+            int bn = static_cast<int>(std::min<long long>(256, (nb + 31) / 32 * 32));
+            while (bn > 64 && ((M + 127) / 128) * ((nb + bn - 1) / bn) * norders < 2LL * h->sm_count)
+                bn = (bn / 2 + 31) / 32 * 32;
             TcParams p;
             memset(&p, 0, sizeof(p));
             for (int s = 0; s < sa; ++s)
@@ -308,8 +355,8 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
             const long long total = M * nb;
             const long long blocks = std::min<long long>((total + 255) / 256, static_cast<long long>(h->sm_count) * 16);
             oz_combine_kernel<<<static_cast<unsigned>(blocks), 256, 0, h->stream>>>(
-                o.d, d_stride, o.ldd, norders, static_cast<int>(M), static_cast<int>(nb), o.ea, o.eb + j0, alpha,
-                beta_pass, C + j0, ldc);
+                o.d, d_stride, o.ldd, norders, static_cast<int>(M), static_cast<int>(nb), o.mxa, a_f32, o.mxb + j0,
+                alpha, beta_pass, C + j0, ldc);
             count_launch();
             GN_CUDA_TRY(cudaGetLastError());
         }

@@ -586,8 +586,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + (acc * MT + hh) * 256 + c0, v);
                     const int col0 = c.tn * G.bn + c0;
                     if (!row_ok || col0 >= G.N) continue;
+                    // columns of this chunk inside both the tile and D
+                    const int ncol = min(min(32, G.bn - c0), G.N - col0);
                     if (c.half) {   // half of the K range: add into the pre-zeroed D
-                        if (G.vec4 && col0 + 32 <= G.N) {
+                        if (G.vec4 && ncol == 32) {
                             float4* dst = reinterpret_cast<float4*>(drow + col0);
 #pragma unroll
                             for (int j = 0; j < 8; ++j)
@@ -597,9 +599,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                         } else {
 #pragma unroll
                             for (int j = 0; j < 32; ++j)
-                                if (col0 + j < G.N) atomicAdd(drow + col0 + j, __uint_as_float(v[j]));
+                                if (j < ncol) atomicAdd(drow + col0 + j, __uint_as_float(v[j]));
                         }
-                    } else if (G.vec4 && col0 + 32 <= G.N) {
+                    } else if (G.vec4 && ncol == 32) {
                         float4* dst = reinterpret_cast<float4*>(drow + col0);
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
@@ -608,7 +610,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
-                            if (col0 + j < G.N) drow[col0 + j] = __uint_as_float(v[j]);
+                            if (j < ncol) drow[col0 + j] = __uint_as_float(v[j]);
                     }
                 }
             }
