@@ -725,10 +725,10 @@ gn_status launch_cfg(gn_handle h, const TcParams& p, int total_ctiles) {
 // clusters of 4 were measured slower (the cluster's lockstep cost more than the
 // L2 traffic saved).
 int pick_mt(const TcGemm* g, int ngemm, int sm_count) {
-    long long tiles2 = 0;
+    long long tiles2 = 0;   // work items with 256-row tiles (a K-split tile counts twice)
     for (int i = 0; i < ngemm; ++i) {
         if (g[i].M < 2 * BM) return 1;
-        tiles2 += ((g[i].M + 2 * BM - 1) / (2 * BM)) * ((g[i].N + g[i].bn - 1) / g[i].bn);
+        tiles2 += ((g[i].M + 2 * BM - 1) / (2 * BM)) * ((g[i].N + g[i].bn - 1) / g[i].bn) * (g[i].ksplit == 2 ? 2 : 1);
     }
     return tiles2 >= 4LL * sm_count ? 2 : 1;   // keep enough tiles to fill the GPU
 }
