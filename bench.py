@@ -328,33 +328,46 @@ def main():
              torch.empty(core.R.shape, dtype=torch.float64, pin_memory=True)] for _ in range(nset)]
     h2d = sum(t.numel() * t.element_size() for t in hosts)
     d2h = sum(o.numel() * o.element_size() for o in outh[0])
-    cstream = torch.cuda.Stream(device=dev)
-    ev_in = [torch.cuda.Event() for _ in range(nset)]    # inputs of the set landed
+    # Two host->device copy streams (large inputs split in row halves, so two copy
+    # engines can carry them) and one device->host stream.
+    hs = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    dstream = torch.cuda.Stream(device=dev)
+    ev_in = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(nset)]   # inputs of the set landed
     ev_done = [torch.cuda.Event() for _ in range(nset)]  # compute on the set finished
     ev_out = [torch.cuda.Event() for _ in range(nset)]   # results of the set copied out
 
     def prefetch(i):
         b = i % nset
-        cstream.wait_event(ev_done[b])            # the set's previous step has finished computing
-        with torch.cuda.stream(cstream):
-            for d_, h_ in zip(ins[b][0], hosts):
-                d_.copy_(h_, non_blocking=True)
-        ev_in[b].record(cstream)
+        for q in hs:
+            q.wait_event(ev_done[b])              # the set's previous step has finished computing
+        for d_, h_ in zip(ins[b][0], hosts):
+            if h_.numel() * h_.element_size() >= (64 << 20) and h_.dim() >= 1 and h_.shape[0] >= 2:
+                half = h_.shape[0] // 2
+                with torch.cuda.stream(hs[0]):
+                    d_[:half].copy_(h_[:half], non_blocking=True)
+                with torch.cuda.stream(hs[1]):
+                    d_[half:].copy_(h_[half:], non_blocking=True)
+            else:
+                with torch.cuda.stream(hs[0]):
+                    d_.copy_(h_, non_blocking=True)
+        for q, ev in zip(hs, ev_in[b]):
+            ev.record(q)
 
     def compute(i):
         b = i % nset
         Ad, Xd, Yd = ins[b][1]
         AXd, YtAd, cd = outd[b]
-        stream.wait_event(ev_in[b])
+        for ev in ev_in[b]:
+            stream.wait_event(ev)
         stream.wait_event(ev_out[b])              # the set's previous results are out
         H.sketch(Ad, Xd, Yd, AXd, YtAd, ws)
         H.core(YtAd, Xd, eps, mode, cd, ws)
         ev_done[b].record(stream)
-        cstream.wait_event(ev_done[b])
-        with torch.cuda.stream(cstream):
+        dstream.wait_event(ev_done[b])
+        with torch.cuda.stream(dstream):
             for o, s_ in zip(outh[b], (AXd, YtAd, cd.Q, cd.R)):
                 o.copy_(s_, non_blocking=True)
-        ev_out[b].record(cstream)
+        ev_out[b].record(dstream)
 
     def e2e_run(k):
         prefetch(0)
@@ -367,9 +380,11 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(cstream)
+    e0.record(hs[0])
+    for q in (hs[1], dstream, stream):   # nothing of the timed steps starts before e0
+        q.wait_stream(hs[0])
     e2e_run(a.steps)
-    e1.record(cstream)
+    e1.record(dstream)                   # after the last step's results are out (which waits for all)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / a.steps
     del ins, outd, outh, hosts
