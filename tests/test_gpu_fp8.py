@@ -86,11 +86,13 @@ def test_e4m3_sketch_exact_on_integer_inputs(gn, H, m, n, r, l):
     assert np.array_equal(npy(YtA), oYtA)
 
 
-def test_e4m3_sketch_large_sampled(gn, H):
-    """16384 x 8192, r = 1000, l = 500: enough tiles for the 256-row tile shape;
-    64 sampled rows of AX and 64 sampled columns of Y^T A against the oracle,
-    bitwise (integer-valued inputs as above, drawn on the device)."""
-    m, n, r, l = 16384, 8192, 1000, 500
+@pytest.mark.parametrize("r", [1000, 780])
+def test_e4m3_sketch_large_sampled(gn, H, r):
+    """16384 x 8192, l = r / 2: enough tiles for the 256-row tile shape (r = 780:
+    an odd number of AX column tiles, the last one ragged); 64 sampled rows of
+    AX and 64 sampled columns of Y^T A against the oracle, bitwise
+    (integer-valued inputs as above, drawn on the device)."""
+    m, n, l = 16384, 8192, r // 2
     g = torch.Generator(device="cuda").manual_seed(77)
     def draw(rows, cols):
         v = torch.randint(-3, 4, (rows, cols), generator=g, device="cuda", dtype=torch.int8).double()
