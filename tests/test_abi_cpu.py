@@ -56,3 +56,42 @@ def test_null_arguments_rejected_on_host():
     assert gn.lib.gn_factors(None, None, None, None, None, None, None, 0) == 1
     assert gn.lib.gn_hmt(None, None, None, None, None, None, 0) == 1
     assert gn.lib.gn_sync_status(None) == 1
+
+
+def test_fp64_tc_workspace_size_is_monotone():
+    """Callers size one workspace for their largest product and reuse it for
+    smaller ones: the digit-sliced product's workspace must not shrink when M,
+    N or K grows (K beyond one pass of 1024 and N beyond one launch's panel
+    included)."""
+    import paper_2009_11392_gb300 as gn
+    b = ctypes.c_size_t()
+    f = gn.lib.gn_dgemm_tc_workspace_size
+    sizes = [1, 15, 16, 100, 255, 256, 257, 1000, 1024, 1500, 4096, 32768]
+    def ws(M, N, K, a32=0):
+        assert f(M, N, K, a32, ctypes.byref(b)) == 0
+        return b.value
+    for M in sizes:
+        for N in (1, 32, 128, 256, 1000, 2000):
+            last = 0
+            for K in (1, 32, 900, 1024, 1025, 3000):
+                v = ws(M, N, K)
+                assert v >= last and v > 0
+                last = v
+    for K in (32, 1500):
+        for N in (32, 1000):
+            vals = [ws(M, N, K) for M in sizes]
+            assert vals == sorted(vals)
+        for M in (256, 32768):
+            vals = [ws(M, N, K) for N in (1, 16, 100, 256, 600, 1000, 5000)]
+            assert vals == sorted(vals)
+    assert f(10, 10, 0, 0, ctypes.byref(b)) == 1      # K < 1
+    assert f(-1, 10, 10, 0, ctypes.byref(b)) == 1
+    assert f(10, 10, 10, 0, None) == 1
+
+
+def test_fp64_tc_arguments_rejected_on_host():
+    import paper_2009_11392_gb300 as gn
+    L = gn.lib
+    assert L.gn_dgemm_tc(None, 4, 4, 4, 1.0, None, 0, 4, 0, None, 4, 0, 0.0, None, 4, None, 0) == 1
+    assert L.gn_set_fp64_tc(None, 1) == 1
+    assert L.gn_set_fp64_g(None, 1) == 1
