@@ -500,12 +500,23 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
         const int np = a > 16 ? 32 : a > 8 ? 16 : a > 4 ? 8 : a > 2 ? 4 : a > 1 ? 2 : 1;
         const int q = lane & (np - 1), sub = lane / np, nsub = 32 / np;
         const int cla = a - r0;
-        double acc = 0.0;
-        if (q < a)
-            for (int li = max(0, cla) + (warp - 1) * nsub + sub; li < nr; li += (CP_WARPS - 1) * nsub) {
+        // two partial sums: each FP64 FMA on the chain costs ~200 cycles on GB300
+        double acc = 0.0, acc1 = 0.0;
+        if (q < a) {
+            const int step = (CP_WARPS - 1) * nsub;
+            int li = max(0, cla) + (warp - 1) * nsub + sub;
+            for (; li + step < nr; li += 2 * step) {
+                const double xa = li == cla ? amb_col[a] : P[li * LDP + a];
+                const double xb = li + step == cla ? amb_col[a] : P[(li + step) * LDP + a];
+                acc = fma(xa, P[li * LDP + q], acc);
+                acc1 = fma(xb, P[(li + step) * LDP + q], acc1);
+            }
+            if (li < nr) {
                 const double xa = li == cla ? amb_col[a] : P[li * LDP + a];
                 acc = fma(xa, P[li * LDP + q], acc);
             }
+        }
+        acc += acc1;
         for (int o = np; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (sub == 0 && q < a) gpart[(warp - 1) * NPAIR + a * (a - 1) / 2 + q] = acc;
     };
@@ -528,17 +539,17 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
             const int nchunk = CP_WARPS * (32 / np);
             const int chunk = warp * (32 / np) + sub;
             const int j = c + off;
-            double acc = 0.0;
+            double acc = 0.0, acc1 = 0.0;   // two partial sums: half the FMA chain
             if (off < na) {
-                if (off == 0) {
-                    for (int li = max(0, cl + 1) + chunk; li < nr; li += nchunk) {
-                        const double x = P[li * LDP + c];
-                        acc = fma(x, x, acc);
-                    }
-                } else {
-                    for (int li = lo + chunk; li < nr; li += nchunk) acc = fma(P[li * LDP + c], P[li * LDP + j], acc);
+                const int jj = off == 0 ? c : j;
+                int li = (off == 0 ? max(0, cl + 1) : lo) + chunk;
+                for (; li + nchunk < nr; li += 2 * nchunk) {
+                    acc = fma(P[li * LDP + c], P[li * LDP + jj], acc);
+                    acc1 = fma(P[(li + nchunk) * LDP + c], P[(li + nchunk) * LDP + jj], acc1);
                 }
+                if (li < nr) acc = fma(P[li * LDP + c], P[li * LDP + jj], acc);
             }
+            acc += acc1;
             for (int o = np; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (sub == 0) tv[warp * 32 + off] = acc;   // tv doubles as the 8 x 32 partial table here
         }
@@ -1800,54 +1811,57 @@ namespace {
 // One warp per column.
 constexpr int QR_SB = 256;   // reflectors per block of the tensor-core Q formation
 
-__global__ void ut_inverse_kernel(const double* __restrict__ G, long long ldg, const double* __restrict__ tau, int n,
-                                  double* __restrict__ X, long long ldx) {
-    const long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= n) return;   // warp-uniform
+__global__ void __launch_bounds__(32) ut_inverse_kernel(const double* __restrict__ G, long long ldg,
+                                                        const double* __restrict__ tau, int n,
+                                                        double* __restrict__ X, long long ldx) {
+    const int w = blockIdx.x;   // the column of T this warp solves for
+    const int lane = threadIdx.x;
+    if (w >= n) return;
     constexpr int NT = QR_SB / 32;
-    // Right-looking form: once x_i is final, x_k -= G_ki x_i for every k < i,
-    // reading row i of the symmetric G (coalesced); rows arrive through a ring
-    // of four prefetched rows.
+    // lane l holds x_{32 t + l}; blocks of 32 rows from the one holding row w up.
+    // Inside a block: back substitution, one row per step (the row's final value
+    // broadcast from its lane, the rows below it in the block updated in their
+    // lanes).  After a block: its contribution removed from the blocks above
+    // with G_{k, 32m + l} = G_{32m + l, k} (G is symmetric), read along rows.
     double x[NT];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) x[t] = (lane + 32 * t == w) ? 1.0 : 0.0;
-    double g0[NT], g1[NT], g2[NT], g3[NT];
-    double ta0, ta1, ta2, ta3;   // tau of the ring's rows
-    auto load_row = [&](int i, double* dst, double& ta) {
+    for (int t = 0; t < NT; ++t) x[t] = (32 * t + lane == w) ? 1.0 : 0.0;
+    const int qb = w >> 5;
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int k = lane + 32 * t;
-            dst[t] = (i > 0 && k < i) ? G[static_cast<long long>(i) * ldg + k] : 0.0;
+    for (int p = NT - 1; p >= 0; --p) {
+        if (p > qb) continue;   // warp-uniform
+#pragma unroll
+        for (int sr = 31; sr >= 0; --sr) {
+            const int i = 32 * p + sr;
+            if (i > w) continue;   // rows past w stay zero
+            // the chain per row is one shuffle and one FMA: tau_i scales the
+            // coefficients (off the chain), not the broadcast value
+            const double ti = tau[i];
+            const double cik = lane < sr ? G[static_cast<long long>(i) * ldg + 32 * p + lane] * ti : 0.0;
+            const double xu = __shfl_sync(0xffffffffu, x[p], sr);
+            x[p] = lane == sr ? xu * ti : fma(-cik, xu, x[p]);
         }
-        ta = i >= 0 ? tau[i] : 0.0;
-    };
-    auto step = [&](int i, double* gr, double& ta) {
-        if (i < 0) return;
-        const int ti = i >> 5;
-        double xs = x[0];
+        if (p == 0) break;
+        // two partial sums per block row: half the FMA chain
+        double y[NT];
 #pragma unroll
-        for (int t = 1; t < NT; ++t)
-            if (t == ti) xs = x[t];   // a move; the owner lane's value is the one broadcast
-        const double xi = __shfl_sync(0xffffffffu, xs * ta, i & 31);
+        for (int m = 0; m < NT; ++m) y[m] = 0.0;
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            if (32 * t > i) continue;   // warp-uniform: rows k >= i take no update
-            const bool own = (t == ti) && lane == (i & 31);
-            x[t] = own ? xi : fma(-gr[t], xi, x[t]);   // gr[t] = 0 for k >= i
+        for (int kk = 0; kk < 32; ++kk) {
+            const int k = 32 * p + kk;
+            if (k > w) break;
+            const double xk = __shfl_sync(0xffffffffu, x[p], kk);
+            const double* gk = G + static_cast<long long>(k) * ldg + lane;
+#pragma unroll
+            for (int m = 0; m < NT; ++m) {
+                if (m >= p) continue;
+                if (kk & 1) y[m] = fma(-gk[32 * m], xk, y[m]);
+                else x[m] = fma(-gk[32 * m], xk, x[m]);
+            }
         }
-        load_row(i - 4, gr, ta);                        // the row four steps on
-    };
-    const int wi = static_cast<int>(w);
-    load_row(wi, g0, ta0);
-    load_row(wi - 1, g1, ta1);
-    load_row(wi - 2, g2, ta2);
-    load_row(wi - 3, g3, ta3);
-    for (int i = wi; i >= 0; i -= 4) {
-        step(i, g0, ta0);
-        step(i - 1, g1, ta1);
-        step(i - 2, g2, ta2);
-        step(i - 3, g3, ta3);
+#pragma unroll
+        for (int m = 0; m < NT; ++m)
+            if (m < p) x[m] += y[m];
     }
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
@@ -1900,7 +1914,7 @@ gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double
         const double* Vb = q.V + j0 * N + j0;   // Mp x nbb, ld N (explicit unit diagonal, zeros above)
         double* Qs = Q + j0 * ldq + j0;
         GN_TRY(oz_dgemm(h, nbb, nbb, Mp, 1.0, Vb, 0, N, 1, Vb, N, 0, 0.0, G, QR_SB, ozw, ozw_bytes));
-        ut_inverse_kernel<<<static_cast<unsigned>(nbb), 32, 0, h->stream>>>(   // a warp per block: all SMs
+        ut_inverse_kernel<<<static_cast<unsigned>(nbb), 32, 0, h->stream>>>(   // a warp per column, on every SM
             G, QR_SB, q.tau + j0, static_cast<int>(nbb), Tb, QR_SB); count_launch();
         GN_CUDA_TRY(cudaGetLastError());
         GN_TRY(oz_dgemm(h, nbb, Nq, Mp, 1.0, Vb, 0, N, 1, Qs, ldq, 0, 0.0, Wb, Nq, ozw, ozw_bytes));
