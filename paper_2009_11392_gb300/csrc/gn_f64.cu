@@ -573,19 +573,21 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
         //      four ranks' partials for every column, warp 0 adds the four sums
         const int cj = lane;
         if (warp < 4 && cj >= c && cj < jb) {
-            double a0 = 0.0, a1 = 0.0;
             const int o0 = cj == c ? 0 : 2 + cj, o1 = cj == c ? 1 : 2 + JB + cj;
+            double p0[4], p1[4];   // all four loads first, then a tree (short FP64 chain)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const int k = 4 * warp + kk;
+                p0[kk] = 0.0;
+                p1[kk] = 0.0;
                 if (k < cs) {
                     const double* rs = cluster.map_shared_rank(slot, k);
-                    a0 += rs[o0];
-                    a1 += rs[o1];
+                    p0[kk] = rs[o0];
+                    p1[kk] = rs[o1];
                 }
             }
-            tv[warp * 64 + cj] = a0;        // tv is free here: 4 x 2 x 32 partial sums
-            tv[warp * 64 + 32 + cj] = a1;
+            tv[warp * 64 + cj] = (p0[0] + p0[1]) + (p0[2] + p0[3]);   // tv is free here: 4 x 2 x 32 partial sums
+            tv[warp * 64 + 32 + cj] = (p1[0] + p1[1]) + (p1[2] + p1[3]);
         }
         __syncthreads();
         if (warp == 0) {
