@@ -47,7 +47,7 @@ typedef enum {
     GN_ERR_CUDA = 5,          /* a CUDA runtime / driver call failed */
     GN_ERR_NONFINITE = 6,     /* a non-finite value reached the core */
     GN_ERR_TIMEOUT = 7,       /* a bounded device-side wait expired */
-    GN_ERR_UNSUPPORTED = 8,   /* valid request this build does not implement */
+    GN_ERR_UNSUPPORTED = 8,   /* valid request the library does not implement */
     GN_ERR_ALIGNMENT = 9      /* operand address / leading dimension breaks a TMA rule */
 } gn_status;
 
