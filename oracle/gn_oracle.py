@@ -249,6 +249,88 @@ def error_fro(A, F, G):
 
 
 # ---------------------------------------------------------------------------
+# Using the approximant without forming it (the text after Algorithm 2)
+# ---------------------------------------------------------------------------
+def core_pinv_apply_left(c, Z):
+    """(Y^T A X)^+_(eps) Z for Z with r+l rows, right to left: Q_1^T Z, then
+    R^{-1} (back substitution, column by column), or after a truncation R_2^{-T}
+    (forward substitution with the lower-triangular R_2^T) and Q_2
+    (Section 5.1.1: the pseudoinverse is Q_2 R_2^{-T} Q_1^T)."""
+    k = c["k"]
+    Z = c["Q"][:, :k].T @ np.asarray(Z, np.float64)
+    out = np.zeros_like(Z)
+    if c["Q2"] is None:
+        for j in range(Z.shape[1]):
+            out[:, j] = back_subst_upper(c["R"], Z[:, j])
+        return out
+    R2t = c["R2"].T
+    for j in range(Z.shape[1]):
+        out[:, j] = forward_subst_lower(R2t, Z[:, j])
+    return c["Q2"] @ out
+
+
+def apply_right(AX, YtA, c, W):
+    """Ahat W = AX (R^{-1} (Q^T (Y^T A W))), in the order the text after
+    Algorithm 2 gives: O((m + n) r k) work, Ahat never formed."""
+    return np.asarray(AX, np.float64) @ core_pinv_apply_left(c, np.asarray(YtA, np.float64) @ W)
+
+
+def apply_left(W, AX, YtA, c):
+    """W Ahat = (((W AX) R^{-1}) Q^T) Y^T A (the text after Algorithm 2); after a
+    truncation (W AX) Q_2 R_2^{-T} Q_1^T, the same order as the factor F."""
+    Z = np.asarray(W, np.float64) @ np.asarray(AX, np.float64)
+    k = c["k"]
+    if c["Q2"] is None:
+        Z = right_solve_upper(Z, c["R"])
+    else:
+        Z = right_solve_upper_transpose(Z @ c["Q2"], c["R2"])
+    return (Z @ c["Q"][:, :k].T) @ np.asarray(YtA, np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Section 6: resampling and updating the sketch state (AX, Y^T A, X, Y)
+# ---------------------------------------------------------------------------
+def resample(A, AX, YtA, X, Y, Xd, Yd):
+    """Rank r -> r + dr (Section 6): new sketch columns Xd (n x dr) and Yd
+    (m x (dr + dl)); only the new products A Xd and Yd^T A touch A, the old
+    sketches are kept.  Returns (AX', Y'^T A, X', Y') with X' = [X, Xd],
+    Y' = [Y, Yd]; the core is then (Y'^T A) X'."""
+    A = np.asarray(A, np.float64)
+    AXn = np.hstack([np.asarray(AX, np.float64), A @ Xd])
+    YtAn = np.vstack([np.asarray(YtA, np.float64), np.asarray(Yd, np.float64).T @ A])
+    return AXn, YtAn, np.hstack([X, Xd]), np.hstack([Y, Yd])
+
+
+def append_rows(AX, YtA, X, Y, B, Yb):
+    """[A; B] with B (mb x n) and a new sketch block Yb (mb x (r+l)) (Section 6):
+    AX' = [AX; BX], Y'^T A' = Y^T A + Yb^T B, Y' = [Y; Yb]; X is unchanged."""
+    B = np.asarray(B, np.float64)
+    return (np.vstack([np.asarray(AX, np.float64), B @ X]),
+            np.asarray(YtA, np.float64) + np.asarray(Yb, np.float64).T @ B, X, np.vstack([Y, Yb]))
+
+
+def append_cols(AX, YtA, X, Y, B, Xb):
+    """[A, B] with B (m x nb) and a new sketch block Xb (nb x r), the column
+    analogue in Section 6: AX' = AX + B Xb, Y^T A' = [Y^T A, Y^T B], X' = [X; Xb]."""
+    B = np.asarray(B, np.float64)
+    return (np.asarray(AX, np.float64) + B @ Xb,
+            np.hstack([np.asarray(YtA, np.float64), np.asarray(Y, np.float64).T @ B]), np.vstack([X, Xb]), Y)
+
+
+def update(AX, YtA, X, Y, E):
+    """A <- A + E, the streaming model of Section 6: AX += E X, Y^T A += Y^T E."""
+    E = np.asarray(E, np.float64)
+    return np.asarray(AX, np.float64) + E @ X, np.asarray(YtA, np.float64) + np.asarray(Y, np.float64).T @ E, X, Y
+
+
+def gn_from_sketches(AX, YtA, X, eps=0.0, mode=AUTO, eps_relative=False, diag_iters=20):
+    """Algorithm 2 steps 2-3 from a sketch state (the core, then the factors)."""
+    c = core(YtA, X, eps, mode, eps_relative=eps_relative, diag_iters=diag_iters)
+    F, G = factors(AX, YtA, c)
+    return F @ G, c
+
+
+# ---------------------------------------------------------------------------
 # Algorithm 1 (HMT) and the comparison forms used only as cross-checks
 # ---------------------------------------------------------------------------
 def hmt(A, X):

@@ -458,3 +458,129 @@ def test_e4m3_tile_scale_rule():
             bound = np.maximum(2.0 ** -4 * np.abs(x32[i * 128:(i + 1) * 128, j * 128:(j + 1) * 128]),
                                2.0 ** (e[i, j] - 10))
             assert np.all(err <= bound)
+
+
+# ------------------------------------------------ sketch-state operations (Section 6)
+def _decaying(m, n, seed, p=1.0):
+    """A with singular values i^-p over min(m, n) modes (a full-rank test matrix)."""
+    k = min(m, n)
+    A, _ = _lowrank(m, n, k, seed, decay=np.arange(1, k + 1, dtype=float) ** -p)
+    return A
+
+
+@pytest.mark.parametrize("truncate", [False, True])
+def test_apply_without_forming_matches_formed_product(truncate):
+    """Ahat W and W Ahat in the orders the text after Algorithm 2 gives equal the
+    formed F G times W (the pinned factors) and, after a truncation, the SVD
+    epsilon-pseudoinverse form; W Ahat W' is consistent both ways."""
+    m, n, r, l = 70, 50, 12, 6
+    A = _decaying(m, n, 21, p=2.0)
+    X, Y = _sk(m, n, r, l, 21)
+    if truncate:
+        X[:, 9:] = X[:, :3] @ np.random.default_rng(3).standard_normal((3, 3))   # rank-deficient core
+    eps = O.scale_eps(1.0, np.linalg.norm(X, 2), np.linalg.norm(Y, 2), O.U64) * 1e3
+    mode = O.SGN if truncate else O.PLAIN
+    Ahat, p = O.gn(A, X, Y, eps, mode)
+    c = {k: p[k] for k in ("Q", "R", "k", "Q2", "R2")}
+    if truncate:
+        assert p["k"] < r
+    rng = np.random.default_rng(4)
+    W = rng.standard_normal((n, 5))
+    Wl = rng.standard_normal((4, m))
+    AW = O.apply_right(p["AX"], p["YtA"], c, W)
+    WA = O.apply_left(Wl, p["AX"], p["YtA"], c)
+    assert np.linalg.norm(AW - Ahat @ W) <= 1e-11 * np.linalg.norm(Ahat @ W)
+    assert np.linalg.norm(WA - Wl @ Ahat) <= 1e-11 * np.linalg.norm(Wl @ Ahat)
+    assert np.allclose(Wl @ AW, WA @ W, rtol=1e-11, atol=1e-11 * np.linalg.norm(Wl @ AW))
+    if truncate:
+        As = O.sgn_svd(A, X, Y, eps)
+        assert np.linalg.norm(AW - As @ W) <= 1e-8 * np.linalg.norm(As @ W)
+
+
+def test_apply_without_forming_recovers_low_rank():
+    """rank(A) <= r: Ahat = A (Section 3.1), so Ahat W = A W and W Ahat = W A."""
+    m, n, r, l = 60, 45, 8, 4
+    A, _ = _lowrank(m, n, 6, 31)
+    X, Y = _sk(m, n, r, l, 31)
+    eps = O.scale_eps(1.0, np.linalg.norm(X, 2), np.linalg.norm(Y, 2), O.U64)
+    _, p = O.gn(A, X, Y, eps, O.SGN)
+    c = {k: p[k] for k in ("Q", "R", "k", "Q2", "R2")}
+    W = np.random.default_rng(5).standard_normal((n, 3))
+    assert np.linalg.norm(O.apply_right(p["AX"], p["YtA"], c, W) - A @ W) <= 1e-11 * np.linalg.norm(A @ W)
+    Wl = np.random.default_rng(6).standard_normal((2, m))
+    assert np.linalg.norm(O.apply_left(Wl, p["AX"], p["YtA"], c) - Wl @ A) <= 1e-11 * np.linalg.norm(Wl @ A)
+
+
+def test_resample_matches_fresh_sketch_and_recovers_added_rank():
+    """r -> r + dr (Section 6): the resampled state equals the sketch taken with
+    [X, Xd], [Y, Yd] from scratch, and a rank-(r + dr) matrix that r could not
+    capture is recovered exactly after resampling."""
+    m, n, r, l, dr, dl = 64, 48, 6, 3, 4, 2
+    A, _ = _lowrank(m, n, r + dr, 41)
+    X, Y = _sk(m, n, r, l, 41)
+    rng = np.random.default_rng(42)
+    Xd, Yd = rng.standard_normal((n, dr)), rng.standard_normal((m, dr + dl))
+    AX, YtA = O.sketch(A, X, Y)
+    before, _ = O.gn_from_sketches(AX, YtA, X, 0.0, O.PLAIN)
+    assert np.linalg.norm(A - before) > 1e-3 * np.linalg.norm(A)
+    AXn, YtAn, Xn, Yn = O.resample(A, AX, YtA, X, Y, Xd, Yd)
+    AXs, YtAs = O.sketch(A, Xn, Yn)
+    assert np.linalg.norm(AXn - AXs) <= 1e-14 * np.linalg.norm(AXs)
+    assert np.linalg.norm(YtAn - YtAs) <= 1e-14 * np.linalg.norm(YtAs)
+    after, c = O.gn_from_sketches(AXn, YtAn, Xn, 0.0, O.PLAIN)
+    assert c["R"].shape == (r + dr, r + dr)
+    assert np.linalg.norm(A - after) <= 1e-11 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("where", ["rows", "cols"])
+def test_append_matches_gn_of_the_enlarged_matrix(where):
+    """Appended rows [A; B] (the display in Section 6) or columns [A, B] (its
+    analogue): the updated state gives the same approximant as GN run from
+    scratch on the enlarged matrix with the enlarged sketch, and recovers an
+    enlarged matrix of rank <= r exactly."""
+    m, n, r, l = 50, 40, 10, 5
+    rng = np.random.default_rng(51)
+    for lowrank in (False, True):
+        if lowrank:
+            U, V = rng.standard_normal((m + 12, 7)), rng.standard_normal((n + 9, 7))
+            big = U @ V.T
+        else:
+            big = _decaying(m + 12, n + 9, 52, p=1.5)
+        if where == "rows":
+            A, B = big[:m, :n], big[m:, :n]
+            X, Y = rng.standard_normal((n, r)), rng.standard_normal((m, r + l))
+            Yb = rng.standard_normal((B.shape[0], r + l))
+            AX, YtA = O.sketch(A, X, Y)
+            AXn, YtAn, Xn, Yn = O.append_rows(AX, YtA, X, Y, B, Yb)
+            whole = np.vstack([A, B])
+        else:
+            A, B = big[:m, :n], big[:m, n:]
+            X, Y = rng.standard_normal((n, r)), rng.standard_normal((m, r + l))
+            Xb = rng.standard_normal((B.shape[1], r))
+            AX, YtA = O.sketch(A, X, Y)
+            AXn, YtAn, Xn, Yn = O.append_cols(AX, YtA, X, Y, B, Xb)
+            whole = np.hstack([A, B])
+        upd, _ = O.gn_from_sketches(AXn, YtAn, Xn, 0.0, O.PLAIN)
+        fresh, _ = O.gn(whole, Xn, Yn, 0.0, O.PLAIN)
+        assert np.linalg.norm(upd - fresh) <= 1e-10 * np.linalg.norm(fresh)
+        if lowrank:
+            assert np.linalg.norm(upd - whole) <= 1e-10 * np.linalg.norm(whole)
+
+
+def test_streaming_update_matches_gn_of_the_updated_matrix():
+    """A <- A + E (Section 6): the updated sketches equal the sketches of A + E,
+    the approximant equals GN of A + E from scratch, and it interpolates:
+    Ahat X = (A + E) X (Section 3's annihilation property)."""
+    m, n, r, l = 60, 44, 9, 5
+    A = _decaying(m, n, 61, p=1.0)
+    E = 1e-2 * _decaying(m, n, 62, p=0.5)
+    X, Y = _sk(m, n, r, l, 61)
+    AX, YtA = O.sketch(A, X, Y)
+    AXn, YtAn, _, _ = O.update(AX, YtA, X, Y, E)
+    AXs, YtAs = O.sketch(A + E, X, Y)
+    assert np.linalg.norm(AXn - AXs) <= 1e-13 * np.linalg.norm(AXs)
+    assert np.linalg.norm(YtAn - YtAs) <= 1e-13 * np.linalg.norm(YtAs)
+    upd, _ = O.gn_from_sketches(AXn, YtAn, X, 0.0, O.PLAIN)
+    fresh, _ = O.gn(A + E, X, Y, 0.0, O.PLAIN)
+    assert np.linalg.norm(upd - fresh) <= 1e-10 * np.linalg.norm(fresh)
+    assert np.linalg.norm(upd @ X - (A + E) @ X) <= 1e-10 * np.linalg.norm((A + E) @ X)
