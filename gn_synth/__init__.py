@@ -36,6 +36,7 @@ __all__ = [
     "config3",
     "config4",
     "config5_problem",
+    "dct_sketch_draws",
 ]
 
 DEFAULT_SEED = 20091139
@@ -169,3 +170,14 @@ def config5_problem(index: int, shape, seed: int = DEFAULT_SEED, device="cpu",
     a = lowrank_plus_noise(m, n, k, sigma, 1e-8, s, device, dtype)
     x, y = sketches(m, n, r, l, s, device, dtype)
     return GNProblem(a, x, y, r, l, 0.0, f"batched #{index}")
+
+
+def dct_sketch_draws(n: int, r: int, seed: int = DEFAULT_SEED, stream: int = _STREAM_X):
+    """The random draws of a subsampled DCT sketch (the sketches of Section 7):
+    n random signs (+-1) and r distinct frequencies out of n, sorted.  Only the
+    draws; the sketch matrix itself is built by whoever applies it."""
+    g = torch.Generator()
+    g.manual_seed(_seed(seed, stream + 16))
+    signs = torch.randint(0, 2, (n,), generator=g).double() * 2.0 - 1.0
+    cols = torch.randperm(n, generator=g)[:r].sort().values
+    return signs, cols

@@ -331,6 +331,22 @@ def gn_from_sketches(AX, YtA, X, eps=0.0, mode=AUTO, eps_relative=False, diag_it
 
 
 # ---------------------------------------------------------------------------
+# Structured sketches (Section 7's subsampled DCT; Section 2.5's fast sketches)
+# ---------------------------------------------------------------------------
+def dct_sketch(n, signs, cols):
+    """X = D C^T S (n x r): D = diag(signs), C the orthonormal DCT-II matrix,
+    C[k, i] = a_k cos(pi (2 i + 1) k / (2 n)) with a_0 = sqrt(1/n) and
+    a_k = sqrt(2/n) otherwise, S the r columns `cols` of the identity.  X has
+    orthonormal columns; the usual sqrt(n/r) scale is left out, GN being
+    invariant under X -> X c.  A X is then row-wise: flip signs, DCT, keep the
+    `cols` frequencies, O(mn log n) with a fast transform (Section 2.5)."""
+    i = np.arange(n, dtype=np.float64)[:, None]
+    k = np.asarray(cols, dtype=np.float64)[None, :]
+    a = np.where(k == 0, np.sqrt(1.0 / n), np.sqrt(2.0 / n))
+    return np.asarray(signs, np.float64)[:, None] * (a * np.cos(np.pi * (2.0 * i + 1.0) * k / (2.0 * n)))
+
+
+# ---------------------------------------------------------------------------
 # Algorithm 1 (HMT) and the comparison forms used only as cross-checks
 # ---------------------------------------------------------------------------
 def hmt(A, X):

@@ -584,3 +584,40 @@ def test_streaming_update_matches_gn_of_the_updated_matrix():
     fresh, _ = O.gn(A + E, X, Y, 0.0, O.PLAIN)
     assert np.linalg.norm(upd - fresh) <= 1e-10 * np.linalg.norm(fresh)
     assert np.linalg.norm(upd @ X - (A + E) @ X) <= 1e-10 * np.linalg.norm((A + E) @ X)
+
+
+# ------------------------------------------------ structured sketches (Section 7)
+@pytest.mark.parametrize("n,r", [(64, 10), (97, 33), (128, 128)])
+def test_dct_sketch_orthonormal_and_matches_fast_transform(n, r):
+    """The subsampled DCT sketch has orthonormal columns, and A X equals the
+    fast route (flip the signs of A's columns, orthonormal DCT-II along rows by
+    SciPy's FFT-based transform, keep the sampled frequencies)."""
+    scipy_fft = pytest.importorskip("scipy.fft")
+    signs, cols = gn_synth.dct_sketch_draws(n, r, seed=n + r)
+    signs, cols = _np(signs), _np(cols)
+    X = O.dct_sketch(n, signs, cols)
+    assert np.linalg.norm(X.T @ X - np.eye(r)) <= 1e-13 * r
+    A = np.random.default_rng(n).standard_normal((23, n))
+    fast = scipy_fft.dct(A * signs[None, :], type=2, norm="ortho", axis=1)[:, cols]
+    assert np.linalg.norm(A @ X - fast) <= 1e-13 * np.linalg.norm(fast)
+
+
+def test_gn_with_dct_sketches_recovers_low_rank_and_tracks_gaussian():
+    """GN with subsampled DCT X and Y (Section 7's choice): exact recovery of a
+    rank-r matrix, and on a decaying spectrum an error within a small factor of
+    GN with Gaussian sketches of the same sizes (any O(1), well-conditioned
+    sketch works, Section 3)."""
+    m, n, r, l = 96, 80, 12, 6
+    sx, cx = (_np(t) for t in gn_synth.dct_sketch_draws(n, r, seed=71))
+    sy, cy = (_np(t) for t in gn_synth.dct_sketch_draws(m, r + l, seed=72))
+    X, Y = O.dct_sketch(n, sx, cx), O.dct_sketch(m, sy, cy)
+    A, _ = _lowrank(m, n, r, 73)
+    Ahat, _ = O.gn(A, X, Y, 0.0, O.PLAIN)
+    assert np.linalg.norm(A - Ahat) <= 1e-11 * np.linalg.norm(A)
+    A = _decaying(m, n, 74, p=2.0)
+    e_dct = np.linalg.norm(A - O.gn(A, X, Y, 0.0, O.PLAIN)[0])
+    Xg, Yg = _sk(m, n, r, l, 74)
+    e_g = np.linalg.norm(A - O.gn(A, Xg, Yg, 0.0, O.PLAIN)[0])
+    s = np.linalg.svd(A, compute_uv=False)
+    assert e_dct >= np.sqrt(np.sum(s[r:] ** 2)) * (1 - 1e-12)
+    assert e_dct <= 10 * e_g
