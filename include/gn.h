@@ -245,6 +245,21 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
 gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_core_t* core,
                      gn_mat* F, gn_mat* G, void* ws, size_t ws_bytes);
 
+/* Use of the approximant without forming it (the text after Algorithm 2):
+ *   side 0: out (m x kw) = Ahat W   = AX (R^{-1} (Q_1^T (Y^T A W)))      W: n x kw
+ *   side 1: out (kw x n) = W Ahat   = (((W AX) R^{-1}) Q_1^T) Y^T A      W: kw x m
+ * in the order given there (O((m + n) r kw) work, no m x n matrix); after a
+ * truncation (core->sgn, k < r) the core pseudoinverse Q_2 R_2^{-T} Q_1^T
+ * (Section 5.1.1) takes the place of R^{-1} Q^T.  AX and Y^T A as gn_sketch
+ * wrote them (GN_F64 or GN_F32), core from gn_core; W and out GN_F64,
+ * row-major, device.  FP64 products and triangular solves.  ws (device) of at
+ * least gn_apply_workspace_size bytes.  GN_ERR_SHAPE / GN_ERR_DTYPE on
+ * mismatched operands; asynchronous on the handle's stream. */
+gn_status gn_apply_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int64_t kw, int32_t side,
+                                  size_t* bytes);
+gn_status gn_apply(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_core_t* core, const gn_mat* W,
+                   gn_mat* out, int32_t side, void* ws, size_t ws_bytes);
+
 /* Sketch + core + factors in one call (Algorithm 2).  AX, YtA are outputs
  * (GN_F64 for FP64 operands, GN_F32 for the tensor-core path). */
 gn_status gn_approx(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,

@@ -39,6 +39,7 @@ ABI_SYMBOLS = (
     "gn_kernel_launches", "gn_error_fro2_noalloc", "gn_backward_workspace_size", "gn_backward",
     "gn_forward_dense", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
     "gn_batched_set_policy", "gn_batched_tune", "gn_set_fp64_tc", "gn_dgemm_tc_workspace_size", "gn_dgemm_tc",
+    "gn_apply_workspace_size", "gn_apply",
 )
 
 
@@ -109,6 +110,8 @@ def _load():
         "gn_batched_run": ([P, D, I32, P, SZ], I32),
         "gn_batched_set_policy": ([P, I32], I32),
         "gn_set_fp64_tc": ([P, I32], I32),
+        "gn_apply_workspace_size": ([I64, I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
+        "gn_apply": ([P, M, M, C, M, M, I32, P, SZ], I32),
         "gn_dgemm_tc_workspace_size": ([I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
         "gn_dgemm_tc": ([P, I64, I64, I64, D, P, I32, I64, I32, P, I64, I32, D, P, I64, P, SZ], I32),
         "gn_batched_tune": ([P, I32, ctypes.POINTER(GnProblem), P, SZ, D, I32, ctypes.POINTER(I32),
@@ -355,6 +358,26 @@ class Handle:
         _check(lib.gn_factors(self._h, ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.byref(c),
                               ctypes.byref(mat(F)), ctypes.byref(mat(G)), ctypes.c_void_p(ws.data_ptr()),
                               ws.numel()), "gn_factors")
+
+    def apply(self, AX, YtA, core: Core, W, out=None, side: int = 0, ws=None) -> torch.Tensor:
+        """Ahat W (side 0, W: n x kw -> m x kw) or W Ahat (side 1, W: kw x m ->
+        kw x n) from the sketches and the core, without forming Ahat."""
+        m, n = AX.shape[0], YtA.shape[1]
+        kw = W.shape[1] if side == 0 else W.shape[0]
+        if out is None:
+            shape = (m, kw) if side == 0 else (kw, n)
+            out = torch.empty(shape, dtype=torch.float64, device=W.device)
+        if ws is None:
+            b = ctypes.c_size_t()
+            _check(lib.gn_apply_workspace_size(m, n, core.r, core.l, kw, side, ctypes.byref(b)),
+                   "gn_apply_workspace_size")
+            with torch.cuda.stream(self.stream):   # freed in order with the handle's stream
+                ws = torch.empty(int(b.value), dtype=torch.uint8, device=W.device)
+        c = core.cstruct()
+        _check(lib.gn_apply(self._h, ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.byref(c),
+                            ctypes.byref(mat(W)), ctypes.byref(mat(out)), int(side),
+                            ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_apply")
+        return out
 
     def approx(self, A, X, Y, eps, mode, AX, YtA, core: Core, F, G, ws, A_lo=None) -> Core:
         c = core.cstruct()

@@ -765,6 +765,110 @@ gn_status gn_error_fro2(gn_handle h, const gn_mat* A, const gn_mat* F, const gn_
                       static_cast<const double*>(G->data), G->ld, k, out, static_cast<double*>(ws), ws_bytes);
 }
 
+// Scratch of gn_apply: two FP64 blocks of at most max(r + l, r) x kw, the
+// triangular solve's and the GEMMs' split-K partials.
+size_t apply_ws(long long m, long long n, long long r, long long l, long long kw, int sms) {
+    const long long rl = r + l;
+    return 2 * align256(sizeof(double) * rl * kw) + trsm_ws_bytes(kw, r, sms) +
+           std::max({dgemm_ws_bytes(rl, kw, n, sms), dgemm_ws_bytes(m, kw, r, sms), dgemm_ws_bytes(kw, r, m, sms),
+                     dgemm_ws_bytes(kw, n, rl, sms), dgemm_ws_bytes(kw, rl, r, sms)}) +
+           1024;
+}
+
+gn_status gn_apply_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int64_t kw, int32_t side,
+                                  size_t* bytes) {
+    if (!bytes || m < 1 || n < 1 || r < 1 || l < 0 || kw < 1 || (side != 0 && side != 1)) return GN_ERR_INVALID_ARG;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *bytes = apply_ws(m, n, r, l, kw, sms);
+    return GN_OK;
+}
+
+gn_status gn_apply(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_core_t* core, const gn_mat* W,
+                   gn_mat* out, int32_t side, void* ws, size_t ws_bytes) {
+    if (!h || !AX || !YtA || !core || !W || !out || !ws || (side != 0 && side != 1)) return GN_ERR_INVALID_ARG;
+    const long long m = AX->rows, n = YtA->cols, r = core->r, l = core->l, k = core->k, rl = r + l;
+    if (k < 1 || k > r || !core->Q || !core->R) return GN_ERR_INVALID_ARG;
+    const bool trunc = core->sgn && k < r;
+    if (trunc && (!core->Q2 || !core->R2)) return GN_ERR_INVALID_ARG;
+    GN_TRY(check_mat(AX, m, r));
+    GN_TRY(check_mat(YtA, rl, n));
+    if (AX->dtype != GN_F64 && AX->dtype != GN_F32) return GN_ERR_DTYPE;
+    if (YtA->dtype != GN_F64 && YtA->dtype != GN_F32) return GN_ERR_DTYPE;
+    if (W->dtype != GN_F64 || out->dtype != GN_F64 || !W->data || !out->data) return GN_ERR_DTYPE;
+    const long long kw = side == 0 ? W->cols : W->rows;
+    if (kw < 1) return GN_ERR_SHAPE;
+    if (side == 0 && (W->rows != n || out->rows != m || out->cols != kw)) return GN_ERR_SHAPE;
+    if (side == 1 && (W->cols != m || out->rows != kw || out->cols != n)) return GN_ERR_SHAPE;
+    if (W->ld < W->cols || out->ld < out->cols) return GN_ERR_SHAPE;
+    if (ws_bytes < apply_ws(m, n, r, l, kw, h->sm_count)) return GN_ERR_WORKSPACE;
+    Carve cv{static_cast<char*>(ws), ws_bytes, 0, true};
+    double* B1 = cv.take<double>(rl * kw);
+    double* B2 = cv.take<double>(rl * kw);
+    if (!cv.ok) return GN_ERR_WORKSPACE;
+    size_t gws_bytes = 0;
+    double* gws = cv.rest(&gws_bytes);
+    const double* Wd = static_cast<const double*>(W->data);
+    double* Od = static_cast<double*>(out->data);
+    const bool ax32 = AX->dtype == GN_F32, yta32 = YtA->dtype == GN_F32;
+    if (side == 0) {
+        // B1 = Y^T A W   ((r+l) x kw)
+        if (yta32)
+            GN_TRY(dgemm_a32(h, rl, kw, n, 1.0, static_cast<const float*>(YtA->data), YtA->ld, 0, Wd, W->ld, 0, 0.0,
+                             B1, kw, gws, gws_bytes));
+        else
+            GN_TRY(dgemm(h, rl, kw, n, 1.0, static_cast<const double*>(YtA->data), YtA->ld, 0, Wd, W->ld, 0, 0.0, B1,
+                         kw, gws, gws_bytes));
+        // B2 = (Q_1^T B1)^T = B1^T Q_1   (kw x k)
+        GN_TRY(dgemm(h, kw, k, rl, 1.0, B1, kw, 1, core->Q, r, 0, 0.0, B2, k, gws, gws_bytes));
+        const double* Zt = B2;   // Z^T (kw x r) with Z the core pseudoinverse applied to Y^T A W
+        if (!trunc) {
+            // (R^{-1} Q^T B1)^T = B2 R^{-T}
+            GN_TRY(trsm_right_upper(h, B2, kw, r, k, core->R, r, 1, gws, gws_bytes));
+        } else {
+            // (R_2^{-T} Q_1^T B1)^T = B2 R_2^{-1}, then Z^T = that Q_2^T (kw x r)
+            GN_TRY(trsm_right_upper(h, B2, kw, k, k, core->R2, r, 0, gws, gws_bytes));
+            GN_TRY(dgemm(h, kw, r, k, 1.0, B2, k, 0, core->Q2, r, 1, 0.0, B1, r, gws, gws_bytes));
+            Zt = B1;
+        }
+        // out = AX Z = AX (Z^T)^T   (m x kw)
+        if (ax32)
+            GN_TRY(dgemm_a32(h, m, kw, r, 1.0, static_cast<const float*>(AX->data), AX->ld, 0, Zt, r, 1, 0.0, Od,
+                             out->ld, gws, gws_bytes));
+        else
+            GN_TRY(dgemm(h, m, kw, r, 1.0, static_cast<const double*>(AX->data), AX->ld, 0, Zt, r, 1, 0.0, Od, out->ld,
+                         gws, gws_bytes));
+        return GN_OK;
+    }
+    // side 1: B1 = W AX   (kw x r)
+    if (ax32)
+        GN_TRY(dgemm_b32(h, kw, r, m, 1.0, Wd, W->ld, 0, static_cast<const float*>(AX->data), AX->ld, 0, 0.0, B1, r,
+                         gws, gws_bytes));
+    else
+        GN_TRY(dgemm(h, kw, r, m, 1.0, Wd, W->ld, 0, static_cast<const double*>(AX->data), AX->ld, 0, 0.0, B1, r,
+                     gws, gws_bytes));
+    const double* P = B1;   // (kw x k): (W AX) times the core pseudoinverse's left part
+    if (!trunc) {
+        GN_TRY(trsm_right_upper(h, B1, kw, r, r, core->R, r, 0, gws, gws_bytes));
+    } else {
+        GN_TRY(dgemm(h, kw, k, r, 1.0, B1, r, 0, core->Q2, r, 0, 0.0, B2, k, gws, gws_bytes));
+        GN_TRY(trsm_right_upper(h, B2, kw, k, k, core->R2, r, 1, gws, gws_bytes));
+        P = B2;
+    }
+    const long long ldp = trunc ? k : r;
+    // B = P Q_1^T   (kw x (r+l)), into the buffer P does not occupy
+    double* Bq = trunc ? B1 : B2;
+    GN_TRY(dgemm(h, kw, rl, k, 1.0, P, ldp, 0, core->Q, r, 1, 0.0, Bq, rl, gws, gws_bytes));
+    // out = B Y^T A   (kw x n)
+    if (yta32)
+        GN_TRY(dgemm_b32(h, kw, n, rl, 1.0, Bq, rl, 0, static_cast<const float*>(YtA->data), YtA->ld, 0, 0.0, Od,
+                         out->ld, gws, gws_bytes));
+    else
+        GN_TRY(dgemm(h, kw, n, rl, 1.0, Bq, rl, 0, static_cast<const double*>(YtA->data), YtA->ld, 0, 0.0, Od, out->ld,
+                     gws, gws_bytes));
+    return GN_OK;
+}
+
 gn_status gn_hmt(gn_handle h, const gn_mat* A, const gn_mat* X, gn_mat* Q, gn_mat* B, void* ws, size_t ws_bytes) {
     if (!h || !A || !X || !Q || !B || !ws) return GN_ERR_INVALID_ARG;
     const long long m = A->rows, n = A->cols, r = X->cols;
