@@ -260,6 +260,16 @@ gn_status gn_apply_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, in
 gn_status gn_apply(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_core_t* core, const gn_mat* W,
                    gn_mat* out, int32_t side, void* ws, size_t ws_bytes);
 
+/* Streaming update A <- A + E (Section 6): AX += E X and Y^T A += Y^T E, the
+ * sketches of E formed exactly as gn_sketch forms those of A (E given the same
+ * way: GN_F64, GN_BF16, GN_BF16X2 or GN_E4M3, with the same X, Y) into scratch
+ * and added elementwise into AX and YtA (as gn_sketch wrote them).  The core
+ * of the updated sketches is then gn_core's.  ws (device) of at least
+ * gn_update_workspace_size bytes; asynchronous on the handle's stream. */
+gn_status gn_update_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t op_dtype, size_t* bytes);
+gn_status gn_update(gn_handle h, const gn_mat* E, const gn_mat* X, const gn_mat* Y, gn_mat* AX, gn_mat* YtA,
+                    void* ws, size_t ws_bytes);
+
 /* Sketch + core + factors in one call (Algorithm 2).  AX, YtA are outputs
  * (GN_F64 for FP64 operands, GN_F32 for the tensor-core path). */
 gn_status gn_approx(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,

@@ -39,7 +39,7 @@ ABI_SYMBOLS = (
     "gn_kernel_launches", "gn_error_fro2_noalloc", "gn_backward_workspace_size", "gn_backward",
     "gn_forward_dense", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
     "gn_batched_set_policy", "gn_batched_tune", "gn_set_fp64_tc", "gn_dgemm_tc_workspace_size", "gn_dgemm_tc",
-    "gn_apply_workspace_size", "gn_apply",
+    "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update",
 )
 
 
@@ -112,6 +112,8 @@ def _load():
         "gn_set_fp64_tc": ([P, I32], I32),
         "gn_apply_workspace_size": ([I64, I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
         "gn_apply": ([P, M, M, C, M, M, I32, P, SZ], I32),
+        "gn_update_workspace_size": ([I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
+        "gn_update": ([P, M, M, M, M, M, P, SZ], I32),
         "gn_dgemm_tc_workspace_size": ([I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
         "gn_dgemm_tc": ([P, I64, I64, I64, D, P, I32, I64, I32, P, I64, I32, D, P, I64, P, SZ], I32),
         "gn_batched_tune": ([P, I32, ctypes.POINTER(GnProblem), P, SZ, D, I32, ctypes.POINTER(I32),
@@ -378,6 +380,21 @@ class Handle:
                             ctypes.byref(mat(W)), ctypes.byref(mat(out)), int(side),
                             ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_apply")
         return out
+
+    def update(self, E, X, Y, AX, YtA, ws=None, E_lo=None):
+        """A <- A + E on the sketch state: AX += E X, Y^T A += Y^T E (E given as
+        gn_sketch takes A)."""
+        m, n = mat(E).rows, mat(E).cols
+        r, rl = mat(X).cols, mat(Y).cols
+        if ws is None:
+            b = ctypes.c_size_t()
+            _check(lib.gn_update_workspace_size(m, n, r, rl - r, mat(E, E_lo).dtype, ctypes.byref(b)),
+                   "gn_update_workspace_size")
+            with torch.cuda.stream(self.stream):   # freed in order with the handle's stream
+                ws = torch.empty(int(b.value), dtype=torch.uint8, device=AX.device)
+        _check(lib.gn_update(self._h, ctypes.byref(mat(E, E_lo)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
+                             ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.c_void_p(ws.data_ptr()),
+                             ws.numel()), "gn_update")
 
     def approx(self, A, X, Y, eps, mode, AX, YtA, core: Core, F, G, ws, A_lo=None) -> Core:
         c = core.cstruct()

@@ -282,6 +282,39 @@ gn_status launch_sketch_e4m3(gn_handle h, const gn_mat* A, const gn_mat* X, cons
     return tc_launch(h, &p);
 }
 
+// dst (rows x cols, ldd) += src (rows x cols, lds), FP32 or FP64.
+template <typename T>
+__global__ void add_into_kernel(T* __restrict__ dst, long long ldd, const T* __restrict__ src, long long lds,
+                                long long rows, long long cols) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e - i * cols;
+        dst[i * ldd + j] += src[i * lds + j];
+    }
+}
+
+gn_status add_into(gn_handle h, gn_mat* dst, const void* src, long long lds) {
+    const long long total = dst->rows * dst->cols;
+    const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 16LL * h->sm_count));
+    if (dst->dtype == GN_F32)
+        add_into_kernel<float><<<blocks, 256, 0, h->stream>>>(static_cast<float*>(dst->data), dst->ld,
+                                                              static_cast<const float*>(src), lds, dst->rows,
+                                                              dst->cols);
+    else
+        add_into_kernel<double><<<blocks, 256, 0, h->stream>>>(static_cast<double*>(dst->data), dst->ld,
+                                                               static_cast<const double*>(src), lds, dst->rows,
+                                                               dst->cols);
+    count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
+size_t update_scratch(long long m, long long n, long long r, long long l, int op_dtype) {
+    const size_t es = op_dtype == GN_F64 ? sizeof(double) : sizeof(float);
+    return align256(es * m * round8(r)) + align256(es * (r + l) * round8(n)) + 512;
+}
+
 }  // namespace
 
 // ============================================================================ API
@@ -763,6 +796,40 @@ gn_status gn_error_fro2(gn_handle h, const gn_mat* A, const gn_mat* F, const gn_
     if (F->dtype != GN_F64 || G->dtype != GN_F64) return GN_ERR_DTYPE;
     return error_fro2(h, A->data, A->dtype, A->lo, m, n, A->ld, static_cast<const double*>(F->data), F->ld,
                       static_cast<const double*>(G->data), G->ld, k, out, static_cast<double*>(ws), ws_bytes);
+}
+
+gn_status gn_update_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t op_dtype, size_t* bytes) {
+    if (!bytes) return GN_ERR_INVALID_ARG;
+    size_t b = 0;
+    GN_TRY(gn_workspace_size(m, n, r, l, op_dtype, &b));
+    *bytes = b + update_scratch(m, n, r, l, op_dtype);
+    return GN_OK;
+}
+
+gn_status gn_update(gn_handle h, const gn_mat* E, const gn_mat* X, const gn_mat* Y, gn_mat* AX, gn_mat* YtA,
+                    void* ws, size_t ws_bytes) {
+    if (!h || !E || !X || !Y || !AX || !YtA || !ws) return GN_ERR_INVALID_ARG;
+    const long long m = E->rows, n = E->cols, r = X->cols, rl = Y->cols;
+    if (rl <= r) return GN_ERR_SHAPE;
+    GN_TRY(check_mat(AX, m, r));
+    GN_TRY(check_mat(YtA, rl, n));
+    if (AX->dtype != YtA->dtype || (AX->dtype != GN_F32 && AX->dtype != GN_F64)) return GN_ERR_DTYPE;
+    const size_t scratch = update_scratch(m, n, r, rl - r, E->dtype);
+    if (ws_bytes <= scratch) return GN_ERR_WORKSPACE;
+    // E's sketches into the front of ws (the layout gn_sketch writes), the rest is gn_sketch's own scratch
+    const size_t es = AX->dtype == GN_F64 ? sizeof(double) : sizeof(float);
+    char* base = static_cast<char*>(ws);
+    const long long ldx = round8(r), ldy = round8(n);
+    gn_mat dAX = *AX, dYtA = *YtA;
+    dAX.data = base;
+    dAX.ld = ldx;
+    dYtA.data = base + align256(es * m * ldx);
+    dYtA.ld = ldy;
+    if (align256(es * m * ldx) + align256(es * rl * ldy) > scratch) return GN_ERR_WORKSPACE;
+    GN_TRY(gn_sketch(h, E, X, Y, &dAX, &dYtA, base + scratch, ws_bytes - scratch));
+    GN_TRY(add_into(h, AX, dAX.data, ldx));
+    GN_TRY(add_into(h, YtA, dYtA.data, ldy));
+    return GN_OK;
 }
 
 // Scratch of gn_apply: two FP64 blocks of at most max(r + l, r) x kw, the

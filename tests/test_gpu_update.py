@@ -1,0 +1,72 @@
+"""A <- A + E on the sketch state (gn_update, Section 6): the updated sketches
+against the sketches of A + E, and the core of the updated state against the
+core of a fresh sketch."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gn_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2009_11392_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def H(gn):
+    return gn.Handle()
+
+
+def npy(t):
+    return t.detach().double().cpu().numpy()
+
+
+def test_update_bf16_exact_on_integer_inputs(gn, H):
+    """Integers in [-3, 3] are exact in BF16 and every sum stays an integer below
+    2^24: the updated AX, Y^T A equal (A + E) X and Y^T (A + E) bit for bit,
+    and the core of the updated state is the core of a fresh sketch of A + E."""
+    m, n, r, l = 700, 520, 60, 30
+    g = torch.Generator().manual_seed(5)
+    draw = lambda a, b: torch.randint(-3, 4, (a, b), generator=g).double()
+    A, E, X, Y = draw(m, n), draw(m, n), draw(n, r), draw(m, r + l)
+    Ab, Eb, Xb, Yb, ABb = (H.quantize(t.cuda()) for t in (A, E, X, Y, A + E))
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    H.update(Eb, Xb, Yb, AX, YtA)
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch((A + E).numpy(), X.numpy(), Y.numpy())
+    assert np.array_equal(npy(AX), oAX)
+    assert np.array_equal(npy(YtA), oYtA)
+    AX2 = torch.empty_like(AX)
+    YtA2 = torch.empty_like(YtA)
+    H.sketch(ABb, Xb, Yb, AX2, YtA2, ws)
+    c1, c2 = gn.Core.empty(r, l, "cuda"), gn.Core.empty(r, l, "cuda")
+    H.core(YtA, Xb, 0.0, gn.PLAIN, c1, ws)
+    H.core(YtA2, Xb, 0.0, gn.PLAIN, c2, ws)
+    assert H.sync_status() == 0
+    assert torch.equal(c1.R, c2.R) and torch.equal(c1.Q, c2.Q)
+
+
+def test_update_fp64_against_oracle(gn, H):
+    m, n, r, l = 400, 300, 25, 12
+    rng = np.random.default_rng(6)
+    A, E = rng.standard_normal((m, n)), 1e-3 * rng.standard_normal((m, n))
+    X, Y = rng.standard_normal((n, r)), rng.standard_normal((m, r + l))
+    cu = lambda t: torch.from_numpy(t).cuda()
+    ws = H.workspace(m, n, r, l, gn.F64)
+    AX = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float64, device="cuda")
+    H.sketch(cu(A), cu(X), cu(Y), AX, YtA, ws)
+    H.update(cu(E), cu(X), cu(Y), AX, YtA)
+    assert H.sync_status() == 0
+    AXn, YtAn, _, _ = O.update(*O.sketch(A, X, Y), X, Y, E)
+    assert np.linalg.norm(npy(AX) - AXn) <= 1e-13 * np.linalg.norm(AXn)
+    assert np.linalg.norm(npy(YtA) - YtAn) <= 1e-13 * np.linalg.norm(YtAn)
