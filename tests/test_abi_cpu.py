@@ -95,3 +95,24 @@ def test_fp64_tc_arguments_rejected_on_host():
     assert L.gn_dgemm_tc(None, 4, 4, 4, 1.0, None, 0, 4, 0, None, 4, 0, 0.0, None, 4, None, 0) == 1
     assert L.gn_set_fp64_tc(None, 1) == 1
     assert L.gn_set_fp64_g(None, 1) == 1
+
+
+def test_apply_and_update_host_validation():
+    """gn_apply / gn_update size their scratch and reject bad arguments on the
+    host, before any launch."""
+    import paper_2009_11392_gb300 as gn
+    L = gn.lib
+    b = ctypes.c_size_t()
+    assert L.gn_apply_workspace_size(1000, 500, 20, 10, 7, 0, ctypes.byref(b)) == 0 and b.value > 0
+    small = b.value
+    assert L.gn_apply_workspace_size(32768, 16384, 1000, 500, 64, 1, ctypes.byref(b)) == 0 and b.value > small
+    assert L.gn_apply_workspace_size(1000, 500, 20, 10, 0, 0, ctypes.byref(b)) == 1     # kw < 1
+    assert L.gn_apply_workspace_size(1000, 500, 20, 10, 7, 2, ctypes.byref(b)) == 1     # side not 0 / 1
+    assert L.gn_apply_workspace_size(1000, 500, 20, 10, 7, 0, None) == 1
+    assert L.gn_apply(None, None, None, None, None, None, 0, None, 0) == 1
+    assert L.gn_update_workspace_size(1000, 500, 20, 10, gn.BF16, ctypes.byref(b)) == 0
+    upd = b.value
+    assert L.gn_workspace_size(1000, 500, 20, 10, gn.BF16, ctypes.byref(b)) == 0 and upd > b.value
+    assert L.gn_update_workspace_size(1000, 500, 20, 10, gn.F32, ctypes.byref(b)) == 3  # no F32 operand path
+    assert L.gn_update_workspace_size(1000, 500, 0, 10, gn.BF16, ctypes.byref(b)) == 2  # r < 1
+    assert L.gn_update(None, None, None, None, None, None, None, 0) == 1
