@@ -249,6 +249,85 @@ def error_fro(A, F, G):
 
 
 # ---------------------------------------------------------------------------
+# Section 5.1.1: stabilising the core by perturbation instead of truncation
+# ---------------------------------------------------------------------------
+def pivoted_householder_qr(C):
+    """Column-pivoted Householder QR (rank revealing): C P = Q R with the
+    column of largest remaining norm moved forward at each step, so that
+    |R_00| >= |R_11| >= ... ; returns (Q, R, perm) with C[:, perm] = Q R.
+    Reflectors as in householder_qr; diag(R) made non-negative at the end."""
+    W = np.array(C, dtype=np.float64, copy=True)
+    M, N = W.shape
+    perm = np.arange(N)
+    V = np.zeros((M, N))
+    tau = np.zeros(N)
+    for j in range(N):
+        norms = np.einsum("ij,ij->j", W[j:, j:], W[j:, j:])
+        p = j + int(np.argmax(norms))
+        if p != j:
+            W[:, [j, p]] = W[:, [p, j]]
+            perm[[j, p]] = perm[[p, j]]
+        x = W[j:, j].copy()
+        alpha = x[0]
+        tail = float(np.dot(x[1:], x[1:]))
+        v = np.zeros(M - j)
+        v[0] = 1.0
+        if tail == 0.0:
+            t = 0.0
+        else:
+            normx = np.sqrt(alpha * alpha + tail)
+            beta = -normx if alpha >= 0.0 else normx
+            v[1:] = x[1:] / (alpha - beta)
+            t = (beta - alpha) / beta
+        if t != 0.0:
+            W[j:, j:] -= t * np.outer(v, v @ W[j:, j:])
+        V[j:, j] = v
+        tau[j] = t
+    R = np.triu(W[:N, :])
+    Q = np.zeros((M, N))
+    Q[:N, :N] = np.eye(N)
+    for j in range(N - 1, -1, -1):
+        if tau[j] != 0.0:
+            v = V[j:, j]
+            Q[j:, :] -= tau[j] * np.outer(v, v @ Q[j:, :])
+    d = np.where(np.diag(R) < 0.0, -1.0, 1.0)
+    return Q * d[None, :], R * d[:, None], perm
+
+
+def perturbed_core_factors(AX, YtA, X, floor, variant):
+    """GN with the core perturbed so that nothing needs truncating (Section
+    5.1.1's three alternatives); floor is the absolute level raised to (the
+    paper's u in its normalisation, here the same threshold as eps):
+      'svd':   C = U S V^T, S -> max(S, floor); F = AX V S^{-1}, G = U^T Y^T A
+      'rrqr':  C P = Q R pivoted, |R_ii| -> max(|R_ii|, floor);
+               F = (AX) P R^{-1} (row-wise solve), G = Q^T Y^T A
+      'diag':  C = Q R unpivoted, |R_ii| -> max(|R_ii|, floor) (sign kept,
+               sign(0) = +1); F = AX R^{-1}, G = Q^T Y^T A.
+    Returns (F, G) with Ahat = F G, multiplied in the stable order."""
+    C = core_matrix(YtA, X)
+    AX = np.asarray(AX, np.float64)
+    YtA = np.asarray(YtA, np.float64)
+
+    def raise_diag(R):
+        R = R.copy()
+        d = np.diag(R)
+        s = np.where(d < 0.0, -1.0, 1.0)
+        R[np.diag_indices_from(R)] = s * np.maximum(np.abs(d), floor)
+        return R
+
+    if variant == "svd":
+        U, sv, Vt = np.linalg.svd(C, full_matrices=False)
+        return (AX @ Vt.T) / np.maximum(sv, floor)[None, :], U.T @ YtA
+    if variant == "rrqr":
+        Q, R, perm = pivoted_householder_qr(C)
+        return right_solve_upper(AX[:, perm], raise_diag(R)), Q.T @ YtA
+    if variant == "diag":
+        Q, R = householder_qr(C)
+        return right_solve_upper(AX, raise_diag(R)), Q.T @ YtA
+    raise ValueError(variant)
+
+
+# ---------------------------------------------------------------------------
 # Using the approximant without forming it (the text after Algorithm 2)
 # ---------------------------------------------------------------------------
 def core_pinv_apply_left(c, Z):

@@ -621,3 +621,78 @@ def test_gn_with_dct_sketches_recovers_low_rank_and_tracks_gaussian():
     s = np.linalg.svd(A, compute_uv=False)
     assert e_dct >= np.sqrt(np.sum(s[r:] ** 2)) * (1 - 1e-12)
     assert e_dct <= 10 * e_g
+
+
+# ------------------------------------------- core stabilised by perturbation (Section 5.1.1)
+@pytest.mark.parametrize("shape", [(30, 20), (45, 45), (60, 12)])
+def test_pivoted_qr_is_rank_revealing_and_backward_stable(shape):
+    """C P = Q R with orthonormal Q, non-increasing |R_ii| (the pivoting rule),
+    backward error at the rounding level, and on an exactly rank-k matrix the
+    trailing diagonal at the rounding level."""
+    rng = np.random.default_rng(shape[0])
+    C = rng.standard_normal(shape) * np.exp2(rng.uniform(-6, 6, shape[1]))[None, :]
+    Q, R, perm = O.pivoted_householder_qr(C)
+    n = shape[1]
+    assert sorted(perm.tolist()) == list(range(n))
+    assert np.linalg.norm(C[:, perm] - Q @ R) <= 50 * n * O.U64 * np.linalg.norm(C)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 50 * n * O.U64
+    d = np.abs(np.diag(R))
+    assert np.all(d[:-1] >= d[1:] * (1 - 1e-12)) and np.all(np.diag(R) >= 0)
+    k = 7
+    Ck = rng.standard_normal((shape[0], k)) @ rng.standard_normal((k, n))
+    _, Rk, _ = O.pivoted_householder_qr(Ck)
+    dk = np.abs(np.diag(Rk))
+    assert dk[k - 1] > 1e-6 * dk[0] and np.all(dk[k:] <= 1e-12 * dk[0])
+
+
+@pytest.mark.parametrize("variant", ["svd", "rrqr", "diag"])
+def test_perturbed_core_equals_plain_gn_when_nothing_is_below_the_floor(variant):
+    m, n, r, l = 70, 55, 10, 5
+    A = _decaying(m, n, 91, p=1.0)
+    X, Y = _sk(m, n, r, l, 91)
+    AX, YtA = O.sketch(A, X, Y)
+    plain, _ = O.gn(A, X, Y, 0.0, O.PLAIN)
+    F, G = O.perturbed_core_factors(AX, YtA, X, 1e-300, variant)
+    assert np.linalg.norm(F @ G - plain) <= 1e-11 * np.linalg.norm(plain)
+
+
+@pytest.mark.parametrize("variant", ["svd", "rrqr", "diag"])
+def test_perturbed_core_recovers_rank_deficient_inputs(variant):
+    """rank(A) = k0 < r makes Y^T A X exactly singular: the unperturbed core has
+    no inverse, the perturbed one (floor at the rounding level of C) keeps
+    ||R^{-1}|| bounded by 1 / floor and still returns A (Section 5.1.1: the
+    perturbation replaces the truncation)."""
+    m, n, r, l, k0 = 70, 55, 12, 6, 5
+    A, _ = _lowrank(m, n, k0, 92)
+    X, Y = _sk(m, n, r, l, 92)
+    AX, YtA = O.sketch(A, X, Y)
+    C = O.core_matrix(YtA, X)
+    floor = 10 * O.U64 * np.linalg.norm(C, 2)
+    F, G = O.perturbed_core_factors(AX, YtA, X, floor, variant)
+    assert np.all(np.isfinite(F)) and np.all(np.isfinite(G))
+    assert np.linalg.norm(F @ G - A) <= 1e-12 * np.linalg.norm(A)
+    sv = np.linalg.svd(C, compute_uv=False)
+    assert sv[k0] <= 1e-12 * sv[0]                  # the core really is singular
+
+
+@pytest.mark.parametrize("variant", ["svd", "rrqr", "diag"])
+def test_perturbed_core_handles_an_exactly_zero_pivot(variant):
+    """A zero column of X gives R_jj = 0 exactly: without the perturbation the
+    solve divides by zero; with it the factors stay finite and the error is
+    SGN's to within 2 % (each variant is a valid approximant of the same
+    quality); the pivoted QR moves the zero column last, where the raised
+    diagonal multiplies nothing, so it returns SGN's approximant itself."""
+    m, n, r, l = 60, 45, 10, 5
+    A = _decaying(m, n, 93, p=1.5)
+    X, Y = _sk(m, n, r, l, 93)
+    X[:, 4] = 0.0
+    AX, YtA = O.sketch(A, X, Y)
+    C = O.core_matrix(YtA, X)
+    floor = 10 * O.U64 * np.linalg.norm(C, 2)
+    F, G = O.perturbed_core_factors(AX, YtA, X, floor, variant)
+    assert np.all(np.isfinite(F)) and np.all(np.isfinite(G))
+    sgn = O.sgn_svd(A, X, Y, floor)
+    e_sgn = np.linalg.norm(A - sgn)
+    assert np.linalg.norm(A - F @ G) <= 1.02 * e_sgn
+    if variant == "rrqr":
+        assert np.linalg.norm(F @ G - sgn) <= 1e-10 * np.linalg.norm(sgn)
