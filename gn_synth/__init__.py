@@ -37,6 +37,8 @@ __all__ = [
     "config4",
     "config5_problem",
     "dct_sketch_draws",
+    "countsketch_draws",
+    "sparse_lowrank_plus_noise",
 ]
 
 DEFAULT_SEED = 20091139
@@ -181,3 +183,41 @@ def dct_sketch_draws(n: int, r: int, seed: int = DEFAULT_SEED, stream: int = _ST
     signs = torch.randint(0, 2, (n,), generator=g).double() * 2.0 - 1.0
     cols = torch.randperm(n, generator=g)[:r].sort().values
     return signs, cols
+
+
+def countsketch_draws(n: int, r: int, seed: int = DEFAULT_SEED, stream: int = _STREAM_X):
+    """The random draws of a CountSketch matrix (Section 2.5: one +-1 per row):
+    a bucket in [0, r) and a sign for each of the n rows.  Only the draws."""
+    g = torch.Generator()
+    g.manual_seed(_seed(seed, stream + 32))
+    buckets = torch.randint(0, r, (n,), generator=g)
+    signs = torch.randint(0, 2, (n,), generator=g).double() * 2.0 - 1.0
+    return buckets, signs
+
+
+def sparse_lowrank_plus_noise(m: int, n: int, k: int, nnz_per_row: int, seed: int = DEFAULT_SEED):
+    """A sparse stand-in for Section 7's sparse experiment (whose matrix is not
+    available): the sum of k sparse rank-1 terms u_t v_t^T, each supported on
+    `per` random rows and `per` random columns with per^2 ~ nnz_per_row m / k
+    (so the k terms hold about nnz_per_row nonzeros per row), term t scaled by
+    1 / (t + 1), plus m nnz_per_row / 4 entries of N(0, 1e-8) noise; COO
+    triplets (rows, cols, values), duplicates summed by the caller.  Only draws."""
+    g = torch.Generator()
+    g.manual_seed(_seed(seed, _STREAM_A1 + 48))
+    rows, cols, vals = [], [], []
+    per = max(1, int(math.sqrt(max(1, nnz_per_row) * m / max(1, k))))
+    for t in range(k):
+        ri = torch.randperm(m, generator=g)[: max(1, min(m, per))]
+        ci = torch.randperm(n, generator=g)[: max(1, min(n, per))]
+        ui = torch.randn(len(ri), generator=g, dtype=torch.float64) * (t + 1) ** -1.0
+        vi = torch.randn(len(ci), generator=g, dtype=torch.float64)
+        rr = ri[:, None].expand(-1, len(ci)).reshape(-1)
+        cc = ci[None, :].expand(len(ri), -1).reshape(-1)
+        rows.append(rr)
+        cols.append(cc)
+        vals.append((ui[:, None] * vi[None, :]).reshape(-1))
+    nz = m * max(1, nnz_per_row) // 4
+    rows.append(torch.randint(0, m, (nz,), generator=g))
+    cols.append(torch.randint(0, n, (nz,), generator=g))
+    vals.append(1e-8 * torch.randn(nz, generator=g, dtype=torch.float64))
+    return torch.cat(rows), torch.cat(cols), torch.cat(vals)

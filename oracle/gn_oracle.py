@@ -8,8 +8,9 @@ it; the two meet only at the seeded inputs drawn by ``gn_synth``.
 Everything here is numpy in FP64, written to be read against the paper
 (Nakatsukasa, "Fast and stable randomized low-rank matrix approximation",
 arXiv:2009.11392).  Citations name the paper's sections, equations and
-algorithms.  Library primitives used as single steps: matrix products (``@``)
-and, for cross-checks only, LAPACK's SVD / pseudoinverse.  The Householder QR,
+algorithms.  Library primitives used as single steps: matrix products (``@``,
+scipy.sparse products for sparse inputs) and, for cross-checks only, LAPACK's
+SVD / pseudoinverse.  The Householder QR,
 the epsilon-truncation, the second QR, the triangular solves, the norm
 estimator and the adjoint are written out step by step here.
 
@@ -423,6 +424,31 @@ def dct_sketch(n, signs, cols):
     k = np.asarray(cols, dtype=np.float64)[None, :]
     a = np.where(k == 0, np.sqrt(1.0 / n), np.sqrt(2.0 / n))
     return np.asarray(signs, np.float64)[:, None] * (a * np.cos(np.pi * (2.0 * i + 1.0) * k / (2.0 * n)))
+
+
+def countsketch(n, r, buckets, signs):
+    """The CountSketch matrix (Section 2.5, Clarkson-Woodruff): n x r with
+    X[i, buckets[i]] = signs[i] and zeros elsewhere, one +-1 per row."""
+    X = np.zeros((n, r))
+    X[np.arange(n), np.asarray(buckets)] = np.asarray(signs, np.float64)
+    return X
+
+
+def countsketch_apply_right(A, buckets, signs, r):
+    """A X for the CountSketch X without forming it: column c of A X is the
+    signed sum of the columns i of A with buckets[i] = c (O(nnz(A)) work, the
+    input-sparsity cost of Section 2.5); A dense or scipy.sparse."""
+    import scipy.sparse as sp
+    n = A.shape[1]
+    S = sp.csr_matrix((np.asarray(signs, np.float64), (np.arange(n), np.asarray(buckets))), shape=(n, r))
+    out = A @ S
+    return out.toarray() if sp.issparse(out) else np.asarray(out)
+
+
+def sparse_from_coo(m, n, rows, cols, vals):
+    """CSR matrix from COO triplets, duplicates summed (scipy.sparse)."""
+    import scipy.sparse as sp
+    return sp.csr_matrix((np.asarray(vals, np.float64), (np.asarray(rows), np.asarray(cols))), shape=(m, n))
 
 
 # ---------------------------------------------------------------------------

@@ -696,3 +696,43 @@ def test_perturbed_core_handles_an_exactly_zero_pivot(variant):
     assert np.linalg.norm(A - F @ G) <= 1.02 * e_sgn
     if variant == "rrqr":
         assert np.linalg.norm(F @ G - sgn) <= 1e-10 * np.linalg.norm(sgn)
+
+
+# ------------------------------------------------ sparse A and CountSketch (Section 2.5, Section 7)
+def test_countsketch_structure_and_input_sparsity_product():
+    """One +-1 per row, X^T X = diag(bucket counts), and the bucket-sum product
+    on a sparse A equals the dense product."""
+    m, n, r = 120, 90, 16
+    b, s = (_np(t) for t in gn_synth.countsketch_draws(n, r, seed=101))
+    X = O.countsketch(n, r, b, s)
+    assert np.all(np.count_nonzero(X, axis=1) == 1) and set(np.unique(np.abs(X[X != 0]))) == {1.0}
+    counts = np.bincount(b, minlength=r).astype(float)
+    assert np.array_equal(X.T @ X, np.diag(counts))
+    rr, cc, vv = (_np(t) for t in gn_synth.sparse_lowrank_plus_noise(m, n, 4, 10, seed=102))
+    As = O.sparse_from_coo(m, n, rr, cc, vv)
+    Ad = As.toarray()
+    fast = O.countsketch_apply_right(As, b, s, r)
+    assert np.linalg.norm(fast - Ad @ X) <= 1e-14 * max(np.linalg.norm(Ad @ X), 1e-300)
+
+
+def test_gn_with_countsketch_on_sparse_input():
+    """GN with CountSketch X, Y on a sparse matrix of rank k <= r (no noise):
+    the sketches by the input-sparsity route give the approximant of the dense
+    route, and it recovers A (the Clarkson-Woodruff special case of GN the
+    paper notes in Section 7)."""
+    m, n, k, r, l = 200, 150, 5, 12, 6
+    rr, cc, vv = (_np(t) for t in gn_synth.sparse_lowrank_plus_noise(m, n, k, 12, seed=103))
+    keep = np.abs(vv) > 1e-6                                   # drop the noise: exactly rank <= k
+    As = O.sparse_from_coo(m, n, rr[keep], cc[keep], vv[keep])
+    Ad = As.toarray()
+    bx, sx = (_np(t) for t in gn_synth.countsketch_draws(n, r, seed=104))
+    by, sy = (_np(t) for t in gn_synth.countsketch_draws(m, r + l, seed=105))
+    X, Y = O.countsketch(n, r, bx, sx), O.countsketch(m, r + l, by, sy)
+    AX = O.countsketch_apply_right(As, bx, sx, r)
+    YtA = O.countsketch_apply_right(As.T.tocsr(), by, sy, r + l).T
+    eps = O.scale_eps(np.linalg.norm(Ad, 2), np.linalg.norm(X, 2), np.linalg.norm(Y, 2), O.U64)
+    Ahat, c = O.gn_from_sketches(AX, YtA, X, eps, O.SGN)       # rank k < r: SGN truncates
+    ref, p = O.gn(Ad, X, Y, eps, O.SGN)
+    assert c["k"] == p["k"] <= k
+    assert np.linalg.norm(Ahat - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert np.linalg.norm(Ahat - Ad) <= 1e-9 * np.linalg.norm(Ad)
