@@ -270,6 +270,25 @@ gn_status gn_update_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, i
 gn_status gn_update(gn_handle h, const gn_mat* E, const gn_mat* X, const gn_mat* Y, gn_mat* AX, gn_mat* YtA,
                     void* ws, size_t ws_bytes);
 
+/* Resampling r -> r + dr (Section 6): AXn (m x (r + dr)) = [AX, A Xd] and
+ * YtAn ((r + l + dr + dl) x n) = [Y^T A; Yd^T A] from the old sketches (copied)
+ * and the sketch of A by the new blocks Xd (n x dr), Yd (m x (dr + dl), dl >= 1)
+ * alone; AX, YtA as gn_sketch wrote them, AXn / YtAn of the same dtype, A, Xd,
+ * Yd as gn_sketch takes them.  The core of the new state is gn_core's on YtAn
+ * and [X, Xd].  ws: gn_workspace_size(m, n, dr, dl, ...) bytes. */
+gn_status gn_resample(gn_handle h, const gn_mat* A, const gn_mat* Xd, const gn_mat* Yd, const gn_mat* AX,
+                      const gn_mat* YtA, gn_mat* AXn, gn_mat* YtAn, void* ws, size_t ws_bytes);
+
+/* Appended data (Section 6).  Rows [A; B], B (mb x n) with a new sketch block
+ * Yb (mb x (r + l)): AXn ((m + mb) x r) = [AX; B X], Y^T A += Yb^T B (in place).
+ * Columns [A, B], B (m x nb) with a new sketch block Xb (nb x r): AX += B Xb
+ * (in place), YtAn ((r + l) x (n + nb)) = [Y^T A, Y^T B].  Operands as for
+ * gn_update; ws: gn_update_workspace_size for B's shape. */
+gn_status gn_append_rows(gn_handle h, const gn_mat* B, const gn_mat* X, const gn_mat* Yb, const gn_mat* AX,
+                         gn_mat* YtA, gn_mat* AXn, void* ws, size_t ws_bytes);
+gn_status gn_append_cols(gn_handle h, const gn_mat* B, const gn_mat* Xb, const gn_mat* Y, gn_mat* AX,
+                         const gn_mat* YtA, gn_mat* YtAn, void* ws, size_t ws_bytes);
+
 /* Sketch + core + factors in one call (Algorithm 2).  AX, YtA are outputs
  * (GN_F64 for FP64 operands, GN_F32 for the tensor-core path). */
 gn_status gn_approx(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,

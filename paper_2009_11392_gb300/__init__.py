@@ -39,7 +39,8 @@ ABI_SYMBOLS = (
     "gn_kernel_launches", "gn_error_fro2_noalloc", "gn_backward_workspace_size", "gn_backward",
     "gn_forward_dense", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
     "gn_batched_set_policy", "gn_batched_tune", "gn_set_fp64_tc", "gn_dgemm_tc_workspace_size", "gn_dgemm_tc",
-    "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update",
+    "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update", "gn_resample",
+    "gn_append_rows", "gn_append_cols",
 )
 
 
@@ -114,6 +115,9 @@ def _load():
         "gn_apply": ([P, M, M, C, M, M, I32, P, SZ], I32),
         "gn_update_workspace_size": ([I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
         "gn_update": ([P, M, M, M, M, M, P, SZ], I32),
+        "gn_resample": ([P, M, M, M, M, M, M, M, P, SZ], I32),
+        "gn_append_rows": ([P, M, M, M, M, M, M, P, SZ], I32),
+        "gn_append_cols": ([P, M, M, M, M, M, M, P, SZ], I32),
         "gn_dgemm_tc_workspace_size": ([I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
         "gn_dgemm_tc": ([P, I64, I64, I64, D, P, I32, I64, I32, P, I64, I32, D, P, I64, P, SZ], I32),
         "gn_batched_tune": ([P, I32, ctypes.POINTER(GnProblem), P, SZ, D, I32, ctypes.POINTER(I32),
@@ -395,6 +399,43 @@ class Handle:
         _check(lib.gn_update(self._h, ctypes.byref(mat(E, E_lo)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
                              ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.c_void_p(ws.data_ptr()),
                              ws.numel()), "gn_update")
+
+    def _scratch(self, nbytes, device):
+        with torch.cuda.stream(self.stream):   # freed in order with the handle's stream
+            return torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+
+    def resample(self, A, Xd, Yd, AX, YtA, AXn, YtAn):
+        """Rank r -> r + dr: AXn = [AX, A Xd], YtAn = [Y^T A; Yd^T A]."""
+        m, n = mat(A).rows, mat(A).cols
+        dr, drl = mat(Xd).cols, mat(Yd).cols
+        b = ctypes.c_size_t()
+        _check(lib.gn_workspace_size(m, n, dr, drl - dr, mat(A).dtype, ctypes.byref(b)), "gn_workspace_size")
+        ws = self._scratch(b.value, AX.device)
+        _check(lib.gn_resample(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(Xd)), ctypes.byref(mat(Yd)),
+                               ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.byref(mat(AXn)),
+                               ctypes.byref(mat(YtAn)), ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_resample")
+
+    def append_rows(self, B, X, Yb, AX, YtA, AXn):
+        """[A; B]: AXn = [AX; B X], Y^T A += Yb^T B."""
+        mb, n, r, rl = mat(B).rows, mat(B).cols, mat(X).cols, mat(Yb).cols
+        b = ctypes.c_size_t()
+        _check(lib.gn_update_workspace_size(mb, n, r, rl - r, mat(B).dtype, ctypes.byref(b)),
+               "gn_update_workspace_size")
+        ws = self._scratch(b.value, AX.device)
+        _check(lib.gn_append_rows(self._h, ctypes.byref(mat(B)), ctypes.byref(mat(X)), ctypes.byref(mat(Yb)),
+                                  ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.byref(mat(AXn)),
+                                  ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_append_rows")
+
+    def append_cols(self, B, Xb, Y, AX, YtA, YtAn):
+        """[A, B]: AX += B Xb, YtAn = [Y^T A, Y^T B]."""
+        m, nb, r, rl = mat(B).rows, mat(B).cols, mat(Xb).cols, mat(Y).cols
+        b = ctypes.c_size_t()
+        _check(lib.gn_update_workspace_size(m, nb, r, rl - r, mat(B).dtype, ctypes.byref(b)),
+               "gn_update_workspace_size")
+        ws = self._scratch(b.value, AX.device)
+        _check(lib.gn_append_cols(self._h, ctypes.byref(mat(B)), ctypes.byref(mat(Xb)), ctypes.byref(mat(Y)),
+                                  ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.byref(mat(YtAn)),
+                                  ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_append_cols")
 
     def approx(self, A, X, Y, eps, mode, AX, YtA, core: Core, F, G, ws, A_lo=None) -> Core:
         c = core.cstruct()

@@ -832,6 +832,84 @@ gn_status gn_update(gn_handle h, const gn_mat* E, const gn_mat* X, const gn_mat*
     return GN_OK;
 }
 
+// Copy rows x cols elements of a sketch matrix (FP32 or FP64) between two
+// strided buffers on the handle's stream.
+static gn_status copy_block(gn_handle h, void* dst, long long ldd, const void* src, long long lds, long long rows,
+                     long long cols, size_t es) {
+    GN_CUDA_TRY(cudaMemcpy2DAsync(dst, es * ldd, src, es * lds, es * cols, rows, cudaMemcpyDeviceToDevice,
+                                  h->stream));
+    return GN_OK;
+}
+
+static size_t sketch_es(const gn_mat* a) { return a->dtype == GN_F64 ? sizeof(double) : sizeof(float); }
+
+gn_status gn_resample(gn_handle h, const gn_mat* A, const gn_mat* Xd, const gn_mat* Yd, const gn_mat* AX,
+                      const gn_mat* YtA, gn_mat* AXn, gn_mat* YtAn, void* ws, size_t ws_bytes) {
+    if (!h || !A || !Xd || !Yd || !AX || !YtA || !AXn || !YtAn) return GN_ERR_INVALID_ARG;
+    const long long m = A->rows, n = A->cols, r = AX->cols, rl = YtA->rows, dr = Xd->cols, drl = Yd->cols;
+    if (dr < 1 || drl <= dr) return GN_ERR_SHAPE;
+    GN_TRY(check_mat(AX, m, r));
+    GN_TRY(check_mat(YtA, rl, n));
+    GN_TRY(check_mat(AXn, m, r + dr));
+    GN_TRY(check_mat(YtAn, rl + drl, n));
+    if (AXn->dtype != AX->dtype || YtAn->dtype != YtA->dtype || AX->dtype != YtA->dtype) return GN_ERR_DTYPE;
+    const size_t es = sketch_es(AX);
+    GN_TRY(copy_block(h, AXn->data, AXn->ld, AX->data, AX->ld, m, r, es));
+    GN_TRY(copy_block(h, YtAn->data, YtAn->ld, YtA->data, YtA->ld, rl, n, es));
+    gn_mat ax = *AXn, yta = *YtAn;   // the new columns / rows, written in place by the sketch
+    ax.data = static_cast<char*>(AXn->data) + es * r;
+    ax.cols = dr;
+    yta.data = static_cast<char*>(YtAn->data) + es * rl * YtAn->ld;
+    yta.rows = drl;
+    return gn_sketch(h, A, Xd, Yd, &ax, &yta, ws, ws_bytes);
+}
+
+gn_status gn_append_rows(gn_handle h, const gn_mat* B, const gn_mat* X, const gn_mat* Yb, const gn_mat* AX,
+                         gn_mat* YtA, gn_mat* AXn, void* ws, size_t ws_bytes) {
+    if (!h || !B || !X || !Yb || !AX || !YtA || !AXn || !ws) return GN_ERR_INVALID_ARG;
+    const long long mb = B->rows, n = B->cols, r = X->cols, rl = Yb->cols, m = AX->rows;
+    GN_TRY(check_mat(AX, m, r));
+    GN_TRY(check_mat(YtA, rl, n));
+    GN_TRY(check_mat(AXn, m + mb, r));
+    if (AXn->dtype != AX->dtype || YtA->dtype != AX->dtype) return GN_ERR_DTYPE;
+    const size_t es = sketch_es(AX);
+    const size_t scratch = update_scratch(mb, n, r, rl - r, B->dtype);
+    if (ws_bytes <= scratch) return GN_ERR_WORKSPACE;
+    GN_TRY(copy_block(h, AXn->data, AXn->ld, AX->data, AX->ld, m, r, es));
+    gn_mat bx = *AXn, dyta = *YtA;   // B X straight into the new rows; Yb^T B into scratch
+    bx.data = static_cast<char*>(AXn->data) + es * m * AXn->ld;
+    bx.rows = mb;
+    const long long ldy = round8(n);
+    dyta.data = ws;
+    dyta.ld = ldy;
+    if (align256(es * rl * ldy) > scratch) return GN_ERR_WORKSPACE;
+    GN_TRY(gn_sketch(h, B, X, Yb, &bx, &dyta, static_cast<char*>(ws) + scratch, ws_bytes - scratch));
+    return add_into(h, YtA, dyta.data, ldy);
+}
+
+gn_status gn_append_cols(gn_handle h, const gn_mat* B, const gn_mat* Xb, const gn_mat* Y, gn_mat* AX,
+                         const gn_mat* YtA, gn_mat* YtAn, void* ws, size_t ws_bytes) {
+    if (!h || !B || !Xb || !Y || !AX || !YtA || !YtAn || !ws) return GN_ERR_INVALID_ARG;
+    const long long m = B->rows, nb = B->cols, r = Xb->cols, rl = Y->cols, n = YtA->cols;
+    GN_TRY(check_mat(AX, m, r));
+    GN_TRY(check_mat(YtA, rl, n));
+    GN_TRY(check_mat(YtAn, rl, n + nb));
+    if (YtAn->dtype != YtA->dtype || YtA->dtype != AX->dtype) return GN_ERR_DTYPE;
+    const size_t es = sketch_es(AX);
+    const size_t scratch = update_scratch(m, nb, r, rl - r, B->dtype);
+    if (ws_bytes <= scratch) return GN_ERR_WORKSPACE;
+    GN_TRY(copy_block(h, YtAn->data, YtAn->ld, YtA->data, YtA->ld, rl, n, es));
+    gn_mat dax = *AX, ytb = *YtAn;   // B Xb into scratch; Y^T B straight into the new columns
+    const long long ldx = round8(r);
+    dax.data = ws;
+    dax.ld = ldx;
+    ytb.data = static_cast<char*>(YtAn->data) + es * n;
+    ytb.cols = nb;
+    if (align256(es * m * ldx) > scratch) return GN_ERR_WORKSPACE;
+    GN_TRY(gn_sketch(h, B, Xb, Y, &dax, &ytb, static_cast<char*>(ws) + scratch, ws_bytes - scratch));
+    return add_into(h, AX, dax.data, ldx);
+}
+
 // Scratch of gn_apply: two FP64 blocks of at most max(r + l, r) x kw, the
 // triangular solve's and the GEMMs' split-K partials.
 size_t apply_ws(long long m, long long n, long long r, long long l, long long kw, int sms) {

@@ -70,3 +70,61 @@ def test_update_fp64_against_oracle(gn, H):
     AXn, YtAn, _, _ = O.update(*O.sketch(A, X, Y), X, Y, E)
     assert np.linalg.norm(npy(AX) - AXn) <= 1e-13 * np.linalg.norm(AXn)
     assert np.linalg.norm(npy(YtA) - YtAn) <= 1e-13 * np.linalg.norm(YtAn)
+
+
+def _ints(g, a, b):
+    return torch.randint(-3, 4, (a, b), generator=g).double()
+
+
+def test_resample_bf16_exact_on_integer_inputs(gn, H):
+    """Rank r -> r + dr (Section 6): the old sketches copied, A Xd and Yd^T A
+    written in place; equal to the sketches with [X, Xd], [Y, Yd] bit for bit."""
+    m, n, r, l, dr, dl = 500, 420, 40, 20, 12, 6
+    g = torch.Generator().manual_seed(11)
+    A, X, Y, Xd, Yd = _ints(g, m, n), _ints(g, n, r), _ints(g, m, r + l), _ints(g, n, dr), _ints(g, m, dr + dl)
+    Ab, Xb, Yb, Xdb, Ydb = (H.quantize(t.cuda()) for t in (A, X, Y, Xd, Yd))
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    AXn = torch.full((m, r + dr), float("nan"), dtype=torch.float32, device="cuda")
+    YtAn = torch.full((r + l + dr + dl, n), float("nan"), dtype=torch.float32, device="cuda")
+    H.resample(Ab, Xdb, Ydb, AX, YtA, AXn, YtAn)
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch(A.numpy(), torch.cat([X, Xd], 1).numpy(), torch.cat([Y, Yd], 1).numpy())
+    assert np.array_equal(npy(AXn), oAX)
+    assert np.array_equal(npy(YtAn), oYtA)
+
+
+def test_append_rows_and_cols_bf16_exact_on_integer_inputs(gn, H):
+    """[A; B] and [A, B] (Section 6): the updated sketches equal the sketches of
+    the enlarged matrix with the enlarged sketch matrix, bit for bit."""
+    m, n, r, l, mb, nb = 460, 380, 36, 18, 70, 54
+    g = torch.Generator().manual_seed(12)
+    A, X, Y = _ints(g, m, n), _ints(g, n, r), _ints(g, m, r + l)
+    Br, Yr = _ints(g, mb, n), _ints(g, mb, r + l)
+    Bc, Xc = _ints(g, m, nb), _ints(g, nb, r)
+    Ab, Xb, Yb, Brb, Yrb, Bcb, Xcb = (H.quantize(t.cuda()) for t in (A, X, Y, Br, Yr, Bc, Xc))
+    ws = H.workspace(m, n, r, l, gn.BF16)
+
+    def fresh():
+        AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+        YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+        H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+        return AX, YtA
+
+    AX, YtA = fresh()
+    AXn = torch.full((m + mb, r), float("nan"), dtype=torch.float32, device="cuda")
+    H.append_rows(Brb, Xb, Yrb, AX, YtA, AXn)
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch(torch.cat([A, Br], 0).numpy(), X.numpy(), torch.cat([Y, Yr], 0).numpy())
+    assert np.array_equal(npy(AXn), oAX)
+    assert np.array_equal(npy(YtA), oYtA)
+
+    AX, YtA = fresh()
+    YtAn = torch.full((r + l, n + nb), float("nan"), dtype=torch.float32, device="cuda")
+    H.append_cols(Bcb, Xcb, Yb, AX, YtA, YtAn)
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch(torch.cat([A, Bc], 1).numpy(), torch.cat([X, Xc], 0).numpy(), Y.numpy())
+    assert np.array_equal(npy(AX), oAX)
+    assert np.array_equal(npy(YtAn), oYtA)
