@@ -116,3 +116,11 @@ def test_apply_and_update_host_validation():
     assert L.gn_update_workspace_size(1000, 500, 20, 10, gn.F32, ctypes.byref(b)) == 3  # no F32 operand path
     assert L.gn_update_workspace_size(1000, 500, 0, 10, gn.BF16, ctypes.byref(b)) == 2  # r < 1
     assert L.gn_update(None, None, None, None, None, None, None, 0) == 1
+
+
+def test_sketch_state_calls_reject_null_arguments():
+    import paper_2009_11392_gb300 as gn
+    L = gn.lib
+    assert L.gn_resample(None, None, None, None, None, None, None, None, None, 0) == 1
+    assert L.gn_append_rows(None, None, None, None, None, None, None, None, 0) == 1
+    assert L.gn_append_cols(None, None, None, None, None, None, None, None, 0) == 1
