@@ -265,17 +265,26 @@ gn_status gn_apply(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_co
  * way: GN_F64, GN_BF16, GN_BF16X2 or GN_E4M3, with the same X, Y) into scratch
  * and added elementwise into AX and YtA (as gn_sketch wrote them).  The core
  * of the updated sketches is then gn_core's.  ws (device) of at least
- * gn_update_workspace_size bytes; asynchronous on the handle's stream. */
+ * gn_update_workspace_size(m, n, r, l, dtype of E) bytes, which needs only
+ * m, n, r >= 1 and l >= 0 (the same sizing serves gn_append_rows /
+ * gn_append_cols for a block B of any size, one row or column included);
+ * asynchronous on the handle's stream. */
 gn_status gn_update_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t op_dtype, size_t* bytes);
 gn_status gn_update(gn_handle h, const gn_mat* E, const gn_mat* X, const gn_mat* Y, gn_mat* AX, gn_mat* YtA,
                     void* ws, size_t ws_bytes);
 
 /* Resampling r -> r + dr (Section 6): AXn (m x (r + dr)) = [AX, A Xd] and
  * YtAn ((r + l + dr + dl) x n) = [Y^T A; Yd^T A] from the old sketches (copied)
- * and the sketch of A by the new blocks Xd (n x dr), Yd (m x (dr + dl), dl >= 1)
- * alone; AX, YtA as gn_sketch wrote them, AXn / YtAn of the same dtype, A, Xd,
- * Yd as gn_sketch takes them.  The core of the new state is gn_core's on YtAn
- * and [X, Xd].  ws: gn_workspace_size(m, n, dr, dl, ...) bytes. */
+ * and the sketch of A by the new blocks Xd (n x dr), Yd (m x (dr + dl)) alone,
+ * with dr >= 0, dl >= 0 and dr + dl >= 1: dl = 0 raises r keeping l, dr = 0
+ * raises l alone (Xd then has no columns and neither it nor AXn's new part is
+ * read).  AX, YtA as gn_sketch wrote them, AXn / YtAn of the same dtype, A,
+ * Xd, Yd as gn_sketch takes them.  The core of the new state is gn_core's on
+ * YtAn and [X, Xd].  ws (device, not NULL) of at least
+ * gn_resample_workspace_size(m, n, dr, dl, dtype of A) bytes; GN_ERR_SHAPE for
+ * dr < 0, dl < 0 or dr + dl = 0. */
+gn_status gn_resample_workspace_size(int64_t m, int64_t n, int64_t dr, int64_t dl, int32_t op_dtype,
+                                     size_t* bytes);
 gn_status gn_resample(gn_handle h, const gn_mat* A, const gn_mat* Xd, const gn_mat* Yd, const gn_mat* AX,
                       const gn_mat* YtA, gn_mat* AXn, gn_mat* YtAn, void* ws, size_t ws_bytes);
 

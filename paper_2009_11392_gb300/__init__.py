@@ -40,7 +40,7 @@ ABI_SYMBOLS = (
     "gn_forward_dense", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
     "gn_batched_set_policy", "gn_batched_tune", "gn_set_fp64_tc", "gn_dgemm_tc_workspace_size", "gn_dgemm_tc",
     "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update", "gn_resample",
-    "gn_append_rows", "gn_append_cols",
+    "gn_append_rows", "gn_append_cols", "gn_resample_workspace_size",
 )
 
 
@@ -75,7 +75,7 @@ def lib_path() -> str:
 
 def _load():
     path = _build.LIB
-    if not os.path.exists(path):
+    if not os.path.exists(path) or _build.stale():
         if os.environ.get("GN_AUTOBUILD", "1") == "1":
             _build.build()
         if not os.path.exists(path):
@@ -116,6 +116,7 @@ def _load():
         "gn_update_workspace_size": ([I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
         "gn_update": ([P, M, M, M, M, M, P, SZ], I32),
         "gn_resample": ([P, M, M, M, M, M, M, M, P, SZ], I32),
+        "gn_resample_workspace_size": ([I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
         "gn_append_rows": ([P, M, M, M, M, M, M, P, SZ], I32),
         "gn_append_cols": ([P, M, M, M, M, M, M, P, SZ], I32),
         "gn_dgemm_tc_workspace_size": ([I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
@@ -208,6 +209,18 @@ class E4M3Mat:
         else:
             v = self.data_t.view(torch.float8_e4m3fn).to(torch.float64).t()
         return v * sc
+
+
+def _cols(t) -> int:
+    return t.cols if isinstance(t, E4M3Mat) else int(t.shape[1])
+
+
+def _mat_or_empty(t, rows: int) -> GnMat:
+    """gn_mat of ``t``, or for a tensor with no columns a descriptor with the
+    right row count that the library does not read."""
+    if not isinstance(t, E4M3Mat) and t.dim() == 2 and t.shape[1] == 0:
+        return GnMat(0, 0, rows, 0, 0, _TORCH_DT.get(t.dtype, F32))
+    return mat(t)
 
 
 def padded(rows: int, cols: int, dtype, device) -> torch.Tensor:
@@ -404,16 +417,20 @@ class Handle:
         with torch.cuda.stream(self.stream):   # freed in order with the handle's stream
             return torch.empty(int(nbytes), dtype=torch.uint8, device=device)
 
-    def resample(self, A, Xd, Yd, AX, YtA, AXn, YtAn):
-        """Rank r -> r + dr: AXn = [AX, A Xd], YtAn = [Y^T A; Yd^T A]."""
-        m, n = mat(A).rows, mat(A).cols
-        dr, drl = mat(Xd).cols, mat(Yd).cols
+    def resample(self, A, Xd, Yd, AX, YtA, AXn, YtAn, A_lo=None):
+        """Rank r -> r + dr, oversampling l -> l + dl: AXn = [AX, A Xd],
+        YtAn = [Y^T A; Yd^T A] (Xd: n x dr, Yd: m x (dr + dl); dr or dl may be 0)."""
+        Am = mat(A, A_lo)
+        m, n = Am.rows, Am.cols
+        dr, drl = _cols(Xd), _cols(Yd)
         b = ctypes.c_size_t()
-        _check(lib.gn_workspace_size(m, n, dr, drl - dr, mat(A).dtype, ctypes.byref(b)), "gn_workspace_size")
-        ws = self._scratch(b.value, AX.device)
-        _check(lib.gn_resample(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(Xd)), ctypes.byref(mat(Yd)),
-                               ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.byref(mat(AXn)),
-                               ctypes.byref(mat(YtAn)), ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_resample")
+        _check(lib.gn_resample_workspace_size(m, n, dr, drl - dr, Am.dtype, ctypes.byref(b)),
+               "gn_resample_workspace_size")
+        ws = self._scratch(max(256, b.value), AX.device)
+        _check(lib.gn_resample(self._h, ctypes.byref(Am), ctypes.byref(_mat_or_empty(Xd, n)),
+                               ctypes.byref(mat(Yd)), ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)),
+                               ctypes.byref(_mat_or_empty(AXn, m)), ctypes.byref(mat(YtAn)),
+                               ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_resample")
 
     def append_rows(self, B, X, Yb, AX, YtA, AXn):
         """[A; B]: AXn = [AX; B X], Y^T A += Yb^T B."""

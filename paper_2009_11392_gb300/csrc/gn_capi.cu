@@ -164,15 +164,15 @@ gn_status launch_sketch_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const 
         GN_TRY(tc_make_map_bf16(&p.maps[mLmn], A->lo, m, n, A->ld, 64, 64));
     }
     const int mX = nm++, mY = nm++;
-    GN_TRY(tc_make_map_bf16(&p.maps[mX], X->data, n, r, X->ld, 64, 64));
-    GN_TRY(tc_make_map_bf16(&p.maps[mY], Y->data, m, rl, Y->ld, 64, 64));
+    if (r > 0) GN_TRY(tc_make_map_bf16(&p.maps[mX], X->data, n, r, X->ld, 64, 64));
+    if (rl > 0) GN_TRY(tc_make_map_bf16(&p.maps[mY], Y->data, m, rl, Y->ld, 64, 64));
 
     // GEMM 0: AX (m x r) = A (K-major) . X (MN-major), K = n
     TcGemm& g0 = p.g[0];
     g0.M = static_cast<int>(m);
     g0.N = static_cast<int>(r);
     g0.K = static_cast<int>(n);
-    g0.bn = static_cast<int>(std::min<long long>(256, (r + 63) / 64 * 64));
+    g0.bn = static_cast<int>(std::min<long long>(256, std::max<long long>(64, (r + 63) / 64 * 64)));
     g0.a_mn = 0;
     g0.b_mn = 1;
     g0.nsrc = nsrc;
@@ -205,6 +205,12 @@ gn_status launch_sketch_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const 
     }
     g1.D = static_cast<float*>(YtA->data);
     g1.ldd = YtA->ld;
+    if (r == 0 || rl == 0) {   // a block sketch that needs one product only
+        if (r == 0) p.g[0] = p.g[1];
+        p.g[0].ksplit = 0;
+        p.ngemm = 1;
+        return tc_launch(h, &p);
+    }
     // Order: the longer-K GEMM first (its tiles are the expensive ones).
     if (m >= n) {
         TcGemm t = p.g[0];
@@ -228,14 +234,18 @@ gn_status launch_sketch_e4m3(gn_handle h, const gn_mat* A, const gn_mat* X, cons
     uint8_t* imY = cv.take<uint8_t>(512 * tY);
     if (!cv.ok) return GN_ERR_WORKSPACE;
     GN_TRY(e4m3_sf_image(h, A->scale, tA, imA));
-    GN_TRY(e4m3_sf_image(h, X->scale, tX, imX));
-    GN_TRY(e4m3_sf_image(h, Y->scale, tY, imY));
+    if (r > 0) GN_TRY(e4m3_sf_image(h, X->scale, tX, imX));
+    if (rl > 0) GN_TRY(e4m3_sf_image(h, Y->scale, tY, imY));
     TcParams p;
     memset(&p, 0, sizeof(p));
-    GN_TRY(tc_make_map_e4m3(&p.maps[0], A->data, m, n, A->ld, 128));
-    GN_TRY(tc_make_map_e4m3(&p.maps[1], X->data_t, r, n, X->ld_t, 128));
-    GN_TRY(tc_make_map_e4m3(&p.maps[2], Y->data_t, rl, m, Y->ld_t, 128));
-    GN_TRY(tc_make_map_e4m3(&p.maps[3], A->data_t, n, m, A->ld_t, 128));
+    if (r > 0) {
+        GN_TRY(tc_make_map_e4m3(&p.maps[0], A->data, m, n, A->ld, 128));
+        GN_TRY(tc_make_map_e4m3(&p.maps[1], X->data_t, r, n, X->ld_t, 128));
+    }
+    if (rl > 0) {
+        GN_TRY(tc_make_map_e4m3(&p.maps[2], Y->data_t, rl, m, Y->ld_t, 128));
+        GN_TRY(tc_make_map_e4m3(&p.maps[3], A->data_t, n, m, A->ld_t, 128));
+    }
     TcGemm& g0 = p.g[0];
     g0.M = static_cast<int>(m);
     g0.N = static_cast<int>(r);
@@ -272,6 +282,12 @@ gn_status launch_sketch_e4m3(gn_handle h, const gn_mat* A, const gn_mat* X, cons
     g1.sfb_ld = static_cast<int>(tiles128(n));
     g1.sfb_tr = 1;
     g1.sfb_rows = static_cast<int>(tiles128(n));
+    if (r == 0 || rl == 0) {   // a block sketch that needs one product only
+        if (r == 0) p.g[0] = p.g[1];
+        p.ngemm = 1;
+        p.f8 = 1;
+        return tc_launch(h, &p);
+    }
     if (m >= n) {   // the longer-K GEMM first
         TcGemm t = p.g[0];
         p.g[0] = p.g[1];
@@ -313,6 +329,76 @@ gn_status add_into(gn_handle h, gn_mat* dst, const void* src, long long lds) {
 size_t update_scratch(long long m, long long n, long long r, long long l, int op_dtype) {
     const size_t es = op_dtype == GN_F64 ? sizeof(double) : sizeof(float);
     return align256(es * m * round8(r)) + align256(es * (r + l) * round8(n)) + 512;
+}
+
+// Scratch of sketch_block for an m x n block with rx = X's and ry = Y's columns.
+size_t block_sketch_ws(long long m, long long n, long long rx, long long ry, int op_dtype, int sms) {
+    if (op_dtype == GN_E4M3) return sketch_e4m3_ws(m, n, rx, ry - rx);
+    if (op_dtype == GN_F64) return std::max(dgemm_ws_bytes(m, rx, n, sms), dgemm_ws_bytes(ry, n, m, sms)) + 1024;
+    return 1024;
+}
+
+// The sketch products A X (m x rx) and Y^T A (ry x n) of any block A (m, n >= 1);
+// either product may be absent (rx == 0 or ry == 0: that operand and its output
+// are not read).  gn_sketch adds GN's own size rules on top (r <= min(m, n),
+// l >= 1); the sketch-state calls of Section 6 sketch blocks of any size.
+gn_status sketch_block(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* AX, gn_mat* YtA,
+                       void* ws, size_t ws_bytes) {
+    if (!h || !A || !X || !Y || !AX || !YtA) return GN_ERR_INVALID_ARG;
+    const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols;
+    if (m < 1 || n < 1 || r < 0 || rl < 0 || r + rl < 1) return GN_ERR_SHAPE;
+    if (m > (1LL << 31) - 1 || n > (1LL << 31) - 1 || r > (1LL << 31) - 1 || rl > (1LL << 31) - 1)
+        return GN_ERR_SHAPE;
+    if (X->rows != n || Y->rows != m) return GN_ERR_SHAPE;
+    if (A->dtype == GN_E4M3) {
+        GN_TRY(check_e4m3(A, m, n, r > 0, rl > 0));
+        if (r > 0) {
+            GN_TRY(check_e4m3(X, n, r, false, true));
+            GN_TRY(check_mat(AX, m, r));
+            if (AX->dtype != GN_F32) return GN_ERR_DTYPE;
+        }
+        if (rl > 0) {
+            GN_TRY(check_e4m3(Y, m, rl, false, true));
+            GN_TRY(check_mat(YtA, rl, n));
+            if (YtA->dtype != GN_F32) return GN_ERR_DTYPE;
+        }
+        if (!ws || ws_bytes < sketch_e4m3_ws(m, n, r, rl - r)) return GN_ERR_WORKSPACE;
+        return launch_sketch_e4m3(h, A, X, Y, AX, YtA, ws, ws_bytes);
+    }
+    GN_TRY(check_mat(A, m, n));
+    if (r > 0) {
+        GN_TRY(check_mat(X, n, r));
+        GN_TRY(check_mat(AX, m, r));
+    }
+    if (rl > 0) {
+        GN_TRY(check_mat(Y, m, rl));
+        GN_TRY(check_mat(YtA, rl, n));
+    }
+    if (A->dtype == GN_F64) {
+        if ((r > 0 && (X->dtype != GN_F64 || AX->dtype != GN_F64)) ||
+            (rl > 0 && (Y->dtype != GN_F64 || YtA->dtype != GN_F64)))
+            return GN_ERR_DTYPE;
+        double* gws = static_cast<double*>(ws);
+        if (r > 0)
+            GN_TRY(dgemm(h, m, r, n, 1.0, static_cast<const double*>(A->data), A->ld, 0,
+                         static_cast<const double*>(X->data), X->ld, 0, 0.0, static_cast<double*>(AX->data),
+                         AX->ld, gws, ws_bytes));
+        if (rl > 0)
+            GN_TRY(dgemm(h, rl, n, m, 1.0, static_cast<const double*>(Y->data), Y->ld, 1,
+                         static_cast<const double*>(A->data), A->ld, 0, 0.0, static_cast<double*>(YtA->data),
+                         YtA->ld, gws, ws_bytes));
+        return GN_OK;
+    }
+    if (A->dtype == GN_BF16 || A->dtype == GN_BF16X2) {
+        if ((r > 0 && (X->dtype != GN_BF16 || AX->dtype != GN_F32)) ||
+            (rl > 0 && (Y->dtype != GN_BF16 || YtA->dtype != GN_F32)))
+            return GN_ERR_DTYPE;
+        GN_TRY(check_tma_operand(A));
+        if (r > 0) GN_TRY(check_tma_operand(X));
+        if (rl > 0) GN_TRY(check_tma_operand(Y));
+        return launch_sketch_tc(h, A, X, Y, AX, YtA);
+    }
+    return GN_ERR_DTYPE;
 }
 
 }  // namespace
@@ -496,46 +582,8 @@ gn_status gn_quantize(gn_handle h, const gn_mat* src, gn_mat* dst) {
 gn_status gn_sketch(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* AX,
                     gn_mat* YtA, void* ws, size_t ws_bytes) {
     if (!h || !A || !X || !Y || !AX || !YtA) return GN_ERR_INVALID_ARG;
-    const long long m = A->rows, n = A->cols, r = X->cols;
-    if (!Y) return GN_ERR_INVALID_ARG;
-    const long long l = Y->cols - r;
-    GN_TRY(check_sizes(m, n, r, l));
-    if (A->dtype == GN_E4M3) {
-        GN_TRY(check_e4m3(A, m, n, true, true));
-        GN_TRY(check_e4m3(X, n, r, false, true));
-        GN_TRY(check_e4m3(Y, m, r + l, false, true));
-        GN_TRY(check_mat(AX, m, r));
-        GN_TRY(check_mat(YtA, r + l, n));
-        if (AX->dtype != GN_F32 || YtA->dtype != GN_F32) return GN_ERR_DTYPE;
-        if (!ws || ws_bytes < sketch_e4m3_ws(m, n, r, l)) return GN_ERR_WORKSPACE;
-        return launch_sketch_e4m3(h, A, X, Y, AX, YtA, ws, ws_bytes);
-    }
-    GN_TRY(check_mat(A, m, n));
-    GN_TRY(check_mat(X, n, r));
-    GN_TRY(check_mat(Y, m, r + l));
-    GN_TRY(check_mat(AX, m, r));
-    GN_TRY(check_mat(YtA, r + l, n));
-    if (A->dtype == GN_F64) {
-        if (X->dtype != GN_F64 || Y->dtype != GN_F64 || AX->dtype != GN_F64 || YtA->dtype != GN_F64)
-            return GN_ERR_DTYPE;
-        double* gws = static_cast<double*>(ws);
-        GN_TRY(dgemm(h, m, r, n, 1.0, static_cast<const double*>(A->data), A->ld, 0,
-                     static_cast<const double*>(X->data), X->ld, 0, 0.0, static_cast<double*>(AX->data),
-                     AX->ld, gws, ws_bytes));
-        GN_TRY(dgemm(h, r + l, n, m, 1.0, static_cast<const double*>(Y->data), Y->ld, 1,
-                     static_cast<const double*>(A->data), A->ld, 0, 0.0, static_cast<double*>(YtA->data),
-                     YtA->ld, gws, ws_bytes));
-        return GN_OK;
-    }
-    if (A->dtype == GN_BF16 || A->dtype == GN_BF16X2) {
-        if (X->dtype != GN_BF16 || Y->dtype != GN_BF16 || AX->dtype != GN_F32 || YtA->dtype != GN_F32)
-            return GN_ERR_DTYPE;
-        GN_TRY(check_tma_operand(A));
-        GN_TRY(check_tma_operand(X));
-        GN_TRY(check_tma_operand(Y));
-        return launch_sketch_tc(h, A, X, Y, AX, YtA);
-    }
-    return GN_ERR_DTYPE;
+    GN_TRY(check_sizes(A->rows, A->cols, X->cols, Y->cols - X->cols));
+    return sketch_block(h, A, X, Y, AX, YtA, ws, ws_bytes);
 }
 
 gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, int32_t mode,
@@ -800,9 +848,23 @@ gn_status gn_error_fro2(gn_handle h, const gn_mat* A, const gn_mat* F, const gn_
 
 gn_status gn_update_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t op_dtype, size_t* bytes) {
     if (!bytes) return GN_ERR_INVALID_ARG;
-    size_t b = 0;
-    GN_TRY(gn_workspace_size(m, n, r, l, op_dtype, &b));
-    *bytes = b + update_scratch(m, n, r, l, op_dtype);
+    if (m < 1 || n < 1 || r < 1 || l < 0) return GN_ERR_SHAPE;
+    if (op_dtype != GN_F64 && op_dtype != GN_BF16 && op_dtype != GN_BF16X2 && op_dtype != GN_E4M3)
+        return GN_ERR_DTYPE;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *bytes = update_scratch(m, n, r, l, op_dtype) + block_sketch_ws(m, n, r, r + l, op_dtype, sms);
+    return GN_OK;
+}
+
+gn_status gn_resample_workspace_size(int64_t m, int64_t n, int64_t dr, int64_t dl, int32_t op_dtype, size_t* bytes) {
+    if (!bytes) return GN_ERR_INVALID_ARG;
+    if (m < 1 || n < 1 || dr < 0 || dl < 0 || dr + dl < 1) return GN_ERR_SHAPE;
+    if (op_dtype != GN_F64 && op_dtype != GN_BF16 && op_dtype != GN_BF16X2 && op_dtype != GN_E4M3)
+        return GN_ERR_DTYPE;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *bytes = block_sketch_ws(m, n, dr, dr + dl, op_dtype, sms);
     return GN_OK;
 }
 
@@ -826,7 +888,7 @@ gn_status gn_update(gn_handle h, const gn_mat* E, const gn_mat* X, const gn_mat*
     dYtA.data = base + align256(es * m * ldx);
     dYtA.ld = ldy;
     if (align256(es * m * ldx) + align256(es * rl * ldy) > scratch) return GN_ERR_WORKSPACE;
-    GN_TRY(gn_sketch(h, E, X, Y, &dAX, &dYtA, base + scratch, ws_bytes - scratch));
+    GN_TRY(sketch_block(h, E, X, Y, &dAX, &dYtA, base + scratch, ws_bytes - scratch));
     GN_TRY(add_into(h, AX, dAX.data, ldx));
     GN_TRY(add_into(h, YtA, dYtA.data, ldy));
     return GN_OK;
@@ -845,9 +907,10 @@ static size_t sketch_es(const gn_mat* a) { return a->dtype == GN_F64 ? sizeof(do
 
 gn_status gn_resample(gn_handle h, const gn_mat* A, const gn_mat* Xd, const gn_mat* Yd, const gn_mat* AX,
                       const gn_mat* YtA, gn_mat* AXn, gn_mat* YtAn, void* ws, size_t ws_bytes) {
-    if (!h || !A || !Xd || !Yd || !AX || !YtA || !AXn || !YtAn) return GN_ERR_INVALID_ARG;
+    if (!h || !A || !Xd || !Yd || !AX || !YtA || !AXn || !YtAn || !ws) return GN_ERR_INVALID_ARG;
     const long long m = A->rows, n = A->cols, r = AX->cols, rl = YtA->rows, dr = Xd->cols, drl = Yd->cols;
-    if (dr < 1 || drl <= dr) return GN_ERR_SHAPE;
+    // dr >= 0 new columns of X, dl = drl - dr >= 0 extra oversampling, dr + dl >= 1
+    if (dr < 0 || drl < dr || drl < 1) return GN_ERR_SHAPE;
     GN_TRY(check_mat(AX, m, r));
     GN_TRY(check_mat(YtA, rl, n));
     GN_TRY(check_mat(AXn, m, r + dr));
@@ -861,7 +924,7 @@ gn_status gn_resample(gn_handle h, const gn_mat* A, const gn_mat* Xd, const gn_m
     ax.cols = dr;
     yta.data = static_cast<char*>(YtAn->data) + es * rl * YtAn->ld;
     yta.rows = drl;
-    return gn_sketch(h, A, Xd, Yd, &ax, &yta, ws, ws_bytes);
+    return sketch_block(h, A, Xd, Yd, &ax, &yta, ws, ws_bytes);
 }
 
 gn_status gn_append_rows(gn_handle h, const gn_mat* B, const gn_mat* X, const gn_mat* Yb, const gn_mat* AX,
@@ -883,7 +946,7 @@ gn_status gn_append_rows(gn_handle h, const gn_mat* B, const gn_mat* X, const gn
     dyta.data = ws;
     dyta.ld = ldy;
     if (align256(es * rl * ldy) > scratch) return GN_ERR_WORKSPACE;
-    GN_TRY(gn_sketch(h, B, X, Yb, &bx, &dyta, static_cast<char*>(ws) + scratch, ws_bytes - scratch));
+    GN_TRY(sketch_block(h, B, X, Yb, &bx, &dyta, static_cast<char*>(ws) + scratch, ws_bytes - scratch));
     return add_into(h, YtA, dyta.data, ldy);
 }
 
@@ -906,7 +969,7 @@ gn_status gn_append_cols(gn_handle h, const gn_mat* B, const gn_mat* Xb, const g
     ytb.data = static_cast<char*>(YtAn->data) + es * n;
     ytb.cols = nb;
     if (align256(es * m * ldx) > scratch) return GN_ERR_WORKSPACE;
-    GN_TRY(gn_sketch(h, B, Xb, Y, &dax, &ytb, static_cast<char*>(ws) + scratch, ws_bytes - scratch));
+    GN_TRY(sketch_block(h, B, Xb, Y, &dax, &ytb, static_cast<char*>(ws) + scratch, ws_bytes - scratch));
     return add_into(h, AX, dax.data, ldx);
 }
 

@@ -4,7 +4,8 @@
 // to four independent GEMMs D_g = sum_s A_{g,s} B_{g,s} in a single launch:
 //
 //   warp 0      : TMA producer -- cp.async.bulk.tensor tiles of both operands
-//                 into a 4-stage shared-memory ring (128B swizzle), one
+//                 into a shared-memory ring (128B swizzle; 4 stages of 48 KB
+//                 for 128-row tiles, 3 of 64 KB for 256-row tiles), one
 //                 mbarrier with a transaction count per stage;
 //   warp 1      : tcgen05.mma issuer (one thread) -- 128 x bn x 16 BF16 MMAs
 //                 with FP32 accumulators in tensor memory, two accumulator
@@ -118,27 +119,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Multicast variant: the box lands at the same shared-memory offset in every CTA
-// of `mask` (cluster ranks) and completes bytes on each CTA's barrier at `bar`'s offset.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -149,16 +129,6 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-
-// Arrive (once the prior MMAs complete) on the barrier at `bar`'s offset in every
-// CTA of `mask`.
-__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            bar),
-        "h"(mask)
         : "memory");
 }
 
@@ -276,8 +246,8 @@ __device__ __forceinline__ const CUtensorMap* map_of(const TcParams& p, int i) {
     return GROUPED ? p.gmaps + i : p.maps + i;
 }
 
-template <bool GROUPED, int CL>
-__device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t, int crank) {
+template <bool GROUPED>
+__device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t) {
     // tiles_m / tiles_n / tile_base are in units of this launch's tile shape
     TileCoord c;
     c.half = 0;
@@ -301,7 +271,7 @@ __device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t, int c
     }
     const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
     const int local = t - G.tile_base;
-    const int ctm_n = (G.tiles_m + CL - 1) / CL;   // cluster tiles along M
+    const int ctm_n = G.tiles_m;
     int ctm;
     if (!GROUPED && G.ksplit == 2) {
         // the two K halves of a tile are separate items; the items that share an
@@ -324,7 +294,7 @@ __device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t, int c
         ctm = local / G.tiles_n;
         c.tn = local % G.tiles_n;
     }
-    c.tm = ctm * CL + crank;   // the CL CTAs of a cluster take consecutive M tiles of one N tile
+    c.tm = ctm;
     return c;
 }
 
@@ -333,11 +303,8 @@ __device__ void latch(int32_t* status, int code, int where, volatile int* abort_
     if (atomicCAS(&status[GN_DEV_STATUS], 0, code) == 0) status[GN_DEV_WHERE] = where;
 }
 
-// CL > 1: thread-block clusters of CL CTAs along M; the B tile (shared by the
-// CL M tiles of one N tile) is split into 64-column boxes, each loaded by one
-// CTA and multicast to all CL; a stage is refilled only after every CTA of the
-// cluster has consumed it (each MMA commit arrives on all CL empty barriers).
-template <bool GROUPED, int CL, int MT, bool F8>
+// Every CTA loads its own operand tiles; CTAs exchange nothing.
+template <bool GROUPED, int MT, bool F8>
 __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __grid_constant__ TcParams p) {
     using K = Cfg<MT, F8>;
     constexpr int KE = F8 ? 128 : BK;                     // K elements per stage (128 bytes per row)
@@ -365,7 +332,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full_bar(s), 1);
-            mbar_init(empty_bar(s), CL);
+            mbar_init(empty_bar(s), 1);
         }
         for (int a = 0; a < K::NACC; ++a) {
             mbar_init(tfull_bar(a), 1);
@@ -384,12 +351,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
     }
     tc_fence_before();
     __syncthreads();
-    if (CL > 1) cluster_sync_all();   // every CTA's barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int crank = CL > 1 ? static_cast<int>(cluster_rank()) : 0;
-    const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
-    const uint16_t cmask = static_cast<uint16_t>((1u << CL) - 1u);
+    const int cid = blockIdx.x, ncl = gridDim.x;
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
@@ -400,7 +364,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             uint32_t last_parity = 0;            // parity of the last armed phase per stage
             bool ok = true;
             for (int t = cid; t < p.total_tiles && ok; t += ncl) {
-                const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
+                const TileCoord c = decode_tile<GROUPED>(p, t);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
                 const int kb0 = c.half == 2 ? nkb / 2 : 0, kb1 = c.half == 1 ? nkb / 2 : nkb;
@@ -451,14 +415,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                                                       : static_cast<long long>(rb) * G.sfb_ld + kk;
                         bulk_load(sfs + stage * K::SF_STAGE + MT * 512, G.sfb + ti * 512, 512, fb);
                     }
-                    if (CL > 1) {   // B boxes: box j from cluster rank j % CL, multicast to all
-                        if (G.b_mn) {
-                            for (int j = crank; j < G.bn / 64; j += CL)
-                                tma_load_2d_mc(sb + 8192 * j, mb, fb, c.tn * G.bn + 64 * j, kk * BK, cmask);
-                        } else if (crank == 0) {
-                            tma_load_2d_mc(sb, mb, fb, kk * KE, c.tn * G.bn, cmask);
-                        }
-                    } else if (G.b_mn) {
+                    if (G.b_mn) {
                         for (int j = 0; j < G.bn / 64; ++j)
                             tma_load_2d(sb + 8192 * j, mb, fb, c.tn * G.bn + 64 * j, kk * BK);
                     } else {
@@ -488,7 +445,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             bool ok = true;
             bool issued_any = false;
             for (int t = cid; t < p.total_tiles && ok; t += ncl) {
-                const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
+                const TileCoord c = decode_tile<GROUPED>(p, t);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
                 const int kb0 = c.half == 2 ? nkb / 2 : 0, kb1 = c.half == 1 ? nkb / 2 : nkb;
@@ -541,7 +498,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                         }
                     }
                     issued_any = true;
-                    if (CL > 1) tc_commit_mc(empty_bar(stage), cmask); else tc_commit(empty_bar(stage));
+                    tc_commit(empty_bar(stage));
                     if (++stage == STAGES) {
                         stage = 0;
                         fphase ^= 1u;
@@ -568,7 +525,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
         int acc = 0;
         uint32_t aphase = 0;
         for (int t = cid; t < p.total_tiles; t += ncl) {
-            const TileCoord c = decode_tile<GROUPED, CL>(p, t, crank);
+            const TileCoord c = decode_tile<GROUPED>(p, t);
             const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
             const bool got = mbar_wait(tfull_bar(acc), aphase, limit, abort_flag);
             if (!__all_sync(0xffffffffu, got)) {   // warp-uniform exit: tcgen05.ld is .sync.aligned
@@ -625,7 +582,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
 
     tc_fence_before();
     __syncthreads();
-    if (CL > 1) cluster_sync_all();   // no CTA leaves while peers may still write its barriers
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -687,43 +643,23 @@ gn_status tc_make_map_e4m3(CUtensorMap* map, const void* base, long long rows, l
     return r == CUDA_SUCCESS ? GN_OK : GN_ERR_CUDA;
 }
 
-template <bool GROUPED, int CL, int MT, bool F8 = false>
-gn_status launch_cfg(gn_handle h, const TcParams& p, int total_ctiles) {
+template <bool GROUPED, int MT, bool F8 = false>
+gn_status launch_cfg(gn_handle h, const TcParams& p, int total_tiles) {
     static bool attr_set = false;
     if (!attr_set) {
-        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel<GROUPED, CL, MT, F8>,
+        GN_CUDA_TRY(cudaFuncSetAttribute(tc_multigemm_kernel<GROUPED, MT, F8>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MT, F8>::SMEM));
         attr_set = true;
     }
-    const int max_clusters = h->sm_count / CL;
-    const int clusters = total_ctiles < max_clusters ? total_ctiles : max_clusters;
-    if (CL == 1) {
-        tc_multigemm_kernel<GROUPED, CL, MT, F8><<<clusters, NUM_THREADS, Cfg<MT, F8>::SMEM, h->stream>>>(p);
-    } else {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(clusters * CL);
-        cfg.blockDim = dim3(NUM_THREADS);
-        cfg.dynamicSmemBytes = Cfg<MT, F8>::SMEM;
-        cfg.stream = h->stream;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = CL;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_multigemm_kernel<GROUPED, CL, MT, F8>, p));
-    }
+    const int ctas = total_tiles < h->sm_count ? total_tiles : h->sm_count;
+    tc_multigemm_kernel<GROUPED, MT, F8><<<ctas, NUM_THREADS, Cfg<MT, F8>::SMEM, h->stream>>>(p);
     count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     return GN_OK;
 }
 
 // Tile shape: 256-row tiles (two MMAs sharing each B stage) when every GEMM has
-// at least 256 rows, else 128-row tiles.  With 256-row tiles, pairs of CTAs
-// share the B stage by multicast (measured 4.5 % faster); 128-row tiles in
-// clusters of 4 were measured slower (the cluster's lockstep cost more than the
-// L2 traffic saved).
+// at least 256 rows and the launch keeps enough tiles, else 128-row tiles.
 int pick_mt(const TcGemm* g, int ngemm, int sm_count) {
     long long tiles2 = 0;   // work items with 256-row tiles (a K-split tile counts twice)
     for (int i = 0; i < ngemm; ++i) {
@@ -741,34 +677,28 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
             return GN_ERR_INVALID_ARG;
         GN_TRY(tc_prepare_gemm(&p->g[i], 0, MT, p->f8));
     }
-    // 256-row tiles run in CTA pairs (two consecutive M tiles of one N tile)
-    // that share each B stage by TMA multicast: 48 instead of 64 KB of L2
-    // traffic per SM and stage.
-    const int CL = (MT == 2 && !p->f8) ? 2 : 1;
     int total = 0;
     for (int i = 0; i < p->ngemm; ++i) {
         TcGemm& G = p->g[i];
         if (G.ksplit == 2 && (p->f8 || G.nsrc * G.kblocks < 8)) G.ksplit = 1;
         G.tile_base = total;
-        total += ((G.tiles_m + CL - 1) / CL) * G.tiles_n * (G.ksplit == 2 ? 2 : 1);
+        total += G.tiles_m * G.tiles_n * (G.ksplit == 2 ? 2 : 1);
         if (G.ksplit == 2)   // both halves add into D
             GN_CUDA_TRY(cudaMemset2DAsync(G.D, sizeof(float) * G.ldd, 0, sizeof(float) * G.N, G.M, h->stream));
     }
-    // Balance the last round: when the cluster tiles leave a partial round of R
-    // tiles (R <= half the clusters) that are whole rows of cluster tiles of the
-    // last GEMM with A K-major (a contiguous row range of its D), those R tiles
-    // run as 2R half-K items adding into D, zeroed first; the last round then
-    // costs half a tile.
+    // Balance the last round: when the tiles leave a partial round of R tiles
+    // (R <= half the CTAs) that are whole rows of tiles of the last GEMM with A
+    // K-major (a contiguous row range of its D), those R tiles run as 2R half-K
+    // items adding into D, zeroed first; the last round then costs half a tile.
     p->split_base = 0;
     p->nsplit = 0;
     if (!p->f8 && total > 0) {
-        const int ncl = std::min(total, h->sm_count / CL);
+        const int ncl = std::min(total, h->sm_count);
         const int R = total % ncl;
         const TcGemm& G = p->g[p->ngemm - 1];
         if (total > ncl && R > 0 && 2 * R <= ncl && !G.a_mn && G.ksplit != 2 && R % G.tiles_n == 0 &&
             G.nsrc * G.kblocks >= 8) {
-            const int ctm_n = (G.tiles_m + CL - 1) / CL;
-            const long long row0 = static_cast<long long>(ctm_n - R / G.tiles_n) * CL * BM * MT;
+            const long long row0 = static_cast<long long>(G.tiles_m - R / G.tiles_n) * BM * MT;
             if (row0 >= 0 && row0 < G.M) {
                 GN_CUDA_TRY(cudaMemset2DAsync(G.D + row0 * G.ldd, sizeof(float) * G.ldd, 0, sizeof(float) * G.N,
                                               G.M - row0, h->stream));
@@ -784,8 +714,8 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
     p->status = h->dstatus;
     p->wait_limit_ns = h->wait_limit_ns;
     if (total == 0) return GN_OK;
-    if (p->f8) return MT == 2 ? launch_cfg<false, 1, 2, true>(h, *p, total) : launch_cfg<false, 1, 1, true>(h, *p, total);
-    return MT == 2 ? launch_cfg<false, 2, 2>(h, *p, total) : launch_cfg<false, 1, 1>(h, *p, total);
+    if (p->f8) return MT == 2 ? launch_cfg<false, 2, true>(h, *p, total) : launch_cfg<false, 1, true>(h, *p, total);
+    return MT == 2 ? launch_cfg<false, 2>(h, *p, total) : launch_cfg<false, 1>(h, *p, total);
 }
 
 gn_status tc_prepare_gemm(TcGemm* G, int tile_base, int mt, int f8) {
@@ -810,7 +740,7 @@ gn_status tc_launch_grouped(gn_handle h, const TcGemm* dev_gemms, int ngemm, con
     p.total_tiles = total_tiles;
     p.status = h->dstatus;
     p.wait_limit_ns = h->wait_limit_ns;
-    return mt == 2 ? launch_cfg<true, 1, 2>(h, p, total_tiles) : launch_cfg<true, 1, 1>(h, p, total_tiles);
+    return mt == 2 ? launch_cfg<true, 2>(h, p, total_tiles) : launch_cfg<true, 1>(h, p, total_tiles);
 }
 
 }  // namespace gn

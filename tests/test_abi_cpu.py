@@ -112,9 +112,15 @@ def test_apply_and_update_host_validation():
     assert L.gn_apply(None, None, None, None, None, None, 0, None, 0) == 1
     assert L.gn_update_workspace_size(1000, 500, 20, 10, gn.BF16, ctypes.byref(b)) == 0
     upd = b.value
-    assert L.gn_workspace_size(1000, 500, 20, 10, gn.BF16, ctypes.byref(b)) == 0 and upd > b.value
+    # the scratch holds E's two sketches in FP32: at least (m r + (r + l) n) floats
+    assert upd >= 4 * (1000 * 20 + 30 * 500)
+    # blocks of any size are sized: one appended row or column (m or n = 1, r > m)
+    assert L.gn_update_workspace_size(1, 500, 20, 10, gn.BF16, ctypes.byref(b)) == 0 and 0 < b.value < upd
+    assert L.gn_update_workspace_size(1000, 1, 20, 10, gn.F64, ctypes.byref(b)) == 0 and b.value > 0
+    assert L.gn_update_workspace_size(1000, 500, 20, 0, gn.BF16, ctypes.byref(b)) == 0   # l = 0 allowed
     assert L.gn_update_workspace_size(1000, 500, 20, 10, gn.F32, ctypes.byref(b)) == 3  # no F32 operand path
     assert L.gn_update_workspace_size(1000, 500, 0, 10, gn.BF16, ctypes.byref(b)) == 2  # r < 1
+    assert L.gn_update_workspace_size(0, 500, 20, 10, gn.BF16, ctypes.byref(b)) == 2   # empty block
     assert L.gn_update(None, None, None, None, None, None, None, 0) == 1
 
 
@@ -124,3 +130,26 @@ def test_sketch_state_calls_reject_null_arguments():
     assert L.gn_resample(None, None, None, None, None, None, None, None, None, 0) == 1
     assert L.gn_append_rows(None, None, None, None, None, None, None, None, 0) == 1
     assert L.gn_append_cols(None, None, None, None, None, None, None, None, 0) == 1
+
+
+def test_resample_sizing_and_null_workspace():
+    """gn_resample_workspace_size accepts dr = 0 or dl = 0 (not both), and
+    gn_resample rejects a null workspace on the host even when every matrix
+    descriptor is valid (device pointers are never dereferenced on the host)."""
+    import paper_2009_11392_gb300 as gn
+    L = gn.lib
+    b = ctypes.c_size_t()
+    f = L.gn_resample_workspace_size
+    assert f(1000, 500, 10, 5, gn.F64, ctypes.byref(b)) == 0 and b.value > 0
+    assert f(1000, 500, 10, 0, gn.BF16, ctypes.byref(b)) == 0
+    assert f(1000, 500, 0, 5, gn.E4M3, ctypes.byref(b)) == 0 and b.value > 0
+    assert f(1000, 500, 0, 0, gn.BF16, ctypes.byref(b)) == 2
+    assert f(1000, 500, -1, 5, gn.BF16, ctypes.byref(b)) == 2
+    assert f(1000, 500, 10, 5, gn.F32, ctypes.byref(b)) == 3
+    assert f(1000, 500, 10, 5, gn.F64, None) == 1
+    m, n, r, l, dr, dl = 40, 30, 4, 2, 3, 1
+    fake = 0x10000   # never dereferenced: the call returns before any launch
+    M = lambda rows, cols: gn.GnMat(fake, 0, rows, cols, cols, gn.F64)
+    h = ctypes.c_void_p(fake)
+    args = [M(m, n), M(n, dr), M(m, dr + dl), M(m, r), M(r + l, n), M(m, r + dr), M(r + l + dr + dl, n)]
+    assert L.gn_resample(h, *[ctypes.byref(a) for a in args], None, 1 << 20) == 1

@@ -104,7 +104,7 @@ def test_tc_sketch_exact_on_integer_inputs(gn, H, m, n, r, l):
 
 def test_tc_sketch_large_sampled(gn, H):
     """16384 x 8192, r = 1000, l = 500: enough tiles for the 256-row tile shape
-    (CTA pairs sharing the B stage by multicast).  Integer inputs drawn on the
+    (two MMAs sharing each B stage).  Integer inputs drawn on the
     device; 64 sampled rows of AX and 64 sampled columns of Y^T A against the
     oracle's products, bitwise."""
     m, n, r, l = 16384, 8192, 1000, 500

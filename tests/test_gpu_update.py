@@ -128,3 +128,82 @@ def test_append_rows_and_cols_bf16_exact_on_integer_inputs(gn, H):
     oAX, oYtA = O.sketch(torch.cat([A, Bc], 1).numpy(), torch.cat([X, Xc], 0).numpy(), Y.numpy())
     assert np.array_equal(npy(AX), oAX)
     assert np.array_equal(npy(YtAn), oYtA)
+
+
+def _resample_case(gn, H, m, n, r, l, dr, dl, seed):
+    """Resample on integer inputs (exact in BF16, sums below 2^24) and compare
+    with the sketches of [X, Xd], [Y, Yd] bit for bit."""
+    g = torch.Generator().manual_seed(seed)
+    A, X, Y = _ints(g, m, n), _ints(g, n, r), _ints(g, m, r + l)
+    Xd, Yd = _ints(g, n, dr), _ints(g, m, dr + dl)
+    Ab, Xb, Yb, Ydb = (H.quantize(t.cuda()) for t in (A, X, Y, Yd))
+    Xdb = H.quantize(Xd.cuda()) if dr > 0 else torch.empty(n, 0, dtype=torch.bfloat16, device="cuda")
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    AXn = torch.full((m, r + dr), float("nan"), dtype=torch.float32, device="cuda")
+    YtAn = torch.full((r + l + dr + dl, n), float("nan"), dtype=torch.float32, device="cuda")
+    H.resample(Ab, Xdb, Ydb, AX, YtA, AXn, YtAn)
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch(A.numpy(), torch.cat([X, Xd], 1).numpy(), torch.cat([Y, Yd], 1).numpy())
+    assert np.array_equal(npy(AXn), oAX)
+    assert np.array_equal(npy(YtAn), oYtA)
+
+
+@pytest.mark.parametrize("r,dr,dl", [(41, 7, 3), (40, 12, 0), (40, 0, 9)])
+def test_resample_odd_r_and_single_sided(gn, H, r, dr, dl):
+    """r odd (the new columns of AX start off a 16-byte boundary: scalar
+    epilogue), dl = 0 (r raised, l kept) and dr = 0 (l raised alone, Xd has no
+    columns and only Yd^T A is formed)."""
+    _resample_case(gn, H, 430, 390, r, 20, dr, dl, seed=31 + r + dr + dl)
+
+
+def test_resample_fp64_against_oracle(gn, H):
+    m, n, r, l, dr, dl = 300, 260, 23, 11, 5, 2
+    rng = np.random.default_rng(8)
+    A, X, Y = rng.standard_normal((m, n)), rng.standard_normal((n, r)), rng.standard_normal((m, r + l))
+    Xd, Yd = rng.standard_normal((n, dr)), rng.standard_normal((m, dr + dl))
+    cu = lambda t: torch.from_numpy(t).cuda()
+    ws = H.workspace(m, n, r, l, gn.F64)
+    AX = torch.empty(m, r, dtype=torch.float64, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float64, device="cuda")
+    H.sketch(cu(A), cu(X), cu(Y), AX, YtA, ws)
+    AXn = torch.full((m, r + dr), float("nan"), dtype=torch.float64, device="cuda")
+    YtAn = torch.full((r + l + dr + dl, n), float("nan"), dtype=torch.float64, device="cuda")
+    H.resample(cu(A), cu(Xd), cu(Yd), AX, YtA, AXn, YtAn)
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch(A, np.hstack([X, Xd]), np.hstack([Y, Yd]))
+    assert np.linalg.norm(npy(AXn) - oAX) <= 1e-13 * np.linalg.norm(oAX)
+    assert np.linalg.norm(npy(YtAn) - oYtA) <= 1e-13 * np.linalg.norm(oYtA)
+
+
+@pytest.mark.parametrize("mb,nb", [(1, 1), (3, 5)])
+def test_append_single_rows_and_cols(gn, H, mb, nb):
+    """Appending fewer rows than r + l or fewer columns than r (one at a time,
+    the usual case of Section 6's appended data): bit for bit against the
+    sketches of the enlarged inputs."""
+    m, n, r, l = 300, 280, 30, 15
+    g = torch.Generator().manual_seed(40 + mb)
+    A, X, Y = _ints(g, m, n), _ints(g, n, r), _ints(g, m, r + l)
+    Br, Yr = _ints(g, mb, n), _ints(g, mb, r + l)
+    Bc, Xc = _ints(g, m, nb), _ints(g, nb, r)
+    Ab, Xb, Yb, Brb, Yrb, Bcb, Xcb = (H.quantize(t.cuda()) for t in (A, X, Y, Br, Yr, Bc, Xc))
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    AXn = torch.full((m + mb, r), float("nan"), dtype=torch.float32, device="cuda")
+    H.append_rows(Brb, Xb, Yrb, AX, YtA, AXn)
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch(torch.cat([A, Br], 0).numpy(), X.numpy(), torch.cat([Y, Yr], 0).numpy())
+    assert np.array_equal(npy(AXn), oAX)
+    assert np.array_equal(npy(YtA), oYtA)
+
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    YtAn = torch.full((r + l, n + nb), float("nan"), dtype=torch.float32, device="cuda")
+    H.append_cols(Bcb, Xcb, Yb, AX, YtA, YtAn)
+    assert H.sync_status() == 0
+    oAX, oYtA = O.sketch(torch.cat([A, Bc], 1).numpy(), torch.cat([X, Xc], 0).numpy(), Y.numpy())
+    assert np.array_equal(npy(AX), oAX)
+    assert np.array_equal(npy(YtAn), oYtA)
