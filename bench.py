@@ -5,16 +5,26 @@ Workload: A = W1 diag(i^-2) W2^T + 1e-8 N (2000 modes), 32768 x 16384, sketch
 sizes r = 1000, l = 500 (Gaussian X, Y), the mixed-precision path: A, X, Y in
 BF16 (tensor-core sketch, FP32 accumulation), FP64 core.  One step = one
 approximation in the paper's output form (Algorithm 2 and the text after it:
-AX, Y^T A, Q, R): the fused sketch launch, the core product C = (Y^T A) X on
-the tensor cores (three bf16 slices of Y^T A), Householder QR of C in FP64 and
-the Section 5.1.2 detector / Section 5.1.1 truncation (mode AUTO).
+AX, Y^T A, Q, R): the sketch launch, the core product C = (Y^T A) X on the
+tensor cores (three bf16 slices of Y^T A), Householder QR of C in FP64 and the
+Section 5.1.2 detector / Section 5.1.1 truncation (mode AUTO).
 
-Prints ONE JSON line (rank 0).  Also reported, outside the timed region:
-the split-BF16 path, the plain FP64 GPU path on the same matrix, the factor
-formation F, G, the error ||A - F G||_F of each path, and the FP64 CPU oracle
-timed on a row sample of the same workload (cpu_baseline).
+Steps run on --inflight handles (default 2), each with its own CUDA stream,
+workspace and outputs: step i's core is enqueued without a host wait
+(GN_CORE_DEFER) and finished after step i + 1 is enqueued, so one step's
+latency-bound FP64 core overlaps the next step's sketch and core.  The latency
+of a single approximation (one in flight) is reported beside it.
 
---impl reference times the FP64 CPU oracle alone (the reference arm).
+Prints ONE JSON line (rank 0).  Also reported, outside the timed region: the
+measured FP8 (e4m3) and FP64 peaks, the split-BF16 and e4m3 paths, the plain
+FP64 GPU path, the error of each precision against the FP64 GPU path on the
+same quantized sketches (and on the same stored A), factor formation, the
+20000 x 10000 and 1000 x 500 FP64 cases with HMT beside GN, the Section 6
+sketch-state operations, r = 2000, the adjoint, the batched path, and the FP64
+CPU oracle timed on one whole approximation of the same matrix.
+
+--impl reference times the FP64 CPU oracle alone (the reference arm): every
+timed step is one whole approximation of the full matrix.
 """
 from __future__ import annotations
 
@@ -50,8 +60,8 @@ def parse():
     ap.add_argument("--m", type=int, default=32768)
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--r", type=int, default=1000)
-    ap.add_argument("--no-extras", action="store_true", help="skip split/FP64/error/CPU side measurements")
-    ap.add_argument("--cpu-rows", type=int, default=512, help="row sample of the CPU-oracle baseline")
+    ap.add_argument("--inflight", type=int, default=2, help="approximations in flight (handles / streams)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the side measurements and the CPU baseline")
     ap.add_argument("--op", default="bf16", choices=["bf16", "e4m3"],
                     help="sketch operand type of the timed step (e4m3: per-128x128-tile scales)")
     return ap.parse_args()
@@ -63,6 +73,7 @@ def config_dict(a, precision=None):
         "workload": f"GN dense {a.m}x{a.n} low-rank+noise (i^-2, 2000 modes, 1e-8 noise), r={a.r}, "
                     f"l={a.r // 2}, Gaussian sketches, {precision} operands, FP64 core, mode AUTO",
         "m": a.m, "n": a.n, "r": a.r, "l": a.r // 2,
+        "inflight": getattr(a, "inflight", 1),
         "l2": "inputs larger than L2 (A alone is %.2f GB in BF16)" % (2.0 * a.m * a.n / 1e9),
         "parallelism": "replicas" if a.gpus > 1 else "single GPU",
     }
@@ -75,6 +86,51 @@ def measured_peaks():
         d = json.load(open(p))
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _best_ms(fn, reps, stream):
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def measure_dtype_peaks(dev, stream):
+    """The FP8 (e4m3, per-tensor scales, cuBLASLt through torch._scaled_mm) and
+    FP64 (torch.matmul) peaks on this GPU, measured the way MEASURED_PEAKS.json
+    measures BF16: best of several CUDA-event timed square products."""
+    out = {}
+    with torch.cuda.stream(stream):
+        try:
+            n = 8192
+            a = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn)
+            b = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn).t()
+            one = torch.tensor(1.0, device=dev)
+            f = lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+            f()
+            ms = _best_ms(f, 10, stream)
+            out["e4m3_tflops"] = 2.0 * n ** 3 / (ms / 1e3) / 1e12
+            out["e4m3_how"] = "torch._scaled_mm e4m3 8192^3, per-tensor scales, bf16 out, best of 10"
+            del a, b
+        except Exception as ex:  # pragma: no cover
+            out["e4m3_tflops"] = None
+            out["e4m3_how"] = f"not measured: {type(ex).__name__}: {ex}"
+        n = 4096
+        a = torch.randn(n, n, device=dev, dtype=torch.float64)
+        b = torch.randn(n, n, device=dev, dtype=torch.float64)
+        f = lambda: torch.matmul(a, b)
+        f()
+        ms = _best_ms(f, 4, stream)
+        out["fp64_tflops"] = 2.0 * n ** 3 / (ms / 1e3) / 1e12
+        out["fp64_how"] = "torch.matmul float64 4096^3, best of 4"
+        del a, b
+    torch.cuda.synchronize()
+    return out
 
 
 # --------------------------------------------------------------------------- clocks
@@ -95,7 +151,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -140,27 +196,6 @@ def gpu_id_for_smi(local_rank):
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def cpu_oracle_sample(a, rows, seed=gn_synth.DEFAULT_SEED):
-    """FP64 CPU oracle on a row sample of the workload: the sketches of `rows`
-    rows (scaled by m/rows to the full matrix) and the full core (C, QR,
-    detector, truncation) on a core of the full shape.  Returns seconds per
-    approximation and a description."""
-    from oracle import gn_oracle as O
-    l = a.r // 2
-    A_s = gn_synth.lowrank_plus_noise(rows, a.n, 2000, gn_synth.power_decay(2000, 2.0), 1e-8, seed + 7).numpy()
-    X, Y_s = gn_synth.sketches(rows, a.n, a.r, l, seed + 7)
-    X, Y_s = X.numpy(), Y_s.numpy()
-    t0 = time.perf_counter()
-    AX_s, YtA_s = O.sketch(A_s, X, Y_s)
-    t1 = time.perf_counter()
-    O.core(YtA_s, X, 10 * 2.0 ** -53, O.AUTO, eps_relative=True, diag_iters=6)
-    t2 = time.perf_counter()
-    per = (t1 - t0) * (a.m / rows) + (t2 - t1)
-    desc = (f"FP64 numpy oracle: sketch of {rows} of {a.m} rows (x{a.m // rows} to the full matrix) "
-            f"+ full {a.r + l}x{a.r} core (QR, detector); sketch {t1 - t0:.2f}s, core {t2 - t1:.2f}s")
-    return per, desc
-
-
 def blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -172,21 +207,49 @@ def blas_threads():
     return os.cpu_count()
 
 
+def oracle_step(A, X, Y, r):
+    """One whole approximation by the FP64 CPU oracle (sketch of the full A,
+    then the core: C, Householder QR, detector, truncation); returns seconds
+    and the split."""
+    from oracle import gn_oracle as O
+    t0 = time.perf_counter()
+    AX, YtA = O.sketch(A, X, Y)
+    t1 = time.perf_counter()
+    O.core(YtA, X, 10 * 2.0 ** -53, O.AUTO, eps_relative=True, diag_iters=6)
+    t2 = time.perf_counter()
+    return t2 - t0, t1 - t0, t2 - t1
+
+
 def run_reference(a, rank, world):
+    """The reference arm: the FP64 CPU oracle on the host cores.  Each timed
+    step is one whole approximation of the full 32768 x 16384 matrix; the
+    warm-up steps (nothing to compile or cache) run the oracle on a 512-row
+    block so that the whole run stays within a few minutes."""
     if rank != 0:
         return
-    rows = 256
-    times = []
-    for i in range(a.warmup + a.steps):
-        per, desc = cpu_oracle_sample(a, rows, gn_synth.DEFAULT_SEED + i)
-        if i >= a.warmup:
-            times.append(per)
-    per = statistics.mean(times)
+    from oracle import gn_oracle as O
+    l = a.r // 2
+    p = gn_synth.config3(r=a.r, m=a.m, n=a.n)
+    A, X, Y = p.a.numpy(), p.x.numpy(), p.y.numpy()
+    del p
+    for _ in range(a.warmup):
+        O.sketch(A[:512], X, Y[:512])
+    times, splits = [], []
+    t_all0 = time.perf_counter()
+    for _ in range(a.steps):
+        t, ts, tc = oracle_step(A, X, Y, a.r)
+        times.append(t)
+        splits.append((ts, tc))
+    wall = time.perf_counter() - t_all0
+    per = wall / a.steps
     v = 1.0 / per
+    desc = (f"FP64 numpy oracle, one whole approximation per step on the full {a.m}x{a.n} matrix "
+            f"(sketch {statistics.mean(s for s, _ in splits):.2f}s + {a.r + l}x{a.r} core "
+            f"{statistics.mean(c for _, c in splits):.2f}s)")
     line = {
         "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "impl": "reference", "config": config_dict(a, "FP64 (oracle)"),
+        "dtype": "f64", "data": "synthetic", "impl": "reference", "config": config_dict(a),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -215,15 +278,16 @@ def main():
         return
 
     import paper_2009_11392_gb300 as gn
-    from paper_2009_11392_gb300 import build as _b  # noqa: F401
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     m, n, r = a.m, a.n, a.r
     l = r // 2
+    nf = max(1, a.inflight)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     H = gn.Handle(stream)
+    Hs = [H] + [gn.Handle(torch.cuda.Stream(device=dev)) for _ in range(nf - 1)]
 
     # ---- inputs (seeded, drawn on the device; FP64)
     p = gn_synth.config3(r=r, device=dev, m=m, n=n)
@@ -250,46 +314,66 @@ def main():
     torch.cuda.synchronize()
     quantize_ms = q0.elapsed_time(q1)
 
-    ws = H.workspace(m, n, r, l, gn.E4M3 if a.op == "e4m3" else gn.BF16X2)
-    AX = torch.empty(m, r, dtype=torch.float32, device=dev)
-    YtA = torch.empty(r + l, n, dtype=torch.float32, device=dev)
-    core = gn.Core.empty(r, l, dev)
+    wsd = gn.E4M3 if a.op == "e4m3" else gn.BF16X2
+    bufs = [(Hj.workspace(m, n, r, l, wsd), torch.empty(m, r, dtype=torch.float32, device=dev),
+             torch.empty(r + l, n, dtype=torch.float32, device=dev), gn.Core.empty(r, l, dev)) for Hj in Hs]
+    ws, AX, YtA, core = bufs[0]
 
-    def step(A_op, A_lo=None, ev=None):
-        if ev is not None:
-            ev[0].record(stream)
-        H.sketch(A_op, Xop, Yop, AX, YtA, ws, A_lo=A_lo)
-        if ev is not None:
-            ev[1].record(stream)
-        H.core(YtA, Xop, eps, mode, core, ws)
+    def run_steps(k, use, evs=None):
+        """k steps on the first `use` handles; step i's core is finished after
+        step i + use - 1 is enqueued."""
+        pend = []
+        for i in range(k):
+            j = i % use
+            Hj = Hs[j]
+            wsj, AXj, YtAj, cj = bufs[j]
+            if evs is not None:
+                evs[i][0].record(Hj.stream)
+            Hj.sketch(Aop, Xop, Yop, AXj, YtAj, wsj)
+            if evs is not None:
+                evs[i][1].record(Hj.stream)
+            Hj.core(YtAj, Xop, eps, mode | gn.CORE_DEFER, cj, wsj)
+            pend.append((Hj, cj))
+            if len(pend) >= use:
+                h_, c_ = pend.pop(0)
+                h_.core_finish(c_)
+        for h_, c_ in pend:
+            h_.core_finish(c_)
 
-    for _ in range(a.warmup):
-        step(Aop)
+    def timed(k, use, evs=None):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(Hs[0].stream)
+        for Hj in Hs[1:use]:
+            Hj.stream.wait_event(t0)
+        run_steps(k, use, evs)
+        for Hj in Hs[1:use]:
+            Hs[0].stream.wait_stream(Hj.stream)
+        t1.record(Hs[0].stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
+
+    run_steps(max(a.warmup, nf), nf)
     torch.cuda.synchronize()
-    if H.sync_status() != 0:
-        raise RuntimeError("device status after warm-up")
+    for Hj in Hs:
+        if Hj.sync_status() != 0:
+            raise RuntimeError("device status after warm-up")
 
     sampler = ClockSampler(gpu_id_for_smi(local))
     sampler.start()
     time.sleep(0.3)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = gn.kernel_launches()
-    t0.record(stream)
-    for i in range(a.steps):
-        step(Aop, ev=evs[i])
-    t1.record(stream)
-    torch.cuda.synchronize()
+    elapsed_ms = timed(a.steps, nf, evs)
     launches = gn.kernel_launches() - launches0
     clocks = sampler.stop()
-    elapsed_ms = t0.elapsed_time(t1)
     sketch_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
-    if H.sync_status() != 0:
-        raise RuntimeError("device status after timed steps")
+    for Hj in Hs:
+        if Hj.sync_status() != 0:
+            raise RuntimeError("device status after timed steps")
     if dist:
         t = torch.tensor([elapsed_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -297,117 +381,45 @@ def main():
     per_step_ms = elapsed_ms / a.steps
     value = world * a.steps / (elapsed_ms / 1e3)
 
-    # ---- end to end through the API with host buffers (H2D inputs, D2H outputs).
-    # Every step copies its own inputs in from pinned host memory and its results
-    # out; two device buffer sets let the copies of one step run on a copy stream
-    # while the previous step computes.
-    nset = 2
-    if a.op == "e4m3":
-        # the e4m3 codes (A in both orientations, X^T, Y^T) and the tile scales
-        srcs = [Aop.data, Aop.data_t, Xop.data_t, Yop.data_t, Aop.scale, Xop.scale, Yop.scale]
-        hosts = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in srcs]
+    # the same loop with one approximation in flight: the latency of one
+    # approximation, and the sketch launch timed alone on the device
+    evs1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    latency_ms = timed(a.steps, 1, evs1) / a.steps
+    sketch_alone_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs1)
 
-        def make_in():
-            d = [torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=dev) for t in srcs]
-            return d, (gn.E4M3Mat(m, n, d[4], d[0], d[1]), gn.E4M3Mat(n, r, d[5], None, d[2]),
-                       gn.E4M3Mat(m, r + l, d[6], None, d[3]))
-    else:
-        srcs = [Ab, Xb, Yb]
-        hosts = [torch.empty(t.shape, dtype=torch.bfloat16, pin_memory=True).copy_(t) for t in srcs]
-
-        def make_in():
-            d = [gn.padded(m, n, torch.bfloat16, dev), gn.padded(n, r, torch.bfloat16, dev),
-                 gn.padded(m, r + l, torch.bfloat16, dev)]
-            return d, tuple(d)
-    ins = [make_in() for _ in range(nset)]
-    outd = [(torch.empty(m, r, dtype=torch.float32, device=dev), torch.empty(r + l, n, dtype=torch.float32, device=dev),
-             gn.Core.empty(r, l, dev)) for _ in range(nset)]
-    outh = [[torch.empty(AX.shape, dtype=torch.float32, pin_memory=True),
-             torch.empty(YtA.shape, dtype=torch.float32, pin_memory=True),
-             torch.empty(core.Q.shape, dtype=torch.float64, pin_memory=True),
-             torch.empty(core.R.shape, dtype=torch.float64, pin_memory=True)] for _ in range(nset)]
-    h2d = sum(t.numel() * t.element_size() for t in hosts)
-    d2h = sum(o.numel() * o.element_size() for o in outh[0])
-    # Two host->device copy streams (large inputs split in row halves, so two copy
-    # engines can carry them) and one device->host stream.
-    hs = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
-    dstream = torch.cuda.Stream(device=dev)
-    ev_in = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(nset)]   # inputs of the set landed
-    ev_done = [torch.cuda.Event() for _ in range(nset)]  # compute on the set finished
-    ev_out = [torch.cuda.Event() for _ in range(nset)]   # results of the set copied out
-
-    def prefetch(i):
-        b = i % nset
-        for q in hs:
-            q.wait_event(ev_done[b])              # the set's previous step has finished computing
-        for d_, h_ in zip(ins[b][0], hosts):
-            if h_.numel() * h_.element_size() >= (64 << 20) and h_.dim() >= 1 and h_.shape[0] >= 2:
-                half = h_.shape[0] // 2
-                with torch.cuda.stream(hs[0]):
-                    d_[:half].copy_(h_[:half], non_blocking=True)
-                with torch.cuda.stream(hs[1]):
-                    d_[half:].copy_(h_[half:], non_blocking=True)
-            else:
-                with torch.cuda.stream(hs[0]):
-                    d_.copy_(h_, non_blocking=True)
-        for q, ev in zip(hs, ev_in[b]):
-            ev.record(q)
-
-    def compute(i):
-        b = i % nset
-        Ad, Xd, Yd = ins[b][1]
-        AXd, YtAd, cd = outd[b]
-        for ev in ev_in[b]:
-            stream.wait_event(ev)
-        stream.wait_event(ev_out[b])              # the set's previous results are out
-        H.sketch(Ad, Xd, Yd, AXd, YtAd, ws)
-        H.core(YtAd, Xd, eps, mode, cd, ws)
-        ev_done[b].record(stream)
-        dstream.wait_event(ev_done[b])
-        with torch.cuda.stream(dstream):
-            for o, s_ in zip(outh[b], (AXd, YtAd, cd.Q, cd.R)):
-                o.copy_(s_, non_blocking=True)
-        ev_out[b].record(dstream)
-
-    def e2e_run(k):
-        prefetch(0)
-        for i in range(k):
-            if i + 1 < k:
-                prefetch(i + 1)
-            compute(i)
-
-    e2e_run(max(1, a.warmup))
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(hs[0])
-    for q in (hs[1], dstream, stream):   # nothing of the timed steps starts before e0
-        q.wait_stream(hs[0])
-    e2e_run(a.steps)
-    e1.record(dstream)                   # after the last step's results are out (which waits for all)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / a.steps
-    del ins, outd, outh, hosts
+    e2e = e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, bufs, eps, mode)
 
     peaks, peak_kind = measured_peaks()
     flops = 2.0 * m * n * (2 * r + l)
-    achieved = flops / (sketch_ms / 1e3) / 1e12
-    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (2.0 if a.op == "e4m3" else 1.0)
+    dpk = measure_dtype_peaks(dev, stream) if rank == 0 else {}
+    if a.op == "e4m3":
+        peak = dpk.get("e4m3_tflops") or 2.0 * peaks["bf16_tflops"]
+        pk = "e4m3 measured in this run (torch._scaled_mm)" if dpk.get("e4m3_tflops") else \
+            f"2 x bf16 burst ({peak_kind}; nominal ratio)"
+    else:
+        peak = peaks["bf16_tflops"]
+        pk = f"bf16 burst, {peak_kind} (MEASURED_PEAKS.json); the kernel runs at full clock inside a short timed region"
     a_bytes = m * n * (1 if a.op == "e4m3" else 2)
     roof_ms = max(a_bytes / (peaks["hbm_gbs"] * 1e9), flops / (peak * 1e12)) * 1e3
+    achieved = flops / (sketch_ms / 1e3) / 1e12
+    achieved_alone = flops / (sketch_alone_ms / 1e3) / 1e12
 
-    # the timed path's core summary, before the side measurements reuse `core`
     core_info = {"eps_rel": eps, "eps_abs": core.eps_abs, "c_norm_est": core.c_norm_est,
                  "k": core.k, "sgn": core.sgn, "rinv_est": core.rinv_est}
     extras = {}
     if not a.no_extras and rank == 0:
-        extras = side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mode, ws, AX, YtA, core, peaks)
+        extras = side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mode, ws, AX, YtA, core,
+                                   peaks, dpk)
 
     cpu = None
-    if rank == 0 and world >= 1 and not a.no_extras:
+    if rank == 0 and not a.no_extras:
         try:
-            per, desc = cpu_oracle_sample(a, a.cpu_rows)
-            cpu = {"value": 1.0 / per, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
+            Ah, Xh, Yh = A64.cpu().numpy(), X64.cpu().numpy(), Y64.cpu().numpy()
+            t, ts, tc = oracle_step(Ah, Xh, Yh, r)
+            del Ah, Xh, Yh
+            cpu = {"value": 1.0 / t, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                   "sample": f"one whole approximation of the same {m}x{n} matrix by the FP64 numpy oracle "
+                             f"(sketch {ts:.2f}s + {r + l}x{r} core {tc:.2f}s), not extrapolated"}
         except Exception as ex:  # pragma: no cover
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
 
@@ -434,32 +446,163 @@ def main():
             "config": config_dict(a),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "tc_multigemm_kernel (fused AX + Y^T A sketch launch)",
-                         "kernel_ms": sketch_ms, "algorithmic_flops": flops,
-                         "peak_kind": (f"bf16 sustained, {peak_kind}" if a.op == "bf16" else
-                                       f"2 x bf16 sustained ({peak_kind}; nominal e4m3 / bf16 ratio)"),
-                         "step_roofline_ms": roof_ms},
+                         "kernel": "tc_multigemm_kernel (AX and Y^T A in one launch)",
+                         "kernel_ms": sketch_ms, "algorithmic_flops": flops, "peak_kind": pk,
+                         "kernel_ms_alone": sketch_alone_ms, "frac_alone": achieved_alone / peak,
+                         "frac_vs_sustained": (achieved / peaks["bf16_tflops_sustained"]) if a.op == "bf16" else None,
+                         "step_roofline_ms": roof_ms, "step_frac": roof_ms / per_step_ms,
+                         "step_frac_latency": roof_ms / latency_ms},
+            "latency_ms": latency_ms,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "quantize_ms": quantize_ms,
+            "dtype_peaks": dpk,
         }
         line.update(core_info)
         line.update(extras)
         if "factors_ms" in extras:   # sketch + core + factors F (FP64 solve) and G
-            line["all_in"] = {"approx_per_s": 1e3 / (per_step_ms + extras["factors_ms"]),
-                              "ms": per_step_ms + extras["factors_ms"]}
+            line["all_in"] = {"approx_per_s": 1e3 / (latency_ms + extras["factors_ms"]),
+                              "ms": latency_ms + extras["factors_ms"], "inflight": 1}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mode, ws, AX, YtA, core, peaks):
-    """Outside the timed region: split-BF16 throughput, factors, errors of each
-    path against the FP64 A, and the plain FP64 GPU path on the same matrix."""
+def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, bufs, eps, mode):
+    """End to end through the API with host buffers: every step copies its own
+    inputs in from pinned host memory and its results (AX, Y^T A, Q, R) out.
+    nf + 1 device buffer sets; the copies run on two host-to-device streams
+    (large inputs in row halves) and one device-to-host stream while the steps
+    compute on the nf handles."""
+    nset = nf + 1
+    if a.op == "e4m3":
+        srcs = [Aop.data, Aop.data_t, Xop.data_t, Yop.data_t, Aop.scale, Xop.scale, Yop.scale]
+        hosts = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in srcs]
+
+        def make_in():
+            d = [torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=dev) for t in srcs]
+            return d, (gn.E4M3Mat(m, n, d[4], d[0], d[1]), gn.E4M3Mat(n, r, d[5], None, d[2]),
+                       gn.E4M3Mat(m, r + l, d[6], None, d[3]))
+    else:
+        srcs = [Ab, Xb, Yb]
+        hosts = [torch.empty(t.shape, dtype=torch.bfloat16, pin_memory=True).copy_(t) for t in srcs]
+
+        def make_in():
+            d = [gn.padded(m, n, torch.bfloat16, dev), gn.padded(n, r, torch.bfloat16, dev),
+                 gn.padded(m, r + l, torch.bfloat16, dev)]
+            return d, tuple(d)
+    ins = [make_in() for _ in range(nset)]
+    outd = [(torch.empty(m, r, dtype=torch.float32, device=dev), torch.empty(r + l, n, dtype=torch.float32, device=dev),
+             gn.Core.empty(r, l, dev)) for _ in range(nset)]
+    outh = [[torch.empty(m, r, dtype=torch.float32, pin_memory=True),
+             torch.empty(r + l, n, dtype=torch.float32, pin_memory=True),
+             torch.empty(r + l, r, dtype=torch.float64, pin_memory=True),
+             torch.empty(r, r, dtype=torch.float64, pin_memory=True)] for _ in range(nset)]
+    h2d = sum(t.numel() * t.element_size() for t in hosts)
+    d2h = sum(o.numel() * o.element_size() for o in outh[0])
+    hs = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    dstream = torch.cuda.Stream(device=dev)
+    ev_in = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(nset)]
+    ev_done = [torch.cuda.Event() for _ in range(nset)]
+    ev_out = [torch.cuda.Event() for _ in range(nset)]
+    step_handle = {}
+
+    def prefetch(i):
+        b = i % nset
+        for q in hs:
+            q.wait_event(ev_done[b])              # the set's previous step has finished computing
+        for d_, h_ in zip(ins[b][0], hosts):
+            if h_.numel() * h_.element_size() >= (64 << 20) and h_.dim() >= 1 and h_.shape[0] >= 2:
+                half = h_.shape[0] // 2
+                with torch.cuda.stream(hs[0]):
+                    d_[:half].copy_(h_[:half], non_blocking=True)
+                with torch.cuda.stream(hs[1]):
+                    d_[half:].copy_(h_[half:], non_blocking=True)
+            else:
+                with torch.cuda.stream(hs[0]):
+                    d_.copy_(h_, non_blocking=True)
+        for q, ev in zip(hs, ev_in[b]):
+            ev.record(q)
+
+    def enqueue(i):
+        b, j = i % nset, i % nf
+        Hj = Hs[j]
+        wsj = bufs[j][0]
+        Ad, Xd, Yd = ins[b][1]
+        AXd, YtAd, cd = outd[b]
+        for ev in ev_in[b]:
+            Hj.stream.wait_event(ev)
+        Hj.stream.wait_event(ev_out[b])           # the set's previous results are out
+        Hj.sketch(Ad, Xd, Yd, AXd, YtAd, wsj)
+        Hj.core(YtAd, Xd, eps, mode | gn.CORE_DEFER, cd, wsj)
+        step_handle[i] = Hj
+
+    def complete(i):
+        b = i % nset
+        Hj = step_handle.pop(i)
+        AXd, YtAd, cd = outd[b]
+        Hj.core_finish(cd)
+        ev_done[b].record(Hj.stream)
+        dstream.wait_event(ev_done[b])
+        with torch.cuda.stream(dstream):
+            for o, s_ in zip(outh[b], (AXd, YtAd, cd.Q, cd.R)):
+                o.copy_(s_, non_blocking=True)
+        ev_out[b].record(dstream)
+
+    def run(k):
+        lag = nf - 1
+        prefetch(0)
+        for i in range(k):
+            enqueue(i)
+            if i - lag >= 0:
+                complete(i - lag)
+            if i + 1 < k:
+                prefetch(i + 1)
+        for i in range(max(0, k - lag), k):
+            complete(i)
+
+    run(max(1, a.warmup))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(hs[0])
+    for q in [hs[1], dstream] + [Hj.stream for Hj in Hs]:   # nothing of the timed steps starts before e0
+        q.wait_stream(hs[0])
+    run(a.steps)
+    e1.record(dstream)                   # after the last step's results are out (which waits for all)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    # the host link's own rates on this box (pinned, one stream each way), for reading the figure above
+    big = hosts[0]
+    dbig = ins[0][0][0]
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(hs[0])
+    with torch.cuda.stream(hs[0]):
+        dbig.copy_(big, non_blocking=True)
+    c1.record(hs[0])
+    torch.cuda.synchronize()
+    h2d_gbs = big.numel() * big.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9
+    c0.record(dstream)
+    with torch.cuda.stream(dstream):
+        big.copy_(dbig, non_blocking=True)
+    c1.record(dstream)
+    torch.cuda.synchronize()
+    d2h_gbs = big.numel() * big.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9
+    del ins, outd, outh, hosts
+    torch.cuda.empty_cache()
+    return {"value": 1e3 / ms, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": ms, "h2d_gbs_one_stream": h2d_gbs, "d2h_gbs_one_stream": d2h_gbs,
+            "copy_floor_ms": (h2d / (2 * h2d_gbs) + d2h / d2h_gbs) / 1e6}
+
+
+# --------------------------------------------------------------------------- side measurements
+def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mode, ws, AX, YtA, core, peaks, dpk):
+    """Outside the timed region: the precision contract, the FP64 path, factors,
+    the FP64 cases with HMT, the Section 6 operations, r = 2000, the adjoint and
+    the batched path."""
     m, n, r = a.m, a.n, a.r
     l = r // 2
     out = {}
@@ -468,30 +611,91 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
     G = torch.empty(r, n, dtype=torch.float64, device=dev)
     e2 = torch.zeros(1, dtype=torch.float64, device=dev)
     normA = A64.norm().item()
+    reps = max(3, a.steps // 2)
 
-    def err_of(AXt, YtAt, c):
+    def err_of(AXt, YtAt, c, Aref):
         H.factors(AXt, YtAt, c, F, G, ws)
-        H.error_fro2(A64, F[:, :c.k], G[:c.k], e2, ws)
+        H.error_fro2(Aref, F[:, :c.k], G[:c.k], e2, ws)
         torch.cuda.synchronize()
         return math.sqrt(e2.item())
 
     # factors time (FP64 trsm + G) for the bf16 path
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    H.core(YtA, Xb, eps, mode, core, ws)
     f0, f1 = ev(), ev()
     f0.record(stream)
     H.factors(AX, YtA, core, F, G, ws)
     f1.record(stream)
     torch.cuda.synchronize()
     out["factors_ms"] = f0.elapsed_time(f1)
-    out["err_bf16"] = err_of(AX, YtA, core)
+    out["err_bf16"] = err_of(AX, YtA, core, A64)
 
-    # split bf16 (hi + lo) path
+    # ---- the plain FP64 GPU path (its own timing, on the unrounded Gaussian sketches)
+    AX64 = torch.empty(m, r, dtype=torch.float64, device=dev)
+    YtA64 = torch.empty(r + l, n, dtype=torch.float64, device=dev)
+    c64 = gn.Core.empty(r, l, dev)
+    ws64 = H.workspace(m, n, r, l, gn.F64)
+    eps64 = 10 * 2.0 ** -53
+    p0, p1, p2 = ev(), ev(), ev()
+    p0.record(stream)
+    H.sketch(A64, X64, Y64, AX64, YtA64, ws64)
+    p1.record(stream)
+    H.core(YtA64, X64, eps64, mode, c64, ws64)
+    p2.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = p0.elapsed_time(p2)
+    sk64 = p0.elapsed_time(p1)
+    fl = 2.0 * m * n * (2 * r + l)
+    fp64_peak = dpk.get("fp64_tflops")
+    out["fp64_path"] = {"approx_per_s": 1e3 / fp64_ms, "ms_per_step": fp64_ms, "sketch_ms": sk64,
+                        "sketch_tflops": fl / (sk64 / 1e3) / 1e12,
+                        "sketch_frac": (fl / (sk64 / 1e3) / 1e12 / fp64_peak) if fp64_peak else None,
+                        "peak_kind": "fp64 measured in this run (torch.matmul float64)",
+                        "err": None}
+
+    def fp64_err(Aexact, Xs, Ys, Aref):
+        """FP64 GPU path (sketch, core, factors) on exact FP64 inputs; error vs Aref."""
+        H.sketch(Aexact, Xs, Ys, AX64, YtA64, ws64)
+        H.core(YtA64, Xs, eps64, mode, c64, ws64)
+        H.factors(AX64, YtA64, c64, F, G, ws64)
+        H.error_fro2(Aref, F[:, :c64.k], G[:c64.k], e2, ws64)
+        torch.cuda.synchronize()
+        return math.sqrt(e2.item())
+
+    out["fp64_path"]["err"] = fp64_err(A64, X64, Y64, A64)
+
+    # ---- precision contract: every mixed path against the FP64 GPU path on the
+    # same quantized sketches (and, for parity, on the same stored A)
+    Xq, Yq = Xb.double(), Yb.double()
+    err_ref = fp64_err(A64, Xq, Yq, A64)
+    prec = {"fp64_matched_err": err_ref,
+            "reading": "ratio_vs_fp64 = err(mixed path, vs FP64 A) / err(FP64 path on the FP64 A with the same "
+                       "quantized X, Y); parity_ratio = the same two paths on the stored (quantized) A, each "
+                       "measured against that stored A; floor = ||A - A_stored||_F (storage error no rank-r "
+                       "approximant removes)"}
+
+    def contract(name, Astored64, Xs64, Ys64, mixed_err_vs_A, mixed_err_vs_Ast):
+        ref_st = fp64_err(Astored64, Xs64, Ys64, Astored64)
+        d = (A64 - Astored64).norm().item()
+        prec[name] = {"err_vs_A": mixed_err_vs_A, "ratio_vs_fp64": mixed_err_vs_A / err_ref,
+                      "err_vs_A_stored": mixed_err_vs_Ast, "fp64_on_A_stored_err": ref_st,
+                      "parity_ratio": mixed_err_vs_Ast / ref_st, "floor_storage": d,
+                      "floor_estimate": math.sqrt(err_ref ** 2 + d ** 2)}
+
+    Ab64 = Ab.double()
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    H.core(YtA, Xb, eps, mode, core, ws)
+    e_a = err_of(AX, YtA, core, A64)
+    e_s = err_of(AX, YtA, core, Ab64)
+    contract("bf16", Ab64, Xq, Yq, e_a, e_s)
+    del Ab64
+
+    # split bf16 (hi + lo) path: throughput and the contract
     Ahi, Alo = H.quantize(A64, split=True)
-    s0, s1 = ev(), ev()
     H.sketch(Ahi, Xb, Yb, AX, YtA, ws, A_lo=Alo)
     H.core(YtA, Xb, eps, mode, core, ws)
     torch.cuda.synchronize()
-    reps = max(3, a.steps // 2)
-    k0, k1 = ev(), ev()
+    k0, k1, s0, s1 = ev(), ev(), ev(), ev()
     s0.record(stream)
     for _ in range(reps):
         k0.record(stream)
@@ -503,12 +707,15 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
     split_ms = s0.elapsed_time(s1) / reps
     split_sketch_ms = k0.elapsed_time(k1)
     H.set_fp64_g(True)   # split BF16 aims at the FP64 path's error: G in FP64 too
-    fl2 = 2 * 2.0 * m * n * (2 * r + l)
-    out["split_bf16"] = {"approx_per_s": 1e3 / split_ms, "ms_per_step": split_ms, "sketch_ms": split_sketch_ms,
-                         "sketch_tflops": fl2 / (split_sketch_ms / 1e3) / 1e12,
-                         "err": err_of(AX, YtA, core), "g_fp64": True}
+    Asp64 = Ahi.double() + Alo.double()
+    e_a = err_of(AX, YtA, core, A64)
+    e_s = err_of(AX, YtA, core, Asp64)
     H.set_fp64_g(False)
-    del Ahi, Alo
+    fl2 = 2 * fl
+    out["split_bf16"] = {"approx_per_s": 1e3 / split_ms, "ms_per_step": split_ms, "sketch_ms": split_sketch_ms,
+                         "sketch_tflops": fl2 / (split_sketch_ms / 1e3) / 1e12, "err": e_a, "g_fp64": True}
+    contract("split_bf16", Asp64, Xq, Yq, e_a, e_s)
+    del Ahi, Alo, Asp64
 
     # e4m3 path: one power-of-two scale per 128 x 128 tile, block-scaled MMAs
     q0, q1 = ev(), ev()
@@ -532,45 +739,177 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
     torch.cuda.synchronize()
     f8_ms = e0.elapsed_time(e1) / reps
     f8_sketch_ms = k0.elapsed_time(k1)
-    fl = 2.0 * m * n * (2 * r + l)
-    peak8 = 2.0 * peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])   # nominal e4m3 / bf16 ratio
+    peak8 = dpk.get("e4m3_tflops") or 2.0 * peaks["bf16_tflops"]
+    A8v = A8.values()
+    e_a = err_of(AX, YtA, core, A64)
+    e_s = err_of(AX, YtA, core, A8v)
     out["fp8_e4m3"] = {"approx_per_s": 1e3 / f8_ms, "ms_per_step": f8_ms, "sketch_ms": f8_sketch_ms,
                        "sketch_tflops": fl / (f8_sketch_ms / 1e3) / 1e12,
-                       "sketch_frac": fl / (f8_sketch_ms / 1e3) / 1e12 / peak8,
-                       "peak_tflops": peak8, "peak_kind": "2 x measured bf16 sustained (nominal ratio)",
-                       "quantize_ms": q0.elapsed_time(q1), "k": core.k, "err": err_of(AX, YtA, core)}
-    del A8, X8, Y8, ws8
-
-    # plain FP64 GPU path on the same matrix (one step)
-    AX64 = torch.empty(m, r, dtype=torch.float64, device=dev)
-    YtA64 = torch.empty(r + l, n, dtype=torch.float64, device=dev)
-    c64 = gn.Core.empty(r, l, dev)
-    ws64 = H.workspace(m, n, r, l, gn.F64)
-    eps64 = 10 * 2.0 ** -53
-    p0, p1, p2 = ev(), ev(), ev()
-    p0.record(stream)
-    H.sketch(A64, X64, Y64, AX64, YtA64, ws64)
-    p1.record(stream)
-    H.core(YtA64, X64, eps64, mode, c64, ws64)
-    p2.record(stream)
-    torch.cuda.synchronize()
-    fp64_ms = p0.elapsed_time(p2)
-    out["fp64_path"] = {"approx_per_s": 1e3 / fp64_ms, "ms_per_step": fp64_ms, "sketch_ms": p0.elapsed_time(p1),
-                        "sketch_tflops": 2.0 * m * n * (2 * r + l) / (p0.elapsed_time(p1) / 1e3) / 1e12,
-                        "err": None}
-    out["fp64_path"]["err"] = err_of(AX64, YtA64, c64)
+                       "sketch_frac": fl / (f8_sketch_ms / 1e3) / 1e12 / peak8, "peak_tflops": peak8,
+                       "peak_kind": ("e4m3 measured in this run (torch._scaled_mm)" if dpk.get("e4m3_tflops")
+                                     else "2 x bf16 burst (nominal ratio)"),
+                       "quantize_ms": q0.elapsed_time(q1), "k": core.k, "err": e_a}
+    contract("e4m3", A8v, X8.values(), Y8.values(), e_a, e_s)
+    prec["e4m3"]["sketches"] = "e4m3 X, Y (their own per-tile scales); ratio_vs_fp64 against the BF16-rounded ones"
+    del A8, X8, Y8, ws8, A8v
+    out["precision"] = prec
     out["norm_A_fro"] = normA
+    del AX64, YtA64, c64, ws64
+    torch.cuda.empty_cache()
+
+    out["fp64_cases"] = fp64_cases(gn, H, stream, dev)
+    out["sketch_state_ops"] = sketch_state_ops(gn, H, stream, dev, a, Ab, Xb, Yb, eps, mode)
     out["r2000"] = r2000_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode)
     out["adjoint"] = adjoint_measurement(gn, H, stream, dev)
     out["batched"] = batched_measurement(gn, H, stream, dev, steps=max(3, a.steps))
-    out["err_floor_note"] = ("errors are ||A - F G||_F against the FP64 A; the bf16 path's floor is the "
-                             "bf16 storage of A, split bf16 and FP64 reach the sketch error itself")
     return out
+
+
+def fp64_cases(gn, H, stream, dev):
+    """The FP64 cases with the HMT baseline (Algorithm 1) beside GN on the same
+    X: 1000 x 500 (sigma_i = 2^(-i/10), r = 20, l = 10, eps = 1e-15 ||A||) and
+    20000 x 10000 (i^-2 over 2000 modes + 1e-8 noise, r = 500, l = 250).  GN
+    time = sketch + core + factors (gn_approx); HMT = AX, its Householder QR and
+    B = Q^T A (gn_hmt)."""
+    res = {}
+    for name, p, reps in (("1000x500_r20", gn_synth.config1(device=dev), 50),
+                          ("20000x10000_r500", gn_synth.config2(device=dev), 3)):
+        A, X, Y, r, l = p.a, p.x, p.y, p.r, p.l
+        m, n = A.shape
+        eps, mode = (p.eps, gn.AUTO) if p.eps > 0 else (10 * 2.0 ** -53, gn.AUTO | gn.EPS_RELATIVE)
+        ws = H.workspace(m, n, r, l, gn.F64)
+        AX = torch.empty(m, r, dtype=torch.float64, device=dev)
+        YtA = torch.empty(r + l, n, dtype=torch.float64, device=dev)
+        c = gn.Core.empty(r, l, dev)
+        F = torch.empty(m, r, dtype=torch.float64, device=dev)
+        G = torch.empty(r, n, dtype=torch.float64, device=dev)
+        Q = torch.empty(m, r, dtype=torch.float64, device=dev)
+        B = torch.empty(r, n, dtype=torch.float64, device=dev)
+        e2 = torch.zeros(1, dtype=torch.float64, device=dev)
+
+        def gn_run():
+            H.approx(A, X, Y, eps, mode, AX, YtA, c, F, G, ws)
+
+        def hmt_run():
+            H.hmt(A, X, Q, B, ws)
+
+        out = {}
+        for nm, f in (("gn", gn_run), ("hmt", hmt_run)):
+            f()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                f()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[nm + "_ms"] = e0.elapsed_time(e1) / reps
+        H.error_fro2(A, F[:, :c.k], G[:c.k], e2, ws)
+        torch.cuda.synchronize()
+        out["gn_err"] = math.sqrt(e2.item())
+        H.error_fro2(A, Q, B, e2, ws)
+        torch.cuda.synchronize()
+        out["hmt_err"] = math.sqrt(e2.item())
+        out["gn_k"] = c.k
+        out["gn_over_hmt_time"] = out["gn_ms"] / out["hmt_ms"]
+        out["gn_over_hmt_err"] = out["gn_err"] / out["hmt_err"]
+        res[name] = out
+        del A, X, Y, AX, YtA, c, F, G, Q, B, ws, p
+        torch.cuda.empty_cache()
+    return res
+
+
+def sketch_state_ops(gn, H, stream, dev, a, Ab, Xb, Yb, eps, mode):
+    """Section 6 on the bench matrix (BF16 operands, FP32 sketches), each timed
+    (CUDA events, best of 3) beside a fresh sketch of the enlarged or updated
+    matrix: the streaming update A <- A + E, resampling r -> r + 100 (l + 50),
+    1024 appended rows, 1024 appended columns, and A_hat W / W A_hat (64
+    vectors) without forming A_hat."""
+    m, n, r = a.m, a.n, a.r
+    l = r // 2
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    AX = torch.empty(m, r, dtype=torch.float32, device=dev)
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device=dev)
+    core = gn.Core.empty(r, l, dev)
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    H.core(YtA, Xb, eps, mode, core, ws)
+    torch.cuda.synchronize()
+    res = {}
+
+    def best(f):
+        f()
+        return _best_ms(f, 3, stream)
+
+    res["fresh_sketch_ms"] = best(lambda: H.sketch(Ab, Xb, Yb, AX, YtA, ws))
+    # streaming update: E of the size of A
+    Eb = H.quantize(gn_synth.gaussian((m, n), 5, 0, device=dev, dtype=torch.float32) * 1e-3)
+    AXu, YtAu = AX.clone(), YtA.clone()
+    wsu = H.update_workspace(m, n, r, l, gn.BF16, dev)
+    res["update_ms"] = best(lambda: H.update(Eb, Xb, Yb, AXu, YtAu, wsu))
+    del Eb, wsu
+    # resampling r -> r + 100, l -> l + 50
+    dr, dl = 100, 50
+    Xd = H.quantize(gn_synth.gaussian((n, dr), 6, 0, device=dev))
+    Yd = H.quantize(gn_synth.gaussian((m, dr + dl), 7, 0, device=dev))
+    AXn = torch.empty(m, r + dr, dtype=torch.float32, device=dev)
+    YtAn = torch.empty(r + l + dr + dl, n, dtype=torch.float32, device=dev)
+    res["resample_ms"] = best(lambda: H.resample(Ab, Xd, Yd, AX, YtA, AXn, YtAn))
+    Xn, Yn = gn.padded(n, r + dr, torch.bfloat16, dev), gn.padded(m, r + l + dr + dl, torch.bfloat16, dev)
+    Xn[:, :r].copy_(Xb)
+    Xn[:, r:].copy_(Xd)
+    Yn[:, :r + l].copy_(Yb)
+    Yn[:, r + l:].copy_(Yd)
+    res["resample_fresh_sketch_ms"] = best(lambda: H.sketch(Ab, Xn, Yn, AXn, YtAn, ws))
+    del Xd, Yd, AXn, YtAn, Xn, Yn
+    # 1024 appended rows and 1024 appended columns
+    mb = nb = 1024
+    Br = H.quantize(gn_synth.gaussian((mb, n), 8, 0, device=dev, dtype=torch.float32))
+    Yr = H.quantize(gn_synth.gaussian((mb, r + l), 9, 0, device=dev))
+    AXr = torch.empty(m + mb, r, dtype=torch.float32, device=dev)
+    YtAc = YtA.clone()
+    res["append_rows_ms"] = best(lambda: H.append_rows(Br, Xb, Yr, AX, YtAc, AXr))
+    Abig = gn.padded(m + mb, n, torch.bfloat16, dev)
+    Abig[:m].copy_(Ab)
+    Abig[m:].copy_(Br)
+    Ybig = gn.padded(m + mb, r + l, torch.bfloat16, dev)
+    Ybig[:m].copy_(Yb)
+    Ybig[m:].copy_(Yr)
+    wsb = H.workspace(m + mb, n, r, l, gn.BF16)
+    res["append_rows_fresh_sketch_ms"] = best(lambda: H.sketch(Abig, Xb, Ybig, AXr, YtAc, wsb))
+    del Br, Yr, AXr, Abig, Ybig, wsb
+    Bc = H.quantize(gn_synth.gaussian((m, nb), 10, 0, device=dev, dtype=torch.float32))
+    Xc = H.quantize(gn_synth.gaussian((nb, r), 11, 0, device=dev))
+    YtAw = torch.empty(r + l, n + nb, dtype=torch.float32, device=dev)
+    AXc = AX.clone()
+    res["append_cols_ms"] = best(lambda: H.append_cols(Bc, Xc, Yb, AXc, YtA, YtAw))
+    Awide = gn.padded(m, n + nb, torch.bfloat16, dev)
+    Awide[:, :n].copy_(Ab)
+    Awide[:, n:].copy_(Bc)
+    Xw = gn.padded(n + nb, r, torch.bfloat16, dev)
+    Xw[:n].copy_(Xb)
+    Xw[n:].copy_(Xc)
+    wsw = H.workspace(m, n + nb, r, l, gn.BF16)
+    res["append_cols_fresh_sketch_ms"] = best(lambda: H.sketch(Awide, Xw, Yb, AXc, YtAw, wsw))
+    del Bc, Xc, YtAw, AXc, Awide, Xw, wsw
+    # A_hat W and W A_hat without forming A_hat (64 vectors)
+    kw = 64
+    W = gn_synth.gaussian((n, kw), 12, 0, device=dev)
+    Wl = gn_synth.gaussian((kw, m), 13, 0, device=dev)
+    o1 = torch.empty(m, kw, dtype=torch.float64, device=dev)
+    o2 = torch.empty(kw, n, dtype=torch.float64, device=dev)
+    res["apply_right_64_ms"] = best(lambda: H.apply(AX, YtA, core, W, o1, 0))
+    res["apply_left_64_ms"] = best(lambda: H.apply(AX, YtA, core, Wl, o2, 1))
+    res["workload"] = (f"{m}x{n}, r={r}, l={l}, BF16 operands: update E {m}x{n}; resample +{dr}/+{dl}; "
+                       f"append {mb} rows / {nb} cols; apply with {kw} vectors")
+    del W, Wl, o1, o2, AXu, YtAu, ws, AX, YtA, core
+    torch.cuda.empty_cache()
+    return res
 
 
 def r2000_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode, r=2000):
     """The same matrix with the larger sketch size, r = 2000, l = 1000 (BF16
-    sketch + FP64 core of 3000 x 2000): approximations/s and the sketch rate."""
+    sketch + FP64 core of 3000 x 2000): approximations/s, the sketch rate and
+    the error against the FP64 A."""
     m, n = a.m, a.n
     l = r // 2
     X64, Y64 = gn_synth.sketches(m, n, r, l, gn_synth.DEFAULT_SEED + 2, device=dev)
@@ -596,10 +935,20 @@ def r2000_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode, r=2000):
     ms = e0.elapsed_time(e1) / reps
     sk = k0.elapsed_time(k1)
     fl = 2.0 * m * n * (2 * r + l)
+    F = torch.empty(m, r, dtype=torch.float64, device=dev)
+    G = torch.empty(r, n, dtype=torch.float64, device=dev)
+    e2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    H.factors(AX, YtA, core, F, G, ws)
+    f1.record(stream)
+    H.error_fro2(A64, F[:, :core.k], G[:core.k], e2, ws)
+    torch.cuda.synchronize()
     out = {"workload": f"{m}x{n}, r={r}, l={l}, bf16 operands, FP64 core, mode AUTO",
            "approx_per_s": 1e3 / ms, "ms_per_step": ms, "sketch_ms": sk,
-           "sketch_tflops": fl / (sk / 1e3) / 1e12, "k": core.k}
-    del Xb, Yb, ws, AX, YtA, core
+           "sketch_tflops": fl / (sk / 1e3) / 1e12, "k": core.k, "factors_ms": f0.elapsed_time(f1),
+           "err": math.sqrt(e2.item())}
+    del Xb, Yb, ws, AX, YtA, core, F, G
     torch.cuda.empty_cache()
     return out
 
@@ -607,24 +956,16 @@ def r2000_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode, r=2000):
 def adjoint_measurement(gn, H, stream, dev, m=4096, n=4096, r=256, l=128):
     """Forward (dense A_hat) and hand-written adjoint of <G, A_hat> on the
     4096 x 4096 FP32 case (sigma_i = i^-1.5 over 1024 modes + 1e-6 noise,
-    r = 256, l = 128), each timed with CUDA events after one warm-up."""
+    r = 256, l = 128), each timed with CUDA events (best of 3 after a warm-up)."""
     p, G = gn_synth.config4(device=dev, m=m, n=n, r=r, l=l, dtype=torch.float32)
     A, X, Y = p.a, p.x, p.y
     ws = H.backward_workspace(m, n, r, l, gn.F32)
     Ah = torch.empty_like(A)
     dA = torch.empty_like(A)
-    H.forward_dense(A, X, Y, Ah, ws)
-    H.backward(A, X, Y, G, dA, ws)
-    torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    e[0].record(stream)
-    H.forward_dense(A, X, Y, Ah, ws)
-    e[1].record(stream)
-    H.backward(A, X, Y, G, dA, ws)
-    e[2].record(stream)
-    torch.cuda.synchronize()
-    return {"workload": f"{m}x{n} FP32, r={r}, l={l}, loss <G, A_hat>", "fwd_ms": e[0].elapsed_time(e[1]),
-            "bwd_ms": e[1].elapsed_time(e[2]), "grad_norm": float(dA.norm().item())}
+    fwd = _best_ms(lambda: H.forward_dense(A, X, Y, Ah, ws), 4, stream)
+    bwd = _best_ms(lambda: H.backward(A, X, Y, G, dA, ws), 4, stream)
+    return {"workload": f"{m}x{n} FP32, r={r}, l={l}, loss <G, A_hat>", "fwd_ms": fwd, "bwd_ms": bwd,
+            "grad_norm": float(dA.norm().item())}
 
 
 def batched_measurement(gn, H, stream, dev, count=512, steps=10):
@@ -666,7 +1007,6 @@ def batched_measurement(gn, H, stream, dev, count=512, steps=10):
     g.replay()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches0 = gn.kernel_launches()
     e0.record(stream)
     for _ in range(steps):
         g.replay()

@@ -67,7 +67,10 @@ typedef enum {
     /* Flag OR'd into the mode: eps is relative to ||C||_2 (estimated by 6 power
      * iterations on R from the all-ones vector), so eps = 10u reproduces the
      * paper's eps = 10u for ||A|| = 1 and O(1) sketches (Section 4.1). */
-    GN_EPS_RELATIVE = 0x100
+    GN_EPS_RELATIVE = 0x100,
+    /* Flag OR'd into the mode of gn_core (SGN / AUTO): return without waiting
+     * for k; the host fields arrive with gn_core_finish (see there). */
+    GN_CORE_DEFER = 0x200
 } gn_mode;
 
 typedef struct {
@@ -230,10 +233,27 @@ gn_status gn_sketch(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat*
  *   of Y^T A on the tensor cores (FP32 accumulate per slice, slices summed in
  *   FP64).
  *   eps >= 0 is an absolute threshold on |R_ii| (the caller scales it).
- * Blocks the host once in SGN / AUTO mode to read k (the later shapes depend
- * on it); PLAIN mode does not block. */
+ * In SGN / AUTO mode the host waits once, for the diagnostics alone (k sizes
+ * the second QR and the factors), while the formation of Q continues on the
+ * device; PLAIN mode does not wait.  A NaN or infinity in R latches
+ * GN_ERR_NONFINITE in the device status word, and in SGN / AUTO mode a NaN
+ * estimate also returns GN_ERR_NONFINITE.
+ * With GN_CORE_DEFER in `mode` (SGN / AUTO) the call does not wait at all: it
+ * returns with core->k = core->sgn = -1 and the handle holds the pending core
+ * until gn_core_finish.  The caller may meanwhile enqueue other work (for
+ * example the next approximation's sketch on another handle), but must not
+ * reuse ws, the core's buffers or this handle's gn_core before finishing. */
 gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, int32_t mode,
                   gn_core_t* core, void* ws, size_t ws_bytes);
+
+/* Completes the core that gn_core left pending on this handle (GN_CORE_DEFER):
+ * waits for its diagnostics (not for the rest of the handle's stream), fills
+ * k, sgn, rinv_est, c_norm_est and eps_abs, and enqueues the second QR of
+ * Section 5.1.1 when the truncated branch is taken.  `core` must be the
+ * descriptor given to that gn_core (same R buffer): GN_ERR_INVALID_ARG
+ * otherwise; GN_OK at once when nothing is pending and core->k >= 1.  Returns
+ * GN_ERR_NONFINITE as gn_core does. */
+gn_status gn_core_finish(gn_handle h, gn_core_t* core);
 
 /* ------------------------------------------------------------- Algorithm 2, step 3 */
 

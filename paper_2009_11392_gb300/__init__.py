@@ -30,6 +30,7 @@ __all__ = [
 F64, F32, BF16, BF16X2, E4M3 = 0, 1, 2, 3, 4
 PLAIN, SGN, AUTO = 0, 1, 2
 EPS_RELATIVE = 0x100
+CORE_DEFER = 0x200
 
 # Every symbol declared in include/gn.h.
 ABI_SYMBOLS = (
@@ -40,7 +41,7 @@ ABI_SYMBOLS = (
     "gn_forward_dense", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
     "gn_batched_set_policy", "gn_batched_tune", "gn_set_fp64_tc", "gn_dgemm_tc_workspace_size", "gn_dgemm_tc",
     "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update", "gn_resample",
-    "gn_append_rows", "gn_append_cols", "gn_resample_workspace_size",
+    "gn_append_rows", "gn_append_cols", "gn_resample_workspace_size", "gn_core_finish",
 )
 
 
@@ -97,6 +98,7 @@ def _load():
         "gn_quantize": ([P, M, M], I32),
         "gn_sketch": ([P, M, M, M, M, M, P, SZ], I32),
         "gn_core": ([P, M, M, D, I32, C, P, SZ], I32),
+        "gn_core_finish": ([P, C], I32),
         "gn_factors": ([P, M, M, C, M, M, P, SZ], I32),
         "gn_approx": ([P, M, M, M, D, I32, M, M, C, M, M, P, SZ], I32),
         "gn_error_fro2": ([P, M, M, M, P, P, SZ], I32),
@@ -366,9 +368,17 @@ class Handle:
                              ws.numel()), "gn_sketch")
 
     def core(self, YtA, X, eps: float, mode: int, core: Core, ws) -> Core:
+        """gn_core; with CORE_DEFER in ``mode`` the host fields stay pending
+        (k = -1) until ``core_finish``."""
         c = core.cstruct()
         _check(lib.gn_core(self._h, ctypes.byref(mat(YtA)), ctypes.byref(mat(X)), float(eps), int(mode),
                            ctypes.byref(c), ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_core")
+        core.update(c)
+        return core
+
+    def core_finish(self, core: Core) -> Core:
+        c = core.cstruct()
+        _check(lib.gn_core_finish(self._h, ctypes.byref(c)), "gn_core_finish")
         core.update(c)
         return core
 
@@ -412,6 +422,12 @@ class Handle:
         _check(lib.gn_update(self._h, ctypes.byref(mat(E, E_lo)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
                              ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.c_void_p(ws.data_ptr()),
                              ws.numel()), "gn_update")
+
+    def update_workspace(self, m, n, r, l, op_dtype, device=None) -> torch.Tensor:
+        """Scratch for update / append_rows / append_cols on an m x n block."""
+        b = ctypes.c_size_t()
+        _check(lib.gn_update_workspace_size(m, n, r, l, op_dtype, ctypes.byref(b)), "gn_update_workspace_size")
+        return torch.empty(int(b.value), dtype=torch.uint8, device=device or "cuda")
 
     def _scratch(self, nbytes, device):
         with torch.cuda.stream(self.stream):   # freed in order with the handle's stream

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 
 #include <atomic>
@@ -459,16 +460,22 @@ gn_status gn_create(gn_handle* out, void* stream) {
         delete h;
         return GN_ERR_CUDA;
     }
+    h->pend.active = 0;
+    void* pin = nullptr;
     if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_crit0, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_crit1, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_crit1, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_defer, cudaEventDisableTiming) != cudaSuccess ||
+        cudaHostAlloc(&pin, 64, cudaHostAllocDefault) != cudaSuccess) {
         cudaStreamDestroy(h->crit);
         cudaStreamDestroy(h->side);
         cudaFree(h->dstatus);
         delete h;
         return GN_ERR_CUDA;
     }
+    h->pin_diag = static_cast<double*>(pin);
+    h->pin_k = reinterpret_cast<int32_t*>(h->pin_diag + 4);
     *out = h;
     return GN_OK;
 }
@@ -482,6 +489,8 @@ gn_status gn_destroy(gn_handle h) {
     cudaEventDestroy(h->ev_join);
     cudaEventDestroy(h->ev_crit0);
     cudaEventDestroy(h->ev_crit1);
+    cudaEventDestroy(h->ev_defer);
+    cudaFreeHost(h->pin_diag);
     cudaStreamDestroy(h->crit);
     cudaStreamDestroy(h->side);
     cudaFree(h->dstatus);
@@ -590,8 +599,10 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
                   gn_core_t* core, void* ws, size_t ws_bytes) {
     if (!h || !YtA || !X || !core || !ws) return GN_ERR_INVALID_ARG;
     const int eps_rel = (mode & GN_EPS_RELATIVE) ? 1 : 0;
-    mode &= ~GN_EPS_RELATIVE;
+    const int defer = (mode & GN_CORE_DEFER) ? 1 : 0;
+    mode &= ~(GN_EPS_RELATIVE | GN_CORE_DEFER);
     if (mode < GN_MODE_PLAIN || mode > GN_MODE_AUTO || !(eps >= 0.0)) return GN_ERR_INVALID_ARG;
+    if (defer && h->pend.active) return GN_ERR_INVALID_ARG;   // finish the pending core first
     const long long n = X->rows, r = X->cols, rl = YtA->rows, l = rl - r;
     if (r < 1 || l < 1 || n < r) return GN_ERR_SHAPE;
     GN_TRY(check_mat(YtA, rl, n));
@@ -692,27 +703,63 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     core->rinv_est = 0.0;
     core->c_norm_est = 0.0;
     core->eps_abs = eps;
-    if (mode == GN_MODE_PLAIN) return qr_form_q(h, W, rl, r, r, core->Q, r, inner, inner_bytes, qoz, qoz_bytes);
+    if (mode == GN_MODE_PLAIN) {
+        GN_TRY(latch_nonfinite_upper(h, core->R, r, r));
+        return qr_form_q(h, W, rl, r, r, core->Q, r, inner, inner_bytes, qoz, qoz_bytes);
+    }
 
     GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
     GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
     {
         gn_handle_s side = *h;
         side.stream = h->side;
+        GN_TRY(latch_nonfinite_upper(&side, core->R, r, r));
         GN_TRY(core_diagnostics(&side, core->R, r, r, eps, eps_rel, 1, DIAG_ITERS, diag_d, k_d, zscr,
                                 sizeof(double) * 2 * std::max<long long>(r, 64)));
+        // k and the three diagnostics to the pinned host words as soon as they exist
+        GN_CUDA_TRY(cudaMemcpyAsync(h->pin_k, k_d, sizeof(int32_t), cudaMemcpyDeviceToHost, h->side));
+        GN_CUDA_TRY(cudaMemcpyAsync(h->pin_diag, diag_d, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->side));
+        GN_CUDA_TRY(cudaEventRecord(h->ev_defer, h->side));
     }
     GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
     GN_TRY(qr_form_q(h, W, rl, r, r, core->Q, r, inner, inner_bytes, qoz, qoz_bytes));
     GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-    int k_h = 0;
-    double diag_h[3] = {0.0, 0.0, 0.0};
-    GN_CUDA_TRY(cudaMemcpyAsync(&k_h, k_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    GN_CUDA_TRY(cudaMemcpyAsync(diag_h, diag_d, sizeof(diag_h), cudaMemcpyDeviceToHost, h->stream));
-    GN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->pend.active = 1;
+    h->pend.mode = mode;
+    h->pend.r = r;
+    h->pend.R = core->R;
+    h->pend.Q2 = core->Q2;
+    h->pend.R2 = core->R2;
+    h->pend.W2 = W2;
+    h->pend.inner = inner;
+    h->pend.inner_bytes = inner_bytes;
+    if (defer) {   // the host fields arrive with gn_core_finish
+        core->k = -1;
+        core->sgn = -1;
+        return GN_OK;
+    }
+    return gn_core_finish(h, core);
+}
+
+gn_status gn_core_finish(gn_handle h, gn_core_t* core) {
+    if (!h || !core) return GN_ERR_INVALID_ARG;
+    if (!h->pend.active) return core->k >= 1 ? GN_OK : GN_ERR_INVALID_ARG;   // nothing pending
+    if (core->R != h->pend.R) return GN_ERR_INVALID_ARG;                     // another core is pending
+    h->pend.active = 0;
+    // Waits for the diagnostics only (the side stream), not for the formation of Q.
+    GN_CUDA_TRY(cudaEventSynchronize(h->ev_defer));
+    const long long r = h->pend.r;
+    const int mode = h->pend.mode;
+    const long long k_h = *h->pin_k;
+    const double diag_h[3] = {h->pin_diag[0], h->pin_diag[1], h->pin_diag[2]};
+    core->k = r;
+    core->sgn = 0;
     core->rinv_est = diag_h[0];
     core->c_norm_est = diag_h[1];
     core->eps_abs = diag_h[2];
+    // A NaN in the core makes the estimates NaN (an exactly zero pivot makes the
+    // estimate of ||R^{-1}|| infinite, which is the SGN branch, not an error).
+    if (std::isnan(diag_h[0]) || std::isnan(diag_h[1]) || std::isnan(diag_h[2])) return GN_ERR_NONFINITE;
     // Section 5.1.2: switch when ||R^{-1}|| >> 1/u in the paper's normalisation,
     // where eps = 10u; ">>" read as a factor 10, i.e. est * eps >= 100.
     const int use_sgn = (mode == GN_MODE_SGN) || (diag_h[2] > 0.0 && diag_h[0] * diag_h[2] >= 100.0);
@@ -722,8 +769,9 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     if (k_h >= r) return GN_OK;
     if (k_h == 0) return GN_ERR_NONFINITE;   // every |R_ii| <= eps: nothing left of the core
     // Section 5.1.1: QR of R_1^T (r x k), R_1 = R[0:k, :].
-    GN_TRY(transpose_rows_f64(h, core->R, k_h, r, r, k_h, W2, k_h));
-    GN_TRY(householder_qr(h, W2, r, k_h, k_h, core->Q2, r, core->R2, r, inner, inner_bytes));
+    GN_TRY(transpose_rows_f64(h, core->R, k_h, r, r, k_h, h->pend.W2, k_h));
+    GN_TRY(householder_qr(h, h->pend.W2, r, k_h, k_h, core->Q2, r, core->R2, r, h->pend.inner,
+                          h->pend.inner_bytes));
     return GN_OK;
 }
 

@@ -1423,6 +1423,22 @@ __global__ void transpose_rows_kernel(const double* __restrict__ s, long long ro
     }
 }
 
+// Latch GN_ERR_NONFINITE when the upper triangle of R (r x r) holds a NaN or an
+// infinity: a non-finite entry anywhere in the core reaches R's last columns.
+__global__ void nonfinite_upper_kernel(const double* __restrict__ R, long long r, long long ldr,
+                                       int32_t* status) {
+    const long long total = r * r;
+    bool bad = false;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / r, j = e - i * r;
+        if (j >= i && !isfinite(R[i * ldr + j])) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
+        if (atomicCAS(&status[GN_DEV_STATUS], 0, GN_ERR_NONFINITE) == 0) status[GN_DEV_WHERE] = 20;
+    }
+}
+
 __global__ void zero_kernel(double* p, long long rows, long long cols, long long ld) {
     const long long total = rows * cols;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
@@ -1457,6 +1473,12 @@ gn_status dgemm_b32(gn_handle h, long long M, long long N, long long K, double a
                     long long lda, int ta, const float* B, long long ldb, int tb, double beta, double* C,
                     long long ldc, double* ws, size_t ws_bytes) {
     return dgemm_impl<double, float>(h, M, N, K, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, ws, ws_bytes);
+}
+
+gn_status latch_nonfinite_upper(gn_handle h, const double* R, long long r, long long ldr) {
+    nonfinite_upper_kernel<<<ew_blocks(h, r * r), 256, 0, h->stream>>>(R, r, ldr, h->dstatus); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
 }
 
 gn_status set_zero_f64(gn_handle h, double* p, long long rows, long long cols, long long ld) {

@@ -27,6 +27,18 @@ struct gn_handle_s {
     int batched_policy;        // tile policy of the next gn_batched_prepare
     int fp64_g;                // gn_factors: FP64 G even for FP32 Y^T A
     int fp64_tc;               // gn_factors: digit-sliced tensor-core FP64 products (FP32 AX)
+    // gn_core with GN_CORE_DEFER: the core whose k and diagnostics are still on
+    // their way to the pinned host words; gn_core_finish completes it.
+    cudaEvent_t ev_defer;
+    int32_t* pin_k;            // pinned host: k
+    double* pin_diag;          // pinned host: est ||R^-1||, est ||C||, eps_abs
+    struct {
+        int active;
+        int mode;
+        long long r;
+        double *R, *Q2, *R2, *W2, *inner;
+        size_t inner_bytes;
+    } pend;
 };
 
 #define GN_CUDA_TRY(expr)                                   \
@@ -199,5 +211,8 @@ gn_status error_fro2(gn_handle h, const void* A, int a_dtype, const void* A_lo, 
                      long long ldg, long long k, double* out, double* ws, size_t ws_bytes);
 size_t error_ws_bytes(long long m, long long n, int sm_count);
 gn_status set_zero_f64(gn_handle h, double* p, long long rows, long long cols, long long ld);
+// Latch GN_ERR_NONFINITE in the handle's status word if R's upper triangle
+// (r x r, FP64) holds a NaN or an infinity.
+gn_status latch_nonfinite_upper(gn_handle h, const double* R, long long r, long long ldr);
 
 }  // namespace gn

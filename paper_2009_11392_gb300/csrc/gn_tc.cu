@@ -328,6 +328,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const unsigned long long limit = p.wait_limit_ns;
+    // Draining the CTA's own copies and MMAs (which always complete) before its
+    // shared and tensor memory are released keeps at least a second, however
+    // short the limit on waits for other roles.
+    const unsigned long long drain = limit > 1000000000ULL ? limit : 1000000000ULL;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             for (int s = 0; s < STAGES; ++s)
                 if (issued_mask & (1u << s)) {
                     volatile int no_abort = 0;
-                    if (!mbar_wait(full_bar(s), (last_parity >> s) & 1u, limit, &no_abort))
+                    if (!mbar_wait(full_bar(s), (last_parity >> s) & 1u, drain, &no_abort))
                         latch(p.status, GN_ERR_TIMEOUT, 2, abort_flag);
                 }
         }
@@ -514,7 +518,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             if (issued_any) {   // all MMAs complete before tensor memory is released
                 tc_commit(final_bar);
                 volatile int no_abort = 0;
-                if (!mbar_wait(final_bar, 0, limit, &no_abort))
+                if (!mbar_wait(final_bar, 0, drain, &no_abort))
                     latch(p.status, GN_ERR_TIMEOUT, 5, abort_flag);
             }
         }

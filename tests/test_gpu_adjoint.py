@@ -101,3 +101,21 @@ def test_autograd_function_gradcheck(gn, H):
     dA = torch.empty_like(tA)
     H.backward(tA.detach(), tX, tY, Gup, dA, ws)
     assert torch.allclose(tA.grad, dA, rtol=1e-12, atol=1e-12)
+
+
+def test_adjoint_config4_fp32_against_oracle(gn, H):
+    """The 4096 x 4096 FP32 case the bench times (sigma_i = i^-1.5 over 1024
+    modes + 1e-6 noise, r = 256, l = 128): the FP32 GPU gradient against the
+    FP64 oracle's adjoint on the same (FP32-rounded) inputs, 1e-3 relative."""
+    import gn_synth
+    m = n = 4096
+    r, l = 256, 128
+    p, G = gn_synth.config4(device="cuda", m=m, n=n, r=r, l=l, dtype=torch.float32)
+    A, X, Y = p.a, p.x, p.y
+    ws = H.backward_workspace(m, n, r, l, gn.F32)
+    dA = torch.empty_like(A)
+    H.backward(A, X, Y, G, dA, ws)
+    assert H.sync_status() == 0
+    h = lambda t: t.double().cpu().numpy()
+    ref = O.gn_backward(h(A), h(X), h(Y), h(G))
+    assert rel(h(dA), ref) <= 1e-3

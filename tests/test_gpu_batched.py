@@ -150,3 +150,50 @@ def test_batched_autotuner_keeps_results(gn, H):
         for p, (ax, yta) in zip(probs, ref):
             assert torch.equal(p["AX"], ax) and torch.equal(p["YtA"], yta)
     H.batched_set_policy(0)
+
+
+def test_batched_512_problem_batch_spot_parity(gn, H):
+    """The bench's own batch: 512 problems, m ~ U[256,4096], n ~ U[128,m],
+    r ~ U{16..128}, l = r/2, each W1 diag(2^(-i/10)) W2^T + 1e-8 N with its own
+    seed, BF16 operands, AUTO mode with eps = 10 u32 relative.  On 16 sampled
+    problems: both sketches against the oracle's products of the same
+    (BF16-exact) operands within the FP32 accumulation bound, and the core
+    against the oracle's Householder QR of (Y^T A) X formed from the GPU's
+    sketch: C = QR to the FP32 level of the core product, Q orthonormal,
+    diag(R) >= 0, R within kappa(R) times that level of the oracle's R, and k."""
+    shapes = gn_synth.batched_shapes(512)
+    probs = []
+    for i, (m, n, r, l) in enumerate(shapes):
+        p = gn_synth.config5_problem(i, (m, n, r, l), device="cuda")
+        d = {"A": H.quantize(p.a), "X": H.quantize(p.x), "Y": H.quantize(p.y)}
+        del p
+        d["AX"] = torch.empty(m, r, dtype=torch.float32, device="cuda")
+        d["YtA"] = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
+        for nm, (a, b) in (("Q", (r + l, r)), ("R", (r, r)), ("Q2", (r, r)), ("R2", (r, r))):
+            d[nm] = torch.empty(a, b, dtype=torch.float64, device="cuda")
+        d["k"] = torch.empty(1, dtype=torch.int32, device="cuda")
+        probs.append(d)
+    ws = H.batched_prepare(probs)
+    eps = 10 * 2.0 ** -24
+    H.batched_run(eps, gn.AUTO | gn.EPS_RELATIVE, ws)
+    torch.cuda.synchronize()
+    assert H.sync_status() == 0
+    rng = np.random.default_rng(512)
+    for i in sorted(rng.choice(len(shapes), 16, replace=False)):
+        m, n, r, l = shapes[i]
+        p = probs[i]
+        A, X, Y = (p[k].double().cpu().numpy() for k in ("A", "X", "Y"))
+        oAX, oYtA = O.sketch(A, X, Y)
+        assert np.all(np.abs(p["AX"].double().cpu().numpy() - oAX) <= 2 * n * 2.0 ** -24 * (np.abs(A) @ np.abs(X)))
+        YtA = p["YtA"].double().cpu().numpy()
+        assert np.all(np.abs(YtA - oYtA) <= 2 * m * 2.0 ** -24 * (np.abs(Y).T @ np.abs(A)))
+        C = YtA @ X
+        Qb, Rb = p["Q"].cpu().numpy(), p["R"].cpu().numpy()
+        d = np.linalg.norm(C - Qb @ Rb) / np.linalg.norm(C)
+        assert d <= 6 * n * 2.0 ** -24
+        assert np.linalg.norm(Qb.T @ Qb - np.eye(r)) <= 1e-12 * r
+        assert np.all(np.diag(Rb) >= 0) and np.allclose(Rb, np.triu(Rb))
+        oc = O.core(YtA, X, eps, O.AUTO, eps_relative=True, diag_iters=6)
+        kappa = np.linalg.cond(oc["R"])
+        assert np.linalg.norm(Rb - oc["R"]) <= (10 * kappa * d + 1e-12) * np.linalg.norm(oc["R"])
+        assert int(p["k"].item()) == oc["k"]

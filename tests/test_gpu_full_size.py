@@ -117,3 +117,90 @@ def test_full_size_factors_tensor_core_vs_fp64_units(gn, H, run):
     assert d <= 1e-11 * torch.linalg.norm(F0).item()
     bound = 4 * (R + L) * U32 * (core.Q.abs().T @ run["YtA"].double().abs())
     assert torch.all((G1 - G0).abs() <= bound)
+
+
+def test_full_size_factors_sampled_rows_against_oracle(gn, H, run):
+    """The tensor-core triangular solve F R = AX (the bench's path) against the
+    oracle's column-oriented back substitution on 64 sampled rows of the same
+    AX with the GPU's R (rows of F are independent solves), and G against
+    Q_1^T (Y^T A) on 64 sampled columns within the FP32 accumulation bound."""
+    core, F, G = run["core"], run["F"], run["G"]
+    rng = np.random.default_rng(17)
+    rows = np.sort(rng.choice(M, 64, replace=False))
+    cols = np.sort(rng.choice(N, 64, replace=False))
+    Rg = npy(core.R)
+    AXs = npy(run["AX"])[rows]
+    Fo = O.right_solve_upper(AXs, Rg)
+    Fs = npy(F)[rows]
+    assert rel(Fs, Fo) <= 1e-10
+    Q1 = npy(core.Q)
+    YtAs = npy(run["YtA"])[:, cols]
+    Go = Q1.T @ YtAs
+    bound = 4 * (R + L) * U32 * (np.abs(Q1).T @ np.abs(YtAs))
+    assert np.all(np.abs(npy(G)[:, cols] - Go) <= bound)
+
+
+@pytest.fixture(scope="module")
+def run2000(gn, H, run):
+    """r = 2000, l = 1000 on the bench's shape with integer inputs (every AX and
+    Y^T A sum an integer below 2^24), through the C ABI: sketch, core (AUTO,
+    relative eps), factors."""
+    r, l = 2000, 1000
+    g = torch.Generator(device="cuda").manual_seed(4001)
+
+    def draw(rows, cols):
+        return torch.randint(-3, 4, (rows, cols), generator=g, device="cuda", dtype=torch.int8)
+
+    A8 = run["A8"]
+    X8, Y8 = draw(N, r), draw(M, r + l)
+    Xb, Yb = H.quantize(X8.double()), H.quantize(Y8.double())
+    ws = H.workspace(M, N, r, l, gn.BF16)
+    AX = torch.empty(M, r, dtype=torch.float32, device="cuda")
+    YtA = torch.empty(r + l, N, dtype=torch.float32, device="cuda")
+    core = gn.Core.empty(r, l, "cuda")
+    F = torch.zeros(M, r, dtype=torch.float64, device="cuda")
+    G = torch.zeros(r, N, dtype=torch.float64, device="cuda")
+    H.sketch(run["Ab"], Xb, Yb, AX, YtA, ws)
+    H.core(YtA, Xb, 10 * U32, gn.AUTO | gn.EPS_RELATIVE, core, ws)
+    H.factors(AX, YtA, core, F, G, ws)
+    assert H.sync_status() == 0
+    out = dict(X8=X8, Y8=Y8, AX=AX, YtA=YtA, core=core, F=F, G=G, ws=ws, r=r, l=l)
+    yield out
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_r2000_sketch_factors_and_error(gn, H, run, run2000):
+    """r = 2000: sampled sketch rows / columns bit for bit, sampled rows of F
+    against the oracle's back substitution with the GPU's R, sampled columns of
+    G within the FP32 bound, and the fused error kernel against numpy on a
+    64-row block (the full n and k = r width)."""
+    d = run2000
+    r, l, core = d["r"], d["l"], d["core"]
+    assert core.k == r and core.sgn == 0
+    rng = np.random.default_rng(23)
+    rows = np.sort(rng.choice(M, 64, replace=False))
+    cols = np.sort(rng.choice(N, 64, replace=False))
+    rows_t = torch.from_numpy(rows).cuda()
+    A8 = run["A8"]
+    Ar = A8[rows_t].double().cpu().numpy()
+    X = d["X8"].double().cpu().numpy()
+    assert np.array_equal(npy(d["AX"])[rows], Ar @ X)
+    Ac = A8[:, torch.from_numpy(cols).cuda()].double()
+    assert np.array_equal(npy(d["YtA"])[:, cols], (d["Y8"].double().T @ Ac).cpu().numpy())
+    Rg = npy(core.R)
+    assert np.all(np.diag(Rg) >= 0) and np.allclose(Rg, np.triu(Rg))
+    Fo = O.right_solve_upper(npy(d["AX"])[rows], Rg)
+    assert rel(npy(d["F"])[rows], Fo) <= 1e-10
+    Q1 = npy(core.Q)
+    YtAs = npy(d["YtA"])[:, cols]
+    bound = 4 * (r + l) * U32 * (np.abs(Q1).T @ np.abs(YtAs))
+    assert np.all(np.abs(npy(d["G"])[:, cols] - Q1.T @ YtAs) <= bound)
+    # fused error on a 64-row block: ||A_s - F_s G||_F^2 against numpy
+    As = A8[rows_t].double().contiguous()
+    Fs = d["F"][rows_t].contiguous()
+    e2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    H.error_fro2(As, Fs, d["G"], e2, d["ws"])
+    assert H.sync_status() == 0
+    ref = np.linalg.norm(As.cpu().numpy() - npy(Fs) @ npy(d["G"])) ** 2
+    assert abs(e2.item() - ref) <= 1e-9 * ref
