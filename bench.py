@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements and the CPU baseline")
     ap.add_argument("--op", default="bf16", choices=["bf16", "e4m3"],
                     help="sketch operand type of the timed step (e4m3: per-128x128-tile scales)")
+    ap.add_argument("--only", default=None, choices=["batched", "adjoint", "fp64_cases"],
+                    help="run one side measurement alone and print its JSON (for profiling it)")
     return ap.parse_args()
 
 
@@ -281,6 +283,15 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if a.only:
+        stream = torch.cuda.Stream(device=dev)
+        torch.cuda.set_stream(stream)
+        H = gn.Handle(stream)
+        f = {"batched": lambda: batched_measurement(gn, H, stream, dev, steps=max(3, a.steps)),
+             "adjoint": lambda: adjoint_measurement(gn, H, stream, dev),
+             "fp64_cases": lambda: fp64_cases(gn, H, stream, dev)}[a.only]
+        print(json.dumps({"only": a.only, "result": f()}), flush=True)
+        return
     m, n, r = a.m, a.n, a.r
     l = r // 2
     nf = max(1, a.inflight)

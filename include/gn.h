@@ -139,6 +139,15 @@ gn_status gn_sync_status(gn_handle h);
  * kernel drains its in-flight copies, frees its tensor memory and returns. */
 gn_status gn_set_wait_limit(gn_handle h, uint64_t ns);
 
+/* Test hook for the timeout path above (on = 1 / 0).  While on, the epilogue
+ * warps of every tensor-core sketch launch on this handle first wait on an
+ * mbarrier that nothing ever completes; that bounded wait runs out after the
+ * wait limit, latches GN_ERR_TIMEOUT and stops the launch, whose other roles
+ * then drain their copies and MMAs, free tensor memory and return.  The
+ * launch's outputs are then incomplete.  Nothing faults or hangs; the handle
+ * stays usable once the hook is off.  Off by default. */
+gn_status gn_set_stall_test(gn_handle h, int32_t on);
+
 /* Precision of the factor G = Q_1^T (Y^T A) in gn_factors / gn_approx when
  * Y^T A is GN_F32 (the tensor-core sketches).  0 (default): on the tensor
  * cores from three BF16 slices of each factor with FP32 accumulation, i.e. at

@@ -42,6 +42,7 @@ ABI_SYMBOLS = (
     "gn_batched_set_policy", "gn_batched_tune", "gn_set_fp64_tc", "gn_dgemm_tc_workspace_size", "gn_dgemm_tc",
     "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update", "gn_resample",
     "gn_append_rows", "gn_append_cols", "gn_resample_workspace_size", "gn_core_finish",
+    "gn_set_stall_test",
 )
 
 
@@ -91,6 +92,7 @@ def _load():
         "gn_set_stream": ([P, P], I32),
         "gn_sync_status": ([P], I32),
         "gn_set_wait_limit": ([P, ctypes.c_uint64], I32),
+        "gn_set_stall_test": ([P, I32], I32),
         "gn_set_fp64_g": ([P, I32], I32),
         "gn_status_string": ([I32], ctypes.c_char_p),
         "gn_device_sm_count": ([P], ctypes.c_int),
@@ -210,7 +212,7 @@ class E4M3Mat:
             v = self.data.view(torch.float8_e4m3fn).to(torch.float64)
         else:
             v = self.data_t.view(torch.float8_e4m3fn).to(torch.float64).t()
-        return v * sc
+        return (v * sc).contiguous()
 
 
 def _cols(t) -> int:
@@ -295,6 +297,11 @@ class Handle:
 
     def set_wait_limit(self, ns: int):
         _check(lib.gn_set_wait_limit(self._h, int(ns)), "gn_set_wait_limit")
+
+    def set_stall_test(self, on: bool):
+        """Test hook: sketch launches wait on a barrier nothing completes, so
+        the bounded wait runs out (GN_ERR_TIMEOUT)."""
+        _check(lib.gn_set_stall_test(self._h, 1 if on else 0), "gn_set_stall_test")
 
     def set_fp64_g(self, on: bool):
         """G = Q_1^T (Y^T A) in FP64 (True) or on the tensor cores (False, default) for FP32 Y^T A."""

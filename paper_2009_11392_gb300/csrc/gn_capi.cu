@@ -442,6 +442,7 @@ gn_status gn_create(gn_handle* out, void* stream) {
     h->batched_policy = 0;
     h->fp64_g = 0;
     h->fp64_tc = 1;
+    h->stall_test = 0;
     if (cudaMalloc(&h->dstatus, 64) != cudaSuccess) {
         delete h;
         return GN_ERR_CUDA;
@@ -536,6 +537,12 @@ gn_status gn_dgemm_tc(gn_handle h, int64_t M, int64_t N, int64_t K, double alpha
 gn_status gn_set_wait_limit(gn_handle h, uint64_t ns) {
     if (!h || ns == 0) return GN_ERR_INVALID_ARG;
     h->wait_limit_ns = ns;
+    return GN_OK;
+}
+
+gn_status gn_set_stall_test(gn_handle h, int32_t on) {
+    if (!h || (on != 0 && on != 1)) return GN_ERR_INVALID_ARG;
+    h->stall_test = on;
     return GN_OK;
 }
 

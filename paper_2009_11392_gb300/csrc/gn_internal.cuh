@@ -27,6 +27,7 @@ struct gn_handle_s {
     int batched_policy;        // tile policy of the next gn_batched_prepare
     int fp64_g;                // gn_factors: FP64 G even for FP32 Y^T A
     int fp64_tc;               // gn_factors: digit-sliced tensor-core FP64 products (FP32 AX)
+    int stall_test;            // gn_set_stall_test: the next sketch launches wait on a barrier nothing completes
     // gn_core with GN_CORE_DEFER: the core whose k and diagnostics are still on
     // their way to the pinned host words; gn_core_finish completes it.
     cudaEvent_t ev_defer;
@@ -99,6 +100,7 @@ struct TcParams {
     int32_t* status;
     unsigned long long wait_limit_ns;
     int f8;                    // 1: e4m3 operands (K-major, block-scaled MMA, bn = 128)
+    int stall_test;            // 1: the epilogue first waits on a barrier nothing completes (tests the timeout path)
     // Balanced last round: cluster tiles [split_base, split_base + nsplit) run
     // as two halves of their K range each (work items split_base + 2u, + 2u + 1),
     // adding into a pre-zeroed D.

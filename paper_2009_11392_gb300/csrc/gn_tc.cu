@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
     auto tfull_bar = [&](int a) { return bars + 8u * (2 * STAGES + a); };
     auto tempty_bar = [&](int a) { return bars + 8u * (2 * STAGES + 2 + a); };
     const uint32_t final_bar = bars + 8u * (2 * STAGES + 4);
+    const uint32_t stall_bar = bars + 8u * (2 * STAGES + 6);   // never completed (timeout-path test)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 5));
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -343,6 +344,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             mbar_init(tempty_bar(a), 128);
         }
         mbar_init(final_bar, 1);
+        mbar_init(stall_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -528,7 +530,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
         const int q = warp & 3;   // TMEM lane quarter this warp may access
         int acc = 0;
         uint32_t aphase = 0;
-        for (int t = cid; t < p.total_tiles; t += ncl) {
+        bool stalled = false;
+        if (p.stall_test) {   // a wait that nothing can satisfy: runs out at the limit
+            stalled = !mbar_wait(stall_bar, 0, limit, abort_flag);
+            if (stalled && lane == 0) latch(p.status, GN_ERR_TIMEOUT, 7, abort_flag);
+        }
+        for (int t = cid; t < p.total_tiles && !stalled; t += ncl) {
             const TileCoord c = decode_tile<GROUPED>(p, t);
             const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
             const bool got = mbar_wait(tfull_bar(acc), aphase, limit, abort_flag);
@@ -717,6 +724,7 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
     p->gmaps = nullptr;
     p->status = h->dstatus;
     p->wait_limit_ns = h->wait_limit_ns;
+    p->stall_test = h->stall_test;
     if (total == 0) return GN_OK;
     if (p->f8) return MT == 2 ? launch_cfg<false, 2, true>(h, *p, total) : launch_cfg<false, 1, true>(h, *p, total);
     return MT == 2 ? launch_cfg<false, 2>(h, *p, total) : launch_cfg<false, 1>(h, *p, total);

@@ -2,10 +2,12 @@
 detection on the device (a bounded wait that runs out, a non-finite core), and
 two approximations in flight on two handles.
 
-No test here faults, traps or hangs the GPU: the timeout test shortens the
-sketch kernel's limit on waits for other roles, which makes the kernel latch
-GN_ERR_TIMEOUT, drain its own copies and MMAs (those waits keep at least a
-second) and return; the context stays usable and the next call is checked."""
+No test here faults, traps or hangs the GPU: the timeout test turns on the
+library's test hook, under which the sketch kernel's epilogue waits on a
+barrier that nothing completes; that bounded wait runs out after a 50 ms
+limit, the kernel latches GN_ERR_TIMEOUT, drains its own copies and MMAs (those
+waits keep at least a second) and returns; the context stays usable and the
+next call is checked."""
 import numpy as np
 import pytest
 import torch
@@ -143,27 +145,29 @@ def test_nonfinite_input_latched(gn):
 
 
 def test_sketch_wait_limit_expires_and_recovers(gn):
-    """A 1 ns limit on the sketch kernel's waits for its other roles: some wait
-    runs out, the kernel latches GN_ERR_TIMEOUT (7), drains its own copies and
-    MMAs, frees its tensor memory and returns.  With the default limit restored
-    the next sketch is exact (integer inputs)."""
+    """The timeout path: with the test hook on, the sketch kernel's epilogue
+    waits on a barrier that nothing completes; after the 50 ms limit that wait
+    latches GN_ERR_TIMEOUT (7), the launch stops, its producer and MMA roles
+    drain their own copies and MMAs and free tensor memory, and the kernel
+    returns.  With the hook off and the default limit, the next sketch on the
+    same handle is exact (integer inputs)."""
+    import time
     m, n, r, l = 1024, 4096, 128, 64
     H = gn.Handle()
     (A, X, Y), (Ab, Xb, Yb) = _problem(gn, H, m, n, r, l, 12)
     ws = H.workspace(m, n, r, l, gn.BF16)
     AX = torch.empty(m, r, dtype=torch.float32, device="cuda")
     YtA = torch.empty(r + l, n, dtype=torch.float32, device="cuda")
-    seen = []
-    H.set_wait_limit(1)
-    for _ in range(3):
-        H.sketch(Ab, Xb, Yb, AX, YtA, ws)
-        st = H.sync_status()
-        assert st in (0, 7)
-        seen.append(st)
-        if st == 7:
-            break
+    H.set_wait_limit(50_000_000)
+    H.set_stall_test(True)
+    t0 = time.perf_counter()
+    H.sketch(Ab, Xb, Yb, AX, YtA, ws)
+    st = H.sync_status()
+    dt = time.perf_counter() - t0
+    H.set_stall_test(False)
     H.set_wait_limit(2_000_000_000)
-    assert 7 in seen
+    assert st == 7
+    assert dt < 5.0
     AX.fill_(float("nan"))
     H.sketch(Ab, Xb, Yb, AX, YtA, ws)
     assert H.sync_status() == 0
