@@ -9,7 +9,7 @@ AX, Y^T A, Q, R): the sketch launch, the core product C = (Y^T A) X on the
 tensor cores (three bf16 slices of Y^T A), Householder QR of C in FP64 and the
 Section 5.1.2 detector / Section 5.1.1 truncation (mode AUTO).
 
-Steps run on --inflight handles (default 2), each with its own CUDA stream,
+Steps run on --inflight handles (default 3), each with its own CUDA stream,
 workspace and outputs: step i's core is enqueued without a host wait
 (GN_CORE_DEFER) and finished after step i + 1 is enqueued, so one step's
 latency-bound FP64 core overlaps the next step's sketch and core.  The latency
@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--m", type=int, default=32768)
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--r", type=int, default=1000)
-    ap.add_argument("--inflight", type=int, default=2, help="approximations in flight (handles / streams)")
+    ap.add_argument("--inflight", type=int, default=3, help="approximations in flight (handles / streams)")
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements and the CPU baseline")
     ap.add_argument("--op", default="bf16", choices=["bf16", "e4m3"],
                     help="sketch operand type of the timed step (e4m3: per-128x128-tile scales)")
@@ -768,11 +768,92 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
     del AX64, YtA64, c64, ws64
     torch.cuda.empty_cache()
 
+    out["dct_sketch"] = dct_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode, out["err_bf16"])
     out["fp64_cases"] = fp64_cases(gn, H, stream, dev)
+    out["sparse_countsketch"] = sparse_measurement(gn, H, stream, dev)
     out["sketch_state_ops"] = sketch_state_ops(gn, H, stream, dev, a, Ab, Xb, Yb, eps, mode)
     out["r2000"] = r2000_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode)
     out["adjoint"] = adjoint_measurement(gn, H, stream, dev)
     out["batched"] = batched_measurement(gn, H, stream, dev, steps=max(3, a.steps))
+    return out
+
+
+def dct_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode, err_gauss):
+    """The subsampled DCT sketches of Section 7's experiments on the bench
+    matrix: X = D C^T S (n x r) and Y (m x (r + l)) made on the device from their
+    draws (BF16), the tensor-core sketch with them, the core, and the error
+    against the FP64 A beside the Gaussian sketches' error."""
+    m, n, r = a.m, a.n, a.r
+    l = r // 2
+    sx, cx = gn_synth.dct_sketch_draws(n, r, seed=gn_synth.DEFAULT_SEED + 5)
+    sy, cy = gn_synth.dct_sketch_draws(m, r + l, seed=gn_synth.DEFAULT_SEED + 6)
+    sx, cx, sy, cy = sx.to(dev), cx.to(dev), sy.to(dev), cy.to(dev)
+    gen_ms = _best_ms(lambda: (H.dct_sketch(n, sx, cx), H.dct_sketch(m, sy, cy)), 3, stream)
+    Xd, Yd = H.dct_sketch(n, sx, cx), H.dct_sketch(m, sy, cy)
+    ws = H.workspace(m, n, r, l, gn.BF16)
+    AX = torch.empty(m, r, dtype=torch.float32, device=dev)
+    YtA = torch.empty(r + l, n, dtype=torch.float32, device=dev)
+    core = gn.Core.empty(r, l, dev)
+    sk_ms = _best_ms(lambda: H.sketch(Ab, Xd, Yd, AX, YtA, ws), 3, stream)
+    H.core(YtA, Xd, eps, mode, core, ws)
+    F = torch.empty(m, r, dtype=torch.float64, device=dev)
+    G = torch.empty(r, n, dtype=torch.float64, device=dev)
+    e2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    H.factors(AX, YtA, core, F, G, ws)
+    H.error_fro2(A64, F[:, :core.k], G[:core.k], e2, ws)
+    torch.cuda.synchronize()
+    err = math.sqrt(e2.item())
+    peaks, _ = measured_peaks()
+    fl = 2.0 * m * n * (2 * r + l)
+    out = {"workload": f"{m}x{n}, r={r}, l={l}, subsampled DCT X, Y (BF16), FP64 core",
+           "generate_ms": gen_ms, "sketch_ms": sk_ms, "sketch_tflops": fl / (sk_ms / 1e3) / 1e12,
+           "sketch_frac": fl / (sk_ms / 1e3) / 1e12 / peaks["bf16_tflops"], "k": core.k, "err": err,
+           "err_over_gaussian": err / err_gauss}
+    del Xd, Yd, ws, AX, YtA, core, F, G
+    torch.cuda.empty_cache()
+    return out
+
+
+def sparse_measurement(gn, H, stream, dev, m=178866, n=178866, r=200, l=100, k=50, per_row=5):
+    """Section 7's sparse experiment with a seeded stand-in of the same size and
+    density as its matrix (178866 x 178866, about a million nonzeros): the
+    O(nnz) CountSketch sketches of the CSR matrix, the core product by
+    CountSketch (C given to the core), the FP64 core, and the HBM bytes of the
+    sketch step (CSR arrays read, outputs zeroed and updated)."""
+    rows, cols, vals = gn_synth.sparse_lowrank_plus_noise(m, n, k, per_row)
+    order = torch.argsort(rows * n + cols)
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    key = rows * n + cols
+    uniq, inv = torch.unique_consecutive(key, return_inverse=True)
+    v = torch.zeros(uniq.numel(), dtype=torch.float64).index_add_(0, inv, vals)
+    rr, cc = uniq // n, uniq % n
+    crow = torch.zeros(m + 1, dtype=torch.int64)
+    crow[1:] = torch.cumsum(torch.bincount(rr, minlength=m), 0)
+    crow, col, val = crow.to(dev), cc.to(torch.int32).to(dev), v.to(dev)
+    nnz = int(val.numel())
+    bx, sx = (t.to(dev) for t in gn_synth.countsketch_draws(n, r, seed=gn_synth.DEFAULT_SEED + 7))
+    by, sy = (t.to(dev) for t in gn_synth.countsketch_draws(m, r + l, seed=gn_synth.DEFAULT_SEED + 8))
+    AX = torch.empty(m, r, dtype=torch.float64, device=dev)
+    YtA = torch.empty(r + l, n, dtype=torch.float64, device=dev)
+    core = gn.Core.empty(r, l, dev)
+    ws = H.workspace(m, n, r, l, gn.F64)
+    Xview = torch.empty(n, r, dtype=torch.float64, device=dev)   # shapes only: C is given, X is not read
+    sk_ms = _best_ms(lambda: H.sketch_csr_countsketch(crow, col, val, (m, n), bx, sx, by, sy, AX, YtA), 3, stream)
+    c_ms = _best_ms(lambda: H.countsketch_apply(YtA, bx, sx, core.C), 3, stream)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    H.core(YtA, Xview, 10 * 2.0 ** -53, gn.AUTO | gn.EPS_RELATIVE | gn.CORE_C_GIVEN, core, ws)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    core_ms = t0.elapsed_time(t1)
+    peaks, _ = measured_peaks()
+    bytes_ = 8 * (m + 1) + 4 * nnz + 8 * nnz + 8 * (m * r + (r + l) * n) * 2 + 8 * (n + m) * 2
+    out = {"workload": f"sparse {m}x{n}, nnz={nnz} (seeded low-rank + noise stand-in), CountSketch r={r}, l={l}, FP64",
+           "nnz": nnz, "sketch_ms": sk_ms, "core_product_ms": c_ms, "core_ms": core_ms, "k": core.k,
+           "sketch_bytes": bytes_, "sketch_hbm_frac": bytes_ / (sk_ms / 1e3) / (peaks["hbm_gbs"] * 1e9),
+           "approx_per_s": 1e3 / (sk_ms + c_ms + core_ms)}
+    del AX, YtA, core, ws, crow, col, val
+    torch.cuda.empty_cache()
     return out
 
 

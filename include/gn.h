@@ -70,7 +70,11 @@ typedef enum {
     GN_EPS_RELATIVE = 0x100,
     /* Flag OR'd into the mode of gn_core (SGN / AUTO): return without waiting
      * for k; the host fields arrive with gn_core_finish (see there). */
-    GN_CORE_DEFER = 0x200
+    GN_CORE_DEFER = 0x200,
+    /* Flag OR'd into the mode of gn_core: core->C already holds C = (Y^T A) X
+     * (FP64, (r+l) x r, ld r; for example from gn_countsketch_apply when X is a
+     * CountSketch), so gn_core does not form it from YtA and X. */
+    GN_CORE_C_GIVEN = 0x400
 } gn_mode;
 
 typedef struct {
@@ -326,6 +330,60 @@ gn_status gn_append_rows(gn_handle h, const gn_mat* B, const gn_mat* X, const gn
                          gn_mat* YtA, gn_mat* AXn, void* ws, size_t ws_bytes);
 gn_status gn_append_cols(gn_handle h, const gn_mat* B, const gn_mat* Xb, const gn_mat* Y, gn_mat* AX,
                          const gn_mat* YtA, gn_mat* YtAn, void* ws, size_t ws_bytes);
+
+/* ------------------------------------------------------- structured sketches */
+
+/* The subsampled DCT sketch matrix of Section 7's experiments (Section 2.5's
+ * fast sketches): X = D C^T S (n x r), D = diag(signs) (device, n doubles, +-1),
+ * C the orthonormal DCT-II matrix C[k, i] = a_k cos(pi (2 i + 1) k / (2 n))
+ * (a_0 = sqrt(1/n), a_k = sqrt(2/n)), S the columns cols[0..r-1] of the
+ * identity (device, r int64 in [0, n), distinct).  X has orthonormal columns;
+ * the sqrt(n/r) scale is left out (GN is invariant under X -> X c).  Written
+ * into X (n x r, GN_F64, GN_F32 or GN_BF16 rounded through FP32 like
+ * gn_quantize; BF16 ld a multiple of 8, 16-byte base), so the sketches of
+ * A with X (and with Y = a DCT sketch of m) then run through gn_sketch.  The
+ * same call makes Y (m x (r + l)) from its own draws.  GN_ERR_SHAPE unless
+ * 1 <= r <= n <= 2^31 and X is n x r. */
+gn_status gn_dct_sketch(gn_handle h, int64_t n, int64_t r, const double* signs, const int64_t* cols, gn_mat* X);
+
+/* A sparse m x n matrix in CSR form (device arrays): row_ptr (m + 1 int64,
+ * row_ptr[0] = 0, row_ptr[m] = nnz, non-decreasing), col_idx (nnz int32 in
+ * [0, n)), vals (nnz entries of `dtype`, GN_F64 or GN_F32). */
+typedef struct {
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+    const void* vals;
+    int64_t rows, cols, nnz;
+    int32_t dtype;
+} gn_csr;
+
+/* The sketches of a sparse A with CountSketch sketches (Section 2.5's
+ * input-sparsity route; Section 7's sparse experiment): X (n x r) has one
+ * entry per row, X[j, bx[j]] = sx[j], and Y (m x (r + l)) likewise with by,
+ * sy (device arrays: bx n int64 in [0, r), sx n doubles, by m int64 in
+ * [0, r + l), sy m doubles).  AX (m x r) and YtA ((r + l) x n), of A's dtype,
+ * are overwritten in O(nnz) work: every nonzero a_ij adds sx[j] a_ij to
+ * AX[i, bx[j]] and sy[i] a_ij to YtA[by[i], j] (device atomic adds; the
+ * order of the additions is not fixed).  r and r + l are AX->cols and
+ * YtA->rows; either output may be NULL to skip it.  A column index or bucket
+ * outside its range skips that nonzero and latches GN_ERR_INVALID_ARG in the
+ * device status word (gn_sync_status).  The core of the sketch state is then
+ * gn_core's, with X given densely by gn_countsketch_matrix. */
+gn_status gn_sketch_csr_countsketch(gn_handle h, const gn_csr* A, const int64_t* bx, const double* sx,
+                                    const int64_t* by, const double* sy, gn_mat* AX, gn_mat* YtA);
+
+/* out (rows x r, GN_F64) = B X for a dense B (rows x n, GN_F64 or GN_F32) and
+ * the CountSketch X of the draws bx, sx (as above): column c of out is the
+ * signed sum of the columns j of B with bx[j] = c, in O(rows n) work (device
+ * FP64 atomic adds; the order of the additions is not fixed).  With B = Y^T A
+ * this is the core C = (Y^T A) X for gn_core's GN_CORE_C_GIVEN.  A bucket
+ * outside [0, r) latches GN_ERR_INVALID_ARG and skips that column. */
+gn_status gn_countsketch_apply(gn_handle h, const gn_mat* B, const int64_t* bx, const double* sx, gn_mat* out);
+
+/* The dense CountSketch matrix (n x r, GN_F64 or GN_F32): X[i, buckets[i]] =
+ * signs[i], zero elsewhere (device draws as for gn_sketch_csr_countsketch). */
+gn_status gn_countsketch_matrix(gn_handle h, int64_t n, int64_t r, const int64_t* buckets, const double* signs,
+                                gn_mat* X);
 
 /* Sketch + core + factors in one call (Algorithm 2).  AX, YtA are outputs
  * (GN_F64 for FP64 operands, GN_F32 for the tensor-core path). */

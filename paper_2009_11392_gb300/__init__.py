@@ -31,6 +31,7 @@ F64, F32, BF16, BF16X2, E4M3 = 0, 1, 2, 3, 4
 PLAIN, SGN, AUTO = 0, 1, 2
 EPS_RELATIVE = 0x100
 CORE_DEFER = 0x200
+CORE_C_GIVEN = 0x400
 
 # Every symbol declared in include/gn.h.
 ABI_SYMBOLS = (
@@ -42,7 +43,8 @@ ABI_SYMBOLS = (
     "gn_batched_set_policy", "gn_batched_tune", "gn_set_fp64_tc", "gn_dgemm_tc_workspace_size", "gn_dgemm_tc",
     "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update", "gn_resample",
     "gn_append_rows", "gn_append_cols", "gn_resample_workspace_size", "gn_core_finish",
-    "gn_set_stall_test",
+    "gn_set_stall_test", "gn_dct_sketch", "gn_sketch_csr_countsketch", "gn_countsketch_matrix",
+    "gn_countsketch_apply",
 )
 
 
@@ -50,6 +52,12 @@ class GnMat(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("rows", ctypes.c_int64),
                 ("cols", ctypes.c_int64), ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32),
                 ("scale", ctypes.c_void_p), ("data_t", ctypes.c_void_p), ("ld_t", ctypes.c_int64)]
+
+
+class GnCsr(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("dtype", ctypes.c_int32)]
 
 
 class GnProblem(ctypes.Structure):
@@ -93,6 +101,10 @@ def _load():
         "gn_sync_status": ([P], I32),
         "gn_set_wait_limit": ([P, ctypes.c_uint64], I32),
         "gn_set_stall_test": ([P, I32], I32),
+        "gn_dct_sketch": ([P, I64, I64, P, P, M], I32),
+        "gn_sketch_csr_countsketch": ([P, ctypes.POINTER(GnCsr), P, P, P, P, M, M], I32),
+        "gn_countsketch_matrix": ([P, I64, I64, P, P, M], I32),
+        "gn_countsketch_apply": ([P, M, P, P, M], I32),
         "gn_set_fp64_g": ([P, I32], I32),
         "gn_status_string": ([I32], ctypes.c_char_p),
         "gn_device_sm_count": ([P], ctypes.c_int),
@@ -547,6 +559,42 @@ class Handle:
     def batched_run(self, eps, mode, ws):
         _check(lib.gn_batched_run(self._h, float(eps), int(mode), ctypes.c_void_p(ws.data_ptr()), ws.numel()),
                "gn_batched_run")
+
+    def dct_sketch(self, n: int, signs: torch.Tensor, cols: torch.Tensor, dtype=torch.bfloat16) -> torch.Tensor:
+        """The subsampled DCT sketch D C^T S (n x len(cols)) from its draws (signs:
+        n float64, cols: int64), made on the device; bf16 with an 8-aligned ld."""
+        r = int(cols.numel())
+        dev = self.stream.device
+        s = signs.to(device=dev, dtype=torch.float64).contiguous()
+        c = cols.to(device=dev, dtype=torch.int64).contiguous()
+        X = padded(n, r, dtype, dev) if dtype == torch.bfloat16 else torch.empty(n, r, dtype=dtype, device=dev)
+        _check(lib.gn_dct_sketch(self._h, n, r, ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                 ctypes.byref(mat(X))), "gn_dct_sketch")
+        return X
+
+    def sketch_csr_countsketch(self, crow, col, vals, shape, bx, sx, by, sy, AX, YtA):
+        """AX, Y^T A of a CSR matrix (crow int64, col int32, vals f64/f32 device
+        tensors, shape (m, n)) with CountSketch X (bx, sx) and Y (by, sy)."""
+        m, n = shape
+        dt = _TORCH_DT[vals.dtype]
+        A = GnCsr(crow.data_ptr(), col.data_ptr(), vals.data_ptr(), m, n, int(vals.numel()), dt)
+        keep = [t.contiguous() for t in (bx, sx, by, sy)]
+        _check(lib.gn_sketch_csr_countsketch(self._h, ctypes.byref(A), *[ctypes.c_void_p(t.data_ptr()) for t in keep],
+                                             ctypes.byref(mat(AX)), ctypes.byref(mat(YtA))), "gn_sketch_csr_countsketch")
+
+    def countsketch_apply(self, B, bx, sx, out):
+        """out (FP64) = B X for the CountSketch X of (bx, sx)."""
+        b, s = bx.contiguous(), sx.contiguous()
+        _check(lib.gn_countsketch_apply(self._h, ctypes.byref(mat(B)), ctypes.c_void_p(b.data_ptr()),
+                                        ctypes.c_void_p(s.data_ptr()), ctypes.byref(mat(out))), "gn_countsketch_apply")
+        return out
+
+    def countsketch_matrix(self, n: int, r: int, buckets, signs, dtype=torch.float64) -> torch.Tensor:
+        X = torch.empty(n, r, dtype=dtype, device=self.stream.device)
+        b, s = buckets.contiguous(), signs.contiguous()
+        _check(lib.gn_countsketch_matrix(self._h, n, r, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(s.data_ptr()),
+                                         ctypes.byref(mat(X))), "gn_countsketch_matrix")
+        return X
 
     def hmt(self, A, X, Q, B, ws):
         _check(lib.gn_hmt(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Q)),

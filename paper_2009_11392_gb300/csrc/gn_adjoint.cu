@@ -10,13 +10,13 @@
 //
 // Every C^+ enters through Q and triangular solves with R (the paper's
 // Section 5.1 rule: never form the core's inverse).  FP64 inputs: every step
-// in FP64 on the FP64 units.  FP32 inputs: every product with an m- or n-sized
-// dimension (the sketches, S1, S2, W, the two rank-r products that form the
-// gradient) runs on the tcgen05 tensor cores as a split-BF16 product (each
-// operand x = hi + lo, hi = bf16(x), lo = bf16(x - hi); the three products
-// hi.hi + hi.lo + lo.hi accumulated in FP32: FP32-level accuracy), C = (Y^T A) X
-// is an FP64-accurate digit-sliced product, and the QR, the two triangular
-// solves and the r x r algebra stay FP64.  With K R^T = (I - Q Q^T) W^T - Q W Q,
+// in FP64 on the FP64 units.  FP32 inputs, all on the tcgen05 tensor cores
+// except the QR, the two triangular solves and the r x r algebra (FP64): the
+// sketches AX, Y^T A and the core C = (Y^T A) X, whose errors the core's
+// conditioning amplifies, as FP64-accurate digit-sliced products; the
+// contractions over G and the two rank-r products that form the gradient (S1,
+// S2, W, P, Q S2, dA) as three-slice BF16 products (x = s0 + s1 + s2, the six
+// slice products of order <= 2, FP32 accumulation: FP32-level accuracy).  With K R^T = (I - Q Q^T) W^T - Q W Q,
 // the two m x r terms share one solve: P = (S1 Q + Y (K R^T)) R^{-T}.  Sketches
 // are recomputed from A in every call (nothing is kept from a forward pass).
 #include "gn_internal.cuh"
@@ -153,53 +153,59 @@ gn_status transpose_f64(gn_handle h, const double* s, long long rows, long long 
 size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
 long long rnd8(long long x) { return (x + 7) / 8 * 8; }
 
-// ---------------------------------------------------------------- split-BF16 products
-// hi / lo BF16 planes of a row-major FP32 or FP64 matrix: hi = bf16(x), lo =
-// bf16(x - hi) (the residual taken in the source precision), so hi + lo holds
-// about 16 significant bits of x.
-__global__ void split2_kernel(const void* __restrict__ src, int f64, long long rows, long long cols, long long lds,
-                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ldd) {
+// ---------------------------------------------------------------- three-slice BF16 products
+// Three BF16 slices of a row-major FP32 or FP64 matrix: s0 = bf16(x), s1 =
+// bf16(x - s0), s2 = bf16(x - s0 - s1) (residuals in the source precision), so
+// s0 + s1 + s2 holds the 24 significant bits of an FP32 x.
+__global__ void split3s_kernel(const void* __restrict__ src, int f64, long long rows, long long cols, long long lds,
+                               __nv_bfloat16* __restrict__ s0, __nv_bfloat16* __restrict__ s1,
+                               __nv_bfloat16* __restrict__ s2, long long ldd) {
     const long long total = rows * cols;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
         const long long i = e / cols, j = e - i * cols;
-        __nv_bfloat16 h, l;
+        __nv_bfloat16 a, b, c;
         if (f64) {
             const double x = static_cast<const double*>(src)[i * lds + j];
-            h = __float2bfloat16_rn(static_cast<float>(x));
-            l = __float2bfloat16_rn(static_cast<float>(x - static_cast<double>(__bfloat162float(h))));
+            a = __float2bfloat16_rn(static_cast<float>(x));
+            const double r1 = x - static_cast<double>(__bfloat162float(a));
+            b = __float2bfloat16_rn(static_cast<float>(r1));
+            c = __float2bfloat16_rn(static_cast<float>(r1 - static_cast<double>(__bfloat162float(b))));
         } else {
             const float x = static_cast<const float*>(src)[i * lds + j];
-            h = __float2bfloat16_rn(x);
-            l = __float2bfloat16_rn(x - __bfloat162float(h));
+            a = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(a);
+            b = __float2bfloat16_rn(r1);
+            c = __float2bfloat16_rn(r1 - __bfloat162float(b));
         }
-        hi[i * ldd + j] = h;
-        lo[i * ldd + j] = l;
+        s0[i * ldd + j] = a;
+        s1[i * ldd + j] = b;
+        s2[i * ldd + j] = c;
     }
 }
 
-// A matrix held as two BF16 planes (row-major, ld a multiple of 8: the TMA rule).
+// A matrix held as three BF16 planes (row-major, ld a multiple of 8: the TMA rule).
 struct Plane {
-    __nv_bfloat16* hi;
-    __nv_bfloat16* lo;
+    __nv_bfloat16* s[3];
     long long rows, cols, ld;
 };
 
-gn_status split2(gn_handle h, const void* src, int f64, long long lds, const Plane& p) {
+gn_status split3s(gn_handle h, const void* src, int f64, long long lds, const Plane& p) {
     const long long total = p.rows * p.cols;
     if (total == 0) return GN_OK;
-    split2_kernel<<<ew(h, total), 256, 0, h->stream>>>(src, f64, p.rows, p.cols, lds, p.hi, p.lo, p.ld);
+    split3s_kernel<<<ew(h, total), 256, 0, h->stream>>>(src, f64, p.rows, p.cols, lds, p.s[0], p.s[1], p.s[2], p.ld);
     count_launch();
     GN_CUDA_TRY(cudaGetLastError());
     return GN_OK;
 }
 
 // One product of a launch: D (M x N, FP32) = sum over pairs of op(A_p) op(B_p),
-// each pair as hi.hi + hi.lo + lo.hi.  a_mn = 0: A plane is M x K (K-major);
-// a_mn = 1: A plane is K x M.  b_mn = 0: B plane is N x K; b_mn = 1: K x N.  A
-// plane narrower than K reads zeros beyond its width (TMA fill), so pairs with
-// different K share the launch's K.
-struct X3 {
+// each pair as the six slice products of order <= 2 (FP32-level accuracy,
+// FP32 accumulation).  a_mn = 0: A plane is M x K (K-major); a_mn = 1: A plane
+// is K x M.  b_mn = 0: B plane is N x K; b_mn = 1: K x N.  A plane narrower than
+// K reads zeros beyond its width (TMA fill), so pairs with different K share
+// the launch's K.
+struct X6 {
     int M, N, K;
     int a_mn, b_mn;
     int npair;
@@ -209,12 +215,13 @@ struct X3 {
     long long ldd;
 };
 
-gn_status x3_launch(gn_handle h, X3* gs, int ng) {
+gn_status x6_launch(gn_handle h, X6* gs, int ng) {
+    static const int ord[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
     TcParams p;
     memset(&p, 0, sizeof(p));
     int nm = 0;
     for (int g = 0; g < ng; ++g) {
-        X3& x = gs[g];
+        X6& x = gs[g];
         TcGemm& G = p.g[g];
         G.M = x.M;
         G.N = x.N;
@@ -227,32 +234,27 @@ gn_status x3_launch(gn_handle h, X3* gs, int ng) {
         while (bn > 64 && static_cast<long long>((x.M + 127) / 128) * ((x.N + bn - 1) / bn) < 2LL * h->sm_count)
             bn = std::max(64, (bn / 2 + q - 1) / q * q);
         G.bn = bn;
-        G.nsrc = 3 * x.npair;
+        G.nsrc = 6 * x.npair;
+        if (G.nsrc > TC_MAX_SRC || nm + 6 * x.npair > TC_MAX_MAPS) return GN_ERR_UNSUPPORTED;
         for (int pi = 0; pi < x.npair; ++pi) {
             const Plane& A = *x.A[pi];
             const Plane& B = *x.B[pi];
-            const int ma = nm, mb = nm + 2;
-            for (int s = 0; s < 2; ++s) {
-                const __nv_bfloat16* pa = s ? A.lo : A.hi;
-                const __nv_bfloat16* pb = s ? B.lo : B.hi;
-                if (x.a_mn) GN_TRY(tc_make_map_bf16(&p.maps[ma + s], pa, A.rows, A.cols, A.ld, 64, 64));
-                else GN_TRY(tc_make_map_bf16(&p.maps[ma + s], pa, A.rows, A.cols, A.ld, 64, 128));
-                if (x.b_mn) GN_TRY(tc_make_map_bf16(&p.maps[mb + s], pb, B.rows, B.cols, B.ld, 64, 64));
-                else GN_TRY(tc_make_map_bf16(&p.maps[mb + s], pb, B.rows, B.cols, B.ld, 64, bn));
+            const int ma = nm, mb = nm + 3;
+            for (int t = 0; t < 3; ++t) {
+                if (x.a_mn) GN_TRY(tc_make_map_bf16(&p.maps[ma + t], A.s[t], A.rows, A.cols, A.ld, 64, 64));
+                else GN_TRY(tc_make_map_bf16(&p.maps[ma + t], A.s[t], A.rows, A.cols, A.ld, 64, 128));
+                if (x.b_mn) GN_TRY(tc_make_map_bf16(&p.maps[mb + t], B.s[t], B.rows, B.cols, B.ld, 64, 64));
+                else GN_TRY(tc_make_map_bf16(&p.maps[mb + t], B.s[t], B.rows, B.cols, B.ld, 64, bn));
             }
-            nm += 4;
-            // hi.hi, hi.lo, lo.hi
-            G.a_map[3 * pi + 0] = ma;
-            G.b_map[3 * pi + 0] = mb;
-            G.a_map[3 * pi + 1] = ma;
-            G.b_map[3 * pi + 1] = mb + 1;
-            G.a_map[3 * pi + 2] = ma + 1;
-            G.b_map[3 * pi + 2] = mb;
+            nm += 6;
+            for (int o = 0; o < 6; ++o) {
+                G.a_map[6 * pi + o] = ma + ord[o][0];
+                G.b_map[6 * pi + o] = mb + ord[o][1];
+            }
         }
         G.D = x.D;
         G.ldd = x.ldd;
     }
-    if (nm > TC_MAX_MAPS) return GN_ERR_UNSUPPORTED;
     p.ngemm = ng;
     return tc_launch(h, &p);
 }
@@ -293,11 +295,11 @@ size_t backward_fixed(long long m, long long n, long long r, long long l, int f3
 }
 
 // ---------------------------------------------------------------- FP32 inputs on the tensor cores
-// Workspace of the FP32 path (forward and backward share the layout's prefix).
+// Workspace of the FP32 path (forward and backward share the layout).
 struct TcWs {
-    Plane As, Gs, Xs, Ys, YtAs, Fs, S1s, S2s, Qs, Kts, Ps, QpTs, Ahs;
-    float *AX32, *YtA32, *S1, *S2, *W32, *P32, *QpT;
-    double *AX, *X64, *C, *Wq, *Q, *R, *W64, *Wt, *M1, *P64, *G64;
+    Plane Gs, Xs, Ys, YtATs, Fs, S1s, S2s, Qs, Kts, Ps, QpTs, Ahs;
+    float *S1, *S2, *W32, *P32, *QpT;
+    double *X64, *Y64, *AX, *YtAT, *C, *Wq, *Q, *R, *W64, *Wt, *M1, *P64;
     double* inner;
     size_t inner_bytes;
     void* oz;
@@ -310,11 +312,12 @@ size_t tc_inner_bytes(long long m, long long n, long long r, long long l, int sm
                      dgemm_ws_bytes(rl, r, r, sms)});
 }
 size_t tc_oz_bytes(long long m, long long n, long long r, long long l) {
-    return std::max(oz_ws_bytes(r + l, r, n, 1), oz_ws_bytes(m, 128, r, 0));
+    return std::max({oz_ws_bytes(m, r, n, 1), oz_ws_bytes(n, r + l, m, 1), oz_ws_bytes(r + l, r, n, 0),
+                     oz_ws_bytes(m, 128, r, 0)});
 }
 
 // Carves (or, with base == nullptr, sizes) the FP32 path's workspace.
-size_t tc_carve(long long m, long long n, long long r, long long l, int sms, char* base, size_t cap, TcWs* w) {
+size_t tc_carve(long long m, long long n, long long r, long long l, int sms, char* base, TcWs* w) {
     const long long rl = r + l;
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
@@ -327,16 +330,14 @@ size_t tc_carve(long long m, long long n, long long r, long long l, int sms, cha
         p.rows = rows;
         p.cols = cols;
         p.ld = rnd8(cols);
-        p.hi = reinterpret_cast<__nv_bfloat16*>(take(2 * rows * p.ld));
-        p.lo = reinterpret_cast<__nv_bfloat16*>(take(2 * rows * p.ld));
+        for (int t = 0; t < 3; ++t) p.s[t] = reinterpret_cast<__nv_bfloat16*>(take(2 * rows * p.ld));
         return p;
     };
     TcWs t;
-    t.As = plane(m, n);
     t.Gs = plane(m, n);
     t.Xs = plane(n, r);
     t.Ys = plane(m, rl);
-    t.YtAs = plane(rl, n);
+    t.YtATs = plane(n, rl);
     t.Fs = plane(m, r);
     t.S1s = plane(m, rl);
     t.S2s = plane(r, n);
@@ -347,15 +348,15 @@ size_t tc_carve(long long m, long long n, long long r, long long l, int sms, cha
     t.Ahs = plane(r, n);
     auto f32 = [&](long long rows, long long cols) { return reinterpret_cast<float*>(take(4 * rows * rnd8(cols))); };
     auto f64 = [&](long long count) { return reinterpret_cast<double*>(take(8 * count)); };
-    t.AX32 = f32(m, r);
-    t.YtA32 = f32(rl, n);
     t.S1 = f32(m, rl);
     t.S2 = f32(r, n);
     t.W32 = f32(r, rl);
     t.P32 = f32(m, r);
     t.QpT = f32(n, rl);
-    t.AX = f64(m * r);
     t.X64 = f64(n * r);
+    t.Y64 = f64(m * rl);
+    t.AX = f64(m * r);
+    t.YtAT = f64(n * rl);
     t.C = f64(rl * r);
     t.Wq = f64(rl * r);
     t.Q = f64(rl * r);
@@ -364,35 +365,32 @@ size_t tc_carve(long long m, long long n, long long r, long long l, int sms, cha
     t.Wt = f64(rl * r);
     t.M1 = f64(r * r);
     t.P64 = f64(m * r);
-    t.G64 = f64(r * n);
     t.oz_bytes = tc_oz_bytes(m, n, r, l);
     t.oz = take(t.oz_bytes);
     t.inner_bytes = tc_inner_bytes(m, n, r, l, sms);
     t.inner = reinterpret_cast<double*>(take(t.inner_bytes));
     if (w) *w = t;
-    (void)cap;
     return off + 256;
 }
 
-// The steps both directions share: planes of A, X, Y; AX and Y^T A on the tensor
-// cores; C = (Y^T A) X to FP64 accuracy; Householder C = QR; F = (AX) R^{-1}.
+// The steps both directions share.  The sketches of the FP32 A feed the core,
+// whose conditioning amplifies their errors, so they are formed to FP64
+// accuracy by digit slicing on the tensor cores: AX (m x r) and (Y^T A)^T =
+// A^T Y (n x (r+l), kept transposed), then C = (Y^T A) X, Householder C = QR,
+// F = (AX) R^{-1}.
 gn_status tc_front(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, long long m, long long n,
                    long long r, long long rl, TcWs& t) {
-    GN_TRY(split2(h, A->data, 0, A->ld, t.As));
-    GN_TRY(split2(h, X->data, 0, X->ld, t.Xs));
-    GN_TRY(split2(h, Y->data, 0, Y->ld, t.Ys));
-    X3 g[2];
-    g[0] = X3{static_cast<int>(m), static_cast<int>(r), static_cast<int>(n), 0, 1, 1, {&t.As}, {&t.Xs},
-              t.AX32, rnd8(r)};
-    g[1] = X3{static_cast<int>(rl), static_cast<int>(n), static_cast<int>(m), 1, 1, 1, {&t.Ys}, {&t.As},
-              t.YtA32, rnd8(n)};
-    GN_TRY(x3_launch(h, g, 2));
-    GN_TRY(copy_f32_to_f64(h, t.AX32, m, r, rnd8(r), t.AX, r));
     GN_TRY(copy_f32_to_f64(h, static_cast<const float*>(X->data), n, r, X->ld, t.X64, r));
-    GN_TRY(oz_dgemm(h, rl, r, n, 1.0, t.YtA32, 1, rnd8(n), 0, t.X64, r, 0, 0.0, t.C, r, t.oz, t.oz_bytes));
+    GN_TRY(copy_f32_to_f64(h, static_cast<const float*>(Y->data), m, rl, Y->ld, t.Y64, rl));
+    GN_TRY(oz_dgemm(h, m, r, n, 1.0, A->data, 1, A->ld, 0, t.X64, r, 0, 0.0, t.AX, r, t.oz, t.oz_bytes));
+    GN_TRY(oz_dgemm(h, n, rl, m, 1.0, A->data, 1, A->ld, 1, t.Y64, rl, 0, 0.0, t.YtAT, rl, t.oz, t.oz_bytes));
+    GN_TRY(oz_dgemm(h, rl, r, n, 1.0, t.YtAT, 0, rl, 1, t.X64, r, 0, 0.0, t.C, r, t.oz, t.oz_bytes));
     GN_CUDA_TRY(cudaMemcpyAsync(t.Wq, t.C, sizeof(double) * rl * r, cudaMemcpyDeviceToDevice, h->stream));
     GN_TRY(householder_qr(h, t.Wq, rl, r, r, t.Q, r, t.R, r, t.inner, t.inner_bytes));
     GN_TRY(trsm_right_upper(h, t.AX, m, r, r, t.R, r, 0, t.inner, t.inner_bytes, t.oz, t.oz_bytes));   // F in AX
+    GN_TRY(split3s(h, t.AX, 1, r, t.Fs));
+    GN_TRY(split3s(h, t.YtAT, 1, rl, t.YtATs));
+    GN_TRY(split3s(h, t.Q, 1, r, t.Qs));
     return GN_OK;
 }
 
@@ -400,69 +398,62 @@ gn_status backward_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_ma
                       void* ws, size_t ws_bytes) {
     const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols;
     TcWs t;
-    if (tc_carve(m, n, r, rl - r, h->sm_count, static_cast<char*>(ws), ws_bytes, &t) > ws_bytes)
-        return GN_ERR_WORKSPACE;
+    if (tc_carve(m, n, r, rl - r, h->sm_count, static_cast<char*>(ws), &t) > ws_bytes) return GN_ERR_WORKSPACE;
     GN_TRY(tc_front(h, A, X, Y, m, n, r, rl, t));
-    const double* F = t.AX;
     // S1 = G (Y^T A)^T (m x (r+l)), S2 = F^T G (r x n)
-    GN_TRY(split2(h, Gup->data, 0, Gup->ld, t.Gs));
-    GN_TRY(split2(h, t.YtA32, 0, rnd8(n), t.YtAs));
-    GN_TRY(split2(h, F, 1, r, t.Fs));
-    X3 g[2];
-    g[0] = X3{static_cast<int>(m), static_cast<int>(rl), static_cast<int>(n), 0, 0, 1, {&t.Gs}, {&t.YtAs},
+    GN_TRY(split3s(h, Gup->data, 0, Gup->ld, t.Gs));
+    X6 g[2];
+    g[0] = X6{static_cast<int>(m), static_cast<int>(rl), static_cast<int>(n), 0, 1, 1, {&t.Gs}, {&t.YtATs},
               t.S1, rnd8(rl)};
-    g[1] = X3{static_cast<int>(r), static_cast<int>(n), static_cast<int>(m), 1, 1, 1, {&t.Fs}, {&t.Gs},
+    g[1] = X6{static_cast<int>(r), static_cast<int>(n), static_cast<int>(m), 1, 1, 1, {&t.Fs}, {&t.Gs},
               t.S2, rnd8(n)};
-    GN_TRY(x3_launch(h, g, 2));
+    GN_TRY(x6_launch(h, g, 2));
     // W = F^T S1 (r x (r+l))
-    GN_TRY(split2(h, t.S1, 0, rnd8(rl), t.S1s));
-    g[0] = X3{static_cast<int>(r), static_cast<int>(rl), static_cast<int>(m), 1, 1, 1, {&t.Fs}, {&t.S1s},
+    GN_TRY(split3s(h, t.S1, 0, rnd8(rl), t.S1s));
+    g[0] = X6{static_cast<int>(r), static_cast<int>(rl), static_cast<int>(m), 1, 1, 1, {&t.Fs}, {&t.S1s},
               t.W32, rnd8(rl)};
-    GN_TRY(x3_launch(h, g, 1));
+    GN_TRY(x6_launch(h, g, 1));
     GN_TRY(copy_f32_to_f64(h, t.W32, r, rl, rnd8(rl), t.W64, rl));
     // K R^T = W^T - Q (Q^T W^T + W Q)   ((r+l) x r, FP64)
     GN_TRY(transpose_f64(h, t.W64, r, rl, rl, t.Wt, r));
     GN_TRY(dgemm(h, r, r, rl, 1.0, t.Q, r, 1, t.Wt, r, 0, 0.0, t.M1, r, t.inner, t.inner_bytes));
     GN_TRY(dgemm(h, r, r, rl, 1.0, t.W64, rl, 0, t.Q, r, 0, 1.0, t.M1, r, t.inner, t.inner_bytes));
     GN_TRY(dgemm(h, rl, r, r, -1.0, t.Q, r, 0, t.M1, r, 0, 1.0, t.Wt, r, t.inner, t.inner_bytes));
-    // P = (S1 Q + Y (K R^T)) R^{-T} (m x r);  Q' ^T = S2^T Q^T (n x (r+l))
-    GN_TRY(split2(h, t.Q, 1, r, t.Qs));
-    GN_TRY(split2(h, t.Wt, 1, r, t.Kts));
-    GN_TRY(split2(h, t.S2, 0, rnd8(n), t.S2s));
-    g[0] = X3{static_cast<int>(m), static_cast<int>(r), static_cast<int>(rl), 0, 1, 2, {&t.S1s, &t.Ys},
+    // P = (S1 Q + Y (K R^T)) R^{-T} (m x r);  Q'^T = S2^T Q^T (n x (r+l))
+    GN_TRY(split3s(h, t.Wt, 1, r, t.Kts));
+    GN_TRY(split3s(h, Y->data, 0, Y->ld, t.Ys));
+    GN_TRY(split3s(h, t.S2, 0, rnd8(n), t.S2s));
+    g[0] = X6{static_cast<int>(m), static_cast<int>(r), static_cast<int>(rl), 0, 1, 2, {&t.S1s, &t.Ys},
               {&t.Qs, &t.Kts}, t.P32, rnd8(r)};
-    g[1] = X3{static_cast<int>(n), static_cast<int>(rl), static_cast<int>(r), 1, 0, 1, {&t.S2s}, {&t.Qs},
+    g[1] = X6{static_cast<int>(n), static_cast<int>(rl), static_cast<int>(r), 1, 0, 1, {&t.S2s}, {&t.Qs},
               t.QpT, rnd8(rl)};
-    GN_TRY(x3_launch(h, g, 2));
+    GN_TRY(x6_launch(h, g, 2));
     GN_TRY(copy_f32_to_f64(h, t.P32, m, r, rnd8(r), t.P64, r));
     GN_TRY(trsm_right_upper(h, t.P64, m, r, r, t.R, r, 1, t.inner, t.inner_bytes, t.oz, t.oz_bytes));
     // dA = P X^T + Y Q'
-    GN_TRY(split2(h, t.P64, 1, r, t.Ps));
-    GN_TRY(split2(h, t.QpT, 0, rnd8(rl), t.QpTs));
-    g[0] = X3{static_cast<int>(m), static_cast<int>(n), static_cast<int>(rl), 0, 0, 2, {&t.Ps, &t.Ys},
+    GN_TRY(split3s(h, t.P64, 1, r, t.Ps));
+    GN_TRY(split3s(h, t.QpT, 0, rnd8(rl), t.QpTs));
+    GN_TRY(split3s(h, X->data, 0, X->ld, t.Xs));
+    g[0] = X6{static_cast<int>(m), static_cast<int>(n), static_cast<int>(rl), 0, 0, 2, {&t.Ps, &t.Ys},
               {&t.Xs, &t.QpTs}, static_cast<float*>(dA->data), dA->ld};
-    return x3_launch(h, g, 1);
+    return x6_launch(h, g, 1);
 }
 
 gn_status forward_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* Ahat, void* ws,
                      size_t ws_bytes) {
     const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols;
     TcWs t;
-    if (tc_carve(m, n, r, rl - r, h->sm_count, static_cast<char*>(ws), ws_bytes, &t) > ws_bytes)
-        return GN_ERR_WORKSPACE;
+    if (tc_carve(m, n, r, rl - r, h->sm_count, static_cast<char*>(ws), &t) > ws_bytes) return GN_ERR_WORKSPACE;
     GN_TRY(tc_front(h, A, X, Y, m, n, r, rl, t));
     // G = Q^T (Y^T A) (r x n), then A_hat = F G
-    GN_TRY(split2(h, t.Q, 1, r, t.Qs));
-    GN_TRY(split2(h, t.YtA32, 0, rnd8(n), t.YtAs));
-    X3 g[1];
-    g[0] = X3{static_cast<int>(r), static_cast<int>(n), static_cast<int>(rl), 1, 1, 1, {&t.Qs}, {&t.YtAs},
+    X6 g[1];
+    g[0] = X6{static_cast<int>(r), static_cast<int>(n), static_cast<int>(rl), 1, 0, 1, {&t.Qs}, {&t.YtATs},
               t.S2, rnd8(n)};
-    GN_TRY(x3_launch(h, g, 1));
-    GN_TRY(split2(h, t.AX, 1, r, t.Fs));
-    GN_TRY(split2(h, t.S2, 0, rnd8(n), t.Ahs));
-    g[0] = X3{static_cast<int>(m), static_cast<int>(n), static_cast<int>(r), 0, 1, 1, {&t.Fs}, {&t.Ahs},
+    GN_TRY(x6_launch(h, g, 1));
+    GN_TRY(split3s(h, t.S2, 0, rnd8(n), t.Ahs));
+    g[0] = X6{static_cast<int>(m), static_cast<int>(n), static_cast<int>(r), 0, 1, 1, {&t.Fs}, {&t.Ahs},
               static_cast<float*>(Ahat->data), Ahat->ld};
-    return x3_launch(h, g, 1);
+    return x6_launch(h, g, 1);
 }
 
 }  // namespace
@@ -478,7 +469,7 @@ extern "C" gn_status gn_backward_workspace_size(int64_t m, int64_t n, int64_t r,
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (dtype == GN_F32) {
-        *bytes = tc_carve(m, n, r, l, sms, nullptr, 0, nullptr);
+        *bytes = tc_carve(m, n, r, l, sms, nullptr, nullptr);
         return GN_OK;
     }
     const size_t inner = std::max({qr_ws_bytes(r + l, r, sms), dgemm_ws_bytes(r + l, r, n, sms),

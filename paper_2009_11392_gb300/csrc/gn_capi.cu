@@ -607,15 +607,21 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     if (!h || !YtA || !X || !core || !ws) return GN_ERR_INVALID_ARG;
     const int eps_rel = (mode & GN_EPS_RELATIVE) ? 1 : 0;
     const int defer = (mode & GN_CORE_DEFER) ? 1 : 0;
-    mode &= ~(GN_EPS_RELATIVE | GN_CORE_DEFER);
+    const int c_given = (mode & GN_CORE_C_GIVEN) ? 1 : 0;
+    mode &= ~(GN_EPS_RELATIVE | GN_CORE_DEFER | GN_CORE_C_GIVEN);
     if (mode < GN_MODE_PLAIN || mode > GN_MODE_AUTO || !(eps >= 0.0)) return GN_ERR_INVALID_ARG;
     if (defer && h->pend.active) return GN_ERR_INVALID_ARG;   // finish the pending core first
     const long long n = X->rows, r = X->cols, rl = YtA->rows, l = rl - r;
     if (r < 1 || l < 1 || n < r) return GN_ERR_SHAPE;
     GN_TRY(check_mat(YtA, rl, n));
     const int x8 = X->dtype == GN_E4M3;
-    if (x8) GN_TRY(check_e4m3(X, n, r, false, true));
-    else GN_TRY(check_mat(X, n, r));
+    if (c_given) {   // X gives the shapes and the path only; its data is not read
+        if (X->dtype != YtA->dtype && !(YtA->dtype == GN_F32 && X->dtype == GN_BF16) && !x8) return GN_ERR_DTYPE;
+    } else if (x8) {
+        GN_TRY(check_e4m3(X, n, r, false, true));
+    } else {
+        GN_TRY(check_mat(X, n, r));
+    }
     if (!core->Q || !core->R || !core->C || ((mode != GN_MODE_PLAIN) && (!core->Q2 || !core->R2)))
         return GN_ERR_INVALID_ARG;
     const int mixed = (YtA->dtype == GN_F32 && (X->dtype == GN_BF16 || x8));
@@ -664,7 +670,9 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     if (!cv.ok) return GN_ERR_WORKSPACE;
 
     // C = (Y^T A) X  ((r+l) x r, FP64, ld = r)
-    if (fp64) {
+    if (c_given) {
+        // the caller formed C (for a structured X, e.g. gn_countsketch_apply)
+    } else if (fp64) {
         GN_TRY(dgemm(h, rl, r, n, 1.0, static_cast<const double*>(YtA->data), YtA->ld, 0,
                      static_cast<const double*>(X->data), X->ld, 0, 0.0, core->C, r, inner, inner_bytes));
     } else {

@@ -65,7 +65,7 @@ void count_launch();
 
 constexpr int TC_MAX_MAPS = 14;
 constexpr int TC_MAX_GEMMS = 7;
-constexpr int TC_MAX_SRC = 7;
+constexpr int TC_MAX_SRC = 12;
 
 struct TcGemm {
     int M, N, K;             // D is M x N, contraction length K
