@@ -161,6 +161,21 @@ gn_status gn_set_stall_test(gn_handle h, int32_t on);
  * (eq. 5.1: it carries the conditioning of R). */
 gn_status gn_set_fp64_g(gn_handle h, int32_t fp64_g);
 
+/* FP64-level accumulation for callers that need the FP64 path's error from
+ * FP32 sketches (split BF16 A): part_k = 0 (default) off; part_k >= 4096 (a
+ * multiple of 64) on.  When on: (1) gn_sketch on GN_BF16X2 operands runs the K
+ * range of each product as parts of about part_k elements, each accumulated
+ * in FP32 in tensor memory, stored, and summed in FP64 (the tensor cores'
+ * FP32 accumulation over the full K = m or n is what limits split BF16
+ * otherwise); the parts live in the caller's workspace, which
+ * gn_workspace_size(..., GN_BF16X2) sizes for part_k = 4096;
+ * (2) gn_core forms C = (Y^T A) X from GN_F32 Y^T A and GN_BF16 X by exact
+ * digit slicing (FP64 accuracy, as gn_dgemm_tc) instead of FP32-accumulated
+ * BF16 slices; (3) gn_factors forms G in FP64 (as gn_set_fp64_g(h, 1)).
+ * GN_ERR_INVALID_ARG for other part_k.  The paper fixes no working precision
+ * for the sketches; this is the library's. */
+gn_status gn_set_fp64_accum(gn_handle h, int64_t part_k);
+
 /* How gn_factors / gn_approx compute the large FP64 products of the solve for
  * F when AX is GN_F32 (the tensor-core sketches): the outer-block updates of
  * the triangular solve F R = AX (eq. 5.1) and, after a truncation, AX Q_2.

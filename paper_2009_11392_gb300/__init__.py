@@ -44,7 +44,7 @@ ABI_SYMBOLS = (
     "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update", "gn_resample",
     "gn_append_rows", "gn_append_cols", "gn_resample_workspace_size", "gn_core_finish",
     "gn_set_stall_test", "gn_dct_sketch", "gn_sketch_csr_countsketch", "gn_countsketch_matrix",
-    "gn_countsketch_apply",
+    "gn_countsketch_apply", "gn_set_fp64_accum",
 )
 
 
@@ -101,6 +101,7 @@ def _load():
         "gn_sync_status": ([P], I32),
         "gn_set_wait_limit": ([P, ctypes.c_uint64], I32),
         "gn_set_stall_test": ([P, I32], I32),
+        "gn_set_fp64_accum": ([P, I64], I32),
         "gn_dct_sketch": ([P, I64, I64, P, P, M], I32),
         "gn_sketch_csr_countsketch": ([P, ctypes.POINTER(GnCsr), P, P, P, P, M, M], I32),
         "gn_countsketch_matrix": ([P, I64, I64, P, P, M], I32),
@@ -318,6 +319,11 @@ class Handle:
     def set_fp64_g(self, on: bool):
         """G = Q_1^T (Y^T A) in FP64 (True) or on the tensor cores (False, default) for FP32 Y^T A."""
         _check(lib.gn_set_fp64_g(self._h, 1 if on else 0), "gn_set_fp64_g")
+
+    def set_fp64_accum(self, part_k: int):
+        """FP64-level accumulation (split-BF16 sketches in stored K parts summed in
+        FP64, digit-sliced C, FP64 G): part_k >= 4096 K elements per part, 0 off."""
+        _check(lib.gn_set_fp64_accum(self._h, int(part_k)), "gn_set_fp64_accum")
 
     def set_fp64_tc(self, on: bool):
         """The factors' large FP64 products (FP32 AX) on the tensor cores by exact

@@ -425,9 +425,10 @@ gn_status backward_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_ma
     GN_TRY(split3s(h, t.S2, 0, rnd8(n), t.S2s));
     g[0] = X6{static_cast<int>(m), static_cast<int>(r), static_cast<int>(rl), 0, 1, 2, {&t.S1s, &t.Ys},
               {&t.Qs, &t.Kts}, t.P32, rnd8(r)};
-    g[1] = X6{static_cast<int>(n), static_cast<int>(rl), static_cast<int>(r), 1, 0, 1, {&t.S2s}, {&t.Qs},
+    GN_TRY(x6_launch(h, g, 1));   // 12 tensor maps: the launch's limit
+    g[0] = X6{static_cast<int>(n), static_cast<int>(rl), static_cast<int>(r), 1, 0, 1, {&t.S2s}, {&t.Qs},
               t.QpT, rnd8(rl)};
-    GN_TRY(x6_launch(h, g, 2));
+    GN_TRY(x6_launch(h, g, 1));
     GN_TRY(copy_f32_to_f64(h, t.P32, m, r, rnd8(r), t.P64, r));
     GN_TRY(trsm_right_upper(h, t.P64, m, r, r, t.R, r, 1, t.inner, t.inner_bytes, t.oz, t.oz_bytes));
     // dA = P X^T + Y Q'

@@ -112,7 +112,19 @@ size_t core_ws(long long n, long long r, long long l, int mixed, int sms) {
         b += align256(qr_oz_ws_bytes(rl, r));          // tensor-core formation of Q
     }
     size_t inner = std::max(qr_ws_bytes(rl, r, sms), dgemm_ws_bytes(rl, r, n, sms));
+    if (mixed)   // FP64-level C (gn_set_fp64_accum): X in FP64 and the digit-sliced product's scratch
+        inner = std::max(inner, align256(sizeof(double) * n * r) + oz_ws_bytes(rl, r, n, 1));
     return b + inner + 1024;
+}
+
+__global__ void bf16_to_f64_kernel(const __nv_bfloat16* __restrict__ s, long long rows, long long cols,
+                                   long long lds, double* __restrict__ d, long long ldd) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e - i * cols;
+        d[i * ldd + j] = static_cast<double>(__bfloat162float(s[i * lds + j]));
+    }
 }
 
 // e4m3 sketch: the scale-factor images of A, X and Y (512 bytes per tile).
@@ -147,8 +159,43 @@ size_t hmt_ws(long long m, long long n, long long r, int sms) {
            dgemm_ws_bytes(r, n, m, sms) + 1024;
 }
 
+// FP64-level accumulation of split-BF16 sketches (gn_set_fp64_accum): the K
+// range of each product runs as parts of about part_k elements, each
+// accumulated in FP32 in tensor memory and stored, then summed in FP64.
+int acc_parts(long long K, int nsrc, long long part_k) {
+    const long long kel = nsrc * ((K + 63) / 64) * 64;
+    return static_cast<int>(std::max<long long>(1, (kel + part_k - 1) / part_k));
+}
+long long round4(long long x) { return (x + 3) / 4 * 4; }
+size_t split_parts_ws(long long m, long long n, long long r, long long rl, long long part_k) {
+    return align256(4 * static_cast<size_t>(acc_parts(n, 2, part_k)) * m * round4(r)) +
+           align256(4 * static_cast<size_t>(acc_parts(m, 2, part_k)) * rl * round4(n)) + 512;
+}
+
+__global__ void sum_parts_kernel(const float* __restrict__ parts, int nparts, long long stride, long long rows,
+                                 long long cols, long long ldp, float* __restrict__ out, long long ldo) {
+    const long long total = rows * cols;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = e / cols, j = e - i * cols;
+        double s = 0.0;
+        for (int c = 0; c < nparts; ++c) s += static_cast<double>(parts[c * stride + i * ldp + j]);
+        out[i * ldo + j] = static_cast<float>(s);
+    }
+}
+
+gn_status sum_parts(gn_handle h, const float* parts, int nparts, long long stride, long long rows, long long cols,
+                    long long ldp, float* out, long long ldo) {
+    const long long total = rows * cols;
+    const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 16LL * h->sm_count));
+    sum_parts_kernel<<<blocks, 256, 0, h->stream>>>(parts, nparts, stride, rows, cols, ldp, out, ldo);
+    count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    return GN_OK;
+}
+
 gn_status launch_sketch_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* AX,
-                           gn_mat* YtA) {
+                           gn_mat* YtA, void* ws, size_t ws_bytes) {
     const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols;
     TcParams p;
     memset(&p, 0, sizeof(p));
@@ -206,11 +253,40 @@ gn_status launch_sketch_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const 
     }
     g1.D = static_cast<float*>(YtA->data);
     g1.ldd = YtA->ld;
+    // split-BF16 operands with FP64-level accumulation: stored K parts, summed in FP64
+    float *pax = nullptr, *pyta = nullptr;
+    int sax = 1, syta = 1;
+    const long long ldpx = round4(r), ldpy = round4(n);
+    if (nsrc == 2 && h->fp64_accum > 0) {
+        const long long pk = h->fp64_accum;
+        sax = acc_parts(n, 2, pk);
+        syta = acc_parts(m, 2, pk);
+        if (!ws || ws_bytes < split_parts_ws(m, n, r, rl, pk)) return GN_ERR_WORKSPACE;
+        pax = static_cast<float*>(ws);
+        pyta = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(4 * static_cast<size_t>(sax) * m * ldpx));
+        g0.D = pax;
+        g0.ldd = ldpx;
+        g0.ksplit = sax;
+        g0.part_stride = m * ldpx;
+        g1.D = pyta;
+        g1.ldd = ldpy;
+        g1.ksplit = syta;
+        g1.part_stride = rl * ldpy;
+        if (sax < 2) g0.ksplit = 0, g0.part_stride = 0;
+        if (syta < 2) g1.ksplit = 0, g1.part_stride = 0;
+    }
+    auto finish = [&]() -> gn_status {
+        if (!pax) return GN_OK;
+        if (r > 0) GN_TRY(sum_parts(h, pax, sax, m * ldpx, m, r, ldpx, static_cast<float*>(AX->data), AX->ld));
+        if (rl > 0) GN_TRY(sum_parts(h, pyta, syta, rl * ldpy, rl, n, ldpy, static_cast<float*>(YtA->data), YtA->ld));
+        return GN_OK;
+    };
     if (r == 0 || rl == 0) {   // a block sketch that needs one product only
         if (r == 0) p.g[0] = p.g[1];
-        p.g[0].ksplit = 0;
+        if (!pax) p.g[0].ksplit = 0;
         p.ngemm = 1;
-        return tc_launch(h, &p);
+        GN_TRY(tc_launch(h, &p));
+        return finish();
     }
     // Order: the longer-K GEMM first (its tiles are the expensive ones).
     if (m >= n) {
@@ -219,7 +295,8 @@ gn_status launch_sketch_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const 
         p.g[1] = t;
     }
     p.ngemm = 2;
-    return tc_launch(h, &p);
+    GN_TRY(tc_launch(h, &p));
+    return finish();
 }
 
 // e4m3 sketch: both products from K-major operands in one block-scaled launch.
@@ -397,7 +474,7 @@ gn_status sketch_block(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_m
         GN_TRY(check_tma_operand(A));
         if (r > 0) GN_TRY(check_tma_operand(X));
         if (rl > 0) GN_TRY(check_tma_operand(Y));
-        return launch_sketch_tc(h, A, X, Y, AX, YtA);
+        return launch_sketch_tc(h, A, X, Y, AX, YtA, ws, ws_bytes);
     }
     return GN_ERR_DTYPE;
 }
@@ -442,6 +519,7 @@ gn_status gn_create(gn_handle* out, void* stream) {
     h->batched_policy = 0;
     h->fp64_g = 0;
     h->fp64_tc = 1;
+    h->fp64_accum = 0;
     h->stall_test = 0;
     if (cudaMalloc(&h->dstatus, 64) != cudaSuccess) {
         delete h;
@@ -511,6 +589,12 @@ gn_status gn_set_fp64_g(gn_handle h, int32_t fp64_g) {
     return GN_OK;
 }
 
+gn_status gn_set_fp64_accum(gn_handle h, int64_t part_k) {
+    if (!h || (part_k != 0 && (part_k < 4096 || part_k % 64))) return GN_ERR_INVALID_ARG;
+    h->fp64_accum = part_k;
+    return GN_OK;
+}
+
 gn_status gn_set_fp64_tc(gn_handle h, int32_t on) {
     if (!h || (on != 0 && on != 1)) return GN_ERR_INVALID_ARG;
     h->fp64_tc = on;
@@ -568,6 +652,7 @@ gn_status gn_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int32_t 
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int mixed = op_dtype != GN_F64;
     size_t b = core_ws(n, r, l, mixed, sms) + (op_dtype == GN_E4M3 ? core_e4m3_ws(n, r) : 0);
+    if (op_dtype == GN_BF16X2) b = std::max(b, split_parts_ws(m, n, r, r + l, 4096));
     if (op_dtype == GN_E4M3) b = std::max(b, sketch_e4m3_ws(m, n, r, l));
     b = std::max(b, factors_ws(m, n, r, l, mixed, sms));
     b = std::max(b, hmt_ws(m, n, r, sms));
@@ -675,6 +760,17 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     } else if (fp64) {
         GN_TRY(dgemm(h, rl, r, n, 1.0, static_cast<const double*>(YtA->data), YtA->ld, 0,
                      static_cast<const double*>(X->data), X->ld, 0, 0.0, core->C, r, inner, inner_bytes));
+    } else if (h->fp64_accum && !x8) {
+        // FP64-level C: (Y^T A) X by exact digit slicing on the tensor cores
+        double* X64 = inner;
+        const size_t xb = align256(sizeof(double) * n * r);
+        const long long total = n * r;
+        bf16_to_f64_kernel<<<static_cast<int>(std::min<long long>((total + 255) / 256, 16LL * h->sm_count)), 256, 0,
+                             h->stream>>>(static_cast<const __nv_bfloat16*>(X->data), n, r, X->ld, X64, r);
+        count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        GN_TRY(oz_dgemm(h, rl, r, n, 1.0, YtA->data, 1, YtA->ld, 0, X64, r, 0, 0.0, core->C, r,
+                        reinterpret_cast<char*>(inner) + xb, inner_bytes - xb));
     } else {
         if (!x8) GN_TRY(check_tma_operand(X));
         GN_TRY(split3_bf16(h, static_cast<const float*>(YtA->data), rl, n, YtA->ld, s_hi, s_mid, s_lo, lds));
@@ -802,7 +898,7 @@ gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_
         return GN_ERR_SHAPE;
     if (AX->dtype != GN_F64 && AX->dtype != GN_F32) return GN_ERR_DTYPE;
     if (YtA->dtype != GN_F64 && YtA->dtype != GN_F32) return GN_ERR_DTYPE;
-    const int tc_g = YtA->dtype == GN_F32 && !h->fp64_g;
+    const int tc_g = YtA->dtype == GN_F32 && !h->fp64_g && !h->fp64_accum;
     const int mixed = AX->dtype == GN_F32 || YtA->dtype == GN_F32;
     if (ws_bytes < factors_ws(m, n, r, l, mixed, h->sm_count)) return GN_ERR_WORKSPACE;
     double* Fd = static_cast<double*>(F->data);

@@ -27,6 +27,7 @@ struct gn_handle_s {
     int batched_policy;        // tile policy of the next gn_batched_prepare
     int fp64_g;                // gn_factors: FP64 G even for FP32 Y^T A
     int fp64_tc;               // gn_factors: digit-sliced tensor-core FP64 products (FP32 AX)
+    long long fp64_accum;      // gn_set_fp64_accum: K per stored part of split sketches (0: off); C, G in FP64
     int stall_test;            // gn_set_stall_test: the next sketch launches wait on a barrier nothing completes
     // gn_core with GN_CORE_DEFER: the core whose k and diagnostics are still on
     // their way to the pinned host words; gn_core_finish completes it.
@@ -79,8 +80,10 @@ struct TcGemm {
     float* D;
     long long ldd;
     int vec4;                // D rows 16-byte aligned -> float4 stores
-    int ksplit;              // 2: every tile runs as two half-K items adding into a pre-zeroed D
+    int ksplit;              // S >= 2: every tile runs as S items over equal parts of its K range
                              // (single launches only; 0 or 1: whole K)
+    long long part_stride;   // 0: the S parts add into a pre-zeroed D; > 0: part c is stored
+                             // (not added) at D + c * part_stride, to be summed by the caller
     // e4m3 launches (TcParams::f8): scale-factor images, 512 bytes of the tile's
     // UE8M0 byte per 128 x 128 tile of the original matrix, row-major over tiles.
     const uint8_t* sfa;

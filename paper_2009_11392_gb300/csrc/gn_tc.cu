@@ -231,7 +231,7 @@ __device__ __forceinline__ uint32_t instr_desc_bf16(int m, int n, int a_mn, int 
 
 struct TileCoord {
     int g, tm, tn;
-    int half;   // 0: whole K range; 1, 2: first / second half (adds into D)
+    int half;   // 0: whole K range; c >= 1: part c of the K range (of ksplit parts, or of 2)
 };
 
 // GEMM descriptors and tensor maps live in the kernel parameters (up to four
@@ -273,19 +273,20 @@ __device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t) {
     const int local = t - G.tile_base;
     const int ctm_n = G.tiles_m;
     int ctm;
-    if (!GROUPED && G.ksplit == 2) {
-        // the two K halves of a tile are separate items; the items that share an
-        // operand panel (same half) stay consecutive
+    if (!GROUPED && G.ksplit >= 2) {
+        // the K parts of a tile are separate items; the items that share an
+        // operand panel (same part) stay consecutive
+        const int S = G.ksplit;
         if (G.a_mn) {
             ctm = local % ctm_n;
             const int v = local / ctm_n;
-            c.half = 1 + (v & 1);
-            c.tn = v >> 1;
+            c.half = 1 + v % S;
+            c.tn = v / S;
         } else {
             c.tn = local % G.tiles_n;
             const int v = local / G.tiles_n;
-            c.half = 1 + (v & 1);
-            ctm = v >> 1;
+            c.half = 1 + v % S;
+            ctm = v / S;
         }
     } else if (G.a_mn) {   // A operand is the small sketch (Y^T): walk M fastest so the big B is shared
         ctm = local % ctm_n;
@@ -373,7 +374,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                 const TileCoord c = decode_tile<GROUPED>(p, t);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
-                const int kb0 = c.half == 2 ? nkb / 2 : 0, kb1 = c.half == 1 ? nkb / 2 : nkb;
+                const int S = G.ksplit >= 2 ? G.ksplit : 2;
+                const int kb0 = c.half ? (c.half - 1) * nkb / S : 0, kb1 = c.half ? c.half * nkb / S : nkb;
                 const uint32_t bytes = A_STAGE_BYTES + G.bn * BK * 2 + K::SF_STAGE;
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(empty_bar(stage), ephase ^ 1u, limit, abort_flag)) {
@@ -454,7 +456,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                 const TileCoord c = decode_tile<GROUPED>(p, t);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
-                const int kb0 = c.half == 2 ? nkb / 2 : 0, kb1 = c.half == 1 ? nkb / 2 : nkb;
+                const int S = G.ksplit >= 2 ? G.ksplit : 2;
+                const int kb0 = c.half ? (c.half - 1) * nkb / S : 0, kb1 = c.half ? c.half * nkb / S : nkb;
                 const uint32_t idesc = F8 ? 0u : instr_desc_bf16(BM, G.bn, G.a_mn, G.b_mn);
                 if (!mbar_wait(tempty_bar(acc), aphase ^ 1u, limit, abort_flag)) {
                     latch(p.status, GN_ERR_TIMEOUT, 3, abort_flag);
@@ -545,10 +548,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             }
             tc_fence_after();
 #pragma unroll 1
+            // part c of a K range split into stored parts goes to its own copy of D
+            const bool stored_part = c.half && G.ksplit >= 2 && G.part_stride > 0;
+            float* Dbase = stored_part ? G.D + (c.half - 1) * G.part_stride : G.D;
             for (int hh = 0; hh < MT; ++hh) {
                 const int row = c.tm * K::TM + hh * BM + q * 32 + lane;
                 const bool row_ok = row < G.M;
-                float* drow = G.D + static_cast<long long>(row_ok ? row : 0) * G.ldd;
+                float* drow = Dbase + static_cast<long long>(row_ok ? row : 0) * G.ldd;
                 for (int c0 = 0; c0 < G.bn; c0 += 32) {
                     uint32_t v[32];
                     tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + (acc * MT + hh) * 256 + c0, v);
@@ -556,7 +562,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
                     if (!row_ok || col0 >= G.N) continue;
                     // columns of this chunk inside both the tile and D
                     const int ncol = min(min(32, G.bn - c0), G.N - col0);
-                    if (c.half) {   // half of the K range: add into the pre-zeroed D
+                    if (c.half && !stored_part) {   // part of the K range: add into the pre-zeroed D
                         if (G.vec4 && ncol == 32) {
                             float4* dst = reinterpret_cast<float4*>(drow + col0);
 #pragma unroll
@@ -675,7 +681,7 @@ int pick_mt(const TcGemm* g, int ngemm, int sm_count) {
     long long tiles2 = 0;   // work items with 256-row tiles (a K-split tile counts twice)
     for (int i = 0; i < ngemm; ++i) {
         if (g[i].M < 2 * BM) return 1;
-        tiles2 += ((g[i].M + 2 * BM - 1) / (2 * BM)) * ((g[i].N + g[i].bn - 1) / g[i].bn) * (g[i].ksplit == 2 ? 2 : 1);
+        tiles2 += ((g[i].M + 2 * BM - 1) / (2 * BM)) * ((g[i].N + g[i].bn - 1) / g[i].bn) * (g[i].ksplit >= 2 ? g[i].ksplit : 1);
     }
     return tiles2 >= 4LL * sm_count ? 2 : 1;   // keep enough tiles to fill the GPU
 }
@@ -691,10 +697,12 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
     int total = 0;
     for (int i = 0; i < p->ngemm; ++i) {
         TcGemm& G = p->g[i];
-        if (G.ksplit == 2 && (p->f8 || G.nsrc * G.kblocks < 8)) G.ksplit = 1;
+        // parts that add into D need enough K to pay; stored parts are the caller's layout
+        if (G.ksplit >= 2 && G.part_stride == 0 && (p->f8 || G.nsrc * G.kblocks < 4 * G.ksplit)) G.ksplit = 1;
+        if (G.ksplit >= 2 && G.part_stride > 0 && G.nsrc * G.kblocks < G.ksplit) return GN_ERR_INVALID_ARG;
         G.tile_base = total;
-        total += G.tiles_m * G.tiles_n * (G.ksplit == 2 ? 2 : 1);
-        if (G.ksplit == 2)   // both halves add into D
+        total += G.tiles_m * G.tiles_n * (G.ksplit >= 2 ? G.ksplit : 1);
+        if (G.ksplit >= 2 && G.part_stride == 0)   // the parts add into D
             GN_CUDA_TRY(cudaMemset2DAsync(G.D, sizeof(float) * G.ldd, 0, sizeof(float) * G.N, G.M, h->stream));
     }
     // Balance the last round: when the tiles leave a partial round of R tiles
@@ -707,7 +715,7 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
         const int ncl = std::min(total, h->sm_count);
         const int R = total % ncl;
         const TcGemm& G = p->g[p->ngemm - 1];
-        if (total > ncl && R > 0 && 2 * R <= ncl && !G.a_mn && G.ksplit != 2 && R % G.tiles_n == 0 &&
+        if (total > ncl && R > 0 && 2 * R <= ncl && !G.a_mn && G.ksplit < 2 && R % G.tiles_n == 0 &&
             G.nsrc * G.kblocks >= 8) {
             const long long row0 = static_cast<long long>(G.tiles_m - R / G.tiles_n) * BM * MT;
             if (row0 >= 0 && row0 < G.M) {

@@ -39,8 +39,13 @@ def test_dct_sketch_matrix_against_oracle(gn, H, n, r):
     Xb = H.dct_sketch(n, signs, cols, dtype=torch.bfloat16)
     got = Xb.double().cpu().numpy()
     want = O.quantize_bf16(ref)
-    diff = got != want
-    # a mismatch only where the oracle's value sits within 1e-11 of a rounding boundary
+    # where the angle is an odd multiple of pi/2 the cosine is exactly 0: the
+    # device reduces the angle exactly and gets 0, numpy's unreduced angle gives
+    # about 1e-16; elsewhere a mismatch only where the oracle's FP64 value sits
+    # within its 1e-11 of a BF16 rounding boundary (one unit apart)
+    exact_zero = np.abs(ref) <= 1e-12
+    assert np.all(got[exact_zero] == 0.0)
+    diff = (got != want) & ~exact_zero
     assert diff.sum() <= max(1, diff.size // 100000)
     if diff.any():
         assert np.all(np.abs(got[diff] - want[diff]) <= 2.0 ** -7 * np.abs(want[diff]))

@@ -435,3 +435,35 @@ def test_core_diagnostics_cluster_path(gn, H, kind):
         assert core.k == 70
     k = core.k
     assert rel(npy(F)[:, :k] @ npy(G)[:k], Ahat) <= 1e-9
+
+
+@pytest.mark.parametrize("part_k", [4096, 8192])
+def test_split_sketch_fp64_accumulation_parts(gn, H, part_k):
+    """Split-BF16 sketches with FP64-level accumulation (gn_set_fp64_accum): the K
+    range runs as stored parts summed in FP64.  Integer inputs (every part sum
+    exact): AX and Y^T A equal the oracle's products bit for bit with several
+    parts on both products and ragged tails; the core's C then equals the exact
+    (Y^T A) X (digit-sliced product, FP64-accurate)."""
+    m, n, r, l = 2500, 9000, 100, 50
+    g = torch.Generator().manual_seed(91)
+    draw = lambda a, b: torch.randint(-3, 4, (a, b), generator=g).double()
+    A, X, Y = draw(m, n), draw(n, r), draw(m, r + l)
+    Ahi, Alo = H.quantize(A.cuda(), split=True)
+    Xb, Yb = H.quantize(X.cuda()), H.quantize(Y.cuda())
+    ws = H.workspace(m, n, r, l, gn.BF16X2)
+    AX = torch.full((m, r), float("nan"), dtype=torch.float32, device="cuda")
+    YtA = torch.full((r + l, n), float("nan"), dtype=torch.float32, device="cuda")
+    H.set_fp64_accum(part_k)
+    try:
+        H.sketch(Ahi, Xb, Yb, AX, YtA, ws, A_lo=Alo)
+        core = gn.Core.empty(r, l, "cuda")
+        H.core(YtA, Xb, 0.0, gn.PLAIN, core, ws)
+        assert H.sync_status() == 0
+    finally:
+        H.set_fp64_accum(0)
+    oAX, oYtA = O.sketch(A.numpy(), X.numpy(), Y.numpy())
+    assert np.array_equal(npy(AX), oAX)
+    assert np.array_equal(npy(YtA), oYtA)
+    C = npy(core.C)
+    oC = oYtA @ X.numpy()
+    assert np.max(np.abs(C - oC)) <= 1e-13 * np.max(np.abs(oC))
