@@ -701,7 +701,11 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
     contract("bf16", Ab64, Xq, Yq, e_a, e_s)
     del Ab64
 
-    # split bf16 (hi + lo) path: throughput and the contract
+    # split bf16 (hi + lo) path: throughput and the contract.  It aims at the FP64
+    # path's error, so its accumulation is FP64-level: sketches in stored K parts
+    # of 8192 summed in FP64, digit-sliced C, FP64 G (gn_set_fp64_accum).
+    part_k = 8192
+    H.set_fp64_accum(part_k)
     Ahi, Alo = H.quantize(A64, split=True)
     H.sketch(Ahi, Xb, Yb, AX, YtA, ws, A_lo=Alo)
     H.core(YtA, Xb, eps, mode, core, ws)
@@ -717,14 +721,14 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
     torch.cuda.synchronize()
     split_ms = s0.elapsed_time(s1) / reps
     split_sketch_ms = k0.elapsed_time(k1)
-    H.set_fp64_g(True)   # split BF16 aims at the FP64 path's error: G in FP64 too
     Asp64 = Ahi.double() + Alo.double()
     e_a = err_of(AX, YtA, core, A64)
     e_s = err_of(AX, YtA, core, Asp64)
-    H.set_fp64_g(False)
+    H.set_fp64_accum(0)
     fl2 = 2 * fl
     out["split_bf16"] = {"approx_per_s": 1e3 / split_ms, "ms_per_step": split_ms, "sketch_ms": split_sketch_ms,
-                         "sketch_tflops": fl2 / (split_sketch_ms / 1e3) / 1e12, "err": e_a, "g_fp64": True}
+                         "sketch_tflops": fl2 / (split_sketch_ms / 1e3) / 1e12, "err": e_a,
+                         "fp64_accum_part_k": part_k, "g_fp64": True}
     contract("split_bf16", Asp64, Xq, Yq, e_a, e_s)
     del Ahi, Alo, Asp64
 

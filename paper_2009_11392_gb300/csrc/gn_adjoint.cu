@@ -12,11 +12,12 @@
 // Section 5.1 rule: never form the core's inverse).  FP64 inputs: every step
 // in FP64 on the FP64 units.  FP32 inputs, all on the tcgen05 tensor cores
 // except the QR, the two triangular solves and the r x r algebra (FP64): the
-// sketches AX, Y^T A and the core C = (Y^T A) X, whose errors the core's
-// conditioning amplifies, as FP64-accurate digit-sliced products; the
-// contractions over G and the two rank-r products that form the gradient (S1,
-// S2, W, P, Q S2, dA) as three-slice BF16 products (x = s0 + s1 + s2, the six
-// slice products of order <= 2, FP32 accumulation: FP32-level accuracy).  With K R^T = (I - Q Q^T) W^T - Q W Q,
+// sketches AX, Y^T A, the core C = (Y^T A) X and the contractions over G (S1,
+// S2, W), whose errors the core's conditioning and the projection I - Q Q^T
+// amplify, as FP64-accurate digit-sliced products; the products after those
+// (P, Q S2 and the two rank-r products that form the gradient) as three-slice
+// BF16 products (x = s0 + s1 + s2, the six slice products of order <= 2, FP32
+// accumulation: FP32-level accuracy).  With K R^T = (I - Q Q^T) W^T - Q W Q,
 // the two m x r terms share one solve: P = (S1 Q + Y (K R^T)) R^{-T}.  Sketches
 // are recomputed from A in every call (nothing is kept from a forward pass).
 #include "gn_internal.cuh"
@@ -297,9 +298,9 @@ size_t backward_fixed(long long m, long long n, long long r, long long l, int f3
 // ---------------------------------------------------------------- FP32 inputs on the tensor cores
 // Workspace of the FP32 path (forward and backward share the layout).
 struct TcWs {
-    Plane Gs, Xs, Ys, YtATs, Fs, S1s, S2s, Qs, Kts, Ps, QpTs, Ahs;
-    float *S1, *S2, *W32, *P32, *QpT;
-    double *X64, *Y64, *AX, *YtAT, *C, *Wq, *Q, *R, *W64, *Wt, *M1, *P64;
+    Plane Xs, Ys, YtATs, Fs, S1s, S2Ts, Qs, Kts, Ps, QpTs, Ahs;
+    float *S2, *P32, *QpT;
+    double *X64, *Y64, *AX, *YtAT, *C, *Wq, *Q, *R, *W64, *Wt, *M1, *P64, *S1, *S2T;
     double* inner;
     size_t inner_bytes;
     void* oz;
@@ -313,7 +314,8 @@ size_t tc_inner_bytes(long long m, long long n, long long r, long long l, int sm
 }
 size_t tc_oz_bytes(long long m, long long n, long long r, long long l) {
     return std::max({oz_ws_bytes(m, r, n, 1), oz_ws_bytes(n, r + l, m, 1), oz_ws_bytes(r + l, r, n, 0),
-                     oz_ws_bytes(m, 128, r, 0)});
+                     oz_ws_bytes(m, 128, r, 0), oz_ws_bytes(m, r + l, n, 1), oz_ws_bytes(n, r, m, 1),
+                     oz_ws_bytes(r, r + l, m, 0)});
 }
 
 // Carves (or, with base == nullptr, sizes) the FP32 path's workspace.
@@ -334,13 +336,12 @@ size_t tc_carve(long long m, long long n, long long r, long long l, int sms, cha
         return p;
     };
     TcWs t;
-    t.Gs = plane(m, n);
     t.Xs = plane(n, r);
     t.Ys = plane(m, rl);
     t.YtATs = plane(n, rl);
     t.Fs = plane(m, r);
     t.S1s = plane(m, rl);
-    t.S2s = plane(r, n);
+    t.S2Ts = plane(n, r);
     t.Qs = plane(rl, r);
     t.Kts = plane(rl, r);
     t.Ps = plane(m, r);
@@ -348,9 +349,7 @@ size_t tc_carve(long long m, long long n, long long r, long long l, int sms, cha
     t.Ahs = plane(r, n);
     auto f32 = [&](long long rows, long long cols) { return reinterpret_cast<float*>(take(4 * rows * rnd8(cols))); };
     auto f64 = [&](long long count) { return reinterpret_cast<double*>(take(8 * count)); };
-    t.S1 = f32(m, rl);
     t.S2 = f32(r, n);
-    t.W32 = f32(r, rl);
     t.P32 = f32(m, r);
     t.QpT = f32(n, rl);
     t.X64 = f64(n * r);
@@ -365,6 +364,8 @@ size_t tc_carve(long long m, long long n, long long r, long long l, int sms, cha
     t.Wt = f64(rl * r);
     t.M1 = f64(r * r);
     t.P64 = f64(m * r);
+    t.S1 = f64(m * rl);
+    t.S2T = f64(n * r);
     t.oz_bytes = tc_oz_bytes(m, n, r, l);
     t.oz = take(t.oz_bytes);
     t.inner_bytes = tc_inner_bytes(m, n, r, l, sms);
@@ -400,33 +401,28 @@ gn_status backward_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_ma
     TcWs t;
     if (tc_carve(m, n, r, rl - r, h->sm_count, static_cast<char*>(ws), &t) > ws_bytes) return GN_ERR_WORKSPACE;
     GN_TRY(tc_front(h, A, X, Y, m, n, r, rl, t));
-    // S1 = G (Y^T A)^T (m x (r+l)), S2 = F^T G (r x n)
-    GN_TRY(split3s(h, Gup->data, 0, Gup->ld, t.Gs));
-    X6 g[2];
-    g[0] = X6{static_cast<int>(m), static_cast<int>(rl), static_cast<int>(n), 0, 1, 1, {&t.Gs}, {&t.YtATs},
-              t.S1, rnd8(rl)};
-    g[1] = X6{static_cast<int>(r), static_cast<int>(n), static_cast<int>(m), 1, 1, 1, {&t.Fs}, {&t.Gs},
-              t.S2, rnd8(n)};
-    GN_TRY(x6_launch(h, g, 2));
-    // W = F^T S1 (r x (r+l))
-    GN_TRY(split3s(h, t.S1, 0, rnd8(rl), t.S1s));
-    g[0] = X6{static_cast<int>(r), static_cast<int>(rl), static_cast<int>(m), 1, 1, 1, {&t.Fs}, {&t.S1s},
-              t.W32, rnd8(rl)};
-    GN_TRY(x6_launch(h, g, 1));
-    GN_TRY(copy_f32_to_f64(h, t.W32, r, rl, rnd8(rl), t.W64, rl));
+    const double* F = t.AX;
+    // The contractions over G feed W and K, where the projection (I - Q Q^T)
+    // cancels most of W^T: FP64-accurate digit-sliced products.
+    //   S1 = G (Y^T A)^T (m x (r+l)),  S2^T = G^T F (n x r),  W = F^T S1 (r x (r+l))
+    GN_TRY(oz_dgemm(h, m, rl, n, 1.0, Gup->data, 1, Gup->ld, 0, t.YtAT, rl, 0, 0.0, t.S1, rl, t.oz, t.oz_bytes));
+    GN_TRY(oz_dgemm(h, n, r, m, 1.0, Gup->data, 1, Gup->ld, 1, F, r, 0, 0.0, t.S2T, r, t.oz, t.oz_bytes));
+    GN_TRY(oz_dgemm(h, r, rl, m, 1.0, F, 0, r, 1, t.S1, rl, 0, 0.0, t.W64, rl, t.oz, t.oz_bytes));
     // K R^T = W^T - Q (Q^T W^T + W Q)   ((r+l) x r, FP64)
     GN_TRY(transpose_f64(h, t.W64, r, rl, rl, t.Wt, r));
     GN_TRY(dgemm(h, r, r, rl, 1.0, t.Q, r, 1, t.Wt, r, 0, 0.0, t.M1, r, t.inner, t.inner_bytes));
     GN_TRY(dgemm(h, r, r, rl, 1.0, t.W64, rl, 0, t.Q, r, 0, 1.0, t.M1, r, t.inner, t.inner_bytes));
     GN_TRY(dgemm(h, rl, r, r, -1.0, t.Q, r, 0, t.M1, r, 0, 1.0, t.Wt, r, t.inner, t.inner_bytes));
     // P = (S1 Q + Y (K R^T)) R^{-T} (m x r);  Q'^T = S2^T Q^T (n x (r+l))
+    GN_TRY(split3s(h, t.S1, 1, rl, t.S1s));
     GN_TRY(split3s(h, t.Wt, 1, r, t.Kts));
     GN_TRY(split3s(h, Y->data, 0, Y->ld, t.Ys));
-    GN_TRY(split3s(h, t.S2, 0, rnd8(n), t.S2s));
+    GN_TRY(split3s(h, t.S2T, 1, r, t.S2Ts));
+    X6 g[1];
     g[0] = X6{static_cast<int>(m), static_cast<int>(r), static_cast<int>(rl), 0, 1, 2, {&t.S1s, &t.Ys},
               {&t.Qs, &t.Kts}, t.P32, rnd8(r)};
     GN_TRY(x6_launch(h, g, 1));   // 12 tensor maps: the launch's limit
-    g[0] = X6{static_cast<int>(n), static_cast<int>(rl), static_cast<int>(r), 1, 0, 1, {&t.S2s}, {&t.Qs},
+    g[0] = X6{static_cast<int>(n), static_cast<int>(rl), static_cast<int>(r), 0, 0, 1, {&t.S2Ts}, {&t.Qs},
               t.QpT, rnd8(rl)};
     GN_TRY(x6_launch(h, g, 1));
     GN_TRY(copy_f32_to_f64(h, t.P32, m, r, rnd8(r), t.P64, r));

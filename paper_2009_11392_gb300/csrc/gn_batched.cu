@@ -93,21 +93,28 @@ __device__ void smem_qr(const Smem& sm, int M, int N) {
     for (int j = 0; j < N; ++j) {
         for (int q0 = j; q0 < N; q0 += 32) {
             const int q = q0 + lane;
-            double acc = 0.0;
+            // two partial sums: a dependent FP64 instruction costs ~200 cycles
+            double a0 = 0.0, a1 = 0.0;
             if (q < N) {
-                if (q == j) {
-                    for (int i = j + 1 + warp; i < M; i += BW) acc = fma(S[i * ld + j], S[i * ld + j], acc);
-                } else {
-                    for (int i = j + warp; i < M; i += BW) acc = fma(S[i * ld + j], S[i * ld + q], acc);
+                const int q2 = q == j ? j : q;
+                int i = (q == j ? j + 1 : j) + warp;
+                for (; i + BW < M; i += 2 * BW) {
+                    a0 = fma(S[i * ld + j], S[i * ld + q2], a0);
+                    a1 = fma(S[(i + BW) * ld + j], S[(i + BW) * ld + q2], a1);
                 }
+                if (i < M) a0 = fma(S[i * ld + j], S[i * ld + q2], a0);
             }
-            if (q < N) sm.red[warp * NMAX + (q - j)] = acc;
+            if (q < N) sm.red[warp * NMAX + (q - j)] = a0 + a1;
         }
         __syncthreads();
         if (tid < N - j) {
-            double s = 0.0;
+            double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-            for (int w = 0; w < BW; ++w) s += sm.red[w * NMAX + tid];
+            for (int w = 0; w < BW; w += 2) {
+                s0 += sm.red[w * NMAX + tid];
+                s1 += sm.red[(w + 1) * NMAX + tid];
+            }
+            const double s = s0 + s1;
             if (tid == 0) {
                 const double alpha = S[j * ld + j];
                 if (s == 0.0) {
@@ -163,20 +170,27 @@ __device__ void smem_form_q(const Smem& sm, int M, int N) {
             // w_q = v^T S[j:, q] for q > j (v_j = 1), then S[j:, q] -= t v w_q
             for (int q0 = j + 1; q0 < N; q0 += 32) {
                 const int q = q0 + lane;
-                double acc = 0.0;
-                if (q < N)
-                    for (int i = j + warp; i < M; i += BW) {
+                double a0 = 0.0, a1 = 0.0;
+                if (q < N) {
+                    int i = j + warp;
+                    for (; i + BW < M; i += 2 * BW) {
                         const double vi = (i == j) ? 1.0 : S[i * ld + j];
-                        acc = fma(vi, S[i * ld + q], acc);
+                        a0 = fma(vi, S[i * ld + q], a0);
+                        a1 = fma(S[(i + BW) * ld + j], S[(i + BW) * ld + q], a1);
                     }
-                if (q < N) sm.red[warp * NMAX + (q - j)] = acc;
+                    if (i < M) a0 = fma((i == j) ? 1.0 : S[i * ld + j], S[i * ld + q], a0);
+                }
+                if (q < N) sm.red[warp * NMAX + (q - j)] = a0 + a1;
             }
             __syncthreads();
             if (tid > 0 && tid < N - j) {
-                double s = 0.0;
+                double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-                for (int w = 0; w < BW; ++w) s += sm.red[w * NMAX + tid];
-                sm.wv[tid] = t * s;
+                for (int w = 0; w < BW; w += 2) {
+                    s0 += sm.red[w * NMAX + tid];
+                    s1 += sm.red[(w + 1) * NMAX + tid];
+                }
+                sm.wv[tid] = t * (s0 + s1);
             }
             __syncthreads();
             for (int q0 = j + 1; q0 < N; q0 += 32) {
@@ -241,22 +255,23 @@ __device__ void smem_tri_solve(const double* R, int ld, int N, double* z, int lo
             if (lane < jb) z[j0 + lane] = zl;
         }
         __syncthreads();
+        // four partial sums per update (short FP64 dependency chains)
         if (lower) {
             for (int jj = j0 + jb + tid; jj < N; jj += BT) {
-                double a = z[jj];
+                double a[4] = {z[jj], 0.0, 0.0, 0.0};
 #pragma unroll
                 for (int i = 0; i < 32; ++i)
-                    if (i < jb) a = fma(-R[(j0 + i) * ld + jj], z[j0 + i], a);
-                z[jj] = a;
+                    if (i < jb) a[i & 3] = fma(-R[(j0 + i) * ld + jj], z[j0 + i], a[i & 3]);
+                z[jj] = (a[0] + a[1]) + (a[2] + a[3]);
             }
         } else {
             for (int i = tid; i < j0; i += BT) {
-                double a = z[i];
+                double a[4] = {z[i], 0.0, 0.0, 0.0};
                 const double* rr = R + i * ld + j0;
 #pragma unroll
                 for (int jj = 0; jj < 32; ++jj)
-                    if (jj < jb) a = fma(-rr[jj], z[j0 + jj], a);
-                z[i] = a;
+                    if (jj < jb) a[jj & 3] = fma(-rr[jj], z[j0 + jj], a[jj & 3]);
+                z[i] = (a[0] + a[1]) + (a[2] + a[3]);
             }
         }
         __syncthreads();
@@ -327,16 +342,30 @@ __global__ void __launch_bounds__(BT) batched_core_kernel(const ProblemDev* __re
             __syncthreads();
             for (int it = 0; it < DIAG_ITERS_B; ++it) {
                 double* y = sm.dsum;
-                for (int i = tid; i < N; i += BT) {
+                // y = R z: a warp per row, lanes over its columns
+                const int warp = tid >> 5, lane = tid & 31;
+                for (int i = warp; i < N; i += BW) {
                     double a = 0.0;
-                    for (int jj = i; jj < N; ++jj) a = fma(p.R[i * N + jj], z[jj], a);
-                    y[i] = a;
+                    for (int jj = i + lane; jj < N; jj += 32) a = fma(p.R[i * N + jj], z[jj], a);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                    if (lane == 0) y[i] = a;
+                }
+                __syncthreads();
+                // w = R^T y: every column split into BT / N row parts, partials combined
+                const int parts = min(BT / N, BW);   // sm.red holds BW rows of NMAX
+                {
+                    const int jj = tid % N, part = tid / N;
+                    double a = 0.0;
+                    if (part < parts)
+                        for (int i = part; i <= jj; i += parts) a = fma(p.R[i * N + jj], y[i], a);
+                    if (part < parts) sm.red[part * NMAX + jj] = a;
                 }
                 __syncthreads();
                 double ss = 0.0;
                 for (int jj = tid; jj < N; jj += BT) {
                     double a = 0.0;
-                    for (int i = 0; i <= jj; ++i) a = fma(p.R[i * N + jj], y[i], a);
+                    for (int part = 0; part < parts; ++part) a += sm.red[part * NMAX + jj];
                     sm.wv[jj] = a;
                     ss = fma(a, a, ss);
                 }
