@@ -775,6 +775,8 @@ def side_measurements(a, gn, H, stream, dev, A64, X64, Y64, Ab, Xb, Yb, eps, mod
     out["dct_sketch"] = dct_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode, out["err_bf16"])
     out["fp64_cases"] = fp64_cases(gn, H, stream, dev)
     out["sparse_countsketch"] = sparse_measurement(gn, H, stream, dev)
+    out["sgn_variants"] = variants_measurement(gn, H, stream, dev)
+    out["oversampling_sweep"] = oversampling_sweep(gn, H, stream, dev)
     out["sketch_state_ops"] = sketch_state_ops(gn, H, stream, dev, a, Ab, Xb, Yb, eps, mode)
     out["r2000"] = r2000_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode)
     out["adjoint"] = adjoint_measurement(gn, H, stream, dev)
@@ -859,6 +861,84 @@ def sparse_measurement(gn, H, stream, dev, m=178866, n=178866, r=200, l=100, k=5
     del AX, YtA, core, ws, crow, col, val
     torch.cuda.empty_cache()
     return out
+
+
+def variants_measurement(gn, H, stream, dev, m=4096, n=2048, r=100, l=50):
+    """Section 5.1.1's alternatives on one FP64 sketch state (W1 diag(i^-2) W2^T
+    + 1e-8 noise): SGN with the SVD eps-pseudoinverse, raised singular values,
+    pivoted QR with raised diagonal, raised diagonal, beside the library's
+    QR-truncation core (AUTO); floor = 10 u ||C||_2 for all; time (after a
+    warm-up) and error against A."""
+    p = gn_synth.config2(m=m, n=n, r=r, l=l, device=dev)
+    A, X, Y = p.a, p.x, p.y
+    ws = H.workspace(m, n, r, l, gn.F64)
+    AX = torch.empty(m, r, dtype=torch.float64, device=dev)
+    YtA = torch.empty(r + l, n, dtype=torch.float64, device=dev)
+    F = torch.zeros(m, r, dtype=torch.float64, device=dev)
+    G = torch.zeros(r, n, dtype=torch.float64, device=dev)
+    e2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    core = gn.Core.empty(r, l, dev)
+    H.sketch(A, X, Y, AX, YtA, ws)
+    H.core(YtA, X, 10 * 2.0 ** -53, gn.AUTO | gn.EPS_RELATIVE, core, ws)
+    torch.cuda.synchronize()
+    floor = core.eps_abs
+    out = {"workload": f"{m}x{n}, r={r}, l={l}, FP64 sketches, floor = 10 u ||C||_2 = {floor:.3e}"}
+
+    def err(k):
+        H.error_fro2(A, F[:, :k], G[:k], e2, ws)
+        torch.cuda.synchronize()
+        return math.sqrt(e2.item())
+
+    def tcore():
+        H.core(YtA, X, 10 * 2.0 ** -53, gn.AUTO | gn.EPS_RELATIVE, core, ws)
+        H.factors(AX, YtA, core, F, G, ws)
+    ms = _best_ms(tcore, 3, stream)
+    out["qr_truncation_auto"] = {"ms": ms, "k": core.k, "err": err(core.k)}
+    for name, code in (("svd_truncate", gn.SVD_TRUNCATE), ("svd_raise", gn.SVD_RAISE),
+                       ("rrqr_raise", gn.RRQR_RAISE), ("diag_raise", gn.DIAG_RAISE)):
+        kk = [0]
+
+        def run():
+            kk[0] = H.factors_variant(AX, YtA, X, floor, code, F, G)
+        ms = _best_ms(run, 3, stream)
+        out[name] = {"ms": ms, "k": kk[0], "err": err(kk[0])}
+    del A, X, Y, ws, AX, YtA, F, G, core
+    torch.cuda.empty_cache()
+    return out
+
+
+def oversampling_sweep(gn, H, stream, dev, m=8192, n=4096, r=200):
+    """The oversampling study of Section 5.2: the FP64 GN error ||A - F G||_F
+    for l in {1, 2, 5, 10, 20, 50, 100, 200} at fixed r, beside HMT's error with
+    the same X (W1 diag(i^-2) W2^T + 1e-8 noise)."""
+    p = gn_synth.config2(m=m, n=n, r=r, l=r, device=dev)
+    A, X = p.a, p.x
+    Yfull = p.y
+    e2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    res = {"workload": f"{m}x{n}, r={r}, FP64, Gaussian X, Y; errors ||A - Ahat||_F"}
+    ws = H.workspace(m, n, r, r, gn.F64)
+    Q = torch.empty(m, r, dtype=torch.float64, device=dev)
+    B = torch.empty(r, n, dtype=torch.float64, device=dev)
+    H.hmt(A, X, Q, B, ws)
+    H.error_fro2(A, Q, B, e2, ws)
+    torch.cuda.synchronize()
+    res["hmt_err"] = math.sqrt(e2.item())
+    errs = {}
+    for l in (1, 2, 5, 10, 20, 50, 100, 200):
+        Y = Yfull[:, :r + l].contiguous()
+        AX = torch.empty(m, r, dtype=torch.float64, device=dev)
+        YtA = torch.empty(r + l, n, dtype=torch.float64, device=dev)
+        core = gn.Core.empty(r, l, dev)
+        F = torch.empty(m, r, dtype=torch.float64, device=dev)
+        G = torch.empty(r, n, dtype=torch.float64, device=dev)
+        H.approx(A, X, Y, 10 * 2.0 ** -53, gn.AUTO | gn.EPS_RELATIVE, AX, YtA, core, F, G, ws)
+        H.error_fro2(A, F[:, :core.k], G[:core.k], e2, ws)
+        torch.cuda.synchronize()
+        errs[str(l)] = {"err": math.sqrt(e2.item()), "over_hmt": math.sqrt(e2.item()) / res["hmt_err"], "k": core.k}
+    res["gn"] = errs
+    del A, X, Yfull, ws, Q, B
+    torch.cuda.empty_cache()
+    return res
 
 
 def fp64_cases(gn, H, stream, dev):

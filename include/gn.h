@@ -400,6 +400,40 @@ gn_status gn_countsketch_apply(gn_handle h, const gn_mat* B, const int64_t* bx, 
 gn_status gn_countsketch_matrix(gn_handle h, int64_t n, int64_t r, const int64_t* buckets, const double* signs,
                                 gn_mat* X);
 
+/* ------------------------------------------ Section 5.1.1's perturbed cores */
+
+/* The alternatives of Section 5.1.1 to truncating R, and SGN with the SVD
+ * epsilon-pseudoinverse (eq. 2.2), from a sketch state:
+ *   GN_VARIANT_SVD_TRUNCATE: C = U S V^T, keep s_i > eps:
+ *                            F = AX V_k S_k^{-1}, G = U_k^T (Y^T A)
+ *   GN_VARIANT_SVD_RAISE   : s_i -> max(s_i, eps): F = AX V S~^{-1}, G = U^T (Y^T A)
+ *   GN_VARIANT_RRQR_RAISE  : column-pivoted Householder C P = Q R (the column of
+ *                            largest remaining norm first), |R_ii| -> max(|R_ii|, eps)
+ *                            with the sign kept: F = (AX P) R~^{-1}, G = Q^T (Y^T A)
+ *   GN_VARIANT_DIAG_RAISE  : unpivoted C = Q R with |R_ii| raised the same way:
+ *                            F = AX R~^{-1}, G = Q^T (Y^T A)
+ * eps is absolute (the caller scales it); the raising variants need eps > 0.
+ * C = (Y^T A) X is formed in FP64; every product and solve is FP64.  AX (m x r)
+ * and YtA ((r+l) x n): both GN_F64 or both GN_F32; X (n x r): GN_F64 or GN_BF16;
+ * F (m x >= r) and G (>= r x n) GN_F64, their first k columns / rows written.
+ * *k_out (host) receives k (r except for SVD_TRUNCATE); sv (device, r doubles,
+ * optional) the singular values by decreasing size (SVD variants) or diag(R)
+ * before raising (QR variants).  The SVD and pivoted variants factor C in one
+ * CTA's shared memory (one-sided Jacobi rotations; pivoted Householder) and
+ * need r <= 128 and r + l <= 192 (GN_ERR_UNSUPPORTED otherwise); DIAG_RAISE
+ * takes any r.  Blocks the host once for k (SVD and pivoted variants).
+ * GN_ERR_NONFINITE when k = 0.  ws: gn_variant_workspace_size bytes. */
+typedef enum {
+    GN_VARIANT_SVD_TRUNCATE = 0,
+    GN_VARIANT_SVD_RAISE = 1,
+    GN_VARIANT_RRQR_RAISE = 2,
+    GN_VARIANT_DIAG_RAISE = 3
+} gn_variant;
+gn_status gn_variant_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, size_t* bytes);
+gn_status gn_factors_variant(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_mat* X, double eps,
+                             int32_t variant, gn_mat* F, gn_mat* G, int64_t* k_out, double* sv, void* ws,
+                             size_t ws_bytes);
+
 /* Sketch + core + factors in one call (Algorithm 2).  AX, YtA are outputs
  * (GN_F64 for FP64 operands, GN_F32 for the tensor-core path). */
 gn_status gn_approx(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,

@@ -29,6 +29,7 @@ __all__ = [
 
 F64, F32, BF16, BF16X2, E4M3 = 0, 1, 2, 3, 4
 PLAIN, SGN, AUTO = 0, 1, 2
+SVD_TRUNCATE, SVD_RAISE, RRQR_RAISE, DIAG_RAISE = 0, 1, 2, 3
 EPS_RELATIVE = 0x100
 CORE_DEFER = 0x200
 CORE_C_GIVEN = 0x400
@@ -44,7 +45,7 @@ ABI_SYMBOLS = (
     "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update", "gn_resample",
     "gn_append_rows", "gn_append_cols", "gn_resample_workspace_size", "gn_core_finish",
     "gn_set_stall_test", "gn_dct_sketch", "gn_sketch_csr_countsketch", "gn_countsketch_matrix",
-    "gn_countsketch_apply", "gn_set_fp64_accum",
+    "gn_countsketch_apply", "gn_set_fp64_accum", "gn_variant_workspace_size", "gn_factors_variant",
 )
 
 
@@ -102,6 +103,8 @@ def _load():
         "gn_set_wait_limit": ([P, ctypes.c_uint64], I32),
         "gn_set_stall_test": ([P, I32], I32),
         "gn_set_fp64_accum": ([P, I64], I32),
+        "gn_variant_workspace_size": ([I64, I64, I64, I64, ctypes.POINTER(SZ)], I32),
+        "gn_factors_variant": ([P, M, M, M, D, I32, M, M, ctypes.POINTER(I64), P, P, SZ], I32),
         "gn_dct_sketch": ([P, I64, I64, P, P, M], I32),
         "gn_sketch_csr_countsketch": ([P, ctypes.POINTER(GnCsr), P, P, P, P, M, M], I32),
         "gn_countsketch_matrix": ([P, I64, I64, P, P, M], I32),
@@ -601,6 +604,21 @@ class Handle:
         _check(lib.gn_countsketch_matrix(self._h, n, r, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(s.data_ptr()),
                                          ctypes.byref(mat(X))), "gn_countsketch_matrix")
         return X
+
+    def factors_variant(self, AX, YtA, X, eps: float, variant: int, F, G, sv=None) -> int:
+        """Section 5.1.1's perturbed cores and SGN with the SVD eps-pseudoinverse:
+        F, G (first k columns / rows) from the sketch state; returns k."""
+        m, r = AX.shape
+        rl, n = YtA.shape
+        b = ctypes.c_size_t()
+        _check(lib.gn_variant_workspace_size(m, n, r, rl - r, ctypes.byref(b)), "gn_variant_workspace_size")
+        ws = self._scratch(b.value, AX.device)
+        k = ctypes.c_int64()
+        _check(lib.gn_factors_variant(self._h, ctypes.byref(mat(AX)), ctypes.byref(mat(YtA)), ctypes.byref(mat(X)),
+                                      float(eps), int(variant), ctypes.byref(mat(F)), ctypes.byref(mat(G)),
+                                      ctypes.byref(k), ctypes.c_void_p(sv.data_ptr() if sv is not None else 0),
+                                      ctypes.c_void_p(ws.data_ptr()), ws.numel()), "gn_factors_variant")
+        return int(k.value)
 
     def hmt(self, A, X, Q, B, ws):
         _check(lib.gn_hmt(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Q)),

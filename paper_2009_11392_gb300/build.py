@@ -16,8 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgn.so")
 SOURCES = ["gn_tc.cu", "gn_f64.cu", "gn_capi.cu", "gn_noalloc.cu", "gn_adjoint.cu", "gn_batched.cu", "gn_fp8.cu",
-           "gn_ozaki.cu", "gn_struct.cu"]
-HEADERS = ["gn_internal.cuh", os.path.join("..", "..", "include", "gn.h")]
+           "gn_ozaki.cu", "gn_struct.cu", "gn_variants.cu"]
+HEADERS = ["gn_internal.cuh", "gn_smem_core.cuh", os.path.join("..", "..", "include", "gn.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "128,177"]
