@@ -300,7 +300,10 @@ gn_status gn_factors(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_
  * truncation (core->sgn, k < r) the core pseudoinverse Q_2 R_2^{-T} Q_1^T
  * (Section 5.1.1) takes the place of R^{-1} Q^T.  AX and Y^T A as gn_sketch
  * wrote them (GN_F64 or GN_F32), core from gn_core; W and out GN_F64,
- * row-major, device.  FP64 products and triangular solves.  ws (device) of at
+ * row-major, device.  FP64 products and triangular solves; with GN_F32
+ * sketches the products whose size grows with m or n run to FP64 accuracy on
+ * the tensor cores by digit slicing (as gn_dgemm_tc) unless gn_set_fp64_tc(h, 0)
+ * keeps them on the FP64 units.  ws (device) of at
  * least gn_apply_workspace_size bytes.  GN_ERR_SHAPE / GN_ERR_DTYPE on
  * mismatched operands; asynchronous on the handle's stream. */
 gn_status gn_apply_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int64_t kw, int32_t side,

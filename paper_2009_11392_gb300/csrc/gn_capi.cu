@@ -1133,13 +1133,20 @@ gn_status gn_append_cols(gn_handle h, const gn_mat* B, const gn_mat* Xb, const g
 }
 
 // Scratch of gn_apply: two FP64 blocks of at most max(r + l, r) x kw, the
-// triangular solve's and the GEMMs' split-K partials.
+// triangular solve's and the GEMMs' split-K partials; for FP32 sketches the
+// transposed products (r x kw, n x kw) and the digit-sliced products' scratch.
+size_t apply_oz_ws(long long m, long long n, long long r, long long l, long long kw) {
+    const long long rl = r + l;
+    return align256(sizeof(double) * r * kw) + align256(sizeof(double) * n * kw) +
+           std::max({oz_ws_bytes(rl, kw, n, 1), oz_ws_bytes(m, kw, r, 1), oz_ws_bytes(r, kw, m, 1),
+                     oz_ws_bytes(n, kw, rl, 1)}) + 512;
+}
 size_t apply_ws(long long m, long long n, long long r, long long l, long long kw, int sms) {
     const long long rl = r + l;
     return 2 * align256(sizeof(double) * rl * kw) + trsm_ws_bytes(kw, r, sms) +
            std::max({dgemm_ws_bytes(rl, kw, n, sms), dgemm_ws_bytes(m, kw, r, sms), dgemm_ws_bytes(kw, r, m, sms),
                      dgemm_ws_bytes(kw, n, rl, sms), dgemm_ws_bytes(kw, rl, r, sms)}) +
-           1024;
+           apply_oz_ws(m, n, r, l, kw) + 1024;
 }
 
 gn_status gn_apply_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l, int64_t kw, int32_t side,
@@ -1172,15 +1179,24 @@ gn_status gn_apply(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_co
     Carve cv{static_cast<char*>(ws), ws_bytes, 0, true};
     double* B1 = cv.take<double>(rl * kw);
     double* B2 = cv.take<double>(rl * kw);
+    // FP32 sketches: the m- and n-sized products by exact digit slicing on the tensor cores
+    const bool ax32 = AX->dtype == GN_F32, yta32 = YtA->dtype == GN_F32;
+    const bool oz = h->fp64_tc && (ax32 || yta32);
+    double* T1 = cv.take<double>(r * kw);   // (W AX)^T
+    double* T2 = cv.take<double>(n * kw);   // (B Y^T A)^T
+    const size_t ozb = std::max({oz_ws_bytes(rl, kw, n, 1), oz_ws_bytes(m, kw, r, 1), oz_ws_bytes(r, kw, m, 1),
+                                 oz_ws_bytes(n, kw, rl, 1)});
+    void* ozw = cv.take<char>(ozb);
     if (!cv.ok) return GN_ERR_WORKSPACE;
     size_t gws_bytes = 0;
     double* gws = cv.rest(&gws_bytes);
     const double* Wd = static_cast<const double*>(W->data);
     double* Od = static_cast<double*>(out->data);
-    const bool ax32 = AX->dtype == GN_F32, yta32 = YtA->dtype == GN_F32;
     if (side == 0) {
         // B1 = Y^T A W   ((r+l) x kw)
-        if (yta32)
+        if (yta32 && oz)
+            GN_TRY(oz_dgemm(h, rl, kw, n, 1.0, YtA->data, 1, YtA->ld, 0, Wd, W->ld, 0, 0.0, B1, kw, ozw, ozb));
+        else if (yta32)
             GN_TRY(dgemm_a32(h, rl, kw, n, 1.0, static_cast<const float*>(YtA->data), YtA->ld, 0, Wd, W->ld, 0, 0.0,
                              B1, kw, gws, gws_bytes));
         else
@@ -1199,7 +1215,9 @@ gn_status gn_apply(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_co
             Zt = B1;
         }
         // out = AX Z = AX (Z^T)^T   (m x kw)
-        if (ax32)
+        if (ax32 && oz)
+            GN_TRY(oz_dgemm(h, m, kw, r, 1.0, AX->data, 1, AX->ld, 0, Zt, r, 1, 0.0, Od, out->ld, ozw, ozb));
+        else if (ax32)
             GN_TRY(dgemm_a32(h, m, kw, r, 1.0, static_cast<const float*>(AX->data), AX->ld, 0, Zt, r, 1, 0.0, Od,
                              out->ld, gws, gws_bytes));
         else
@@ -1208,7 +1226,10 @@ gn_status gn_apply(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_co
         return GN_OK;
     }
     // side 1: B1 = W AX   (kw x r)
-    if (ax32)
+    if (ax32 && oz) {   // (W AX)^T = AX^T W^T, then transposed
+        GN_TRY(oz_dgemm(h, r, kw, m, 1.0, AX->data, 1, AX->ld, 1, Wd, W->ld, 1, 0.0, T1, kw, ozw, ozb));
+        GN_TRY(transpose_rows_f64(h, T1, r, kw, kw, r, B1, r));
+    } else if (ax32)
         GN_TRY(dgemm_b32(h, kw, r, m, 1.0, Wd, W->ld, 0, static_cast<const float*>(AX->data), AX->ld, 0, 0.0, B1, r,
                          gws, gws_bytes));
     else
@@ -1227,7 +1248,10 @@ gn_status gn_apply(gn_handle h, const gn_mat* AX, const gn_mat* YtA, const gn_co
     double* Bq = trunc ? B1 : B2;
     GN_TRY(dgemm(h, kw, rl, k, 1.0, P, ldp, 0, core->Q, r, 1, 0.0, Bq, rl, gws, gws_bytes));
     // out = B Y^T A   (kw x n)
-    if (yta32)
+    if (yta32 && oz) {   // (B Y^T A)^T = (Y^T A)^T B^T, then transposed
+        GN_TRY(oz_dgemm(h, n, kw, rl, 1.0, YtA->data, 1, YtA->ld, 1, Bq, rl, 1, 0.0, T2, kw, ozw, ozb));
+        GN_TRY(transpose_rows_f64(h, T2, n, kw, kw, n, Od, out->ld));
+    } else if (yta32)
         GN_TRY(dgemm_b32(h, kw, n, rl, 1.0, Bq, rl, 0, static_cast<const float*>(YtA->data), YtA->ld, 0, 0.0, Od,
                          out->ld, gws, gws_bytes));
     else
