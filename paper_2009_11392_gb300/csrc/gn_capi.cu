@@ -808,7 +808,7 @@ gn_status gn_core(gn_handle h, const gn_mat* YtA, const gn_mat* X, double eps, i
     // while the main stream forms Q.
     GN_CUDA_TRY(cudaMemcpy2DAsync(W, r * sizeof(double), core->C, r * sizeof(double), r * sizeof(double), rl,
                                   cudaMemcpyDeviceToDevice, h->stream));
-    GN_TRY(qr_factor(h, W, rl, r, r, core->R, r, inner, inner_bytes));
+    GN_TRY(qr_factor(h, W, rl, r, r, core->R, r, inner, inner_bytes, qoz, qoz_bytes));
     core->k = r;
     core->sgn = 0;
     core->rinv_est = 0.0;

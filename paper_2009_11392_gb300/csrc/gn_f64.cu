@@ -1726,7 +1726,7 @@ gn_status wy_apply(gn_handle h, double* W, long long ldw, long long Mp, long lon
 }
 
 gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R, long long ldr,
-                    double* ws, size_t ws_bytes) {
+                    double* ws, size_t ws_bytes, void* oz, size_t oz_bytes) {
     if (M < N || N <= 0) return GN_ERR_SHAPE;
     if (ws_bytes < qr_ws_bytes(M, N, h->sm_count)) return GN_ERR_WORKSPACE;
     QrWs q = qr_carve(M, N, ws, ws_bytes);
@@ -1794,7 +1794,18 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
                 side.stream = h->side;
                 GN_TRY(wy_apply(&side, W2 + nnext, ld, Mp, nsec, Vb, N, jb, T, 1, 1));
                 GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
-                if (nrest > 0) GN_TRY(wy_apply(&side, W2 + nnext + nsec, ld, Mp, nrest, Vb, N, jb, T, 1, 1));
+                if (nrest >= 128 && oz) {
+                    // W3 <- W3 - V (T^T (V^T W3)) with the two large products digit-sliced
+                    double* W3 = W2 + nnext + nsec;
+                    GN_TRY(oz_dgemm(&side, jb, nrest, Mp, 1.0, Vb, 0, N, 1, W3, ld, 0, 0.0, q.Z1, nrest, oz,
+                                    oz_bytes));
+                    GN_TRY(dgemm(&side, jb, nrest, jb, 1.0, T, jb, 1, q.Z1, nrest, 0, 0.0, q.Z2, nrest, q.gws,
+                                 q.gws_bytes));
+                    GN_TRY(oz_dgemm(&side, Mp, nrest, jb, -1.0, Vb, 0, N, 0, q.Z2, nrest, 0, 1.0, W3, ld, oz,
+                                    oz_bytes));
+                } else if (nrest > 0) {
+                    GN_TRY(wy_apply(&side, W2 + nnext + nsec, ld, Mp, nrest, Vb, N, jb, T, 1, 1));
+                }
                 side_used = true;
             }
             had_second = nsec > 0;

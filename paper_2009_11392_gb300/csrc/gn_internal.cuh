@@ -165,8 +165,11 @@ gn_status householder_qr(gn_handle h, double* W, long long M, long long N, long 
                          double* ws, size_t ws_bytes);
 // The two halves of householder_qr: the factorization (R written, reflectors
 // kept in ws) and the formation of the thin Q from them (same W and ws).
+// oz (optional, >= qr_oz_ws_bytes(M, N)): the lagging trailing updates of the
+// look-ahead (the columns beyond the next two panels) as digit-sliced products
+// on the tensor cores (for cores of FP32 sketches); null: FP64 units only.
 gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R,
-                    long long ldr, double* ws, size_t ws_bytes);
+                    long long ldr, double* ws, size_t ws_bytes, void* oz = nullptr, size_t oz_bytes = 0);
 // oz (optional, >= qr_oz_ws_bytes(M, N)): form Q in blocks of 256 reflectors with
 // the large products on the tensor cores (oz_dgemm); null: FP64 units only.
 gn_status qr_form_q(gn_handle h, const double* W, long long M, long long N, long long ld, double* Q,
