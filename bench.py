@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements and the CPU baseline")
     ap.add_argument("--op", default="bf16", choices=["bf16", "e4m3"],
                     help="sketch operand type of the timed step (e4m3: per-128x128-tile scales)")
+    ap.add_argument("--prio", type=int, default=0,
+                    help="stream priority of the approximations' streams (0 default, -1 high)")
+    ap.add_argument("--h2d-streams", type=int, default=2, help="host-to-device copy streams of the e2e loop")
     ap.add_argument("--only", default=None, choices=["batched", "adjoint", "fp64_cases"],
                     help="run one side measurement alone and print its JSON (for profiling it)")
     return ap.parse_args()
@@ -295,10 +298,10 @@ def main():
     m, n, r = a.m, a.n, a.r
     l = r // 2
     nf = max(1, a.inflight)
-    stream = torch.cuda.Stream(device=dev)
+    stream = torch.cuda.Stream(device=dev, priority=a.prio)
     torch.cuda.set_stream(stream)
     H = gn.Handle(stream)
-    Hs = [H] + [gn.Handle(torch.cuda.Stream(device=dev)) for _ in range(nf - 1)]
+    Hs = [H] + [gn.Handle(torch.cuda.Stream(device=dev, priority=a.prio)) for _ in range(nf - 1)]
 
     # ---- inputs (seeded, drawn on the device; FP64)
     p = gn_synth.config3(r=r, device=dev, m=m, n=n)
@@ -514,9 +517,10 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
              torch.empty(r, r, dtype=torch.float64, pin_memory=True)] for _ in range(nset)]
     h2d = sum(t.numel() * t.element_size() for t in hosts)
     d2h = sum(o.numel() * o.element_size() for o in outh[0])
-    hs = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    nh = max(1, a.h2d_streams)
+    hs = [torch.cuda.Stream(device=dev) for _ in range(nh)]
     dstream = torch.cuda.Stream(device=dev)
-    ev_in = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(nset)]
+    ev_in = [[torch.cuda.Event() for _ in range(nh)] for _ in range(nset)]
     ev_done = [torch.cuda.Event() for _ in range(nset)]
     ev_out = [torch.cuda.Event() for _ in range(nset)]
     step_handle = {}
@@ -526,12 +530,11 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
         for q in hs:
             q.wait_event(ev_done[b])              # the set's previous step has finished computing
         for d_, h_ in zip(ins[b][0], hosts):
-            if h_.numel() * h_.element_size() >= (64 << 20) and h_.dim() >= 1 and h_.shape[0] >= 2:
-                half = h_.shape[0] // 2
-                with torch.cuda.stream(hs[0]):
-                    d_[:half].copy_(h_[:half], non_blocking=True)
-                with torch.cuda.stream(hs[1]):
-                    d_[half:].copy_(h_[half:], non_blocking=True)
+            if h_.numel() * h_.element_size() >= (64 << 20) and h_.dim() >= 1 and h_.shape[0] >= nh:
+                step = (h_.shape[0] + nh - 1) // nh   # row blocks, one per copy stream
+                for qi, q in enumerate(hs):
+                    with torch.cuda.stream(q):
+                        d_[qi * step:(qi + 1) * step].copy_(h_[qi * step:(qi + 1) * step], non_blocking=True)
             else:
                 with torch.cuda.stream(hs[0]):
                     d_.copy_(h_, non_blocking=True)
@@ -580,7 +583,7 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(hs[0])
-    for q in [hs[1], dstream] + [Hj.stream for Hj in Hs]:   # nothing of the timed steps starts before e0
+    for q in hs[1:] + [dstream] + [Hj.stream for Hj in Hs]:   # nothing of the timed steps starts before e0
         q.wait_stream(hs[0])
     run(a.steps)
     e1.record(dstream)                   # after the last step's results are out (which waits for all)
@@ -606,7 +609,7 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
     torch.cuda.empty_cache()
     return {"value": 1e3 / ms, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": ms, "h2d_gbs_one_stream": h2d_gbs, "d2h_gbs_one_stream": d2h_gbs,
-            "copy_floor_ms": (h2d / (2 * h2d_gbs) + d2h / d2h_gbs) / 1e6}
+            "h2d_streams": nh, "copy_floor_ms": (h2d / (nh * h2d_gbs) + d2h / d2h_gbs) / 1e6}
 
 
 # --------------------------------------------------------------------------- side measurements

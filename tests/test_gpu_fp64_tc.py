@@ -139,11 +139,11 @@ def test_factors_tensor_core_truncated_branch(gn, H):
 
 @pytest.mark.parametrize("n,r,l", [(2048, 600, 300), (700, 96, 48)])
 def test_core_q_tensor_core_vs_fp64_units(gn, H, n, r, l):
-    """The thin Q of the core's Householder QR formed in 256-reflector blocks with
-    the products on the tensor cores: equal to the FP64-unit formation to
-    1e-11 (each digit-sliced product errs by ~1e-13 of |A||B| per element,
-    three blocks deep) and orthonormal to 1e-12 r; R untouched (the same
-    factorization)."""
+    """The core's Householder QR with its lagging trailing updates and the
+    formation of Q (256-reflector blocks) as digit-sliced products on the
+    tensor cores, against the same QR on the FP64 units: R and Q equal to a
+    few 1e-11 (each digit-sliced product errs by ~1e-13 of |A||B| per
+    element), Q orthonormal to 1e-12 r and C = QR to 1e-12 (backward stable)."""
     g = torch.Generator(device="cuda").manual_seed(n + r)
     YtA = torch.randn(r + l, n, generator=g, device="cuda", dtype=torch.float32)
     X = H.quantize(torch.randn(n, r, generator=g, device="cuda", dtype=torch.float64))
@@ -157,8 +157,10 @@ def test_core_q_tensor_core_vs_fp64_units(gn, H, n, r, l):
             assert H.sync_status() == 0
         finally:
             H.set_fp64_tc(True)
-        out.append((npy(core.Q), npy(core.R)))
-    (Q1, R1), (Q0, R0) = out
-    assert np.array_equal(R1, R0)
-    assert np.linalg.norm(Q1 - Q0) <= 1e-11 * np.linalg.norm(Q0)
+        out.append((npy(core.Q), npy(core.R), npy(core.C)))
+    (Q1, R1, C1), (Q0, R0, C0) = out
+    assert np.array_equal(C1, C0)   # the same core matrix
+    assert np.linalg.norm(R1 - R0) <= 3e-11 * np.linalg.norm(R0)
+    assert np.linalg.norm(Q1 - Q0) <= 3e-11 * np.linalg.norm(Q0)
+    assert np.linalg.norm(C1 - Q1 @ R1) <= 1e-12 * np.linalg.norm(C1)
     assert np.linalg.norm(Q1.T @ Q1 - np.eye(r)) <= 1e-12 * r
