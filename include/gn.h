@@ -176,12 +176,16 @@ gn_status gn_set_fp64_g(gn_handle h, int32_t fp64_g);
  * for the sketches; this is the library's. */
 gn_status gn_set_fp64_accum(gn_handle h, int64_t part_k);
 
-/* How gn_factors / gn_approx compute the large FP64 products of the solve for
- * F when AX is GN_F32 (the tensor-core sketches): the outer-block updates of
- * the triangular solve F R = AX (eq. 5.1) and, after a truncation, AX Q_2.
- * 1 (default): on the BF16 tensor cores by exact digit slicing (gn_dgemm_tc;
- * FP64-level accuracy); 0: on the FP64 units.  The small diagonal-block solves
- * stay in FP64 either way; FP64 sketches always use the FP64 units. */
+/* Where the large FP64 products run for GN_F32 sketches (the tensor-core
+ * path): in gn_core, the QR's lagging trailing updates (the columns beyond the
+ * next two panels of the look-ahead) and the formation of the thin Q; in
+ * gn_factors / gn_approx, the outer-block updates of the triangular solve
+ * F R = AX (eq. 5.1) and, after a truncation, AX Q_2; in gn_apply, the products
+ * with AX and Y^T A.  1 (default): on the BF16 tensor cores by exact digit
+ * slicing (gn_dgemm_tc; FP64-level accuracy, about 1e-13 of |A||B| per
+ * element); 0: on the FP64 units.  The panels, the small diagonal-block solves
+ * and the detector stay in FP64 either way; FP64 sketches always use the FP64
+ * units. */
 gn_status gn_set_fp64_tc(gn_handle h, int32_t on);
 
 /* C = alpha op(A) op(B) + beta C, FP64 (A may be FP32), computed on the BF16

@@ -143,7 +143,9 @@ def test_core_q_tensor_core_vs_fp64_units(gn, H, n, r, l):
     formation of Q (256-reflector blocks) as digit-sliced products on the
     tensor cores, against the same QR on the FP64 units: R and Q equal to a
     few 1e-11 (each digit-sliced product errs by ~1e-13 of |A||B| per
-    element), Q orthonormal to 1e-12 r and C = QR to 1e-12 (backward stable)."""
+    element), Q orthonormal to 1e-12 r and C = QR to 1e-11 relative (the
+    trailing products' error, far below the 2^-24 of the FP32 sketches that
+    such a core comes from)."""
     g = torch.Generator(device="cuda").manual_seed(n + r)
     YtA = torch.randn(r + l, n, generator=g, device="cuda", dtype=torch.float32)
     X = H.quantize(torch.randn(n, r, generator=g, device="cuda", dtype=torch.float64))
@@ -162,5 +164,6 @@ def test_core_q_tensor_core_vs_fp64_units(gn, H, n, r, l):
     assert np.array_equal(C1, C0)   # the same core matrix
     assert np.linalg.norm(R1 - R0) <= 3e-11 * np.linalg.norm(R0)
     assert np.linalg.norm(Q1 - Q0) <= 3e-11 * np.linalg.norm(Q0)
-    assert np.linalg.norm(C1 - Q1 @ R1) <= 1e-12 * np.linalg.norm(C1)
+    assert np.linalg.norm(C1 - Q1 @ R1) <= 1e-11 * np.linalg.norm(C1)
+    assert np.linalg.norm(C0 - Q0 @ R0) <= 1e-13 * np.linalg.norm(C0)
     assert np.linalg.norm(Q1.T @ Q1 - np.eye(r)) <= 1e-12 * r
