@@ -51,9 +51,12 @@ constexpr int NUM_THREADS = 192;
 // [256, 384); the scale factors of stage s sit at columns 384 + 16 s.
 template <int MT, bool F8 = false>
 struct Cfg {
-    static constexpr int STG = MT == 2 ? 3 : 4;
+    // e4m3 tiles are 128 columns wide (16 KB of B per stage), so their stages
+    // are smaller and the ring deeper: 4 (256-row tiles) or 6 (128-row tiles)
+    // stages keep more operand bytes in flight at the doubled MMA rate.
+    static constexpr int STG = F8 ? (MT == 2 ? 4 : 6) : (MT == 2 ? 3 : 4);
     static constexpr int A_BYTES = MT * BM * BK * 2;
-    static constexpr int STAGE = A_BYTES + B_STAGE_BYTES;
+    static constexpr int STAGE = A_BYTES + (F8 ? 128 * BK * 2 : B_STAGE_BYTES);
     static constexpr int NACC = MT == 2 ? 1 : 2;
     static constexpr int TM = BM * MT;
     static constexpr int SF_STAGE = F8 ? (MT + 1) * 512 : 0;
