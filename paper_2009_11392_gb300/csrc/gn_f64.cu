@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
         const int np = a > 16 ? 32 : a > 8 ? 16 : a > 4 ? 8 : a > 2 ? 4 : a > 1 ? 2 : 1;
         const int q = lane & (np - 1), sub = lane / np, nsub = 32 / np;
         const int cla = a - r0;
-        // two partial sums: each FP64 FMA on the chain costs ~200 cycles on GB300
+        // two partial sums: the loads of one overlap the other's FMA (~64 cycles each on GB300)
         double acc = 0.0, acc1 = 0.0;
         if (q < a) {
             const int step = (CP_WARPS - 1) * nsub;
@@ -523,8 +523,8 @@ __global__ void __launch_bounds__(CP_THREADS) qr_panel_cluster_kernel(double* W,
     // Per-column thread tiles cover only the live columns: with na live columns
     // (padded to np, a power of two), lane = sub * np + column offset and the
     // 8 * 32 / np row chunks split the rows.  On GB300 each FP64 warp
-    // instruction holds the SM's FP64 pipe for ~16 cycles whatever its mask,
-    // so idle lanes are what this avoids.
+    // instruction holds its sub-partition's FP64 unit for ~64 cycles whatever
+    // its mask, so idle lanes are what this avoids.
     for (int c = 0; c < jb; ++c) {
         double* slot = xch + (c & 1) * SLOT;
         const int cl = c - r0;                       // local index of row c (owner iff 0 <= cl < nr)

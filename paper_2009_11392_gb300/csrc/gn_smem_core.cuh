@@ -15,8 +15,9 @@ constexpr int MMAX = 192;        // (r + l) <= 192 rows
 
 // S is M x N in shared memory (ld = N + 1).
 //    Partial sums are formed per (row chunk, column) and combined once: on GB300
-//    a single warp's FP64 instruction occupies its sub-partition for ~64 cycles,
-//    so work is spread over all 16 warps rather than reduced by butterflies.
+//    a warp's FP64 instruction occupies its sub-partition's FP64 unit for ~64
+//    cycles whatever its mask, so work is spread over all 16 warps rather than
+//    reduced by butterflies.
 struct Smem {
     double* S;
     int ld;
@@ -90,7 +91,7 @@ __device__ inline void smem_qr(const Smem& sm, int M, int N, int* perm = nullptr
         }
         for (int q0 = j; q0 < N; q0 += 32) {
             const int q = q0 + lane;
-            // two partial sums: a dependent FP64 instruction costs ~200 cycles
+            // two partial sums: the loads of one overlap the other's FMA (~64 cycles)
             double a0 = 0.0, a1 = 0.0;
             if (q < N) {
                 const int q2 = q == j ? j : q;
