@@ -66,7 +66,8 @@ def parse():
                     help="sketch operand type of the timed step (e4m3: per-128x128-tile scales)")
     ap.add_argument("--prio", type=int, default=0,
                     help="stream priority of the approximations' streams (0 default, -1 high)")
-    ap.add_argument("--h2d-streams", type=int, default=2, help="host-to-device copy streams of the e2e loop")
+    ap.add_argument("--h2d-streams", type=int, default=1, help="host-to-device copy streams of the e2e loop")
+    ap.add_argument("--e2e-sets", type=int, default=0, help="device buffer sets of the e2e loop (0: in-flight + 1)")
     ap.add_argument("--only", default=None, choices=["batched", "adjoint", "fp64_cases"],
                     help="run one side measurement alone and print its JSON (for profiling it)")
     return ap.parse_args()
@@ -491,7 +492,7 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
     nf + 1 device buffer sets; the copies run on two host-to-device streams
     (large inputs in row halves) and one device-to-host stream while the steps
     compute on the nf handles."""
-    nset = nf + 1
+    nset = a.e2e_sets if a.e2e_sets > nf else nf + 1
     if a.op == "e4m3":
         srcs = [Aop.data, Aop.data_t, Xop.data_t, Yop.data_t, Aop.scale, Xop.scale, Yop.scale]
         hosts = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in srcs]
@@ -567,14 +568,17 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
         ev_out[b].record(dstream)
 
     def run(k):
+        # the next step's copies are queued before the host waits on an older
+        # step: their buffer set was released by step i + 1 - nset, whose
+        # done-event the previous iteration recorded
         lag = nf - 1
         prefetch(0)
         for i in range(k):
             enqueue(i)
-            if i - lag >= 0:
-                complete(i - lag)
             if i + 1 < k:
                 prefetch(i + 1)
+            if i - lag >= 0:
+                complete(i - lag)
         for i in range(max(0, k - lag), k):
             complete(i)
 
@@ -609,7 +613,8 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
     torch.cuda.empty_cache()
     return {"value": 1e3 / ms, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": ms, "h2d_gbs_one_stream": h2d_gbs, "d2h_gbs_one_stream": d2h_gbs,
-            "h2d_streams": nh, "copy_floor_ms": (h2d / (nh * h2d_gbs) + d2h / d2h_gbs) / 1e6}
+            "h2d_streams": nh, "buffer_sets": nset,
+            "copy_floor_ms": max(h2d / h2d_gbs, d2h / d2h_gbs) / 1e6}
 
 
 # --------------------------------------------------------------------------- side measurements

@@ -180,30 +180,33 @@ __global__ void oz_digits_cols_kernel(const T* __restrict__ src, long long s_k, 
 
 // C[i, j] = beta C[i, j] + alpha 2^{ea_i + eb_j} sum_o D_o[i, j].  The exact
 // orders 0..3 are summed as integers in units of 2^-35 (one rounding), the
-// rounded orders 4.. in FP32 below them.
+// rounded orders 4.. in FP32 below them.  A thread per column, rows across
+// blockIdx.y (no division per element); each exact order is an integer below
+// 2^24 units, so it converts through a 32-bit integer.
 __global__ void oz_combine_kernel(const float* __restrict__ D, long long d_stride, long long ldd, int norders,
                                   int M, int N, const unsigned long long* __restrict__ mxa, int a_f32,
                                   const unsigned long long* __restrict__ mxb, double alpha, double beta,
                                   double* __restrict__ C, long long ldc) {
-    const long long total = static_cast<long long>(M) * N;
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long i = e / N, j = e - i * N;
-        const float* d = D + i * ldd + j;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int eb = row_exponent<double>(mxb[j]);
+    const int nexact = norders < 4 ? norders : 4;
+    for (int i = blockIdx.y; i < M; i += gridDim.y) {
+        const float* d = D + static_cast<long long>(i) * ldd + j;
         long long acc = 0;
-        const int nexact = norders < 4 ? norders : 4;
         for (int o = 0; o < nexact; ++o)   // D_o is an integer number of units 2^{-7(o+2)}
-            acc += __float2ll_rn(d[o * d_stride] * __int_as_float((127 + 7 * (o + 2)) << 23)) << (7 * (3 - o));
+            acc += static_cast<long long>(__float2int_rn(d[o * d_stride] * __int_as_float((127 + 7 * (o + 2)) << 23)))
+                   << (7 * (3 - o));
         float low = 0.0f;
         for (int o = norders - 1; o >= 4; --o) low += d[o * d_stride];
         // times 2^(ea + eb - 35): a power of two built from its bits when normal
         const int ea = a_f32 ? row_exponent<float>(mxa[i]) : row_exponent<double>(mxa[i]);
-        const int p = ea + row_exponent<double>(mxb[j]) - 35;
+        const int p = ea + eb - 35;
         const double x = fma(static_cast<double>(low), 34359738368.0, static_cast<double>(acc));
         const double v = (p >= -1022 && p <= 1023)
                              ? x * (alpha * __longlong_as_double(static_cast<long long>(p + 1023) << 52))
                              : alpha * ldexp(x, p);
-        double* c = C + i * ldc + j;
+        double* c = C + static_cast<long long>(i) * ldc + j;
         *c = beta == 0.0 ? v : fma(beta, *c, v);
     }
 }
@@ -352,9 +355,10 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
             }
             p.ngemm = norders;
             GN_TRY(tc_launch(h, &p));
-            const long long total = M * nb;
-            const long long blocks = std::min<long long>((total + 255) / 256, static_cast<long long>(h->sm_count) * 16);
-            oz_combine_kernel<<<static_cast<unsigned>(blocks), 256, 0, h->stream>>>(
+            const unsigned gx = static_cast<unsigned>((nb + 255) / 256);
+            const unsigned gy = static_cast<unsigned>(
+                std::max<long long>(1, std::min<long long>(M, static_cast<long long>(h->sm_count) * 16 / gx)));
+            oz_combine_kernel<<<dim3(gx, gy), 256, 0, h->stream>>>(
                 o.d, d_stride, o.ldd, norders, static_cast<int>(M), static_cast<int>(nb), o.mxa, a_f32, o.mxb + j0,
                 alpha, beta_pass, C + j0, ldc);
             count_launch();
