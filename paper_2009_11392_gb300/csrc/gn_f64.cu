@@ -1725,117 +1725,6 @@ gn_status wy_apply(gn_handle h, double* W, long long ldw, long long Mp, long lon
     return GN_OK;
 }
 
-gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R, long long ldr,
-                    double* ws, size_t ws_bytes, void* oz, size_t oz_bytes) {
-    if (M < N || N <= 0) return GN_ERR_SHAPE;
-    if (ws_bytes < qr_ws_bytes(M, N, h->sm_count)) return GN_ERR_WORKSPACE;
-    QrWs q = qr_carve(M, N, ws, ws_bytes);
-    static bool attr = false;
-    if (!attr) {
-        GN_CUDA_TRY(cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(QR_SMEM_PANEL_MAX)));
-        attr = true;
-    }
-    const PanelCfg pc = panel_cfg(h, M);
-    const int nb = pc.nb;
-    auto factor_panel = [&](long long j0) -> gn_status {
-        const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
-        const long long Mp = M - j0;
-        double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
-        if (pc.cluster) return launch_cluster_panel(h, pc, W, ld, M, j0, jb, q.V, N, q.tau, T);
-        const size_t panel_bytes = static_cast<size_t>(Mp) * (jb + 1) * sizeof(double);
-        const int use_smem = panel_bytes <= QR_SMEM_PANEL_MAX ? 1 : 0;
-        qr_panel_kernel<<<1, QR_THREADS, use_smem ? panel_bytes : 0, h->stream>>>(
-            W, ld, static_cast<int>(M), static_cast<int>(j0), jb, q.V, N, q.tau, T, use_smem); count_launch();
-        GN_CUDA_TRY(cudaGetLastError());
-        return GN_OK;
-    };
-    // Look-ahead: after panel j only panel j+1's columns are updated on the main
-    // stream; panel j+1 is then factored (16-SM cluster) while the rest of the
-    // trailing update runs on the side stream.  Requires the one-launch WY path.
-    const bool lookahead = pc.cluster && h->side != nullptr && h->crit != nullptr && wy_usable(M);
-    // The look-ahead chain (next-block updates and panels) runs on a
-    // high-priority stream so the block scheduler places its clusters ahead of
-    // the trailing updates queued on the side stream.
-    const gn_handle h0 = h;
-    gn_handle_s crit = *h;
-    if (lookahead) {
-        crit.stream = h->crit;
-        GN_CUDA_TRY(cudaEventRecord(h->ev_crit0, h->stream));
-        GN_CUDA_TRY(cudaStreamWaitEvent(h->crit, h->ev_crit0, 0));
-        h = &crit;
-    }
-    GN_TRY(factor_panel(0));
-    bool had_second = false, side_used = false;
-    for (long long j0 = 0; j0 < N; j0 += nb) {
-        const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
-        const long long Mp = M - j0;
-        const long long N2 = N - j0 - jb;
-        if (N2 <= 0) break;
-        double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
-        double* W2 = W + j0 * ld + j0 + jb;
-        const double* Vb = q.V + j0 * N + j0;
-        if (lookahead) {
-            // W2 <- (I - V T V^T)^T W2 = W2 - V T^T (V^T W2), in three column ranges:
-            //   next panel (main stream, before it is factored);
-            //   the panel after it (side stream, then ev_join marks it done);
-            //   everything further right (side stream, may lag behind the panels).
-            // Each column range receives the panels' updates in order: the side
-            // stream is in order, and the main stream's next-panel update waits for
-            // the side stream's update of the same columns by the previous panel.
-            const long long nnext = std::min<long long>(nb, N2);
-            const long long nsec = std::min<long long>(nb, N2 - nnext);
-            const long long nrest = N2 - nnext - nsec;
-            if (j0 > 0 && had_second) GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-            if (nsec > 0) {
-                GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));   // panel j0 factored
-                GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-                gn_handle_s side = *h;
-                side.stream = h->side;
-                GN_TRY(wy_apply(&side, W2 + nnext, ld, Mp, nsec, Vb, N, jb, T, 1, 1));
-                GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
-                if (nrest >= 128 && oz) {
-                    // W3 <- W3 - V (T^T (V^T W3)) with the two large products digit-sliced
-                    double* W3 = W2 + nnext + nsec;
-                    GN_TRY(oz_dgemm(&side, jb, nrest, Mp, 1.0, Vb, 0, N, 1, W3, ld, 0, 0.0, q.Z1, nrest, oz,
-                                    oz_bytes));
-                    GN_TRY(dgemm(&side, jb, nrest, jb, 1.0, T, jb, 1, q.Z1, nrest, 0, 0.0, q.Z2, nrest, q.gws,
-                                 q.gws_bytes));
-                    GN_TRY(oz_dgemm(&side, Mp, nrest, jb, -1.0, Vb, 0, N, 0, q.Z2, nrest, 0, 1.0, W3, ld, oz,
-                                    oz_bytes));
-                } else if (nrest > 0) {
-                    GN_TRY(wy_apply(&side, W2 + nnext + nsec, ld, Mp, nrest, Vb, N, jb, T, 1, 1));
-                }
-                side_used = true;
-            }
-            had_second = nsec > 0;
-            GN_TRY(wy_apply(h, W2, ld, Mp, nnext, Vb, N, jb, T, 1, 0));
-            GN_TRY(factor_panel(j0 + jb));
-            continue;
-        }
-        const gn_status st = wy_apply(h, W2, ld, Mp, N2, Vb, N, jb, T, 1, 0);
-        if (st == GN_ERR_UNSUPPORTED) {
-            GN_TRY(dgemm(h, jb, N2, Mp, 1.0, Vb, N, 1, W2, ld, 0, 0.0, q.Z1, N2, q.gws, q.gws_bytes));
-            GN_TRY(dgemm(h, jb, N2, jb, 1.0, T, jb, 1, q.Z1, N2, 0, 0.0, q.Z2, N2, q.gws, q.gws_bytes));
-            GN_TRY(dgemm(h, Mp, N2, jb, -1.0, Vb, N, 0, q.Z2, N2, 0, 1.0, W2, ld, q.gws, q.gws_bytes));
-        } else {
-            GN_TRY(st);
-        }
-        GN_TRY(factor_panel(j0 + jb));
-    }
-    if (side_used) {   // every lagging update is done before R and the reflectors are used
-        GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
-        GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-    }
-    qr_write_r_kernel<<<ew_blocks(h, N * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(N), R, ldr); count_launch();
-    GN_CUDA_TRY(cudaGetLastError());
-    if (h != h0) {   // join the high-priority chain back into the caller's stream
-        GN_CUDA_TRY(cudaEventRecord(h0->ev_crit1, h->stream));
-        GN_CUDA_TRY(cudaStreamWaitEvent(h0->stream, h0->ev_crit1, 0));
-    }
-    return GN_OK;
-}
-
 namespace {
 
 // T = S^{-1} for S = striu(G) + diag(1 / tau) (n x n upper triangular, n <=
@@ -1919,9 +1808,236 @@ __global__ void v_zero_upper_kernel(double* V, long long ldv, int N) {
 
 }  // namespace
 
+// Two-level blocking of the look-ahead factorization (tensor-core trailing
+// updates): blocks of QR_BB columns, each factored as nb-wide panels whose
+// FP64 updates stay inside the block; after a block, its QR_BB reflectors
+// update the next block on the high-priority chain and everything further
+// right on the side stream (one block behind), as three digit-sliced products
+// with the block's T from its Gram matrix (ut_inverse).  The trailing matrix is
+// sliced and combined once per block instead of once per panel.
+constexpr int QR_BB = 128;
+
+size_t qr_oz_side_bytes(long long M, long long N) {
+    return oz_ws_bytes(std::max<long long>(M, QR_SB), std::max<long long>(N, QR_SB), M, 0);
+}
+size_t qr_oz_crit_bytes(long long M) { return oz_ws_bytes(std::max<long long>(M, QR_BB), QR_BB, M, 0); }
+size_t al256d(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+size_t qr_blk_bytes(long long M, long long N) {
+    const long long nblk = (N + QR_BB - 1) / QR_BB;
+    return al256d(qr_oz_crit_bytes(M)) + al256d(sizeof(double) * nblk * QR_BB * QR_BB) +
+           al256d(sizeof(double) * QR_BB * QR_BB) + 2 * al256d(sizeof(double) * QR_BB * N) +
+           2 * al256d(sizeof(double) * QR_BB * QR_BB) + 1024;
+}
+
+struct QrBlk {
+    void* oz_side;
+    size_t oz_side_bytes;
+    void* oz_crit;
+    size_t oz_crit_bytes;
+    double *TB, *GB, *Z1s, *Z2s, *Z1c, *Z2c;
+};
+
+bool qr_blk_carve(long long M, long long N, void* oz, size_t oz_bytes, QrBlk* b) {
+    if (!oz || (reinterpret_cast<uintptr_t>(oz) & 255)) return false;
+    char* p = static_cast<char*>(oz);
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        char* q = p + off;
+        off += al256d(n);
+        return q;
+    };
+    const long long nblk = (N + QR_BB - 1) / QR_BB;
+    b->oz_side_bytes = qr_oz_side_bytes(M, N);
+    b->oz_side = take(b->oz_side_bytes);
+    b->oz_crit_bytes = qr_oz_crit_bytes(M);
+    b->oz_crit = take(b->oz_crit_bytes);
+    b->TB = reinterpret_cast<double*>(take(sizeof(double) * nblk * QR_BB * QR_BB));
+    b->GB = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * QR_BB));
+    b->Z1s = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * N));
+    b->Z2s = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * N));
+    b->Z1c = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * QR_BB));
+    b->Z2c = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * QR_BB));
+    return off <= oz_bytes;
+}
+
+// C (Mp x nc at ldc) <- (I - V T V^T)^T C = C - V T^T (V^T C), V: Mp x bw at ldv,
+// T: bw x bw upper triangular at ldt; the three products digit-sliced.
+gn_status block_apply(gn_handle h, double* C, long long ldc, long long Mp, long long nc, const double* V,
+                      long long ldv, int bw, const double* T, long long ldt, double* Z1, double* Z2, void* oz,
+                      size_t oz_bytes) {
+    GN_TRY(oz_dgemm(h, bw, nc, Mp, 1.0, V, 0, ldv, 1, C, ldc, 0, 0.0, Z1, nc, oz, oz_bytes));
+    GN_TRY(oz_dgemm(h, bw, nc, bw, 1.0, T, 0, ldt, 1, Z1, nc, 0, 0.0, Z2, nc, oz, oz_bytes));
+    return oz_dgemm(h, Mp, nc, bw, -1.0, V, 0, ldv, 0, Z2, nc, 0, 1.0, C, ldc, oz, oz_bytes);
+}
+
+gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R, long long ldr,
+                    double* ws, size_t ws_bytes, void* oz, size_t oz_bytes) {
+    if (M < N || N <= 0) return GN_ERR_SHAPE;
+    if (ws_bytes < qr_ws_bytes(M, N, h->sm_count)) return GN_ERR_WORKSPACE;
+    QrWs q = qr_carve(M, N, ws, ws_bytes);
+    static bool attr = false;
+    if (!attr) {
+        GN_CUDA_TRY(cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(QR_SMEM_PANEL_MAX)));
+        attr = true;
+    }
+    const PanelCfg pc = panel_cfg(h, M);
+    const int nb = pc.nb;
+    auto factor_panel = [&](long long j0) -> gn_status {
+        const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
+        const long long Mp = M - j0;
+        double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
+        if (pc.cluster) return launch_cluster_panel(h, pc, W, ld, M, j0, jb, q.V, N, q.tau, T);
+        const size_t panel_bytes = static_cast<size_t>(Mp) * (jb + 1) * sizeof(double);
+        const int use_smem = panel_bytes <= QR_SMEM_PANEL_MAX ? 1 : 0;
+        qr_panel_kernel<<<1, QR_THREADS, use_smem ? panel_bytes : 0, h->stream>>>(
+            W, ld, static_cast<int>(M), static_cast<int>(j0), jb, q.V, N, q.tau, T, use_smem); count_launch();
+        GN_CUDA_TRY(cudaGetLastError());
+        return GN_OK;
+    };
+    // Look-ahead: after panel j only panel j+1's columns are updated on the main
+    // stream; panel j+1 is then factored (16-SM cluster) while the rest of the
+    // trailing update runs on the side stream.  Requires the one-launch WY path.
+    const bool lookahead = pc.cluster && h->side != nullptr && h->crit != nullptr && wy_usable(M);
+    // The look-ahead chain (next-block updates and panels) runs on a
+    // high-priority stream so the block scheduler places its clusters ahead of
+    // the trailing updates queued on the side stream.
+    const gn_handle h0 = h;
+    gn_handle_s crit = *h;
+    if (lookahead) {
+        crit.stream = h->crit;
+        GN_CUDA_TRY(cudaEventRecord(h->ev_crit0, h->stream));
+        GN_CUDA_TRY(cudaStreamWaitEvent(h->crit, h->ev_crit0, 0));
+        h = &crit;
+    }
+    bool had_second = false, side_used = false;
+    QrBlk bk;
+    const bool blocked = lookahead && N >= 2 * QR_BB && QR_BB % nb == 0 && qr_blk_carve(M, N, oz, oz_bytes, &bk);
+    if (blocked) {
+        // rows above a panel inside its block are part of V_B and must read zero
+        GN_CUDA_TRY(cudaMemsetAsync(q.V, 0, sizeof(double) * M * N, h->stream));
+        bool pending = false;   // the previous block's side update of the next block's columns is queued
+        const long long nblk = (N + QR_BB - 1) / QR_BB;
+        for (long long bi = 0; bi < nblk; ++bi) {
+            const long long b0 = bi * QR_BB, bw = std::min<long long>(QR_BB, N - b0);
+            for (long long j0 = b0; j0 < b0 + bw; j0 += nb) {
+                GN_TRY(factor_panel(j0));
+                const int jb = static_cast<int>(std::min<long long>(nb, b0 + bw - j0));
+                const long long rest = b0 + bw - j0 - jb;
+                if (rest > 0)
+                    GN_TRY(wy_apply(h, W + j0 * ld + j0 + jb, ld, M - j0, rest, q.V + j0 * N + j0, N, jb,
+                                    q.Tall + (j0 / nb) * QR_NB * QR_NB, 1, 0));
+            }
+            const long long N2 = N - b0 - bw;
+            if (N2 <= 0) break;
+            const long long Mp = M - b0;
+            const double* VB = q.V + b0 * N + b0;
+            double* TB = bk.TB + bi * QR_BB * QR_BB;
+            GN_TRY(oz_dgemm(h, bw, bw, Mp, 1.0, VB, 0, N, 1, VB, N, 0, 0.0, bk.GB, QR_BB, bk.oz_crit,
+                            bk.oz_crit_bytes));
+            ut_inverse_kernel<<<static_cast<unsigned>(bw), 32, 0, h->stream>>>(bk.GB, QR_BB, q.tau + b0,
+                                                                              static_cast<int>(bw), TB, QR_BB);
+            count_launch();
+            GN_CUDA_TRY(cudaGetLastError());
+            // the next block's columns already have the block before this one (side stream)
+            if (pending) GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+            const long long nnext = std::min<long long>(QR_BB, N2);
+            const long long nsec = std::min<long long>(QR_BB, N2 - nnext);
+            const long long nrest = N2 - nnext - nsec;
+            if (nsec > 0) {   // the block after next, then everything further right, on the side stream
+                GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+                GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+                gn_handle_s side = *h;
+                side.stream = h->side;
+                double* C2 = W + b0 * ld + b0 + bw + nnext;
+                GN_TRY(block_apply(&side, C2, ld, Mp, nsec, VB, N, static_cast<int>(bw), TB, QR_BB, bk.Z1s, bk.Z2s,
+                                   bk.oz_side, bk.oz_side_bytes));
+                GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+                if (nrest > 0)
+                    GN_TRY(block_apply(&side, C2 + nsec, ld, Mp, nrest, VB, N, static_cast<int>(bw), TB, QR_BB,
+                                       bk.Z1s, bk.Z2s, bk.oz_side, bk.oz_side_bytes));
+                side_used = true;
+            }
+            pending = nsec > 0;
+            GN_TRY(block_apply(h, W + b0 * ld + b0 + bw, ld, Mp, nnext, VB, N, static_cast<int>(bw), TB, QR_BB,
+                               bk.Z1c, bk.Z2c, bk.oz_crit, bk.oz_crit_bytes));
+        }
+    } else {
+        GN_TRY(factor_panel(0));
+    }
+    for (long long j0 = 0; j0 < N && !blocked; j0 += nb) {
+        const int jb = static_cast<int>(std::min<long long>(nb, N - j0));
+        const long long Mp = M - j0;
+        const long long N2 = N - j0 - jb;
+        if (N2 <= 0) break;
+        double* T = q.Tall + (j0 / nb) * QR_NB * QR_NB;
+        double* W2 = W + j0 * ld + j0 + jb;
+        const double* Vb = q.V + j0 * N + j0;
+        if (lookahead) {
+            // W2 <- (I - V T V^T)^T W2 = W2 - V T^T (V^T W2), in three column ranges:
+            //   next panel (main stream, before it is factored);
+            //   the panel after it (side stream, then ev_join marks it done);
+            //   everything further right (side stream, may lag behind the panels).
+            // Each column range receives the panels' updates in order: the side
+            // stream is in order, and the main stream's next-panel update waits for
+            // the side stream's update of the same columns by the previous panel.
+            const long long nnext = std::min<long long>(nb, N2);
+            const long long nsec = std::min<long long>(nb, N2 - nnext);
+            const long long nrest = N2 - nnext - nsec;
+            if (j0 > 0 && had_second) GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+            if (nsec > 0) {
+                GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));   // panel j0 factored
+                GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+                gn_handle_s side = *h;
+                side.stream = h->side;
+                GN_TRY(wy_apply(&side, W2 + nnext, ld, Mp, nsec, Vb, N, jb, T, 1, 1));
+                GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+                if (nrest >= 128 && oz) {
+                    // W3 <- W3 - V (T^T (V^T W3)) with the two large products digit-sliced
+                    double* W3 = W2 + nnext + nsec;
+                    GN_TRY(oz_dgemm(&side, jb, nrest, Mp, 1.0, Vb, 0, N, 1, W3, ld, 0, 0.0, q.Z1, nrest, oz,
+                                    oz_bytes));
+                    GN_TRY(dgemm(&side, jb, nrest, jb, 1.0, T, jb, 1, q.Z1, nrest, 0, 0.0, q.Z2, nrest, q.gws,
+                                 q.gws_bytes));
+                    GN_TRY(oz_dgemm(&side, Mp, nrest, jb, -1.0, Vb, 0, N, 0, q.Z2, nrest, 0, 1.0, W3, ld, oz,
+                                    oz_bytes));
+                } else if (nrest > 0) {
+                    GN_TRY(wy_apply(&side, W2 + nnext + nsec, ld, Mp, nrest, Vb, N, jb, T, 1, 1));
+                }
+                side_used = true;
+            }
+            had_second = nsec > 0;
+            GN_TRY(wy_apply(h, W2, ld, Mp, nnext, Vb, N, jb, T, 1, 0));
+            GN_TRY(factor_panel(j0 + jb));
+            continue;
+        }
+        const gn_status st = wy_apply(h, W2, ld, Mp, N2, Vb, N, jb, T, 1, 0);
+        if (st == GN_ERR_UNSUPPORTED) {
+            GN_TRY(dgemm(h, jb, N2, Mp, 1.0, Vb, N, 1, W2, ld, 0, 0.0, q.Z1, N2, q.gws, q.gws_bytes));
+            GN_TRY(dgemm(h, jb, N2, jb, 1.0, T, jb, 1, q.Z1, N2, 0, 0.0, q.Z2, N2, q.gws, q.gws_bytes));
+            GN_TRY(dgemm(h, Mp, N2, jb, -1.0, Vb, N, 0, q.Z2, N2, 0, 1.0, W2, ld, q.gws, q.gws_bytes));
+        } else {
+            GN_TRY(st);
+        }
+        GN_TRY(factor_panel(j0 + jb));
+    }
+    if (side_used) {   // every lagging update is done before R and the reflectors are used
+        GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+        GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    }
+    qr_write_r_kernel<<<ew_blocks(h, N * N), 256, 0, h->stream>>>(W, ld, static_cast<int>(N), R, ldr); count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    if (h != h0) {   // join the high-priority chain back into the caller's stream
+        GN_CUDA_TRY(cudaEventRecord(h0->ev_crit1, h->stream));
+        GN_CUDA_TRY(cudaStreamWaitEvent(h0->stream, h0->ev_crit1, 0));
+    }
+    return GN_OK;
+}
+
 size_t qr_oz_ws_bytes(long long M, long long N) {
-    return oz_ws_bytes(std::max<long long>(M, QR_SB), std::max<long long>(N, QR_SB), M, 0) +
-           sizeof(double) * (2 * QR_SB * QR_SB + 2 * QR_SB * N) + 2048;
+    // the Q formation's buffers, or the blocked factorization's, after the side stream's products' scratch
+    return qr_oz_side_bytes(M, N) +
+           std::max<size_t>(sizeof(double) * (2 * QR_SB * QR_SB + 2 * QR_SB * N) + 2048, qr_blk_bytes(M, N));
 }
 
 namespace {
