@@ -1815,7 +1815,7 @@ __global__ void v_zero_upper_kernel(double* V, long long ldv, int N) {
 // right on the side stream (one block behind), as three digit-sliced products
 // with the block's T from its Gram matrix (ut_inverse).  The trailing matrix is
 // sliced and combined once per block instead of once per panel.
-constexpr int QR_BB = 128;
+constexpr int QR_BB = 256;
 
 size_t qr_oz_side_bytes(long long M, long long N) {
     return oz_ws_bytes(std::max<long long>(M, QR_SB), std::max<long long>(N, QR_SB), M, 0);
@@ -1870,6 +1870,15 @@ gn_status block_apply(gn_handle h, double* C, long long ldc, long long Mp, long 
     return oz_dgemm(h, Mp, nc, bw, -1.0, V, 0, ldv, 0, Z2, nc, 0, 1.0, C, ldc, oz, oz_bytes);
 }
 
+// Whether qr_factor takes the blocked path for this shape and workspace (and,
+// when it does, the workspace's regions): the look-ahead (cluster panels, side
+// and high-priority streams, one-launch WY) and at least two blocks.
+bool qr_blocked_path(gn_handle h, long long M, long long N, void* oz, size_t oz_bytes, QrBlk* bk) {
+    const PanelCfg pc = panel_cfg(h, M);
+    const bool lookahead = pc.cluster && h->side != nullptr && h->crit != nullptr && wy_usable(M);
+    return lookahead && N >= 2 * QR_BB && QR_BB % pc.nb == 0 && qr_blk_carve(M, N, oz, oz_bytes, bk);
+}
+
 gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R, long long ldr,
                     double* ws, size_t ws_bytes, void* oz, size_t oz_bytes) {
     if (M < N || N <= 0) return GN_ERR_SHAPE;
@@ -1912,7 +1921,7 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
     }
     bool had_second = false, side_used = false;
     QrBlk bk;
-    const bool blocked = lookahead && N >= 2 * QR_BB && QR_BB % nb == 0 && qr_blk_carve(M, N, oz, oz_bytes, &bk);
+    const bool blocked = lookahead && qr_blocked_path(h0, M, N, oz, oz_bytes, &bk);
     if (blocked) {
         // rows above a panel inside its block are part of V_B and must read zero
         GN_CUDA_TRY(cudaMemsetAsync(q.V, 0, sizeof(double) * M * N, h->stream));
@@ -2048,6 +2057,34 @@ namespace {
 // ut_inverse.
 gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double* Q, long long ldq, void* oz,
                     size_t oz_bytes) {
+    static_assert(QR_BB == QR_SB, "the blocked factorization's T_b serve the Q formation's blocks");
+    QrBlk bk;
+    if (qr_blocked_path(h, M, N, oz, oz_bytes, &bk)) {
+        // the factorization left V zero above each block's diagonal and T_b of
+        // every block but the last in bk.TB (same V_b, tau and construction)
+        const long long nblk = (N + QR_BB - 1) / QR_BB;
+        for (long long bi = nblk - 1; bi >= 0; --bi) {
+            const long long j0 = bi * QR_BB;
+            const long long nbb = std::min<long long>(QR_BB, N - j0), Mp = M - j0, Nq = N - j0;
+            const double* Vb = q.V + j0 * N + j0;
+            double* Qs = Q + j0 * ldq + j0;
+            double* Tb = bk.TB + bi * QR_BB * QR_BB;
+            if (bi == nblk - 1) {
+                GN_TRY(oz_dgemm(h, nbb, nbb, Mp, 1.0, Vb, 0, N, 1, Vb, N, 0, 0.0, bk.GB, QR_BB, bk.oz_side,
+                                bk.oz_side_bytes));
+                ut_inverse_kernel<<<static_cast<unsigned>(nbb), 32, 0, h->stream>>>(
+                    bk.GB, QR_BB, q.tau + j0, static_cast<int>(nbb), Tb, QR_BB); count_launch();
+                GN_CUDA_TRY(cudaGetLastError());
+            }
+            GN_TRY(oz_dgemm(h, nbb, Nq, Mp, 1.0, Vb, 0, N, 1, Qs, ldq, 0, 0.0, bk.Z1s, Nq, bk.oz_side,
+                            bk.oz_side_bytes));
+            GN_TRY(oz_dgemm(h, nbb, Nq, nbb, 1.0, Tb, 0, QR_BB, 0, bk.Z1s, Nq, 0, 0.0, bk.Z2s, Nq, bk.oz_side,
+                            bk.oz_side_bytes));
+            GN_TRY(oz_dgemm(h, Mp, Nq, nbb, -1.0, Vb, 0, N, 0, bk.Z2s, Nq, 0, 1.0, Qs, ldq, bk.oz_side,
+                            bk.oz_side_bytes));
+        }
+        return GN_OK;
+    }
     char* base = static_cast<char*>(oz);
     const size_t g_bytes = (sizeof(double) * QR_SB * QR_SB + 255) & ~static_cast<size_t>(255);
     const size_t w_bytes = (sizeof(double) * QR_SB * N + 255) & ~static_cast<size_t>(255);
