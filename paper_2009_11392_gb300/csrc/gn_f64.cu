@@ -1754,33 +1754,42 @@ __global__ void __launch_bounds__(32) ut_inverse_kernel(const double* __restrict
 #pragma unroll
     for (int p = NT - 1; p >= 0; --p) {
         if (p > qb) continue;   // warp-uniform
+        // the block's coefficients in registers first (loads off the chain):
+        // G rows 32p .. 32p + 31 of this lane's column (G is ldg x ldg, ldg >=
+        // QR_SB, so every row read exists; rows past w are never used) and tau
+        double gcol[32];
+#pragma unroll
+        for (int sr = 0; sr < 32; ++sr) gcol[sr] = G[static_cast<long long>(32 * p + sr) * ldg + 32 * p + lane];
+        const double tl = 32 * p + lane < n ? tau[32 * p + lane] : 0.0;
 #pragma unroll
         for (int sr = 31; sr >= 0; --sr) {
             const int i = 32 * p + sr;
             if (i > w) continue;   // rows past w stay zero
             // the chain per row is one shuffle and one FMA: tau_i scales the
             // coefficients (off the chain), not the broadcast value
-            const double ti = tau[i];
-            const double cik = lane < sr ? G[static_cast<long long>(i) * ldg + 32 * p + lane] * ti : 0.0;
+            const double ti = __shfl_sync(0xffffffffu, tl, sr);
+            const double cik = lane < sr ? gcol[sr] * ti : 0.0;
             const double xu = __shfl_sync(0xffffffffu, x[p], sr);
             x[p] = lane == sr ? xu * ti : fma(-cik, xu, x[p]);
         }
         if (p == 0) break;
-        // two partial sums per block row: half the FMA chain
+        // two partial sums per block row: half the FMA chain; rows past w
+        // contribute nothing (their coefficient is taken as 0, not their value)
         double y[NT];
 #pragma unroll
         for (int m = 0; m < NT; ++m) y[m] = 0.0;
 #pragma unroll
         for (int kk = 0; kk < 32; ++kk) {
             const int k = 32 * p + kk;
-            if (k > w) break;
+            const bool on = k <= w;
             const double xk = __shfl_sync(0xffffffffu, x[p], kk);
             const double* gk = G + static_cast<long long>(k) * ldg + lane;
 #pragma unroll
             for (int m = 0; m < NT; ++m) {
                 if (m >= p) continue;
-                if (kk & 1) y[m] = fma(-gk[32 * m], xk, y[m]);
-                else x[m] = fma(-gk[32 * m], xk, x[m]);
+                const double g = on ? gk[32 * m] : 0.0;
+                if (kk & 1) y[m] = fma(-g, xk, y[m]);
+                else x[m] = fma(-g, xk, x[m]);
             }
         }
 #pragma unroll
@@ -1953,18 +1962,15 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
             const long long nnext = std::min<long long>(QR_BB, N2);
             const long long nsec = std::min<long long>(QR_BB, N2 - nnext);
             const long long nrest = N2 - nnext - nsec;
-            if (nsec > 0) {   // the block after next, then everything further right, on the side stream
+            if (nsec > 0) {   // everything right of the next block, on the side stream, in one update: the
+                              // chain waits for it only after the next block's panels
                 GN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
                 GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
                 gn_handle_s side = *h;
                 side.stream = h->side;
-                double* C2 = W + b0 * ld + b0 + bw + nnext;
-                GN_TRY(block_apply(&side, C2, ld, Mp, nsec, VB, N, static_cast<int>(bw), TB, QR_BB, bk.Z1s, bk.Z2s,
-                                   bk.oz_side, bk.oz_side_bytes));
+                GN_TRY(block_apply(&side, W + b0 * ld + b0 + bw + nnext, ld, Mp, nsec + nrest, VB, N,
+                                   static_cast<int>(bw), TB, QR_BB, bk.Z1s, bk.Z2s, bk.oz_side, bk.oz_side_bytes));
                 GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
-                if (nrest > 0)
-                    GN_TRY(block_apply(&side, C2 + nsec, ld, Mp, nrest, VB, N, static_cast<int>(bw), TB, QR_BB,
-                                       bk.Z1s, bk.Z2s, bk.oz_side, bk.oz_side_bytes));
                 side_used = true;
             }
             pending = nsec > 0;
