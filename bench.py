@@ -54,7 +54,7 @@ UNIT = "approximations/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gn", choices=["gn", "reference"])
     ap.add_argument("--m", type=int, default=32768)
