@@ -374,6 +374,11 @@ size_t tc_carve(long long m, long long n, long long r, long long l, int sms, cha
     return off + 256;
 }
 
+// BF16 digits per operand of the FP32 adjoint's digit-sliced products: every
+// term within about 2^-27 of max|a_i.| max|b_.j| (orders 0..3, all exact in the
+// FP32 accumulators), far inside the FP32 gradient's 1e-3.
+constexpr int ADJ_DIGITS = 4;
+
 // The steps both directions share.  The sketches of the FP32 A feed the core,
 // whose conditioning amplifies their errors, so they are formed to FP64
 // accuracy by digit slicing on the tensor cores: AX (m x r) and (Y^T A)^T =
@@ -383,9 +388,9 @@ gn_status tc_front(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* 
                    long long r, long long rl, TcWs& t) {
     GN_TRY(copy_f32_to_f64(h, static_cast<const float*>(X->data), n, r, X->ld, t.X64, r));
     GN_TRY(copy_f32_to_f64(h, static_cast<const float*>(Y->data), m, rl, Y->ld, t.Y64, rl));
-    GN_TRY(oz_dgemm(h, m, r, n, 1.0, A->data, 1, A->ld, 0, t.X64, r, 0, 0.0, t.AX, r, t.oz, t.oz_bytes));
-    GN_TRY(oz_dgemm(h, n, rl, m, 1.0, A->data, 1, A->ld, 1, t.Y64, rl, 0, 0.0, t.YtAT, rl, t.oz, t.oz_bytes));
-    GN_TRY(oz_dgemm(h, rl, r, n, 1.0, t.YtAT, 0, rl, 1, t.X64, r, 0, 0.0, t.C, r, t.oz, t.oz_bytes));
+    GN_TRY(oz_dgemm(h, m, r, n, 1.0, A->data, 1, A->ld, 0, t.X64, r, 0, 0.0, t.AX, r, t.oz, t.oz_bytes, ADJ_DIGITS));
+    GN_TRY(oz_dgemm(h, n, rl, m, 1.0, A->data, 1, A->ld, 1, t.Y64, rl, 0, 0.0, t.YtAT, rl, t.oz, t.oz_bytes, ADJ_DIGITS));
+    GN_TRY(oz_dgemm(h, rl, r, n, 1.0, t.YtAT, 0, rl, 1, t.X64, r, 0, 0.0, t.C, r, t.oz, t.oz_bytes, ADJ_DIGITS));
     GN_CUDA_TRY(cudaMemcpyAsync(t.Wq, t.C, sizeof(double) * rl * r, cudaMemcpyDeviceToDevice, h->stream));
     GN_TRY(householder_qr(h, t.Wq, rl, r, r, t.Q, r, t.R, r, t.inner, t.inner_bytes));
     GN_TRY(trsm_right_upper(h, t.AX, m, r, r, t.R, r, 0, t.inner, t.inner_bytes, t.oz, t.oz_bytes));   // F in AX
@@ -405,9 +410,9 @@ gn_status backward_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_ma
     // The contractions over G feed W and K, where the projection (I - Q Q^T)
     // cancels most of W^T: FP64-accurate digit-sliced products.
     //   S1 = G (Y^T A)^T (m x (r+l)),  S2^T = G^T F (n x r),  W = F^T S1 (r x (r+l))
-    GN_TRY(oz_dgemm(h, m, rl, n, 1.0, Gup->data, 1, Gup->ld, 0, t.YtAT, rl, 0, 0.0, t.S1, rl, t.oz, t.oz_bytes));
-    GN_TRY(oz_dgemm(h, n, r, m, 1.0, Gup->data, 1, Gup->ld, 1, F, r, 0, 0.0, t.S2T, r, t.oz, t.oz_bytes));
-    GN_TRY(oz_dgemm(h, r, rl, m, 1.0, F, 0, r, 1, t.S1, rl, 0, 0.0, t.W64, rl, t.oz, t.oz_bytes));
+    GN_TRY(oz_dgemm(h, m, rl, n, 1.0, Gup->data, 1, Gup->ld, 0, t.YtAT, rl, 0, 0.0, t.S1, rl, t.oz, t.oz_bytes, ADJ_DIGITS));
+    GN_TRY(oz_dgemm(h, n, r, m, 1.0, Gup->data, 1, Gup->ld, 1, F, r, 0, 0.0, t.S2T, r, t.oz, t.oz_bytes, ADJ_DIGITS));
+    GN_TRY(oz_dgemm(h, r, rl, m, 1.0, F, 0, r, 1, t.S1, rl, 0, 0.0, t.W64, rl, t.oz, t.oz_bytes, ADJ_DIGITS));
     // K R^T = W^T - Q (Q^T W^T + W Q)   ((r+l) x r, FP64)
     GN_TRY(transpose_f64(h, t.W64, r, rl, rl, t.Wt, r));
     GN_TRY(dgemm(h, r, r, rl, 1.0, t.Q, r, 1, t.Wt, r, 0, 0.0, t.M1, r, t.inner, t.inner_bytes));

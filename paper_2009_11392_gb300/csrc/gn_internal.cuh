@@ -165,9 +165,11 @@ gn_status householder_qr(gn_handle h, double* W, long long M, long long N, long 
                          double* ws, size_t ws_bytes);
 // The two halves of householder_qr: the factorization (R written, reflectors
 // kept in ws) and the formation of the thin Q from them (same W and ws).
-// oz (optional, >= qr_oz_ws_bytes(M, N)): the lagging trailing updates of the
-// look-ahead (the columns beyond the next two panels) as digit-sliced products
-// on the tensor cores (for cores of FP32 sketches); null: FP64 units only.
+// oz (optional, >= qr_oz_ws_bytes(M, N)): with the look-ahead and at least two
+// 256-column blocks, the factorization is blocked and each block's update of the
+// columns to its right runs as digit-sliced products on the tensor cores (for
+// cores of FP32 sketches); the blocks' T stay in oz for qr_form_q; null: FP64
+// units only.
 gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long ld, double* R,
                     long long ldr, double* ws, size_t ws_bytes, void* oz = nullptr, size_t oz_bytes = 0);
 // oz (optional, >= qr_oz_ws_bytes(M, N)): form Q in blocks of 256 reflectors with
@@ -187,11 +189,13 @@ gn_status trsm_right_upper(gn_handle h, double* F, long long m, long long k, lon
                            void* oz = nullptr, size_t oz_bytes = 0);
 
 // FP64 product on the BF16 tensor cores by exact digit slicing (gn_ozaki.cu);
-// same operand conventions as dgemm, A FP64 or (a_f32) FP32.
+// same operand conventions as dgemm, A FP64 or (a_f32) FP32.  digits: BF16
+// digits per operand row / column (7: FP64 accuracy; d < 7: every term carries
+// an error of about 2^(1 - 7d) max|a_i.| max|b_.j|).
 size_t oz_ws_bytes(long long M, long long N, long long K, int a_f32);
 gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double alpha, const void* A, int a_f32,
                    long long lda, int ta, const double* B, long long ldb, int tb, double beta, double* C,
-                   long long ldc, void* ws, size_t ws_bytes);
+                   long long ldc, void* ws, size_t ws_bytes, int digits = 7);
 
 // Core diagnostics (one CTA): out3[0] = est ||R^{-1}||_2 (if want_estimate),
 // out3[1] = est ||R||_2 (if eps_relative), out3[2] = the absolute threshold

@@ -281,10 +281,10 @@ size_t oz_ws_bytes(long long M, long long N, long long K, int a_f32) {
 
 gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double alpha, const void* A, int a_f32,
                    long long lda, int ta, const double* B, long long ldb, int tb, double beta, double* C,
-                   long long ldc, void* ws, size_t ws_bytes) {
+                   long long ldc, void* ws, size_t ws_bytes, int digits) {
     if (M <= 0 || N <= 0) return GN_OK;
-    if (K <= 0 || !A || !B || !C || !ws) return GN_ERR_INVALID_ARG;
-    const int sa = OZ_MAX_DIGITS, sb = OZ_MAX_DIGITS;
+    if (K <= 0 || !A || !B || !C || !ws || digits < 2 || digits > OZ_MAX_DIGITS) return GN_ERR_INVALID_ARG;
+    const int sa = digits, sb = digits;
     if (M > (1LL << 30) || N > (1LL << 30)) return GN_ERR_SHAPE;
     OzWs o;
     if (!oz_carve(M, N, K, sa, sb, ws, ws_bytes, &o)) return GN_ERR_WORKSPACE;
