@@ -139,9 +139,9 @@ def test_factors_tensor_core_truncated_branch(gn, H):
 
 @pytest.mark.parametrize("n,r,l", [(2048, 600, 300), (700, 96, 48)])
 def test_core_q_tensor_core_vs_fp64_units(gn, H, n, r, l):
-    """The core's Householder QR with its lagging trailing updates and the
-    formation of Q (256-reflector blocks) as digit-sliced products on the
-    tensor cores, against the same QR on the FP64 units: R and Q equal to a
+    """The core's Householder QR with its block updates (256-column blocks,
+    r = 600) and the formation of Q as digit-sliced products on the tensor
+    cores, against the same QR on the FP64 units: R and Q equal to a
     few 1e-11 (each digit-sliced product errs by ~1e-13 of |A||B| per
     element), Q orthonormal to 1e-12 r and C = QR to 1e-11 relative (the
     trailing products' error, far below the 2^-24 of the FP32 sketches that
