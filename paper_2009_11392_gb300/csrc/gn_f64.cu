@@ -1735,11 +1735,15 @@ namespace {
 // One warp per column.
 constexpr int QR_SB = 256;   // reflectors per block of the tensor-core Q formation
 
-__global__ void __launch_bounds__(32) ut_inverse_kernel(const double* __restrict__ G, long long ldg,
-                                                        const double* __restrict__ tau, int n,
-                                                        double* __restrict__ X, long long ldx) {
-    const int w = blockIdx.x;   // the column of T this warp solves for
-    const int lane = threadIdx.x;
+// Four warps per CTA, one per SM sub-partition (each warp's FP64 instructions
+// then have a sub-partition's FP64 unit to themselves); CTA b takes columns b,
+// b + G, b + 2G, b + 3G (G = gridDim.x), one from each quarter, so the CTAs
+// carry equal work.  No CTA-wide barrier: a warp past n just returns.
+__global__ void __launch_bounds__(128) ut_inverse_kernel(const double* __restrict__ G, long long ldg,
+                                                         const double* __restrict__ tau, int n,
+                                                         double* __restrict__ X, long long ldx) {
+    const int w = blockIdx.x + gridDim.x * (threadIdx.x >> 5);   // the column of T this warp solves for
+    const int lane = threadIdx.x & 31;
     if (w >= n) return;
     constexpr int NT = QR_SB / 32;
     // lane l holds x_{32 t + l}; blocks of 32 rows from the one holding row w up.
@@ -1801,6 +1805,12 @@ __global__ void __launch_bounds__(32) ut_inverse_kernel(const double* __restrict
         const int k = lane + 32 * t;
         if (k < n) X[k * ldx + w] = x[t];
     }
+}
+
+void launch_ut_inverse(gn_handle h, const double* G, long long ldg, const double* tau, int n, double* X,
+                       long long ldx) {
+    ut_inverse_kernel<<<static_cast<unsigned>((n + 3) / 4), 128, 0, h->stream>>>(G, ldg, tau, n, X, ldx);
+    count_launch();
 }
 
 // Zero V above the diagonal inside each block of QR_SB reflectors: a panel
@@ -1953,9 +1963,7 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
             double* TB = bk.TB + bi * QR_BB * QR_BB;
             GN_TRY(oz_dgemm(h, bw, bw, Mp, 1.0, VB, 0, N, 1, VB, N, 0, 0.0, bk.GB, QR_BB, bk.oz_crit,
                             bk.oz_crit_bytes));
-            ut_inverse_kernel<<<static_cast<unsigned>(bw), 32, 0, h->stream>>>(bk.GB, QR_BB, q.tau + b0,
-                                                                              static_cast<int>(bw), TB, QR_BB);
-            count_launch();
+            launch_ut_inverse(h, bk.GB, QR_BB, q.tau + b0, static_cast<int>(bw), TB, QR_BB);
             GN_CUDA_TRY(cudaGetLastError());
             // the next block's columns already have the block before this one (side stream)
             if (pending) GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
@@ -2078,8 +2086,7 @@ gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double
             if (bi == nblk - 1) {
                 GN_TRY(oz_dgemm(h, nbb, nbb, Mp, 1.0, Vb, 0, N, 1, Vb, N, 0, 0.0, bk.GB, QR_BB, bk.oz_side,
                                 bk.oz_side_bytes));
-                ut_inverse_kernel<<<static_cast<unsigned>(nbb), 32, 0, h->stream>>>(
-                    bk.GB, QR_BB, q.tau + j0, static_cast<int>(nbb), Tb, QR_BB); count_launch();
+                launch_ut_inverse(h, bk.GB, QR_BB, q.tau + j0, static_cast<int>(nbb), Tb, QR_BB);
                 GN_CUDA_TRY(cudaGetLastError());
             }
             GN_TRY(oz_dgemm(h, nbb, Nq, Mp, 1.0, Vb, 0, N, 1, Qs, ldq, 0, 0.0, bk.Z1s, Nq, bk.oz_side,
@@ -2108,8 +2115,7 @@ gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double
         const double* Vb = q.V + j0 * N + j0;   // Mp x nbb, ld N (explicit unit diagonal, zeros above)
         double* Qs = Q + j0 * ldq + j0;
         GN_TRY(oz_dgemm(h, nbb, nbb, Mp, 1.0, Vb, 0, N, 1, Vb, N, 0, 0.0, G, QR_SB, ozw, ozw_bytes));
-        ut_inverse_kernel<<<static_cast<unsigned>(nbb), 32, 0, h->stream>>>(   // a warp per column, on every SM
-            G, QR_SB, q.tau + j0, static_cast<int>(nbb), Tb, QR_SB); count_launch();
+        launch_ut_inverse(h, G, QR_SB, q.tau + j0, static_cast<int>(nbb), Tb, QR_SB);
         GN_CUDA_TRY(cudaGetLastError());
         GN_TRY(oz_dgemm(h, nbb, Nq, Mp, 1.0, Vb, 0, N, 1, Qs, ldq, 0, 0.0, Wb, Nq, ozw, ozw_bytes));
         GN_TRY(oz_dgemm(h, nbb, Nq, nbb, 1.0, Tb, 0, QR_SB, 0, Wb, Nq, 0, 0.0, Wb2, Nq, ozw, ozw_bytes));
