@@ -8,10 +8,12 @@
 //   DIAG_RAISE  : C = Q R (no pivoting), |R_ii| raised the same way: F = AX R~^{-1}
 //
 // The SVD and pivoted variants factor C in one CTA's shared memory (r <= 128,
-// r + l <= 192, the batched path's limits): the SVD by one-sided (Hestenes)
-// Jacobi rotations of the rows of C^T, in round-robin order, with V^T
-// accumulated in global memory; the pivoted QR by Householder reflectors with
-// the column of largest remaining norm moved forward at each step.  DIAG_RAISE
+// r + l <= 192, the batched path's limits): the pivoted QR by Householder
+// reflectors with the column of largest remaining norm moved forward at each
+// step; the SVD from it, preconditioned as Drmac and Veselic (2008) do, by
+// one-sided (Hestenes) Jacobi rotations of the rows of R in round-robin order
+// (C P = Q R, G^T R = T with orthogonal rows, so U = Q G and V = P T^T S^-1),
+// with the rotations accumulated in global memory.  DIAG_RAISE
 // takes the library's blocked Householder QR for any r.  The products that
 // form F and G and the triangular solves are the FP64 routines of gn_f64.cu.
 #include "gn_internal.cuh"
@@ -33,17 +35,45 @@ __device__ inline double group_sum(double v, int g) {
 }
 
 // C (M x N, global, ld N) -> one of the small-core factorizations.
-//   Ul (M x N, ld N): U (SVD variants, columns by decreasing s) or Q (RRQR)
-//   Wr (N x N, ld N): V S~^{-1} (SVD variants) or R~ (RRQR, upper triangular)
-//   VT (N x N, ld N): scratch for V^T
+//   Ul (M x N, ld N): Q (RRQR); unused by the SVD variants
+//   Wr (N x N, ld N): V S~^{-1} (SVD variants, columns by decreasing s) or R~ (RRQR, upper triangular)
+//   VT (N x N, ld N): scratch for the rotations G^T
+//   Qg (M x N), Rg (N x N): SVD variants: the pivoted QR's Q and R; Rg then
+//     receives G with columns by decreasing s (U = Qg Rg, formed by the caller)
 //   perm (N): RRQR column order; sv (N): s (SVD) or diag(R) after pivoting
 //   out[0] = k, out[1] = Jacobi sweeps
 __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restrict__ C, int M, int N, int variant,
                                                           double eps, double* Ul, double* Wr, double* VT, int* perm,
-                                                          double* sv, int* out) {
+                                                          double* sv, int* out, double* Qg, double* Rg) {
     extern __shared__ double shm[];
     const int tid = threadIdx.x;
-    if (variant == GN_VARIANT_RRQR_RAISE) {
+    if (variant != GN_VARIANT_RRQR_RAISE) {
+        // SVD variants, preconditioned (Drmac and Veselic): C P = Q R by the
+        // pivoted QR, R to Rg and the explicit Q to Qg; the Jacobi below then
+        // runs on the rows of R (N x N), which the pivoting leaves nearly
+        // orthogonal, instead of on the columns of C.
+        Smem sm;
+        sm.ld = N + 1;
+        sm.S = shm;
+        sm.red = sm.S + static_cast<size_t>(MMAX) * (NMAX + 1);
+        sm.tau = sm.red + BW * NMAX;
+        sm.dsum = sm.tau + NMAX;
+        sm.wv = sm.dsum + NMAX;
+        sm.scal = sm.wv + NMAX;
+        const int ld = sm.ld;
+        for (int e = tid; e < M * N; e += BT) sm.S[(e / N) * ld + e % N] = C[e];
+        for (int j = tid; j < N; j += BT) perm[j] = j;
+        __syncthreads();
+        smem_qr(sm, M, N, perm);
+        for (int e = tid; e < N * N; e += BT) {
+            const int i = e / N, j = e - i * N;
+            Rg[e] = j >= i ? sm.S[i * ld + j] : 0.0;
+        }
+        __syncthreads();
+        smem_form_q(sm, M, N);
+        for (int e = tid; e < M * N; e += BT) Qg[e] = sm.S[(e / N) * ld + e % N];
+        __syncthreads();   // R and Q written (block-wide visibility) before shared memory is reused
+    } else {
         Smem sm;
         sm.ld = N + 1;
         sm.S = shm;
@@ -83,15 +113,18 @@ __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restri
         return;
     }
 
-    // ---- one-sided Jacobi on the rows of T = C^T (N x M, ld M + 1)
-    const int ldt = M + 1;
+    // ---- one-sided Jacobi on the rows of T = R (N x N, ld N + 1): plane
+    // rotations of row pairs in round-robin order until every pair is
+    // orthogonal to tol; G^T (the product of the rotations) accumulates in VT.
+    const int MJ = N;                       // row length
+    const int ldt = MJ + 1;
     double* T = shm;
     double* s_norm = T + static_cast<size_t>(N) * ldt;   // [NMAX]
     int* s_rank = reinterpret_cast<int*>(s_norm + NMAX);  // [NMAX]
     __shared__ int s_rot;
-    for (int e = tid; e < M * N; e += BT) {
-        const int i = e / N, j = e - i * N;
-        T[j * ldt + i] = C[e];
+    for (int e = tid; e < N * N; e += BT) {
+        const int j = e / N, i = e - j * N;
+        T[j * ldt + i] = Rg[e];
     }
     for (int e = tid; e < N * N; e += BT) VT[e] = (e / N == e % N) ? 1.0 : 0.0;
     __syncthreads();
@@ -100,7 +133,7 @@ __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restri
     int g = 32;
     while (g > 1 && g * npairs > BT) g >>= 1;   // threads per pair (a power of two <= 32)
     const int pair = tid / g, gl = tid % g;
-    const double tol = 2.0 * static_cast<double>(M) * 1.1102230246251565e-16;
+    const double tol = 2.0 * static_cast<double>(MJ) * 1.1102230246251565e-16;
     int sweeps = 0;
     for (; sweeps < JACOBI_MAX_SWEEPS; ++sweeps) {
         if (tid == 0) s_rot = 0;
@@ -117,7 +150,7 @@ __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restri
             const bool act = q < N;
             double al = 0.0, be = 0.0, ga = 0.0;
             if (act)
-                for (int i = gl; i < M; i += g) {
+                for (int i = gl; i < MJ; i += g) {
                     const double tp = T[p * ldt + i], tq = T[q * ldt + i];
                     al = fma(tp, tp, al);
                     be = fma(tq, tq, be);
@@ -131,7 +164,7 @@ __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restri
                 const double zeta = (be - al) / (2.0 * ga);
                 const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                 const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                for (int i = gl; i < M; i += g) {
+                for (int i = gl; i < MJ; i += g) {
                     const double tp = T[p * ldt + i], tq = T[q * ldt + i];
                     T[p * ldt + i] = c * tp - s * tq;
                     T[q * ldt + i] = s * tp + c * tq;
@@ -153,7 +186,7 @@ __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restri
     // singular values = row norms of T; ranks by decreasing value (index order on ties)
     for (int j = tid / 32; j < N; j += BW) {
         double a = 0.0;
-        for (int i = tid % 32; i < M; i += 32) a = fma(T[j * ldt + i], T[j * ldt + i], a);
+        for (int i = tid % 32; i < MJ; i += 32) a = fma(T[j * ldt + i], T[j * ldt + i], a);
         a = group_sum(a, 32);
         if (tid % 32 == 0) s_norm[j] = sqrt(a);
     }
@@ -180,21 +213,24 @@ __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restri
     }
     __syncthreads();
     const int k = s_k;
-    // U (M x N): column rank_j = T_j / s_j;  Wr (N x N): column rank_j = V_j / s~_j
-    for (int e = tid; e < M * N; e += BT) {
-        const int i = e / N, j = e - i * N;
-        const double sj = s_norm[j];
-        Ul[i * N + s_rank[j]] = sj > 0.0 ? T[j * ldt + i] / sj : 0.0;
+    // R = G T with T_j = s_j W_j (W orthonormal rows), so C P = (Q G) diag(s) W:
+    //   U = Q G, column rank_j = Q G_j  (G_j = row j of VT): Rg[:, rank_j] = VT[j, :]^T,
+    //     multiplied by Q outside the kernel;
+    //   V = P W^T: V[perm[i]][rank_j] = T[j][i] / s_j, stored as Wr = V S~^{-1}.
+    for (int e = tid; e < N * N; e += BT) {
+        const int j = e / N, i = e - j * N;   // Rg[i][rank_j] = G[i][j] = VT[j][i]
+        Rg[i * N + s_rank[j]] = VT[e];
     }
     for (int e = tid; e < N * N; e += BT) {
-        const int i = e / N, j = e - i * N;   // Wr[i][rank_j] = V[i][j] / s~_j = VT[j][i] / s~_j
+        const int j = e / N, i = e - j * N;
         const double sj = s_norm[j];
         const int pos = s_rank[j];
         double w;
-        if (variant == GN_VARIANT_SVD_TRUNCATE) w = pos < k ? VT[j * N + i] / sj : 0.0;
-        else w = VT[j * N + i] / fmax(sj, eps);
-        Wr[i * N + pos] = w;
+        if (variant == GN_VARIANT_SVD_TRUNCATE) w = pos < k && sj > 0.0 ? T[j * ldt + i] / (sj * sj) : 0.0;
+        else w = sj > 0.0 ? T[j * ldt + i] / (sj * fmax(sj, eps)) : 0.0;
+        Wr[perm[i] * N + pos] = w;
     }
+    (void)Ul;
 }
 
 size_t variant_smem_bytes() {
@@ -348,9 +384,12 @@ extern "C" gn_status gn_factors_variant(gn_handle h, const gn_mat* AX, const gn_
         double* svd = sv ? sv : v.VT;   // sv optional: any N doubles of scratch otherwise
         double* vt = sv ? v.VT : v.Wq;
         variant_core_kernel<<<1, BT, variant_smem_bytes(), h->stream>>>(
-            v.C, static_cast<int>(rl), static_cast<int>(r), variant, eps, v.Ul, v.Wr, vt, v.perm, svd, v.out);
+            v.C, static_cast<int>(rl), static_cast<int>(r), variant, eps, v.Ul, v.Wr, vt, v.perm, svd, v.out, v.Q,
+            v.R);
         count_launch();
         GN_CUDA_TRY(cudaGetLastError());
+        if (variant != GN_VARIANT_RRQR_RAISE)   // U = Q G (the kernel left G, columns by rank, in v.R)
+            GN_TRY(dgemm(h, rl, r, r, 1.0, v.Q, r, 0, v.R, r, 0, 0.0, v.Ul, r, v.inner, v.inner_bytes));
         int out_h[2] = {0, 0};
         GN_CUDA_TRY(cudaMemcpyAsync(out_h, v.out, sizeof(out_h), cudaMemcpyDeviceToHost, h->stream));
         GN_CUDA_TRY(cudaStreamSynchronize(h->stream));
