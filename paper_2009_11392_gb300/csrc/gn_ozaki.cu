@@ -4,10 +4,11 @@
 // Ogita, Oishi and Rump (Numer. Algorithms 59, 2012), here with BF16 digits and
 // the FP32 accumulators of tcgen05:
 //   * every row i of A (over the K range of one pass) is scaled by 2^-ea_i so that
-//     its entries lie in (-1/2, 1/2), and written as sum_s d_s 2^{-7(s+1)} with
-//     signed integer digits |d_s| <= 64 (round to nearest at each step, so every
-//     remainder stays in [-1/2, 1/2]); slice s holds d_s 2^{-7(s+1)}, exact in
-//     BF16.  Columns of B the same with 2^-eb_j.
+//     its entries lie in (-1/2, 1/2), rounded to 49 fractional bits and written
+//     as sum_s d_s 2^{-7(s+1)} with balanced base-128 digits |d_s| <= 64 (the
+//     plain digits of the value plus a bias of 64 per position, less 64); slice
+//     s holds d_s 2^{-7(s+1)}, exact in BF16.  Columns of B the same with 2^-eb_j.
+//     Both operands of a pass are sliced in one launch.
 //   * the slice products of one order o = s + t carry the unit 2^{-7(o+2)}; each
 //     term is at most 2^12 units, so the FP32 accumulation of the (o+1) products
 //     of order o over K terms is exact while (o+1) K 2^12 <= 2^24.  A pass covers
@@ -20,6 +21,8 @@
 // worst-case rounding error.  FP32 operands take 7 digits too: the digits cover
 // a window below the row's largest entry, not each entry's own 24 bits.
 #include "gn_internal.cuh"
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 
@@ -78,6 +81,7 @@ __device__ __forceinline__ long long fixed49(double x, int e) {
     else v = 0;
     return (b >> 63) ? -v : v;
 }
+
 __device__ __forceinline__ long long fixed49(float x, int e) {
     const uint32_t b = __float_as_uint(x);
     const int E = static_cast<int>((b >> 23) & 0xFF);
@@ -90,92 +94,234 @@ __device__ __forceinline__ long long fixed49(float x, int e) {
     return (b >> 31) ? -v : v;
 }
 
-// Signed base-2^7 digits of Y (round to nearest at each step): slice s holds
-// d_s 2^{-7(s+1)}, Y 2^-49 = sum_s d_s 2^{-7(s+1)}, |d_s| <= 64.
-__device__ __forceinline__ void write_digits(long long Y, int S, __nv_bfloat16* out, long long slice_stride) {
+// Signed base-2^7 digits of Y (|Y| <= 2^48): slice s holds d_s 2^{-7(s+1)},
+// |d_s| <= 64.  With a bias of 64 in each kept digit position (plus half of the
+// last kept unit when S < 7), U = Y + bias >= 0 has plain base-128 digits u_s,
+// and d_s = u_s - 64: the S digits sum to Y exactly for S = 7 and to Y rounded
+// to the last kept unit (nearest, ties up) for S < 7.  Bit fields of one 64-bit
+// integer, no carries to propagate.
+__device__ __forceinline__ unsigned long long digit_bias(int S) {
+    unsigned long long b = 0;
+#pragma unroll
+    for (int s = 0; s < OZ_MAX_DIGITS; ++s)
+        if (s < S) b += 64ull << (7 * (OZ_MAX_DIGITS - 1 - s));
+    if (S < OZ_MAX_DIGITS) b += 1ull << (7 * (OZ_MAX_DIGITS - S) - 1);
+    return b;
+}
+
+// Digits of two entries adjacent along K, stored as one bf16 pair per slice
+// (out 4-byte aligned, slice_stride even).
+__device__ __forceinline__ void write_digits2(long long Y0, long long Y1, int S, unsigned long long bias,
+                                              __nv_bfloat16* out, long long slice_stride) {
+    const unsigned long long U0 = static_cast<unsigned long long>(Y0) + bias;
+    const unsigned long long U1 = static_cast<unsigned long long>(Y1) + bias;
 #pragma unroll
     for (int s = 0; s < OZ_MAX_DIGITS; ++s) {
         if (s >= S) break;
         const int sh = 7 * (OZ_MAX_DIGITS - 1 - s);
-        const long long d = sh ? (Y + (1ll << (sh - 1))) >> sh : Y;
-        Y -= d * (1ll << sh);
-        out[s * slice_stride] = __float2bfloat16_rn(static_cast<float>(static_cast<int>(d)) *
-                                                    __int_as_float((127 - 7 * (s + 1)) << 23));
+        const unsigned u0 = s ? static_cast<unsigned>(U0 >> sh) & 127u : static_cast<unsigned>(U0 >> sh);
+        const unsigned u1 = s ? static_cast<unsigned>(U1 >> sh) & 127u : static_cast<unsigned>(U1 >> sh);
+        const float sc = __int_as_float((127 - 7 * (s + 1)) << 23);   // 2^{-7(s+1)}
+        const float2 f = make_float2(fmaf(__uint2float_rn(u0), sc, -64.0f * sc), fmaf(__uint2float_rn(u1), sc, -64.0f * sc));
+        *reinterpret_cast<__nv_bfloat162*>(out + s * slice_stride) = __float22bfloat162_rn(f);
     }
 }
 
-// Largest |entry| of every operand row, as the bits of |x|.  Rows contiguous
-// along K (s_k == 1): a warp per row.
+// ---- slicing of both operands of one pass in one launch
+//
+// An operand is `rows` rows of K entries (row i, entry k at src[i s_row + k s_k];
+// one of the strides is 1).  Its slices go to out[s slice_stride + i ldk + k] and
+// the bits of max_k |x_ik| to mx[i].  FP32 sources are widened to FP64 on load
+// (exact), so mx always holds FP64 bits.
+struct OzOperand {
+    const void* src;   // FP32 for operand 0 of the FP32-A instance, FP64 otherwise
+    long long s_row, s_k, ldk, slice_stride;
+    __nv_bfloat16* out;
+    unsigned long long* mx;
+    int rows, K, S;
+    int clusters;   // ceil(rows / 32): one cluster of OZ_CS CTAs per 32 rows
+};
+struct OzSliceArgs {
+    OzOperand op[2];
+};
+
+constexpr int OZ_CS = 8;                      // CTAs per cluster (the K split of a strided operand)
+constexpr int OZ_ST = 512;                    // threads per CTA
+constexpr int OZ_NW = OZ_ST / 32;
+constexpr int OZ_KC_MAX = OZ_KPASS / OZ_CS;   // K per CTA of a strided operand (<= 128)
+
+struct OzSmem {
+    long long ys[OZ_KC_MAX][33];
+    unsigned long long part[OZ_NW][32];
+    unsigned long long lmax[32], rmax[32];
+};
+
+// mx[i] in FP64 form for the combine: the largest |entry| itself for FP64 rows;
+// for FP32 rows an FP64 power of two with the same row exponent.
+__device__ __forceinline__ unsigned long long mx_word(unsigned long long m, double*) { return m; }
+__device__ __forceinline__ unsigned long long mx_word(unsigned long long m, float*) {
+    return m ? static_cast<unsigned long long>(row_exponent<float>(m) + 1021) << 52 : 0ull;
+}
+
+// K contiguous (s_k == 1): 4 rows per CTA, 128 threads (four warps) per row,
+// pairs of entries along K (8 entries per thread); the row maximum is a
+// shuffle plus an exchange between the row's four warps.
 template <typename T>
-__global__ void oz_rowmax_rows_kernel(const T* __restrict__ src, long long s_row, int rows, int K,
-                                      unsigned long long* __restrict__ mx) {
-    const long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= rows) return;   // warp-uniform
-    const T* row = src + w * s_row;
+__device__ __forceinline__ void slice_kcontig(const OzOperand& o, int q, int rank, OzSmem& sm) {
+    const T* src = static_cast<const T*>(o.src);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = tid >> 7, l = tid & 127;
+    const long long i = static_cast<long long>(q) * 32 + rank * 4 + r;
+    const bool live = i < o.rows;
+    const int K = o.K;
+    T v[8];
     unsigned long long m = 0;
-    for (int k = lane; k < K; k += 32) m = max(m, abs_bits(row[k]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) mx[w] = m;
+    for (int u = 0; u < 4; ++u) {
+        const int k = 2 * l + 256 * u;
+        v[2 * u] = live && k < K ? src[i * o.s_row + k] : T(0);
+        v[2 * u + 1] = live && k + 1 < K ? src[i * o.s_row + k + 1] : T(0);
+        m = max(m, max(abs_bits(v[2 * u]), abs_bits(v[2 * u + 1])));
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
+    if (lane == 0) sm.part[warp][0] = m;
+    __syncthreads();
+    m = max(max(sm.part[4 * r][0], sm.part[4 * r + 1][0]), max(sm.part[4 * r + 2][0], sm.part[4 * r + 3][0]));
+    if (!live) return;   // no barrier follows in this path
+    if (l == 0) o.mx[i] = mx_word(m, static_cast<T*>(nullptr));
+    const int e = row_exponent<T>(m);
+    const unsigned long long bias = digit_bias(o.S);
+    __nv_bfloat16* out = o.out + i * o.ldk;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int k = 2 * l + 256 * u;   // k + 1 < ldk: ldk is K rounded up to 8
+        if (k < K) write_digits2(fixed49(v[2 * u], e), fixed49(v[2 * u + 1], e), o.S, bias, out + k, o.slice_stride);
+    }
 }
 
-// Rows contiguous across rows (s_row == 1): blocks of 32 rows x one chunk of K,
-// the 8 warps striding the chunk; atomicMax into mx (zeroed before).
+// Rows contiguous (s_row == 1): the cluster's 8 CTAs split K into chunks of
+// <= 128; a CTA reads its 32 x chunk block along the rows (coalesced, 8
+// entries per thread), the partial row maxima go through distributed shared
+// memory, and the digits are written along K after a transpose in shared memory.
 template <typename T>
-__global__ void oz_rowmax_cols_kernel(const T* __restrict__ src, long long s_k, int rows, int K, int kchunk,
-                                      unsigned long long* __restrict__ mx) {
-    __shared__ unsigned long long part[8][32];
-    const int lane = threadIdx.x & 31, kg = threadIdx.x >> 5;
-    const long long i = static_cast<long long>(blockIdx.x) * 32 + lane;
-    const int k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
+__device__ __forceinline__ void slice_strided(const OzOperand& o, int q, int rank, OzSmem& sm) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const T* src = static_cast<const T*>(o.src);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = o.K;
+    const int kc = ((K + OZ_CS - 1) / OZ_CS + 7) / 8 * 8;   // <= 128, a multiple of 8
+    const int k0 = rank * kc, k1 = min(K, k0 + kc);
+    const long long i = static_cast<long long>(q) * 32 + lane;
+    const bool live = i < o.rows;
+    T v[8];
     unsigned long long m = 0;
-    if (i < rows)
-        for (int k = k0 + kg; k < k1; k += 8) m = max(m, abs_bits(src[i + k * s_k]));
-    part[kg][lane] = m;
-    __syncthreads();
-    if (kg == 0 && i < rows) {
 #pragma unroll
-        for (int g = 1; g < 8; ++g) m = max(m, part[g][lane]);
-        if (m) atomicMax(mx + i, m);
+    for (int u = 0; u < 8; ++u) {
+        const int k = k0 + warp + OZ_NW * u;
+        v[u] = live && k < k1 ? src[i + static_cast<long long>(k) * o.s_k] : T(0);
+        m = max(m, abs_bits(v[u]));
+    }
+    sm.part[warp][lane] = m;
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int g = 1; g < OZ_NW; ++g) m = max(m, sm.part[g][lane]);
+        sm.lmax[lane] = m;
+    }
+    cluster.sync();   // every CTA's partial maxima written
+    if (warp == 0) {
+        unsigned long long mr = 0;
+#pragma unroll
+        for (int c = 0; c < OZ_CS; ++c) mr = max(mr, cluster.map_shared_rank(sm.lmax, c)[lane]);
+        sm.rmax[lane] = mr;
+        if (rank == 0 && live) o.mx[i] = mx_word(mr, static_cast<T*>(nullptr));
+    }
+    cluster.sync();   // peers' reads of lmax done before any CTA moves on or exits
+    const int e = row_exponent<T>(sm.rmax[lane]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int kk = warp + OZ_NW * u;
+        if (kk < kc) sm.ys[kk][lane] = fixed49(v[u], e);
+    }
+    __syncthreads();
+    const int w = k1 - k0;
+    if (w <= 0) return;
+    // pairs along K: w is a multiple of 8 except in the last chunk, where an odd
+    // w pairs the last entry with the zero row kk = w < kc (column K < ldk).
+    // Thread: pair kp = tid % 64, rows tid / 64 + 8 j.
+    const int wp = (w + 1) / 2, kp = tid & 63;
+    if (kp >= wp) return;
+    const unsigned long long bias = digit_bias(o.S);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int ii = (tid >> 6) + 8 * j;
+        const long long row = static_cast<long long>(q) * 32 + ii;
+        if (row < o.rows)
+            write_digits2(sm.ys[2 * kp][ii], sm.ys[2 * kp + 1][ii], o.S, bias, o.out + row * o.ldk + k0 + 2 * kp,
+                          o.slice_stride);
     }
 }
 
-// Digits, rows contiguous along K: one thread per entry, k fastest.
-template <typename T>
-__global__ void oz_digits_rows_kernel(const T* __restrict__ src, long long s_row, int rows, int K, int S,
-                                      const unsigned long long* __restrict__ mx, __nv_bfloat16* __restrict__ out,
-                                      long long ldk, long long slice_stride) {
-    const long long total = static_cast<long long>(rows) * K;
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long i = e / K, k = e - i * K;
-        write_digits(fixed49(src[i * s_row + k], row_exponent<T>(mx[i])), S, out + i * ldk + k, slice_stride);
+// Cluster q of the grid slices rows [32 q', 32 q' + 32) of operand 0 (q' = q;
+// FP32 when A32) or of operand 1 (q' = q - op[0].clusters; FP64).
+template <bool A32>
+__global__ void __launch_bounds__(OZ_ST) oz_slice_kernel(const __grid_constant__ OzSliceArgs args) {
+    __shared__ OzSmem sm;
+    const int rank = static_cast<int>(cooperative_groups::this_cluster().block_rank());
+    int q = static_cast<int>(blockIdx.x) / OZ_CS;
+    const int which = q < args.op[0].clusters ? 0 : 1;
+    const OzOperand& o = args.op[which];
+    if (which) q -= args.op[0].clusters;
+    if (which == 0 && A32) {
+        if (o.s_k == 1) slice_kcontig<float>(o, q, rank, sm);
+        else slice_strided<float>(o, q, rank, sm);
+    } else {
+        if (o.s_k == 1) slice_kcontig<double>(o, q, rank, sm);
+        else slice_strided<double>(o, q, rank, sm);
     }
 }
 
-// Digits, rows contiguous across rows: 32 x 32 tiles through shared memory,
-// read along the rows, written along K.
-template <typename T>
-__global__ void oz_digits_cols_kernel(const T* __restrict__ src, long long s_k, int rows, int K, int S,
-                                      const unsigned long long* __restrict__ mx, __nv_bfloat16* __restrict__ out,
-                                      long long ldk, long long slice_stride) {
-    __shared__ long long ys[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads
-    const long long i0 = static_cast<long long>(blockIdx.x) * 32, k0 = static_cast<long long>(blockIdx.y) * 32;
-    const long long i = i0 + tx;
-    const int e = i < rows ? row_exponent<T>(mx[i]) : 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const long long k = k0 + ty + 8 * q;
-        ys[ty + 8 * q][tx] = (i < rows && k < K) ? fixed49(src[i + k * s_k], e) : 0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const long long ii = i0 + ty + 8 * q, kk = k0 + tx;
-        if (ii < rows && kk < K) write_digits(ys[tx][ty + 8 * q], S, out + ii * ldk + kk, slice_stride);
-    }
+OzOperand oz_operand(const void* src, long long s_row, long long s_k, long long rows, long long K, int S,
+                     __nv_bfloat16* out, long long ldk, long long slice_stride, unsigned long long* mx) {
+    OzOperand o;
+    o.src = src;
+    o.s_row = s_row;
+    o.s_k = s_k;
+    o.rows = static_cast<int>(rows);
+    o.K = static_cast<int>(K);
+    o.S = S;
+    o.out = out;
+    o.ldk = ldk;
+    o.slice_stride = slice_stride;
+    o.mx = mx;
+    o.clusters = static_cast<int>((rows + 31) / 32);
+    return o;
+}
+
+// Both operands of one pass in one launch (K <= OZ_KPASS).
+gn_status slice_pair(gn_handle h, const OzOperand& a, int a_f32, const OzOperand& b) {
+    OzSliceArgs args;
+    args.op[0] = a;
+    args.op[1] = b;
+    for (const OzOperand& o : args.op)
+        if ((o.s_k != 1 && o.s_row != 1) || o.K < 1 || o.K > OZ_KPASS || o.rows < 1) return GN_ERR_INVALID_ARG;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(OZ_CS * (static_cast<long long>(a.clusters) + b.clusters)));
+    cfg.blockDim = dim3(OZ_ST);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = OZ_CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (a_f32) GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, oz_slice_kernel<true>, args));
+    else GN_CUDA_TRY(cudaLaunchKernelEx(&cfg, oz_slice_kernel<false>, args));
+    count_launch();
+    return GN_OK;
 }
 
 // C[i, j] = beta C[i, j] + alpha 2^{ea_i + eb_j} sum_o D_o[i, j].  The exact
@@ -184,7 +330,7 @@ __global__ void oz_digits_cols_kernel(const T* __restrict__ src, long long s_k, 
 // blockIdx.y (no division per element); each exact order is an integer below
 // 2^24 units, so it converts through a 32-bit integer.
 __global__ void oz_combine_kernel(const float* __restrict__ D, long long d_stride, long long ldd, int norders,
-                                  int M, int N, const unsigned long long* __restrict__ mxa, int a_f32,
+                                  int M, int N, const unsigned long long* __restrict__ mxa,
                                   const unsigned long long* __restrict__ mxb, double alpha, double beta,
                                   double* __restrict__ C, long long ldc) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -200,7 +346,7 @@ __global__ void oz_combine_kernel(const float* __restrict__ D, long long d_strid
         float low = 0.0f;
         for (int o = norders - 1; o >= 4; --o) low += d[o * d_stride];
         // times 2^(ea + eb - 35): a power of two built from its bits when normal
-        const int ea = a_f32 ? row_exponent<float>(mxa[i]) : row_exponent<double>(mxa[i]);
+        const int ea = row_exponent<double>(mxa[i]);
         const int p = ea + eb - 35;
         const double x = fma(static_cast<double>(low), 34359738368.0, static_cast<double>(acc));
         const double v = (p >= -1022 && p <= 1023)
@@ -209,37 +355,6 @@ __global__ void oz_combine_kernel(const float* __restrict__ D, long long d_strid
         double* c = C + static_cast<long long>(i) * ldc + j;
         *c = beta == 0.0 ? v : fma(beta, *c, v);
     }
-}
-
-template <typename T>
-gn_status slice(gn_handle h, const T* src, long long s_row, long long s_k, long long rows, long long K, int S,
-                __nv_bfloat16* out, long long ldk, long long slice_stride, unsigned long long* mx) {
-    if (s_k == 1) {
-        oz_rowmax_rows_kernel<T><<<static_cast<unsigned>((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
-            src, s_row, static_cast<int>(rows), static_cast<int>(K), mx);
-        count_launch();
-        GN_CUDA_TRY(cudaGetLastError());
-        const long long total = rows * K;
-        const long long blocks = std::min<long long>((total + 255) / 256, static_cast<long long>(h->sm_count) * 16);
-        oz_digits_rows_kernel<T><<<static_cast<unsigned>(blocks), 256, 0, h->stream>>>(
-            src, s_row, static_cast<int>(rows), static_cast<int>(K), S, mx, out, ldk, slice_stride);
-    } else if (s_row == 1) {
-        constexpr int KCHUNK = 64;
-        GN_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * rows, h->stream));
-        const dim3 g1(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((K + KCHUNK - 1) / KCHUNK));
-        oz_rowmax_cols_kernel<T><<<g1, 256, 0, h->stream>>>(src, s_k, static_cast<int>(rows), static_cast<int>(K),
-                                                            KCHUNK, mx);
-        count_launch();
-        GN_CUDA_TRY(cudaGetLastError());
-        const dim3 g2(static_cast<unsigned>((rows + 31) / 32), static_cast<unsigned>((K + 31) / 32));
-        oz_digits_cols_kernel<T><<<g2, 256, 0, h->stream>>>(src, s_k, static_cast<int>(rows), static_cast<int>(K), S,
-                                                            mx, out, ldk, slice_stride);
-    } else {
-        return GN_ERR_INVALID_ARG;
-    }
-    count_launch();
-    GN_CUDA_TRY(cudaGetLastError());
-    return GN_OK;
 }
 
 struct OzWs {
@@ -309,14 +424,13 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
         // A rows (i over M, k along the pass) and B "rows" (j over N)
         const long long a_row = ta ? 1 : lda, a_k = ta ? lda : 1;
         const long long a_off = ta ? k0 * lda : k0;
-        if (a_f32)
-            GN_TRY(slice(h, static_cast<const float*>(A) + a_off, a_row, a_k, M, kc, sa, o.as, o.ldk, as_stride, o.mxa));
-        else
-            GN_TRY(slice(h, static_cast<const double*>(A) + a_off, a_row, a_k, M, kc, sa, o.as, o.ldk, as_stride,
-                         o.mxa));
         const long long b_row = tb ? ldb : 1, b_k = tb ? 1 : ldb;
         const long long b_off = tb ? k0 : k0 * ldb;
-        GN_TRY(slice(h, B + b_off, b_row, b_k, N, kc, sb, o.bs, o.ldk, bs_stride, o.mxb));
+        const size_t esz = a_f32 ? sizeof(float) : sizeof(double);
+        GN_TRY(slice_pair(h,
+                          oz_operand(static_cast<const char*>(A) + esz * a_off, a_row, a_k, M, kc, sa, o.as, o.ldk,
+                                     as_stride, o.mxa),
+                          a_f32, oz_operand(B + b_off, b_row, b_k, N, kc, sb, o.bs, o.ldk, bs_stride, o.mxb)));
         const double beta_pass = k0 == 0 ? beta : 1.0;
         const long long npanel = oz_npanel(M, N);
         for (long long j0 = 0; j0 < N; j0 += npanel) {
@@ -359,7 +473,7 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
             const unsigned gy = static_cast<unsigned>(
                 std::max<long long>(1, std::min<long long>(M, static_cast<long long>(h->sm_count) * 16 / gx)));
             oz_combine_kernel<<<dim3(gx, gy), 256, 0, h->stream>>>(
-                o.d, d_stride, o.ldd, norders, static_cast<int>(M), static_cast<int>(nb), o.mxa, a_f32, o.mxb + j0,
+                o.d, d_stride, o.ldd, norders, static_cast<int>(M), static_cast<int>(nb), o.mxa, o.mxb + j0,
                 alpha, beta_pass, C + j0, ldc);
             count_launch();
             GN_CUDA_TRY(cudaGetLastError());
