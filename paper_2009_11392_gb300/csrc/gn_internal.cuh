@@ -108,6 +108,14 @@ struct TcParams {
     // as two halves of their K range each (work items split_base + 2u, + 2u + 1),
     // adding into a pre-zeroed D.
     int split_base, nsplit;
+    // snake_groups > 0: CTA c takes tile k ncl + c in even rounds k and
+    // k ncl + ncl - 1 - c in odd ones, on snake_groups x (tiles of GEMM 0) CTAs
+    // at most.  With the GEMMs in decreasing cost order this pairs the longest
+    // with the shortest (GEMMs of n, n-1, ..., 1 units on ceil(n/2) groups: n
+    // units per CTA); the last-round split is off.
+    int snake_groups;
+    int snake;   // set by tc_launch from snake_groups
+    int max_ctas;
 };
 
 // Host helpers (gn_tc.cu).

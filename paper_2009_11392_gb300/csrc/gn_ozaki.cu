@@ -468,6 +468,9 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
                 g.ldd = o.ldd;
             }
             p.ngemm = norders;
+            // orders of 7, 6, ..., 1 slice products: the boustrophedon order on
+            // 4 groups of CTAs gives every CTA 7 (order 6; 5 + 0; 4 + 1; 3 + 2)
+            p.snake_groups = (norders + 1) / 2;
             GN_TRY(tc_launch(h, &p));
             const unsigned gx = static_cast<unsigned>((nb + 255) / 256);
             const unsigned gy = static_cast<unsigned>(

@@ -302,6 +302,12 @@ __device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t) {
     return c;
 }
 
+// Tile of round k for CTA cid (boustrophedon order when snake).  Once a CTA's
+// tile is past the end, so are all its later ones.
+__device__ __forceinline__ int sched_tile(int k, int cid, int ncl, int snake) {
+    return k * ncl + ((snake && (k & 1)) ? ncl - 1 - cid : cid);
+}
+
 __device__ void latch(int32_t* status, int code, int where, volatile int* abort_flag) {
     *abort_flag = 1;
     if (atomicCAS(&status[GN_DEV_STATUS], 0, code) == 0) status[GN_DEV_WHERE] = where;
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             uint32_t issued_mask = 0;            // stages that ever received a load
             uint32_t last_parity = 0;            // parity of the last armed phase per stage
             bool ok = true;
-            for (int t = cid; t < p.total_tiles && ok; t += ncl) {
+            for (int k = 0, t = sched_tile(0, cid, ncl, p.snake); t < p.total_tiles && ok; t = sched_tile(++k, cid, ncl, p.snake)) {
                 const TileCoord c = decode_tile<GROUPED>(p, t);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             uint32_t aphase = 0;
             bool ok = true;
             bool issued_any = false;
-            for (int t = cid; t < p.total_tiles && ok; t += ncl) {
+            for (int k = 0, t = sched_tile(0, cid, ncl, p.snake); t < p.total_tiles && ok; t = sched_tile(++k, cid, ncl, p.snake)) {
                 const TileCoord c = decode_tile<GROUPED>(p, t);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
                 const int nkb = G.nsrc * G.kblocks;
@@ -541,7 +547,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             stalled = !mbar_wait(stall_bar, 0, limit, abort_flag);
             if (stalled && lane == 0) latch(p.status, GN_ERR_TIMEOUT, 7, abort_flag);
         }
-        for (int t = cid; t < p.total_tiles && !stalled; t += ncl) {
+        for (int k = 0, t = sched_tile(0, cid, ncl, p.snake); t < p.total_tiles && !stalled; t = sched_tile(++k, cid, ncl, p.snake)) {
             const TileCoord c = decode_tile<GROUPED>(p, t);
             const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
             const bool got = mbar_wait(tfull_bar(acc), aphase, limit, abort_flag);
@@ -671,7 +677,8 @@ gn_status launch_cfg(gn_handle h, const TcParams& p, int total_tiles) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MT, F8>::SMEM));
         attr_set = true;
     }
-    const int ctas = total_tiles < h->sm_count ? total_tiles : h->sm_count;
+    int ctas = total_tiles < h->sm_count ? total_tiles : h->sm_count;
+    if (p.max_ctas > 0 && p.max_ctas < ctas) ctas = p.max_ctas;
     tc_multigemm_kernel<GROUPED, MT, F8><<<ctas, NUM_THREADS, Cfg<MT, F8>::SMEM, h->stream>>>(p);
     count_launch();
     GN_CUDA_TRY(cudaGetLastError());
@@ -714,7 +721,9 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
     // items adding into D, zeroed first; the last round then costs half a tile.
     p->split_base = 0;
     p->nsplit = 0;
-    if (!p->f8 && total > 0) {
+    p->snake = p->snake_groups > 0 ? 1 : 0;
+    p->max_ctas = p->snake ? p->snake_groups * p->g[0].tiles_m * p->g[0].tiles_n : 0;
+    if (!p->f8 && !p->snake && total > 0) {
         const int ncl = std::min(total, h->sm_count);
         const int R = total % ncl;
         const TcGemm& G = p->g[p->ngemm - 1];
