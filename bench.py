@@ -9,7 +9,7 @@ AX, Y^T A, Q, R): the sketch launch, the core product C = (Y^T A) X on the
 tensor cores (three bf16 slices of Y^T A), Householder QR of C in FP64 and the
 Section 5.1.2 detector / Section 5.1.1 truncation (mode AUTO).
 
-Steps run on --inflight handles (default 3), each with its own CUDA stream,
+Steps run on --inflight handles (default 5), each with its own CUDA stream,
 workspace and outputs: step i's core is enqueued without a host wait
 (GN_CORE_DEFER) and finished once the next steps are enqueued, so one step's
 latency-bound FP64 core overlaps the following steps' sketches and cores.  The latency
@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--m", type=int, default=32768)
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--r", type=int, default=1000)
-    ap.add_argument("--inflight", type=int, default=3, help="approximations in flight (handles / streams)")
+    ap.add_argument("--inflight", type=int, default=5, help="approximations in flight (handles / streams)")
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements and the CPU baseline")
     ap.add_argument("--op", default="bf16", choices=["bf16", "e4m3"],
                     help="sketch operand type of the timed step (e4m3: per-128x128-tile scales)")
