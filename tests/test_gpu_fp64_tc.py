@@ -57,6 +57,35 @@ def test_dgemm_tc_exact_on_scaled_integers(gn, H, M, N, K, ta, tb):
         assert np.all(np.abs(npy(C) - exact) <= 2.0 ** -52 * np.abs(exact))
 
 
+@pytest.mark.parametrize("M,N,K,ta,tb,a32", [(1, 1, 1, False, False, False), (33, 31, 1025, True, True, False),
+                                             (65, 40, 7, True, False, True), (40, 65, 2049, False, True, True),
+                                             (31, 97, 9, True, True, True)])
+def test_dgemm_tc_exact_slicing_edges(gn, H, M, N, K, ta, tb, a32):
+    """The slicing's edge cases on exact integer products: operands strided or
+    contiguous along K, FP32 or FP64 A, K = 1, odd K, a last pass of one
+    element, three passes, and row counts off the 32-row grain of the slicing
+    launch.  Each pass of at most 1024 of K is exact; the FP64 sum of the
+    passes rounds once per pass."""
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    Ai = rng.integers(-(1 << 20), 1 << 20, (M, K), dtype=np.int64)
+    Bi = rng.integers(-(1 << 20), 1 << 20, (K, N), dtype=np.int64)
+    ps = rng.integers(-20, 21, M)
+    qs = rng.integers(-20, 21, N)
+    parts = [(Ai[:, k0:k0 + 1024] @ Bi[k0:k0 + 1024]).astype(np.float64) for k0 in range(0, K, 1024)]
+    exact = np.ldexp(sum(parts), ps[:, None] + qs[None, :])
+    A = np.ldexp(Ai.astype(np.float64), ps[:, None])
+    B = np.ldexp(Bi.astype(np.float64), qs[None, :])
+    An = np.ascontiguousarray(A.T if ta else A)
+    At = torch.from_numpy(An.astype(np.float32) if a32 else An).cuda()
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T if tb else B)).cuda()
+    C = npy(H.dgemm_tc(At, Bt, ta=ta, tb=tb))
+    assert H.sync_status() == 0
+    if len(parts) == 1:
+        assert np.array_equal(C, exact)
+    else:
+        assert np.all(np.abs(C - exact) <= (len(parts) - 1) * 2.0 ** -52 * np.abs(exact))
+
+
 def test_dgemm_tc_alpha_beta_and_fp32_operand(gn, H):
     M, N, K = 200, 90, 150
     rng = np.random.default_rng(7)
