@@ -68,6 +68,8 @@ constexpr int TC_MAX_MAPS = 14;
 constexpr int TC_MAX_GEMMS = 7;
 constexpr int TC_MAX_SRC = 12;
 
+constexpr int TC_BK = 64;   // K elements per stage of the BF16 multi-GEMM (one K block)
+
 struct TcGemm {
     int M, N, K;             // D is M x N, contraction length K
     int bn;                  // N tile: multiple of 64 (MN-major B) or 16 (K-major B), <= 256
@@ -84,6 +86,8 @@ struct TcGemm {
                              // (single launches only; 0 or 1: whole K)
     long long part_stride;   // 0: the S parts add into a pre-zeroed D; > 0: part c is stored
                              // (not added) at D + c * part_stride, to be summed by the caller
+    int kpart;               // > 0 (stored parts only): part c covers K blocks [c kpart, (c + 1) kpart)
+                             // of every source (K-aligned); 0: parts of the sources' joint K sequence
     // e4m3 launches (TcParams::f8): scale-factor images, 512 bytes of the tile's
     // UE8M0 byte per 128 x 128 tile of the original matrix, row-major over tiles.
     const uint8_t* sfa;

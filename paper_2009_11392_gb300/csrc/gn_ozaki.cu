@@ -32,13 +32,14 @@ namespace {
 constexpr int OZ_KPASS = 1024;   // K per pass (exactness of the orders <= 3)
 constexpr int OZ_NPANEL = 256;   // least N per GEMM launch (oz_npanel bounds the FP32 outputs)
 constexpr int OZ_MAX_DIGITS = 7;
+constexpr int OZ_PGRP = 4;       // passes per group of launches (slicing, products, combination)
 
 size_t al256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
 
 // Columns of C per GEMM launch: at least 256, more while the FP32 outputs of all
-// orders stay within 64 MB (short, wide products in one launch).
-long long oz_npanel(long long M, long long N) {
-    long long np = (64LL << 20) / (4LL * OZ_MAX_DIGITS * std::max<long long>(M, 1));
+// orders and K parts stay within 64 MB (short, wide products in one launch).
+long long oz_npanel(long long M, long long N, long long parts) {
+    long long np = (64LL << 20) / (4LL * OZ_MAX_DIGITS * std::max<long long>(M, 1) * std::max<long long>(parts, 1));
     np = std::max<long long>(np, OZ_NPANEL) / 16 * 16;
     return std::min<long long>(N, np);
 }
@@ -137,9 +138,10 @@ struct OzOperand {
     const void* src;   // FP32 for operand 0 of the FP32-A instance, FP64 otherwise
     long long s_row, s_k, ldk, slice_stride;
     __nv_bfloat16* out;
-    unsigned long long* mx;
+    unsigned long long* mx;   // [passes][rows]
     int rows, K, S;
-    int clusters;   // ceil(rows / 32): one cluster of OZ_CS CTAs per 32 rows
+    int passes;     // ceil(K / OZ_KPASS): pass p is K range [p OZ_KPASS, min(K, (p + 1) OZ_KPASS))
+    int clusters;   // passes x ceil(rows / 32): one cluster of OZ_CS CTAs per pass and 32 rows
 };
 struct OzSliceArgs {
     OzOperand op[2];
@@ -167,13 +169,14 @@ __device__ __forceinline__ unsigned long long mx_word(unsigned long long m, floa
 // pairs of entries along K (8 entries per thread); the row maximum is a
 // shuffle plus an exchange between the row's four warps.
 template <typename T>
-__device__ __forceinline__ void slice_kcontig(const OzOperand& o, int q, int rank, OzSmem& sm) {
-    const T* src = static_cast<const T*>(o.src);
+__device__ __forceinline__ void slice_kcontig(const OzOperand& o, int pass, int q, int rank, OzSmem& sm) {
+    const long long koff = static_cast<long long>(pass) * OZ_KPASS;
+    const T* src = static_cast<const T*>(o.src) + koff;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r = tid >> 7, l = tid & 127;
     const long long i = static_cast<long long>(q) * 32 + rank * 4 + r;
     const bool live = i < o.rows;
-    const int K = o.K;
+    const int K = min(OZ_KPASS, o.K - pass * OZ_KPASS);
     T v[8];
     unsigned long long m = 0;
 #pragma unroll
@@ -189,10 +192,10 @@ __device__ __forceinline__ void slice_kcontig(const OzOperand& o, int q, int ran
     __syncthreads();
     m = max(max(sm.part[4 * r][0], sm.part[4 * r + 1][0]), max(sm.part[4 * r + 2][0], sm.part[4 * r + 3][0]));
     if (!live) return;   // no barrier follows in this path
-    if (l == 0) o.mx[i] = mx_word(m, static_cast<T*>(nullptr));
+    if (l == 0) o.mx[static_cast<long long>(pass) * o.rows + i] = mx_word(m, static_cast<T*>(nullptr));
     const int e = row_exponent<T>(m);
     const unsigned long long bias = digit_bias(o.S);
-    __nv_bfloat16* out = o.out + i * o.ldk;
+    __nv_bfloat16* out = o.out + i * o.ldk + koff;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int k = 2 * l + 256 * u;   // k + 1 < ldk: ldk is K rounded up to 8
@@ -205,12 +208,13 @@ __device__ __forceinline__ void slice_kcontig(const OzOperand& o, int q, int ran
 // entries per thread), the partial row maxima go through distributed shared
 // memory, and the digits are written along K after a transpose in shared memory.
 template <typename T>
-__device__ __forceinline__ void slice_strided(const OzOperand& o, int q, int rank, OzSmem& sm) {
+__device__ __forceinline__ void slice_strided(const OzOperand& o, int pass, int q, int rank, OzSmem& sm) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    const T* src = static_cast<const T*>(o.src);
+    const long long koff = static_cast<long long>(pass) * OZ_KPASS;
+    const T* src = static_cast<const T*>(o.src) + koff * o.s_k;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = o.K;
+    const int K = min(OZ_KPASS, o.K - pass * OZ_KPASS);
     const int kc = ((K + OZ_CS - 1) / OZ_CS + 7) / 8 * 8;   // <= 128, a multiple of 8
     const int k0 = rank * kc, k1 = min(K, k0 + kc);
     const long long i = static_cast<long long>(q) * 32 + lane;
@@ -236,7 +240,7 @@ __device__ __forceinline__ void slice_strided(const OzOperand& o, int q, int ran
 #pragma unroll
         for (int c = 0; c < OZ_CS; ++c) mr = max(mr, cluster.map_shared_rank(sm.lmax, c)[lane]);
         sm.rmax[lane] = mr;
-        if (rank == 0 && live) o.mx[i] = mx_word(mr, static_cast<T*>(nullptr));
+        if (rank == 0 && live) o.mx[static_cast<long long>(pass) * o.rows + i] = mx_word(mr, static_cast<T*>(nullptr));
     }
     cluster.sync();   // peers' reads of lmax done before any CTA moves on or exits
     const int e = row_exponent<T>(sm.rmax[lane]);
@@ -259,13 +263,14 @@ __device__ __forceinline__ void slice_strided(const OzOperand& o, int q, int ran
         const int ii = (tid >> 6) + 8 * j;
         const long long row = static_cast<long long>(q) * 32 + ii;
         if (row < o.rows)
-            write_digits2(sm.ys[2 * kp][ii], sm.ys[2 * kp + 1][ii], o.S, bias, o.out + row * o.ldk + k0 + 2 * kp,
+            write_digits2(sm.ys[2 * kp][ii], sm.ys[2 * kp + 1][ii], o.S, bias, o.out + row * o.ldk + koff + k0 + 2 * kp,
                           o.slice_stride);
     }
 }
 
-// Cluster q of the grid slices rows [32 q', 32 q' + 32) of operand 0 (q' = q;
-// FP32 when A32) or of operand 1 (q' = q - op[0].clusters; FP64).
+// Cluster q of the grid slices pass p, rows [32 q', 32 q' + 32) of operand 0
+// (FP32 when A32) for q < op[0].clusters, else of operand 1 (FP64), with
+// q - (operand base) = p ceil(rows / 32) + q'.
 template <bool A32>
 __global__ void __launch_bounds__(OZ_ST) oz_slice_kernel(const __grid_constant__ OzSliceArgs args) {
     __shared__ OzSmem sm;
@@ -274,12 +279,15 @@ __global__ void __launch_bounds__(OZ_ST) oz_slice_kernel(const __grid_constant__
     const int which = q < args.op[0].clusters ? 0 : 1;
     const OzOperand& o = args.op[which];
     if (which) q -= args.op[0].clusters;
+    const int rq = (o.rows + 31) / 32;
+    const int pass = q / rq;
+    q -= pass * rq;
     if (which == 0 && A32) {
-        if (o.s_k == 1) slice_kcontig<float>(o, q, rank, sm);
-        else slice_strided<float>(o, q, rank, sm);
+        if (o.s_k == 1) slice_kcontig<float>(o, pass, q, rank, sm);
+        else slice_strided<float>(o, pass, q, rank, sm);
     } else {
-        if (o.s_k == 1) slice_kcontig<double>(o, q, rank, sm);
-        else slice_strided<double>(o, q, rank, sm);
+        if (o.s_k == 1) slice_kcontig<double>(o, pass, q, rank, sm);
+        else slice_strided<double>(o, pass, q, rank, sm);
     }
 }
 
@@ -296,17 +304,18 @@ OzOperand oz_operand(const void* src, long long s_row, long long s_k, long long 
     o.ldk = ldk;
     o.slice_stride = slice_stride;
     o.mx = mx;
-    o.clusters = static_cast<int>((rows + 31) / 32);
+    o.passes = static_cast<int>((K + OZ_KPASS - 1) / OZ_KPASS);
+    o.clusters = o.passes * static_cast<int>((rows + 31) / 32);
     return o;
 }
 
-// Both operands of one pass in one launch (K <= OZ_KPASS).
+// Both operands, every pass of their K range (at most OZ_PGRP passes), in one launch.
 gn_status slice_pair(gn_handle h, const OzOperand& a, int a_f32, const OzOperand& b) {
     OzSliceArgs args;
     args.op[0] = a;
     args.op[1] = b;
     for (const OzOperand& o : args.op)
-        if ((o.s_k != 1 && o.s_row != 1) || o.K < 1 || o.K > OZ_KPASS || o.rows < 1) return GN_ERR_INVALID_ARG;
+        if ((o.s_k != 1 && o.s_row != 1) || o.K < 1 || o.passes > OZ_PGRP || o.rows < 1) return GN_ERR_INVALID_ARG;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(OZ_CS * (static_cast<long long>(a.clusters) + b.clusters)));
     cfg.blockDim = dim3(OZ_ST);
@@ -324,36 +333,43 @@ gn_status slice_pair(gn_handle h, const OzOperand& a, int a_f32, const OzOperand
     return GN_OK;
 }
 
-// C[i, j] = beta C[i, j] + alpha 2^{ea_i + eb_j} sum_o D_o[i, j].  The exact
-// orders 0..3 are summed as integers in units of 2^-35 (one rounding), the
-// rounded orders 4.. in FP32 below them.  A thread per column, rows across
-// blockIdx.y (no division per element); each exact order is an integer below
-// 2^24 units, so it converts through a 32-bit integer.
-__global__ void oz_combine_kernel(const float* __restrict__ D, long long d_stride, long long ldd, int norders,
-                                  int M, int N, const unsigned long long* __restrict__ mxa,
-                                  const unsigned long long* __restrict__ mxb, double alpha, double beta,
-                                  double* __restrict__ C, long long ldc) {
+// C[i, j] = beta C[i, j] + sum_q alpha 2^{ea_qi + eb_qj} sum_o D_qo[i, j] over
+// the K parts q (passes, each with its own row exponents), added in part
+// order with one rounding each.  Within a part the exact orders 0..3 are
+// summed as integers in units of 2^-35 (one rounding), the rounded orders 4..
+// in FP32 below them.  A thread per column, rows across blockIdx.y (no
+// division per element); each exact order is an integer below 2^24 units, so
+// it converts through a 32-bit integer.
+__global__ void oz_combine_kernel(const float* __restrict__ D, long long d_stride, long long part_stride,
+                                  long long ldd, int norders, int nparts, int M, int N,
+                                  const unsigned long long* __restrict__ mxa,
+                                  const unsigned long long* __restrict__ mxb, long long mxb_part, double alpha,
+                                  double beta, double* __restrict__ C, long long ldc) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
-    const int eb = row_exponent<double>(mxb[j]);
     const int nexact = norders < 4 ? norders : 4;
     for (int i = blockIdx.y; i < M; i += gridDim.y) {
-        const float* d = D + static_cast<long long>(i) * ldd + j;
-        long long acc = 0;
-        for (int o = 0; o < nexact; ++o)   // D_o is an integer number of units 2^{-7(o+2)}
-            acc += static_cast<long long>(__float2int_rn(d[o * d_stride] * __int_as_float((127 + 7 * (o + 2)) << 23)))
-                   << (7 * (3 - o));
-        float low = 0.0f;
-        for (int o = norders - 1; o >= 4; --o) low += d[o * d_stride];
-        // times 2^(ea + eb - 35): a power of two built from its bits when normal
-        const int ea = row_exponent<double>(mxa[i]);
-        const int p = ea + eb - 35;
-        const double x = fma(static_cast<double>(low), 34359738368.0, static_cast<double>(acc));
-        const double v = (p >= -1022 && p <= 1023)
-                             ? x * (alpha * __longlong_as_double(static_cast<long long>(p + 1023) << 52))
-                             : alpha * ldexp(x, p);
         double* c = C + static_cast<long long>(i) * ldc + j;
-        *c = beta == 0.0 ? v : fma(beta, *c, v);
+        double out = 0.0;
+        for (int q = 0; q < nparts; ++q) {   // K parts (passes) in order, as separate passes would add them
+            const float* d = D + q * part_stride + static_cast<long long>(i) * ldd + j;
+            long long acc = 0;
+            for (int o = 0; o < nexact; ++o)   // D_o is an integer number of units 2^{-7(o+2)}
+                acc += static_cast<long long>(__float2int_rn(d[o * d_stride] * __int_as_float((127 + 7 * (o + 2)) << 23)))
+                       << (7 * (3 - o));
+            float low = 0.0f;
+            for (int o = norders - 1; o >= 4; --o) low += d[o * d_stride];
+            // times 2^(ea + eb - 35): a power of two built from its bits when normal
+            const int ea = row_exponent<double>(mxa[static_cast<long long>(q) * M + i]);
+            const int eb = row_exponent<double>(mxb[q * mxb_part + j]);
+            const int p = ea + eb - 35;
+            const double x = fma(static_cast<double>(low), 34359738368.0, static_cast<double>(acc));
+            const double v = (p >= -1022 && p <= 1023)
+                                 ? x * (alpha * __longlong_as_double(static_cast<long long>(p + 1023) << 52))
+                                 : alpha * ldexp(x, p);
+            out = q ? out + v : (beta == 0.0 ? v : fma(beta, *c, v));
+        }
+        *c = out;
     }
 }
 
@@ -364,9 +380,13 @@ struct OzWs {
     long long ldk, ldd;
 };
 
+// K per group of passes, its passes, and the workspace carve for them.
+long long oz_kgroup(long long K) { return std::min<long long>(std::max<long long>(K, 1), OZ_PGRP * OZ_KPASS); }
+long long oz_parts(long long kg) { return (kg + OZ_KPASS - 1) / OZ_KPASS; }
+
 bool oz_carve(long long M, long long N, long long K, int sa, int sb, void* ws, size_t ws_bytes, OzWs* o) {
-    const long long kp = std::min<long long>(K, OZ_KPASS), np = oz_npanel(M, N);
-    o->ldk = r8(kp);
+    const long long kg = oz_kgroup(K), S = oz_parts(kg), np = oz_npanel(M, N, S);
+    o->ldk = r8(kg);
     o->ldd = r4(np);
     char* p = static_cast<char*>(ws);
     size_t off = 0;
@@ -377,9 +397,9 @@ bool oz_carve(long long M, long long N, long long K, int sa, int sb, void* ws, s
     };
     o->as = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * sa * M * o->ldk));
     o->bs = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * sb * N * o->ldk));
-    o->d = reinterpret_cast<float*>(take(sizeof(float) * OZ_MAX_DIGITS * M * o->ldd));
-    o->mxa = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * M));
-    o->mxb = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * N));
+    o->d = reinterpret_cast<float*>(take(sizeof(float) * S * OZ_MAX_DIGITS * M * o->ldd));
+    o->mxa = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * S * M));
+    o->mxb = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * S * N));
     return off <= ws_bytes;
 }
 
@@ -388,10 +408,14 @@ bool oz_carve(long long M, long long N, long long K, int sa, int sb, void* ws, s
 size_t oz_ws_bytes(long long M, long long N, long long K, int a_f32) {
     (void)a_f32;
     const int sa = OZ_MAX_DIGITS, sb = OZ_MAX_DIGITS;
-    const long long kp = std::min<long long>(std::max<long long>(K, 1), OZ_KPASS);
-    const long long np = oz_npanel(M, std::max<long long>(N, 1));
-    return al256(sizeof(__nv_bfloat16) * sa * M * r8(kp)) + al256(sizeof(__nv_bfloat16) * sb * N * r8(kp)) +
-           al256(sizeof(float) * OZ_MAX_DIGITS * M * r4(np)) + al256(8 * M) + al256(8 * N) + 256;
+    const long long kg = oz_kgroup(K), S = oz_parts(kg);
+    // the FP32 outputs of s parts at the panel for s parts, largest over s <= S:
+    // the panel narrows as the parts grow, and the size must not shrink with K
+    size_t d = 0;
+    for (long long s = 1; s <= S; ++s)
+        d = std::max(d, al256(sizeof(float) * s * OZ_MAX_DIGITS * M * r4(oz_npanel(M, std::max<long long>(N, 1), s))));
+    return al256(sizeof(__nv_bfloat16) * sa * M * r8(kg)) + al256(sizeof(__nv_bfloat16) * sb * N * r8(kg)) + d +
+           al256(8 * S * M) + al256(8 * S * N) + 256;
 }
 
 gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double alpha, const void* A, int a_f32,
@@ -419,9 +443,15 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
     // every order 0 .. omax has the pair (0, ord): no order is empty
     if (norders > TC_MAX_GEMMS || sa + sb > TC_MAX_MAPS || npairs[omax] > TC_MAX_SRC) return GN_ERR_UNSUPPORTED;
     const long long as_stride = M * o.ldk, bs_stride = N * o.ldk, d_stride = M * o.ldd;
-    for (long long k0 = 0; k0 < K; k0 += OZ_KPASS) {
-        const long long kc = std::min<long long>(OZ_KPASS, K - k0);
-        // A rows (i over M, k along the pass) and B "rows" (j over N)
+    // groups of at most OZ_PGRP passes: one slicing launch for all of them, the
+    // passes as K-aligned parts of one multi-GEMM launch (stored apart), one
+    // combination adding them in order
+    const long long part_stride = OZ_MAX_DIGITS * d_stride;
+    const long long npanel = oz_npanel(M, N, oz_parts(oz_kgroup(K)));   // the carve's panel (largest group)
+    for (long long k0 = 0; k0 < K; k0 += OZ_PGRP * OZ_KPASS) {
+        const long long kc = std::min<long long>(OZ_PGRP * OZ_KPASS, K - k0);
+        const int S = static_cast<int>(oz_parts(kc));
+        // A rows (i over M, k along the group) and B "rows" (j over N)
         const long long a_row = ta ? 1 : lda, a_k = ta ? lda : 1;
         const long long a_off = ta ? k0 * lda : k0;
         const long long b_row = tb ? ldb : 1, b_k = tb ? 1 : ldb;
@@ -431,14 +461,13 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
                           oz_operand(static_cast<const char*>(A) + esz * a_off, a_row, a_k, M, kc, sa, o.as, o.ldk,
                                      as_stride, o.mxa),
                           a_f32, oz_operand(B + b_off, b_row, b_k, N, kc, sb, o.bs, o.ldk, bs_stride, o.mxb)));
-        const double beta_pass = k0 == 0 ? beta : 1.0;
-        const long long npanel = oz_npanel(M, N);
+        const double beta_grp = k0 == 0 ? beta : 1.0;
         for (long long j0 = 0; j0 < N; j0 += npanel) {
             const long long nb = std::min<long long>(npanel, N - j0);
             // N tile: the widest of 256 / 128 / 64 that still gives the GPU about
-            // two tiles per SM over the orders (small products are latency-bound)
+            // two work items per SM over the orders and parts (small products are latency-bound)
             int bn = static_cast<int>(std::min<long long>(256, (nb + 31) / 32 * 32));
-            while (bn > 64 && ((M + 127) / 128) * ((nb + bn - 1) / bn) * norders < 2LL * h->sm_count)
+            while (bn > 64 && ((M + 127) / 128) * ((nb + bn - 1) / bn) * norders * S < 2LL * h->sm_count)
                 bn = (bn / 2 + 31) / 32 * 32;
             TcParams p;
             memset(&p, 0, sizeof(p));
@@ -466,6 +495,11 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
                 }
                 g.D = o.d + ord * d_stride;
                 g.ldd = o.ldd;
+                if (S >= 2) {   // pass q of the group: its own row scaling, stored at D + q part_stride
+                    g.ksplit = S;
+                    g.part_stride = part_stride;
+                    g.kpart = OZ_KPASS / TC_BK;
+                }
             }
             p.ngemm = norders;
             // orders of 7, 6, ..., 1 slice products: the boustrophedon order on
@@ -476,8 +510,8 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
             const unsigned gy = static_cast<unsigned>(
                 std::max<long long>(1, std::min<long long>(M, static_cast<long long>(h->sm_count) * 16 / gx)));
             oz_combine_kernel<<<dim3(gx, gy), 256, 0, h->stream>>>(
-                o.d, d_stride, o.ldd, norders, static_cast<int>(M), static_cast<int>(nb), o.mxa, o.mxb + j0,
-                alpha, beta_pass, C + j0, ldc);
+                o.d, d_stride, part_stride, o.ldd, norders, S, static_cast<int>(M), static_cast<int>(nb), o.mxa,
+                o.mxb + j0, N, alpha, beta_grp, C + j0, ldc);
             count_launch();
             GN_CUDA_TRY(cudaGetLastError());
         }

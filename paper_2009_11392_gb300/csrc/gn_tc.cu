@@ -29,7 +29,7 @@ namespace gn {
 namespace {
 
 constexpr int BM = 128;                          // M of one tcgen05 MMA
-constexpr int BK = 64;                           // K per stage: 64 bf16 = one 128B swizzle row
+constexpr int BK = TC_BK;                        // K per stage: 64 bf16 = one 128B swizzle row
 constexpr int B_STAGE_BYTES = 256 * BK * 2;      // 32 KB (bn <= 256)
 constexpr int TMEM_COLS = 512;
 constexpr int NUM_THREADS = 192;
@@ -302,6 +302,31 @@ __device__ __forceinline__ TileCoord decode_tile(const TcParams& p, int t) {
     return c;
 }
 
+// K blocks of one work item: sequence positions [kb0, kb1), position j being
+// K block kk0 + j % nk of source j / nk.  Whole tiles and parts of the joint
+// sequence (ksplit without kpart) have nk = kblocks, kk0 = 0; a K-aligned part
+// runs its K range for every source.
+struct KRange {
+    int kb0, kb1, nk, kk0;
+};
+__device__ __forceinline__ KRange k_range(const TcGemm& G, int half) {
+    KRange r;
+    if (half && G.kpart > 0) {
+        r.kk0 = (half - 1) * G.kpart;
+        r.nk = min(G.kpart, G.kblocks - r.kk0);
+        r.kb0 = 0;
+        r.kb1 = G.nsrc * r.nk;
+    } else {
+        const int nkb = G.nsrc * G.kblocks;
+        const int S = G.ksplit >= 2 ? G.ksplit : 2;
+        r.kb0 = half ? (half - 1) * nkb / S : 0;
+        r.kb1 = half ? half * nkb / S : nkb;
+        r.nk = G.kblocks;
+        r.kk0 = 0;
+    }
+    return r;
+}
+
 // Tile of round k for CTA cid (boustrophedon order when snake).  Once a CTA's
 // tile is past the end, so are all its later ones.
 __device__ __forceinline__ int sched_tile(int k, int cid, int ncl, int snake) {
@@ -382,18 +407,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             for (int k = 0, t = sched_tile(0, cid, ncl, p.snake); t < p.total_tiles && ok; t = sched_tile(++k, cid, ncl, p.snake)) {
                 const TileCoord c = decode_tile<GROUPED>(p, t);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
-                const int nkb = G.nsrc * G.kblocks;
-                const int S = G.ksplit >= 2 ? G.ksplit : 2;
-                const int kb0 = c.half ? (c.half - 1) * nkb / S : 0, kb1 = c.half ? c.half * nkb / S : nkb;
+                const KRange kr = k_range(G, c.half);
                 const uint32_t bytes = A_STAGE_BYTES + G.bn * BK * 2 + K::SF_STAGE;
-                for (int kb = kb0; kb < kb1; ++kb) {
+                for (int kb = kr.kb0; kb < kr.kb1; ++kb) {
                     if (!mbar_wait(empty_bar(stage), ephase ^ 1u, limit, abort_flag)) {
                         latch(p.status, GN_ERR_TIMEOUT, 1, abort_flag);
                         ok = false;
                         break;
                     }
-                    const int src = kb / G.kblocks;
-                    const int kk = kb - src * G.kblocks;
+                    const int src = kb / kr.nk;
+                    const int kk = kr.kk0 + (kb - src * kr.nk);
                     const CUtensorMap* ma = map_of<GROUPED>(p, G.a_map[src]);
                     const CUtensorMap* mb = map_of<GROUPED>(p, G.b_map[src]);
                     if (GROUPED && kk == 0) {   // maps written to device memory before the launch
@@ -464,9 +487,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_multigemm_kernel(const __gr
             for (int k = 0, t = sched_tile(0, cid, ncl, p.snake); t < p.total_tiles && ok; t = sched_tile(++k, cid, ncl, p.snake)) {
                 const TileCoord c = decode_tile<GROUPED>(p, t);
                 const TcGemm& G = *gemm_of<GROUPED>(p, c.g);
-                const int nkb = G.nsrc * G.kblocks;
-                const int S = G.ksplit >= 2 ? G.ksplit : 2;
-                const int kb0 = c.half ? (c.half - 1) * nkb / S : 0, kb1 = c.half ? c.half * nkb / S : nkb;
+                const KRange kr = k_range(G, c.half);
+                const int kb0 = kr.kb0, kb1 = kr.kb1;
                 const uint32_t idesc = F8 ? 0u : instr_desc_bf16(BM, G.bn, G.a_mn, G.b_mn);
                 if (!mbar_wait(tempty_bar(acc), aphase ^ 1u, limit, abort_flag)) {
                     latch(p.status, GN_ERR_TIMEOUT, 3, abort_flag);
@@ -722,7 +744,7 @@ gn_status tc_launch(gn_handle h, TcParams* p) {
     p->split_base = 0;
     p->nsplit = 0;
     p->snake = p->snake_groups > 0 ? 1 : 0;
-    p->max_ctas = p->snake ? p->snake_groups * p->g[0].tiles_m * p->g[0].tiles_n : 0;
+    p->max_ctas = p->snake ? p->snake_groups * p->g[0].tiles_m * p->g[0].tiles_n * std::max(1, p->g[0].ksplit) : 0;
     if (!p->f8 && !p->snake && total > 0) {
         const int ncl = std::min(total, h->sm_count);
         const int R = total % ncl;
