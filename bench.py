@@ -67,7 +67,8 @@ def parse():
     ap.add_argument("--prio", type=int, default=0,
                     help="stream priority of the approximations' streams (0 default, -1 high)")
     ap.add_argument("--h2d-streams", type=int, default=1, help="host-to-device copy streams of the e2e loop")
-    ap.add_argument("--e2e-sets", type=int, default=0, help="device buffer sets of the e2e loop (0: in-flight + 1)")
+    ap.add_argument("--e2e-sets", type=int, default=0, help="device buffer sets of the e2e loop (0: in-flight + ahead)")
+    ap.add_argument("--e2e-ahead", type=int, default=2, help="steps whose input copies are queued ahead in the e2e loop")
     ap.add_argument("--only", default=None, choices=["batched", "adjoint", "fp64_cases"],
                     help="run one side measurement alone and print its JSON (for profiling it)")
     return ap.parse_args()
@@ -489,10 +490,11 @@ def main():
 def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, bufs, eps, mode):
     """End to end through the API with host buffers: every step copies its own
     inputs in from pinned host memory and its results (AX, Y^T A, Q, R) out.
-    nf + 1 device buffer sets; the copies run on two host-to-device streams
-    (large inputs in row halves) and one device-to-host stream while the steps
-    compute on the nf handles."""
-    nset = a.e2e_sets if a.e2e_sets > nf else nf + 1
+    nf + ahead device buffer sets; the input copies of the next `ahead` steps
+    are queued on the host-to-device stream(s) and the results go out on one
+    device-to-host stream while the steps compute on the nf handles."""
+    ahead = max(1, a.e2e_ahead)
+    nset = max(a.e2e_sets, nf + ahead)   # a set's previous step is complete before its next copy is queued
     if a.op == "e4m3":
         srcs = [Aop.data, Aop.data_t, Xop.data_t, Yop.data_t, Aop.scale, Xop.scale, Yop.scale]
         hosts = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in srcs]
@@ -568,15 +570,16 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
         ev_out[b].record(dstream)
 
     def run(k):
-        # the next step's copies are queued before the host waits on an older
-        # step: their buffer set was released by step i + 1 - nset, whose
-        # done-event the previous iteration recorded
+        # the copies of step i + ahead are queued before the host waits on an
+        # older step: their buffer set was released by step i + ahead - nset
+        # <= i - nf, whose done-event an earlier iteration recorded
         lag = nf - 1
-        prefetch(0)
+        for i in range(min(ahead, k)):
+            prefetch(i)
         for i in range(k):
             enqueue(i)
-            if i + 1 < k:
-                prefetch(i + 1)
+            if i + ahead < k:
+                prefetch(i + ahead)
             if i - lag >= 0:
                 complete(i - lag)
         for i in range(max(0, k - lag), k):
@@ -613,7 +616,7 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
     torch.cuda.empty_cache()
     return {"value": 1e3 / ms, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": ms, "h2d_gbs_one_stream": h2d_gbs, "d2h_gbs_one_stream": d2h_gbs,
-            "h2d_streams": nh, "buffer_sets": nset,
+            "h2d_streams": nh, "buffer_sets": nset, "ahead": ahead,
             "copy_floor_ms": max(h2d / h2d_gbs, d2h / d2h_gbs) / 1e6}
 
 
