@@ -118,6 +118,35 @@ def test_dgemm_tc_accuracy_general(gn, H):
     assert np.max(err / scale) <= 1e-13
 
 
+@pytest.mark.parametrize("K,ta,a32", [(9000, False, False), (5000, True, True)])
+def test_dgemm_tc_groups_of_passes(gn, H, K, ta, a32):
+    """K beyond one group of four 1024-element passes: the groups run one after
+    another, beta applies to the first only and alpha to every pass.  Against an
+    extended-precision reference of alpha op(A) B + beta C0, within 2^-44 K
+    max|a_i.| max|b_.j| |alpha| plus one rounding per pass of the partial sums."""
+    M, N = 96, 70
+    alpha, beta = -1.5, 0.75
+    rng = np.random.default_rng(K)
+    A = rng.standard_normal((M, K)) * np.exp2(rng.uniform(-8, 8, M))[:, None]
+    if a32:
+        A = A.astype(np.float32).astype(np.float64)
+    B = rng.standard_normal((K, N)) * np.exp2(rng.uniform(-8, 8, N))[None, :]
+    C0 = rng.standard_normal((M, N))
+    ref = alpha * (A.astype(np.longdouble) @ B.astype(np.longdouble)) + beta * C0.astype(np.longdouble)
+    An = np.ascontiguousarray(A.T if ta else A)
+    At = torch.from_numpy(An.astype(np.float32) if a32 else An).cuda()
+    C = torch.from_numpy(C0.copy()).cuda()
+    H.dgemm_tc(At, torch.from_numpy(B).cuda(), C, alpha=alpha, beta=beta, ta=ta)
+    assert H.sync_status() == 0
+    err = np.abs(npy(C) - ref).astype(np.float64)
+    # the passes' FP64 additions round against their partial sums (at most one per pass)
+    passes = -(-K // 1024)
+    scale = np.abs(beta * C0) + abs(alpha) * (np.abs(A) @ np.abs(B))
+    bound = (2.0 ** -44 * K * abs(alpha) * np.abs(A).max(1)[:, None] * np.abs(B).max(0)[None, :]
+             + (passes + 1) * 2.0 ** -53 * scale)
+    assert np.all(err <= bound)
+
+
 def _mixed_factors(gn, H, A, X, Y, eps, mode, tc):
     m, n = A.shape
     r, l = X.shape[1], Y.shape[1] - X.shape[1]
