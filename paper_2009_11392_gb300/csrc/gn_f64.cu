@@ -2069,6 +2069,31 @@ namespace {
 // Q_s <- Q_s - V_b T_b (V_b^T Q_s), with G_b = V_b^T V_b, V_b^T Q_s, T_b (.) and the
 // update on the tensor cores (oz_dgemm, FP64 accuracy); T_b from G_b by
 // ut_inverse.
+// Z[c][j] = V[j][c] for c, j < nb.  When block b's reflectors are applied to Q
+// (from the last block back), Q's columns j0 .. j0 + nb - 1 below row j0 are
+// still [I; 0], so that part of V_b^T Q is the transpose of V_b's top nb rows:
+// copied, not multiplied.
+__global__ void vtop_t_kernel(const double* __restrict__ V, long long ldv, int nb, double* __restrict__ Z,
+                              long long ldz) {
+    const int total = nb * nb;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int c = e / nb, j = e - c * nb;
+        Z[c * ldz + j] = V[j * ldv + c];
+    }
+}
+
+// Z (nb x Nq, ld Nq) = V_b^T Q_s for the block of reflectors at column j0: the
+// first nb columns by the copy above, the rest as a digit-sliced product.
+gn_status block_vtq(gn_handle h, const double* Vb, long long ldv, long long Mp, long long nbb, const double* Qs,
+                    long long ldq, long long Nq, double* Z, void* oz, size_t oz_bytes) {
+    vtop_t_kernel<<<ew_blocks(h, nbb * nbb), 256, 0, h->stream>>>(Vb, ldv, static_cast<int>(nbb), Z, Nq);
+    count_launch();
+    GN_CUDA_TRY(cudaGetLastError());
+    if (Nq > nbb)
+        GN_TRY(oz_dgemm(h, nbb, Nq - nbb, Mp, 1.0, Vb, 0, ldv, 1, Qs + nbb, ldq, 0, 0.0, Z + nbb, Nq, oz, oz_bytes));
+    return GN_OK;
+}
+
 gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double* Q, long long ldq, void* oz,
                     size_t oz_bytes) {
     static_assert(QR_BB == QR_SB, "the blocked factorization's T_b serve the Q formation's blocks");
@@ -2089,8 +2114,7 @@ gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double
                 launch_ut_inverse(h, bk.GB, QR_BB, q.tau + j0, static_cast<int>(nbb), Tb, QR_BB);
                 GN_CUDA_TRY(cudaGetLastError());
             }
-            GN_TRY(oz_dgemm(h, nbb, Nq, Mp, 1.0, Vb, 0, N, 1, Qs, ldq, 0, 0.0, bk.Z1s, Nq, bk.oz_side,
-                            bk.oz_side_bytes));
+            GN_TRY(block_vtq(h, Vb, N, Mp, nbb, Qs, ldq, Nq, bk.Z1s, bk.oz_side, bk.oz_side_bytes));
             GN_TRY(oz_dgemm(h, nbb, Nq, nbb, 1.0, Tb, 0, QR_BB, 0, bk.Z1s, Nq, 0, 0.0, bk.Z2s, Nq, bk.oz_side,
                             bk.oz_side_bytes));
             GN_TRY(oz_dgemm(h, Mp, Nq, nbb, -1.0, Vb, 0, N, 0, bk.Z2s, Nq, 0, 1.0, Qs, ldq, bk.oz_side,
@@ -2117,7 +2141,7 @@ gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double
         GN_TRY(oz_dgemm(h, nbb, nbb, Mp, 1.0, Vb, 0, N, 1, Vb, N, 0, 0.0, G, QR_SB, ozw, ozw_bytes));
         launch_ut_inverse(h, G, QR_SB, q.tau + j0, static_cast<int>(nbb), Tb, QR_SB);
         GN_CUDA_TRY(cudaGetLastError());
-        GN_TRY(oz_dgemm(h, nbb, Nq, Mp, 1.0, Vb, 0, N, 1, Qs, ldq, 0, 0.0, Wb, Nq, ozw, ozw_bytes));
+        GN_TRY(block_vtq(h, Vb, N, Mp, nbb, Qs, ldq, Nq, Wb, ozw, ozw_bytes));
         GN_TRY(oz_dgemm(h, nbb, Nq, nbb, 1.0, Tb, 0, QR_SB, 0, Wb, Nq, 0, 0.0, Wb2, Nq, ozw, ozw_bytes));
         GN_TRY(oz_dgemm(h, Mp, Nq, nbb, -1.0, Vb, 0, N, 0, Wb2, Nq, 0, 1.0, Qs, ldq, ozw, ozw_bytes));
     }
