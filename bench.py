@@ -1150,7 +1150,9 @@ def r2000_measurement(gn, H, stream, dev, a, A64, Ab, eps, mode, r=2000):
 def adjoint_measurement(gn, H, stream, dev, m=4096, n=4096, r=256, l=128):
     """Forward (dense A_hat) and hand-written adjoint of <G, A_hat> on the
     4096 x 4096 FP32 case (sigma_i = i^-1.5 over 1024 modes + 1e-6 noise,
-    r = 256, l = 128), each timed with CUDA events (best of 3 after a warm-up)."""
+    r = 256, l = 128), each timed with CUDA events (best of 3 after a warm-up):
+    the standalone backward, the backward from the forward's front, and forward
+    plus that backward as one step."""
     p, G = gn_synth.config4(device=dev, m=m, n=n, r=r, l=l, dtype=torch.float32)
     A, X, Y = p.a, p.x, p.y
     ws = H.backward_workspace(m, n, r, l, gn.F32)
@@ -1158,8 +1160,17 @@ def adjoint_measurement(gn, H, stream, dev, m=4096, n=4096, r=256, l=128):
     dA = torch.empty_like(A)
     fwd = _best_ms(lambda: H.forward_dense(A, X, Y, Ah, ws), 4, stream)
     bwd = _best_ms(lambda: H.backward(A, X, Y, G, dA, ws), 4, stream)
+    # the backward from the front the forward leaves in ws (as autograd runs it)
+    H.forward_dense(A, X, Y, Ah, ws)
+    bwd_saved = _best_ms(lambda: H.backward_saved(X, Y, G, dA, ws), 4, stream)
+
+    def step():
+        H.forward_dense(A, X, Y, Ah, ws)
+        H.backward_saved(X, Y, G, dA, ws)
+
+    fwd_bwd = _best_ms(step, 4, stream)
     return {"workload": f"{m}x{n} FP32, r={r}, l={l}, loss <G, A_hat>", "fwd_ms": fwd, "bwd_ms": bwd,
-            "grad_norm": float(dA.norm().item())}
+            "bwd_saved_ms": bwd_saved, "fwd_bwd_saved_ms": fwd_bwd, "grad_norm": float(dA.norm().item())}
 
 
 def batched_measurement(gn, H, stream, dev, count=512, steps=10):

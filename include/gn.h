@@ -492,16 +492,31 @@ gn_status gn_backward_workspace_size(int64_t m, int64_t n, int64_t r, int64_t l,
  * paper does not differentiate GN).  The core's pseudoinverse is never formed.
  * A, X, Y, Gup, dA share one dtype: GN_F64 (every step in FP64) or GN_F32
  * (the m x n contractions in FP32, the r-sized algebra in FP64).  A: m x n,
- * X: n x r, Y: m x (r+l), Gup, dA: m x n (dA overwritten).  The sketches are
- * recomputed from A (nothing is kept from a forward pass). */
+ * X: n x r, Y: m x (r+l), Gup, dA: m x n (dA overwritten).  The sketches,
+ * C = QR and F are formed from A in ws (the "front") and left there for
+ * gn_backward_saved.  FP32: data 16-byte aligned, ld a multiple of 4 (dA
+ * exempt from the ld rule); GN_ERR_ALIGNMENT otherwise. */
 gn_status gn_backward(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,
                       const gn_mat* Gup, gn_mat* dA, void* ws, size_t ws_bytes);
 
 /* The dense approximant A_hat = F G (m x n) of plain GN in the dtype of A
  * (GN_F64 or GN_F32, same precision split as gn_backward); the forward value
- * of the differentiable map whose adjoint gn_backward computes. */
+ * of the differentiable map whose adjoint gn_backward computes.  Forms the
+ * same front in ws as gn_backward and leaves it there. */
 gn_status gn_forward_dense(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y,
                            gn_mat* Ahat, void* ws, size_t ws_bytes);
+
+/* gn_backward from the front that the handle's last gn_forward_dense or
+ * gn_backward call left in ws (what an autograd forward saves for its
+ * backward): the same dA, without the sketches, the core's QR and F.  A is not
+ * read.  X, Y must be the matrices of that call (same pointers and leading
+ * dimensions), Gup and dA m x n in its dtype, ws and ws_bytes the same, and
+ * ws untouched since; the handle keeps one such record (a later
+ * gn_forward_dense or gn_backward replaces it).  GN_ERR_INVALID_ARG when the
+ * record does not match (checked on the host); may be called again with
+ * another Gup.  Asynchronous on the handle's stream. */
+gn_status gn_backward_saved(gn_handle h, const gn_mat* X, const gn_mat* Y, const gn_mat* Gup,
+                            gn_mat* dA, void* ws, size_t ws_bytes);
 
 /* ---------------------------------------------------------------- batched */
 

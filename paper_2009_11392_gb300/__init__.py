@@ -40,7 +40,7 @@ ABI_SYMBOLS = (
     "gn_status_string", "gn_device_sm_count", "gn_workspace_size", "gn_quantize",
     "gn_sketch", "gn_core", "gn_factors", "gn_approx", "gn_error_fro2", "gn_hmt",
     "gn_kernel_launches", "gn_error_fro2_noalloc", "gn_backward_workspace_size", "gn_backward",
-    "gn_forward_dense", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
+    "gn_forward_dense", "gn_backward_saved", "gn_batched_workspace_size", "gn_batched_prepare", "gn_batched_run",
     "gn_batched_set_policy", "gn_batched_tune", "gn_set_fp64_tc", "gn_dgemm_tc_workspace_size", "gn_dgemm_tc",
     "gn_apply_workspace_size", "gn_apply", "gn_update_workspace_size", "gn_update", "gn_resample",
     "gn_append_rows", "gn_append_cols", "gn_resample_workspace_size", "gn_core_finish",
@@ -126,6 +126,7 @@ def _load():
         "gn_backward_workspace_size": ([I64, I64, I64, I64, I32, ctypes.POINTER(SZ)], I32),
         "gn_backward": ([P, M, M, M, M, M, P, SZ], I32),
         "gn_forward_dense": ([P, M, M, M, M, P, SZ], I32),
+        "gn_backward_saved": ([P, M, M, M, M, P, SZ], I32),
         "gn_batched_workspace_size": ([I32, ctypes.POINTER(GnProblem), ctypes.POINTER(SZ)], I32),
         "gn_batched_prepare": ([P, I32, ctypes.POINTER(GnProblem), P, SZ], I32),
         "gn_batched_run": ([P, D, I32, P, SZ], I32),
@@ -289,6 +290,7 @@ class Handle:
         h = ctypes.c_void_p()
         _check(lib.gn_create(ctypes.byref(h), ctypes.c_void_p(self.stream.cuda_stream)), "gn_create")
         self._h = h
+        self.front_calls = 0   # gn_forward_dense / gn_backward calls (each leaves a front in its ws)
 
     @property
     def h(self):
@@ -526,14 +528,22 @@ class Handle:
         return torch.empty(int(b.value), dtype=torch.uint8, device="cuda")
 
     def backward(self, A, X, Y, Gup, dA, ws):
+        self.front_calls += 1
         _check(lib.gn_backward(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
                                ctypes.byref(mat(Gup)), ctypes.byref(mat(dA)), ctypes.c_void_p(ws.data_ptr()),
                                ws.numel()), "gn_backward")
 
     def forward_dense(self, A, X, Y, Ahat, ws):
+        self.front_calls += 1
         _check(lib.gn_forward_dense(self._h, ctypes.byref(mat(A)), ctypes.byref(mat(X)), ctypes.byref(mat(Y)),
                                     ctypes.byref(mat(Ahat)), ctypes.c_void_p(ws.data_ptr()), ws.numel()),
                "gn_forward_dense")
+
+    def backward_saved(self, X, Y, Gup, dA, ws):
+        """gn_backward from the front the last forward_dense / backward left in ws."""
+        _check(lib.gn_backward_saved(self._h, ctypes.byref(mat(X)), ctypes.byref(mat(Y)), ctypes.byref(mat(Gup)),
+                                     ctypes.byref(mat(dA)), ctypes.c_void_p(ws.data_ptr()), ws.numel()),
+               "gn_backward_saved")
 
     # ------------------------------------------------------------ batched
     def batched_prepare(self, problems):
@@ -630,9 +640,10 @@ _DT = {torch.float64: F64, torch.float32: F32}
 
 class GNApprox(torch.autograd.Function):
     """A -> A_hat = (AX)(Y^T A X)^+(Y^T A) (plain GN) with X, Y fixed, as a
-    differentiable torch op.  forward: gn_forward_dense; backward: gn_backward
-    (the hand-written adjoint), which recomputes the sketches from A instead of
-    keeping them from the forward pass."""
+    differentiable torch op.  forward: gn_forward_dense, whose workspace keeps
+    the sketches, the core's QR and F; backward: gn_backward_saved from them when
+    no other forward_dense / backward ran on the handle since (the handle keeps
+    one front), else gn_backward, which forms them again from A."""
 
     @staticmethod
     def forward(ctx, A, X, Y, handle):
@@ -643,6 +654,8 @@ class GNApprox(torch.autograd.Function):
         handle.forward_dense(A, X, Y, Ahat, ws)
         ctx.save_for_backward(A, X, Y)
         ctx.handle = handle
+        ctx.ws = ws
+        ctx.front = handle.front_calls
         return Ahat
 
     @staticmethod
@@ -650,9 +663,13 @@ class GNApprox(torch.autograd.Function):
         A, X, Y = ctx.saved_tensors
         m, n = A.shape
         r, l = X.shape[1], Y.shape[1] - X.shape[1]
-        ws = ctx.handle.backward_workspace(m, n, r, l, _DT[A.dtype])
         dA = torch.empty_like(A)
-        ctx.handle.backward(A, X, Y, grad.contiguous(), dA, ws)
+        if ctx.handle.front_calls == ctx.front:
+            ctx.handle.backward_saved(X, Y, grad.contiguous(), dA, ctx.ws)
+        else:
+            ws = ctx.handle.backward_workspace(m, n, r, l, _DT[A.dtype])
+            ctx.handle.backward(A, X, Y, grad.contiguous(), dA, ws)
+        ctx.ws = None
         return dA, None, None, None
 
 

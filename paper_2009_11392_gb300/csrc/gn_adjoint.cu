@@ -18,8 +18,10 @@
 // (P, Q S2 and the two rank-r products that form the gradient) as three-slice
 // BF16 products (x = s0 + s1 + s2, the six slice products of order <= 2, FP32
 // accumulation: FP32-level accuracy).  With K R^T = (I - Q Q^T) W^T - Q W Q,
-// the two m x r terms share one solve: P = (S1 Q + Y (K R^T)) R^{-T}.  Sketches
-// are recomputed from A in every call (nothing is kept from a forward pass).
+// the two m x r terms share one solve: P = (S1 Q + Y (K R^T)) R^{-T}.
+// gn_forward_dense and gn_backward form the shared front (the sketches, C's QR
+// and F) in the workspace and leave it there; gn_backward_saved starts from it,
+// as an autograd backward starts from what its forward saved.
 #include "gn_internal.cuh"
 
 #include <algorithm>
@@ -27,96 +29,6 @@
 
 namespace gn {
 namespace {
-
-// ---------------------------------------------------------------- FP32 GEMM
-constexpr int ST = 128;   // tile (M and N)
-constexpr int SK = 8;     // K step
-constexpr int STHREADS = 256;
-
-// C = alpha op(A) op(B) + beta C, FP32, 128 x 128 tiles, 256 threads as 16 x 16,
-// each an 8 x 8 block of outputs at rows ty + 16 i, columns tx + 16 j.
-__global__ void __launch_bounds__(STHREADS) sgemm_kernel(int M, int N, int K, float alpha,
-                                                        const float* __restrict__ A, long long lda, int ta,
-                                                        const float* __restrict__ B, long long ldb, int tb,
-                                                        float beta, float* C, long long ldc) {
-    __shared__ float As[SK][ST + 4];
-    __shared__ float Bs[SK][ST + 4];
-    const int m0 = blockIdx.y * ST, n0 = blockIdx.x * ST;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += SK) {
-#pragma unroll
-        for (int e = threadIdx.x; e < ST * SK; e += STHREADS) {
-            int mm, kk;
-            if (ta) { mm = e & (ST - 1); kk = e >> 7; } else { kk = e & (SK - 1); mm = e >> 3; }
-            const int gm = m0 + mm, gk = k0 + kk;
-            float v = 0.f;
-            if (gm < M && gk < K)
-                v = ta ? A[static_cast<long long>(gk) * lda + gm] : A[static_cast<long long>(gm) * lda + gk];
-            As[kk][mm] = v;
-        }
-#pragma unroll
-        for (int e = threadIdx.x; e < ST * SK; e += STHREADS) {
-            int nn, kk;
-            if (tb) { kk = e & (SK - 1); nn = e >> 3; } else { nn = e & (ST - 1); kk = e >> 7; }
-            const int gn_ = n0 + nn, gk = k0 + kk;
-            float v = 0.f;
-            if (gn_ < N && gk < K)
-                v = tb ? B[static_cast<long long>(gn_) * ldb + gk] : B[static_cast<long long>(gk) * ldb + gn_];
-            Bs[kk][nn] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < SK; ++kk) {
-            float a[8], b[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int gm = m0 + ty + 16 * i, gn_ = n0 + tx + 16 * j;
-            if (gm < M && gn_ < N) {
-                float* c = C + static_cast<long long>(gm) * ldc + gn_;
-                *c = beta == 0.f ? alpha * acc[i][j] : fmaf(beta, *c, alpha * acc[i][j]);
-            }
-        }
-}
-
-gn_status sgemm(gn_handle h, long long M, long long N, long long K, float alpha, const float* A, long long lda,
-                int ta, const float* B, long long ldb, int tb, float beta, float* C, long long ldc) {
-    if (M <= 0 || N <= 0) return GN_OK;
-    dim3 grid(static_cast<unsigned>((N + ST - 1) / ST), static_cast<unsigned>((M + ST - 1) / ST));
-    sgemm_kernel<<<grid, STHREADS, 0, h->stream>>>((int)M, (int)N, (int)K, alpha, A, lda, ta, B, ldb, tb, beta, C,
-                                                   ldc);
-    count_launch();
-    GN_CUDA_TRY(cudaGetLastError());
-    return GN_OK;
-}
-
-__global__ void cvt_kernel_d2f(const double* __restrict__ s, long long rows, long long cols, long long lds, float* d,
-                               long long ldd, int transpose) {
-    const long long total = rows * cols;
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-         e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long i = e / cols, j = e % cols;
-        const float v = static_cast<float>(s[i * lds + j]);
-        if (transpose) d[j * ldd + i] = v; else d[i * ldd + j] = v;
-    }
-}
 
 __global__ void copy_t_kernel(const double* __restrict__ s, long long rows, long long cols, long long lds, double* d,
                               long long ldd) {
@@ -131,15 +43,6 @@ __global__ void copy_t_kernel(const double* __restrict__ s, long long rows, long
 
 int ew(gn_handle h, long long total) {
     return static_cast<int>(std::max<long long>(1, std::min<long long>((total + 255) / 256, 8LL * h->sm_count)));
-}
-
-gn_status d2f(gn_handle h, const double* s, long long rows, long long cols, long long lds, float* d, long long ldd,
-              int transpose) {
-    if (rows * cols == 0) return GN_OK;
-    cvt_kernel_d2f<<<ew(h, rows * cols), 256, 0, h->stream>>>(s, rows, cols, lds, d, ldd, transpose);
-    count_launch();
-    GN_CUDA_TRY(cudaGetLastError());
-    return GN_OK;
 }
 
 gn_status transpose_f64(gn_handle h, const double* s, long long rows, long long cols, long long lds, double* d,
@@ -278,7 +181,7 @@ struct Bump {
 };
 
 // Scratch of the adjoint; the QR / GEMM scratch is the tail after these.
-size_t backward_fixed(long long m, long long n, long long r, long long l, int f32) {
+size_t backward_fixed(long long m, long long n, long long r, long long l) {
     const long long rl = r + l;
     size_t b = 0;
     b += align256(8 * m * r) * 3;     // AX (f64), F, P
@@ -288,10 +191,6 @@ size_t backward_fixed(long long m, long long n, long long r, long long l, int f3
     b += align256(8 * m * rl);        // S1
     b += align256(8 * r * n);         // S2
     b += align256(8 * r * rl) * 2;    // W, W^T
-    if (f32) {
-        b += align256(4 * m * r) * 2 + align256(4 * rl * n) * 2 + align256(4 * m * rl) + align256(4 * r * n);
-        b += align256(4 * n * r) + align256(4 * m * rl);   // X^T? (unused) and Y copies
-    }
     return b + 4096;
 }
 
@@ -400,12 +299,10 @@ gn_status tc_front(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* 
     return GN_OK;
 }
 
-gn_status backward_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, const gn_mat* Gup, gn_mat* dA,
-                      void* ws, size_t ws_bytes) {
-    const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols;
-    TcWs t;
-    if (tc_carve(m, n, r, rl - r, h->sm_count, static_cast<char*>(ws), &t) > ws_bytes) return GN_ERR_WORKSPACE;
-    GN_TRY(tc_front(h, A, X, Y, m, n, r, rl, t));
+// The backward's own part, from the front in t (F in t.AX, (Y^T A)^T, Q, R and
+// their BF16 slices); reads nothing of A and leaves the front as it was.
+gn_status tc_back(gn_handle h, const gn_mat* X, const gn_mat* Y, const gn_mat* Gup, gn_mat* dA, long long m,
+                  long long n, long long r, long long rl, TcWs& t) {
     const double* F = t.AX;
     // The contractions over G feed W and K, where the projection (I - Q Q^T)
     // cancels most of W^T: FP64-accurate digit-sliced products.
@@ -441,13 +338,9 @@ gn_status backward_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_ma
     return x6_launch(h, g, 1);
 }
 
-gn_status forward_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* Ahat, void* ws,
-                     size_t ws_bytes) {
-    const long long m = A->rows, n = A->cols, r = X->cols, rl = Y->cols;
-    TcWs t;
-    if (tc_carve(m, n, r, rl - r, h->sm_count, static_cast<char*>(ws), &t) > ws_bytes) return GN_ERR_WORKSPACE;
-    GN_TRY(tc_front(h, A, X, Y, m, n, r, rl, t));
-    // G = Q^T (Y^T A) (r x n), then A_hat = F G
+// The forward's own part: G = Q^T (Y^T A) (r x n), then A_hat = F G; the front
+// stays in t for a later backward.
+gn_status tc_forward_rest(gn_handle h, gn_mat* Ahat, long long m, long long n, long long r, long long rl, TcWs& t) {
     X6 g[1];
     g[0] = X6{static_cast<int>(r), static_cast<int>(n), static_cast<int>(rl), 1, 0, 1, {&t.Qs}, {&t.YtATs},
               t.S2, rnd8(n)};
@@ -456,6 +349,95 @@ gn_status forward_tc(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat
     g[0] = X6{static_cast<int>(m), static_cast<int>(n), static_cast<int>(r), 0, 1, 1, {&t.Fs}, {&t.Ahs},
               static_cast<float*>(Ahat->data), Ahat->ld};
     return x6_launch(h, g, 1);
+}
+
+// ---------------------------------------------------------------- FP64 inputs
+// Workspace of the FP64 path (forward and backward share the layout), the QR /
+// GEMM scratch in the tail.
+struct F64Ws {
+    double *AX, *F, *P, *YtA, *Qp, *C, *Wq, *Q, *K1, *Wt, *R, *QtZ, *WQ, *S1, *S2, *W;
+    double* inner;
+    size_t inner_bytes;
+};
+
+bool f64_carve(void* ws, size_t ws_bytes, long long m, long long n, long long r, long long rl, F64Ws* w) {
+    Bump b{static_cast<char*>(ws), ws_bytes, 0, true};
+    w->AX = b.take<double>(m * r);
+    w->F = b.take<double>(m * r);
+    w->P = b.take<double>(m * r);
+    w->YtA = b.take<double>(rl * n);
+    w->Qp = b.take<double>(rl * n);   // Q' = Q S2 (backward) or G = Q^T (Y^T A) (forward)
+    w->C = b.take<double>(rl * r);
+    w->Wq = b.take<double>(rl * r);
+    w->Q = b.take<double>(rl * r);
+    w->K1 = b.take<double>(rl * r);
+    w->Wt = b.take<double>(rl * r);
+    w->R = b.take<double>(r * r);
+    w->QtZ = b.take<double>(r * r);
+    w->WQ = b.take<double>(r * r);
+    w->S1 = b.take<double>(m * rl);
+    w->S2 = b.take<double>(r * n);
+    w->W = b.take<double>(r * rl);
+    if (!b.ok) return false;
+    const size_t o = align256(b.off);
+    w->inner = reinterpret_cast<double*>(static_cast<char*>(ws) + o);
+    w->inner_bytes = ws_bytes > o ? ws_bytes - o : 0;
+    return true;
+}
+
+// Sketches and the core (Algorithm 2 step 2), then F = AX R^{-1}.
+gn_status f64_front(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, long long m, long long n,
+                    long long r, long long rl, F64Ws& w) {
+    const double* A64 = static_cast<const double*>(A->data);
+    const double* X64 = static_cast<const double*>(X->data);
+    GN_TRY(dgemm(h, m, r, n, 1.0, A64, A->ld, 0, X64, X->ld, 0, 0.0, w.AX, r, w.inner, w.inner_bytes));
+    GN_TRY(dgemm(h, rl, n, m, 1.0, static_cast<const double*>(Y->data), Y->ld, 1, A64, A->ld, 0, 0.0, w.YtA, n,
+                 w.inner, w.inner_bytes));
+    GN_TRY(dgemm(h, rl, r, n, 1.0, w.YtA, n, 0, X64, X->ld, 0, 0.0, w.C, r, w.inner, w.inner_bytes));
+    GN_CUDA_TRY(cudaMemcpyAsync(w.Wq, w.C, sizeof(double) * rl * r, cudaMemcpyDeviceToDevice, h->stream));
+    GN_TRY(householder_qr(h, w.Wq, rl, r, r, w.Q, r, w.R, r, w.inner, w.inner_bytes));
+    GN_CUDA_TRY(cudaMemcpyAsync(w.F, w.AX, sizeof(double) * m * r, cudaMemcpyDeviceToDevice, h->stream));
+    return trsm_right_upper(h, w.F, m, r, r, w.R, r, 0, w.inner, w.inner_bytes);
+}
+
+// The backward's own part from the front (F, Y^T A, Q, R), which it leaves as it was.
+gn_status f64_back(gn_handle h, const gn_mat* X, const gn_mat* Y, const gn_mat* Gup, gn_mat* dA, long long m,
+                   long long n, long long r, long long rl, F64Ws& w) {
+    const double* G64 = static_cast<const double*>(Gup->data);
+    const double* X64 = static_cast<const double*>(X->data);
+    const double* Y64 = static_cast<const double*>(Y->data);
+    double* inner = w.inner;
+    const size_t ib = w.inner_bytes;
+    // S1 = G (Y^T A)^T (m x (r+l)), S2 = F^T G (r x n): the two contractions over G
+    GN_TRY(dgemm(h, m, rl, n, 1.0, G64, Gup->ld, 0, w.YtA, n, 1, 0.0, w.S1, rl, inner, ib));
+    GN_TRY(dgemm(h, r, n, m, 1.0, w.F, r, 1, G64, Gup->ld, 0, 0.0, w.S2, n, inner, ib));
+    // W = F^T S1 (r x (r+l)); K1 = W^T R^{-T}; K1 -= Q (Q^T K1)
+    GN_TRY(dgemm(h, r, rl, m, 1.0, w.F, r, 1, w.S1, rl, 0, 0.0, w.W, rl, inner, ib));
+    GN_TRY(transpose_f64(h, w.W, r, rl, rl, w.K1, r));
+    GN_TRY(trsm_right_upper(h, w.K1, rl, r, r, w.R, r, 1, inner, ib));
+    GN_TRY(dgemm(h, r, r, rl, 1.0, w.Q, r, 1, w.K1, r, 0, 0.0, w.QtZ, r, inner, ib));
+    GN_TRY(dgemm(h, rl, r, r, -1.0, w.Q, r, 0, w.QtZ, r, 0, 1.0, w.K1, r, inner, ib));
+    // WQ = (W Q) R^{-T};  K = K1 - Q WQ   (stored in K1)
+    GN_TRY(dgemm(h, r, r, rl, 1.0, w.W, rl, 0, w.Q, r, 0, 0.0, w.WQ, r, inner, ib));
+    GN_TRY(trsm_right_upper(h, w.WQ, r, r, r, w.R, r, 1, inner, ib));
+    GN_TRY(dgemm(h, rl, r, r, -1.0, w.Q, r, 0, w.WQ, r, 0, 1.0, w.K1, r, inner, ib));
+    // P = (S1 Q) R^{-T} + Y K  (m x r);  Q' = Q S2 ((r+l) x n)
+    GN_TRY(dgemm(h, m, r, rl, 1.0, w.S1, rl, 0, w.Q, r, 0, 0.0, w.P, r, inner, ib));
+    GN_TRY(trsm_right_upper(h, w.P, m, r, r, w.R, r, 1, inner, ib));
+    GN_TRY(dgemm(h, m, r, rl, 1.0, Y64, Y->ld, 0, w.K1, r, 0, 1.0, w.P, r, inner, ib));
+    GN_TRY(dgemm(h, rl, n, r, 1.0, w.Q, r, 0, w.S2, n, 0, 0.0, w.Qp, n, inner, ib));
+    // dA = P X^T + Y Q'
+    double* dA64 = static_cast<double*>(dA->data);
+    GN_TRY(dgemm(h, m, n, r, 1.0, w.P, r, 0, X64, X->ld, 1, 0.0, dA64, dA->ld, inner, ib));
+    return dgemm(h, m, n, rl, 1.0, Y64, Y->ld, 0, w.Qp, n, 0, 1.0, dA64, dA->ld, inner, ib);
+}
+
+// The forward's own part: G = Q^T (Y^T A) (first r rows, in Qp), A_hat = F G.
+gn_status f64_forward_rest(gn_handle h, gn_mat* Ahat, long long m, long long n, long long r, long long rl,
+                           F64Ws& w) {
+    GN_TRY(dgemm(h, r, n, rl, 1.0, w.Q, r, 1, w.YtA, n, 0, 0.0, w.Qp, n, w.inner, w.inner_bytes));
+    return dgemm(h, m, n, r, 1.0, w.F, r, 0, w.Qp, n, 0, 0.0, static_cast<double*>(Ahat->data), Ahat->ld, w.inner,
+                 w.inner_bytes);
 }
 
 }  // namespace
@@ -477,9 +459,49 @@ extern "C" gn_status gn_backward_workspace_size(int64_t m, int64_t n, int64_t r,
     const size_t inner = std::max({qr_ws_bytes(r + l, r, sms), dgemm_ws_bytes(r + l, r, n, sms),
                                    dgemm_ws_bytes(r, r + l, m, sms), trsm_ws_bytes(m, r, sms),
                                    dgemm_ws_bytes(m, r, r + l, sms)});
-    *bytes = backward_fixed(m, n, r, l, 0) + inner;
+    *bytes = backward_fixed(m, n, r, l) + inner;
     return GN_OK;
 }
+
+namespace {
+
+// Shapes, leading dimensions and one shared dtype (FP64 or FP32) of the adjoint's
+// matrices; FP32 operands also need 16-byte aligned data and ld % 4 == 0
+// (tensor maps), except the last (an output written row by row).
+gn_status check_adj(const gn_mat* const* mats, const long long (*shp)[2], int count, int dtype) {
+    for (int i = 0; i < count; ++i) {
+        if (!mats[i]->data) return GN_ERR_INVALID_ARG;
+        if (mats[i]->rows != shp[i][0] || mats[i]->cols != shp[i][1]) return GN_ERR_SHAPE;
+        if (mats[i]->ld < mats[i]->cols) return GN_ERR_INVALID_ARG;
+        if (mats[i]->dtype != dtype) return GN_ERR_DTYPE;
+    }
+    if (dtype != GN_F32 && dtype != GN_F64) return GN_ERR_DTYPE;
+    if (dtype == GN_F32)
+        for (int i = 0; i < count; ++i)
+            if ((reinterpret_cast<uintptr_t>(mats[i]->data) & 15) || (i < count - 1 && mats[i]->ld % 4))
+                return GN_ERR_ALIGNMENT;
+    return GN_OK;
+}
+
+void adj_record(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, const void* ws, size_t ws_bytes,
+                long long m, long long n, long long r, long long l) {
+    h->adj.valid = 1;
+    h->adj.ws = ws;
+    h->adj.ws_bytes = ws_bytes;
+    h->adj.A = A->data;
+    h->adj.X = X->data;
+    h->adj.Y = Y->data;
+    h->adj.m = m;
+    h->adj.n = n;
+    h->adj.r = r;
+    h->adj.l = l;
+    h->adj.lda = A->ld;
+    h->adj.ldx = X->ld;
+    h->adj.ldy = Y->ld;
+    h->adj.dtype = A->dtype;
+}
+
+}  // namespace
 
 extern "C" gn_status gn_backward(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, const gn_mat* Gup,
                                  gn_mat* dA, void* ws, size_t ws_bytes) {
@@ -488,139 +510,28 @@ extern "C" gn_status gn_backward(gn_handle h, const gn_mat* A, const gn_mat* X, 
     if (m <= 0 || n <= 0 || r < 1 || l < 1 || r > std::min(m, n) || rl > m) return GN_ERR_SHAPE;
     const gn_mat* mats[5] = {A, X, Y, Gup, dA};
     const long long shp[5][2] = {{m, n}, {n, r}, {m, rl}, {m, n}, {m, n}};
-    for (int i = 0; i < 5; ++i) {
-        if (!mats[i]->data) return GN_ERR_INVALID_ARG;
-        if (mats[i]->rows != shp[i][0] || mats[i]->cols != shp[i][1]) return GN_ERR_SHAPE;
-        if (mats[i]->ld < mats[i]->cols) return GN_ERR_INVALID_ARG;
-        if (mats[i]->dtype != A->dtype) return GN_ERR_DTYPE;
-    }
-    const int f32 = A->dtype == GN_F32;
-    if (!f32 && A->dtype != GN_F64) return GN_ERR_DTYPE;
+    GN_TRY(check_adj(mats, shp, 5, A->dtype));
     size_t need = 0;
     GN_TRY(gn_backward_workspace_size(m, n, r, l, A->dtype, &need));
     if (ws_bytes < need) return GN_ERR_WORKSPACE;
-    if (f32) {
-        for (int i = 0; i < 5; ++i)
-            if ((reinterpret_cast<uintptr_t>(mats[i]->data) & 15) || (i < 4 && mats[i]->ld % 4)) return GN_ERR_ALIGNMENT;
-        return backward_tc(h, A, X, Y, Gup, dA, ws, ws_bytes);
+    h->adj.valid = 0;
+    if (A->dtype == GN_F32) {
+        TcWs t;
+        if (tc_carve(m, n, r, l, h->sm_count, static_cast<char*>(ws), &t) > ws_bytes) return GN_ERR_WORKSPACE;
+        GN_TRY(tc_front(h, A, X, Y, m, n, r, rl, t));
+        adj_record(h, A, X, Y, ws, ws_bytes, m, n, r, l);
+        return tc_back(h, X, Y, Gup, dA, m, n, r, rl, t);
     }
-
-    Bump b{static_cast<char*>(ws), ws_bytes, 0, true};
-    double* AX = b.take<double>(m * r);
-    double* F = b.take<double>(m * r);
-    double* P = b.take<double>(m * r);
-    double* YtA = b.take<double>(rl * n);
-    double* Qp = b.take<double>(rl * n);
-    double* C = b.take<double>(rl * r);
-    double* Wq = b.take<double>(rl * r);
-    double* Q = b.take<double>(rl * r);
-    double* K1 = b.take<double>(rl * r);
-    double* Wt = b.take<double>(rl * r);
-    double* R = b.take<double>(r * r);
-    double* QtZ = b.take<double>(r * r);
-    double* WQ = b.take<double>(r * r);
-    double* S1 = b.take<double>(m * rl);
-    double* S2 = b.take<double>(r * n);
-    double* W = b.take<double>(r * rl);
-    float *AX32 = nullptr, *P32 = nullptr, *YtA32 = nullptr, *Qp32 = nullptr, *S1_32 = nullptr, *S2_32 = nullptr,
-          *F32 = nullptr;
-    if (f32) {
-        AX32 = b.take<float>(m * r);
-        P32 = b.take<float>(m * r);
-        YtA32 = b.take<float>(rl * n);
-        Qp32 = b.take<float>(rl * n);
-        S1_32 = b.take<float>(m * rl);
-        S2_32 = b.take<float>(r * n);
-        F32 = b.take<float>(m * r);
-    }
-    if (!b.ok) return GN_ERR_WORKSPACE;
-    const size_t o = align256(b.off);
-    double* inner = reinterpret_cast<double*>(static_cast<char*>(ws) + o);
-    const size_t inner_bytes = ws_bytes > o ? ws_bytes - o : 0;
-
-    // ---- sketches and the core (Algorithm 2 step 2)
-    if (f32) {
-        const float* A32 = static_cast<const float*>(A->data);
-        GN_TRY(sgemm(h, m, r, n, 1.f, A32, A->ld, 0, static_cast<const float*>(X->data), X->ld, 0, 0.f, AX32, r));
-        GN_TRY(sgemm(h, rl, n, m, 1.f, static_cast<const float*>(Y->data), Y->ld, 1, A32, A->ld, 0, 0.f, YtA32, n));
-        GN_TRY(copy_f32_to_f64(h, AX32, m, r, r, AX, r));
-        GN_TRY(copy_f32_to_f64(h, YtA32, rl, n, n, YtA, n));
-        // C from the FP32 sketch and the FP32 X, accumulated in FP64
-        GN_TRY(dgemm_b32(h, rl, r, n, 1.0, YtA, n, 0, static_cast<const float*>(X->data), X->ld, 0, 0.0, C, r,
-                         inner, inner_bytes));
-    } else {
-        const double* A64 = static_cast<const double*>(A->data);
-        GN_TRY(dgemm(h, m, r, n, 1.0, A64, A->ld, 0, static_cast<const double*>(X->data), X->ld, 0, 0.0, AX, r,
-                     inner, inner_bytes));
-        GN_TRY(dgemm(h, rl, n, m, 1.0, static_cast<const double*>(Y->data), Y->ld, 1, A64, A->ld, 0, 0.0, YtA, n,
-                     inner, inner_bytes));
-        GN_TRY(dgemm(h, rl, r, n, 1.0, YtA, n, 0, static_cast<const double*>(X->data), X->ld, 0, 0.0, C, r, inner,
-                     inner_bytes));
-    }
-    GN_CUDA_TRY(cudaMemcpyAsync(Wq, C, sizeof(double) * rl * r, cudaMemcpyDeviceToDevice, h->stream));
-    GN_TRY(householder_qr(h, Wq, rl, r, r, Q, r, R, r, inner, inner_bytes));
-    // F = AX R^{-1}
-    GN_CUDA_TRY(cudaMemcpyAsync(F, AX, sizeof(double) * m * r, cudaMemcpyDeviceToDevice, h->stream));
-    GN_TRY(trsm_right_upper(h, F, m, r, r, R, r, 0, inner, inner_bytes));
-
-    // ---- S1 = G (Y^T A)^T (m x (r+l)), S2 = F^T G (r x n): the two contractions over G
-    if (f32) {
-        const float* G32 = static_cast<const float*>(Gup->data);
-        GN_TRY(sgemm(h, m, rl, n, 1.f, G32, Gup->ld, 0, YtA32, n, 1, 0.f, S1_32, rl));
-        GN_TRY(d2f(h, F, m, r, r, F32, r, 0));
-        GN_TRY(sgemm(h, r, n, m, 1.f, F32, r, 1, G32, Gup->ld, 0, 0.f, S2_32, n));
-        GN_TRY(copy_f32_to_f64(h, S1_32, m, rl, rl, S1, rl));
-        GN_TRY(copy_f32_to_f64(h, S2_32, r, n, n, S2, n));
-    } else {
-        const double* G64 = static_cast<const double*>(Gup->data);
-        GN_TRY(dgemm(h, m, rl, n, 1.0, G64, Gup->ld, 0, YtA, n, 1, 0.0, S1, rl, inner, inner_bytes));
-        GN_TRY(dgemm(h, r, n, m, 1.0, F, r, 1, G64, Gup->ld, 0, 0.0, S2, n, inner, inner_bytes));
-    }
-    // ---- the r-sized core terms (FP64)
-    // W = F^T S1 (r x (r+l))
-    GN_TRY(dgemm(h, r, rl, m, 1.0, F, r, 1, S1, rl, 0, 0.0, W, rl, inner, inner_bytes));
-    // K1 = W^T R^{-T} ((r+l) x r)
-    GN_TRY(transpose_f64(h, W, r, rl, rl, K1, r));
-    GN_TRY(trsm_right_upper(h, K1, rl, r, r, R, r, 1, inner, inner_bytes));
-    // K1 -= Q (Q^T K1)
-    GN_TRY(dgemm(h, r, r, rl, 1.0, Q, r, 1, K1, r, 0, 0.0, QtZ, r, inner, inner_bytes));
-    GN_TRY(dgemm(h, rl, r, r, -1.0, Q, r, 0, QtZ, r, 0, 1.0, K1, r, inner, inner_bytes));
-    // WQ = (W Q) R^{-T};  K = K1 - Q WQ   (stored in K1)
-    GN_TRY(dgemm(h, r, r, rl, 1.0, W, rl, 0, Q, r, 0, 0.0, WQ, r, inner, inner_bytes));
-    GN_TRY(trsm_right_upper(h, WQ, r, r, r, R, r, 1, inner, inner_bytes));
-    GN_TRY(dgemm(h, rl, r, r, -1.0, Q, r, 0, WQ, r, 0, 1.0, K1, r, inner, inner_bytes));
-    // P = (S1 Q) R^{-T} + Y K  (m x r)
-    GN_TRY(dgemm(h, m, r, rl, 1.0, S1, rl, 0, Q, r, 0, 0.0, P, r, inner, inner_bytes));
-    GN_TRY(trsm_right_upper(h, P, m, r, r, R, r, 1, inner, inner_bytes));
-    if (f32) {
-        GN_TRY(dgemm_a32(h, m, r, rl, 1.0, static_cast<const float*>(Y->data), Y->ld, 0, K1, r, 0, 1.0, P, r, inner,
-                         inner_bytes));
-    } else {
-        GN_TRY(dgemm(h, m, r, rl, 1.0, static_cast<const double*>(Y->data), Y->ld, 0, K1, r, 0, 1.0, P, r, inner,
-                     inner_bytes));
-    }
-    // Q' = Q S2 ((r+l) x n)
-    GN_TRY(dgemm(h, rl, n, r, 1.0, Q, r, 0, S2, n, 0, 0.0, Qp, n, inner, inner_bytes));
-
-    // ---- dA = P X^T + Y Q'
-    if (f32) {
-        float* dA32 = static_cast<float*>(dA->data);
-        GN_TRY(d2f(h, P, m, r, r, P32, r, 0));
-        GN_TRY(d2f(h, Qp, rl, n, n, Qp32, n, 0));
-        GN_TRY(sgemm(h, m, n, r, 1.f, P32, r, 0, static_cast<const float*>(X->data), X->ld, 1, 0.f, dA32, dA->ld));
-        GN_TRY(sgemm(h, m, n, rl, 1.f, static_cast<const float*>(Y->data), Y->ld, 0, Qp32, n, 0, 1.f, dA32, dA->ld));
-    } else {
-        double* dA64 = static_cast<double*>(dA->data);
-        GN_TRY(dgemm(h, m, n, r, 1.0, P, r, 0, static_cast<const double*>(X->data), X->ld, 1, 0.0, dA64, dA->ld,
-                     inner, inner_bytes));
-        GN_TRY(dgemm(h, m, n, rl, 1.0, static_cast<const double*>(Y->data), Y->ld, 0, Qp, n, 0, 1.0, dA64, dA->ld,
-                     inner, inner_bytes));
-    }
-    return GN_OK;
+    F64Ws w;
+    if (!f64_carve(ws, ws_bytes, m, n, r, rl, &w)) return GN_ERR_WORKSPACE;
+    GN_TRY(f64_front(h, A, X, Y, m, n, r, rl, w));
+    adj_record(h, A, X, Y, ws, ws_bytes, m, n, r, l);
+    return f64_back(h, X, Y, Gup, dA, m, n, r, rl, w);
 }
 
 // Forward value A_hat = F G of plain GN in the precision of A (for the autograd
-// wrapper): A_hat (m x n) from A, X, Y.
+// wrapper): A_hat (m x n) from A, X, Y.  The front stays in ws for
+// gn_backward_saved.
 extern "C" gn_status gn_forward_dense(gn_handle h, const gn_mat* A, const gn_mat* X, const gn_mat* Y, gn_mat* Ahat,
                                       void* ws, size_t ws_bytes) {
     if (!h || !A || !X || !Y || !Ahat || !ws) return GN_ERR_INVALID_ARG;
@@ -628,67 +539,42 @@ extern "C" gn_status gn_forward_dense(gn_handle h, const gn_mat* A, const gn_mat
     if (m <= 0 || n <= 0 || r < 1 || l < 1 || r > std::min(m, n) || rl > m) return GN_ERR_SHAPE;
     const gn_mat* mats[4] = {A, X, Y, Ahat};
     const long long shp[4][2] = {{m, n}, {n, r}, {m, rl}, {m, n}};
-    for (int i = 0; i < 4; ++i) {
-        if (!mats[i]->data) return GN_ERR_INVALID_ARG;
-        if (mats[i]->rows != shp[i][0] || mats[i]->cols != shp[i][1]) return GN_ERR_SHAPE;
-        if (mats[i]->ld < mats[i]->cols) return GN_ERR_INVALID_ARG;
-        if (mats[i]->dtype != A->dtype) return GN_ERR_DTYPE;
-    }
-    const int f32 = A->dtype == GN_F32;
-    if (!f32 && A->dtype != GN_F64) return GN_ERR_DTYPE;
+    GN_TRY(check_adj(mats, shp, 4, A->dtype));
     size_t need = 0;
     GN_TRY(gn_backward_workspace_size(m, n, r, l, A->dtype, &need));
     if (ws_bytes < need) return GN_ERR_WORKSPACE;
-    if (f32) return forward_tc(h, A, X, Y, Ahat, ws, ws_bytes);
-    Bump b{static_cast<char*>(ws), ws_bytes, 0, true};
-    double* AX = b.take<double>(m * r);
-    double* F = b.take<double>(m * r);
-    double* Gf = b.take<double>(rl * n);   // G factor = Q^T (Y^T A), first r rows used
-    double* YtA = b.take<double>(rl * n);
-    double* C = b.take<double>(rl * r);
-    double* Wq = b.take<double>(rl * r);
-    double* Q = b.take<double>(rl * r);
-    double* R = b.take<double>(r * r);
-    float *AX32 = nullptr, *YtA32 = nullptr, *F32 = nullptr, *G32 = nullptr;
-    if (f32) {
-        AX32 = b.take<float>(m * r);
-        YtA32 = b.take<float>(rl * n);
-        F32 = b.take<float>(m * r);
-        G32 = b.take<float>(r * n);
+    h->adj.valid = 0;
+    if (A->dtype == GN_F32) {
+        TcWs t;
+        if (tc_carve(m, n, r, l, h->sm_count, static_cast<char*>(ws), &t) > ws_bytes) return GN_ERR_WORKSPACE;
+        GN_TRY(tc_front(h, A, X, Y, m, n, r, rl, t));
+        adj_record(h, A, X, Y, ws, ws_bytes, m, n, r, l);
+        return tc_forward_rest(h, Ahat, m, n, r, rl, t);
     }
-    if (!b.ok) return GN_ERR_WORKSPACE;
-    const size_t o = align256(b.off);
-    double* inner = reinterpret_cast<double*>(static_cast<char*>(ws) + o);
-    const size_t inner_bytes = ws_bytes > o ? ws_bytes - o : 0;
-    if (f32) {
-        const float* A32 = static_cast<const float*>(A->data);
-        GN_TRY(sgemm(h, m, r, n, 1.f, A32, A->ld, 0, static_cast<const float*>(X->data), X->ld, 0, 0.f, AX32, r));
-        GN_TRY(sgemm(h, rl, n, m, 1.f, static_cast<const float*>(Y->data), Y->ld, 1, A32, A->ld, 0, 0.f, YtA32, n));
-        GN_TRY(copy_f32_to_f64(h, AX32, m, r, r, AX, r));
-        GN_TRY(copy_f32_to_f64(h, YtA32, rl, n, n, YtA, n));
-        GN_TRY(dgemm_b32(h, rl, r, n, 1.0, YtA, n, 0, static_cast<const float*>(X->data), X->ld, 0, 0.0, C, r,
-                         inner, inner_bytes));
-    } else {
-        const double* A64 = static_cast<const double*>(A->data);
-        GN_TRY(dgemm(h, m, r, n, 1.0, A64, A->ld, 0, static_cast<const double*>(X->data), X->ld, 0, 0.0, AX, r,
-                     inner, inner_bytes));
-        GN_TRY(dgemm(h, rl, n, m, 1.0, static_cast<const double*>(Y->data), Y->ld, 1, A64, A->ld, 0, 0.0, YtA, n,
-                     inner, inner_bytes));
-        GN_TRY(dgemm(h, rl, r, n, 1.0, YtA, n, 0, static_cast<const double*>(X->data), X->ld, 0, 0.0, C, r, inner,
-                     inner_bytes));
+    F64Ws w;
+    if (!f64_carve(ws, ws_bytes, m, n, r, rl, &w)) return GN_ERR_WORKSPACE;
+    GN_TRY(f64_front(h, A, X, Y, m, n, r, rl, w));
+    adj_record(h, A, X, Y, ws, ws_bytes, m, n, r, l);
+    return f64_forward_rest(h, Ahat, m, n, r, rl, w);
+}
+
+extern "C" gn_status gn_backward_saved(gn_handle h, const gn_mat* X, const gn_mat* Y, const gn_mat* Gup, gn_mat* dA,
+                                       void* ws, size_t ws_bytes) {
+    if (!h || !X || !Y || !Gup || !dA || !ws) return GN_ERR_INVALID_ARG;
+    const long long m = Gup->rows, n = Gup->cols, r = X->cols, rl = Y->cols, l = rl - r;
+    if (!h->adj.valid || h->adj.ws != ws || h->adj.ws_bytes != ws_bytes || h->adj.X != X->data ||
+        h->adj.Y != Y->data || h->adj.ldx != X->ld || h->adj.ldy != Y->ld || h->adj.m != m || h->adj.n != n ||
+        h->adj.r != r || h->adj.l != l || h->adj.dtype != Gup->dtype)
+        return GN_ERR_INVALID_ARG;
+    const gn_mat* mats[4] = {X, Y, Gup, dA};
+    const long long shp[4][2] = {{n, r}, {m, rl}, {m, n}, {m, n}};
+    GN_TRY(check_adj(mats, shp, 4, Gup->dtype));
+    if (Gup->dtype == GN_F32) {
+        TcWs t;
+        if (tc_carve(m, n, r, l, h->sm_count, static_cast<char*>(ws), &t) > ws_bytes) return GN_ERR_WORKSPACE;
+        return tc_back(h, X, Y, Gup, dA, m, n, r, rl, t);
     }
-    GN_CUDA_TRY(cudaMemcpyAsync(Wq, C, sizeof(double) * rl * r, cudaMemcpyDeviceToDevice, h->stream));
-    GN_TRY(householder_qr(h, Wq, rl, r, r, Q, r, R, r, inner, inner_bytes));
-    GN_CUDA_TRY(cudaMemcpyAsync(F, AX, sizeof(double) * m * r, cudaMemcpyDeviceToDevice, h->stream));
-    GN_TRY(trsm_right_upper(h, F, m, r, r, R, r, 0, inner, inner_bytes));
-    GN_TRY(dgemm(h, r, n, rl, 1.0, Q, r, 1, YtA, n, 0, 0.0, Gf, n, inner, inner_bytes));
-    if (f32) {
-        GN_TRY(d2f(h, F, m, r, r, F32, r, 0));
-        GN_TRY(d2f(h, Gf, r, n, n, G32, n, 0));
-        GN_TRY(sgemm(h, m, n, r, 1.f, F32, r, 0, G32, n, 0, 0.f, static_cast<float*>(Ahat->data), Ahat->ld));
-    } else {
-        GN_TRY(dgemm(h, m, n, r, 1.0, F, r, 0, Gf, n, 0, 0.0, static_cast<double*>(Ahat->data), Ahat->ld, inner,
-                     inner_bytes));
-    }
-    return GN_OK;
+    F64Ws w;
+    if (!f64_carve(ws, ws_bytes, m, n, r, rl, &w)) return GN_ERR_WORKSPACE;
+    return f64_back(h, X, Y, Gup, dA, m, n, r, rl, w);
 }

@@ -521,6 +521,7 @@ gn_status gn_create(gn_handle* out, void* stream) {
     h->fp64_tc = 1;
     h->fp64_accum = 0;
     h->stall_test = 0;
+    h->adj.valid = 0;
     if (cudaMalloc(&h->dstatus, 64) != cudaSuccess) {
         delete h;
         return GN_ERR_CUDA;

@@ -41,6 +41,16 @@ struct gn_handle_s {
         double *R, *Q2, *R2, *W2, *inner;
         size_t inner_bytes;
     } pend;
+    // gn_forward_dense / gn_backward: the workspace whose shared front (sketches,
+    // core QR, F) was formed last, and from which inputs; gn_backward_saved
+    // requires a match
+    struct {
+        int valid;
+        const void *ws, *A, *X, *Y;
+        size_t ws_bytes;
+        long long m, n, r, l, lda, ldx, ldy;
+        int dtype;
+    } adj;
 };
 
 #define GN_CUDA_TRY(expr)                                   \

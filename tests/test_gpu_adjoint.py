@@ -119,3 +119,73 @@ def test_adjoint_config4_fp32_against_oracle(gn, H):
     h = lambda t: t.double().cpu().numpy()
     ref = O.gn_backward(h(A), h(X), h(Y), h(G))
     assert rel(h(dA), ref) <= 1e-3
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 1e-6)])
+def test_backward_saved_matches_backward(gn, H, dtype, tol):
+    """gn_backward_saved from the front gn_forward_dense left in the workspace
+    equals gn_backward (which forms the front again), for two Gup on one front;
+    in FP64 also against the oracle's adjoint."""
+    m, n, r, l = 320, 192, 16, 8
+    (A, X, Y, G), (tA, tX, tY, tG) = _case(m, n, r, l, 6, dtype)
+    G2 = torch.randn(m, n, dtype=dtype, device="cuda")
+    dt = gn.F64 if dtype == torch.float64 else gn.F32
+    ws = H.backward_workspace(m, n, r, l, dt)
+    Ah = torch.empty_like(tA)
+    H.forward_dense(tA, tX, tY, Ah, ws)
+    saved = []
+    for Gup in (tG, G2):
+        dA = torch.empty_like(tA)
+        H.backward_saved(tX, tY, Gup, dA, ws)
+        saved.append(dA)
+    assert H.sync_status() == 0
+    ws2 = H.backward_workspace(m, n, r, l, dt)
+    for Gup, dA in zip((tG, G2), saved):
+        full = torch.empty_like(tA)
+        H.backward(tA, tX, tY, Gup, full, ws2)
+        assert H.sync_status() == 0
+        assert torch.linalg.norm(dA - full) <= tol * torch.linalg.norm(full)
+    if dtype == torch.float64:
+        assert rel(saved[0].cpu().numpy(), O.gn_backward(A, X, Y, G)) <= 1e-9
+
+
+def test_backward_saved_needs_the_matching_front(gn, H):
+    """The handle keeps the front of its last gn_forward_dense / gn_backward:
+    another workspace, other X or Y, or a later forward on another workspace
+    make gn_backward_saved fail (GN_ERR_INVALID_ARG, checked on the host)."""
+    m, n, r, l = 96, 64, 8, 4
+    _, (tA, tX, tY, tG) = _case(m, n, r, l, 7)
+    ws1 = H.backward_workspace(m, n, r, l, gn.F64)
+    ws2 = H.backward_workspace(m, n, r, l, gn.F64)
+    Ah, dA = torch.empty_like(tA), torch.empty_like(tA)
+    H.forward_dense(tA, tX, tY, Ah, ws1)
+    with pytest.raises(gn.GNError) as e:
+        H.backward_saved(tX, tY, tG, dA, ws2)
+    assert e.value.status == 1
+    with pytest.raises(gn.GNError):
+        H.backward_saved(tX.clone(), tY, tG, dA, ws1)
+    H.backward_saved(tX, tY, tG, dA, ws1)          # the matching front
+    H.forward_dense(tA, tX, tY, Ah, ws2)           # replaces the record
+    with pytest.raises(gn.GNError):
+        H.backward_saved(tX, tY, tG, dA, ws1)
+    assert H.sync_status() == 0
+
+
+def test_autograd_uses_the_saved_front(gn, H):
+    """The autograd wrapper's backward from the forward's front equals the
+    C-ABI adjoint, and so does a backward after another forward on the same
+    handle (which re-forms the front)."""
+    m, n, r, l = 40, 30, 6, 3
+    _, (tA, tX, tY, _) = _case(m, n, r, l, 8)
+    Gup = torch.randn(m, n, dtype=torch.float64, device="cuda")
+    ws = H.backward_workspace(m, n, r, l, gn.F64)
+    ref = torch.empty_like(tA)
+    H.backward(tA, tX, tY, Gup, ref, ws)
+    a1 = tA.clone().requires_grad_(True)
+    (gn.gn_approx_dense(a1, tX, tY, H) * Gup).sum().backward()
+    a2 = tA.clone().requires_grad_(True)
+    out2 = gn.gn_approx_dense(a2, tX, tY, H)
+    gn.gn_approx_dense(tA.clone(), tX, tY, H)      # another forward on the handle
+    (out2 * Gup).sum().backward()
+    for g in (a1.grad, a2.grad):
+        assert torch.allclose(g, ref, rtol=1e-12, atol=1e-12)
