@@ -1845,7 +1845,7 @@ size_t qr_blk_bytes(long long M, long long N) {
     const long long nblk = (N + QR_BB - 1) / QR_BB;
     return al256d(qr_oz_crit_bytes(M)) + al256d(sizeof(double) * nblk * QR_BB * QR_BB) +
            al256d(sizeof(double) * QR_BB * QR_BB) + 2 * al256d(sizeof(double) * QR_BB * N) +
-           2 * al256d(sizeof(double) * QR_BB * QR_BB) + 1024;
+           al256d(sizeof(double) * QR_BB * QR_BB) + al256d(sizeof(double) * M * QR_BB) + 1024;
 }
 
 struct QrBlk {
@@ -1853,7 +1853,8 @@ struct QrBlk {
     size_t oz_side_bytes;
     void* oz_crit;
     size_t oz_crit_bytes;
-    double *TB, *GB, *Z1s, *Z2s, *Z1c, *Z2c;
+    double *TB, *GB, *Z1s, *Z2s, *Z1c;
+    double* UB;   // U_b = V_b T_b (M_p x b_w, ld QR_BB) of the block being applied
 };
 
 bool qr_blk_carve(long long M, long long N, void* oz, size_t oz_bytes, QrBlk* b) {
@@ -1875,18 +1876,17 @@ bool qr_blk_carve(long long M, long long N, void* oz, size_t oz_bytes, QrBlk* b)
     b->Z1s = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * N));
     b->Z2s = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * N));
     b->Z1c = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * QR_BB));
-    b->Z2c = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * QR_BB));
+    b->UB = reinterpret_cast<double*>(take(sizeof(double) * M * QR_BB));
     return off <= oz_bytes;
 }
 
-// C (Mp x nc at ldc) <- (I - V T V^T)^T C = C - V T^T (V^T C), V: Mp x bw at ldv,
-// T: bw x bw upper triangular at ldt; the three products digit-sliced.
-gn_status block_apply(gn_handle h, double* C, long long ldc, long long Mp, long long nc, const double* V,
-                      long long ldv, int bw, const double* T, long long ldt, double* Z1, double* Z2, void* oz,
-                      size_t oz_bytes) {
-    GN_TRY(oz_dgemm(h, bw, nc, Mp, 1.0, V, 0, ldv, 1, C, ldc, 0, 0.0, Z1, nc, oz, oz_bytes));
-    GN_TRY(oz_dgemm(h, bw, nc, bw, 1.0, T, 0, ldt, 1, Z1, nc, 0, 0.0, Z2, nc, oz, oz_bytes));
-    return oz_dgemm(h, Mp, nc, bw, -1.0, V, 0, ldv, 0, Z2, nc, 0, 1.0, C, ldc, oz, oz_bytes);
+// C (Mp x nc at ldc) <- (I - V T V^T)^T C = C - V (T^T V^T C), V: Mp x bw at
+// ldv, T bw x bw upper triangular, given as U = V T (Mp x bw at ldu, formed once
+// per block): Z = U^T C, C -= V Z, both digit-sliced.
+gn_status block_apply_u(gn_handle h, double* C, long long ldc, long long Mp, long long nc, const double* V,
+                        long long ldv, int bw, const double* U, long long ldu, double* Z, void* oz, size_t oz_bytes) {
+    GN_TRY(oz_dgemm(h, bw, nc, Mp, 1.0, U, 0, ldu, 1, C, ldc, 0, 0.0, Z, nc, oz, oz_bytes));
+    return oz_dgemm(h, Mp, nc, bw, -1.0, V, 0, ldv, 0, Z, nc, 0, 1.0, C, ldc, oz, oz_bytes);
 }
 
 // Whether qr_factor takes the blocked path for this shape and workspace (and,
@@ -1965,8 +1965,12 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
                             bk.oz_crit_bytes));
             launch_ut_inverse(h, bk.GB, QR_BB, q.tau + b0, static_cast<int>(bw), TB, QR_BB);
             GN_CUDA_TRY(cudaGetLastError());
-            // the next block's columns already have the block before this one (side stream)
+            // the next block's columns already have the block before this one (side stream),
+            // which has also stopped reading the previous U_b
             if (pending) GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+            // U_b = V_b T_b: each update below is then two products, Z = U_b^T C and C -= V_b Z
+            GN_TRY(oz_dgemm(h, Mp, bw, bw, 1.0, VB, 0, N, 0, TB, QR_BB, 0, 0.0, bk.UB, QR_BB, bk.oz_crit,
+                            bk.oz_crit_bytes));
             const long long nnext = std::min<long long>(QR_BB, N2);
             const long long nsec = std::min<long long>(QR_BB, N2 - nnext);
             const long long nrest = N2 - nnext - nsec;
@@ -1976,14 +1980,14 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
                 GN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
                 gn_handle_s side = *h;
                 side.stream = h->side;
-                GN_TRY(block_apply(&side, W + b0 * ld + b0 + bw + nnext, ld, Mp, nsec + nrest, VB, N,
-                                   static_cast<int>(bw), TB, QR_BB, bk.Z1s, bk.Z2s, bk.oz_side, bk.oz_side_bytes));
+                GN_TRY(block_apply_u(&side, W + b0 * ld + b0 + bw + nnext, ld, Mp, nsec + nrest, VB, N,
+                                     static_cast<int>(bw), bk.UB, QR_BB, bk.Z1s, bk.oz_side, bk.oz_side_bytes));
                 GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
                 side_used = true;
             }
             pending = nsec > 0;
-            GN_TRY(block_apply(h, W + b0 * ld + b0 + bw, ld, Mp, nnext, VB, N, static_cast<int>(bw), TB, QR_BB,
-                               bk.Z1c, bk.Z2c, bk.oz_crit, bk.oz_crit_bytes));
+            GN_TRY(block_apply_u(h, W + b0 * ld + b0 + bw, ld, Mp, nnext, VB, N, static_cast<int>(bw), bk.UB, QR_BB,
+                                 bk.Z1c, bk.oz_crit, bk.oz_crit_bytes));
         }
     } else {
         GN_TRY(factor_panel(0));
