@@ -179,7 +179,7 @@ gn_status gn_set_fp64_accum(gn_handle h, int64_t part_k);
 /* Where the large FP64 products run for GN_F32 sketches (the tensor-core
  * path): in gn_core, the QR's trailing updates (for r >= 512 the
  * factorization runs in 256-column blocks and each block's reflectors update
- * the columns to its right as three products; below that, the columns beyond
+ * the columns to its right as two products after U = V T; below that, the columns beyond
  * the next two panels of the look-ahead) and the formation of the thin Q; in
  * gn_factors / gn_approx, the outer-block updates of the triangular solve
  * F R = AX (eq. 5.1) and, after a truncation, AX Q_2; in gn_apply, the products
