@@ -13,11 +13,14 @@
 // step; the SVD from it, preconditioned as Drmac and Veselic (2008) do, by
 // one-sided (Hestenes) Jacobi rotations of the rows of R in round-robin order
 // (C P = Q R, G^T R = T with orthogonal rows, so U = Q G and V = P T^T S^-1),
-// with the rotations accumulated in global memory.  DIAG_RAISE
+// run over a thread-block cluster whose CTAs each hold a slice of the columns
+// of T and of the accumulated rotations.  DIAG_RAISE
 // takes the library's blocked Householder QR for any r.  The products that
 // form F and G and the triangular solves are the FP64 routines of gn_f64.cu.
 #include "gn_internal.cuh"
 #include "gn_smem_core.cuh"
+
+#include <cooperative_groups.h>
 
 #include <string.h>
 
@@ -29,22 +32,14 @@ using namespace smemcore;
 
 constexpr int JACOBI_MAX_SWEEPS = 40;
 
-__device__ inline double group_sum(double v, int g) {
-    for (int o = g >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// C (M x N, global, ld N) -> one of the small-core factorizations.
-//   Ul (M x N, ld N): Q (RRQR); unused by the SVD variants
-//   Wr (N x N, ld N): V S~^{-1} (SVD variants, columns by decreasing s) or R~ (RRQR, upper triangular)
-//   VT (N x N, ld N): scratch for the rotations G^T
-//   Qg (M x N), Rg (N x N): SVD variants: the pivoted QR's Q and R; Rg then
-//     receives G with columns by decreasing s (U = Qg Rg, formed by the caller)
-//   perm (N): RRQR column order; sv (N): s (SVD) or diag(R) after pivoting
-//   out[0] = k, out[1] = Jacobi sweeps
-__global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restrict__ C, int M, int N, int variant,
-                                                          double eps, double* Ul, double* Wr, double* VT, int* perm,
-                                                          double* sv, int* out, double* Qg, double* Rg) {
+// C (M x N, global, ld N) -> the core's pivoted QR, C P = Q R.
+//   SVD variants: Q to Qg (M x N), R to Rg (N x N); jacobi_cluster_kernel follows.
+//   RRQR_RAISE: Q with diag(R) >= 0 to Ul (M x N, ld N), R~ (|R_ii| raised to
+//     eps) to Wr (N x N, upper triangular), diag(R) to sv, out[0] = N, out[1] = 0.
+//   perm (N): the column order.
+__global__ void __launch_bounds__(BT, 1) variant_core_kernel(const double* __restrict__ C, int M, int N, int variant,
+                                                          double eps, double* Ul, double* Wr, int* perm, double* sv,
+                                                          int* out, double* Qg, double* Rg) {
     extern __shared__ double shm[];
     const int tid = threadIdx.x;
     if (variant != GN_VARIANT_RRQR_RAISE) {
@@ -72,7 +67,6 @@ __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restri
         __syncthreads();
         smem_form_q(sm, M, N);
         for (int e = tid; e < M * N; e += BT) Qg[e] = sm.S[(e / N) * ld + e % N];
-        __syncthreads();   // R and Q written (block-wide visibility) before shared memory is reused
     } else {
         Smem sm;
         sm.ld = N + 1;
@@ -110,37 +104,60 @@ __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restri
             out[0] = N;
             out[1] = 0;
         }
-        return;
     }
+}
 
-    // ---- one-sided Jacobi on the rows of T = R (N x N, ld N + 1): plane
-    // rotations of row pairs in round-robin order until every pair is
-    // orthogonal to tol; G^T (the product of the rotations) accumulates in VT.
-    const int MJ = N;                       // row length
-    const int ldt = MJ + 1;
-    double* T = shm;
-    double* s_norm = T + static_cast<size_t>(N) * ldt;   // [NMAX]
-    int* s_rank = reinterpret_cast<int*>(s_norm + NMAX);  // [NMAX]
-    __shared__ int s_rot;
-    for (int e = tid; e < N * N; e += BT) {
-        const int j = e / N, i = e - j * N;
-        T[j * ldt + i] = Rg[e];
+// ---- one-sided Jacobi on the rows of T = R (N x N) over a cluster: CTA c holds
+// columns [c w, c w + w) of T and of G^T (the accumulated rotations), w =
+// ceil(N / JC_CS).  A round's pairs are disjoint: every CTA forms the pairs'
+// partial dot products over its columns, the partials go through distributed
+// shared memory (double-buffered by round parity, one cluster barrier per
+// round), every CTA adds them in rank order (so all CTAs take the same
+// decisions and run the same number of barriers) and rotates its own columns.
+constexpr int JC_CS = 8;                    // CTAs per cluster
+constexpr int JC_T = 256;                   // threads per CTA
+constexpr int JC_W = NMAX / JC_CS;          // columns per CTA (at most)
+constexpr int JC_PAIRS = NMAX / 2;          // pairs per round (at most)
+constexpr int JC_G = JC_T / JC_PAIRS;       // threads per pair
+
+struct JcSmem {
+    double T[NMAX][JC_W + 1];
+    double V[NMAX][JC_W + 1];
+    double part[2][JC_PAIRS][4];   // alpha, beta, gamma of every pair, by round parity
+    double normp[NMAX];            // partial squared row norms (after the sweeps)
+    double s[NMAX];
+    int rank[NMAX];
+    int k;
+};
+
+// Rg (N x N): R on entry, G with columns by decreasing s on exit (U = Q Rg,
+// formed by the caller); Wr (N x N): V S~^{-1}, rows permuted back by perm;
+// sv: s in decreasing order; out[0] = k, out[1] = sweeps.
+__global__ void __cluster_dims__(JC_CS, 1, 1) __launch_bounds__(JC_T)
+    jacobi_cluster_kernel(int N, int variant, double eps, double* Rg, double* Wr, const int* __restrict__ perm,
+                          double* sv, int* out) {
+    namespace cg = cooperative_groups;
+    __shared__ JcSmem sm;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = static_cast<int>(cluster.block_rank());
+    const int tid = threadIdx.x;
+    const int wc = (N + JC_CS - 1) / JC_CS;
+    const int c0 = rank * wc, ncol = max(0, min(N, c0 + wc) - c0);   // this CTA's columns
+    for (int e = tid; e < N * wc; e += JC_T) {
+        const int j = e / wc, i = e - j * wc;
+        sm.T[j][i] = i < ncol ? Rg[j * N + c0 + i] : 0.0;
+        sm.V[j][i] = i < ncol && j == c0 + i ? 1.0 : 0.0;
     }
-    for (int e = tid; e < N * N; e += BT) VT[e] = (e / N == e % N) ? 1.0 : 0.0;
     __syncthreads();
-    const int n2 = (N + 1) & ~1;          // even player count (a dummy when N is odd)
+    const int n2 = (N + 1) & ~1;
     const int npairs = n2 / 2;
-    int g = 32;
-    while (g > 1 && g * npairs > BT) g >>= 1;   // threads per pair (a power of two <= 32)
-    const int pair = tid / g, gl = tid % g;
-    const double tol = 2.0 * static_cast<double>(MJ) * 1.1102230246251565e-16;
-    int sweeps = 0;
+    const int pair = tid / JC_G, gl = tid % JC_G;
+    const double tol = 2.0 * static_cast<double>(N) * 1.1102230246251565e-16;
+    int sweeps = 0, parity = 0;
     for (; sweeps < JACOBI_MAX_SWEEPS; ++sweeps) {
-        if (tid == 0) s_rot = 0;
-        __syncthreads();
         int rotated = 0;
-        for (int round = 0; round < n2 - 1; ++round) {
-            int p = 0, q = N;   // q = N: an idle group (no pair, or the dummy player)
+        for (int round = 0; round < n2 - 1; ++round, parity ^= 1) {
+            int p = 0, q = N;   // q = N: no pair, or the dummy player
             if (pair < npairs) {
                 const int a = (round + pair) % (n2 - 1);
                 const int b = pair == 0 ? n2 - 1 : (round - pair + n2 - 1) % (n2 - 1);
@@ -150,93 +167,105 @@ __global__ void __launch_bounds__(BT) variant_core_kernel(const double* __restri
             const bool act = q < N;
             double al = 0.0, be = 0.0, ga = 0.0;
             if (act)
-                for (int i = gl; i < MJ; i += g) {
-                    const double tp = T[p * ldt + i], tq = T[q * ldt + i];
+                for (int i = gl; i < ncol; i += JC_G) {
+                    const double tp = sm.T[p][i], tq = sm.T[q][i];
                     al = fma(tp, tp, al);
                     be = fma(tq, tq, be);
                     ga = fma(tp, tq, ga);
                 }
-            // every lane of every warp takes part in the shuffles
-            al = group_sum(al, g);
-            be = group_sum(be, g);
-            ga = group_sum(ga, g);
-            if (act && fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
-                const double zeta = (be - al) / (2.0 * ga);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                for (int i = gl; i < MJ; i += g) {
-                    const double tp = T[p * ldt + i], tq = T[q * ldt + i];
-                    T[p * ldt + i] = c * tp - s * tq;
-                    T[q * ldt + i] = s * tp + c * tq;
-                }
-                for (int i = gl; i < N; i += g) {
-                    const double vp = VT[p * N + i], vq = VT[q * N + i];
-                    VT[p * N + i] = c * vp - s * vq;
-                    VT[q * N + i] = s * vp + c * vq;
-                }
-                rotated = 1;
+#pragma unroll
+            for (int o = 1; o < JC_G; o <<= 1) {   // the pair's JC_G lanes are adjacent in one warp
+                al += __shfl_xor_sync(0xffffffffu, al, o);
+                be += __shfl_xor_sync(0xffffffffu, be, o);
+                ga += __shfl_xor_sync(0xffffffffu, ga, o);
             }
-            __syncthreads();
+            if (gl == 0 && pair < JC_PAIRS) {
+                sm.part[parity][pair][0] = al;
+                sm.part[parity][pair][1] = be;
+                sm.part[parity][pair][2] = ga;
+            }
+            cluster.sync();   // every CTA's partials of this round written
+            if (act) {
+                al = be = ga = 0.0;
+                for (int c = 0; c < JC_CS; ++c) {   // rank order: the same sums in every CTA
+                    const double* pc = cluster.map_shared_rank(&sm.part[parity][pair][0], c);
+                    al += pc[0];
+                    be += pc[1];
+                    ga += pc[2];
+                }
+                if (fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                    for (int i = gl; i < ncol; i += JC_G) {
+                        const double tp = sm.T[p][i], tq = sm.T[q][i];
+                        sm.T[p][i] = cs * tp - sn * tq;
+                        sm.T[q][i] = sn * tp + cs * tq;
+                        const double vp = sm.V[p][i], vq = sm.V[q][i];
+                        sm.V[p][i] = cs * vp - sn * vq;
+                        sm.V[q][i] = sn * vp + cs * vq;
+                    }
+                    rotated = 1;
+                }
+            }
+            __syncthreads();   // the round's rotations in place before the next round's partials
         }
-        if (rotated) s_rot = 1;
-        __syncthreads();
-        if (!s_rot) break;
-        __syncthreads();
+        // the same decisions in every CTA: the same answer here, the same number of barriers
+        if (!__syncthreads_or(rotated)) break;
     }
-    // singular values = row norms of T; ranks by decreasing value (index order on ties)
-    for (int j = tid / 32; j < N; j += BW) {
+    // singular values = row norms of T (partials over the CTAs' columns, added in rank order)
+    for (int j = tid; j < N; j += JC_T) {
         double a = 0.0;
-        for (int i = tid % 32; i < MJ; i += 32) a = fma(T[j * ldt + i], T[j * ldt + i], a);
-        a = group_sum(a, 32);
-        if (tid % 32 == 0) s_norm[j] = sqrt(a);
+        for (int i = 0; i < ncol; ++i) a = fma(sm.T[j][i], sm.T[j][i], a);
+        sm.normp[j] = a;
+    }
+    cluster.sync();
+    for (int j = tid; j < N; j += JC_T) {
+        double a = 0.0;
+        for (int c = 0; c < JC_CS; ++c) a += cluster.map_shared_rank(sm.normp, c)[j];
+        sm.s[j] = sqrt(a);
     }
     __syncthreads();
-    for (int j = tid; j < N; j += BT) {
+    for (int j = tid; j < N; j += JC_T) {
         int rk = 0;
-        const double sj = s_norm[j];
-        for (int i = 0; i < N; ++i) rk += (s_norm[i] > sj || (s_norm[i] == sj && i < j)) ? 1 : 0;
-        s_rank[j] = rk;
-        sv[rk] = sj;
+        const double sj = sm.s[j];
+        for (int i = 0; i < N; ++i) rk += (sm.s[i] > sj || (sm.s[i] == sj && i < j)) ? 1 : 0;
+        sm.rank[j] = rk;
+        if (rank == 0) sv[rk] = sj;
     }
-    __syncthreads();
-    __shared__ int s_k;
     if (tid == 0) {
         int k = 0;
         if (variant == GN_VARIANT_SVD_TRUNCATE) {
-            for (int j = 0; j < N; ++j) k += s_norm[j] > eps ? 1 : 0;
+            for (int j = 0; j < N; ++j) k += sm.s[j] > eps ? 1 : 0;
         } else {
             k = N;
         }
-        s_k = k;
-        out[0] = k;
-        out[1] = sweeps;
+        sm.k = k;
+        if (rank == 0) {
+            out[0] = k;
+            out[1] = sweeps;
+        }
     }
     __syncthreads();
-    const int k = s_k;
     // R = G T with T_j = s_j W_j (W orthonormal rows), so C P = (Q G) diag(s) W:
-    //   U = Q G, column rank_j = Q G_j  (G_j = row j of VT): Rg[:, rank_j] = VT[j, :]^T,
-    //     multiplied by Q outside the kernel;
+    //   U = Q G: Rg[i][rank_j] = G[i][j] = V[j][i] (this CTA's rows i of G);
     //   V = P W^T: V[perm[i]][rank_j] = T[j][i] / s_j, stored as Wr = V S~^{-1}.
-    for (int e = tid; e < N * N; e += BT) {
-        const int j = e / N, i = e - j * N;   // Rg[i][rank_j] = G[i][j] = VT[j][i]
-        Rg[i * N + s_rank[j]] = VT[e];
-    }
-    for (int e = tid; e < N * N; e += BT) {
-        const int j = e / N, i = e - j * N;
-        const double sj = s_norm[j];
-        const int pos = s_rank[j];
+    const int k = sm.k;
+    for (int e = tid; e < N * ncol; e += JC_T) {
+        const int j = e / ncol, i = e - j * ncol;
+        const int gi = c0 + i, pos = sm.rank[j];
+        Rg[gi * N + pos] = sm.V[j][i];
+        const double sj = sm.s[j];
         double w;
-        if (variant == GN_VARIANT_SVD_TRUNCATE) w = pos < k && sj > 0.0 ? T[j * ldt + i] / (sj * sj) : 0.0;
-        else w = sj > 0.0 ? T[j * ldt + i] / (sj * fmax(sj, eps)) : 0.0;
-        Wr[perm[i] * N + pos] = w;
+        if (variant == GN_VARIANT_SVD_TRUNCATE) w = pos < k && sj > 0.0 ? sm.T[j][i] / (sj * sj) : 0.0;
+        else w = sj > 0.0 ? sm.T[j][i] / (sj * fmax(sj, eps)) : 0.0;
+        Wr[perm[gi] * N + pos] = w;
     }
-    (void)Ul;
+    cluster.sync();   // peers' reads of normp done before any CTA exits
 }
 
 size_t variant_smem_bytes() {
-    const size_t qr = sizeof(double) * (static_cast<size_t>(MMAX) * (NMAX + 1) + BW * NMAX + 3 * NMAX + 8 + 2 * NMAX);
-    const size_t jac = sizeof(double) * (static_cast<size_t>(NMAX) * (MMAX + 1) + NMAX) + sizeof(int) * NMAX;
-    return std::max(qr, jac);
+    return sizeof(double) * (static_cast<size_t>(MMAX) * (NMAX + 1) + BW * NMAX + 3 * NMAX + 8 + 2 * NMAX);
 }
 
 // |R_ii| -> max(|R_ii|, eps) with the sign kept (sign(0) = +1); sv_i = R_ii before.
@@ -382,14 +411,18 @@ extern "C" gn_status gn_factors_variant(gn_handle h, const gn_mat* AX, const gn_
             attr = true;
         }
         double* svd = sv ? sv : v.VT;   // sv optional: any N doubles of scratch otherwise
-        double* vt = sv ? v.VT : v.Wq;
         variant_core_kernel<<<1, BT, variant_smem_bytes(), h->stream>>>(
-            v.C, static_cast<int>(rl), static_cast<int>(r), variant, eps, v.Ul, v.Wr, vt, v.perm, svd, v.out, v.Q,
-            v.R);
+            v.C, static_cast<int>(rl), static_cast<int>(r), variant, eps, v.Ul, v.Wr, v.perm, svd, v.out, v.Q, v.R);
         count_launch();
         GN_CUDA_TRY(cudaGetLastError());
-        if (variant != GN_VARIANT_RRQR_RAISE)   // U = Q G (the kernel left G, columns by rank, in v.R)
+        if (variant != GN_VARIANT_RRQR_RAISE) {
+            // Jacobi on the rows of R over one cluster; G (columns by rank) left in v.R, then U = Q G
+            jacobi_cluster_kernel<<<JC_CS, JC_T, 0, h->stream>>>(static_cast<int>(r), variant, eps, v.R, v.Wr, v.perm,
+                                                                 svd, v.out);
+            count_launch();
+            GN_CUDA_TRY(cudaGetLastError());
             GN_TRY(dgemm(h, rl, r, r, 1.0, v.Q, r, 0, v.R, r, 0, 0.0, v.Ul, r, v.inner, v.inner_bytes));
+        }
         int out_h[2] = {0, 0};
         GN_CUDA_TRY(cudaMemcpyAsync(out_h, v.out, sizeof(out_h), cudaMemcpyDeviceToHost, h->stream));
         GN_CUDA_TRY(cudaStreamSynchronize(h->stream));
