@@ -141,7 +141,9 @@ struct OzOperand {
     unsigned long long* mx;   // [passes][rows]
     int rows, K, S;
     int passes;     // ceil(K / OZ_KPASS): pass p is K range [p OZ_KPASS, min(K, (p + 1) OZ_KPASS))
-    int clusters;   // passes x ceil(rows / 32): one cluster of OZ_CS CTAs per pass and 32 rows
+    int tpr;        // K contiguous: threads per row, 32 (K <= 256) or 128
+    int rpc;        // rows per cluster: OZ_CS OZ_ST / tpr (K contiguous) or 32 (rows contiguous)
+    int clusters;   // passes x ceil(rows / rpc): one cluster of OZ_CS CTAs per pass and rpc rows
 };
 struct OzSliceArgs {
     OzOperand op[2];
@@ -165,32 +167,36 @@ __device__ __forceinline__ unsigned long long mx_word(unsigned long long m, floa
     return m ? static_cast<unsigned long long>(row_exponent<float>(m) + 1021) << 52 : 0ull;
 }
 
-// K contiguous (s_k == 1): 4 rows per CTA, 128 threads (four warps) per row,
-// pairs of entries along K (8 entries per thread); the row maximum is a
-// shuffle plus an exchange between the row's four warps.
+// K contiguous (s_k == 1): tpr threads per row (a warp when K <= 256, else four
+// warps), OZ_ST / tpr rows per CTA, pairs of entries along K (8 entries per
+// thread); the row maximum is a shuffle, plus an exchange between the row's
+// warps when there are four.
 template <typename T>
 __device__ __forceinline__ void slice_kcontig(const OzOperand& o, int pass, int q, int rank, OzSmem& sm) {
     const long long koff = static_cast<long long>(pass) * OZ_KPASS;
     const T* src = static_cast<const T*>(o.src) + koff;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int r = tid >> 7, l = tid & 127;
-    const long long i = static_cast<long long>(q) * 32 + rank * 4 + r;
+    const int tpr = o.tpr;   // uniform over the cluster
+    const int r = tid / tpr, l = tid - r * tpr;
+    const long long i = static_cast<long long>(q) * o.rpc + rank * (OZ_ST / tpr) + r;
     const bool live = i < o.rows;
-    const int K = min(OZ_KPASS, o.K - pass * OZ_KPASS);
+    const int K = min(OZ_KPASS, o.K - pass * OZ_KPASS);   // <= 8 tpr
     T v[8];
     unsigned long long m = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int k = 2 * l + 256 * u;
+        const int k = 2 * l + 2 * tpr * u;
         v[2 * u] = live && k < K ? src[i * o.s_row + k] : T(0);
         v[2 * u + 1] = live && k + 1 < K ? src[i * o.s_row + k + 1] : T(0);
         m = max(m, max(abs_bits(v[2 * u]), abs_bits(v[2 * u + 1])));
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
-    if (lane == 0) sm.part[warp][0] = m;
-    __syncthreads();
-    m = max(max(sm.part[4 * r][0], sm.part[4 * r + 1][0]), max(sm.part[4 * r + 2][0], sm.part[4 * r + 3][0]));
+    if (tpr > 32) {   // four warps per row
+        if (lane == 0) sm.part[warp][0] = m;
+        __syncthreads();
+        m = max(max(sm.part[4 * r][0], sm.part[4 * r + 1][0]), max(sm.part[4 * r + 2][0], sm.part[4 * r + 3][0]));
+    }
     if (!live) return;   // no barrier follows in this path
     if (l == 0) o.mx[static_cast<long long>(pass) * o.rows + i] = mx_word(m, static_cast<T*>(nullptr));
     const int e = row_exponent<T>(m);
@@ -198,7 +204,7 @@ __device__ __forceinline__ void slice_kcontig(const OzOperand& o, int pass, int 
     __nv_bfloat16* out = o.out + i * o.ldk + koff;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int k = 2 * l + 256 * u;   // k + 1 < ldk: ldk is K rounded up to 8
+        const int k = 2 * l + 2 * tpr * u;   // k + 1 < ldk: ldk is K rounded up to 8
         if (k < K) write_digits2(fixed49(v[2 * u], e), fixed49(v[2 * u + 1], e), o.S, bias, out + k, o.slice_stride);
     }
 }
@@ -268,9 +274,9 @@ __device__ __forceinline__ void slice_strided(const OzOperand& o, int pass, int 
     }
 }
 
-// Cluster q of the grid slices pass p, rows [32 q', 32 q' + 32) of operand 0
+// Cluster q of the grid slices pass p, rows [rpc q', rpc q' + rpc) of operand 0
 // (FP32 when A32) for q < op[0].clusters, else of operand 1 (FP64), with
-// q - (operand base) = p ceil(rows / 32) + q'.
+// q - (operand base) = p ceil(rows / rpc) + q'.
 template <bool A32>
 __global__ void __launch_bounds__(OZ_ST) oz_slice_kernel(const __grid_constant__ OzSliceArgs args) {
     __shared__ OzSmem sm;
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(OZ_ST) oz_slice_kernel(const __grid_constant__
     const int which = q < args.op[0].clusters ? 0 : 1;
     const OzOperand& o = args.op[which];
     if (which) q -= args.op[0].clusters;
-    const int rq = (o.rows + 31) / 32;
+    const int rq = (o.rows + o.rpc - 1) / o.rpc;
     const int pass = q / rq;
     q -= pass * rq;
     if (which == 0 && A32) {
@@ -305,7 +311,9 @@ OzOperand oz_operand(const void* src, long long s_row, long long s_k, long long 
     o.slice_stride = slice_stride;
     o.mx = mx;
     o.passes = static_cast<int>((K + OZ_KPASS - 1) / OZ_KPASS);
-    o.clusters = o.passes * static_cast<int>((rows + 31) / 32);
+    o.tpr = s_k == 1 ? (K <= 256 ? 32 : 128) : 0;
+    o.rpc = s_k == 1 ? OZ_CS * (OZ_ST / o.tpr) : 32;
+    o.clusters = o.passes * static_cast<int>((rows + o.rpc - 1) / o.rpc);
     return o;
 }
 
@@ -337,18 +345,20 @@ gn_status slice_pair(gn_handle h, const OzOperand& a, int a_f32, const OzOperand
 // the K parts q (passes, each with its own row exponents), added in part
 // order with one rounding each.  Within a part the exact orders 0..3 are
 // summed as integers in units of 2^-35 (one rounding), the rounded orders 4..
-// in FP32 below them.  A thread per column, rows across blockIdx.y (no
-// division per element); each exact order is an integer below 2^24 units, so
-// it converts through a 32-bit integer.
+// in FP32 below them.  A thread per column and row group (no division per
+// element; narrow products fill a block with more rows); each exact order is
+// an integer below 2^24 units, so it converts through a 32-bit integer.
 __global__ void oz_combine_kernel(const float* __restrict__ D, long long d_stride, long long part_stride,
                                   long long ldd, int norders, int nparts, int M, int N,
                                   const unsigned long long* __restrict__ mxa,
                                   const unsigned long long* __restrict__ mxb, long long mxb_part, double alpha,
-                                  double beta, double* __restrict__ C, long long ldc) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+                                  double beta, double* __restrict__ C, long long ldc, int cw) {
+    // a block is cw columns by blockDim.x / cw rows (cw: a power of two >= min(N, 256), >= 32)
+    const int j = blockIdx.x * cw + static_cast<int>(threadIdx.x) % cw;
+    const int rb = static_cast<int>(blockDim.x) / cw;
     if (j >= N) return;
     const int nexact = norders < 4 ? norders : 4;
-    for (int i = blockIdx.y; i < M; i += gridDim.y) {
+    for (int i = blockIdx.y * rb + static_cast<int>(threadIdx.x) / cw; i < M; i += gridDim.y * rb) {
         double* c = C + static_cast<long long>(i) * ldc + j;
         double out = 0.0;
         for (int q = 0; q < nparts; ++q) {   // K parts (passes) in order, as separate passes would add them
@@ -506,12 +516,16 @@ gn_status oz_dgemm(gn_handle h, long long M, long long N, long long K, double al
             // 4 groups of CTAs gives every CTA 7 (order 6; 5 + 0; 4 + 1; 3 + 2)
             p.snake_groups = (norders + 1) / 2;
             GN_TRY(tc_launch(h, &p));
-            const unsigned gx = static_cast<unsigned>((nb + 255) / 256);
-            const unsigned gy = static_cast<unsigned>(
-                std::max<long long>(1, std::min<long long>(M, static_cast<long long>(h->sm_count) * 16 / gx)));
+            int cw = 32;   // a power of two, so that it divides the block's 256 threads
+            while (cw < nb && cw < 256) cw *= 2;
+            const long long rows_per_block = 256 / cw;
+            const unsigned gx = static_cast<unsigned>((nb + cw - 1) / cw);
+            const unsigned gy = static_cast<unsigned>(std::max<long long>(
+                1, std::min<long long>((M + rows_per_block - 1) / rows_per_block,
+                                       static_cast<long long>(h->sm_count) * 16 / gx)));
             oz_combine_kernel<<<dim3(gx, gy), 256, 0, h->stream>>>(
                 o.d, d_stride, part_stride, o.ldd, norders, S, static_cast<int>(M), static_cast<int>(nb), o.mxa,
-                o.mxb + j0, N, alpha, beta_grp, C + j0, ldc);
+                o.mxb + j0, N, alpha, beta_grp, C + j0, ldc, cw);
             count_launch();
             GN_CUDA_TRY(cudaGetLastError());
         }
