@@ -1845,7 +1845,7 @@ size_t qr_blk_bytes(long long M, long long N) {
     const long long nblk = (N + QR_BB - 1) / QR_BB;
     return al256d(qr_oz_crit_bytes(M)) + al256d(sizeof(double) * nblk * QR_BB * QR_BB) +
            al256d(sizeof(double) * QR_BB * QR_BB) + 2 * al256d(sizeof(double) * QR_BB * N) +
-           al256d(sizeof(double) * QR_BB * QR_BB) + al256d(sizeof(double) * M * QR_BB) + 1024;
+           al256d(sizeof(double) * QR_BB * QR_BB) + al256d(sizeof(double) * nblk * M * QR_BB) + 1024;
 }
 
 struct QrBlk {
@@ -1854,7 +1854,7 @@ struct QrBlk {
     void* oz_crit;
     size_t oz_crit_bytes;
     double *TB, *GB, *Z1s, *Z2s, *Z1c;
-    double* UB;   // U_b = V_b T_b (M_p x b_w, ld QR_BB) of the block being applied
+    double* UB;   // U_b = V_b T_b (M_p x b_w, ld QR_BB) of every block but the last, at UB + b M QR_BB
 };
 
 bool qr_blk_carve(long long M, long long N, void* oz, size_t oz_bytes, QrBlk* b) {
@@ -1876,7 +1876,7 @@ bool qr_blk_carve(long long M, long long N, void* oz, size_t oz_bytes, QrBlk* b)
     b->Z1s = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * N));
     b->Z2s = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * N));
     b->Z1c = reinterpret_cast<double*>(take(sizeof(double) * QR_BB * QR_BB));
-    b->UB = reinterpret_cast<double*>(take(sizeof(double) * M * QR_BB));
+    b->UB = reinterpret_cast<double*>(take(sizeof(double) * nblk * M * QR_BB));
     return off <= oz_bytes;
 }
 
@@ -1965,11 +1965,12 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
                             bk.oz_crit_bytes));
             launch_ut_inverse(h, bk.GB, QR_BB, q.tau + b0, static_cast<int>(bw), TB, QR_BB);
             GN_CUDA_TRY(cudaGetLastError());
-            // the next block's columns already have the block before this one (side stream),
-            // which has also stopped reading the previous U_b
+            // the next block's columns already have the block before this one (side stream)
             if (pending) GN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-            // U_b = V_b T_b: each update below is then two products, Z = U_b^T C and C -= V_b Z
-            GN_TRY(oz_dgemm(h, Mp, bw, bw, 1.0, VB, 0, N, 0, TB, QR_BB, 0, 0.0, bk.UB, QR_BB, bk.oz_crit,
+            // U_b = V_b T_b (kept for the formation of Q): each update below is then two
+            // products, Z = U_b^T C and C -= V_b Z
+            double* UB = bk.UB + bi * M * QR_BB;
+            GN_TRY(oz_dgemm(h, Mp, bw, bw, 1.0, VB, 0, N, 0, TB, QR_BB, 0, 0.0, UB, QR_BB, bk.oz_crit,
                             bk.oz_crit_bytes));
             const long long nnext = std::min<long long>(QR_BB, N2);
             const long long nsec = std::min<long long>(QR_BB, N2 - nnext);
@@ -1981,12 +1982,12 @@ gn_status qr_factor(gn_handle h, double* W, long long M, long long N, long long 
                 gn_handle_s side = *h;
                 side.stream = h->side;
                 GN_TRY(block_apply_u(&side, W + b0 * ld + b0 + bw + nnext, ld, Mp, nsec + nrest, VB, N,
-                                     static_cast<int>(bw), bk.UB, QR_BB, bk.Z1s, bk.oz_side, bk.oz_side_bytes));
+                                     static_cast<int>(bw), UB, QR_BB, bk.Z1s, bk.oz_side, bk.oz_side_bytes));
                 GN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
                 side_used = true;
             }
             pending = nsec > 0;
-            GN_TRY(block_apply_u(h, W + b0 * ld + b0 + bw, ld, Mp, nnext, VB, N, static_cast<int>(bw), bk.UB, QR_BB,
+            GN_TRY(block_apply_u(h, W + b0 * ld + b0 + bw, ld, Mp, nnext, VB, N, static_cast<int>(bw), UB, QR_BB,
                                  bk.Z1c, bk.oz_crit, bk.oz_crit_bytes));
         }
     } else {
@@ -2103,8 +2104,8 @@ gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double
     static_assert(QR_BB == QR_SB, "the blocked factorization's T_b serve the Q formation's blocks");
     QrBlk bk;
     if (qr_blocked_path(h, M, N, oz, oz_bytes, &bk)) {
-        // the factorization left V zero above each block's diagonal and T_b of
-        // every block but the last in bk.TB (same V_b, tau and construction)
+        // the factorization left V zero above each block's diagonal, and T_b and
+        // U_b = V_b T_b of every block but the last in bk.TB and bk.UB
         const long long nblk = (N + QR_BB - 1) / QR_BB;
         for (long long bi = nblk - 1; bi >= 0; --bi) {
             const long long j0 = bi * QR_BB;
@@ -2112,13 +2113,17 @@ gn_status form_q_tc(gn_handle h, const QrWs& q, long long M, long long N, double
             const double* Vb = q.V + j0 * N + j0;
             double* Qs = Q + j0 * ldq + j0;
             double* Tb = bk.TB + bi * QR_BB * QR_BB;
-            if (bi == nblk - 1) {
-                GN_TRY(oz_dgemm(h, nbb, nbb, Mp, 1.0, Vb, 0, N, 1, Vb, N, 0, 0.0, bk.GB, QR_BB, bk.oz_side,
-                                bk.oz_side_bytes));
-                launch_ut_inverse(h, bk.GB, QR_BB, q.tau + j0, static_cast<int>(nbb), Tb, QR_BB);
-                GN_CUDA_TRY(cudaGetLastError());
-            }
             GN_TRY(block_vtq(h, Vb, N, Mp, nbb, Qs, ldq, Nq, bk.Z1s, bk.oz_side, bk.oz_side_bytes));
+            if (bi < nblk - 1) {   // Q_s -= U_b (V_b^T Q_s) with the factorization's U_b = V_b T_b
+                GN_TRY(oz_dgemm(h, Mp, Nq, nbb, -1.0, bk.UB + bi * M * QR_BB, 0, QR_BB, 0, bk.Z1s, Nq, 0, 1.0, Qs,
+                                ldq, bk.oz_side, bk.oz_side_bytes));
+                continue;
+            }
+            // the last block: its T here, then Q_s -= V_b (T_b (V_b^T Q_s))
+            GN_TRY(oz_dgemm(h, nbb, nbb, Mp, 1.0, Vb, 0, N, 1, Vb, N, 0, 0.0, bk.GB, QR_BB, bk.oz_side,
+                            bk.oz_side_bytes));
+            launch_ut_inverse(h, bk.GB, QR_BB, q.tau + j0, static_cast<int>(nbb), Tb, QR_BB);
+            GN_CUDA_TRY(cudaGetLastError());
             GN_TRY(oz_dgemm(h, nbb, Nq, nbb, 1.0, Tb, 0, QR_BB, 0, bk.Z1s, Nq, 0, 0.0, bk.Z2s, Nq, bk.oz_side,
                             bk.oz_side_bytes));
             GN_TRY(oz_dgemm(h, Mp, Nq, nbb, -1.0, Vb, 0, N, 0, bk.Z2s, Nq, 0, 1.0, Qs, ldq, bk.oz_side,
