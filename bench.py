@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--h2d-streams", type=int, default=1, help="host-to-device copy streams of the e2e loop")
     ap.add_argument("--e2e-sets", type=int, default=0, help="device buffer sets of the e2e loop (0: in-flight + ahead)")
     ap.add_argument("--e2e-ahead", type=int, default=2, help="steps whose input copies are queued ahead in the e2e loop")
-    ap.add_argument("--e2e-reps", type=int, default=3, help="timed repetitions of the e2e loop (the median is reported)")
+    ap.add_argument("--e2e-reps", type=int, default=5, help="timed repetitions of the e2e loop (the median is reported)")
     ap.add_argument("--only", default=None, choices=["batched", "adjoint", "fp64_cases"],
                     help="run one side measurement alone and print its JSON (for profiling it)")
     return ap.parse_args()
@@ -529,10 +529,14 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
     ev_out = [torch.cuda.Event() for _ in range(nset)]
     step_handle = {}
 
+    copy_ev = []   # per step: events around its input copies on the first copy stream
+
     def prefetch(i):
         b = i % nset
         for q in hs:
             q.wait_event(ev_done[b])              # the set's previous step has finished computing
+        c0 = torch.cuda.Event(enable_timing=True)
+        c0.record(hs[0])
         for d_, h_ in zip(ins[b][0], hosts):
             if h_.numel() * h_.element_size() >= (64 << 20) and h_.dim() >= 1 and h_.shape[0] >= nh:
                 step = (h_.shape[0] + nh - 1) // nh   # row blocks, one per copy stream
@@ -544,6 +548,9 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
                     d_.copy_(h_, non_blocking=True)
         for q, ev in zip(hs, ev_in[b]):
             ev.record(q)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c1.record(hs[0])
+        copy_ev.append((c0, c1))
 
     def enqueue(i):
         b, j = i % nset, i % nf
@@ -590,8 +597,9 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
     torch.cuda.synchronize()
     # the median of a few timed repetitions of the K steps: a rare host-side
     # stall of tens of ms (seen in about one run in six) otherwise decides the figure
-    reps_ms = []
+    reps_ms, reps_copy, reps_idle = [], [], []
     for _ in range(max(1, a.e2e_reps)):
+        copy_ev.clear()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(hs[0])
@@ -601,6 +609,11 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
         e1.record(dstream)                   # after the last step's results are out (which waits for all)
         torch.cuda.synchronize()
         reps_ms.append(e0.elapsed_time(e1) / a.steps)
+        # the input copies of each step, and the host-to-device stream's idle time between them
+        durs = sorted(c0.elapsed_time(c1) for c0, c1 in copy_ev)
+        reps_copy.append(durs[len(durs) // 2])
+        reps_idle.append(sum(max(0.0, copy_ev[t][1].elapsed_time(copy_ev[t + 1][0]))
+                             for t in range(len(copy_ev) - 1)))
     ms = sorted(reps_ms)[len(reps_ms) // 2]
     # the host link's own rates on this machine (pinned, one stream each way), for reading the figure above
     big = hosts[0]
@@ -624,6 +637,7 @@ def e2e_measurement(a, gn, Hs, nf, dev, m, n, r, l, Aop, Xop, Yop, Ab, Xb, Yb, b
             "ms_per_step": ms, "h2d_gbs_one_stream": h2d_gbs, "d2h_gbs_one_stream": d2h_gbs,
             "h2d_streams": nh, "buffer_sets": nset, "ahead": ahead,
             "reps": len(reps_ms), "statistic": "median", "ms_per_step_reps": reps_ms,
+            "h2d_ms_per_step_median_reps": reps_copy, "h2d_idle_ms_reps": reps_idle,
             "copy_floor_ms": max(h2d / h2d_gbs, d2h / d2h_gbs) / 1e6}
 
 
