@@ -1,7 +1,10 @@
 // Tensor-core engine for the sketch products of generalized Nystrom
 // (Algorithm 2, step 2: AX and Y^T A) and for the split-precision core product
-// C = (Y^T A) X.  One persistent, warp-specialised sm_103a kernel computes up
-// to four independent GEMMs D_g = sum_s A_{g,s} B_{g,s} in a single launch:
+// C = (Y^T A) X, and for the digit-sliced FP64 products (one GEMM per digit
+// order).  One persistent, warp-specialised sm_103a kernel computes up to
+// TC_MAX_GEMMS independent GEMMs D_g = sum_s A_{g,s} B_{g,s} in a single launch
+// (any number in grouped mode), tiles in round-robin or boustrophedon order,
+// optionally as K parts (added into D, or stored apart, K-aligned or not):
 //
 //   warp 0      : TMA producer -- cp.async.bulk.tensor tiles of both operands
 //                 into a shared-memory ring (128B swizzle; 4 stages of 48 KB
@@ -237,9 +240,10 @@ struct TileCoord {
     int half;   // 0: whole K range; c >= 1: part c of the K range (of ksplit parts, or of 2)
 };
 
-// GEMM descriptors and tensor maps live in the kernel parameters (up to four
-// GEMMs) or, in grouped mode, in device memory (any number of GEMMs; the
-// batched path).  Tiles are numbered GEMM after GEMM (tile_base ascending).
+// GEMM descriptors and tensor maps live in the kernel parameters (up to
+// TC_MAX_GEMMS GEMMs) or, in grouped mode, in device memory (any number of
+// GEMMs; the batched path).  Tiles are numbered GEMM after GEMM (tile_base
+// ascending).
 template <bool GROUPED>
 __device__ __forceinline__ const TcGemm* gemm_of(const TcParams& p, int i) {
     return GROUPED ? p.gg + i : p.g + i;
