@@ -124,6 +124,14 @@ def test_apply_and_update_host_validation():
     assert L.gn_update(None, None, None, None, None, None, None, 0) == 1
 
 
+def test_backward_saved_rejects_null_arguments():
+    """gn_backward_saved checks its arguments on the host before looking at
+    the handle's record of the last front."""
+    import paper_2009_11392_gb300 as gn
+    L = gn.lib
+    assert L.gn_backward_saved(None, None, None, None, None, None, 0) == 1
+
+
 def test_sketch_state_calls_reject_null_arguments():
     import paper_2009_11392_gb300 as gn
     L = gn.lib
