@@ -12,8 +12,11 @@ Section 5.1.2 detector / Section 5.1.1 truncation (mode AUTO).
 Steps run on --inflight handles (default 5), each with its own CUDA stream,
 workspace and outputs: step i's core is enqueued without a host wait
 (GN_CORE_DEFER) and finished once the next steps are enqueued, so one step's
-latency-bound FP64 core overlaps the following steps' sketches and cores.  The latency
-of a single approximation (one in flight) is reported beside it.
+latency-bound FP64 core overlaps the following steps' sketches and cores.  The K
+steps are timed --reps times (default 3), each repetition exactly K steps between
+a barrier and device synchronizations; the median repetition is the value and
+all of them are in the line.  The latency of a single approximation (one in
+flight) is reported beside it.
 
 Prints ONE JSON line (rank 0).  Also reported, outside the timed region: the
 measured FP8 (e4m3) and FP64 peaks, the split-BF16 and e4m3 paths, the plain
@@ -70,6 +73,7 @@ def parse():
     ap.add_argument("--e2e-sets", type=int, default=0, help="device buffer sets of the e2e loop (0: in-flight + ahead)")
     ap.add_argument("--e2e-ahead", type=int, default=2, help="steps whose input copies are queued ahead in the e2e loop")
     ap.add_argument("--e2e-reps", type=int, default=5, help="timed repetitions of the e2e loop (the median is reported)")
+    ap.add_argument("--reps", type=int, default=3, help="timed repetitions of the K steps (the median is reported)")
     ap.add_argument("--only", default=None, choices=["batched", "adjoint", "fp64_cases"],
                     help="run one side measurement alone and print its JSON (for profiling it)")
     return ap.parse_args()
@@ -379,22 +383,30 @@ def main():
     sampler = ClockSampler(gpu_id_for_smi(local))
     sampler.start()
     time.sleep(0.3)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    launches0 = gn.kernel_launches()
-    elapsed_ms = timed(a.steps, nf, evs)
-    launches = gn.kernel_launches() - launches0
+    # a few timed repetitions of exactly K steps each (barrier and synchronize
+    # around every one, max over ranks); the median one is reported, all of them
+    # are in the line: a host-side stall of tens of ms otherwise decides a
+    # region of ~0.1 s
+    reps = []   # (elapsed ms, launches, mean sketch ms)
+    for _ in range(max(1, a.reps)):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches0 = gn.kernel_launches()
+        el = timed(a.steps, nf, evs)
+        nl = gn.kernel_launches() - launches0
+        sk = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+        if dist:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        reps.append((el, nl, sk))
     clocks = sampler.stop()
-    sketch_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
     for Hj in Hs:
         if Hj.sync_status() != 0:
             raise RuntimeError("device status after timed steps")
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms, launches, sketch_ms = sorted(reps)[len(reps) // 2]
     per_step_ms = elapsed_ms / a.steps
     value = world * a.steps / (elapsed_ms / 1e3)
 
@@ -459,6 +471,8 @@ def main():
             "metric": METRIC if a.op == "bf16" else METRIC.replace("BF16", "e4m3 block-scaled"),
             "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak",
+            "reps": len(reps), "statistic": "median of the timed repetitions of K steps",
+            "ms_per_step_reps": [el / a.steps for el, _, _ in reps],
             "vs_baseline": None, "dtype": a.op, "data": "synthetic (seeded low-rank + noise, Gaussian sketches)",
             "config": config_dict(a),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
