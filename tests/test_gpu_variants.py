@@ -159,3 +159,25 @@ def test_diag_raise_any_r(gn, H):
     with pytest.raises(gn.GNError) as ei:
         _run(gn, H, AX, YtA, X, floor, gn.SVD_RAISE, cu)
     assert ei.value.status == 8
+
+
+@pytest.mark.parametrize("r,l", [(9, 5), (37, 19), (128, 64)])
+def test_svd_variants_cluster_edges(gn, H, r, l):
+    """The Jacobi sweeps run over an 8-CTA cluster, each CTA holding a slice of
+    the columns: r = 9 leaves CTAs with no column, r = 37 is odd (a dummy player
+    every round), r = 128 and r + l = 192 are the largest core.  Singular values
+    against LAPACK's, and both SVD variants' approximants against the oracle's."""
+    m, n = 700, 500
+    A, X, Y, AX, YtA, cu = _state(gn, H, m, n, r, l, 9 + r)
+    C = YtA @ X
+    s = np.linalg.svd(C, compute_uv=False)
+    floor, gap = _gap_floor(s)
+    assert gap > 1.05
+    k, F, G, sv = _run(gn, H, AX, YtA, X, floor, gn.SVD_RAISE, cu)
+    assert k == r
+    assert np.max(np.abs(sv - s)) <= 1e-12 * s[0]
+    Fo, Go = O.perturbed_core_factors(AX, YtA, X, floor, "svd")
+    assert rel(F @ G, Fo @ Go) <= 1e-9
+    k, F, G, sv = _run(gn, H, AX, YtA, X, floor, gn.SVD_TRUNCATE, cu)
+    assert k == int(np.sum(s > floor))
+    assert rel(F @ G, O.sgn_svd(A, X, Y, floor)) <= 1e-9
