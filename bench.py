@@ -60,9 +60,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gn", choices=["gn", "reference"])
-    ap.add_argument("--m", type=int, default=32768)
-    ap.add_argument("--n", type=int, default=16384)
-    ap.add_argument("--r", type=int, default=1000)
+    ap.add_argument("--m", "--rows", type=int, default=32768)
+    ap.add_argument("--n", "--cols", type=int, default=16384)
+    ap.add_argument("--r", "--sketch-r", type=int, default=1000,
+                    help="r (l = r / 2); --rows, --cols, --sketch-r: spellings that launchers do not take for their own options")
     ap.add_argument("--inflight", type=int, default=5, help="approximations in flight (handles / streams)")
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements and the CPU baseline")
     ap.add_argument("--op", default="bf16", choices=["bf16", "e4m3"],
