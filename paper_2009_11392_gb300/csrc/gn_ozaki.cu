@@ -8,14 +8,17 @@
 //     as sum_s d_s 2^{-7(s+1)} with balanced base-128 digits |d_s| <= 64 (the
 //     plain digits of the value plus a bias of 64 per position, less 64); slice
 //     s holds d_s 2^{-7(s+1)}, exact in BF16.  Columns of B the same with 2^-eb_j.
-//     Both operands of a pass are sliced in one launch.
+//     Both operands of up to four passes are sliced in one launch.
 //   * the slice products of one order o = s + t carry the unit 2^{-7(o+2)}; each
 //     term is at most 2^12 units, so the FP32 accumulation of the (o+1) products
 //     of order o over K terms is exact while (o+1) K 2^12 <= 2^24.  A pass covers
 //     at most 1024 of K: orders 0..3 are exact; orders 4..6 are rounded, their
 //     rounding sits below 2^-52 of the leading term.
 //   * one launch of the multi-GEMM engine computes D_o = sum_{s+t=o} A_s B_t for
-//     every kept order; C = beta C + alpha 2^{ea_i + eb_j} sum_o D_o in FP64.
+//     every kept order and every pass of the group (the passes as K-aligned
+//     parts stored apart; the orders of 7, 6, ..., 1 slice products paired on
+//     the CTAs by the boustrophedon tile order); C = beta C + sum over the
+//     passes of alpha 2^{ea_i + eb_j} sum_o D_o in FP64, the passes in order.
 // Orders above 6 are dropped: with 7 digits per operand the error per element is
 // about 2^-46 K max_k|a_ik| max_k|b_kj|, the size of an FP64 product's own
 // worst-case rounding error.  FP32 operands take 7 digits too: the digits cover
